@@ -1,0 +1,1 @@
+"""FP64 oracle (test infrastructure only; see oracle.py)."""
