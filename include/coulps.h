@@ -1,0 +1,211 @@
+/*
+ * coulps — lattice path-integral Coulomb energy sampler for one GB300 GPU.
+ *
+ * The method (Sugihara, Higo & Nakamura, JPSJ 2014): the N-body Coulomb energy
+ * Eq. (s1) is written, through the two-point function of a free scalar field
+ * (Eqs. (2body), (path)), as the lattice expectation value Eq. (nsum)
+ *
+ *     E_N ~ < (sum_i q_i phi_{n_i})^2 - sum_i (q_i phi_{n_i})^2 >,
+ *
+ * taken under exp(-H_L), H_L = 1/2 sum_<m,n> (phi_m - phi_n)^2 (Eq. (proplat)),
+ * with phi = 0 outside the box (the paper's open-boundary modification of
+ * Eq. (phi)).  The expectation is estimated by Markov-chain Monte Carlo:
+ * heatbath updates Eq. (phi), optionally over-relaxation reflections, and the
+ * sample mean Eq. (nsum2).
+ *
+ * Conventions for every entry point:
+ *   - Return value: COULPS_OK (0) or a negative status below.  No C++
+ *     exception ever crosses this interface.  On error nothing is left half
+ *     done unless the description says otherwise.
+ *   - Sites are 0-based (x, y, z) with 0 <= x < Lx etc.; x is the fastest
+ *     index of every natural-order host array, i.e. element x + Lx*(y + Ly*z).
+ *   - The library owns every device buffer it allocates.  Device memory comes
+ *     from the allocator installed with coulps_set_allocator (for example a
+ *     framework's caching allocator) or, by default, from cudaMallocAsync on
+ *     the handle's stream.  Host pointers passed in are only read or written
+ *     during the call; the caller keeps ownership.
+ *   - Work is queued asynchronously on the handle's CUDA stream unless a call
+ *     says it synchronises.  Device-side failures (a timed-out wait, a
+ *     non-finite sample) are recorded in a per-lattice error word and reported
+ *     by the next synchronising call.
+ *   - A handle must not be used from two host threads at once.
+ */
+#ifndef COULPS_H
+#define COULPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define COULPS_OK 0
+#define COULPS_EINVAL (-1)       /* bad argument (sizes, pointers, ranges)      */
+#define COULPS_ENOMEM (-2)       /* device or host allocation failed            */
+#define COULPS_ECUDA (-3)        /* a CUDA runtime call failed                  */
+#define COULPS_ETIMEOUT (-4)     /* a device-side bounded wait gave up          */
+#define COULPS_ENONFINITE (-5)   /* a sample or running sum became non-finite   */
+#define COULPS_EIO (-6)          /* checkpoint file could not be read/written   */
+#define COULPS_ECORRUPT (-7)     /* checkpoint checksum / header mismatch       */
+#define COULPS_EUNSUPPORTED (-8) /* shape or mode this build does not handle    */
+
+#define COULPS_F32 0 /* field and sweeps in FP32, estimator sums in FP64 */
+#define COULPS_F64 1 /* field, sweeps and estimator in FP64              */
+
+typedef struct coulps_lattice *coulps_lattice_t;
+typedef struct coulps_charges *coulps_charges_t;
+
+/* Human-readable text for a status code (static storage, never NULL). */
+const char *coulps_error_string(int status);
+
+/* Library version as 10000*major + 100*minor + patch. */
+int coulps_version(void);
+
+/* ---- device memory ----------------------------------------------------- */
+/* Allocation hooks.  alloc(bytes, stream, ctx) returns device memory usable on
+ * `stream` or NULL; free(ptr, stream, ctx) releases it.  Passing two NULLs
+ * restores the default (cudaMallocAsync / cudaFreeAsync).  Affects handles
+ * created afterwards; each handle remembers the hooks it was created with. */
+typedef void *(*coulps_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*coulps_free_fn)(void *ptr, void *stream, void *ctx);
+int coulps_set_allocator(coulps_alloc_fn alloc, coulps_free_fn free_fn, void *ctx);
+
+/* ---- lattice ----------------------------------------------------------- */
+/* Create n_chains independent Markov chains of the field phi on an
+ * Lx x Ly x Lz box (Eq. (proplat)'s lattice, phi = 0 outside), cold start
+ * phi = 0, on the current CUDA device.
+ *   precision: COULPS_F32 or COULPS_F64.
+ *   seed:      Philox key (low word, high word) of every random draw.
+ *   stream:    cudaStream_t to queue work on (NULL = legacy default stream).
+ * Limits: 1 <= Lx <= 512, 1 <= Ly, Lz <= 65535, 1 <= n_chains <= 65535,
+ * and the quad index (z*Ly + y)*ceil(Lx/8) must fit in 32 bits.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+int coulps_lattice_create(int Lx, int Ly, int Lz, int n_chains, int precision,
+                          uint64_t seed, void *stream, coulps_lattice_t *out);
+
+/* Release a lattice (queues the frees on its stream).  NULL is ignored.
+ * Charge sets created on it must be destroyed first. */
+void coulps_lattice_destroy(coulps_lattice_t lat);
+
+/* Change the stream later work is queued on. */
+int coulps_set_stream(coulps_lattice_t lat, void *stream);
+
+/* info[0..9] = Lx, Ly, Lz, n_chains, precision, row stride W (elements),
+ * pass counter, device bytes held, tile rows TY, slab depth DZ. */
+int coulps_lattice_info(coulps_lattice_t lat, int64_t info[10]);
+
+/* Tile shape of the half-sweep kernel: ty rows of y per CTA, dz planes of z
+ * per CTA (0 = keep).  Used by the autotuner; results do not depend on it.
+ * Errors: EINVAL (ty*W/4 > 1024 threads, ty < 1, dz < 1). */
+int coulps_set_tile(coulps_lattice_t lat, int ty, int dz);
+
+/* Copy chain `chain`'s field to / from a host array of Lx*Ly*Lz doubles in
+ * natural order.  Synchronises the stream.  field_set does not change the
+ * pass counter.  Errors: EINVAL, ECUDA, and any recorded device error. */
+int coulps_field_get(coulps_lattice_t lat, int chain, double *host_xyz);
+int coulps_field_set(coulps_lattice_t lat, int chain, const double *host_xyz);
+
+/* n_compound compound sweeps on every chain.  A compound sweep is n_hb
+ * heatbath passes (Eq. (phi) at every site) followed by n_or over-relaxation
+ * passes (phi -> S/3 - phi, S the sum of the six neighbours); a pass is the
+ * red half-sweep ((x+y+z) even) then the black one.  Each pass advances the
+ * pass counter by one; heatbath pass p of chain k draws its uniforms from
+ * Philox4x32-10 with counter (quad, p, k, colour).  Asynchronous.
+ * Errors: EINVAL (negative counts), ECUDA. */
+int coulps_sweep(coulps_lattice_t lat, int n_compound, int n_hb, int n_or);
+
+/* Wait for the lattice's stream and report any recorded device error. */
+int coulps_sync(coulps_lattice_t lat);
+
+/* ---- charge sets and the estimator ------------------------------------- */
+/* Register n point charges q[i] at sites site_xyz[3i..3i+2] of lattice `lat`
+ * (copied; the arrays are the caller's).  All chains of the lattice are
+ * measured against this set.  Coincident sites are allowed.  log_capacity
+ * samples of (Q, P, e) per chain are kept on the device for
+ * coulps_samples (0 = keep none).  Errors: EINVAL (site outside the box,
+ * n < 0, non-finite q), ENOMEM, ECUDA. */
+int coulps_charges_create(coulps_lattice_t lat, int64_t n, const int32_t *site_xyz,
+                          const double *q, int64_t log_capacity, coulps_charges_t *out);
+
+void coulps_charges_destroy(coulps_charges_t ch);
+
+/* Take one sample per chain of the current fields (one term of Eq. (nsum2)):
+ *   Q = sum_i q_i phi(r_i),  P = sum_i (q_i phi(r_i))^2,  e = Q^2 - P,
+ * Q and P summed in FP64 in a fixed order (bitwise reproducible), e formed in
+ * FP64; then update the per-chain running sums of e and e^2 and the batch
+ * sums.  Asynchronous.  Errors: EINVAL (charges of another lattice), ECUDA. */
+int coulps_measure(coulps_lattice_t lat, coulps_charges_t ch);
+
+/* n_therm unmeasured compound sweeps, then n_meas measured ones (one
+ * coulps_measure after each).  The measured loop is captured once into a
+ * CUDA graph and replayed.  Asynchronous.  Errors: EINVAL, ECUDA. */
+int coulps_run(coulps_lattice_t lat, coulps_charges_t ch, int n_therm, int n_meas,
+               int n_hb, int n_or);
+
+/* Synchronise and return the estimate of E_N pooled over all chains:
+ *   mean      = sum of all samples / their number (Eq. (nsum2)),
+ *   stderr_bm = batch-means standard error (chains give independent batches;
+ *               the batch length doubles as samples accumulate so that
+ *               between 32 and 64 batches per chain are kept),
+ *   tau_int   = integrated autocorrelation time in samples, from the ratio of
+ *               the batch-mean variance to the per-sample variance,
+ *   n         = number of samples (all chains).
+ * Any pointer may be NULL.  Errors: ECUDA, ETIMEOUT, ENONFINITE. */
+int coulps_estimate(coulps_charges_t ch, double *mean, double *stderr_bm, double *tau_int,
+                    int64_t *n);
+
+/* Synchronise and copy the logged samples: QPe[(s*n_chains + k)*3 + {0,1,2}]
+ * = (Q, P, e) of sample s of chain k, for s < min(samples taken, cap,
+ * log_capacity).  *n receives the number of samples copied per chain. */
+int coulps_samples(coulps_charges_t ch, double *QPe, int64_t cap, int64_t *n);
+
+/* Forget all samples (running sums, batches and log). Asynchronous. */
+int coulps_reset_stats(coulps_charges_t ch);
+
+/* Replace the positions and values of the ch's n charges (same n as at
+ * creation) from host arrays, asynchronously: the arrays are converted and
+ * staged in library-owned pinned memory before the call returns, so the
+ * caller may reuse them at once.  Running sums are kept.  Errors: EINVAL
+ * (site outside the box, non-finite q), ECUDA. */
+int coulps_charges_update(coulps_charges_t ch, const int32_t *site_xyz, const double *q);
+
+/* Per-chain estimator state, COULPS_STAT_STRIDE doubles per chain:
+ *   [0] samples n, [1] sum e, [2] sum e^2, [3] open batch sum, [4] open batch
+ *   count, [5] batch length b, [6] completed batches m (32 <= m < 64 once
+ *   n >= 32 b), [7] unused, [8 + j] sum of e over completed batch j.
+ * coulps_chain_stats synchronises and copies n_chains rows into out (cap =
+ * doubles available).  coulps_pool_stats is pure host arithmetic: it pools
+ * any number of such rows (for example gathered from several processes, each
+ * running its own chains with its own seed) exactly as coulps_estimate does,
+ * summing in row order.  Rows must share one batch length.  Errors: EINVAL. */
+#define COULPS_STAT_STRIDE 72
+int coulps_chain_stats(coulps_charges_t ch, double *out, int64_t cap);
+int coulps_pool_stats(const double *stats, int64_t n_rows, double *mean, double *stderr_bm,
+                      double *tau_int, int64_t *n);
+
+/* ---- kernel timing ----------------------------------------------------- */
+/* With profiling on, every half-sweep launched by coulps_sweep (and by
+ * coulps_run, which then launches directly instead of replaying its graph)
+ * is bracketed by CUDA events on the lattice stream.  coulps_kernel_times
+ * synchronises and returns, since profiling was enabled or last read:
+ *   out[0] total ms of heatbath half-sweeps, out[1] their count,
+ *   out[2] total ms of over-relaxation half-sweeps, out[3] their count,
+ * and restarts the accumulation. */
+int coulps_set_profiling(coulps_lattice_t lat, int enable);
+int coulps_kernel_times(coulps_lattice_t lat, double out[4]);
+
+/* ---- checkpoint -------------------------------------------------------- */
+/* Save / restore the full sampler state: fields of all chains, the pass
+ * counter, seed and shape, and (if ch != NULL) the estimator state of the
+ * charge set, with a checksum.  Restoring then continuing gives bitwise the
+ * same samples as an uninterrupted run.  Synchronises.
+ * Errors: EIO, ECORRUPT (checksum or shape mismatch), ECUDA. */
+int coulps_checkpoint_save(coulps_lattice_t lat, coulps_charges_t ch, const char *path);
+int coulps_checkpoint_load(coulps_lattice_t lat, coulps_charges_t ch, const char *path);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* COULPS_H */

@@ -1,0 +1,336 @@
+"""Python binding of the coulps C ABI (include/coulps.h).
+
+Argument marshalling only: every step of the sampler runs in libcoulps.so.
+The module-level functions carry the C names; ``Lattice`` and ``Charges`` wrap
+the handles.  PyTorch supplies device memory (its caching allocator is
+installed as the library's allocator) and streams.
+
+If libcoulps.so cannot be loaded this module raises on first use; there is no
+fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+
+import numpy as np
+
+_PKG = Path(__file__).resolve().parent
+LIB_PATH = _PKG / "libcoulps.so"
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENONFINITE, EIO, ECORRUPT, EUNSUPPORTED = (
+    0, -1, -2, -3, -4, -5, -6, -7, -8)
+F32, F64 = 0, 1
+
+# Every symbol include/coulps.h declares (checked by the CPU test suite).
+EXPORTS = (
+    "coulps_error_string", "coulps_version", "coulps_set_allocator",
+    "coulps_lattice_create", "coulps_lattice_destroy", "coulps_set_stream",
+    "coulps_lattice_info", "coulps_set_tile", "coulps_field_get", "coulps_field_set",
+    "coulps_sweep", "coulps_sync", "coulps_charges_create", "coulps_charges_destroy",
+    "coulps_measure", "coulps_run", "coulps_estimate", "coulps_samples",
+    "coulps_reset_stats", "coulps_checkpoint_save", "coulps_checkpoint_load",
+    "coulps_charges_update", "coulps_chain_stats", "coulps_pool_stats", "coulps_set_profiling",
+    "coulps_kernel_times",
+)
+STAT_STRIDE = 72
+
+
+class CoulpsError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {error_string(status)} ({status})")
+
+
+_lib = None
+_ALLOC_T = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_T = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+_keep = []  # ctypes callbacks must outlive the library's use of them
+
+
+def load(path: str | Path | None = None):
+    """Load libcoulps.so (built in-tree by __graft_entry__.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = Path(path) if path else LIB_PATH
+    if not p.exists():
+        raise RuntimeError(f"libcoulps.so not found at {p}: build it first "
+                           "(python -c 'import __graft_entry__ as g; g.build()')")
+    L = ctypes.CDLL(str(p))
+    vp, i32, i64, u64, f64 = (ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64,
+                              ctypes.c_double)
+    P = ctypes.POINTER
+    sig = {
+        "coulps_error_string": (ctypes.c_char_p, [i32]),
+        "coulps_version": (i32, []),
+        "coulps_set_allocator": (i32, [_ALLOC_T, _FREE_T, vp]),
+        "coulps_lattice_create": (i32, [i32, i32, i32, i32, i32, u64, vp, P(vp)]),
+        "coulps_lattice_destroy": (None, [vp]),
+        "coulps_set_stream": (i32, [vp, vp]),
+        "coulps_lattice_info": (i32, [vp, P(i64)]),
+        "coulps_set_tile": (i32, [vp, i32, i32]),
+        "coulps_field_get": (i32, [vp, i32, P(f64)]),
+        "coulps_field_set": (i32, [vp, i32, P(f64)]),
+        "coulps_sweep": (i32, [vp, i32, i32, i32]),
+        "coulps_sync": (i32, [vp]),
+        "coulps_charges_create": (i32, [vp, i64, P(ctypes.c_int32), P(f64), i64, P(vp)]),
+        "coulps_charges_destroy": (None, [vp]),
+        "coulps_measure": (i32, [vp, vp]),
+        "coulps_run": (i32, [vp, vp, i32, i32, i32, i32]),
+        "coulps_estimate": (i32, [vp, P(f64), P(f64), P(f64), P(i64)]),
+        "coulps_samples": (i32, [vp, P(f64), i64, P(i64)]),
+        "coulps_reset_stats": (i32, [vp]),
+        "coulps_checkpoint_save": (i32, [vp, vp, ctypes.c_char_p]),
+        "coulps_checkpoint_load": (i32, [vp, vp, ctypes.c_char_p]),
+        "coulps_charges_update": (i32, [vp, P(ctypes.c_int32), P(f64)]),
+        "coulps_chain_stats": (i32, [vp, P(f64), i64]),
+        "coulps_pool_stats": (i32, [P(f64), i64, P(f64), P(f64), P(f64), P(i64)]),
+        "coulps_set_profiling": (i32, [vp, i32]),
+        "coulps_kernel_times": (i32, [vp, P(f64)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def error_string(status: int) -> str:
+    return load().coulps_error_string(int(status)).decode()
+
+
+def _check(status: int, where: str):
+    if status != OK:
+        raise CoulpsError(status, where)
+
+
+def use_torch_allocator():
+    """Route the library's device allocations through torch's caching allocator."""
+    import torch
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+        except Exception:  # out of memory: the library reports COULPS_ENOMEM
+            return None
+
+    def _free(ptr, stream, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    a, f = _ALLOC_T(_alloc), _FREE_T(_free)
+    _keep.extend([a, f])
+    _check(load().coulps_set_allocator(a, f, None), "coulps_set_allocator")
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream or None
+    return stream.cuda_stream or None
+
+
+def _f64p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+# --------------------------------------------------------------------------
+class Lattice:
+    """n_chains independent chains of phi on an Lx x Ly x Lz Dirichlet box."""
+
+    def __init__(self, L, n_chains=1, precision=F32, seed=0, stream=None):
+        self._lib = load()
+        self.L = tuple(int(v) for v in L)
+        self.n_chains = int(n_chains)
+        self.precision = int(precision)
+        self.seed = int(seed)
+        self._stream = stream
+        h = ctypes.c_void_p()
+        _check(self._lib.coulps_lattice_create(*self.L, self.n_chains, self.precision,
+                                               self.seed, _stream_handle(stream), ctypes.byref(h)),
+               "coulps_lattice_create")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.coulps_lattice_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        a = (ctypes.c_int64 * 10)()
+        _check(self._lib.coulps_lattice_info(self.handle, a), "coulps_lattice_info")
+        keys = ("Lx", "Ly", "Lz", "n_chains", "precision", "W", "pass", "bytes", "ty", "dz")
+        return dict(zip(keys, list(a)))
+
+    def set_stream(self, stream):
+        self._stream = stream
+        _check(self._lib.coulps_set_stream(self.handle, _stream_handle(stream)), "coulps_set_stream")
+
+    def set_tile(self, ty=0, dz=0):
+        _check(self._lib.coulps_set_tile(self.handle, int(ty), int(dz)), "coulps_set_tile")
+
+    def field(self, chain=0):
+        Lx, Ly, Lz = self.L
+        out = np.empty((Lz, Ly, Lx), dtype=np.float64)
+        _check(self._lib.coulps_field_get(self.handle, int(chain), _f64p(out)), "coulps_field_get")
+        return out
+
+    def set_field(self, chain, phi):
+        phi = np.ascontiguousarray(phi, dtype=np.float64)
+        Lx, Ly, Lz = self.L
+        assert phi.shape == (Lz, Ly, Lx)
+        _check(self._lib.coulps_field_set(self.handle, int(chain), _f64p(phi)), "coulps_field_set")
+
+    def sweep(self, n_compound=1, n_hb=1, n_or=0):
+        _check(self._lib.coulps_sweep(self.handle, int(n_compound), int(n_hb), int(n_or)),
+               "coulps_sweep")
+
+    def sync(self):
+        _check(self._lib.coulps_sync(self.handle), "coulps_sync")
+
+    def set_profiling(self, enable=True):
+        _check(self._lib.coulps_set_profiling(self.handle, int(bool(enable))), "coulps_set_profiling")
+
+    def kernel_times(self):
+        """{'hb_ms', 'hb_n', 'or_ms', 'or_n'} accumulated since the last call."""
+        a = (ctypes.c_double * 4)()
+        _check(self._lib.coulps_kernel_times(self.handle, a), "coulps_kernel_times")
+        return {"hb_ms": a[0], "hb_n": int(a[1]), "or_ms": a[2], "or_n": int(a[3])}
+
+    def checkpoint_save(self, path, charges=None):
+        _check(self._lib.coulps_checkpoint_save(self.handle, charges.handle if charges else None,
+                                                str(path).encode()), "coulps_checkpoint_save")
+
+    def checkpoint_load(self, path, charges=None):
+        _check(self._lib.coulps_checkpoint_load(self.handle, charges.handle if charges else None,
+                                                str(path).encode()), "coulps_checkpoint_load")
+
+
+class Charges:
+    """A charge set measured on every chain of a lattice."""
+
+    def __init__(self, lattice: Lattice, sites, q, log_capacity=0):
+        self._lib = load()
+        self.lattice = lattice
+        s = np.ascontiguousarray(np.asarray(sites, dtype=np.int32).reshape(-1, 3))
+        qq = np.ascontiguousarray(np.asarray(q, dtype=np.float64).reshape(-1))
+        assert len(s) == len(qq)
+        self.n = len(qq)
+        h = ctypes.c_void_p()
+        _check(self._lib.coulps_charges_create(
+            lattice.handle, self.n, s.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _f64p(qq),
+            int(log_capacity), ctypes.byref(h)), "coulps_charges_create")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.coulps_charges_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def measure(self):
+        _check(self._lib.coulps_measure(self.lattice.handle, self.handle), "coulps_measure")
+
+    def run(self, n_therm, n_meas, n_hb=1, n_or=0):
+        _check(self._lib.coulps_run(self.lattice.handle, self.handle, int(n_therm), int(n_meas),
+                                    int(n_hb), int(n_or)), "coulps_run")
+
+    def estimate(self):
+        m, s, t = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        n = ctypes.c_int64()
+        _check(self._lib.coulps_estimate(self.handle, ctypes.byref(m), ctypes.byref(s),
+                                         ctypes.byref(t), ctypes.byref(n)), "coulps_estimate")
+        return {"mean": m.value, "stderr": s.value, "tau_int": t.value, "n": n.value}
+
+    def samples(self, cap=None):
+        """(n_samples, n_chains, 3) array of logged (Q, P, e)."""
+        nc = self.lattice.n_chains
+        if cap is None:
+            cap = 1 << 20
+        buf = np.empty((cap, nc, 3), dtype=np.float64)
+        n = ctypes.c_int64()
+        _check(self._lib.coulps_samples(self.handle, _f64p(buf), int(cap), ctypes.byref(n)),
+               "coulps_samples")
+        return buf[: n.value].copy()
+
+    def reset_stats(self):
+        _check(self._lib.coulps_reset_stats(self.handle), "coulps_reset_stats")
+
+    def update(self, sites, q):
+        """Replace the charges' positions and values (same count)."""
+        s = np.ascontiguousarray(np.asarray(sites, dtype=np.int32).reshape(-1, 3))
+        qq = np.ascontiguousarray(np.asarray(q, dtype=np.float64).reshape(-1))
+        assert len(s) == len(qq) == self.n
+        _check(self._lib.coulps_charges_update(
+            self.handle, s.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _f64p(qq)),
+            "coulps_charges_update")
+
+    def chain_stats(self):
+        """(n_chains, STAT_STRIDE) raw per-chain estimator state."""
+        nc = self.lattice.n_chains
+        out = np.empty((nc, STAT_STRIDE), dtype=np.float64)
+        _check(self._lib.coulps_chain_stats(self.handle, _f64p(out), out.size), "coulps_chain_stats")
+        return out
+
+
+def pool_stats(rows):
+    """Pool per-chain estimator rows (any number, e.g. gathered from several
+    processes) exactly as Charges.estimate does."""
+    rows = np.ascontiguousarray(np.asarray(rows, dtype=np.float64).reshape(-1, STAT_STRIDE))
+    m, s, t = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    n = ctypes.c_int64()
+    _check(load().coulps_pool_stats(_f64p(rows), len(rows), ctypes.byref(m), ctypes.byref(s),
+                                    ctypes.byref(t), ctypes.byref(n)), "coulps_pool_stats")
+    return {"mean": m.value, "stderr": s.value, "tau_int": t.value, "n": n.value}
+
+
+# C-named module functions -------------------------------------------------
+def coulps_lattice_create(Lx, Ly, Lz, n_chains, precision, seed, stream=None):
+    return Lattice((Lx, Ly, Lz), n_chains, precision, seed, stream)
+
+
+def coulps_charges_create(lattice, sites, q, log_capacity=0):
+    return Charges(lattice, sites, q, log_capacity)
+
+
+def coulps_sweep(lattice, n_compound, n_hb, n_or):
+    lattice.sweep(n_compound, n_hb, n_or)
+
+
+def coulps_measure(lattice, charges):
+    assert charges.lattice is lattice
+    charges.measure()
+
+
+def coulps_run(lattice, charges, n_therm, n_meas, n_hb, n_or):
+    assert charges.lattice is lattice
+    charges.run(n_therm, n_meas, n_hb, n_or)
+
+
+def coulps_estimate(charges):
+    return charges.estimate()
+
+
+def coulps_samples(charges, cap=None):
+    return charges.samples(cap)
+
+
+def coulps_field_get(lattice, chain):
+    return lattice.field(chain)
+
+
+def coulps_field_set(lattice, chain, phi):
+    lattice.set_field(chain, phi)

@@ -1,0 +1,803 @@
+// Host side of the C ABI declared in include/coulps.h.
+//
+// Owns the device buffers, validates arguments, builds the TMA tensor maps,
+// sequences the half-sweep / gather / finalize launches on the handle's
+// stream, captures the measured loop into a CUDA graph, and turns the
+// per-chain running sums into the pooled estimate with its batch-means error
+// (the host-side counterpart of the paper's final mpi_reduce).
+#include <cudaTypedefs.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+
+using namespace coulps;
+
+namespace coulps {
+
+static Allocator g_allocator = {nullptr, nullptr, nullptr};
+
+void *dev_alloc(const Allocator &a, size_t bytes, cudaStream_t s) {
+  if (bytes == 0) bytes = 16;
+  if (a.alloc) return a.alloc(bytes, (void *)s, a.ctx);
+  void *p = nullptr;
+  if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void dev_free(const Allocator &a, void *p, cudaStream_t s) {
+  if (!p) return;
+  if (a.free_fn) {
+    a.free_fn(p, (void *)s, a.ctx);
+    return;
+  }
+  cudaFreeAsync(p, s);
+}
+
+}  // namespace coulps
+
+struct coulps_lattice {
+  Geometry g;
+  Tile tile;
+  uint64_t seed;
+  cudaStream_t stream;
+  Allocator alloc;
+  void *field = nullptr;
+  uint32_t *d_pass = nullptr;
+  int *d_err = nullptr;
+  uint64_t pass = 0;  // host mirror of *d_pass
+  CUtensorMap tm_halo, tm_own;
+  size_t bytes = 0;
+  int n_charge_sets = 0;
+  // measured compound sweep captured as a graph
+  cudaGraphExec_t graph = nullptr;
+  const void *graph_key = nullptr;
+  int graph_hb = -1, graph_or = -1;
+  Tile graph_tile = {0, 0};
+  // per-kernel event timing
+  bool profiling = false;
+  struct Timed {
+    cudaEvent_t a, b;
+    int kind;  // 0 heatbath, 1 over-relaxation
+  };
+  std::vector<cudaEvent_t> spare_events;
+  std::vector<Timed> pending;
+  double times[4] = {0, 0, 0, 0};
+};
+
+struct coulps_charges {
+  coulps_lattice *lat = nullptr;
+  int64_t n = 0;
+  uint32_t *d_idx = nullptr;
+  double *d_q = nullptr;
+  int nblk = 1;
+  double *d_partials = nullptr;  // scratch: [chain][nblk][2]
+  double *d_stats = nullptr;     // [chain][kStatStride]
+  double *d_log = nullptr;       // [sample][chain][3]
+  int64_t log_cap = 0;
+  size_t bytes = 0;
+  // pinned staging for coulps_charges_update
+  uint32_t *h_idx = nullptr;
+  double *h_q = nullptr;
+  cudaEvent_t staged = nullptr;  // recorded after the last upload's copies
+};
+
+namespace {
+
+#define CK(expr)                          \
+  do {                                    \
+    cudaError_t e_ = (expr);              \
+    if (e_ != cudaSuccess) {              \
+      cudaGetLastError();                 \
+      return COULPS_ECUDA;                \
+    }                                     \
+  } while (0)
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    cudaGetLastError();
+  }
+  return fn;
+}
+
+// 4D map over field[chain*2 + colour][z][y][h] with a box of `rows` rows of W
+// elements of one plane.  Out-of-range boxes read as zeros.
+int make_map(CUtensorMap *m, const Geometry &g, void *base, int rows) {
+  auto fn = encode_fn();
+  if (!fn) return COULPS_ECUDA;
+  cuuint64_t dims[4] = {(cuuint64_t)g.W, (cuuint64_t)g.Ly, (cuuint64_t)g.Lz,
+                        (cuuint64_t)g.n_chains * 2};
+  cuuint64_t strides[3] = {(cuuint64_t)g.W * g.es, (cuuint64_t)g.W * g.Ly * g.es,
+                           (cuuint64_t)g.W * g.Ly * g.Lz * g.es};
+  cuuint32_t box[4] = {(cuuint32_t)g.W, (cuuint32_t)rows, 1, 1};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = fn(m,
+                  g.precision == COULPS_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                            : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                  4, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? COULPS_OK : COULPS_ECUDA;
+}
+
+int rebuild_maps(coulps_lattice *L) {
+  int st = make_map(&L->tm_halo, L->g, L->field, L->tile.ty + 2);
+  if (st) return st;
+  return make_map(&L->tm_own, L->g, L->field, L->tile.ty);
+}
+
+Tile default_tile(const Geometry &g) {
+  // About 256 threads per CTA (W/4 threads per row), 16 z planes per CTA.
+  const int qw = g.W / 4;
+  int ty = 256 / qw;
+  if (ty < 1) ty = 1;
+  if (ty > 254) ty = 254;  // TMA box rows ty + 2 <= 256
+  if (ty > g.Ly) ty = g.Ly;
+  while (ty > 1 && qw * ty > 1024) --ty;
+  int dz = g.Lz < 16 ? g.Lz : 16;
+  return Tile{ty, dz};
+}
+
+int check_device_error(coulps_lattice *L) {
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, L->d_err, sizeof(int), cudaMemcpyDeviceToHost, L->stream));
+  CK(cudaStreamSynchronize(L->stream));
+  if (h & kErrTimeout) return COULPS_ETIMEOUT;
+  if (h & kErrNonFinite) return COULPS_ENONFINITE;
+  return COULPS_OK;
+}
+
+// Queue the half-sweeps of one compound sweep.  The pass index of every
+// half-sweep is read on the device as *d_pass + offset, and the counter is
+// advanced at the end, so the same launches can be captured once and
+// replayed.
+cudaEvent_t take_event(coulps_lattice *L) {
+  if (!L->spare_events.empty()) {
+    cudaEvent_t e = L->spare_events.back();
+    L->spare_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+int enqueue_compound(coulps_lattice *L, int n_hb, int n_or) {
+  SweepArgs a;
+  a.field = L->field;
+  a.Lx = L->g.Lx; a.Ly = L->g.Ly; a.Lz = L->g.Lz;
+  a.W = L->g.W; a.Wq = L->g.Wq; a.QW = L->g.W / 4;
+  a.TY = L->tile.ty; a.DZ = L->tile.dz;
+  a.seed_lo = (uint32_t)(L->seed & 0xffffffffu);
+  a.seed_hi = (uint32_t)(L->seed >> 32);
+  a.pass_ptr = L->d_pass;
+  a.chain_elems = L->g.chain_elems;
+  a.colour_elems = L->g.colour_elems;
+  a.err = L->d_err;
+  uint32_t off = 0;
+  for (int i = 0; i < n_hb + n_or; ++i, ++off) {
+    const bool orx = i >= n_hb;
+    for (int c = 0; c < 2; ++c) {
+      a.colour = c;
+      a.pass_off = off;
+      cudaEvent_t ea = nullptr, eb = nullptr;
+      if (L->profiling) {
+        ea = take_event(L);
+        eb = take_event(L);
+        if (!ea || !eb) return COULPS_ECUDA;
+        CK(cudaEventRecord(ea, L->stream));
+      }
+      CK(launch_halfsweep(L->g, L->tile, L->tm_halo, L->tm_own, a, orx, L->stream));
+      if (L->profiling) {
+        CK(cudaEventRecord(eb, L->stream));
+        L->pending.push_back({ea, eb, orx ? 1 : 0});
+      }
+    }
+  }
+  if (n_hb + n_or > 0) CK(launch_advance_pass(L->d_pass, (uint32_t)(n_hb + n_or), L->stream));
+  return COULPS_OK;
+}
+
+int enqueue_measure(coulps_lattice *L, coulps_charges *C) {
+  CK(launch_gather(L->g, L->field, C->d_idx, C->d_q, C->n, C->d_partials, C->nblk, L->stream));
+  CK(launch_finalize(C->d_partials, C->nblk, L->g.n_chains, C->d_stats, C->d_log, C->log_cap,
+                     L->d_err, L->stream));
+  return COULPS_OK;
+}
+
+void drop_graph(coulps_lattice *L) {
+  if (L->graph) cudaGraphExecDestroy(L->graph);
+  L->graph = nullptr;
+  L->graph_key = nullptr;
+}
+
+uint64_t fnv1a(uint64_t h, const void *p, size_t n) {
+  const unsigned char *b = static_cast<const unsigned char *>(p);
+  for (size_t i = 0; i < n; ++i) {
+    h ^= b[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *coulps_error_string(int status) {
+  switch (status) {
+    case COULPS_OK: return "ok";
+    case COULPS_EINVAL: return "invalid argument";
+    case COULPS_ENOMEM: return "out of memory";
+    case COULPS_ECUDA: return "CUDA runtime error";
+    case COULPS_ETIMEOUT: return "device wait timed out";
+    case COULPS_ENONFINITE: return "non-finite sample";
+    case COULPS_EIO: return "checkpoint I/O error";
+    case COULPS_ECORRUPT: return "checkpoint corrupt or mismatched";
+    case COULPS_EUNSUPPORTED: return "unsupported shape or mode";
+    default: return "unknown status";
+  }
+}
+
+int coulps_version(void) { return 100; }
+
+int coulps_set_allocator(coulps_alloc_fn alloc, coulps_free_fn free_fn, void *ctx) {
+  if ((alloc == nullptr) != (free_fn == nullptr)) return COULPS_EINVAL;
+  g_allocator = Allocator{alloc, free_fn, ctx};
+  return COULPS_OK;
+}
+
+int coulps_lattice_create(int Lx, int Ly, int Lz, int n_chains, int precision, uint64_t seed,
+                          void *stream, coulps_lattice_t *out) {
+  if (!out) return COULPS_EINVAL;
+  *out = nullptr;
+  if (Lx < 1 || Ly < 1 || Lz < 1 || Lx > 512 || Ly > 65535 || Lz > 65535) return COULPS_EINVAL;
+  if (n_chains < 1 || n_chains > 65535) return COULPS_EINVAL;
+  if (precision != COULPS_F32 && precision != COULPS_F64) return COULPS_EINVAL;
+  Geometry g;
+  g.Lx = Lx; g.Ly = Ly; g.Lz = Lz;
+  g.n_chains = n_chains;
+  g.precision = precision;
+  g.es = precision == COULPS_F32 ? 4 : 8;
+  g.Wq = (Lx + 7) / 8;
+  const int align_elems = 32 / g.es;  // 32-byte rows
+  g.W = ((4 * g.Wq + align_elems - 1) / align_elems) * align_elems;
+  if ((uint64_t)Lz * (uint64_t)Ly * (uint64_t)g.Wq > 0xffffffffull) return COULPS_EINVAL;
+  g.colour_elems = (size_t)Lz * Ly * g.W;
+  g.chain_elems = 2 * g.colour_elems;
+  if (g.W > 256) return COULPS_EUNSUPPORTED;
+
+  coulps_lattice *L = new (std::nothrow) coulps_lattice();
+  if (!L) return COULPS_ENOMEM;
+  L->g = g;
+  L->tile = default_tile(g);
+  L->seed = seed;
+  L->stream = (cudaStream_t)stream;
+  L->alloc = g_allocator;
+  const size_t fbytes = g.chain_elems * g.es * (size_t)n_chains;
+  L->field = dev_alloc(L->alloc, fbytes, L->stream);
+  L->d_pass = (uint32_t *)dev_alloc(L->alloc, 64, L->stream);
+  L->d_err = (int *)dev_alloc(L->alloc, 64, L->stream);
+  if (!L->field || !L->d_pass || !L->d_err) {
+    coulps_lattice_destroy(L);
+    return COULPS_ENOMEM;
+  }
+  L->bytes = fbytes + 128;
+  if (cudaMemsetAsync(L->field, 0, fbytes, L->stream) != cudaSuccess ||
+      cudaMemsetAsync(L->d_pass, 0, 64, L->stream) != cudaSuccess ||
+      cudaMemsetAsync(L->d_err, 0, 64, L->stream) != cudaSuccess) {
+    cudaGetLastError();
+    coulps_lattice_destroy(L);
+    return COULPS_ECUDA;
+  }
+  int st = rebuild_maps(L);
+  if (st) {
+    coulps_lattice_destroy(L);
+    return st;
+  }
+  *out = L;
+  return COULPS_OK;
+}
+
+void coulps_lattice_destroy(coulps_lattice_t L) {
+  if (!L) return;
+  drop_graph(L);
+  for (auto &t : L->pending) {
+    cudaEventDestroy(t.a);
+    cudaEventDestroy(t.b);
+  }
+  for (auto e : L->spare_events) cudaEventDestroy(e);
+  dev_free(L->alloc, L->field, L->stream);
+  dev_free(L->alloc, L->d_pass, L->stream);
+  dev_free(L->alloc, L->d_err, L->stream);
+  delete L;
+}
+
+int coulps_set_stream(coulps_lattice_t L, void *stream) {
+  if (!L) return COULPS_EINVAL;
+  if ((cudaStream_t)stream != L->stream) drop_graph(L);
+  L->stream = (cudaStream_t)stream;
+  return COULPS_OK;
+}
+
+int coulps_lattice_info(coulps_lattice_t L, int64_t info[10]) {
+  if (!L || !info) return COULPS_EINVAL;
+  info[0] = L->g.Lx; info[1] = L->g.Ly; info[2] = L->g.Lz;
+  info[3] = L->g.n_chains; info[4] = L->g.precision; info[5] = L->g.W;
+  info[6] = (int64_t)L->pass; info[7] = (int64_t)L->bytes;
+  info[8] = L->tile.ty; info[9] = L->tile.dz;
+  return COULPS_OK;
+}
+
+int coulps_set_tile(coulps_lattice_t L, int ty, int dz) {
+  if (!L) return COULPS_EINVAL;
+  Tile t = L->tile;
+  if (ty > 0) t.ty = ty;
+  if (dz > 0) t.dz = dz;
+  if (ty < 0 || dz < 0 || t.ty < 1 || t.dz < 1 || t.ty + 2 > 256) return COULPS_EINVAL;
+  if ((L->g.W / 4) * t.ty > 1024) return COULPS_EINVAL;
+  if (halfsweep_smem_bytes(L->g, t, true) > 227 * 1024) return COULPS_EINVAL;
+  L->tile = t;
+  drop_graph(L);
+  return rebuild_maps(L);
+}
+
+int coulps_sync(coulps_lattice_t L) {
+  if (!L) return COULPS_EINVAL;
+  return check_device_error(L);
+}
+
+int coulps_field_get(coulps_lattice_t L, int chain, double *host) {
+  if (!L || !host || chain < 0 || chain >= L->g.n_chains) return COULPS_EINVAL;
+  const Geometry &g = L->g;
+  std::vector<unsigned char> buf(g.chain_elems * g.es);
+  CK(cudaMemcpyAsync(buf.data(), (const char *)L->field + (size_t)chain * g.chain_elems * g.es,
+                     buf.size(), cudaMemcpyDeviceToHost, L->stream));
+  int st = check_device_error(L);
+  if (st) return st;
+  for (int z = 0; z < g.Lz; ++z)
+    for (int y = 0; y < g.Ly; ++y)
+      for (int x = 0; x < g.Lx; ++x) {
+        const int c = (x + y + z) & 1;
+        const size_t s = (size_t)c * g.colour_elems + ((size_t)z * g.Ly + y) * g.W + (x >> 1);
+        double v;
+        if (g.precision == COULPS_F32)
+          v = reinterpret_cast<const float *>(buf.data())[s];
+        else
+          v = reinterpret_cast<const double *>(buf.data())[s];
+        host[x + (size_t)g.Lx * (y + (size_t)g.Ly * z)] = v;
+      }
+  return COULPS_OK;
+}
+
+int coulps_field_set(coulps_lattice_t L, int chain, const double *host) {
+  if (!L || !host || chain < 0 || chain >= L->g.n_chains) return COULPS_EINVAL;
+  const Geometry &g = L->g;
+  std::vector<unsigned char> buf(g.chain_elems * g.es, 0);
+  for (int z = 0; z < g.Lz; ++z)
+    for (int y = 0; y < g.Ly; ++y)
+      for (int x = 0; x < g.Lx; ++x) {
+        const int c = (x + y + z) & 1;
+        const size_t s = (size_t)c * g.colour_elems + ((size_t)z * g.Ly + y) * g.W + (x >> 1);
+        const double v = host[x + (size_t)g.Lx * (y + (size_t)g.Ly * z)];
+        if (g.precision == COULPS_F32)
+          reinterpret_cast<float *>(buf.data())[s] = (float)v;
+        else
+          reinterpret_cast<double *>(buf.data())[s] = v;
+      }
+  CK(cudaMemcpyAsync((char *)L->field + (size_t)chain * g.chain_elems * g.es, buf.data(),
+                     buf.size(), cudaMemcpyHostToDevice, L->stream));
+  CK(cudaStreamSynchronize(L->stream));
+  return COULPS_OK;
+}
+
+int coulps_sweep(coulps_lattice_t L, int n_compound, int n_hb, int n_or) {
+  if (!L || n_compound < 0 || n_hb < 0 || n_or < 0) return COULPS_EINVAL;
+  for (int k = 0; k < n_compound; ++k) {
+    int st = enqueue_compound(L, n_hb, n_or);
+    if (st) return st;
+    L->pass += (uint64_t)(n_hb + n_or);
+  }
+  return COULPS_OK;
+}
+
+int coulps_charges_create(coulps_lattice_t L, int64_t n, const int32_t *site, const double *q,
+                          int64_t log_capacity, coulps_charges_t *out) {
+  if (!L || !out || n < 0 || log_capacity < 0) return COULPS_EINVAL;
+  *out = nullptr;
+  if (n > 0 && (!site || !q)) return COULPS_EINVAL;
+  if (n > (int64_t)1 << 31) return COULPS_EINVAL;
+  const Geometry &g = L->g;
+  std::vector<uint32_t> idx((size_t)n);
+  for (int64_t i = 0; i < n; ++i) {
+    const int x = site[3 * i], y = site[3 * i + 1], z = site[3 * i + 2];
+    if (x < 0 || x >= g.Lx || y < 0 || y >= g.Ly || z < 0 || z >= g.Lz) return COULPS_EINVAL;
+    if (!std::isfinite(q[i])) return COULPS_EINVAL;
+    const int c = (x + y + z) & 1;
+    idx[i] = (uint32_t)((size_t)c * g.colour_elems + ((size_t)z * g.Ly + y) * g.W + (x >> 1));
+  }
+  coulps_charges *C = new (std::nothrow) coulps_charges();
+  if (!C) return COULPS_ENOMEM;
+  C->lat = L;
+  C->n = n;
+  C->nblk = gather_blocks(n);
+  C->log_cap = log_capacity;
+  const size_t b_idx = sizeof(uint32_t) * (size_t)n, b_q = sizeof(double) * (size_t)n;
+  const size_t b_part = sizeof(double) * 2 * (size_t)C->nblk * g.n_chains;
+  const size_t b_stats = sizeof(double) * kStatStride * (size_t)g.n_chains;
+  const size_t b_log = sizeof(double) * 3 * (size_t)log_capacity * g.n_chains;
+  C->d_idx = (uint32_t *)dev_alloc(L->alloc, b_idx, L->stream);
+  C->d_q = (double *)dev_alloc(L->alloc, b_q, L->stream);
+  C->d_partials = (double *)dev_alloc(L->alloc, b_part, L->stream);
+  C->d_stats = (double *)dev_alloc(L->alloc, b_stats, L->stream);
+  if (log_capacity > 0) C->d_log = (double *)dev_alloc(L->alloc, b_log, L->stream);
+  C->bytes = b_idx + b_q + b_part + b_stats + b_log;
+  if (!C->d_idx || !C->d_q || !C->d_partials || !C->d_stats || (log_capacity > 0 && !C->d_log)) {
+    coulps_charges_destroy(C);
+    return COULPS_ENOMEM;
+  }
+  L->n_charge_sets++;
+  if (n > 0) {
+    if (cudaMemcpyAsync(C->d_idx, idx.data(), b_idx, cudaMemcpyHostToDevice, L->stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(C->d_q, q, b_q, cudaMemcpyHostToDevice, L->stream) != cudaSuccess) {
+      cudaGetLastError();
+      coulps_charges_destroy(C);
+      return COULPS_ECUDA;
+    }
+  }
+  if (launch_reset_stats(C->d_stats, g.n_chains, L->stream) != cudaSuccess) {
+    cudaGetLastError();
+    coulps_charges_destroy(C);
+    return COULPS_ECUDA;
+  }
+  // host vectors are copied from pageable memory: make sure the copy is done
+  if (cudaStreamSynchronize(L->stream) != cudaSuccess) {
+    cudaGetLastError();
+    coulps_charges_destroy(C);
+    return COULPS_ECUDA;
+  }
+  *out = C;
+  return COULPS_OK;
+}
+
+void coulps_charges_destroy(coulps_charges_t C) {
+  if (!C) return;
+  coulps_lattice *L = C->lat;
+  if (L->graph_key == C) drop_graph(L);
+  dev_free(L->alloc, C->d_idx, L->stream);
+  dev_free(L->alloc, C->d_q, L->stream);
+  dev_free(L->alloc, C->d_partials, L->stream);
+  dev_free(L->alloc, C->d_stats, L->stream);
+  dev_free(L->alloc, C->d_log, L->stream);
+  if (C->staged) {
+    cudaEventSynchronize(C->staged);
+    cudaEventDestroy(C->staged);
+  }
+  if (C->h_idx) cudaFreeHost(C->h_idx);
+  if (C->h_q) cudaFreeHost(C->h_q);
+  L->n_charge_sets--;
+  delete C;
+}
+
+int coulps_measure(coulps_lattice_t L, coulps_charges_t C) {
+  if (!L || !C || C->lat != L) return COULPS_EINVAL;
+  return enqueue_measure(L, C);
+}
+
+int coulps_run(coulps_lattice_t L, coulps_charges_t C, int n_therm, int n_meas, int n_hb,
+               int n_or) {
+  if (!L || !C || C->lat != L || n_therm < 0 || n_meas < 0 || n_hb < 0 || n_or < 0)
+    return COULPS_EINVAL;
+  int st = coulps_sweep(L, n_therm, n_hb, n_or);
+  if (st) return st;
+  if (n_meas == 0) return COULPS_OK;
+  const bool capturable = L->stream != nullptr && !L->profiling;
+  if (capturable && (L->graph_key != C || L->graph_hb != n_hb || L->graph_or != n_or ||
+                     L->graph_tile.ty != L->tile.ty || L->graph_tile.dz != L->tile.dz)) {
+    drop_graph(L);
+    cudaGraph_t gr = nullptr;
+    CK(cudaStreamBeginCapture(L->stream, cudaStreamCaptureModeThreadLocal));
+    int s1 = enqueue_compound(L, n_hb, n_or);
+    int s2 = s1 ? s1 : enqueue_measure(L, C);
+    cudaError_t e = cudaStreamEndCapture(L->stream, &gr);
+    if (s2 || e != cudaSuccess) {
+      cudaGetLastError();
+      if (gr) cudaGraphDestroy(gr);
+      return s2 ? s2 : COULPS_ECUDA;
+    }
+    e = cudaGraphInstantiate(&L->graph, gr, 0);
+    cudaGraphDestroy(gr);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      L->graph = nullptr;
+      return COULPS_ECUDA;
+    }
+    L->graph_key = C;
+    L->graph_hb = n_hb;
+    L->graph_or = n_or;
+    L->graph_tile = L->tile;
+  }
+  for (int k = 0; k < n_meas; ++k) {
+    if (capturable) {
+      CK(cudaGraphLaunch(L->graph, L->stream));
+    } else {
+      st = enqueue_compound(L, n_hb, n_or);
+      if (!st) st = enqueue_measure(L, C);
+      if (st) return st;
+    }
+    L->pass += (uint64_t)(n_hb + n_or);
+  }
+  return COULPS_OK;
+}
+
+int coulps_pool_stats(const double *st, int64_t n_rows, double *mean, double *stderr_bm,
+                      double *tau_int, int64_t *n) {
+  if (n_rows < 0 || (n_rows > 0 && !st)) return COULPS_EINVAL;
+  // Pool over rows (chains) in order.  Batches of all rows share one length.
+  double N = 0, S = 0, S2 = 0;
+  double nb_tot = 0, bsum = 0, bsum2 = 0, blen = 0;
+  for (int64_t k = 0; k < n_rows; ++k) {
+    const double *p = st + (size_t)k * kStatStride;
+    N += p[kStatN];
+    S += p[kStatSum];
+    S2 += p[kStatSum2];
+    if (k > 0 && p[kStatBatchLen] != blen) return COULPS_EINVAL;
+    blen = p[kStatBatchLen];
+    const int nb = (int)p[kStatNBatch];
+    if (nb < 0 || nb >= 2 * kBatchMin) return COULPS_EINVAL;
+    for (int b = 0; b < nb; ++b) {
+      const double m = p[kStatBatch0 + b] / blen;
+      bsum += m;
+      bsum2 += m * m;
+      nb_tot += 1;
+    }
+  }
+  const double mu = N > 0 ? S / N : NAN;
+  double se = NAN, tau = NAN;
+  if (nb_tot >= 2) {
+    const double bm = bsum / nb_tot;
+    const double bvar = (bsum2 - nb_tot * bm * bm) / (nb_tot - 1);
+    se = std::sqrt(bvar > 0 ? bvar / nb_tot : 0.0);
+    const double var = N > 1 ? (S2 - N * mu * mu) / (N - 1) : NAN;
+    if (var > 0) tau = 0.5 * blen * bvar / var;
+  }
+  if (mean) *mean = mu;
+  if (stderr_bm) *stderr_bm = se;
+  if (tau_int) *tau_int = tau;
+  if (n) *n = (int64_t)N;
+  if (N > 0 && !std::isfinite(mu)) return COULPS_ENONFINITE;
+  return COULPS_OK;
+}
+
+int coulps_chain_stats(coulps_charges_t C, double *out, int64_t cap) {
+  if (!C || !out) return COULPS_EINVAL;
+  coulps_lattice *L = C->lat;
+  const int64_t need = (int64_t)L->g.n_chains * kStatStride;
+  if (cap < need) return COULPS_EINVAL;
+  CK(cudaMemcpyAsync(out, C->d_stats, need * sizeof(double), cudaMemcpyDeviceToHost, L->stream));
+  return check_device_error(L);
+}
+
+int coulps_estimate(coulps_charges_t C, double *mean, double *stderr_bm, double *tau_int,
+                    int64_t *n) {
+  if (!C) return COULPS_EINVAL;
+  coulps_lattice *L = C->lat;
+  std::vector<double> st((size_t)L->g.n_chains * kStatStride);
+  int s = coulps_chain_stats(C, st.data(), (int64_t)st.size());
+  if (s) return s;
+  return coulps_pool_stats(st.data(), L->g.n_chains, mean, stderr_bm, tau_int, n);
+}
+
+int coulps_samples(coulps_charges_t C, double *QPe, int64_t cap, int64_t *n) {
+  if (!C || (cap > 0 && !QPe) || cap < 0) return COULPS_EINVAL;
+  coulps_lattice *L = C->lat;
+  const int nc = L->g.n_chains;
+  double ns = 0;
+  CK(cudaMemcpyAsync(&ns, C->d_stats + kStatN, sizeof(double), cudaMemcpyDeviceToHost,
+                     L->stream));
+  int s = check_device_error(L);
+  if (s) return s;
+  int64_t m = (int64_t)ns;
+  if (m > C->log_cap) m = C->log_cap;
+  if (m > cap) m = cap;
+  if (m > 0) {
+    CK(cudaMemcpyAsync(QPe, C->d_log, sizeof(double) * 3 * (size_t)m * nc,
+                       cudaMemcpyDeviceToHost, L->stream));
+    CK(cudaStreamSynchronize(L->stream));
+  }
+  if (n) *n = m;
+  return COULPS_OK;
+}
+
+int coulps_reset_stats(coulps_charges_t C) {
+  if (!C) return COULPS_EINVAL;
+  CK(launch_reset_stats(C->d_stats, C->lat->g.n_chains, C->lat->stream));
+  return COULPS_OK;
+}
+
+int coulps_charges_update(coulps_charges_t C, const int32_t *site, const double *q) {
+  if (!C) return COULPS_EINVAL;
+  if (C->n == 0) return COULPS_OK;
+  if (!site || !q) return COULPS_EINVAL;
+  coulps_lattice *L = C->lat;
+  const Geometry &g = L->g;
+  const int64_t n = C->n;
+  if (!C->h_idx) {
+    if (cudaMallocHost((void **)&C->h_idx, sizeof(uint32_t) * (size_t)n) != cudaSuccess ||
+        cudaMallocHost((void **)&C->h_q, sizeof(double) * (size_t)n) != cudaSuccess ||
+        cudaEventCreateWithFlags(&C->staged, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return COULPS_ENOMEM;
+    }
+  } else {
+    // the previous upload must have left the staging buffers
+    CK(cudaEventSynchronize(C->staged));
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    const int x = site[3 * i], y = site[3 * i + 1], z = site[3 * i + 2];
+    if (x < 0 || x >= g.Lx || y < 0 || y >= g.Ly || z < 0 || z >= g.Lz || !std::isfinite(q[i]))
+      return COULPS_EINVAL;
+    const int c = (x + y + z) & 1;
+    C->h_idx[i] = (uint32_t)((size_t)c * g.colour_elems + ((size_t)z * g.Ly + y) * g.W + (x >> 1));
+    C->h_q[i] = q[i];
+  }
+  CK(cudaMemcpyAsync(C->d_idx, C->h_idx, sizeof(uint32_t) * (size_t)n, cudaMemcpyHostToDevice,
+                     L->stream));
+  CK(cudaMemcpyAsync(C->d_q, C->h_q, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice,
+                     L->stream));
+  CK(cudaEventRecord(C->staged, L->stream));
+  return COULPS_OK;
+}
+
+int coulps_set_profiling(coulps_lattice_t L, int enable) {
+  if (!L) return COULPS_EINVAL;
+  L->profiling = enable != 0;
+  if (L->profiling) drop_graph(L);
+  return COULPS_OK;
+}
+
+int coulps_kernel_times(coulps_lattice_t L, double out[4]) {
+  if (!L || !out) return COULPS_EINVAL;
+  CK(cudaStreamSynchronize(L->stream));
+  for (auto &t : L->pending) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, t.a, t.b));
+    L->times[2 * t.kind] += ms;
+    L->times[2 * t.kind + 1] += 1;
+    L->spare_events.push_back(t.a);
+    L->spare_events.push_back(t.b);
+  }
+  L->pending.clear();
+  for (int i = 0; i < 4; ++i) {
+    out[i] = L->times[i];
+    L->times[i] = 0;
+  }
+  return COULPS_OK;
+}
+
+// ---- checkpoint ------------------------------------------------------------
+namespace {
+struct CkptHeader {
+  char magic[8];
+  int64_t version;
+  int64_t Lx, Ly, Lz, n_chains, precision, W;
+  uint64_t seed, pass;
+  int64_t has_charges, n_charges, stat_stride, log_cap;
+};
+}  // namespace
+
+int coulps_checkpoint_save(coulps_lattice_t L, coulps_charges_t C, const char *path) {
+  if (!L || !path || (C && C->lat != L)) return COULPS_EINVAL;
+  const Geometry &g = L->g;
+  CkptHeader h;
+  std::memset(&h, 0, sizeof(h));
+  std::memcpy(h.magic, "COULPS1", 8);
+  h.version = 1;
+  h.Lx = g.Lx; h.Ly = g.Ly; h.Lz = g.Lz; h.n_chains = g.n_chains;
+  h.precision = g.precision; h.W = g.W;
+  h.seed = L->seed;
+  h.pass = L->pass;
+  h.has_charges = C ? 1 : 0;
+  h.n_charges = C ? C->n : 0;
+  h.stat_stride = kStatStride;
+  h.log_cap = C ? C->log_cap : 0;
+  std::vector<unsigned char> field(g.chain_elems * g.es * (size_t)g.n_chains);
+  std::vector<double> stats, log;
+  CK(cudaMemcpyAsync(field.data(), L->field, field.size(), cudaMemcpyDeviceToHost, L->stream));
+  if (C) {
+    stats.resize((size_t)kStatStride * g.n_chains);
+    log.resize((size_t)3 * C->log_cap * g.n_chains);
+    CK(cudaMemcpyAsync(stats.data(), C->d_stats, stats.size() * sizeof(double),
+                       cudaMemcpyDeviceToHost, L->stream));
+    if (!log.empty())
+      CK(cudaMemcpyAsync(log.data(), C->d_log, log.size() * sizeof(double),
+                         cudaMemcpyDeviceToHost, L->stream));
+  }
+  uint32_t dpass = 0;
+  CK(cudaMemcpyAsync(&dpass, L->d_pass, sizeof(dpass), cudaMemcpyDeviceToHost, L->stream));
+  int s = check_device_error(L);
+  if (s) return s;
+  h.pass = dpass;  // the device counter is authoritative
+  uint64_t sum = 1469598103934665603ull;
+  sum = fnv1a(sum, &h, sizeof(h));
+  sum = fnv1a(sum, field.data(), field.size());
+  sum = fnv1a(sum, stats.data(), stats.size() * sizeof(double));
+  sum = fnv1a(sum, log.data(), log.size() * sizeof(double));
+  FILE *f = std::fopen(path, "wb");
+  if (!f) return COULPS_EIO;
+  bool ok = std::fwrite(&h, sizeof(h), 1, f) == 1 &&
+            std::fwrite(field.data(), 1, field.size(), f) == field.size() &&
+            std::fwrite(stats.data(), sizeof(double), stats.size(), f) == stats.size() &&
+            std::fwrite(log.data(), sizeof(double), log.size(), f) == log.size() &&
+            std::fwrite(&sum, sizeof(sum), 1, f) == 1;
+  ok = (std::fclose(f) == 0) && ok;
+  return ok ? COULPS_OK : COULPS_EIO;
+}
+
+int coulps_checkpoint_load(coulps_lattice_t L, coulps_charges_t C, const char *path) {
+  if (!L || !path || (C && C->lat != L)) return COULPS_EINVAL;
+  const Geometry &g = L->g;
+  FILE *f = std::fopen(path, "rb");
+  if (!f) return COULPS_EIO;
+  CkptHeader h;
+  if (std::fread(&h, sizeof(h), 1, f) != 1) {
+    std::fclose(f);
+    return COULPS_ECORRUPT;
+  }
+  if (std::memcmp(h.magic, "COULPS1", 8) != 0 || h.version != 1 || h.Lx != g.Lx ||
+      h.Ly != g.Ly || h.Lz != g.Lz || h.n_chains != g.n_chains || h.precision != g.precision ||
+      h.W != g.W || h.seed != L->seed || h.stat_stride != kStatStride ||
+      (C && (!h.has_charges || h.n_charges != C->n || h.log_cap != C->log_cap))) {
+    std::fclose(f);
+    return COULPS_ECORRUPT;
+  }
+  std::vector<unsigned char> field(g.chain_elems * g.es * (size_t)g.n_chains);
+  std::vector<double> stats(h.has_charges ? (size_t)kStatStride * g.n_chains : 0);
+  std::vector<double> log(h.has_charges ? (size_t)3 * h.log_cap * g.n_chains : 0);
+  uint64_t sum_file = 0;
+  bool ok = std::fread(field.data(), 1, field.size(), f) == field.size() &&
+            std::fread(stats.data(), sizeof(double), stats.size(), f) == stats.size() &&
+            std::fread(log.data(), sizeof(double), log.size(), f) == log.size() &&
+            std::fread(&sum_file, sizeof(sum_file), 1, f) == 1;
+  std::fclose(f);
+  if (!ok) return COULPS_ECORRUPT;
+  uint64_t sum = 1469598103934665603ull;
+  sum = fnv1a(sum, &h, sizeof(h));
+  sum = fnv1a(sum, field.data(), field.size());
+  sum = fnv1a(sum, stats.data(), stats.size() * sizeof(double));
+  sum = fnv1a(sum, log.data(), log.size() * sizeof(double));
+  if (sum != sum_file) return COULPS_ECORRUPT;
+  const uint32_t dpass = (uint32_t)h.pass;
+  CK(cudaMemcpyAsync(L->field, field.data(), field.size(), cudaMemcpyHostToDevice, L->stream));
+  CK(cudaMemcpyAsync(L->d_pass, &dpass, sizeof(dpass), cudaMemcpyHostToDevice, L->stream));
+  if (C) {
+    CK(cudaMemcpyAsync(C->d_stats, stats.data(), stats.size() * sizeof(double),
+                       cudaMemcpyHostToDevice, L->stream));
+    if (!log.empty())
+      CK(cudaMemcpyAsync(C->d_log, log.data(), log.size() * sizeof(double),
+                         cudaMemcpyHostToDevice, L->stream));
+  }
+  CK(cudaStreamSynchronize(L->stream));
+  L->pass = h.pass;
+  return COULPS_OK;
+}
+
+}  // extern "C"

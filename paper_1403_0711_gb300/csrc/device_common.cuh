@@ -1,0 +1,144 @@
+// Device helpers shared by the sweep and measurement kernels.
+//
+//   philox4x32_10     counter-based generator of Salmon, Moraes, Dror & Shaw
+//                     (SC'11), 10 rounds, Weyl key schedule.
+//   hb_noise_*        the random term -erfc^-1(2r)/sqrt(3) of the heatbath
+//                     update Eq. (phi), for r = (w + 1/2) 2^-32, w a 32-bit
+//                     Philox word.  For 2r > 1 it uses
+//                     erfc^-1(2r) = -erfc^-1(2 - 2r) so that the argument of
+//                     erfc^-1 is always the small side, u in (0, 1].
+//   mbar_* / tma_*    inline-PTX wrappers for mbarrier and cp.async.bulk.tensor
+//                     (TMA).  Every wait is bounded by wall-clock time read
+//                     from %globaltimer; a wait that gives up returns false and
+//                     the caller records COULPS_ERR_TIMEOUT.
+#pragma once
+
+#include <cstdint>
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace coulps {
+
+// Longest a single mbarrier wait may spin before giving up (ns).
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+// Small-side argument u = (t + 1/2) 2^-31 in (0, 1] and the sign of the
+// deviate: w < 2^31 means 2r < 1 and the deviate is -erfc^-1(u)/sqrt(3).
+__device__ __forceinline__ uint32_t hb_small_side(uint32_t w) {
+  return ((w >> 31) ? ~w : w) & 0x7fffffffu;
+}
+
+__device__ __forceinline__ float hb_noise_f32(uint32_t w) {
+  const float u = fmaf(__uint2float_rn(hb_small_side(w)), 0x1p-31f, 0x1p-32f);
+  const float y = erfcinvf(u) * 0.577350269189625764509f;  // 1/sqrt(3)
+  return (w >> 31) ? y : -y;
+}
+
+__device__ __forceinline__ double hb_noise_f64(uint32_t w) {
+  const double u = ((double)hb_small_side(w) + 0.5) * 0x1p-31;
+  const double y = erfcinv(u) * 0.57735026918962576450914878;  // 1/sqrt(3)
+  return (w >> 31) ? y : -y;
+}
+
+template <typename T> struct Noise;
+template <> struct Noise<float> {
+  __device__ __forceinline__ static float of(uint32_t w) { return hb_noise_f32(w); }
+};
+template <> struct Noise<double> {
+  __device__ __forceinline__ static double of(uint32_t w) { return hb_noise_f64(w); }
+};
+
+// ---------------------------------------------------------------------------
+// mbarrier / TMA
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t global_timer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait until the phase with the given parity has completed, or give up after
+// kWaitLimitNs.  Returns true on completion.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_timer_ns();
+  for (;;) {
+#pragma unroll 1
+    for (int i = 0; i < 32; ++i)
+      if (mbar_try_wait(bar, parity)) return true;
+    if (global_timer_ns() - t0 > kWaitLimitNs) return false;
+  }
+}
+
+// 4D tiled TMA load global -> shared, completion signalled on `bar`.
+// The innermost coordinate c0 must be a multiple of 16 bytes / element size;
+// every caller in this library passes c0 = 0.
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int c0, int c1,
+                                            int c2, int c3, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void prefetch_tensormap(const CUtensorMap *map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Reductions
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+}  // namespace coulps

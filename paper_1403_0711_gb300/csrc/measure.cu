@@ -1,0 +1,142 @@
+// Estimator kernels: one term of Eq. (nsum2) per chain and the running sums.
+//
+//   gather:   Q = sum_i q_i phi(r_i),  P = sum_i (q_i phi(r_i))^2
+//             Each product q_i * phi(r_i) is formed in FP64 (exact for an
+//             FP32 field), summed per thread, then by warp shuffles and a
+//             shared-memory tree into one (Q, P) partial per CTA.
+//   finalize: per chain, the CTA partials are added in a fixed order (so the
+//             result is bitwise reproducible), e = Q^2 - P is formed in FP64
+//             (the cancelling difference of the estimator), and the running
+//             sums, batch sums and optional sample log are updated.
+//
+// This replaces the paper's per-core partial sums and mpi_reduce with a
+// deterministic two-level reduction on the device.
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace coulps {
+namespace {
+
+constexpr int kGatherThreads = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(kGatherThreads)
+    gather_kernel(const T *__restrict__ field, size_t chain_elems,
+                  const uint32_t *__restrict__ idx, const double *__restrict__ q, int64_t n,
+                  double *__restrict__ partials, int nblk) {
+  const int chain = blockIdx.y;
+  const T *f = field + (size_t)chain * chain_elems;
+  double sq = 0.0, sp = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * kGatherThreads + threadIdx.x; i < n;
+       i += (int64_t)nblk * kGatherThreads) {
+    const double t = q[i] * (double)f[idx[i]];
+    sq += t;
+    sp += t * t;
+  }
+  sq = warp_sum(sq);
+  sp = warp_sum(sp);
+  __shared__ double red[2][kGatherThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][wid] = sq;
+    red[1][wid] = sp;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    sq = lane < kGatherThreads / 32 ? red[0][lane] : 0.0;
+    sp = lane < kGatherThreads / 32 ? red[1][lane] : 0.0;
+    sq = warp_sum(sq);
+    sp = warp_sum(sp);
+    if (lane == 0) {
+      partials[2 * ((size_t)chain * nblk + blockIdx.x) + 0] = sq;
+      partials[2 * ((size_t)chain * nblk + blockIdx.x) + 1] = sp;
+    }
+  }
+}
+
+__global__ void finalize_kernel(const double *__restrict__ partials, int nblk, int n_chains,
+                                double *__restrict__ stats, double *__restrict__ log,
+                                int64_t log_cap, int *err) {
+  const int chain = blockIdx.x * blockDim.x + threadIdx.x;
+  if (chain >= n_chains) return;
+  double Q = 0.0, P = 0.0;
+  for (int b = 0; b < nblk; ++b) {
+    Q += partials[2 * ((size_t)chain * nblk + b) + 0];
+    P += partials[2 * ((size_t)chain * nblk + b) + 1];
+  }
+  const double e = Q * Q - P;
+  double *st = stats + (size_t)chain * kStatStride;
+  const int64_t s = (int64_t)st[kStatN];
+  if (log != nullptr && s < log_cap) {
+    double *row = log + 3 * ((size_t)s * n_chains + chain);
+    row[0] = Q;
+    row[1] = P;
+    row[2] = e;
+  }
+  if (!isfinite(e)) atomicOr(err, kErrNonFinite);
+  st[kStatN] += 1.0;
+  st[kStatSum] += e;
+  st[kStatSum2] += e * e;
+  st[kStatCurSum] += e;
+  st[kStatCurN] += 1.0;
+  if (st[kStatCurN] >= st[kStatBatchLen]) {
+    int nb = (int)st[kStatNBatch];
+    st[kStatBatch0 + nb] = st[kStatCurSum];
+    st[kStatCurSum] = 0.0;
+    st[kStatCurN] = 0.0;
+    ++nb;
+    if (nb == 2 * kBatchMin) {
+      // merge neighbouring batches: kBatchMin batches of twice the length
+      for (int i = 0; i < kBatchMin; ++i)
+        st[kStatBatch0 + i] = st[kStatBatch0 + 2 * i] + st[kStatBatch0 + 2 * i + 1];
+      for (int i = kBatchMin; i < 2 * kBatchMin; ++i) st[kStatBatch0 + i] = 0.0;
+      nb = kBatchMin;
+      st[kStatBatchLen] *= 2.0;
+    }
+    st[kStatNBatch] = (double)nb;
+  }
+}
+
+__global__ void reset_stats_kernel(double *stats, int n_chains) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_chains * kStatStride) return;
+  stats[i] = (i % kStatStride == kStatBatchLen) ? 1.0 : 0.0;
+}
+
+}  // namespace
+
+int gather_blocks(int64_t n) {
+  // about 4 charges per thread, at least one CTA, at most 64 per chain
+  int64_t b = (n + 4 * kGatherThreads - 1) / (4 * kGatherThreads);
+  if (b < 1) b = 1;
+  if (b > 64) b = 64;
+  return (int)b;
+}
+
+cudaError_t launch_gather(const Geometry &g, const void *field, const uint32_t *idx,
+                          const double *q, int64_t n, double *partials, int nblk,
+                          cudaStream_t s) {
+  dim3 grid(nblk, g.n_chains);
+  if (g.precision == COULPS_F32)
+    gather_kernel<float><<<grid, kGatherThreads, 0, s>>>(
+        reinterpret_cast<const float *>(field), g.chain_elems, idx, q, n, partials, nblk);
+  else
+    gather_kernel<double><<<grid, kGatherThreads, 0, s>>>(
+        reinterpret_cast<const double *>(field), g.chain_elems, idx, q, n, partials, nblk);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const double *partials, int nblk, int n_chains, double *stats,
+                            double *log, int64_t log_cap, int *err, cudaStream_t s) {
+  finalize_kernel<<<(n_chains + 127) / 128, 128, 0, s>>>(partials, nblk, n_chains, stats, log,
+                                                          log_cap, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reset_stats(double *stats, int n_chains, cudaStream_t s) {
+  const int total = n_chains * kStatStride;
+  reset_stats_kernel<<<(total + 255) / 256, 256, 0, s>>>(stats, n_chains);
+  return cudaGetLastError();
+}
+
+}  // namespace coulps
