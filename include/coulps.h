@@ -205,6 +205,45 @@ int coulps_kernel_times(coulps_lattice_t lat, double out[4]);
 int coulps_checkpoint_save(coulps_lattice_t lat, coulps_charges_t ch, const char *path);
 int coulps_checkpoint_load(coulps_lattice_t lat, coulps_charges_t ch, const char *path);
 
+/* ---- allocation-free measurement --------------------------------------- */
+/* The paper has no counterpart to this entry point.  It serves callers that
+ * cannot allocate device memory when they measure: code running while a CUDA
+ * stream is being captured (cudaMalloc is not allowed there), real-time or
+ * embedded controllers that forbid allocation after start-up, and plugins
+ * whose host application has reserved all device memory.  It computes, for
+ * each of n_chains fields the caller owns, the same (Q, P, e) as
+ * coulps_measure, and allocates nothing: no cudaMalloc, no cudaFree, no
+ * allocating library call.  Its only working memory is a file-scope device
+ * array of COULPS_STATIC_SCRATCH_DOUBLES doubles (512 KiB) that every GPU
+ * loading this library holds until the process exits.
+ *   field      device pointer to n_chains fields in the library's storage
+ *              layout: field[chain][colour][z][y][h] with colour (x+y+z)&1,
+ *              h = x>>1, row stride W = 4*ceil(Lx/8) rounded up to a
+ *              multiple of 8 (FP32) or 4 (FP64) elements, every other element
+ *              0; one chain is 2*Lz*Ly*W elements (float or double by
+ *              precision).  This is the layout coulps_lattice_create uses.
+ *   site_index device pointer to n uint32 offsets within one chain's field:
+ *              colour*(Lz*Ly*W) + (z*Ly + y)*W + (x>>1).
+ *   q          device pointer to n doubles.
+ *   QPe        device pointer to 3*n_chains doubles, written as
+ *              (Q, P, e) of chain k at QPe[3k..3k+2].
+ *   stream     cudaStream_t the work is queued on (asynchronous).
+ * Limit: n_chains * b * 2 <= COULPS_STATIC_SCRATCH_DOUBLES, where
+ * b = min(64, max(1, ceil(n / 1024))) CTAs per chain; e.g. any n with up to
+ * 512 chains, or up to 32768 chains when n <= 1024.  Larger requests return
+ * COULPS_EINVAL and queue nothing.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  All calls share the one array and it keeps the
+ * last call's contents; every slot a call reads is first written by that same
+ * call, so nothing needs clearing, but calls that overlap on the GPU (for
+ * example on two streams at once) race on it and must be serialised by the
+ * caller.  Errors: EINVAL, ECUDA, EUNSUPPORTED (device ordinal >= 64). */
+#define COULPS_STATIC_SCRATCH_DOUBLES 65536
+int coulps_measure_static(const void *field, int Lx, int Ly, int Lz, int n_chains, int precision,
+                          const uint32_t *site_index, const double *q, int64_t n, double *QPe,
+                          void *stream);
+
 #ifdef __cplusplus
 }
 #endif

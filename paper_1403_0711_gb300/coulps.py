@@ -31,7 +31,7 @@ EXPORTS = (
     "coulps_measure", "coulps_run", "coulps_estimate", "coulps_samples",
     "coulps_reset_stats", "coulps_checkpoint_save", "coulps_checkpoint_load",
     "coulps_charges_update", "coulps_chain_stats", "coulps_pool_stats", "coulps_set_profiling",
-    "coulps_kernel_times",
+    "coulps_kernel_times", "coulps_measure_static",
 )
 STAT_STRIDE = 72
 
@@ -88,6 +88,7 @@ def load(path: str | Path | None = None):
         "coulps_pool_stats": (i32, [P(f64), i64, P(f64), P(f64), P(f64), P(i64)]),
         "coulps_set_profiling": (i32, [vp, i32]),
         "coulps_kernel_times": (i32, [vp, P(f64)]),
+        "coulps_measure_static": (i32, [vp, i32, i32, i32, i32, i32, vp, vp, i64, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
