@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--chains", type=int, default=N_CHAINS,
+                    help="chains per GPU (smaller values only for profiler captures)")
     return ap.parse_args()
 
 
@@ -222,6 +224,9 @@ def run_ours(args):
     import numpy as np
     import torch
 
+    n_chains = args.chains
+    sites_per_step = n_chains * L ** 3 * PASSES
+
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     if world > 1:
@@ -237,7 +242,7 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     box = (L, L, L)
     sites, q = inputs.plus_minus(box, N_CHARGES, seed=1)
-    lat = coulps.Lattice(box, n_chains=N_CHAINS, precision=coulps.F32, seed=20140303 + 7919 * rank,
+    lat = coulps.Lattice(box, n_chains=n_chains, precision=coulps.F32, seed=20140303 + 7919 * rank,
                          stream=stream)
     ch = coulps.Charges(lat, sites, q)
 
@@ -274,13 +279,13 @@ def run_ours(args):
     if world > 1:
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
     ms_max = float(t.item())
-    value = world * SITES_PER_STEP * args.steps / (ms_max / 1e3)
+    value = world * sites_per_step * args.steps / (ms_max / 1e3)
 
     # roofline of the dominant kernel: the over-relaxation half-sweep
     # (3 of the 4 passes; 12 B per updated site: read other colour, read own, write own)
     or_ms = kt["or_ms"] / max(1, kt["or_n"])
     hb_ms = kt["hb_ms"] / max(1, kt["hb_n"])
-    sites_per_launch = N_CHAINS * L ** 3 // 2
+    sites_per_launch = n_chains * L ** 3 // 2
     or_bytes = 12 * sites_per_launch
     hb_bytes = 8 * sites_per_launch
     peak, peak_kind = measured_peaks()
@@ -316,9 +321,9 @@ def run_ours(args):
     if world > 1:
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
     e2e_s = float(t.item())
-    e2e = {"value": world * SITES_PER_STEP * args.e2e_steps / e2e_s, "unit": "site-updates/s",
+    e2e = {"value": world * sites_per_step * args.e2e_steps / e2e_s, "unit": "site-updates/s",
            "h2d_bytes_per_step": N_CHARGES * (4 + 8),
-           "d2h_bytes_per_step": N_CHAINS * coulps.STAT_STRIDE * 8 + 4,
+           "d2h_bytes_per_step": n_chains * coulps.STAT_STRIDE * 8 + 4,
            "steps": args.e2e_steps,
            "path": "coulps_charges_update + coulps_run(0, 1, 1, 3) + coulps_estimate"}
 
@@ -329,7 +334,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "site-updates/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic", "config": dict(CONFIG, parallelism=f"replicas{world}"),
+            "data": "synthetic", "config": dict(CONFIG, parallelism=f"replicas{world}", n_chains_per_gpu=n_chains),
             "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "estimate_after_e2e": est,
         }
