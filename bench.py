@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--workload", choices=["chains128", "large512", "sweep", "batched"],
+                    default="chains128", help="secondary workloads print their own line")
     ap.add_argument("--chains", type=int, default=N_CHAINS,
                     help="chains per GPU (smaller values only for profiler captures)")
     return ap.parse_args()
@@ -247,8 +249,8 @@ def run_ours(args):
     ch = coulps.Charges(lat, sites, q)
 
     def step():
-        lat.sweep(1, N_HB, N_OR)
-        ch.measure()
+        # one measured compound sweep; the sample is gathered by its last half-sweep
+        ch.run(0, 1, N_HB, N_OR)
 
     lat.set_profiling(True)
     for _ in range(args.warmup):
@@ -329,7 +331,7 @@ def run_ours(args):
 
     out = None
     if rank == 0:
-        launches = args.steps * (2 * PASSES + 1 + 2)
+        launches = args.steps * (2 * PASSES + 1 + 1)  # half-sweeps, pass counter, finalize
         line = {
             "metric": METRIC, "value": value, "unit": "site-updates/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
@@ -353,9 +355,67 @@ def run_ours(args):
         print(json.dumps(out), flush=True)
 
 
+def run_extra(args):
+    """Secondary workloads (single GPU; not the headline line):
+    large512  512^3, N = 10^6 charges in 200 Gaussian blobs, 1 chain;
+    sweep     128^3 .. 512^3 at the fixed charge density N / L^3 = 0.00745;
+    batched   256 systems, edges from {32,48,64,80,96}, N log-uniform in [64, 2048]."""
+    import torch
+
+    from paper_1403_0711_gb300 import _build, coulps, inputs
+    _build.build()
+    coulps.load()
+    coulps.use_torch_allocator()
+    stream = torch.cuda.Stream()
+    results = []
+
+    def timed(step, sites_per_step, steps, warmup):
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        return sites_per_step * steps / (ms / 1e3), ms / steps
+
+    if args.workload in ("large512", "sweep"):
+        sizes = [512] if args.workload == "large512" else [128, 256, 384, 512]
+        for n in sizes:
+            box = (n, n, n)
+            nq = 1_000_000 if n == 512 else int(round(0.00745 * n ** 3))
+            sites, q = inputs.blobs(box, nq, seed=3)
+            lat = coulps.Lattice(box, n_chains=1, precision=coulps.F32, seed=77, stream=stream)
+            ch = coulps.Charges(lat, sites, q)
+            steps = max(20, min(args.steps, int(2e10 / n ** 3)))
+            rate, ms = timed(lambda: ch.run(0, 1, N_HB, N_OR), n ** 3 * PASSES, steps, 5)
+            results.append({"L": n, "n_charges": nq, "site_updates_per_s": rate, "ms_per_step": ms,
+                            "algorithmic_GBps": rate / PASSES * (8 + 12 * N_OR) / N_HB / 1e9
+                            if N_HB == 1 else None})
+            ch.close()
+            lat.close()
+    elif args.workload == "batched":
+        systems = inputs.batch_systems(256, seed=7)
+        b = coulps.Batch([L_ for L_, _, _ in systems], precision=coulps.F32, seed=77, stream=stream)
+        b.set_charges([(s_, q_) for _, s_, q_ in systems])
+        info = b.info()
+        rate, ms = timed(lambda: b.run(0, 1, N_HB, N_OR), info["sites"] * PASSES, args.steps, 10)
+        results.append({"systems": 256, "sites": info["sites"], "tiles": info["tiles"],
+                        "persistent_ctas": info["grid"], "site_updates_per_s": rate,
+                        "ms_per_step": ms,
+                        "algorithmic_GBps": rate / PASSES * (8 + 12 * N_OR) / 1e9})
+        b.close()
+    print(json.dumps({"workload": args.workload, "metric": METRIC, "results": results}), flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload != "chains128":
+        run_extra(a)
     else:
         run_ours(a)

@@ -98,7 +98,7 @@ int coulps_lattice_info(coulps_lattice_t lat, int64_t info[10]);
 
 /* Tile shape of the half-sweep kernel: ty rows of y per CTA, dz planes of z
  * per CTA (0 = keep).  Used by the autotuner; results do not depend on it.
- * Errors: EINVAL (ty*W/4 > 1024 threads, ty < 1, dz < 1). */
+ * Errors: EINVAL (ty*W/4 > 256 threads, ty < 1, dz < 1). */
 int coulps_set_tile(coulps_lattice_t lat, int ty, int dz);
 
 /* Copy chain `chain`'s field to / from a host array of Lx*Ly*Lz doubles in
@@ -138,9 +138,12 @@ void coulps_charges_destroy(coulps_charges_t ch);
  * sums.  Asynchronous.  Errors: EINVAL (charges of another lattice), ECUDA. */
 int coulps_measure(coulps_lattice_t lat, coulps_charges_t ch);
 
-/* n_therm unmeasured compound sweeps, then n_meas measured ones (one
- * coulps_measure after each).  The measured loop is captured once into a
- * CUDA graph and replayed.  Asynchronous.  Errors: EINVAL, ECUDA. */
+/* n_therm unmeasured compound sweeps, then n_meas measured ones, each
+ * followed by one sample per chain as coulps_measure takes it.  In the
+ * measured sweeps the sample is gathered by the last half-sweep itself (the
+ * charge gather fused into the sweep); the per-CTA partial sums are then
+ * added in a fixed order.  The measured loop is captured once into a CUDA
+ * graph and replayed (not on the legacy default stream, nor while profiling).  Asynchronous.  Errors: EINVAL, ECUDA. */
 int coulps_run(coulps_lattice_t lat, coulps_charges_t ch, int n_therm, int n_meas,
                int n_hb, int n_or);
 
@@ -204,6 +207,81 @@ int coulps_kernel_times(coulps_lattice_t lat, double out[4]);
  * Errors: EIO, ECORRUPT (checksum or shape mismatch), ECUDA. */
 int coulps_checkpoint_save(coulps_lattice_t lat, coulps_charges_t ch, const char *path);
 int coulps_checkpoint_load(coulps_lattice_t lat, coulps_charges_t ch, const char *path);
+
+/* ---- many independent systems ----------------------------------------- */
+/* A batch holds n_systems independent lattices of (possibly) different
+ * shapes, each with one chain and its own charge set and estimator, and
+ * sweeps them all with one launch per half-sweep: a persistent grid walks a
+ * work list of (system, y tile, z slab) tiles.  System s uses Philox counter
+ * word 2 = s (its "chain" id), so each system reproduces a one-chain lattice
+ * with that chain id.  Storage, boundary, update rules and estimator are those
+ * of the lattice API above; the measured compound sweep gathers Q, P in its
+ * last half-sweep and is replayed as one CUDA graph. */
+typedef struct coulps_batch *coulps_batch_t;
+
+/* dims[3s..3s+2] = (Lx, Ly, Lz) of system s, limits as coulps_lattice_create.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+int coulps_batch_create(int n_systems, const int32_t *dims, int precision, uint64_t seed,
+                        void *stream, coulps_batch_t *out);
+void coulps_batch_destroy(coulps_batch_t b);
+
+/* Tile shape of every system: ty_dz[2s] rows, ty_dz[2s+1] planes (0 = keep).
+ * Results do not depend on it.  Errors: EINVAL (more than 256 threads, box
+ * rows > 256, shared memory > 227 KiB). */
+int coulps_batch_set_tiles(coulps_batch_t b, const int32_t *ty_dz);
+int coulps_batch_system_tile(coulps_batch_t b, int system, int32_t *ty_dz);
+
+/* info[0..6] = n_systems, work-list tiles, persistent CTAs, shared memory
+ * bytes per CTA, pass counter, field bytes, total sites. */
+int coulps_batch_info(coulps_batch_t b, int64_t *info);
+
+/* Charges of all systems: those of system s are entries offsets[s] ..
+ * offsets[s+1]-1 of site_xyz (3 per charge, inside that system's box) and q.
+ * Replaces any previous set and resets the estimators.  log_capacity samples
+ * of (Q, P, e) per system are kept.  Errors: EINVAL, ENOMEM, ECUDA. */
+int coulps_batch_charges(coulps_batch_t b, const int64_t *offsets, const int32_t *site_xyz,
+                         const double *q, int64_t log_capacity);
+
+/* Unmeasured compound sweeps of all systems (asynchronous). */
+int coulps_batch_sweep(coulps_batch_t b, int n_compound, int n_hb, int n_or);
+
+/* n_therm unmeasured then n_meas measured compound sweeps of all systems.
+ * Errors: EINVAL (no charges, or a measured sweep with no pass), ECUDA. */
+int coulps_batch_run(coulps_batch_t b, int n_therm, int n_meas, int n_hb, int n_or);
+
+int coulps_batch_sync(coulps_batch_t b);
+
+/* Per-system estimates (arrays of n_systems; any pointer may be NULL), as
+ * coulps_estimate for a one-chain lattice.  Synchronises. */
+int coulps_batch_estimate(coulps_batch_t b, double *mean, double *stderr_bm, double *tau_int,
+                          int64_t *n);
+
+/* Logged samples: QPe[(k*n_systems + s)*3 + {0,1,2}] = (Q, P, e) of sample k
+ * of system s, for k < min(samples, cap, log_capacity).  Synchronises. */
+int coulps_batch_samples(coulps_batch_t b, double *QPe, int64_t cap, int64_t *n);
+
+/* System s's field as Lx*Ly*Lz doubles in natural order.  Synchronises. */
+int coulps_batch_field_get(coulps_batch_t b, int system, double *host_xyz);
+
+/* ---- Stein control variate kernels -------------------------------------- */
+/* Building blocks of the learned control variate (not in the paper): a small
+ * 3D conv net g(phi) whose Stein term sum_x (dg_x/dphi_x - g_x (A phi)_x) has
+ * zero mean under exp(-H_L) (integration by parts; A phi = grad H_L).
+ *
+ * coulps_cv_pack_weights (host only): PyTorch conv3d weights w[co][ci][kz][ky][kx]
+ * (16 x 16 x 3 x 3 x 3 floats) -> 27 x 256 BF16 (round to nearest even) in the
+ * order coulps_cv_conv3d reads them.
+ *
+ * coulps_cv_conv3d: h = conv3d(a, w) + bias, 3x3x3, zero padding, 16 -> 16
+ * channels, on the tensor cores (BF16 operands, FP32 accumulation).
+ *   in_bf16 device [nb][Lz][Ly][Lx][16] BF16, channels last (16-byte aligned)
+ *   wpack   device, the 27 x 256 BF16 of coulps_cv_pack_weights
+ *   bias    device, 16 floats;  out device [nb][Lz][Ly][Lx][16] FP32
+ *   err     device int; a timed-out wait ORs COULPS_ERR bit 1 into it
+ * Asynchronous on stream.  Errors: EINVAL, ECUDA. */
+int coulps_cv_pack_weights(const float *w, uint16_t *wpack);
+int coulps_cv_conv3d(const void *in_bf16, const void *wpack, const float *bias, float *out,
+                     int nb, int Lx, int Ly, int Lz, int *err, void *stream);
 
 /* ---- allocation-free measurement --------------------------------------- */
 /* The paper has no counterpart to this entry point.  It serves callers that

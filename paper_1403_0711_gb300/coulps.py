@@ -32,6 +32,10 @@ EXPORTS = (
     "coulps_reset_stats", "coulps_checkpoint_save", "coulps_checkpoint_load",
     "coulps_charges_update", "coulps_chain_stats", "coulps_pool_stats", "coulps_set_profiling",
     "coulps_kernel_times", "coulps_measure_static",
+    "coulps_batch_create", "coulps_batch_destroy", "coulps_batch_set_tiles",
+    "coulps_batch_system_tile", "coulps_batch_info", "coulps_batch_charges", "coulps_batch_sweep",
+    "coulps_batch_run", "coulps_batch_sync", "coulps_batch_estimate", "coulps_batch_samples",
+    "coulps_batch_field_get", "coulps_cv_pack_weights", "coulps_cv_conv3d",
 )
 STAT_STRIDE = 72
 
@@ -89,6 +93,20 @@ def load(path: str | Path | None = None):
         "coulps_set_profiling": (i32, [vp, i32]),
         "coulps_kernel_times": (i32, [vp, P(f64)]),
         "coulps_measure_static": (i32, [vp, i32, i32, i32, i32, i32, vp, vp, i64, vp, vp]),
+        "coulps_batch_create": (i32, [i32, P(ctypes.c_int32), i32, u64, vp, P(vp)]),
+        "coulps_batch_destroy": (None, [vp]),
+        "coulps_batch_set_tiles": (i32, [vp, P(ctypes.c_int32)]),
+        "coulps_batch_system_tile": (i32, [vp, i32, P(ctypes.c_int32)]),
+        "coulps_batch_info": (i32, [vp, P(i64)]),
+        "coulps_batch_charges": (i32, [vp, P(i64), P(ctypes.c_int32), P(f64), i64]),
+        "coulps_batch_sweep": (i32, [vp, i32, i32, i32]),
+        "coulps_batch_run": (i32, [vp, i32, i32, i32, i32]),
+        "coulps_batch_sync": (i32, [vp]),
+        "coulps_batch_estimate": (i32, [vp, P(f64), P(f64), P(f64), P(i64)]),
+        "coulps_batch_samples": (i32, [vp, P(f64), i64, P(i64)]),
+        "coulps_batch_field_get": (i32, [vp, i32, P(f64)]),
+        "coulps_cv_pack_weights": (i32, [P(ctypes.c_float), P(ctypes.c_uint16)]),
+        "coulps_cv_conv3d": (i32, [vp, vp, vp, vp, i32, i32, i32, i32, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -296,6 +314,104 @@ def pool_stats(rows):
     _check(load().coulps_pool_stats(_f64p(rows), len(rows), ctypes.byref(m), ctypes.byref(s),
                                     ctypes.byref(t), ctypes.byref(n)), "coulps_pool_stats")
     return {"mean": m.value, "stderr": s.value, "tau_int": t.value, "n": n.value}
+
+
+class Batch:
+    """Many independent one-chain systems of different shapes, swept together."""
+
+    def __init__(self, dims, precision=F32, seed=0, stream=None):
+        self._lib = load()
+        d = np.ascontiguousarray(np.asarray(dims, dtype=np.int32).reshape(-1, 3))
+        self.dims = [tuple(int(v) for v in r) for r in d]
+        self.n = len(d)
+        self.precision = int(precision)
+        h = ctypes.c_void_p()
+        _check(self._lib.coulps_batch_create(self.n, d.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                             self.precision, int(seed), _stream_handle(stream),
+                                             ctypes.byref(h)), "coulps_batch_create")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.coulps_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        a = (ctypes.c_int64 * 7)()
+        _check(self._lib.coulps_batch_info(self.handle, a), "coulps_batch_info")
+        keys = ("n_systems", "tiles", "grid", "smem", "pass", "field_bytes", "sites")
+        return dict(zip(keys, list(a)))
+
+    def set_tiles(self, ty_dz):
+        t = np.ascontiguousarray(np.asarray(ty_dz, dtype=np.int32).reshape(-1, 2))
+        assert len(t) == self.n
+        _check(self._lib.coulps_batch_set_tiles(self.handle, t.ctypes.data_as(
+            ctypes.POINTER(ctypes.c_int32))), "coulps_batch_set_tiles")
+
+    def tiles(self):
+        out = []
+        for s in range(self.n):
+            a = (ctypes.c_int32 * 2)()
+            _check(self._lib.coulps_batch_system_tile(self.handle, s, a), "coulps_batch_system_tile")
+            out.append((a[0], a[1]))
+        return out
+
+    def set_charges(self, systems, log_capacity=0):
+        """systems: list of (sites, q), one per system."""
+        assert len(systems) == self.n
+        offs = np.zeros(self.n + 1, dtype=np.int64)
+        for i, (s_, q_) in enumerate(systems):
+            offs[i + 1] = offs[i] + len(q_)
+        sites = np.ascontiguousarray(np.concatenate(
+            [np.asarray(s_, dtype=np.int32).reshape(-1, 3) for s_, _ in systems]))
+        q = np.ascontiguousarray(np.concatenate(
+            [np.asarray(q_, dtype=np.float64).reshape(-1) for _, q_ in systems]))
+        self.log_capacity = int(log_capacity)
+        _check(self._lib.coulps_batch_charges(
+            self.handle, offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+            sites.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _f64p(q), int(log_capacity)),
+            "coulps_batch_charges")
+
+    def sweep(self, n_compound=1, n_hb=1, n_or=0):
+        _check(self._lib.coulps_batch_sweep(self.handle, int(n_compound), int(n_hb), int(n_or)),
+               "coulps_batch_sweep")
+
+    def run(self, n_therm, n_meas, n_hb=1, n_or=0):
+        _check(self._lib.coulps_batch_run(self.handle, int(n_therm), int(n_meas), int(n_hb),
+                                          int(n_or)), "coulps_batch_run")
+
+    def sync(self):
+        _check(self._lib.coulps_batch_sync(self.handle), "coulps_batch_sync")
+
+    def estimate(self):
+        m, s, t = (np.empty(self.n) for _ in range(3))
+        n = np.empty(self.n, dtype=np.int64)
+        _check(self._lib.coulps_batch_estimate(self.handle, _f64p(m), _f64p(s), _f64p(t),
+                                               n.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))),
+               "coulps_batch_estimate")
+        return {"mean": m, "stderr": s, "tau_int": t, "n": n}
+
+    def samples(self, cap=None):
+        """(n_samples, n_systems, 3) array of logged (Q, P, e)."""
+        cap = self.log_capacity if cap is None else cap
+        buf = np.empty((max(1, cap), self.n, 3))
+        n = ctypes.c_int64()
+        _check(self._lib.coulps_batch_samples(self.handle, _f64p(buf), int(cap), ctypes.byref(n)),
+               "coulps_batch_samples")
+        return buf[: n.value].copy()
+
+    def field(self, system):
+        Lx, Ly, Lz = self.dims[system]
+        out = np.empty((Lz, Ly, Lx))
+        _check(self._lib.coulps_batch_field_get(self.handle, int(system), _f64p(out)),
+               "coulps_batch_field_get")
+        return out
 
 
 # C-named module functions -------------------------------------------------

@@ -21,6 +21,8 @@ namespace coulps {
 
 static Allocator g_allocator = {nullptr, nullptr, nullptr};
 
+Allocator current_allocator() { return g_allocator; }
+
 void *dev_alloc(const Allocator &a, size_t bytes, cudaStream_t s) {
   if (bytes == 0) bytes = 16;
   if (a.alloc) return a.alloc(bytes, (void *)s, a.ctx);
@@ -87,6 +89,22 @@ struct coulps_charges {
   uint32_t *h_idx = nullptr;
   double *h_q = nullptr;
   cudaEvent_t staged = nullptr;  // recorded after the last upload's copies
+  // host copy of the set (to regroup it for the fused gather)
+  std::vector<int32_t> sites;
+  std::vector<double> qv;
+  // fused gather: charges grouped by (y tile, z plane) of the lattice's tile
+  bool gather_dirty = true;
+  Tile gather_tile = {0, 0};
+  size_t goff_n = 0;
+  uint32_t *d_goff = nullptr, *d_gent = nullptr;
+  double *d_gq = nullptr;
+  double *d_fpart = nullptr;  // [chain][y tiles * z slabs][2]
+  size_t fpart_n = 0;
+  int fused_nblk = 0;
+  uint32_t *h_goff = nullptr, *h_gent = nullptr;
+  double *h_gq = nullptr;
+  size_t h_goff_cap = 0;
+  cudaEvent_t gstaged = nullptr;
 };
 
 namespace {
@@ -100,7 +118,9 @@ namespace {
     }                                     \
   } while (0)
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+}  // namespace
+
+PFN_cuTensorMapEncodeTiled_v12000 coulps::tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
     void *p = nullptr;
@@ -114,10 +134,12 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
+namespace {
+
 // 4D map over field[chain*2 + colour][z][y][h] with a box of `rows` rows of W
 // elements of one plane.  Out-of-range boxes read as zeros.
 int make_map(CUtensorMap *m, const Geometry &g, void *base, int rows) {
-  auto fn = encode_fn();
+  auto fn = tensor_map_encoder();
   if (!fn) return COULPS_ECUDA;
   cuuint64_t dims[4] = {(cuuint64_t)g.W, (cuuint64_t)g.Ly, (cuuint64_t)g.Lz,
                         (cuuint64_t)g.n_chains * 2};
@@ -179,24 +201,37 @@ cudaEvent_t take_event(coulps_lattice *L) {
   return e;
 }
 
-int enqueue_compound(coulps_lattice *L, int n_hb, int n_or) {
+int enqueue_compound(coulps_lattice *L, int n_hb, int n_or, coulps_charges *fuse = nullptr) {
   SweepArgs a;
   a.field = L->field;
   a.Lx = L->g.Lx; a.Ly = L->g.Ly; a.Lz = L->g.Lz;
   a.W = L->g.W; a.Wq = L->g.Wq; a.QW = L->g.W / 4;
   a.TY = L->tile.ty; a.DZ = L->tile.dz;
-  a.seed_lo = (uint32_t)(L->seed & 0xffffffffu);
-  a.seed_hi = (uint32_t)(L->seed >> 32);
+  {
+    const PhiloxKeys K = philox_keys((uint32_t)(L->seed & 0xffffffffu), (uint32_t)(L->seed >> 32));
+    for (int i = 0; i < 20; ++i) a.round_keys[i] = K.k[i];
+  }
   a.pass_ptr = L->d_pass;
   a.chain_elems = L->g.chain_elems;
   a.colour_elems = L->g.colour_elems;
   a.err = L->d_err;
+  a.g_off = nullptr;
+  a.g_ent = nullptr;
+  a.g_q = nullptr;
+  a.g_partials = nullptr;
   uint32_t off = 0;
   for (int i = 0; i < n_hb + n_or; ++i, ++off) {
     const bool orx = i >= n_hb;
     for (int c = 0; c < 2; ++c) {
       a.colour = c;
       a.pass_off = off;
+      if (fuse && i == n_hb + n_or - 1 && c == 1) {
+        // last half-sweep of the compound sweep: gather Q, P in the same pass
+        a.g_off = fuse->d_goff;
+        a.g_ent = fuse->d_gent;
+        a.g_q = fuse->d_gq;
+        a.g_partials = fuse->d_fpart;
+      }
       cudaEvent_t ea = nullptr, eb = nullptr;
       if (L->profiling) {
         ea = take_event(L);
@@ -212,6 +247,94 @@ int enqueue_compound(coulps_lattice *L, int n_hb, int n_or) {
     }
   }
   if (n_hb + n_or > 0) CK(launch_advance_pass(L->d_pass, (uint32_t)(n_hb + n_or), L->stream));
+  if (fuse)
+    CK(launch_finalize(fuse->d_fpart, fuse->fused_nblk, L->g.n_chains, fuse->d_stats, fuse->d_log,
+                       fuse->log_cap, L->d_err, L->stream));
+  return COULPS_OK;
+}
+
+void drop_graph(coulps_lattice *L);
+
+// Group the charge set by (y tile, z plane) of the lattice's current tile and
+// queue the upload of the lists the fused gather reads.  Buffers are reused
+// when their sizes do not change, so a captured graph stays valid.
+int stage_gather(coulps_lattice *L, coulps_charges *C) {
+  const Geometry &g = L->g;
+  const Tile t = L->tile;
+  if (!C->gather_dirty && C->gather_tile.ty == t.ty && C->gather_tile.dz == t.dz) return COULPS_OK;
+  const int ytiles = (g.Ly + t.ty - 1) / t.ty, zslabs = (g.Lz + t.dz - 1) / t.dz;
+  const size_t goff_n = (size_t)ytiles * g.Lz + 1;
+  const size_t n = (size_t)C->n;
+  const size_t fpart_n = (size_t)g.n_chains * ytiles * zslabs * 2;
+  if (goff_n != C->goff_n || !C->d_goff) {
+    drop_graph(L);
+    dev_free(L->alloc, C->d_goff, L->stream);
+    C->d_goff = (uint32_t *)dev_alloc(L->alloc, goff_n * sizeof(uint32_t), L->stream);
+    if (!C->d_goff) return COULPS_ENOMEM;
+    C->goff_n = goff_n;
+  }
+  if (!C->d_gent) {
+    C->d_gent = (uint32_t *)dev_alloc(L->alloc, n * sizeof(uint32_t), L->stream);
+    C->d_gq = (double *)dev_alloc(L->alloc, n * sizeof(double), L->stream);
+    if (!C->d_gent || !C->d_gq) return COULPS_ENOMEM;
+  }
+  if (fpart_n != C->fpart_n || !C->d_fpart) {
+    drop_graph(L);
+    dev_free(L->alloc, C->d_fpart, L->stream);
+    C->d_fpart = (double *)dev_alloc(L->alloc, fpart_n * sizeof(double), L->stream);
+    if (!C->d_fpart) return COULPS_ENOMEM;
+    C->fpart_n = fpart_n;
+  }
+  C->fused_nblk = ytiles * zslabs;
+  if (!C->gstaged) {
+    if (cudaEventCreateWithFlags(&C->gstaged, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return COULPS_ECUDA;
+    }
+    if (n > 0 && (cudaMallocHost((void **)&C->h_gent, n * sizeof(uint32_t)) != cudaSuccess ||
+                  cudaMallocHost((void **)&C->h_gq, n * sizeof(double)) != cudaSuccess)) {
+      cudaGetLastError();
+      return COULPS_ENOMEM;
+    }
+  } else {
+    CK(cudaEventSynchronize(C->gstaged));  // the previous upload has left the staging
+  }
+  if (goff_n > C->h_goff_cap) {
+    if (C->h_goff) cudaFreeHost(C->h_goff);
+    C->h_goff = nullptr;
+    if (cudaMallocHost((void **)&C->h_goff, goff_n * sizeof(uint32_t)) != cudaSuccess) {
+      cudaGetLastError();
+      C->h_goff_cap = 0;
+      return COULPS_ENOMEM;
+    }
+    C->h_goff_cap = goff_n;
+  }
+  // counting sort by key = y_tile * Lz + z
+  std::vector<uint32_t> count(goff_n, 0);
+  for (size_t i = 0; i < n; ++i) {
+    const int y = C->sites[3 * i + 1], z = C->sites[3 * i + 2];
+    count[(size_t)(y / t.ty) * g.Lz + z + 1]++;
+  }
+  for (size_t k = 1; k < goff_n; ++k) count[k] += count[k - 1];
+  for (size_t k = 0; k < goff_n; ++k) C->h_goff[k] = count[k];
+  for (size_t i = 0; i < n; ++i) {
+    const int x = C->sites[3 * i], y = C->sites[3 * i + 1], z = C->sites[3 * i + 2];
+    const int yt = y / t.ty;
+    const uint32_t pos = count[(size_t)yt * g.Lz + z]++;
+    const uint32_t colour = (uint32_t)((x + y + z) & 1);
+    C->h_gent[pos] = (colour << 31) | (uint32_t)((y - yt * t.ty) * g.W + (x >> 1));
+    C->h_gq[pos] = C->qv[i];
+  }
+  CK(cudaMemcpyAsync(C->d_goff, C->h_goff, goff_n * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                     L->stream));
+  if (n > 0) {
+    CK(cudaMemcpyAsync(C->d_gent, C->h_gent, n * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                       L->stream));
+    CK(cudaMemcpyAsync(C->d_gq, C->h_gq, n * sizeof(double), cudaMemcpyHostToDevice, L->stream));
+  }
+  CK(cudaEventRecord(C->gstaged, L->stream));
+  C->gather_tile = t;
+  C->gather_dirty = false;
   return COULPS_OK;
 }
 
@@ -352,7 +475,7 @@ int coulps_set_tile(coulps_lattice_t L, int ty, int dz) {
   if (ty > 0) t.ty = ty;
   if (dz > 0) t.dz = dz;
   if (ty < 0 || dz < 0 || t.ty < 1 || t.dz < 1 || t.ty + 2 > 256) return COULPS_EINVAL;
-  if ((L->g.W / 4) * t.ty > 1024) return COULPS_EINVAL;
+  if ((L->g.W / 4) * t.ty > 256) return COULPS_EINVAL;
   if (halfsweep_smem_bytes(L->g, t, true) > 227 * 1024) return COULPS_EINVAL;
   L->tile = t;
   drop_graph(L);
@@ -437,6 +560,13 @@ int coulps_charges_create(coulps_lattice_t L, int64_t n, const int32_t *site, co
   if (!C) return COULPS_ENOMEM;
   C->lat = L;
   C->n = n;
+  try {
+    C->sites.assign(site, site + 3 * n);
+    C->qv.assign(q, q + n);
+  } catch (...) {
+    delete C;
+    return COULPS_ENOMEM;
+  }
   C->nblk = gather_blocks(n);
   C->log_cap = log_capacity;
   const size_t b_idx = sizeof(uint32_t) * (size_t)n, b_q = sizeof(double) * (size_t)n;
@@ -493,6 +623,17 @@ void coulps_charges_destroy(coulps_charges_t C) {
   }
   if (C->h_idx) cudaFreeHost(C->h_idx);
   if (C->h_q) cudaFreeHost(C->h_q);
+  if (C->gstaged) {
+    cudaEventSynchronize(C->gstaged);
+    cudaEventDestroy(C->gstaged);
+  }
+  if (C->h_goff) cudaFreeHost(C->h_goff);
+  if (C->h_gent) cudaFreeHost(C->h_gent);
+  if (C->h_gq) cudaFreeHost(C->h_gq);
+  dev_free(L->alloc, C->d_goff, L->stream);
+  dev_free(L->alloc, C->d_gent, L->stream);
+  dev_free(L->alloc, C->d_gq, L->stream);
+  dev_free(L->alloc, C->d_fpart, L->stream);
   L->n_charge_sets--;
   delete C;
 }
@@ -509,14 +650,20 @@ int coulps_run(coulps_lattice_t L, coulps_charges_t C, int n_therm, int n_meas, 
   int st = coulps_sweep(L, n_therm, n_hb, n_or);
   if (st) return st;
   if (n_meas == 0) return COULPS_OK;
+  // The measured sweeps gather Q, P inside their last half-sweep.
+  const bool fused = n_hb + n_or > 0;
+  if (fused) {
+    st = stage_gather(L, C);
+    if (st) return st;
+  }
   const bool capturable = L->stream != nullptr && !L->profiling;
   if (capturable && (L->graph_key != C || L->graph_hb != n_hb || L->graph_or != n_or ||
                      L->graph_tile.ty != L->tile.ty || L->graph_tile.dz != L->tile.dz)) {
     drop_graph(L);
     cudaGraph_t gr = nullptr;
     CK(cudaStreamBeginCapture(L->stream, cudaStreamCaptureModeThreadLocal));
-    int s1 = enqueue_compound(L, n_hb, n_or);
-    int s2 = s1 ? s1 : enqueue_measure(L, C);
+    int s1 = enqueue_compound(L, n_hb, n_or, fused ? C : nullptr);
+    int s2 = s1 ? s1 : (fused ? COULPS_OK : enqueue_measure(L, C));
     cudaError_t e = cudaStreamEndCapture(L->stream, &gr);
     if (s2 || e != cudaSuccess) {
       cudaGetLastError();
@@ -539,8 +686,8 @@ int coulps_run(coulps_lattice_t L, coulps_charges_t C, int n_therm, int n_meas, 
     if (capturable) {
       CK(cudaGraphLaunch(L->graph, L->stream));
     } else {
-      st = enqueue_compound(L, n_hb, n_or);
-      if (!st) st = enqueue_measure(L, C);
+      st = enqueue_compound(L, n_hb, n_or, fused ? C : nullptr);
+      if (!st && !fused) st = enqueue_measure(L, C);
       if (st) return st;
     }
     L->pass += (uint64_t)(n_hb + n_or);
@@ -659,6 +806,9 @@ int coulps_charges_update(coulps_charges_t C, const int32_t *site, const double 
     C->h_idx[i] = (uint32_t)((size_t)c * g.colour_elems + ((size_t)z * g.Ly + y) * g.W + (x >> 1));
     C->h_q[i] = q[i];
   }
+  for (int64_t i = 0; i < 3 * n; ++i) C->sites[i] = site[i];
+  for (int64_t i = 0; i < n; ++i) C->qv[i] = q[i];
+  C->gather_dirty = true;
   CK(cudaMemcpyAsync(C->d_idx, C->h_idx, sizeof(uint32_t) * (size_t)n, cudaMemcpyHostToDevice,
                      L->stream));
   CK(cudaMemcpyAsync(C->d_q, C->h_q, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice,

@@ -24,16 +24,13 @@ namespace coulps {
 // Longest a single mbarrier wait may spin before giving up (ns).
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
 
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const PhiloxKeys &K) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    if (r > 0) {
-      k0 += 0x9E3779B9u;
-      k1 += 0xBB67AE85u;
-    }
-    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
-    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
+    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ K.k[2 * r], (uint32_t)p1,
+                   (uint32_t)(p0 >> 32) ^ c.w ^ K.k[2 * r + 1], (uint32_t)p0);
   }
   return c;
 }
@@ -139,6 +136,41 @@ __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
+}
+
+// One sample of one chain (or system): e = Q^2 - P formed in FP64 (the
+// cancelling difference of Eq. (nsum2)), then the running sums, the batch
+// sums (kBatchMin..2*kBatchMin batches; neighbours merge and the batch length
+// doubles when 2*kBatchMin complete) and, if row != nullptr, the log row.
+__device__ __forceinline__ void record_sample(double *st, double Q, double P, double *row,
+                                              int *err) {
+  const double e = Q * Q - P;
+  if (row != nullptr) {
+    row[0] = Q;
+    row[1] = P;
+    row[2] = e;
+  }
+  if (!isfinite(e)) atomicOr(err, kErrNonFinite);
+  st[kStatN] += 1.0;
+  st[kStatSum] += e;
+  st[kStatSum2] += e * e;
+  st[kStatCurSum] += e;
+  st[kStatCurN] += 1.0;
+  if (st[kStatCurN] >= st[kStatBatchLen]) {
+    int nb = (int)st[kStatNBatch];
+    st[kStatBatch0 + nb] = st[kStatCurSum];
+    st[kStatCurSum] = 0.0;
+    st[kStatCurN] = 0.0;
+    ++nb;
+    if (nb == 2 * kBatchMin) {
+      for (int i = 0; i < kBatchMin; ++i)
+        st[kStatBatch0 + i] = st[kStatBatch0 + 2 * i] + st[kStatBatch0 + 2 * i + 1];
+      for (int i = kBatchMin; i < 2 * kBatchMin; ++i) st[kStatBatch0 + i] = 0.0;
+      nb = kBatchMin;
+      st[kStatBatchLen] *= 2.0;
+    }
+    st[kStatNBatch] = (double)nb;
+  }
 }
 
 }  // namespace coulps

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cstddef>
@@ -39,16 +40,42 @@ struct Tile {
   int dz;  // planes of z per CTA
 };
 
+// Round keys of Philox4x32-10's Weyl schedule: (k0 + r W0, k1 + r W1), r = 0..9.
+struct PhiloxKeys {
+  uint32_t k[20];
+};
+
+__host__ __device__ inline PhiloxKeys philox_keys(uint32_t k0, uint32_t k1) {
+  PhiloxKeys K;
+  for (int r = 0; r < 10; ++r) {
+    K.k[2 * r] = k0 + (uint32_t)r * 0x9E3779B9u;
+    K.k[2 * r + 1] = k1 + (uint32_t)r * 0xBB67AE85u;
+  }
+  return K;
+}
+
 struct SweepArgs {
   void *field;
   int Lx, Ly, Lz, W, Wq, QW, TY, DZ;
   int colour;
-  uint32_t seed_lo, seed_hi;
+  uint32_t round_keys[20];  // Philox round keys of the lattice's seed
   const uint32_t *pass_ptr;  // device pass counter
   uint32_t pass_off;         // added to *pass_ptr
   size_t chain_elems, colour_elems;
   int *err;
+  // Fused gather (used on the last half-sweep of a measured compound sweep;
+  // null otherwise).  Charges are grouped by (y tile, z plane) of the launch's
+  // tile shape: entries of tile column ty_idx and plane z are
+  // [g_off[ty_idx*Lz + z], g_off[ty_idx*Lz + z + 1]).  An entry packs the
+  // colour in bit 31 and r*W + h in bits 0..30 (r = y - y0, h = x >> 1).
+  const uint32_t *g_off;
+  const uint32_t *g_ent;
+  const double *g_q;
+  double *g_partials;  // [chain][y tiles * z slabs][2]
 };
+
+// Entry packing of the fused gather.
+constexpr uint32_t kGatherColourBit = 0x80000000u;
 
 // Estimator state, per chain, in doubles.
 constexpr int kBatchMin = 32;  // batches kept per chain: between kBatchMin and 2*kBatchMin
@@ -62,6 +89,12 @@ struct Allocator {
   coulps_free_fn free_fn;
   void *ctx;
 };
+
+// cuTensorMapEncodeTiled from the driver, looked up once (NULL if missing).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
+
+// The allocation hooks installed by coulps_set_allocator (NULLs = default).
+Allocator current_allocator();
 
 void *dev_alloc(const Allocator &a, size_t bytes, cudaStream_t s);
 void dev_free(const Allocator &a, void *p, cudaStream_t s);

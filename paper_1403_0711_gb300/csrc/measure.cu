@@ -64,37 +64,10 @@ __global__ void finalize_kernel(const double *__restrict__ partials, int nblk, i
     Q += partials[2 * ((size_t)chain * nblk + b) + 0];
     P += partials[2 * ((size_t)chain * nblk + b) + 1];
   }
-  const double e = Q * Q - P;
   double *st = stats + (size_t)chain * kStatStride;
   const int64_t s = (int64_t)st[kStatN];
-  if (log != nullptr && s < log_cap) {
-    double *row = log + 3 * ((size_t)s * n_chains + chain);
-    row[0] = Q;
-    row[1] = P;
-    row[2] = e;
-  }
-  if (!isfinite(e)) atomicOr(err, kErrNonFinite);
-  st[kStatN] += 1.0;
-  st[kStatSum] += e;
-  st[kStatSum2] += e * e;
-  st[kStatCurSum] += e;
-  st[kStatCurN] += 1.0;
-  if (st[kStatCurN] >= st[kStatBatchLen]) {
-    int nb = (int)st[kStatNBatch];
-    st[kStatBatch0 + nb] = st[kStatCurSum];
-    st[kStatCurSum] = 0.0;
-    st[kStatCurN] = 0.0;
-    ++nb;
-    if (nb == 2 * kBatchMin) {
-      // merge neighbouring batches: kBatchMin batches of twice the length
-      for (int i = 0; i < kBatchMin; ++i)
-        st[kStatBatch0 + i] = st[kStatBatch0 + 2 * i] + st[kStatBatch0 + 2 * i + 1];
-      for (int i = kBatchMin; i < 2 * kBatchMin; ++i) st[kStatBatch0 + i] = 0.0;
-      nb = kBatchMin;
-      st[kStatBatchLen] *= 2.0;
-    }
-    st[kStatNBatch] = (double)nb;
-  }
+  double *row = (log != nullptr && s < log_cap) ? log + 3 * ((size_t)s * n_chains + chain) : nullptr;
+  record_sample(st, Q, P, row, err);
 }
 
 __global__ void reset_stats_kernel(double *stats, int n_chains) {

@@ -1,0 +1,294 @@
+// Per-tile z-march shared by the single-lattice and the many-system
+// half-sweep kernels (see sweep.cu for the design).
+#pragma once
+
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace coulps {
+namespace tile {
+
+constexpr int kStages = 4;
+
+__host__ __device__ inline int round_up_int(int v, int m) { return (v + m - 1) / m * m; }
+
+struct SmemLayout {
+  int halo_bytes;  // exact TMA box bytes of the other colour: (TY + 2) * W * es
+  int own_bytes;   // exact TMA box bytes of the own colour: TY * W * es (OR only)
+  int slot_bytes;  // one ring slot, both boxes, each rounded to 128 bytes
+  int out_bytes;   // fused gather: this plane's new values, TY * W * es
+  int total;       // header (barriers, flags, reduction) + ring + out, no alignment slack
+};
+
+// barriers at 0, abort flag at 64, block reduction (2 x 32 doubles) at 128
+constexpr int kHeaderBytes = 1024;
+
+__host__ __device__ inline SmemLayout smem_layout(int TY, int W, int es, bool orx, bool gather) {
+  SmemLayout L;
+  L.halo_bytes = (TY + 2) * W * es;
+  L.own_bytes = orx ? TY * W * es : 0;
+  L.slot_bytes = round_up_int(L.halo_bytes, 128) + round_up_int(L.own_bytes, 128);
+  L.out_bytes = gather ? round_up_int(TY * W * es, 128) : 0;
+  L.total = kHeaderBytes + kStages * L.slot_bytes + L.out_bytes;
+  return L;
+}
+
+template <typename T>
+__device__ __forceinline__ void ld_quad(const T *p, T (&v)[4]);
+template <>
+__device__ __forceinline__ void ld_quad<float>(const float *p, float (&v)[4]) {
+  const float4 f = *reinterpret_cast<const float4 *>(p);
+  v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
+}
+template <>
+__device__ __forceinline__ void ld_quad<double>(const double *p, double (&v)[4]) {
+  const double2 a = reinterpret_cast<const double2 *>(p)[0];
+  const double2 b = reinterpret_cast<const double2 *>(p)[1];
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
+template <typename T>
+__device__ __forceinline__ void st_quad(T *p, const T (&v)[4]);
+template <>
+__device__ __forceinline__ void st_quad<float>(float *p, const float (&v)[4]) {
+  *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+template <>
+__device__ __forceinline__ void st_quad<double>(double *p, const double (&v)[4]) {
+  reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+}
+
+template <typename T> struct Coef;
+template <> struct Coef<float> {
+  static constexpr float sixth = 0.166666666666666666667f;
+  static constexpr float third = 0.333333333333333333333f;
+};
+template <> struct Coef<double> {
+  static constexpr double sixth = 0.166666666666666666667;
+  static constexpr double third = 0.333333333333333333333;
+};
+
+// One tile of one half-sweep: TY rows (all of x) of one chain, planes
+// z0 .. z0+nz-1, streamed as described at the top of this file.
+template <typename T>
+struct TileJob {
+  const CUtensorMap *tm_halo, *tm_own;
+  int map_other, map_own;  // 4th TMA coordinate of the other / own colour
+  T *out;                  // own colour of this chain: element (z*Ly + y)*W + h
+  int Lx, Ly, Lz, W, Wq, QW, TY;
+  int y0, z0, nz;
+  int colour;
+  uint32_t rng_id;  // Philox counter word 2 (chain)
+  uint32_t pass;    // Philox counter word 1
+  const uint32_t *g_off, *g_ent;  // fused gather of this tile column (GATHER only)
+  const double *g_q;
+};
+
+// Shared-memory ring header: kStages mbarriers and the abort flag.  Done
+// once per CTA; the barriers' phases then run on across every tile the CTA
+// streams (see `gbase` below).
+__device__ __forceinline__ void ring_init(unsigned char *smem) {
+  if (threadIdx.x == 0) {
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
+    for (int s = 0; s < kStages; ++s) mbar_init(smem_addr(&bars[s]), 1);
+    *reinterpret_cast<volatile int *>(smem + 64) = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+}
+
+// Runs the tile; with GATHER also accumulates this thread's share of
+// Q = sum q phi and P = sum (q phi)^2 over the tile's charges into (sq, sp).
+// `gbase` counts the planes this CTA has already streamed through its ring
+// (the ring position and barrier phases continue from there) and is advanced
+// past this tile's planes.  Returns false if a bounded wait gave up (the error
+// word is set and no copy is left in flight).
+template <typename T, bool OR, bool GATHER>
+__device__ bool march_tile(const TileJob<T> &j, const PhiloxKeys &K, unsigned char *smem,
+                           int *err, int &gbase, double &sq, double &sp) {
+  const SmemLayout lay = smem_layout(j.TY, j.W, (int)sizeof(T), OR, GATHER);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem);  // kStages barriers
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 64);
+  unsigned char *ring = smem + kHeaderBytes;
+  T *outbuf = reinterpret_cast<T *>(ring + kStages * lay.slot_bytes);
+  auto halo_slot = [&](int s) -> T * {
+    return reinterpret_cast<T *>(ring + s * lay.slot_bytes);
+  };
+  auto own_slot = [&](int s) -> T * {
+    return reinterpret_cast<T *>(ring + s * lay.slot_bytes + round_up_int(lay.halo_bytes, 128));
+  };
+
+  const int tid = threadIdx.x;
+  const int W = j.W;
+  const int qx = tid % j.QW, ty = tid / j.QW;
+  const int n_planes = j.nz + 2;  // other-colour planes z0-1 .. z0+nz
+  const int c = j.colour;
+  const int y = j.y0 + ty;
+  // A CTA may have more threads than the tile has quads (the many-system
+  // kernel runs tiles of different shapes with one block size): threads past
+  // row TY - 1 touch no shared or global memory of the tile.
+  const bool in_tile = ty < j.TY;
+  const bool live = in_tile && (y < j.Ly) && (qx < j.Wq);
+
+  const int gb = gbase;
+  if (tid == 0) {
+    prefetch_tensormap(j.tm_halo);
+    if (OR) prefetch_tensormap(j.tm_own);
+  }
+
+  // Plane k of this tile is other-colour plane z0 - 1 + k; it is ring plane
+  // gb + k, in slot (gb + k) % kStages, completed in that slot's phase
+  // (gb + k) / kStages.
+  auto slot_of = [&](int k) { return (gb + k) % kStages; };
+  auto issue = [&](int k) {
+    const int s = slot_of(k);
+    const uint32_t bar = smem_addr(&bars[s]);
+    const bool own = OR && k >= 1 && k <= j.nz;
+    mbar_arrive_expect_tx(bar, lay.halo_bytes + (own ? lay.own_bytes : 0));
+    tma_load_4d(smem_addr(halo_slot(s)), j.tm_halo, 0, j.y0 - 1, j.z0 - 1 + k, j.map_other, bar);
+    if (own) tma_load_4d(smem_addr(own_slot(s)), j.tm_own, 0, j.y0, j.z0 - 1 + k, j.map_own, bar);
+  };
+  auto wait_plane = [&](int k) -> bool {
+    return mbar_wait_bounded(smem_addr(&bars[slot_of(k)]), (uint32_t)(((gb + k) / kStages) & 1));
+  };
+
+  int issued = 0;  // meaningful in thread 0 only
+  if (tid == 0)
+    for (; issued < min(kStages, n_planes); ++issued) issue(issued);
+
+  T cm[4] = {T(0), T(0), T(0), T(0)}, c0[4] = {T(0), T(0), T(0), T(0)}, cp[4];
+  bool ok = wait_plane(0);
+  if (ok && in_tile) ld_quad(halo_slot(slot_of(0)) + (ty + 1) * W + 4 * qx, cm);
+  ok = ok && wait_plane(1);
+  if (ok && in_tile) ld_quad(halo_slot(slot_of(1)) + (ty + 1) * W + 4 * qx, c0);
+  if (!ok) {
+    atomicOr(err, kErrTimeout);
+    *abort_flag = 1;
+  }
+  __syncthreads();
+  bool aborted = *abort_flag != 0;
+  int done = 1;  // planes 0..done completed for every thread
+  if (!aborted) {
+    if (tid == 0 && issued < n_planes) issue(issued++);
+    for (int k = 1; k <= j.nz; ++k) {
+      const bool got = wait_plane(k + 1);
+      const int z = j.z0 + k - 1;
+      const T *Pz = halo_slot(slot_of(k));
+      if (got) {
+        if (in_tile) {
+          ld_quad(halo_slot(slot_of(k + 1)) + (ty + 1) * W + 4 * qx, cp);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) cp[i] = T(0);
+        }
+        if (live) {
+          T ym[4], yp[4], xs[4], S[4], v[4];
+          ld_quad(Pz + ty * W + 4 * qx, ym);
+          ld_quad(Pz + (ty + 2) * W + 4 * qx, yp);
+          const int par = (c + y + z) & 1;  // row holds x = 2h + par
+          if (par == 0) {
+            // x - 1 of h lies at h - 1 in the other colour, x + 1 at h
+            xs[0] = qx > 0 ? Pz[(ty + 1) * W + 4 * qx - 1] : T(0);
+            xs[1] = c0[0]; xs[2] = c0[1]; xs[3] = c0[2];
+          } else {
+            // x - 1 of h lies at h, x + 1 at h + 1
+            xs[0] = c0[1]; xs[1] = c0[2]; xs[2] = c0[3];
+            xs[3] = (4 * qx + 4 < W) ? Pz[(ty + 1) * W + 4 * qx + 4] : T(0);
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i) S[i] = ((cm[i] + cp[i]) + (ym[i] + yp[i])) + (c0[i] + xs[i]);
+          if (!OR) {
+            const uint32_t quad = ((uint32_t)z * (uint32_t)j.Ly + (uint32_t)y) * (uint32_t)j.Wq +
+                                  (uint32_t)qx;
+            const uint4 w = philox4x32_10(make_uint4(quad, j.pass, j.rng_id, (uint32_t)c), K);
+            v[0] = fma(S[0], Coef<T>::sixth, Noise<T>::of(w.x));
+            v[1] = fma(S[1], Coef<T>::sixth, Noise<T>::of(w.y));
+            v[2] = fma(S[2], Coef<T>::sixth, Noise<T>::of(w.z));
+            v[3] = fma(S[3], Coef<T>::sixth, Noise<T>::of(w.w));
+          } else {
+            T old[4];
+            ld_quad(own_slot(slot_of(k)) + ty * W + 4 * qx, old);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) v[i] = fma(S[i], Coef<T>::third, -old[i]);
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            if (2 * (4 * qx + i) + par >= j.Lx) v[i] = T(0);  // keep the row padding at 0
+          st_quad(j.out + ((size_t)z * j.Ly + y) * W + 4 * qx, v);
+          if (GATHER) st_quad(outbuf + ty * W + 4 * qx, v);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          cm[i] = c0[i];
+          c0[i] = cp[i];
+        }
+      } else {
+        atomicOr(err, kErrTimeout);
+        *abort_flag = 1;
+      }
+      if (GATHER) {
+        // Q and P over the charges of this plane of the tile: the own colour
+        // from the values just computed, the other colour from the ring.
+        __syncthreads();
+        if (!*abort_flag) {
+          const uint32_t e1 = j.g_off[z + 1];
+          for (uint32_t e = j.g_off[z] + tid; e < e1; e += blockDim.x) {
+            const uint32_t ent = j.g_ent[e];
+            const uint32_t idx = ent & ~kGatherColourBit;
+            const bool own = ((ent >> 31) & 1u) == (uint32_t)c;
+            const T val = own ? outbuf[idx] : Pz[W + idx];
+            const double t = j.g_q[e] * (double)val;
+            sq += t;
+            sp += t * t;
+          }
+        }
+      }
+      __syncthreads();
+      if (*abort_flag) {
+        aborted = true;
+        break;
+      }
+      done = k + 1;
+      // plane k is no longer read: refill its slot with plane k + kStages
+      if (tid == 0 && issued < n_planes) issue(issued++);
+    }
+  }
+  if (aborted && tid == 0) {
+    // Leave no copy in flight into this CTA's shared memory.
+    for (int k = done + 1; k < issued; ++k)
+      if (!wait_plane(k)) break;
+  }
+  gbase = gb + n_planes;
+  return !aborted;
+}
+
+// Block reduction of (sq, sp) into one partial per CTA (fixed order).
+__device__ __forceinline__ void block_partials(double sq, double sp, unsigned char *smem,
+                                               double *out) {
+  double *red = reinterpret_cast<double *>(smem + 128);  // 2 x 32 doubles
+  sq = warp_sum(sq);
+  sp = warp_sum(sp);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (lane == 0) {
+    red[wid] = sq;
+    red[32 + wid] = sp;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    sq = lane < nw ? red[lane] : 0.0;
+    sp = lane < nw ? red[32 + lane] : 0.0;
+    sq = warp_sum(sq);
+    sp = warp_sum(sp);
+    if (lane == 0) {
+      out[0] = sq;
+      out[1] = sp;
+    }
+  }
+  __syncthreads();  // red[] is free again
+}
+
+}  // namespace tile
+}  // namespace coulps
