@@ -1,0 +1,55 @@
+"""The tcgen05 BF16 3x3x3 convolution (16 -> 16 channels, FP32 accumulate)
+against a plain PyTorch FP32 conv3d of the same BF16-rounded operands."""
+import ctypes
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1403_0711_gb300 import _build, coulps
+    _build.build()
+    lib = coulps.load()
+    return torch, coulps, lib
+
+
+def _pack(lib, w):
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    out = np.zeros(27 * 256, dtype=np.uint16)
+    assert lib.coulps_cv_pack_weights(w.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                      out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint16))) == 0
+    return out
+
+
+@pytest.mark.parametrize("shape", [(2, 5, 4, 128), (1, 3, 7, 37), (2, 4, 3, 130), (1, 1, 1, 1),
+                                   (1, 6, 5, 300)])
+def test_conv3d_matches_torch(env, shape):
+    torch, coulps, lib = env
+    nb, Lz, Ly, Lx = shape
+    g = torch.Generator().manual_seed(sum(shape))
+    a = torch.randn(nb, Lz, Ly, Lx, 16, generator=g).to(torch.bfloat16)
+    w = (torch.randn(16, 16, 3, 3, 3, generator=g) * 0.2).to(torch.bfloat16).float()
+    bias = torch.randn(16, generator=g)
+    ref = torch.nn.functional.conv3d(a.float().permute(0, 4, 1, 2, 3), w, bias, padding=1)
+    ref = ref.permute(0, 2, 3, 4, 1).contiguous()
+    wp = torch.from_numpy(_pack(lib, w.numpy()).view(np.int16)).cuda()
+    d_a = a.cuda().contiguous()
+    d_b = bias.cuda()
+    out = torch.full((nb, Lz, Ly, Lx, 16), float("nan"), device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    st = lib.coulps_cv_conv3d(ctypes.c_void_p(d_a.data_ptr()), ctypes.c_void_p(wp.data_ptr()),
+                              ctypes.c_void_p(d_b.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                              nb, Lx, Ly, Lz, ctypes.c_void_p(err.data_ptr()), None)
+    assert st == 0
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    got = out.cpu()
+    scale = (a.float().abs().max() * w.abs().sum(dim=(1, 2, 3, 4)).max()).item()
+    assert torch.isfinite(got).all()
+    assert (got - ref).abs().max().item() < 2e-6 * scale + 1e-6
