@@ -159,6 +159,30 @@ def profiled_traffic():
         return None
 
 
+def golden_e_lat(name):
+    """Exact lattice energy of a seeded workload (tests/golden/e_lat.txt, written
+    by tests/golden/make_golden.py from the FP64 oracle)."""
+    for ln in (ROOT / "tests" / "golden" / "e_lat.txt").read_text().splitlines():
+        if ln.startswith(name + " "):
+            return float(ln.split()[8])
+    return None
+
+
+def time_to_accuracy(est, seconds, world, eps=1e-3, name="bench_128c_n4096_pm"):
+    """Projected wall time to a batch-means error of eps |E_lat|: the timed run
+    reached est['stderr'] in `seconds` (all GPUs), and the error falls as
+    1/sqrt(time)."""
+    e_lat = golden_e_lat(name)
+    if not e_lat or not (est.get("stderr") or 0) > 0:
+        return None
+    t = seconds * (est["stderr"] / (eps * abs(e_lat))) ** 2
+    return {"eps": eps, "e_lat": e_lat, "mean": est["mean"], "stderr": est["stderr"],
+            "tau_int": est["tau_int"], "samples": est["n"] * world,
+            "delta": abs(est["mean"] - e_lat) / abs(e_lat),
+            "projected_seconds": t, "projected_hours": t / 3600.0,
+            "estimator": "plain, batch means over all chains"}
+
+
 # --------------------------------------------------------------------------
 def cpu_oracle_rate(seconds, Lz=L):
     """Site-updates/s of the FP64 oracle on one chain of a 128 x 128 x Lz box,
@@ -257,6 +281,7 @@ def run_ours(args):
         step()
     lat.sync()
     lat.kernel_times()  # discard warm-up timings
+    ch.reset_stats()  # the timed samples alone feed the time-to-accuracy projection
 
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -282,6 +307,8 @@ def run_ours(args):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
     ms_max = float(t.item())
     value = world * sites_per_step * args.steps / (ms_max / 1e3)
+    est_timed = ch.estimate()
+    tta = time_to_accuracy(est_timed, ms_max / 1e3, world)
 
     # roofline of the dominant kernel: the over-relaxation half-sweep
     # (3 of the 4 passes; 12 B per updated site: read other colour, read own, write own)
@@ -338,7 +365,7 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": dict(CONFIG, parallelism=f"replicas{world}", n_chains_per_gpu=n_chains),
             "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-            "estimate_after_e2e": est,
+            "time_to_1e-3": tta, "estimate_after_e2e": est,
         }
         if world == 1:
             rate, cores, n = cpu_oracle_rate(args.cpu_seconds)

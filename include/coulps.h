@@ -283,6 +283,38 @@ int coulps_cv_pack_weights(const float *w, uint16_t *wpack);
 int coulps_cv_conv3d(const void *in_bf16, const void *wpack, const float *bias, float *out,
                      int nb, int Lx, int Ly, int Lz, int *err, void *stream);
 
+/* coulps_cv_conv3d_wgrad: weight gradient of coulps_cv_conv3d,
+ *   dW[co][ci][o] = sum_{b, p} dh[b, p, co] a[b, p + o, ci]   (a = 0 outside),
+ * o = 9 kz + 3 ky + kx, i.e. dW has PyTorch's [co][ci][kz][ky][kx] order.
+ * a, dh: device BF16 [nb][Lz][Ly][Lx][16]; dW device 16*16*27 floats;
+ * scratch: device, >= min(256, ceil(nb*Lx*Ly*Lz / 4096)) * 27 * 256 floats.
+ * Summed in a fixed order (reproducible).  Asynchronous. */
+int coulps_cv_conv3d_wgrad(const void *a_bf16, const void *dh_bf16, float *dW, int nb, int Lx,
+                           int Ly, int Lz, float *scratch, int64_t scratch_floats, void *stream);
+
+/* coulps_cv_pack_field: the net's input for every chain of an FP32 lattice,
+ * on the lattice's stream: act[chain][z][y][x][16] BF16 = (phi, rho, 0, ...)
+ * and Aphi[chain][z][y][x] = (A phi) = 6 phi - (sum of the six neighbours),
+ * phi = 0 outside the box (the gradient of H_L).  rho: device Lz*Ly*Lx floats
+ * (charge density per site).  act must be 16-byte aligned.
+ * coulps_cv_activate: a = tanh(h), s = 1 - a^2 (BF16) for n floats h. */
+int coulps_cv_pack_field(coulps_lattice_t lat, const float *rho, void *act_bf16, float *Aphi);
+int coulps_cv_activate(const float *h, void *a_bf16, void *s_bf16, int64_t n, void *stream);
+
+/* coulps_cv_stein_sum: per chain b, the Stein term of the net,
+ *   out[b] = sum_x (dg_x/dphi_x - g_x (A phi)_x)
+ *          = sum_q sum_c s2[c, q] D[c, q] - sum_x g_x Aphi_x
+ *            + sum_{q on a face} sum_c2 s2[c2, q] sum_{c1, e} dK_b(q)[c2][c1][e] s1[c1, q + e]
+ * with D = conv(s1, K) (coulps_cv_conv3d with the divergence kernel K), g =
+ * channel 0 of g16 ([b][site][16] FP32), s1, s2 BF16 [b][site][16], and dK
+ * (device, 64 x 16 x 16 x 27 floats) the face corrections indexed by
+ * class b = cx + 4 cy + 16 cz, c = 0 low face, 1 inside, 2 high face, 3 both
+ * (edge 1).  Sums in FP64, fixed order.  scratch: >= 128 * nb doubles.  out:
+ * device nb doubles. */
+int coulps_cv_stein_sum(const float *g16, const float *D, const void *s2_bf16, const float *Aphi,
+                        const void *s1_bf16, const float *dK, int nb, int Lx, int Ly, int Lz,
+                        double *scratch, int64_t scratch_doubles, double *out, void *stream);
+
 /* ---- allocation-free measurement --------------------------------------- */
 /* The paper has no counterpart to this entry point.  It serves callers that
  * cannot allocate device memory when they measure: code running while a CUDA

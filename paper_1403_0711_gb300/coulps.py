@@ -36,6 +36,7 @@ EXPORTS = (
     "coulps_batch_system_tile", "coulps_batch_info", "coulps_batch_charges", "coulps_batch_sweep",
     "coulps_batch_run", "coulps_batch_sync", "coulps_batch_estimate", "coulps_batch_samples",
     "coulps_batch_field_get", "coulps_cv_pack_weights", "coulps_cv_conv3d",
+    "coulps_cv_conv3d_wgrad", "coulps_cv_pack_field", "coulps_cv_activate", "coulps_cv_stein_sum",
 )
 STAT_STRIDE = 72
 
@@ -107,6 +108,10 @@ def load(path: str | Path | None = None):
         "coulps_batch_field_get": (i32, [vp, i32, P(f64)]),
         "coulps_cv_pack_weights": (i32, [P(ctypes.c_float), P(ctypes.c_uint16)]),
         "coulps_cv_conv3d": (i32, [vp, vp, vp, vp, i32, i32, i32, i32, vp, vp]),
+        "coulps_cv_conv3d_wgrad": (i32, [vp, vp, vp, i32, i32, i32, i32, vp, i64, vp]),
+        "coulps_cv_pack_field": (i32, [vp, vp, vp, vp]),
+        "coulps_cv_activate": (i32, [vp, vp, vp, i64, vp]),
+        "coulps_cv_stein_sum": (i32, [vp, vp, vp, vp, vp, vp, i32, i32, i32, i32, vp, i64, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)

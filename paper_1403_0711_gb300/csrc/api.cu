@@ -843,6 +843,13 @@ int coulps_kernel_times(coulps_lattice_t L, double out[4]) {
   return COULPS_OK;
 }
 
+int coulps_cv_pack_field(coulps_lattice_t L, const float *rho, void *act_bf16, float *Aphi) {
+  if (!L || !rho || !act_bf16 || !Aphi) return COULPS_EINVAL;
+  if (L->g.precision != COULPS_F32) return COULPS_EUNSUPPORTED;
+  if (reinterpret_cast<uintptr_t>(act_bf16) & 15) return COULPS_EINVAL;
+  return coulps_cv_pack_field_impl(L->field, L->g, rho, act_bf16, Aphi, L->stream);
+}
+
 // ---- checkpoint ------------------------------------------------------------
 namespace {
 struct CkptHeader {

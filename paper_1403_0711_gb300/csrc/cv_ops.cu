@@ -1,0 +1,305 @@
+// Elementwise, reduction and weight-gradient kernels of the Stein control
+// variate (the convolutions themselves are in cv_conv.cu).
+//
+//   pack:      lattice field (split colours, FP32) -> channels-last BF16 input
+//              (phi, rho, 0 ...) and A phi (FP32), A = -Delta_lat with phi = 0
+//              outside the box (A phi = dH_L/dphi).
+//   activate:  a = tanh(h), s = tanh'(h) = 1 - a^2, both BF16.
+//   stein_sum: per chain, sum_q sum_c s2[c, q] D[c, q] - sum_x g_x (A phi)_x,
+//              D = conv(s1, K) over all sites (the divergence of g for every
+//              site not on a face of the box, see below), g = channel 0 of the
+//              last conv.
+//   boundary:  per chain, the divergence correction of the face sites:
+//              sum_q s2[c2, q] sum_{c1, e} dK_b(q)[c2, c1, e] s1[c1, q + e],
+//              dK_b = K_b - K for the face class b(q) of q.
+//   wgrad:     dW[co, ci, o] = sum_{b, p} dh[b, p, co] a[b, p + o, ci]
+//              (zero outside), per-CTA partials then a fixed-order sum.
+//
+// Divergence of the net g (three 3x3x3 convs, tanh between them): with
+// s1 = tanh'(h1), s2 = tanh'(h2),
+//   sum_x dg_x/dphi_x = sum_q sum_c2 s2[c2, q] sum_{c1, e} K_b(q)[c2, c1, e] s1[c1, q+e],
+//   K_b[c2, c1, e] = W2[c2, c1, e] sum_{f in F_b} W3[c2, f] W1[c1, phi, -(e + f)],
+// where F_b holds the offsets f whose x = q - f lies inside the box; for q
+// off the faces F_b is all 27 offsets and K_b = K.
+#include <cstdint>
+
+#include <cuda_bf16.h>
+
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace coulps {
+namespace {
+
+__device__ __forceinline__ float ld_field(const float *f, const Geometry &g, int chain, int x,
+                                          int y, int z) {
+  if (x < 0 || y < 0 || z < 0 || x >= g.Lx || y >= g.Ly || z >= g.Lz) return 0.f;
+  const int c = (x + y + z) & 1;
+  return f[(size_t)chain * g.chain_elems + (size_t)c * g.colour_elems +
+           ((size_t)z * g.Ly + y) * g.W + (x >> 1)];
+}
+
+__global__ void cv_pack_kernel(const float *__restrict__ field, Geometry g,
+                               const float *__restrict__ rho, __nv_bfloat16 *__restrict__ act,
+                               float *__restrict__ Aphi) {
+  const int64_t sites = (int64_t)g.Lx * g.Ly * g.Lz;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int chain = blockIdx.y;
+  if (i >= sites) return;
+  const int x = (int)(i % g.Lx), y = (int)((i / g.Lx) % g.Ly), z = (int)(i / ((int64_t)g.Lx * g.Ly));
+  const float p = ld_field(field, g, chain, x, y, z);
+  const float S = ld_field(field, g, chain, x - 1, y, z) + ld_field(field, g, chain, x + 1, y, z) +
+                  ld_field(field, g, chain, x, y - 1, z) + ld_field(field, g, chain, x, y + 1, z) +
+                  ld_field(field, g, chain, x, y, z - 1) + ld_field(field, g, chain, x, y, z + 1);
+  const int64_t o = (int64_t)chain * sites + i;
+  Aphi[o] = 6.f * p - S;
+  __align__(16) __nv_bfloat16 v[16];
+  v[0] = __float2bfloat16_rn(p);
+  v[1] = __float2bfloat16_rn(rho[i]);
+#pragma unroll
+  for (int k = 2; k < 16; ++k) v[k] = __float2bfloat16_rn(0.f);
+  uint4 *dst = reinterpret_cast<uint4 *>(act + o * 16);
+  dst[0] = reinterpret_cast<const uint4 *>(v)[0];
+  dst[1] = reinterpret_cast<const uint4 *>(v)[1];
+}
+
+__global__ void cv_activate_kernel(const float *__restrict__ h, __nv_bfloat16 *__restrict__ a,
+                                   __nv_bfloat16 *__restrict__ s, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float t = tanhf(h[i]);
+  a[i] = __float2bfloat16_rn(t);
+  s[i] = __float2bfloat16_rn(1.f - t * t);
+}
+
+constexpr int kRedThreads = 256;
+
+__device__ __forceinline__ void block_sum_to(double v, double *out) {
+  __shared__ double red[kRedThreads / 32];
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    v = lane < kRedThreads / 32 ? red[lane] : 0.0;
+    v = warp_sum(v);
+    if (lane == 0) *out = v;
+  }
+}
+
+// per (chain, block) partial of sum_q s2 . D - sum_x g_x (A phi)_x
+__global__ void __launch_bounds__(kRedThreads)
+    cv_stein_partial_kernel(const float *__restrict__ g16, const float *__restrict__ D,
+                            const __nv_bfloat16 *__restrict__ s2, const float *__restrict__ Aphi,
+                            int64_t sites, double *__restrict__ partials) {
+  const int chain = blockIdx.y;
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * kRedThreads + threadIdx.x; i < sites;
+       i += (int64_t)gridDim.x * kRedThreads) {
+    const int64_t o = (int64_t)chain * sites + i;
+    float d = 0.f;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) d = fmaf(__bfloat162float(s2[o * 16 + c]), D[o * 16 + c], d);
+    acc += (double)d - (double)g16[o * 16] * (double)Aphi[o];
+  }
+  block_sum_to(acc, partials + (size_t)chain * gridDim.x + blockIdx.x);
+}
+
+// face class of coordinate v in [0, n): 0 low face, 1 inside, 2 high face, 3 both (n == 1)
+__device__ __forceinline__ int face_class(int v, int n) {
+  return n == 1 ? 3 : (v == 0 ? 0 : (v == n - 1 ? 2 : 1));
+}
+
+// per (chain, block) partial of the face-site divergence correction
+__global__ void __launch_bounds__(kRedThreads)
+    cv_boundary_partial_kernel(const __nv_bfloat16 *__restrict__ s1,
+                               const __nv_bfloat16 *__restrict__ s2, const float *__restrict__ dK,
+                               int Lx, int Ly, int Lz, int64_t nface, double *__restrict__ partials) {
+  // one thread per (face site, c2); face sites enumerated as all sites with
+  // some coordinate on a face
+  const int chain = blockIdx.y;
+  const int64_t sites = (int64_t)Lx * Ly * Lz;
+  double acc = 0.0;
+  for (int64_t t = (int64_t)blockIdx.x * kRedThreads + threadIdx.x; t < nface * 16;
+       t += (int64_t)gridDim.x * kRedThreads) {
+    const int c2 = (int)(t & 15);
+    int64_t k = t >> 4;  // k-th face site in (z, y, x) order
+    // decode: walk planes z = 0 and z = Lz-1 fully, the other planes only on their rim
+    int x, y, z;
+    {
+      const int64_t plane = (int64_t)Lx * Ly;
+      const int64_t rim = (Ly <= 2 || Lx <= 2) ? plane : 2LL * Lx + 2LL * (Ly - 2);
+      const int nfull = Lz == 1 ? 1 : 2;
+      if (k < plane) {
+        z = 0;
+        x = (int)(k % Lx);
+        y = (int)(k / Lx);
+      } else if (nfull == 2 && k < 2 * plane) {
+        z = Lz - 1;
+        k -= plane;
+        x = (int)(k % Lx);
+        y = (int)(k / Lx);
+      } else {
+        k -= (int64_t)nfull * plane;
+        z = 1 + (int)(k / rim);
+        int64_t r = k % rim;
+        if (rim == plane) {
+          x = (int)(r % Lx);
+          y = (int)(r / Lx);
+        } else if (r < Lx) {
+          y = 0;
+          x = (int)r;
+        } else if (r < 2LL * Lx) {
+          y = Ly - 1;
+          x = (int)(r - Lx);
+        } else {
+          r -= 2LL * Lx;
+          y = 1 + (int)(r / 2);
+          x = (r & 1) ? Lx - 1 : 0;
+        }
+      }
+    }
+    const int b = face_class(x, Lx) + 4 * face_class(y, Ly) + 16 * face_class(z, Lz);
+    const float *dk = dK + ((size_t)b * 16 + c2) * 16 * 27;
+    const int64_t q = ((int64_t)z * Ly + y) * Lx + x;
+    float d = 0.f;
+    for (int e = 0; e < 27; ++e) {
+      const int ez = e / 9 - 1, ey = (e / 3) % 3 - 1, ex = e % 3 - 1;
+      const int xx = x + ex, yy = y + ey, zz = z + ez;
+      if (xx < 0 || yy < 0 || zz < 0 || xx >= Lx || yy >= Ly || zz >= Lz) continue;
+      const __nv_bfloat16 *sp = s1 + ((int64_t)chain * sites + ((int64_t)zz * Ly + yy) * Lx + xx) * 16;
+#pragma unroll
+      for (int c1 = 0; c1 < 16; ++c1) d = fmaf(dk[c1 * 27 + e], __bfloat162float(sp[c1]), d);
+    }
+    acc += (double)__bfloat162float(s2[((int64_t)chain * sites + q) * 16 + c2]) * (double)d;
+  }
+  block_sum_to(acc, partials + (size_t)chain * gridDim.x + blockIdx.x);
+}
+
+__global__ void cv_sum_partials_kernel(const double *__restrict__ partials, int nblk, int nb,
+                                       double *__restrict__ out, int accumulate) {
+  const int chain = blockIdx.x * blockDim.x + threadIdx.x;
+  if (chain >= nb) return;
+  double s = 0.0;
+  for (int k = 0; k < nblk; ++k) s += partials[(size_t)chain * nblk + k];
+  out[chain] = accumulate ? out[chain] + s : s;
+}
+
+constexpr int kWgTile = 64;  // positions per shared-memory tile
+
+// per (block, offset) partial of dW[co][ci][o]; thread t = co * 16 + ci
+__global__ void __launch_bounds__(256)
+    cv_wgrad_partial_kernel(const __nv_bfloat16 *__restrict__ a,
+                            const __nv_bfloat16 *__restrict__ dh, int Lx, int Ly, int Lz,
+                            int64_t npos, int64_t per_block, float *__restrict__ partials) {
+  __shared__ float sd[kWgTile][17], sa[kWgTile][17];
+  const int o = blockIdx.y;
+  const int oz = o / 9 - 1, oy = (o / 3) % 3 - 1, ox = o % 3 - 1;
+  const int t = threadIdx.x, co = t >> 4, ci = t & 15;
+  const int64_t p0 = (int64_t)blockIdx.x * per_block;
+  const int64_t p1 = p0 + per_block < npos ? p0 + per_block : npos;
+  float acc = 0.f;
+  for (int64_t base = p0; base < p1; base += kWgTile) {
+    for (int k = t; k < kWgTile * 16; k += 256) {
+      const int j = k >> 4, c = k & 15;
+      const int64_t p = base + j;
+      float vd = 0.f, va = 0.f;
+      if (p < p1) {
+        vd = __bfloat162float(dh[p * 16 + c]);
+        int64_t r = p;
+        const int x = (int)(r % Lx);
+        r /= Lx;
+        const int y = (int)(r % Ly);
+        r /= Ly;
+        const int z = (int)(r % Lz);
+        const int64_t bb = r / Lz;
+        const int xx = x + ox, yy = y + oy, zz = z + oz;
+        if (xx >= 0 && yy >= 0 && zz >= 0 && xx < Lx && yy < Ly && zz < Lz)
+          va = __bfloat162float(a[((((bb * Lz) + zz) * Ly + yy) * (int64_t)Lx + xx) * 16 + c]);
+      }
+      sd[j][c] = vd;
+      sa[j][c] = va;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int j = 0; j < kWgTile; ++j) acc = fmaf(sd[j][co], sa[j][ci], acc);
+    __syncthreads();
+  }
+  partials[((size_t)blockIdx.x * 27 + o) * 256 + t] = acc;
+}
+
+__global__ void cv_wgrad_reduce_kernel(const float *__restrict__ partials, int nblk,
+                                       float *__restrict__ dW) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;  // o * 256 + t
+  if (i >= 27 * 256) return;
+  const int o = i / 256, t = i % 256;
+  float s = 0.f;
+  for (int b = 0; b < nblk; ++b) s += partials[((size_t)b * 27 + o) * 256 + t];
+  dW[(size_t)t * 27 + o] = s;  // [co][ci][o]
+}
+
+}  // namespace
+}  // namespace coulps
+
+using namespace coulps;
+
+// Layout and size rules are in include/coulps.h.
+extern "C" {
+
+int coulps_cv_activate(const float *h, void *a_bf16, void *s_bf16, int64_t n, void *stream) {
+  if (!h || !a_bf16 || !s_bf16 || n < 0) return COULPS_EINVAL;
+  if (n == 0) return COULPS_OK;
+  cv_activate_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+      h, (__nv_bfloat16 *)a_bf16, (__nv_bfloat16 *)s_bf16, n);
+  return cudaGetLastError() == cudaSuccess ? COULPS_OK : COULPS_ECUDA;
+}
+
+int coulps_cv_stein_sum(const float *g16, const float *D, const void *s2_bf16, const float *Aphi,
+                        const void *s1_bf16, const float *dK, int nb, int Lx, int Ly, int Lz,
+                        double *scratch, int64_t scratch_doubles, double *out, void *stream) {
+  if (!g16 || !D || !s2_bf16 || !Aphi || !s1_bf16 || !dK || !scratch || !out) return COULPS_EINVAL;
+  if (nb < 1 || Lx < 1 || Ly < 1 || Lz < 1) return COULPS_EINVAL;
+  const int nblk = 128;
+  if (scratch_doubles < (int64_t)nb * nblk) return COULPS_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t sites = (int64_t)Lx * Ly * Lz;
+  cv_stein_partial_kernel<<<dim3(nblk, nb), kRedThreads, 0, s>>>(
+      g16, D, (const __nv_bfloat16 *)s2_bf16, Aphi, sites, scratch);
+  cv_sum_partials_kernel<<<(nb + 127) / 128, 128, 0, s>>>(scratch, nblk, nb, out, 0);
+  const int64_t interior = (int64_t)(Lx > 2 ? Lx - 2 : 0) * (Ly > 2 ? Ly - 2 : 0) * (Lz > 2 ? Lz - 2 : 0);
+  const int64_t nface = sites - interior;
+  cv_boundary_partial_kernel<<<dim3(nblk, nb), kRedThreads, 0, s>>>(
+      (const __nv_bfloat16 *)s1_bf16, (const __nv_bfloat16 *)s2_bf16, dK, Lx, Ly, Lz, nface,
+      scratch);
+  cv_sum_partials_kernel<<<(nb + 127) / 128, 128, 0, s>>>(scratch, nblk, nb, out, 1);
+  return cudaGetLastError() == cudaSuccess ? COULPS_OK : COULPS_ECUDA;
+}
+
+int coulps_cv_conv3d_wgrad(const void *a_bf16, const void *dh_bf16, float *dW, int nb, int Lx,
+                           int Ly, int Lz, float *scratch, int64_t scratch_floats, void *stream) {
+  if (!a_bf16 || !dh_bf16 || !dW || !scratch) return COULPS_EINVAL;
+  if (nb < 1 || Lx < 1 || Ly < 1 || Lz < 1) return COULPS_EINVAL;
+  const int64_t npos = (int64_t)nb * Lx * Ly * Lz;
+  int nblk = (int)((npos + 4095) / 4096);
+  if (nblk > 256) nblk = 256;
+  if (scratch_floats < (int64_t)nblk * 27 * 256) return COULPS_EINVAL;
+  const int64_t per_block = (npos + nblk - 1) / nblk;
+  cudaStream_t s = (cudaStream_t)stream;
+  cv_wgrad_partial_kernel<<<dim3(nblk, 27), 256, 0, s>>>(
+      (const __nv_bfloat16 *)a_bf16, (const __nv_bfloat16 *)dh_bf16, Lx, Ly, Lz, npos, per_block,
+      scratch);
+  cv_wgrad_reduce_kernel<<<(27 * 256 + 255) / 256, 256, 0, s>>>(scratch, nblk, dW);
+  return cudaGetLastError() == cudaSuccess ? COULPS_OK : COULPS_ECUDA;
+}
+
+}  // extern "C"
+
+// coulps_cv_pack_field (api.cu) supplies the lattice's geometry and stream.
+int coulps::coulps_cv_pack_field_impl(const void *field, const Geometry &g, const float *rho,
+                              void *act_bf16, float *Aphi, cudaStream_t s) {
+  const int64_t sites = (int64_t)g.Lx * g.Ly * g.Lz;
+  dim3 grid((unsigned)((sites + 255) / 256), g.n_chains);
+  cv_pack_kernel<<<grid, 256, 0, s>>>(reinterpret_cast<const float *>(field), g, rho,
+                                      (__nv_bfloat16 *)act_bf16, Aphi);
+  return cudaGetLastError() == cudaSuccess ? COULPS_OK : COULPS_ECUDA;
+}

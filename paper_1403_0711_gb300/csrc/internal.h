@@ -115,4 +115,8 @@ cudaError_t launch_reset_stats(double *stats, int n_chains, cudaStream_t s);
 
 int gather_blocks(int64_t n);
 
+// Control variate input packing (cv_ops.cu) for a lattice's FP32 field.
+int coulps_cv_pack_field_impl(const void *field, const Geometry &g, const float *rho,
+                              void *act_bf16, float *Aphi, cudaStream_t s);
+
 }  // namespace coulps

@@ -1,0 +1,337 @@
+"""Learned Stein control variate for the Eq. (nsum2) estimator.
+
+For the lattice measure exp(-H_L) (Eq. (proplat), phi = 0 outside the box)
+and any smooth vector field g(phi) with one component per site,
+    E[ T g ] = 0,   T g = sum_x ( dg_x/dphi_x - g_x (A phi)_x ),   A phi = dH_L/dphi,
+so e_CV = e - c T g has the mean of the plain sample e for any fixed c.
+g is a 3-layer 3x3x3 conv net on the input channels (phi, rho), 16 hidden
+channels, tanh, zero padding; c and the weights are fitted to minimise
+Var(e - c T g) on stored samples of the chain.
+
+All convolutions run in libcoulps.so's tcgen05 kernel (BF16 operands, FP32
+accumulate), wrapped in a torch.autograd.Function whose backward uses the same
+kernel for the input gradient (flipped, transposed weights) and the library's
+weight-gradient kernel.  The divergence uses the identity
+    sum_x dg_x/dphi_x = sum_q sum_c2 s2[c2,q] (conv(s1, K) + face corrections)[c2,q],
+    K[c2,c1,e] = W2[c2,c1,e] sum_f W3[c2,f] W1[c1,phi,-(e+f)],
+with s = tanh' of the pre-activations: one extra 16 -> 16 conv plus a
+correction on the box's face sites (where some x = q - f fall outside).
+
+Training runs through autograd (the convs are the library's kernels; the
+elementwise glue is PyTorch).  Evaluation inside the sampler (``evaluate``)
+calls only library kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+import itertools
+
+import numpy as np
+import torch
+
+from . import coulps
+
+OFFS = list(itertools.product((-1, 0, 1), repeat=3))  # index 9 (dz+1) + 3 (dy+1) + (dx+1)
+
+
+def _vp(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def pack_weights(W: torch.Tensor) -> torch.Tensor:
+    """(16,16,3,3,3) float -> packed BF16 bits on the device (coulps_cv_pack_weights)."""
+    w = np.ascontiguousarray(W.detach().float().cpu().numpy())
+    out = np.zeros(27 * 256, dtype=np.uint16)
+    st = coulps.load().coulps_cv_pack_weights(w.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                              out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint16)))
+    coulps._check(st, "coulps_cv_pack_weights")
+    return torch.from_numpy(out.view(np.int16)).to(W.device)
+
+
+def conv3d_tc(a: torch.Tensor, W: torch.Tensor, b: torch.Tensor) -> torch.Tensor:
+    """h = conv3d(a, W) + b with the library's tensor-core kernel.
+    a: (n, Z, Y, X, 16) BF16 contiguous; W (16, 16, 3, 3, 3); b (16,)."""
+    n, Z, Y, X, C = a.shape
+    assert C == 16 and a.dtype == torch.bfloat16 and a.is_contiguous()
+    out = torch.empty((n, Z, Y, X, 16), dtype=torch.float32, device=a.device)
+    err = torch.zeros(1, dtype=torch.int32, device=a.device)
+    wp = pack_weights(W)
+    bias = b.detach().float().contiguous()
+    st = coulps.load().coulps_cv_conv3d(_vp(a), _vp(wp), _vp(bias), _vp(out), n, X, Y, Z, _vp(err),
+                                        _stream())
+    coulps._check(st, "coulps_cv_conv3d")
+    return out
+
+
+def conv3d_wgrad(a: torch.Tensor, dh: torch.Tensor) -> torch.Tensor:
+    n, Z, Y, X, _ = a.shape
+    npos = n * Z * Y * X
+    nblk = min(256, (npos + 4095) // 4096)
+    scratch = torch.empty(nblk * 27 * 256, dtype=torch.float32, device=a.device)
+    dW = torch.empty(16 * 16 * 27, dtype=torch.float32, device=a.device)
+    st = coulps.load().coulps_cv_conv3d_wgrad(_vp(a), _vp(dh), _vp(dW), n, X, Y, Z, _vp(scratch),
+                                              scratch.numel(), _stream())
+    coulps._check(st, "coulps_cv_conv3d_wgrad")
+    return dW.view(16, 16, 3, 3, 3)
+
+
+class Conv3dTC(torch.autograd.Function):
+    """conv3d 3x3x3, 16 -> 16 channels, channels last, on the tensor cores."""
+
+    @staticmethod
+    def forward(ctx, a, W, b):
+        ctx.save_for_backward(a, W)
+        return conv3d_tc(a, W, b)
+
+    @staticmethod
+    def backward(ctx, dh):
+        a, W = ctx.saved_tensors
+        dh16 = dh.contiguous().to(torch.bfloat16)
+        da = dW = db = None
+        if ctx.needs_input_grad[0]:
+            Wt = W.detach().transpose(0, 1).flip(2, 3, 4).contiguous()
+            da = conv3d_tc(dh16, Wt, torch.zeros(16, device=dh.device)).to(a.dtype)
+        if ctx.needs_input_grad[1]:
+            dW = conv3d_wgrad(a, dh16)
+        if ctx.needs_input_grad[2]:
+            db = dh.sum(dim=(0, 1, 2, 3))
+        return da, dW, db
+
+
+def _face_masks():
+    """Allowed f (x = q - f inside) per face class c: 0 low, 1 inside, 2 high, 3 both."""
+    allowed = {0: (-1, 0), 1: (-1, 0, 1), 2: (0, 1), 3: (0,)}
+    masks = {}
+    for cz, cy, cx in itertools.product(range(4), repeat=3):
+        m = torch.tensor([1.0 if (f[0] in allowed[cz] and f[1] in allowed[cy]
+                                  and f[2] in allowed[cx]) else 0.0 for f in OFFS])
+        masks[cx + 4 * cy + 16 * cz] = m
+    return masks
+
+
+_FACE_MASKS = _face_masks()
+_FACE_CLASSES = sorted(_FACE_MASKS)
+_INSIDE = 1 + 4 + 16
+
+
+def _pair_tensor():
+    """P[e, f, u] = 1 where u = -(e + f) is a kernel offset."""
+    P = torch.zeros(27, 27, 27)
+    for ei, e in enumerate(OFFS):
+        for fi, f in enumerate(OFFS):
+            u = (-(e[0] + f[0]), -(e[1] + f[1]), -(e[2] + f[2]))
+            if max(abs(v) for v in u) <= 1:
+                P[ei, fi, OFFS.index(u)] = 1.0
+    return P
+
+
+_P = _pair_tensor()
+
+
+def divergence_kernel(W1, W2, W3, fmask=None):
+    """K[c2, c1, e] = W2[c2, c1, e] sum_f fmask[f] W3[0, c2, f] W1[c1, 0, -(e+f)];
+    with fmask of shape (k, 27) returns (k, 16, 16, 3, 3, 3)."""
+    w1 = W1[:, 0].reshape(16, 27)
+    w2 = W2.reshape(16, 16, 27)
+    w3 = W3[0].reshape(16, 27)
+    P = _P.to(W1.device, W1.dtype)
+    if fmask is None:
+        M = torch.einsum("efu,af,bu->abe", P, w3, w1)
+        return (w2 * M).reshape(16, 16, 3, 3, 3)
+    M = torch.einsum("efu,kf,af,bu->kabe", P, fmask.to(W1.device, W1.dtype), w3, w1)
+    return (w2[None] * M).reshape(-1, 16, 16, 3, 3, 3)
+
+
+class SteinCV(torch.nn.Module):
+    def __init__(self, seed=0, scale=0.3, device="cuda"):
+        super().__init__()
+        g = torch.Generator().manual_seed(seed)
+
+        def rnd(*s, sc):
+            return torch.nn.Parameter((torch.randn(*s, generator=g) * sc).to(device))
+
+        self.W1 = rnd(16, 2, 3, 3, 3, sc=scale)
+        self.b1 = rnd(16, sc=0.1)
+        self.W2 = rnd(16, 16, 3, 3, 3, sc=scale / 4)
+        self.b2 = rnd(16, sc=0.1)
+        self.W3 = rnd(1, 16, 3, 3, 3, sc=scale / 16)
+        self.b3 = rnd(1, sc=0.0)
+        self.c = 1.0  # coefficient of T g, set by fit()
+
+    # -- parameters in the 16-channel form the kernel takes
+    def _w1p(self):
+        return torch.cat([self.W1, torch.zeros(16, 14, 3, 3, 3, device=self.W1.device)], dim=1)
+
+    def _w3p(self):
+        return torch.cat([self.W3, torch.zeros(15, 16, 3, 3, 3, device=self.W3.device)], dim=0)
+
+    def _b3p(self):
+        return torch.cat([self.b3, torch.zeros(15, device=self.b3.device)])
+
+    def face_corrections(self):
+        """(64, 16, 16, 27) K_b - K for every face class (zero for class 'inside')."""
+        masks = torch.stack([_FACE_MASKS[b] for b in range(64)])
+        Kb = divergence_kernel(self.W1, self.W2, self.W3, masks).reshape(64, 16, 16, 27)
+        return Kb - Kb[_INSIDE][None]
+
+    # -- differentiable T g for training: x0 (n, Z, Y, X, 16) BF16 input, Aphi (n, Z, Y, X)
+    def stein_term(self, x0, Aphi):
+        h1 = Conv3dTC.apply(x0, self._w1p(), self.b1)
+        a1 = torch.tanh(h1)
+        s1 = 1.0 - a1 * a1
+        h2 = Conv3dTC.apply(a1.to(torch.bfloat16), self.W2, self.b2)
+        a2 = torch.tanh(h2)
+        s2 = 1.0 - a2 * a2
+        g = Conv3dTC.apply(a2.to(torch.bfloat16), self._w3p(), self._b3p())[..., 0]
+        K = divergence_kernel(self.W1, self.W2, self.W3)
+        D = Conv3dTC.apply(s1.to(torch.bfloat16), K, torch.zeros(16, device=x0.device))
+        div = (s2 * D).sum(dim=(1, 2, 3, 4)) + self._face_term(s1, s2)
+        return div - (g * Aphi).sum(dim=(1, 2, 3))
+
+    def _face_term(self, s1, s2):
+        n, Z, Y, X, _ = s1.shape
+        s1p = torch.nn.functional.pad(s1, (0, 0, 1, 1, 1, 1, 1, 1))  # zero ring
+        total = torch.zeros(n, device=s1.device)
+        dK = self.face_corrections()
+        zz, yy, xx = torch.meshgrid(torch.arange(Z), torch.arange(Y), torch.arange(X), indexing="ij")
+
+        def cls(v, L):
+            c = torch.ones_like(v)
+            c[v == 0] = 0
+            c[v == L - 1] = 2
+            if L == 1:
+                c[:] = 3
+            return c
+
+        cl = cls(xx, X) + 4 * cls(yy, Y) + 16 * cls(zz, Z)
+        for b in torch.unique(cl).tolist():
+            if b == _INSIDE:
+                continue
+            sel = (cl == b).nonzero()  # (m, 3) z, y, x
+            patches = torch.stack([s1p[:, sel[:, 0] + 1 + o[0], sel[:, 1] + 1 + o[1],
+                                       sel[:, 2] + 1 + o[2]] for o in OFFS], dim=2)  # (n, m, 27, 16)
+            dD = torch.einsum("nmec,dce->nmd", patches, dK[b])
+            total = total + (s2[:, sel[:, 0], sel[:, 1], sel[:, 2]] * dD).sum(dim=(1, 2))
+        return total
+
+    # -- evaluation with library kernels only
+    @torch.no_grad()
+    def evaluate(self, lat: "coulps.Lattice", rho: torch.Tensor) -> torch.Tensor:
+        """T g for every chain of an FP32 lattice (float64 tensor of n_chains),
+        computed on the lattice's stream."""
+        lib = coulps.load()
+        Lx, Ly, Lz = lat.L
+        n = lat.n_chains
+        dev = rho.device
+        stream = lat._stream if isinstance(lat._stream, torch.cuda.Stream) else \
+            torch.cuda.current_stream()
+        K = divergence_kernel(self.W1, self.W2, self.W3)
+        dK = self.face_corrections().contiguous()
+        torch.cuda.current_stream().synchronize()
+        with torch.cuda.stream(stream):
+            x0 = torch.empty((n, Lz, Ly, Lx, 16), dtype=torch.bfloat16, device=dev)
+            Aphi = torch.empty((n, Lz, Ly, Lx), dtype=torch.float32, device=dev)
+            coulps._check(lib.coulps_cv_pack_field(lat.handle, _vp(rho), _vp(x0), _vp(Aphi)),
+                          "coulps_cv_pack_field")
+            h1 = conv3d_tc(x0, self._w1p(), self.b1)
+            a1 = torch.empty(h1.shape, dtype=torch.bfloat16, device=dev)
+            s1 = torch.empty_like(a1)
+            coulps._check(lib.coulps_cv_activate(_vp(h1), _vp(a1), _vp(s1), h1.numel(), _stream()),
+                          "coulps_cv_activate")
+            h2 = conv3d_tc(a1, self.W2, self.b2)
+            a2 = torch.empty_like(a1)
+            s2 = torch.empty_like(a1)
+            coulps._check(lib.coulps_cv_activate(_vp(h2), _vp(a2), _vp(s2), h2.numel(), _stream()),
+                          "coulps_cv_activate")
+            g16 = conv3d_tc(a2, self._w3p(), self._b3p())
+            D = conv3d_tc(s1, K, torch.zeros(16, device=dev))
+            out = torch.empty(n, dtype=torch.float64, device=dev)
+            scratch = torch.empty(128 * n, dtype=torch.float64, device=dev)
+            coulps._check(lib.coulps_cv_stein_sum(
+                _vp(g16), _vp(D), _vp(s2), _vp(Aphi), _vp(s1), _vp(dK), n, Lx, Ly, Lz,
+                _vp(scratch), scratch.numel(), _vp(out), _stream()), "coulps_cv_stein_sum")
+        stream.synchronize()
+        return out
+
+
+def charge_density(L, sites, q, device="cuda") -> torch.Tensor:
+    Lx, Ly, Lz = L
+    rho = np.zeros((Lz, Ly, Lx), dtype=np.float32)
+    s = np.asarray(sites, dtype=np.int64).reshape(-1, 3)
+    np.add.at(rho, (s[:, 2], s[:, 1], s[:, 0]), np.asarray(q, dtype=np.float32))
+    return torch.from_numpy(rho).to(device)
+
+
+# --------------------------------------------------------------------------
+# Training data and fitting
+# --------------------------------------------------------------------------
+@torch.no_grad()
+def pack_inputs(lat: "coulps.Lattice", rho: torch.Tensor):
+    """(phi BF16 (n, Z, Y, X), A phi FP32 (n, Z, Y, X)) of every chain, by the
+    library's packing kernel."""
+    Lx, Ly, Lz = lat.L
+    n = lat.n_chains
+    x0 = torch.empty((n, Lz, Ly, Lx, 16), dtype=torch.bfloat16, device=rho.device)
+    Aphi = torch.empty((n, Lz, Ly, Lx), dtype=torch.float32, device=rho.device)
+    coulps._check(coulps.load().coulps_cv_pack_field(lat.handle, _vp(rho), _vp(x0), _vp(Aphi)),
+                  "coulps_cv_pack_field")
+    lat.sync()
+    return x0[..., 0].clone(), Aphi
+
+
+def inputs_from(phi16: torch.Tensor, rho: torch.Tensor) -> torch.Tensor:
+    """Rebuild the net input (phi, rho, 0, ...) from stored BF16 phi."""
+    x0 = torch.zeros(phi16.shape + (16,), dtype=torch.bfloat16, device=phi16.device)
+    x0[..., 0] = phi16
+    x0[..., 1] = rho.to(torch.bfloat16)
+    return x0
+
+
+def collect(lat, ch, rho, n_rounds, every=1, n_hb=1, n_or=3):
+    """Run the sampler and keep, after every `every`-th measured compound
+    sweep, each chain's (BF16 phi, A phi, e).  The charge set must log at
+    least n_rounds * every samples."""
+    phis, Aphis, es = [], [], []
+    for r in range(n_rounds):
+        ch.run(0, every, n_hb, n_or)
+        p, a = pack_inputs(lat, rho)
+        phis.append(p)
+        Aphis.append(a)
+        es.append(torch.from_numpy(ch.samples()[-1, :, 2].copy()))
+    return torch.cat(phis), torch.cat(Aphis), torch.cat(es).double()
+
+
+def fit(cv: SteinCV, phis, Aphis, es, rho, steps=200, batch=16, lr=2e-3, seed=0, log=None):
+    """Minimise Var(e - T g) over the stored samples (Adam on all weights),
+    then set cv.c = Cov(e, T g) / Var(T g) on the same samples."""
+    g = torch.Generator().manual_seed(seed)
+    opt = torch.optim.Adam([cv.W1, cv.b1, cv.W2, cv.b2, cv.W3, cv.b3], lr=lr)
+    n = len(es)
+    dev = phis.device
+    es_d = es.to(dev)
+    for step in range(steps):
+        idx = torch.randperm(n, generator=g)[:batch].to(dev)
+        tg = cv.stein_term(inputs_from(phis[idx], rho), Aphis[idx])
+        r = es_d[idx].float() - tg
+        loss = ((r - r.mean()) ** 2).mean() / (es_d.float().var() + 1e-30)
+        opt.zero_grad()
+        loss.backward()
+        opt.step()
+        if log is not None:
+            log.append(float(loss.detach()))
+    tgs = stein_terms(cv, phis, Aphis, rho)
+    e = es.to(tgs.device)
+    cv.c = float(((e - e.mean()) * (tgs - tgs.mean())).sum() / ((tgs - tgs.mean()) ** 2).sum())
+    return tgs
+
+
+@torch.no_grad()
+def stein_terms(cv: SteinCV, phis, Aphis, rho, batch=16):
+    out = []
+    for i in range(0, len(phis), batch):
+        out.append(cv.stein_term(inputs_from(phis[i:i + batch], rho), Aphis[i:i + batch]).double())
+    return torch.cat(out)
