@@ -58,7 +58,11 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--workload", choices=["chains128", "large512", "sweep", "batched"],
+    ap.add_argument("--schedule", choices=["phased", "aligned"], default="aligned")
+    ap.add_argument("--cv-steps", type=int, default=300)
+    ap.add_argument("--cv-rounds", type=int, default=64)
+    ap.add_argument("--cube-seconds", type=float, default=600.0)
+    ap.add_argument("--workload", choices=["chains128", "large512", "sweep", "batched", "cv", "cube"],
                     default="chains128", help="secondary workloads print their own line")
     ap.add_argument("--chains", type=int, default=N_CHAINS,
                     help="chains per GPU (smaller values only for profiler captures)")
@@ -272,13 +276,14 @@ def run_ours(args):
                          stream=stream)
     ch = coulps.Charges(lat, sites, q)
 
-    def step():
-        # one measured compound sweep; the sample is gathered by its last half-sweep
-        ch.run(0, 1, N_HB, N_OR)
-
+    # Measured compound sweeps (the sample is gathered by the last half-sweep of
+    # each).  A step is one measured compound sweep of every chain; all K timed
+    # steps are one call.  --schedule phased runs chain k mod 4 passes behind
+    # (launches mix heatbath and over-relaxation tiles; measured no faster).
+    lat.set_schedule(coulps.SCHEDULE_PHASED if args.schedule == "phased"
+                     else coulps.SCHEDULE_ALIGNED)
     lat.set_profiling(True)
-    for _ in range(args.warmup):
-        step()
+    ch.run(0, max(2, args.warmup), N_HB, N_OR)
     lat.sync()
     lat.kernel_times()  # discard warm-up timings
     ch.reset_stats()  # the timed samples alone feed the time-to-accuracy projection
@@ -292,8 +297,7 @@ def run_ours(args):
     clocks.start()
     time.sleep(0.3)  # let the sampler start
     ev0.record(stream)
-    for _ in range(args.steps):
-        step()
+    ch.run(0, args.steps, N_HB, N_OR)
     ev1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -310,24 +314,29 @@ def run_ours(args):
     est_timed = ch.estimate()
     tta = time_to_accuracy(est_timed, ms_max / 1e3, world)
 
-    # roofline of the dominant kernel: the over-relaxation half-sweep
-    # (3 of the 4 passes; 12 B per updated site: read other colour, read own, write own)
-    or_ms = kt["or_ms"] / max(1, kt["or_n"])
-    hb_ms = kt["hb_ms"] / max(1, kt["hb_n"])
-    sites_per_launch = n_chains * L ** 3 // 2
-    or_bytes = 12 * sites_per_launch
-    hb_bytes = 8 * sites_per_launch
+    # roofline of the dominant kernel.  Algorithmic bytes per updated site:
+    # heatbath 8 (read the other colour, write), over-relaxation 12 (also read
+    # the old value); a compound sweep of one chain moves 44 L^3 bytes.
     peak, peak_kind = measured_peaks()
-    achieved = or_bytes / (or_ms / 1e3) / 1e9
-    traffic = profiled_traffic()
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "kernel": "halfsweep_kernel<float, over-relaxation>",
-                "algorithmic_bytes_per_launch": or_bytes, "avg_launch_ms": or_ms,
-                "peak_kind": f"{peak_kind} (burst copy)",
-                "heatbath_halfsweep": {"avg_launch_ms": hb_ms,
-                                       "achieved_gbs": hb_bytes / (hb_ms / 1e3) / 1e9,
-                                       "algorithmic_bytes_per_launch": hb_bytes}}
+    sites_per_launch = n_chains * L ** 3 // 2
+    if kt["mixed_n"] > 0:
+        total_bytes = args.steps * n_chains * (8 * N_HB + 12 * N_OR) * L ** 3
+        mixed_ms = kt["mixed_ms"] / kt["mixed_n"]
+        achieved = total_bytes / (kt["mixed_ms"] / 1e3) / 1e9
+        dom = {"kernel": "halfsweep_mixed_kernel<float> (phase-shifted heatbath + over-relaxation)",
+               "algorithmic_bytes_per_launch": total_bytes / kt["mixed_n"],
+               "avg_launch_ms": mixed_ms, "launches": kt["mixed_n"]}
+        traffic = None
+    else:
+        or_ms = kt["or_ms"] / max(1, kt["or_n"])
+        achieved = 12 * sites_per_launch / (or_ms / 1e3) / 1e9
+        dom = {"kernel": "halfsweep_kernel<float, over-relaxation>",
+               "algorithmic_bytes_per_launch": 12 * sites_per_launch, "avg_launch_ms": or_ms,
+               "heatbath_avg_launch_ms": kt["hb_ms"] / max(1, kt["hb_n"])}
+        traffic = profiled_traffic()
+    roofline = dict({"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_kind": f"{peak_kind} (burst copy)"}, **dom)
 
     # end to end through the C ABI with host buffers: upload the charge set
     # from host memory, one measured compound sweep (graph replay), read back
@@ -358,7 +367,7 @@ def run_ours(args):
 
     out = None
     if rank == 0:
-        launches = args.steps * (2 * PASSES + 1 + 1)  # half-sweeps, pass counter, finalize
+        launches = args.steps * (2 * PASSES + 1)  # half-sweeps and finalizes; few advances
         line = {
             "metric": METRIC, "value": value, "unit": "site-updates/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
@@ -435,7 +444,119 @@ def run_extra(args):
                         "ms_per_step": ms,
                         "algorithmic_GBps": rate / PASSES * (8 + 12 * N_OR) / 1e9})
         b.close()
+    elif args.workload == "cv":
+        results.extend(cv_experiment(args, stream))
+    elif args.workload == "cube":
+        results.append(cube_time_to_accuracy(args, stream))
     print(json.dumps({"workload": args.workload, "metric": METRIC, "results": results}), flush=True)
+
+
+def cv_experiment(args, stream):
+    """Learned Stein control variate on the 128^3 lattice: train on 2048 of the
+    chains' own samples, then compare plain and CV estimators on fresh samples.
+    Runs on the +-1 zero-net N=4096 system and on the paper's q=1 cube (N=8)."""
+    import numpy as np
+    import torch
+
+    from paper_1403_0711_gb300 import coulps, inputs, stein
+    out = []
+    box = (L, L, L)
+    for name, (sites, q), gold in (
+            ("pm4096", inputs.plus_minus(box, N_CHARGES, seed=1), "bench_128c_n4096_pm"),
+            ("cube8", inputs.cube(box, 2), "cube_128c_n8_q1")):
+        lat = coulps.Lattice(box, n_chains=N_CHAINS, precision=coulps.F32, seed=4242, stream=stream)
+        ch = coulps.Charges(lat, sites, q, log_capacity=4096)
+        rho = stein.charge_density(box, sites, q)
+        lat.sweep(300, N_HB, N_OR)
+        t0 = time.perf_counter()
+        phis, Aphis, es = stein.collect(lat, ch, rho, n_rounds=32, every=4, n_hb=N_HB, n_or=N_OR)
+        t_collect = time.perf_counter() - t0
+        cv = stein.SteinCV(seed=0, scale=0.3)
+        log = []
+        t0 = time.perf_counter()
+        stein.fit(cv, phis, Aphis, es, rho, steps=args.cv_steps, batch=16, lr=2e-3, log=log)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        del phis, Aphis
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e_list, tg_list, ms_sweep, ms_cv = [], [], 0.0, 0.0
+        rounds = args.cv_rounds
+        for r in range(rounds):
+            ev[0].record(stream)
+            ch.run(0, 1, N_HB, N_OR)
+            ev[1].record(stream)
+            tg = cv.evaluate(lat, rho)
+            ev[2].record(stream)
+            torch.cuda.synchronize()
+            ms_sweep += ev[0].elapsed_time(ev[1])
+            ms_cv += ev[1].elapsed_time(ev[2])
+            e_list.append(ch.samples()[-1, :, 2].copy())
+            tg_list.append(tg.cpu().numpy())
+        e = np.stack(e_list)  # (rounds, chains)
+        tgv = np.stack(tg_list)
+        ecv = e - cv.c * tgv
+        e_lat = golden_e_lat(gold)
+        ms_sweep /= rounds
+        ms_cv /= rounds
+        # per-chain means are independent; the time to eps|E| scales with the
+        # variance of one chain's mean per unit time
+        def proj(x, ms):
+            var_chain_mean = x.mean(axis=0).var(ddof=1)  # over chains, `rounds` samples each
+            se_now = (var_chain_mean / x.shape[1]) ** 0.5
+            t_now = rounds * ms / 1e3
+            return t_now * (se_now / (1e-3 * abs(e_lat))) ** 2, float(x.mean()), se_now
+        t_plain, m_plain, se_plain = proj(e, ms_sweep)
+        t_cv, m_cv, se_cv = proj(ecv, ms_sweep + ms_cv)
+        k = 4  # CV on every 4th sample: the other samples stay plain
+        mix = np.concatenate([e[i::k] if i else ecv[0::k] for i in range(k)], axis=0)
+        t_cv4, m_cv4, se_cv4 = proj(mix, ms_sweep + ms_cv / k)
+        out.append({
+            "system": name, "e_lat": e_lat, "training_samples": int(len(es)),
+            "collect_s": t_collect, "train_s": t_train, "train_steps": args.cv_steps,
+            "loss_first10": float(np.mean(log[:10])), "loss_last10": float(np.mean(log[-10:])),
+            "c": cv.c, "var_plain": float(e.var()), "var_cv": float(ecv.var()),
+            "variance_ratio": float(ecv.var() / e.var()),
+            "mean_plain": m_plain, "se_plain": se_plain, "mean_cv": m_cv, "se_cv": se_cv,
+            "ms_compound_sweep": ms_sweep, "ms_cv_eval": ms_cv,
+            "projected_s_to_1e-3_plain": t_plain, "projected_s_to_1e-3_cv": t_cv,
+            "projected_s_to_1e-3_cv_every4": t_cv4, "eval_rounds": rounds})
+        ch.close()
+        lat.close()
+        torch.cuda.empty_cache()
+    return out
+
+
+def cube_time_to_accuracy(args, stream):
+    """The paper's Fig. 2 geometry (N=8 charges q=1 in a cube at the centre of a
+    128^3 box): run until the batch-means error is 1e-3 |E_lat| (or a time
+    limit) and report the wall time and the error against E_lat."""
+    import torch
+
+    from paper_1403_0711_gb300 import coulps, inputs
+    box = (L, L, L)
+    sites, q = inputs.cube(box, 2)
+    e_lat = golden_e_lat("cube_128c_n8_q1")
+    lat = coulps.Lattice(box, n_chains=N_CHAINS, precision=coulps.F32, seed=99, stream=stream)
+    ch = coulps.Charges(lat, sites, q)
+    lat.sweep(300, N_HB, N_OR)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    est = None
+    while time.perf_counter() - t0 < args.cube_seconds:
+        ch.run(0, 500, N_HB, N_OR)
+        est = ch.estimate()
+        if est["stderr"] == est["stderr"] and est["stderr"] <= 1e-3 * abs(e_lat) and \
+                est["n"] > 64 * 2000:
+            break
+    wall = time.perf_counter() - t0
+    r = {"system": "cube8_q1", "e_lat": e_lat, "wall_s": wall, "samples": est["n"],
+         "mean": est["mean"], "stderr": est["stderr"], "tau_int": est["tau_int"],
+         "rel_stderr": est["stderr"] / abs(e_lat),
+         "delta": abs(est["mean"] - e_lat) / abs(e_lat),
+         "reached_1e-3": bool(est["stderr"] <= 1e-3 * abs(e_lat))}
+    ch.close()
+    lat.close()
+    return r
 
 
 if __name__ == "__main__":

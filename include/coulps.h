@@ -188,6 +188,19 @@ int coulps_chain_stats(coulps_charges_t ch, double *out, int64_t cap);
 int coulps_pool_stats(const double *stats, int64_t n_rows, double *mean, double *stderr_bm,
                       double *tau_int, int64_t *n);
 
+/* ---- schedule of the measured phase ------------------------------------ */
+/* COULPS_SCHEDULE_ALIGNED (default): every chain does the same kind of pass in
+ * the same launch.  COULPS_SCHEDULE_PHASED: in coulps_run's measured phase
+ * (n_hb > 0, n_or > 0, n_hb + n_or <= 8, n_meas >= 2, n_chains >= n_hb + n_or),
+ * chain k is delayed by k mod (n_hb + n_or) passes, so each launch mixes
+ * heatbath tiles (ALU-bound) of some chains with over-relaxation tiles
+ * (memory-bound) of the others.  Every chain does exactly the same passes,
+ * Philox draws and samples as with the aligned schedule (results are
+ * bitwise identical); only the order across chains changes. */
+#define COULPS_SCHEDULE_ALIGNED 0
+#define COULPS_SCHEDULE_PHASED 1
+int coulps_set_schedule(coulps_lattice_t lat, int schedule);
+
 /* ---- kernel timing ----------------------------------------------------- */
 /* With profiling on, every half-sweep launched by coulps_sweep (and by
  * coulps_run, which then launches directly instead of replaying its graph)
@@ -195,9 +208,10 @@ int coulps_pool_stats(const double *stats, int64_t n_rows, double *mean, double 
  * synchronises and returns, since profiling was enabled or last read:
  *   out[0] total ms of heatbath half-sweeps, out[1] their count,
  *   out[2] total ms of over-relaxation half-sweeps, out[3] their count,
+ *   out[4] total ms of mixed half-sweeps (phased schedule), out[5] their count,
  * and restarts the accumulation. */
 int coulps_set_profiling(coulps_lattice_t lat, int enable);
-int coulps_kernel_times(coulps_lattice_t lat, double out[4]);
+int coulps_kernel_times(coulps_lattice_t lat, double out[6]);
 
 /* ---- checkpoint -------------------------------------------------------- */
 /* Save / restore the full sampler state: fields of all chains, the pass

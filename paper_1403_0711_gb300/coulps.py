@@ -37,7 +37,9 @@ EXPORTS = (
     "coulps_batch_run", "coulps_batch_sync", "coulps_batch_estimate", "coulps_batch_samples",
     "coulps_batch_field_get", "coulps_cv_pack_weights", "coulps_cv_conv3d",
     "coulps_cv_conv3d_wgrad", "coulps_cv_pack_field", "coulps_cv_activate", "coulps_cv_stein_sum",
+    "coulps_set_schedule",
 )
+SCHEDULE_ALIGNED, SCHEDULE_PHASED = 0, 1
 STAT_STRIDE = 72
 
 
@@ -112,6 +114,7 @@ def load(path: str | Path | None = None):
         "coulps_cv_pack_field": (i32, [vp, vp, vp, vp]),
         "coulps_cv_activate": (i32, [vp, vp, vp, i64, vp]),
         "coulps_cv_stein_sum": (i32, [vp, vp, vp, vp, vp, vp, i32, i32, i32, i32, vp, i64, vp, vp]),
+        "coulps_set_schedule": (i32, [vp, i32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -224,10 +227,14 @@ class Lattice:
         _check(self._lib.coulps_set_profiling(self.handle, int(bool(enable))), "coulps_set_profiling")
 
     def kernel_times(self):
-        """{'hb_ms', 'hb_n', 'or_ms', 'or_n'} accumulated since the last call."""
-        a = (ctypes.c_double * 4)()
+        """{'hb_ms', 'hb_n', 'or_ms', 'or_n', 'mixed_ms', 'mixed_n'} since the last call."""
+        a = (ctypes.c_double * 6)()
         _check(self._lib.coulps_kernel_times(self.handle, a), "coulps_kernel_times")
-        return {"hb_ms": a[0], "hb_n": int(a[1]), "or_ms": a[2], "or_n": int(a[3])}
+        return {"hb_ms": a[0], "hb_n": int(a[1]), "or_ms": a[2], "or_n": int(a[3]),
+                "mixed_ms": a[4], "mixed_n": int(a[5])}
+
+    def set_schedule(self, schedule):
+        _check(self._lib.coulps_set_schedule(self.handle, int(schedule)), "coulps_set_schedule")
 
     def checkpoint_save(self, path, charges=None):
         _check(self._lib.coulps_checkpoint_save(self.handle, charges.handle if charges else None,

@@ -67,11 +67,17 @@ struct coulps_lattice {
   bool profiling = false;
   struct Timed {
     cudaEvent_t a, b;
-    int kind;  // 0 heatbath, 1 over-relaxation
+    int kind;  // 0 heatbath, 1 over-relaxation, 2 mixed (phase-shifted schedule)
   };
   std::vector<cudaEvent_t> spare_events;
   std::vector<Timed> pending;
-  double times[4] = {0, 0, 0, 0};
+  double times[6] = {0, 0, 0, 0, 0, 0};
+  // measured-phase schedule (COULPS_SCHEDULE_*) and its steady-state graph
+  int schedule = COULPS_SCHEDULE_ALIGNED;
+  cudaGraphExec_t sgraph = nullptr;
+  const void *sgraph_key = nullptr;
+  int sgraph_hb = -1, sgraph_or = -1;
+  Tile sgraph_tile = {0, 0};
 };
 
 struct coulps_charges {
@@ -349,6 +355,141 @@ void drop_graph(coulps_lattice *L) {
   if (L->graph) cudaGraphExecDestroy(L->graph);
   L->graph = nullptr;
   L->graph_key = nullptr;
+  if (L->sgraph) cudaGraphExecDestroy(L->sgraph);
+  L->sgraph = nullptr;
+  L->sgraph_key = nullptr;
+}
+
+// ---- phase-shifted schedule ------------------------------------------------
+// Chain k is in group k % P (P = passes per compound sweep) and runs P - ...
+// its pass p at slot t = p + g.  In every launch of the steady state one
+// group does heatbath passes while the others do over-relaxation, so the
+// ALU-bound and the memory-bound half-sweeps share the GPU.  Every chain
+// still does exactly the passes and samples of the aligned schedule.
+//
+// One slot: red and black mixed half-sweeps, then the finalize of any group
+// that completed a measured compound sweep.  The pass index of group g is
+// *d_pass + (t - g - t_dev), where the device counter holds B + t_dev.
+int enqueue_slot(coulps_lattice *L, coulps_charges *C, int n_hb, int n_or, int64_t t,
+                 int64_t t_dev, int64_t T) {
+  const int P = n_hb + n_or;
+  MixedArgs m;
+  std::memset(&m, 0, sizeof(m));
+  SweepArgs &a = m.base;
+  a.field = L->field;
+  a.Lx = L->g.Lx; a.Ly = L->g.Ly; a.Lz = L->g.Lz;
+  a.W = L->g.W; a.Wq = L->g.Wq; a.QW = L->g.W / 4;
+  a.TY = L->tile.ty; a.DZ = L->tile.dz;
+  {
+    const PhiloxKeys K = philox_keys((uint32_t)(L->seed & 0xffffffffu), (uint32_t)(L->seed >> 32));
+    for (int i = 0; i < 20; ++i) a.round_keys[i] = K.k[i];
+  }
+  a.pass_ptr = L->d_pass;
+  a.chain_elems = L->g.chain_elems;
+  a.colour_elems = L->g.colour_elems;
+  a.err = L->d_err;
+  a.g_off = C->d_goff;
+  a.g_ent = C->d_gent;
+  a.g_q = C->d_gq;
+  a.g_partials = C->d_fpart;
+  m.groups = P;
+  bool any_gather = false;
+  for (int g = 0; g < P; ++g) {
+    const int64_t p = t - g;
+    const bool active = p >= 0 && p < T;
+    m.mode[g] = active ? ((p % P) < n_hb ? 1 : 2) : 0;
+    m.pass_delta[g] = (uint32_t)(p - t_dev);
+  }
+  for (int c = 0; c < 2; ++c) {
+    a.colour = c;
+    for (int g = 0; g < P; ++g) {
+      const int64_t p = t - g;
+      m.gather[g] = (c == 1 && m.mode[g] != 0 && p % P == P - 1) ? 1 : 0;
+      any_gather = any_gather || m.gather[g];
+    }
+    cudaEvent_t ea = nullptr, eb = nullptr;
+    if (L->profiling) {
+      ea = take_event(L);
+      eb = take_event(L);
+      if (!ea || !eb) return COULPS_ECUDA;
+      CK(cudaEventRecord(ea, L->stream));
+    }
+    CK(launch_halfsweep_mixed(L->g, L->tile, L->tm_halo, L->tm_own, m, L->stream));
+    if (L->profiling) {
+      CK(cudaEventRecord(eb, L->stream));
+      L->pending.push_back({ea, eb, 2});
+    }
+  }
+  if (any_gather)
+    for (int g = 0; g < P; ++g)
+      if (m.gather[g])
+        CK(launch_finalize_group(C->d_fpart, C->fused_nblk, L->g.n_chains, g, P, C->d_stats,
+                                 C->d_log, C->log_cap, L->d_err, L->stream));
+  return COULPS_OK;
+}
+
+// The measured phase of coulps_run on the phase-shifted schedule (all chains
+// start aligned at pass counter B and end aligned at B + n_meas * P).
+int run_staggered(coulps_lattice *L, coulps_charges *C, int n_meas, int n_hb, int n_or) {
+  const int P = n_hb + n_or;
+  const int64_t T = (int64_t)n_meas * P;
+  int st;
+  // prologue: slots 0 .. P-2 (no group completes a compound sweep yet)
+  for (int64_t t = 0; t < P - 1; ++t)
+    if ((st = enqueue_slot(L, C, n_hb, n_or, t, 0, T))) return st;
+  CK(launch_advance_pass(L->d_pass, (uint32_t)(P - 1), L->stream));
+  int64_t t_dev = P - 1;
+  // steady state: n_meas - 1 periods of P slots, one graph
+  const bool capturable = L->stream != nullptr && !L->profiling;
+  auto enqueue_period = [&](int64_t t0) -> int {
+    for (int s = 0; s < P; ++s) {
+      int r = enqueue_slot(L, C, n_hb, n_or, t0 + s, t0, T);
+      if (r) return r;
+    }
+    CK(launch_advance_pass(L->d_pass, (uint32_t)P, L->stream));
+    return COULPS_OK;
+  };
+  if (n_meas > 1 && capturable &&
+      (L->sgraph_key != C || L->sgraph_hb != n_hb || L->sgraph_or != n_or ||
+       L->sgraph_tile.ty != L->tile.ty || L->sgraph_tile.dz != L->tile.dz)) {
+    if (L->sgraph) cudaGraphExecDestroy(L->sgraph);
+    L->sgraph = nullptr;
+    cudaGraph_t gr = nullptr;
+    CK(cudaStreamBeginCapture(L->stream, cudaStreamCaptureModeThreadLocal));
+    // a steady period is the same for every t0 once T is large: capture it
+    // with T large enough that no group is idle
+    const int s1 = enqueue_period(t_dev);
+    cudaError_t e = cudaStreamEndCapture(L->stream, &gr);
+    if (s1 || e != cudaSuccess) {
+      cudaGetLastError();
+      if (gr) cudaGraphDestroy(gr);
+      return s1 ? s1 : COULPS_ECUDA;
+    }
+    e = cudaGraphInstantiate(&L->sgraph, gr, 0);
+    cudaGraphDestroy(gr);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      L->sgraph = nullptr;
+      return COULPS_ECUDA;
+    }
+    L->sgraph_key = C;
+    L->sgraph_hb = n_hb;
+    L->sgraph_or = n_or;
+    L->sgraph_tile = L->tile;
+  }
+  for (int k = 0; k < n_meas - 1; ++k) {
+    if (capturable) {
+      CK(cudaGraphLaunch(L->sgraph, L->stream));
+    } else if ((st = enqueue_period(t_dev))) {
+      return st;
+    }
+    t_dev += P;
+  }
+  // epilogue: slots T - 1 .. T + P - 2
+  for (int64_t t = t_dev; t < T + P - 1; ++t)
+    if ((st = enqueue_slot(L, C, n_hb, n_or, t, t_dev, T))) return st;
+  CK(launch_advance_pass(L->d_pass, (uint32_t)(T - t_dev), L->stream));
+  return COULPS_OK;
 }
 
 uint64_t fnv1a(uint64_t h, const void *p, size_t n) {
@@ -656,6 +797,13 @@ int coulps_run(coulps_lattice_t L, coulps_charges_t C, int n_therm, int n_meas, 
     st = stage_gather(L, C);
     if (st) return st;
   }
+  const int P = n_hb + n_or;
+  if (L->schedule == COULPS_SCHEDULE_PHASED && n_hb > 0 && n_or > 0 && P <= kMaxGroups &&
+      n_meas >= 2 && L->g.n_chains >= P) {
+    st = run_staggered(L, C, n_meas, n_hb, n_or);
+    if (!st) L->pass += (uint64_t)n_meas * P;
+    return st;
+  }
   const bool capturable = L->stream != nullptr && !L->profiling;
   if (capturable && (L->graph_key != C || L->graph_hb != n_hb || L->graph_or != n_or ||
                      L->graph_tile.ty != L->tile.ty || L->graph_tile.dz != L->tile.dz)) {
@@ -817,6 +965,14 @@ int coulps_charges_update(coulps_charges_t C, const int32_t *site, const double 
   return COULPS_OK;
 }
 
+int coulps_set_schedule(coulps_lattice_t L, int schedule) {
+  if (!L || (schedule != COULPS_SCHEDULE_ALIGNED && schedule != COULPS_SCHEDULE_PHASED))
+    return COULPS_EINVAL;
+  if (schedule != L->schedule) drop_graph(L);
+  L->schedule = schedule;
+  return COULPS_OK;
+}
+
 int coulps_set_profiling(coulps_lattice_t L, int enable) {
   if (!L) return COULPS_EINVAL;
   L->profiling = enable != 0;
@@ -824,7 +980,7 @@ int coulps_set_profiling(coulps_lattice_t L, int enable) {
   return COULPS_OK;
 }
 
-int coulps_kernel_times(coulps_lattice_t L, double out[4]) {
+int coulps_kernel_times(coulps_lattice_t L, double out[6]) {
   if (!L || !out) return COULPS_EINVAL;
   CK(cudaStreamSynchronize(L->stream));
   for (auto &t : L->pending) {
@@ -836,7 +992,7 @@ int coulps_kernel_times(coulps_lattice_t L, double out[4]) {
     L->spare_events.push_back(t.b);
   }
   L->pending.clear();
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < 6; ++i) {
     out[i] = L->times[i];
     L->times[i] = 0;
   }

@@ -40,12 +40,11 @@ constexpr int kPlaneBytes = ((kRowSites * 16 + 127) / 128) * 128;  // 8 channels
 constexpr int kRowBytes = 2 * kPlaneBytes;               // both channel halves
 constexpr int kABytes = 9 * kRowBytes;                   // nine input rows
 constexpr int kWBytes = 27 * 512;                        // 27 offsets x (16 x 16) BF16
-// Shared memory: [header 128][A 9 rows][W 27 x 512][slack]; the slack keeps
-// every address a descriptor could form inside this CTA's allocation.
+// Shared memory: [header 128][A 9 rows][W 27 x 512] (54 KB: four CTAs per SM).
 constexpr int kHdr = 128;
 constexpr int kAOff = kHdr;
 constexpr int kWOff = kAOff + ((kABytes + 127) / 128) * 128;
-constexpr int kCvSmem = kWOff + kWBytes + 40 * 1024;
+constexpr int kCvSmem = kWOff + kWBytes;
 
 // tcgen05 instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1),
 // A = B = BF16 (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0),
@@ -262,10 +261,17 @@ int cv_conv3d_launch(const void *in_bf16, const void *wpack, const float *bias, 
     }
     configured = true;
   }
-  int dev = 0, sms = 0;
+  int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int grid = sms * 2;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cv_conv3d_kernel, kCvThreads, smem) !=
+          cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  if (per_sm > 8) per_sm = 8;  // 8 x 32 TMEM columns of 512
+  int grid = sms * per_sm;
   if (grid > a.n_tiles) grid = a.n_tiles;
   if (grid < 1) return COULPS_OK;
   cv_conv3d_kernel<<<grid, kCvThreads, smem, s>>>(map, a);

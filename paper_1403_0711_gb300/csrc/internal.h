@@ -74,6 +74,24 @@ struct SweepArgs {
   double *g_partials;  // [chain][y tiles * z slabs][2]
 };
 
+// Phase-shifted schedule: chain k belongs to group k % groups; per group the
+// launch does nothing (mode 0), a heatbath (1) or an over-relaxation (2)
+// half-sweep with pass index *pass_ptr + pass_delta, gathering Q, P if
+// gather != 0.
+constexpr int kMaxGroups = 8;
+struct MixedArgs {
+  SweepArgs base;  // pass_off and g_* of base are ignored except g_off/g_ent/g_q/g_partials
+  int groups;
+  int mode[kMaxGroups];
+  uint32_t pass_delta[kMaxGroups];
+  int gather[kMaxGroups];
+};
+cudaError_t launch_halfsweep_mixed(const Geometry &g, const Tile &t, const CUtensorMap &tm_halo,
+                                   const CUtensorMap &tm_own, const MixedArgs &a, cudaStream_t s);
+cudaError_t launch_finalize_group(const double *partials, int nblk, int n_chains, int first,
+                                  int stride, double *stats, double *log, int64_t log_cap,
+                                  int *err, cudaStream_t s);
+
 // Entry packing of the fused gather.
 constexpr uint32_t kGatherColourBit = 0x80000000u;
 

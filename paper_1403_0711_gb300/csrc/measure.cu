@@ -70,6 +70,23 @@ __global__ void finalize_kernel(const double *__restrict__ partials, int nblk, i
   record_sample(st, Q, P, row, err);
 }
 
+// finalize for the chains first, first + stride, ... only
+__global__ void finalize_group_kernel(const double *__restrict__ partials, int nblk, int n_chains,
+                                      int first, int stride, double *__restrict__ stats,
+                                      double *__restrict__ log, int64_t log_cap, int *err) {
+  const int chain = first + (blockIdx.x * blockDim.x + threadIdx.x) * stride;
+  if (chain >= n_chains) return;
+  double Q = 0.0, P = 0.0;
+  for (int b = 0; b < nblk; ++b) {
+    Q += partials[2 * ((size_t)chain * nblk + b) + 0];
+    P += partials[2 * ((size_t)chain * nblk + b) + 1];
+  }
+  double *st = stats + (size_t)chain * kStatStride;
+  const int64_t s = (int64_t)st[kStatN];
+  double *row = (log != nullptr && s < log_cap) ? log + 3 * ((size_t)s * n_chains + chain) : nullptr;
+  record_sample(st, Q, P, row, err);
+}
+
 __global__ void reset_stats_kernel(double *stats, int n_chains) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_chains * kStatStride) return;
@@ -103,6 +120,16 @@ cudaError_t launch_finalize(const double *partials, int nblk, int n_chains, doub
                             double *log, int64_t log_cap, int *err, cudaStream_t s) {
   finalize_kernel<<<(n_chains + 127) / 128, 128, 0, s>>>(partials, nblk, n_chains, stats, log,
                                                           log_cap, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_group(const double *partials, int nblk, int n_chains, int first,
+                                  int stride, double *stats, double *log, int64_t log_cap,
+                                  int *err, cudaStream_t s) {
+  const int count = (n_chains - first + stride - 1) / stride;
+  if (count <= 0) return cudaSuccess;
+  finalize_group_kernel<<<(count + 127) / 128, 128, 0, s>>>(partials, nblk, n_chains, first, stride,
+                                                            stats, log, log_cap, err);
   return cudaGetLastError();
 }
 

@@ -85,6 +85,74 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Phase-shifted schedule: every CTA looks up its chain's group and runs that
+// group's half-sweep kind; idle groups' CTAs return before touching anything.
+template <typename T>
+__global__ void __launch_bounds__(256)
+    halfsweep_mixed_kernel(const __grid_constant__ CUtensorMap tm_halo,
+                           const __grid_constant__ CUtensorMap tm_own, const MixedArgs m) {
+  const SweepArgs &a = m.base;
+  const int chain = blockIdx.z;
+  const int grp = chain % m.groups;
+  const int mode = m.mode[grp];
+  if (mode == 0) return;
+  const bool gather = m.gather[grp] != 0;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *smem = reinterpret_cast<unsigned char *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
+  TileJob<T> j;
+  j.tm_halo = &tm_halo;
+  j.tm_own = &tm_own;
+  j.colour = a.colour;
+  j.map_other = 2 * chain + (a.colour ^ 1);
+  j.map_own = 2 * chain + a.colour;
+  j.out = reinterpret_cast<T *>(a.field) + (size_t)chain * a.chain_elems +
+          (size_t)a.colour * a.colour_elems;
+  j.Lx = a.Lx; j.Ly = a.Ly; j.Lz = a.Lz; j.W = a.W; j.Wq = a.Wq; j.QW = a.QW; j.TY = a.TY;
+  j.y0 = blockIdx.x * a.TY;
+  j.z0 = blockIdx.y * a.DZ;
+  j.nz = min(a.DZ, a.Lz - j.z0);
+  j.rng_id = (uint32_t)chain;
+  j.pass = *a.pass_ptr + m.pass_delta[grp];
+  j.g_off = a.g_off + (size_t)blockIdx.x * a.Lz;
+  j.g_ent = a.g_ent;
+  j.g_q = a.g_q;
+  const PhiloxKeys &K = *reinterpret_cast<const PhiloxKeys *>(a.round_keys);
+  double sq = 0.0, sp = 0.0;
+  int gbase = 0;
+  ring_init(smem);
+  if (mode == 1) {
+    if (gather) march_tile<T, false, true>(j, K, smem, a.err, gbase, sq, sp);
+    else march_tile<T, false, false>(j, K, smem, a.err, gbase, sq, sp);
+  } else {
+    if (gather) march_tile<T, true, true>(j, K, smem, a.err, gbase, sq, sp);
+    else march_tile<T, true, false>(j, K, smem, a.err, gbase, sq, sp);
+  }
+  if (gather) {
+    const size_t cta = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+    block_partials(sq, sp, smem,
+                   a.g_partials + 2 * ((size_t)chain * gridDim.x * gridDim.y + cta));
+  }
+}
+
+template <typename T>
+cudaError_t launch_mixed_t(const Geometry &g, const Tile &t, const CUtensorMap &tm_halo,
+                           const CUtensorMap &tm_own, const MixedArgs &m, cudaStream_t s) {
+  const SmemLayout lay = smem_layout(t.ty, g.W, (int)sizeof(T), true, true);
+  const size_t smem = (size_t)lay.total + 128;
+  auto kfn = halfsweep_mixed_kernel<T>;
+  static int configured_bytes = 0;
+  if ((int)smem > configured_bytes) {
+    cudaError_t e =
+        cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured_bytes = (int)smem;
+  }
+  dim3 grid((g.Ly + t.ty - 1) / t.ty, (g.Lz + t.dz - 1) / t.dz, g.n_chains);
+  kfn<<<grid, dim3((g.W / 4) * t.ty), smem, s>>>(tm_halo, tm_own, m);
+  return cudaGetLastError();
+}
+
 __global__ void advance_pass_kernel(uint32_t *pass, uint32_t n) { *pass += n; }
 
 template <typename T, bool OR, bool GATHER>
@@ -129,6 +197,13 @@ cudaError_t launch_halfsweep(const Geometry &g, const Tile &t, const CUtensorMap
                              cudaStream_t s) {
   if (g.precision == COULPS_F32) return launch_p<float>(g, t, tm_halo, tm_own, a, overrelax, s);
   return launch_p<double>(g, t, tm_halo, tm_own, a, overrelax, s);
+}
+
+cudaError_t launch_halfsweep_mixed(const Geometry &g, const Tile &t, const CUtensorMap &tm_halo,
+                                   const CUtensorMap &tm_own, const MixedArgs &m, cudaStream_t s) {
+  if (m.groups < 1 || m.groups > kMaxGroups) return cudaErrorInvalidValue;
+  if (g.precision == COULPS_F32) return launch_mixed_t<float>(g, t, tm_halo, tm_own, m, s);
+  return launch_mixed_t<double>(g, t, tm_halo, tm_own, m, s);
 }
 
 cudaError_t launch_advance_pass(uint32_t *pass, uint32_t n, cudaStream_t s) {

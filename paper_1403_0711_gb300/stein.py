@@ -147,7 +147,7 @@ def divergence_kernel(W1, W2, W3, fmask=None):
 
 
 class SteinCV(torch.nn.Module):
-    def __init__(self, seed=0, scale=0.3, device="cuda"):
+    def __init__(self, seed=0, scale=0.3, device="cuda", w3_scale=0.0):
         super().__init__()
         g = torch.Generator().manual_seed(seed)
 
@@ -158,7 +158,8 @@ class SteinCV(torch.nn.Module):
         self.b1 = rnd(16, sc=0.1)
         self.W2 = rnd(16, 16, 3, 3, 3, sc=scale / 4)
         self.b2 = rnd(16, sc=0.1)
-        self.W3 = rnd(1, 16, 3, 3, 3, sc=scale / 16)
+        # the output layer starts at zero: T g = 0, i.e. the plain estimator
+        self.W3 = rnd(1, 16, 3, 3, 3, sc=w3_scale)
         self.b3 = rnd(1, sc=0.0)
         self.c = 1.0  # coefficient of T g, set by fit()
 

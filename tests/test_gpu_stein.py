@@ -35,7 +35,7 @@ def test_evaluate_matches_autograd_path_and_oracle(env):
     lat = coulps.Lattice(L, n_chains=3, precision=coulps.F32, seed=5, stream=stream)
     lat.sweep(20, 1, 1)
     rho = stein.charge_density(L, sites, q)
-    cv = stein.SteinCV(seed=2, scale=0.6)
+    cv = stein.SteinCV(seed=2, scale=0.6, w3_scale=0.1)
     tg_eval = cv.evaluate(lat, rho).cpu().numpy()
     phis, Aphis = stein.pack_inputs(lat, rho)
     with torch.no_grad():
@@ -83,7 +83,7 @@ def test_stein_term_has_zero_mean_under_sampler(env):
     lat = coulps.Lattice(L, n_chains=512, precision=coulps.F32, seed=77, stream=stream)
     lat.sweep(200, 1, 0)
     rho = stein.charge_density(L, sites, q)
-    cv = stein.SteinCV(seed=4, scale=0.6)
+    cv = stein.SteinCV(seed=4, scale=0.6, w3_scale=0.1)
     vals = []
     for _ in range(40):
         lat.sweep(8, 1, 0)
