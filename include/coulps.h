@@ -296,12 +296,17 @@ int coulps_batch_field_get(coulps_batch_t b, int system, double *host_xyz);
 int coulps_cv_pack_weights(const float *w, uint16_t *wpack);
 int coulps_cv_conv3d(const void *in_bf16, const void *wpack, const float *bias, float *out,
                      int nb, int Lx, int Ly, int Lz, int *err, void *stream);
+/* Same convolution with the activation fused into its epilogue: writes
+ * a = tanh(h) and s = 1 - a^2 as BF16 [nb][Lz][Ly][Lx][16] (16-byte aligned). */
+int coulps_cv_conv3d_tanh(const void *in_bf16, const void *wpack, const float *bias,
+                          void *a_bf16, void *s_bf16, int nb, int Lx, int Ly, int Lz, int *err,
+                          void *stream);
 
 /* coulps_cv_conv3d_wgrad: weight gradient of coulps_cv_conv3d,
  *   dW[co][ci][o] = sum_{b, p} dh[b, p, co] a[b, p + o, ci]   (a = 0 outside),
  * o = 9 kz + 3 ky + kx, i.e. dW has PyTorch's [co][ci][kz][ky][kx] order.
  * a, dh: device BF16 [nb][Lz][Ly][Lx][16]; dW device 16*16*27 floats;
- * scratch: device, >= min(256, ceil(nb*Lx*Ly*Lz / 4096)) * 27 * 256 floats.
+ * scratch: device, >= min(1024, ceil(T / 32)) * 27 * 256 floats, T = nb*Lz*Ly*ceil(Lx/64).
  * Summed in a fixed order (reproducible).  Asynchronous. */
 int coulps_cv_conv3d_wgrad(const void *a_bf16, const void *dh_bf16, float *dW, int nb, int Lx,
                            int Ly, int Lz, float *scratch, int64_t scratch_floats, void *stream);

@@ -37,7 +37,7 @@ EXPORTS = (
     "coulps_batch_run", "coulps_batch_sync", "coulps_batch_estimate", "coulps_batch_samples",
     "coulps_batch_field_get", "coulps_cv_pack_weights", "coulps_cv_conv3d",
     "coulps_cv_conv3d_wgrad", "coulps_cv_pack_field", "coulps_cv_activate", "coulps_cv_stein_sum",
-    "coulps_set_schedule",
+    "coulps_set_schedule", "coulps_cv_conv3d_tanh",
 )
 SCHEDULE_ALIGNED, SCHEDULE_PHASED = 0, 1
 STAT_STRIDE = 72
@@ -115,6 +115,7 @@ def load(path: str | Path | None = None):
         "coulps_cv_activate": (i32, [vp, vp, vp, i64, vp]),
         "coulps_cv_stein_sum": (i32, [vp, vp, vp, vp, vp, vp, i32, i32, i32, i32, vp, i64, vp, vp]),
         "coulps_set_schedule": (i32, [vp, i32]),
+        "coulps_cv_conv3d_tanh": (i32, [vp, vp, vp, vp, vp, i32, i32, i32, i32, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)

@@ -11,21 +11,26 @@
 // N = 16 output channels, and K = 27 offsets x 16 input channels, issued as 27
 // tcgen05.mma of shape 128 x 16 x 16 (kind::f16, BF16 operands, FP32
 // accumulator in 16 TMEM columns).  The A operand of offset (dz, dy, dx) is the
-// tile's x range shifted by dx in input row (y + dy, z + dz): the CTA loads the
-// nine input rows (x0-1 .. x0+128) once per tile by TMA, each as two planes
+// tile's x range shifted by dx in input row (y + dy, z + dz): the input rows
+// (x0-1 .. x0+128) arrive by TMA, each as two planes
 // of 8 channels (16 bytes per site), which is exactly the tensor core's
 // K-major core-matrix layout without swizzle (8 rows x 16 bytes per core
 // matrix, next 8 rows at +128 bytes, the second 8 channels at +plane): a shift
 // by dx is just a +16 byte start address.  Out-of-box rows, planes and x are
-// zero-filled by the TMA unit.  Weights sit in shared memory in the same
-// layout (prepared on the host), loaded once per CTA.  One elected thread
-// issues the MMAs and commits them to an mbarrier; then each warp reads its
-// 32 TMEM lanes (sites) x 16 columns (channels) with tcgen05.ld, adds the bias
-// and stores.  Every wait is bounded; on a timeout the CTA sets the error word,
-// waits for its own copies and MMAs (bounded again), frees its TMEM and
-// returns.
+// zero-filled by the TMA unit.  A CTA walks all y of a column (b, z, x tile)
+// keeping 4 rows per input plane in a ring, so each tile loads one new row per
+// plane, one tile ahead.  Weights sit in shared memory in the same layout
+// (prepared on the host), loaded once per CTA.  One elected thread issues the
+// MMAs of tile y into one of two TMEM accumulators and commits them to an
+// mbarrier while the warps read tile y-1 from the other (tcgen05.ld: 32 lanes
+// = sites x 16 columns = channels per warp), add the bias and store either h
+// (FP32) or tanh(h) and 1 - tanh(h)^2 (BF16).  Every wait is bounded; on a
+// timeout the CTA sets the error word, waits for its own copies and MMAs
+// (bounded again), frees its TMEM and returns.
 #include <cstdint>
 #include <cstring>
+
+#include <cuda_bf16.h>
 
 #include "device_common.cuh"
 #include "internal.h"
@@ -38,9 +43,10 @@ constexpr int kTileX = 128;           // sites per tile (MMA M)
 constexpr int kRowSites = kTileX + 2; // with the x halo
 constexpr int kPlaneBytes = ((kRowSites * 16 + 127) / 128) * 128;  // 8 channels x 2 B per site
 constexpr int kRowBytes = 2 * kPlaneBytes;               // both channel halves
-constexpr int kABytes = 9 * kRowBytes;                   // nine input rows
+constexpr int kRing = 4;                                 // input rows kept per z plane
+constexpr int kABytes = 3 * kRing * kRowBytes;           // 3 planes x 4 rows
 constexpr int kWBytes = 27 * 512;                        // 27 offsets x (16 x 16) BF16
-// Shared memory: [header 128][A 9 rows][W 27 x 512] (54 KB: four CTAs per SM).
+// Shared memory: [header 128][A: 3 planes x 4-row ring][W 27 x 512]
 constexpr int kHdr = 128;
 constexpr int kAOff = kHdr;
 constexpr int kWOff = kAOff + ((kABytes + 127) / 128) * 128;
@@ -119,31 +125,35 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 struct CvConvArgs {
   const uint4 *wpack;  // kWBytes of weights in shared-memory order
   const float *bias;   // 16
-  float *out;          // [b][z][y][x][16]
+  float *out;          // mode 0: h [b][z][y][x][16] FP32
+  __nv_bfloat16 *out_a, *out_s;  // mode 1: tanh(h), 1 - tanh(h)^2, BF16
+  int mode;
   int Lx, Ly, Lz, nb;
-  int n_tiles;         // nb * Lz * Ly * ceil(Lx / 128)
+  int n_cols;          // nb * Lz * ceil(Lx / 128): one column = all y of (b, z, x tile)
   int *err;
 };
 
+// One CTA walks columns (b, z, x tile) and, within a column, the tiles y =
+// 0 .. Ly-1.  Tile y needs input rows y-1, y, y+1 of planes z-1, z, z+1; the
+// rows of each plane sit in a 4-row ring, so each tile loads one new row per
+// plane (row y+2, one tile ahead).  Tile y's 27 MMAs go to TMEM buffer
+// (count & 1) while the warps read tile y-1 from the other buffer.
 __global__ void __launch_bounds__(kCvThreads)
     cv_conv3d_kernel(const __grid_constant__ CUtensorMap tm_in, const CvConvArgs a) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem);  // [0] TMA, [1] MMA
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem);  // [0..3] row ring, [4..5] MMA buffers
   volatile uint32_t *tmem_slot = reinterpret_cast<volatile uint32_t *>(smem + 64);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 80);
   const uint32_t sA = smem_addr(smem + kAOff), sW = smem_addr(smem + kWOff);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  // weights into shared memory (generic proxy), then make them visible to
-  // the tensor core (async proxy)
   for (int i = tid; i < kWBytes / 16; i += kCvThreads)
     reinterpret_cast<uint4 *>(smem + kWOff)[i] = a.wpack[i];
   if (tid == 0) {
     prefetch_tensormap(&tm_in);
-    mbar_init(smem_addr(&bars[0]), 1);
-    mbar_init(smem_addr(&bars[1]), 1);
+    for (int i = 0; i < 6; ++i) mbar_init(smem_addr(&bars[i]), 1);
     *abort_flag = 0;
     fence_mbar_init();
   }
@@ -161,67 +171,147 @@ __global__ void __launch_bounds__(kCvThreads)
   for (int i = 0; i < 16; ++i) bias[i] = a.bias[i];
 
   const int xt = (a.Lx + kTileX - 1) / kTileX;
-  uint32_t phase = 0;
-  int pending_tma = 0, pending_mma = 0;  // thread 0: operations not yet waited
-  for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
-    int r = t;
-    const int tx = r % xt; r /= xt;
-    const int y = r % a.Ly; r /= a.Ly;
-    const int z = r % a.Lz;
-    const int b = r / a.Lz;
-    const int x0 = tx * kTileX;
-    if (tid == 0) {
-      const uint32_t bar = smem_addr(&bars[0]);
-      mbar_arrive_expect_tx(bar, 18 * kRowSites * 16);
-      for (int dz = 0; dz < 3; ++dz)
-        for (int dy = 0; dy < 3; ++dy)
-          for (int h = 0; h < 2; ++h)
-            tma_load_5d(sA + (dz * 3 + dy) * kRowBytes + h * kPlaneBytes, &tm_in, 8 * h, x0 - 1,
-                        y + dy - 1, z + dz - 1, b, bar);
-      pending_tma = 1;
-    }
-    bool ok = mbar_wait_bounded(smem_addr(&bars[0]), phase);
-    if (tid == 0 && ok) {
-      pending_tma = 0;
-      fence_after_sync();
-      for (int o = 0; o < 27; ++o) {
-        const int dz = o / 9, dy = (o / 3) % 3, dx = o % 3;
-        const uint64_t da = smem_desc(sA + (dz * 3 + dy) * kRowBytes + dx * 16, kPlaneBytes, 128);
-        const uint64_t db = smem_desc(sW + o * 512, 256, 128);
-        mma_bf16(tmem, da, db, kIdesc, o > 0 ? 1u : 0u);
-      }
-      mma_commit(smem_addr(&bars[1]));
-      pending_mma = 1;
-    }
-    ok = ok && mbar_wait_bounded(smem_addr(&bars[1]), phase);
-    if (!ok) {
-      atomicOr(a.err, kErrTimeout);
-      *abort_flag = 1;
-    }
-    __syncthreads();
-    if (*abort_flag) break;
-    if (tid == 0) pending_mma = 0;
-    fence_after_sync();
+  int64_t grow = 0;  // rows this CTA has loaded (ring position and phase)
+  int64_t gtile = 0;  // tiles this CTA has issued MMAs for (TMEM buffer and phase)
+  // thread 0's counts, for draining after a timeout
+  int64_t rows_issued = 0, rows_waited = 0, mma_issued = 0, mma_waited = 0;
+  bool aborted = false;
+
+  // row k of a column is input row yrow = k - 1; ring slot (grow + k) % 4
+  auto row_slot = [&](int64_t g) { return (int)(g % kRing); };
+  auto row_parity = [&](int64_t g) { return (uint32_t)((g / kRing) & 1); };
+  auto row_base = [&](int dzi, int64_t g) {
+    return sA + (uint32_t)((dzi * kRing + row_slot(g)) * kRowBytes);
+  };
+
+  auto epilogue = [&](int64_t tt, int b, int z, int y, int x0) {
     float v[16];
-    tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16), v);
+    tmem_ld16(tmem + (uint32_t)((tt & 1) * 16) + ((uint32_t)(32 * warp) << 16), v);
     const int x = x0 + 32 * warp + lane;
     if (x < a.Lx) {
-      float4 *o4 = reinterpret_cast<float4 *>(
-          a.out + ((((size_t)b * a.Lz + z) * a.Ly + y) * a.Lx + x) * 16);
+      const size_t site = (((size_t)b * a.Lz + z) * a.Ly + y) * a.Lx + x;
+      if (a.mode == 0) {
+        float4 *o4 = reinterpret_cast<float4 *>(a.out + site * 16);
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
-        o4[i] = make_float4(v[4 * i] + bias[4 * i], v[4 * i + 1] + bias[4 * i + 1],
-                            v[4 * i + 2] + bias[4 * i + 2], v[4 * i + 3] + bias[4 * i + 3]);
+        for (int i = 0; i < 4; ++i)
+          o4[i] = make_float4(v[4 * i] + bias[4 * i], v[4 * i + 1] + bias[4 * i + 1],
+                              v[4 * i + 2] + bias[4 * i + 2], v[4 * i + 3] + bias[4 * i + 3]);
+      } else {
+        __align__(16) __nv_bfloat16 ta[16], ts[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const float t = tanhf(v[i] + bias[i]);
+          ta[i] = __float2bfloat16_rn(t);
+          ts[i] = __float2bfloat16_rn(1.f - t * t);
+        }
+        uint4 *pa = reinterpret_cast<uint4 *>(a.out_a + site * 16);
+        uint4 *ps = reinterpret_cast<uint4 *>(a.out_s + site * 16);
+        pa[0] = reinterpret_cast<const uint4 *>(ta)[0];
+        pa[1] = reinterpret_cast<const uint4 *>(ta)[1];
+        ps[0] = reinterpret_cast<const uint4 *>(ts)[0];
+        ps[1] = reinterpret_cast<const uint4 *>(ts)[1];
+      }
     }
-    fence_before_sync();
-    __syncthreads();  // TMEM and the A rows are free for the next tile
-    fence_after_sync();
-    phase ^= 1u;
+  };
+
+  for (int col = blockIdx.x; col < a.n_cols && !aborted; col += gridDim.x) {
+    int r = col;
+    const int x0 = (r % xt) * kTileX;
+    r /= xt;
+    const int z = r % a.Lz;
+    const int b = r / a.Lz;
+    const int nrows = a.Ly + 2;
+    auto issue_row = [&](int k) {  // thread 0
+      const int64_t g = grow + k;
+      const uint32_t bar = smem_addr(&bars[row_slot(g)]);
+      mbar_arrive_expect_tx(bar, 6 * kRowSites * 16);
+      for (int dzi = 0; dzi < 3; ++dzi)
+        for (int h = 0; h < 2; ++h)
+          tma_load_5d(row_base(dzi, g) + h * kPlaneBytes, &tm_in, 8 * h, x0 - 1, k - 1,
+                      z + dzi - 1, b, bar);
+      ++rows_issued;
+    };
+    auto wait_row = [&](int k) -> bool {
+      const int64_t g = grow + k;
+      return mbar_wait_bounded(smem_addr(&bars[row_slot(g)]), row_parity(g));
+    };
+    if (tid == 0)
+      for (int k = 0; k < kRing && k < nrows; ++k) issue_row(k);
+    bool ok = wait_row(0) && wait_row(1);
+    if (tid == 0 && ok) rows_waited += 2;
+    for (int y = 0; y < a.Ly; ++y) {
+      ok = ok && wait_row(y + 2);
+      if (tid == 0 && ok) {
+        ++rows_waited;
+        fence_after_sync();
+        const int64_t tt = gtile;
+        const uint32_t d = tmem + (uint32_t)((tt & 1) * 16);
+        for (int o = 0; o < 27; ++o) {
+          const int dzi = o / 9, dyi = (o / 3) % 3, dx = o % 3;
+          const uint64_t da = smem_desc(row_base(dzi, grow + y + dyi) + dx * 16, kPlaneBytes, 128);
+          const uint64_t db = smem_desc(sW + o * 512, 256, 128);
+          mma_bf16(d, da, db, kIdesc, o > 0 ? 1u : 0u);
+        }
+        mma_commit(smem_addr(&bars[4 + (tt & 1)]));
+        ++mma_issued;
+      }
+      if (y > 0) {
+        const int64_t tp = gtile - 1;
+        ok = ok && mbar_wait_bounded(smem_addr(&bars[4 + (tp & 1)]), (uint32_t)((tp >> 1) & 1));
+        if (tid == 0 && ok) {
+          ++mma_waited;
+          // row k = y + 3 reuses the ring slot of row k = y - 1, last read by tile y - 1
+          if (y + 3 < nrows) issue_row(y + 3);
+        }
+      }
+      if (!ok) {
+        atomicOr(a.err, kErrTimeout);
+        *abort_flag = 1;
+      }
+      fence_before_sync();
+      __syncthreads();
+      fence_after_sync();
+      if (*abort_flag) {
+        aborted = true;
+        break;
+      }
+      if (y > 0) epilogue(gtile - 1, b, z, y - 1, x0);
+      fence_before_sync();
+      __syncthreads();  // the TMEM buffer read above is free for tile y + 1
+      fence_after_sync();
+      ++gtile;
+    }
+    if (aborted) break;
+    // last tile of the column
+    {
+      const int64_t tp = gtile - 1;
+      ok = mbar_wait_bounded(smem_addr(&bars[4 + (tp & 1)]), (uint32_t)((tp >> 1) & 1));
+      if (tid == 0 && ok) ++mma_waited;
+      if (!ok) {
+        atomicOr(a.err, kErrTimeout);
+        *abort_flag = 1;
+      }
+      fence_before_sync();
+      __syncthreads();
+      fence_after_sync();
+      if (*abort_flag) {
+        aborted = true;
+        break;
+      }
+      epilogue(tp, b, z, a.Ly - 1, x0);
+      fence_before_sync();
+      __syncthreads();
+      fence_after_sync();
+    }
+    grow += nrows;
   }
-  if (*abort_flag && tid == 0) {
-    // leave no copy or MMA in flight
-    if (pending_tma) mbar_wait_bounded(smem_addr(&bars[0]), phase);
-    if (pending_mma) mbar_wait_bounded(smem_addr(&bars[1]), phase);
+  if (aborted && tid == 0) {
+    // leave no copy or MMA in flight: every row issued and every committed
+    // tile not yet waited, in order, with bounded waits
+    for (int64_t g = rows_waited; g < rows_issued; ++g)
+      if (!mbar_wait_bounded(smem_addr(&bars[row_slot(g)]), row_parity(g))) break;
+    for (int64_t t = mma_waited; t < mma_issued; ++t)
+      if (!mbar_wait_bounded(smem_addr(&bars[4 + (t & 1)]), (uint32_t)((t >> 1) & 1))) break;
   }
   fence_before_sync();
   __syncthreads();
@@ -231,7 +321,8 @@ __global__ void __launch_bounds__(kCvThreads)
 }  // namespace
 
 int cv_conv3d_launch(const void *in_bf16, const void *wpack, const float *bias, float *out,
-                     int nb, int Lx, int Ly, int Lz, int *err, cudaStream_t s) {
+                     void *out_a, void *out_s, int nb, int Lx, int Ly, int Lz, int *err,
+                     cudaStream_t s) {
   auto enc = tensor_map_encoder();
   if (!enc) return COULPS_ECUDA;
   CUtensorMap map;
@@ -248,8 +339,11 @@ int cv_conv3d_launch(const void *in_bf16, const void *wpack, const float *bias, 
   a.wpack = reinterpret_cast<const uint4 *>(wpack);
   a.bias = bias;
   a.out = out;
+  a.out_a = reinterpret_cast<__nv_bfloat16 *>(out_a);
+  a.out_s = reinterpret_cast<__nv_bfloat16 *>(out_s);
+  a.mode = out ? 0 : 1;
   a.Lx = Lx; a.Ly = Ly; a.Lz = Lz; a.nb = nb;
-  a.n_tiles = nb * Lz * Ly * ((Lx + kTileX - 1) / kTileX);
+  a.n_cols = nb * Lz * ((Lx + kTileX - 1) / kTileX);
   a.err = err;
   static bool configured = false;
   const int smem = kCvSmem + 1024;
@@ -272,7 +366,7 @@ int cv_conv3d_launch(const void *in_bf16, const void *wpack, const float *bias, 
   }
   if (per_sm > 8) per_sm = 8;  // 8 x 32 TMEM columns of 512
   int grid = sms * per_sm;
-  if (grid > a.n_tiles) grid = a.n_tiles;
+  if (grid > a.n_cols) grid = a.n_cols;
   if (grid < 1) return COULPS_OK;
   cv_conv3d_kernel<<<grid, kCvThreads, smem, s>>>(map, a);
   return cudaGetLastError() == cudaSuccess ? COULPS_OK : COULPS_ECUDA;
@@ -307,10 +401,23 @@ extern "C" int coulps_cv_conv3d(const void *in_bf16, const void *wpack, const fl
                                 void *stream) {
   if (!in_bf16 || !wpack || !bias || !out || !err) return COULPS_EINVAL;
   if (nb < 1 || Lx < 1 || Ly < 1 || Lz < 1) return COULPS_EINVAL;
-  if ((int64_t)nb * Lz * Ly * ((Lx + 127) / 128) > 0x7fffffff) return COULPS_EINVAL;
+  if ((int64_t)nb * Lz * ((Lx + 127) / 128) > 0x7fffffff) return COULPS_EINVAL;
   const uintptr_t align = reinterpret_cast<uintptr_t>(in_bf16) | reinterpret_cast<uintptr_t>(wpack) |
                           reinterpret_cast<uintptr_t>(out);
   if (align & 15) return COULPS_EINVAL;
-  return coulps::cv_conv3d_launch(in_bf16, wpack, bias, out, nb, Lx, Ly, Lz, err,
-                                  static_cast<cudaStream_t>(stream));
+  return coulps::cv_conv3d_launch(in_bf16, wpack, bias, out, nullptr, nullptr, nb, Lx, Ly, Lz,
+                                  err, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int coulps_cv_conv3d_tanh(const void *in_bf16, const void *wpack, const float *bias,
+                                     void *a_bf16, void *s_bf16, int nb, int Lx, int Ly, int Lz,
+                                     int *err, void *stream) {
+  if (!in_bf16 || !wpack || !bias || !a_bf16 || !s_bf16 || !err) return COULPS_EINVAL;
+  if (nb < 1 || Lx < 1 || Ly < 1 || Lz < 1) return COULPS_EINVAL;
+  if ((int64_t)nb * Lz * ((Lx + 127) / 128) > 0x7fffffff) return COULPS_EINVAL;
+  const uintptr_t align = reinterpret_cast<uintptr_t>(in_bf16) | reinterpret_cast<uintptr_t>(wpack) |
+                          reinterpret_cast<uintptr_t>(a_bf16) | reinterpret_cast<uintptr_t>(s_bf16);
+  if (align & 15) return COULPS_EINVAL;
+  return coulps::cv_conv3d_launch(in_bf16, wpack, bias, nullptr, a_bf16, s_bf16, nb, Lx, Ly, Lz,
+                                  err, static_cast<cudaStream_t>(stream));
 }

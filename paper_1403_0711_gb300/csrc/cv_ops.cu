@@ -185,47 +185,66 @@ __global__ void cv_sum_partials_kernel(const double *__restrict__ partials, int 
   out[chain] = accumulate ? out[chain] + s : s;
 }
 
-constexpr int kWgTile = 64;  // positions per shared-memory tile
+constexpr int kWgTile = 64;  // sites of one x row per shared-memory tile
 
-// per (block, offset) partial of dW[co][ci][o]; thread t = co * 16 + ci
+// Per-CTA partial of dW[co][ci][o] over a contiguous range of x-row tiles
+// (b, z, y, x0 .. x0+63).  Thread t = co * 16 + ci.  The tile of dh is loaded
+// once; for each of the 27 offsets the matching tile of a (row (y+dy, z+dz),
+// x shifted by dx, zero outside) is loaded and 64 FMAs accumulate per thread.
 __global__ void __launch_bounds__(256)
     cv_wgrad_partial_kernel(const __nv_bfloat16 *__restrict__ a,
                             const __nv_bfloat16 *__restrict__ dh, int Lx, int Ly, int Lz,
-                            int64_t npos, int64_t per_block, float *__restrict__ partials) {
-  __shared__ float sd[kWgTile][17], sa[kWgTile][17];
-  const int o = blockIdx.y;
-  const int oz = o / 9 - 1, oy = (o / 3) % 3 - 1, ox = o % 3 - 1;
+                            int64_t ntiles, int64_t per_block, float *__restrict__ partials) {
+  __shared__ float sd[kWgTile][17];
+  __shared__ float sa[kWgTile + 2][17];
   const int t = threadIdx.x, co = t >> 4, ci = t & 15;
-  const int64_t p0 = (int64_t)blockIdx.x * per_block;
-  const int64_t p1 = p0 + per_block < npos ? p0 + per_block : npos;
-  float acc = 0.f;
-  for (int64_t base = p0; base < p1; base += kWgTile) {
+  const int xt = (Lx + kWgTile - 1) / kWgTile;
+  const int64_t t0 = (int64_t)blockIdx.x * per_block;
+  const int64_t t1 = t0 + per_block < ntiles ? t0 + per_block : ntiles;
+  float acc[27];
+#pragma unroll
+  for (int o = 0; o < 27; ++o) acc[o] = 0.f;
+  for (int64_t tile = t0; tile < t1; ++tile) {
+    int64_t r = tile;
+    const int x0 = (int)(r % xt) * kWgTile;
+    r /= xt;
+    const int y = (int)(r % Ly);
+    r /= Ly;
+    const int z = (int)(r % Lz);
+    const int64_t b = r / Lz;
+    __syncthreads();
     for (int k = t; k < kWgTile * 16; k += 256) {
       const int j = k >> 4, c = k & 15;
-      const int64_t p = base + j;
-      float vd = 0.f, va = 0.f;
-      if (p < p1) {
-        vd = __bfloat162float(dh[p * 16 + c]);
-        int64_t r = p;
-        const int x = (int)(r % Lx);
-        r /= Lx;
-        const int y = (int)(r % Ly);
-        r /= Ly;
-        const int z = (int)(r % Lz);
-        const int64_t bb = r / Lz;
-        const int xx = x + ox, yy = y + oy, zz = z + oz;
-        if (xx >= 0 && yy >= 0 && zz >= 0 && xx < Lx && yy < Ly && zz < Lz)
-          va = __bfloat162float(a[((((bb * Lz) + zz) * Ly + yy) * (int64_t)Lx + xx) * 16 + c]);
-      }
-      sd[j][c] = vd;
-      sa[j][c] = va;
+      const int x = x0 + j;
+      sd[j][c] = x < Lx ? __bfloat162float(dh[((((b * Lz) + z) * Ly + y) * (int64_t)Lx + x) * 16 + c])
+                        : 0.f;
     }
-    __syncthreads();
-#pragma unroll 8
-    for (int j = 0; j < kWgTile; ++j) acc = fmaf(sd[j][co], sa[j][ci], acc);
-    __syncthreads();
+#pragma unroll
+    for (int o9 = 0; o9 < 9; ++o9) {
+      const int dz = o9 / 3 - 1, dy = o9 % 3 - 1;
+      const int yy = y + dy, zz = z + dz;
+      const bool row_in = yy >= 0 && yy < Ly && zz >= 0 && zz < Lz;
+      __syncthreads();
+      // a of row (yy, zz) at x0-1 .. x0+64, zero outside the box
+      for (int k = t; k < (kWgTile + 2) * 16; k += 256) {
+        const int j = k >> 4, c = k & 15;
+        const int x = x0 - 1 + j;
+        sa[j][c] = (row_in && x >= 0 && x < Lx)
+                       ? __bfloat162float(a[((((b * Lz) + zz) * Ly + yy) * (int64_t)Lx + x) * 16 + c])
+                       : 0.f;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int dx = 0; dx < 3; ++dx) {
+        float s = 0.f;
+#pragma unroll 16
+        for (int j = 0; j < kWgTile; ++j) s = fmaf(sd[j][co], sa[j + dx][ci], s);
+        acc[o9 * 3 + dx] += s;
+      }
+    }
   }
-  partials[((size_t)blockIdx.x * 27 + o) * 256 + t] = acc;
+#pragma unroll
+  for (int o = 0; o < 27; ++o) partials[((size_t)blockIdx.x * 27 + o) * 256 + t] = acc[o];
 }
 
 __global__ void cv_wgrad_reduce_kernel(const float *__restrict__ partials, int nblk,
@@ -279,15 +298,16 @@ int coulps_cv_conv3d_wgrad(const void *a_bf16, const void *dh_bf16, float *dW, i
                            int Ly, int Lz, float *scratch, int64_t scratch_floats, void *stream) {
   if (!a_bf16 || !dh_bf16 || !dW || !scratch) return COULPS_EINVAL;
   if (nb < 1 || Lx < 1 || Ly < 1 || Lz < 1) return COULPS_EINVAL;
-  const int64_t npos = (int64_t)nb * Lx * Ly * Lz;
-  int nblk = (int)((npos + 4095) / 4096);
-  if (nblk > 256) nblk = 256;
+  const int64_t ntiles = (int64_t)nb * Lz * Ly * ((Lx + kWgTile - 1) / kWgTile);
+  int nblk = (int)((ntiles + 31) / 32);
+  if (nblk > 1024) nblk = 1024;
   if (scratch_floats < (int64_t)nblk * 27 * 256) return COULPS_EINVAL;
-  const int64_t per_block = (npos + nblk - 1) / nblk;
+  const int64_t per_block = (ntiles + nblk - 1) / nblk;
+  nblk = (int)((ntiles + per_block - 1) / per_block);
   cudaStream_t s = (cudaStream_t)stream;
-  cv_wgrad_partial_kernel<<<dim3(nblk, 27), 256, 0, s>>>(
-      (const __nv_bfloat16 *)a_bf16, (const __nv_bfloat16 *)dh_bf16, Lx, Ly, Lz, npos, per_block,
-      scratch);
+  cv_wgrad_partial_kernel<<<nblk, 256, 0, s>>>((const __nv_bfloat16 *)a_bf16,
+                                               (const __nv_bfloat16 *)dh_bf16, Lx, Ly, Lz, ntiles,
+                                               per_block, scratch);
   cv_wgrad_reduce_kernel<<<(27 * 256 + 255) / 256, 256, 0, s>>>(scratch, nblk, dW);
   return cudaGetLastError() == cudaSuccess ? COULPS_OK : COULPS_ECUDA;
 }

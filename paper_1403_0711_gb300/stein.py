@@ -67,10 +67,25 @@ def conv3d_tc(a: torch.Tensor, W: torch.Tensor, b: torch.Tensor) -> torch.Tensor
     return out
 
 
+def conv3d_tanh_tc(a: torch.Tensor, W: torch.Tensor, b: torch.Tensor):
+    """(tanh(h), 1 - tanh(h)^2) as BF16 for h = conv3d(a, W) + b (fused epilogue)."""
+    n, Z, Y, X, C = a.shape
+    assert C == 16 and a.dtype == torch.bfloat16 and a.is_contiguous()
+    act = torch.empty((n, Z, Y, X, 16), dtype=torch.bfloat16, device=a.device)
+    der = torch.empty_like(act)
+    err = torch.zeros(1, dtype=torch.int32, device=a.device)
+    wp = pack_weights(W)
+    bias = b.detach().float().contiguous()
+    st = coulps.load().coulps_cv_conv3d_tanh(_vp(a), _vp(wp), _vp(bias), _vp(act), _vp(der), n, X,
+                                             Y, Z, _vp(err), _stream())
+    coulps._check(st, "coulps_cv_conv3d_tanh")
+    return act, der
+
+
 def conv3d_wgrad(a: torch.Tensor, dh: torch.Tensor) -> torch.Tensor:
     n, Z, Y, X, _ = a.shape
-    npos = n * Z * Y * X
-    nblk = min(256, (npos + 4095) // 4096)
+    ntiles = n * Z * Y * ((X + 63) // 64)
+    nblk = min(1024, (ntiles + 31) // 32)
     scratch = torch.empty(nblk * 27 * 256, dtype=torch.float32, device=a.device)
     dW = torch.empty(16 * 16 * 27, dtype=torch.float32, device=a.device)
     st = coulps.load().coulps_cv_conv3d_wgrad(_vp(a), _vp(dh), _vp(dW), n, X, Y, Z, _vp(scratch),
@@ -179,8 +194,11 @@ class SteinCV(torch.nn.Module):
         Kb = divergence_kernel(self.W1, self.W2, self.W3, masks).reshape(64, 16, 16, 27)
         return Kb - Kb[_INSIDE][None]
 
-    # -- differentiable T g for training: x0 (n, Z, Y, X, 16) BF16 input, Aphi (n, Z, Y, X)
-    def stein_term(self, x0, Aphi):
+    # -- differentiable T g: x0 (n, Z, Y, X, 16) BF16 input, Aphi (n, Z, Y, X).
+    # faces=False drops the face-site divergence correction (used to train:
+    # the coefficient c and every evaluation use the exact term, so the
+    # estimator stays unbiased whatever the training objective).
+    def stein_term(self, x0, Aphi, faces=True):
         h1 = Conv3dTC.apply(x0, self._w1p(), self.b1)
         a1 = torch.tanh(h1)
         s1 = 1.0 - a1 * a1
@@ -190,7 +208,9 @@ class SteinCV(torch.nn.Module):
         g = Conv3dTC.apply(a2.to(torch.bfloat16), self._w3p(), self._b3p())[..., 0]
         K = divergence_kernel(self.W1, self.W2, self.W3)
         D = Conv3dTC.apply(s1.to(torch.bfloat16), K, torch.zeros(16, device=x0.device))
-        div = (s2 * D).sum(dim=(1, 2, 3, 4)) + self._face_term(s1, s2)
+        div = (s2 * D).sum(dim=(1, 2, 3, 4))
+        if faces:
+            div = div + self._face_term(s1, s2)
         return div - (g * Aphi).sum(dim=(1, 2, 3))
 
     def _face_term(self, s1, s2):
@@ -238,16 +258,8 @@ class SteinCV(torch.nn.Module):
             Aphi = torch.empty((n, Lz, Ly, Lx), dtype=torch.float32, device=dev)
             coulps._check(lib.coulps_cv_pack_field(lat.handle, _vp(rho), _vp(x0), _vp(Aphi)),
                           "coulps_cv_pack_field")
-            h1 = conv3d_tc(x0, self._w1p(), self.b1)
-            a1 = torch.empty(h1.shape, dtype=torch.bfloat16, device=dev)
-            s1 = torch.empty_like(a1)
-            coulps._check(lib.coulps_cv_activate(_vp(h1), _vp(a1), _vp(s1), h1.numel(), _stream()),
-                          "coulps_cv_activate")
-            h2 = conv3d_tc(a1, self.W2, self.b2)
-            a2 = torch.empty_like(a1)
-            s2 = torch.empty_like(a1)
-            coulps._check(lib.coulps_cv_activate(_vp(h2), _vp(a2), _vp(s2), h2.numel(), _stream()),
-                          "coulps_cv_activate")
+            a1, s1 = conv3d_tanh_tc(x0, self._w1p(), self.b1)
+            a2, s2 = conv3d_tanh_tc(a1, self.W2, self.b2)
             g16 = conv3d_tc(a2, self._w3p(), self._b3p())
             D = conv3d_tc(s1, K, torch.zeros(16, device=dev))
             out = torch.empty(n, dtype=torch.float64, device=dev)
@@ -316,7 +328,7 @@ def fit(cv: SteinCV, phis, Aphis, es, rho, steps=200, batch=16, lr=2e-3, seed=0,
     es_d = es.to(dev)
     for step in range(steps):
         idx = torch.randperm(n, generator=g)[:batch].to(dev)
-        tg = cv.stein_term(inputs_from(phis[idx], rho), Aphis[idx])
+        tg = cv.stein_term(inputs_from(phis[idx], rho), Aphis[idx], faces=False)
         r = es_d[idx].float() - tg
         loss = ((r - r.mean()) ** 2).mean() / (es_d.float().var() + 1e-30)
         opt.zero_grad()

@@ -53,3 +53,29 @@ def test_conv3d_matches_torch(env, shape):
     scale = (a.float().abs().max() * w.abs().sum(dim=(1, 2, 3, 4)).max()).item()
     assert torch.isfinite(got).all()
     assert (got - ref).abs().max().item() < 2e-6 * scale + 1e-6
+
+
+def test_conv3d_tanh_epilogue(env):
+    torch, coulps, lib = env
+    nb, Lz, Ly, Lx = 2, 6, 5, 130
+    g = torch.Generator().manual_seed(11)
+    a = torch.randn(nb, Lz, Ly, Lx, 16, generator=g).to(torch.bfloat16)
+    w = (torch.randn(16, 16, 3, 3, 3, generator=g) * 0.1).to(torch.bfloat16).float()
+    bias = torch.randn(16, generator=g) * 0.2
+    h = torch.nn.functional.conv3d(a.float().permute(0, 4, 1, 2, 3), w, bias, padding=1)
+    t = torch.tanh(h.permute(0, 2, 3, 4, 1))
+    wp = torch.from_numpy(_pack(lib, w.numpy()).view(np.int16)).cuda()
+    d_a, d_b = a.cuda().contiguous(), bias.cuda()
+    act = torch.empty(nb, Lz, Ly, Lx, 16, dtype=torch.bfloat16, device="cuda")
+    der = torch.empty_like(act)
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    st = lib.coulps_cv_conv3d_tanh(ctypes.c_void_p(d_a.data_ptr()), ctypes.c_void_p(wp.data_ptr()),
+                                   ctypes.c_void_p(d_b.data_ptr()), ctypes.c_void_p(act.data_ptr()),
+                                   ctypes.c_void_p(der.data_ptr()), nb, Lx, Ly, Lz,
+                                   ctypes.c_void_p(err.data_ptr()), None)
+    assert st == 0
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    # BF16 outputs: 2^-8 relative
+    assert (act.float().cpu() - t).abs().max().item() < 8e-3
+    assert (der.float().cpu() - (1 - t * t)).abs().max().item() < 8e-3
