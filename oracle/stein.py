@@ -68,11 +68,24 @@ def forward(phi, rho, p):
     return {"h1": h1, "a1": a1, "h2": h2, "a2": a2, "g": g}
 
 
-def divergence(phi, rho, p):
-    """sum_x dg_x/dphi_x by the chain rule (positions outside the box absent)."""
+def region_mask(shape, region):
+    """1 inside region = ((z0, z1), (y0, y1), (x0, x1)) (half-open), else 0."""
+    m = np.zeros(shape)
+    if region is None:
+        m[...] = 1.0
+        return m
+    (z0, z1), (y0, y1), (x0, x1) = region
+    m[z0:z1, y0:y1, x0:x1] = 1.0
+    return m
+
+
+def divergence(phi, rho, p, region=None):
+    """sum_x dg_x/dphi_x by the chain rule (positions outside the box absent);
+    with a region, only x inside it (g is taken as 0 elsewhere)."""
     f = forward(phi, rho, p)
     s1, s2 = 1.0 - f["a1"] ** 2, 1.0 - f["a2"] ** 2
     W1, W2, W3 = p["W1"], p["W2"], p["W3"]
+    mask = region_mask(phi.shape, region)[None]
     total = 0.0
     for fo in OFFS:
         s2f = _shift(s2, fo)  # s2[c2, x+f] (0 outside)
@@ -86,7 +99,7 @@ def divergence(phi, rho, p):
             # s1 at x+f+e, defined only where x+f is inside (s2f carries that)
             s1fe = _shift(_shift(s1, eo), fo)
             inner = np.tensordot(w2 * w1[None, :], s1fe, axes=(1, 0))  # (c2, Z, Y, X)
-            total += float(np.sum(w3[:, None, None, None] * s2f * inner))
+            total += float(np.sum(w3[:, None, None, None] * s2f * inner * mask))
     return total
 
 
@@ -101,10 +114,11 @@ def apply_A(phi):
     return out
 
 
-def stein_term(phi, rho, p):
-    """T g = sum_x (dg_x/dphi_x - g_x (A phi)_x)."""
-    g = forward(phi, rho, p)["g"]
-    return divergence(phi, rho, p) - float(np.sum(g * apply_A(phi)))
+def stein_term(phi, rho, p, region=None):
+    """T g = sum_x (dg_x/dphi_x - g_x (A phi)_x); with a region, g is the net
+    inside it and 0 outside (still a smooth field, so E[T g] = 0)."""
+    g = forward(phi, rho, p)["g"] * region_mask(phi.shape, region)
+    return divergence(phi, rho, p, region) - float(np.sum(g * apply_A(phi)))
 
 
 def random_params(seed, scale=0.3):

@@ -57,3 +57,26 @@ def test_stein_term_has_zero_mean_under_exact_samples(orc):
     # each part alone has a clearly non-zero mean
     d = np.array(div_only)
     assert abs(d.mean()) > 8 * d.std(ddof=1) / math.sqrt(n)
+
+
+def test_region_divergence_matches_finite_differences():
+    """g restricted to a region (zero outside): the divergence sums over the
+    region only and still equals finite differences of the masked g."""
+    from oracle import stein
+    rng = np.random.default_rng(2)
+    Z, Y, X = 5, 6, 7
+    phi = rng.standard_normal((Z, Y, X))
+    rho = np.zeros((Z, Y, X))
+    rho[2, 3, 3] = 1.0
+    p = stein.random_params(4)
+    region = ((1, 4), (2, 5), (0, 3))
+    m = stein.region_mask(phi.shape, region)
+    div = stein.divergence(phi, rho, p, region)
+    h = 1e-5
+    fd = 0.0
+    for z, y, x in zip(*np.nonzero(m)):
+        a, b = phi.copy(), phi.copy()
+        a[z, y, x] += h
+        b[z, y, x] -= h
+        fd += (stein.forward(a, rho, p)["g"][z, y, x] - stein.forward(b, rho, p)["g"][z, y, x]) / (2 * h)
+    assert abs(div - fd) < 1e-7 * max(1.0, abs(div))
