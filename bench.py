@@ -62,6 +62,12 @@ def parse():
     ap.add_argument("--cv-steps", type=int, default=300)
     ap.add_argument("--cv-rounds", type=int, default=64)
     ap.add_argument("--cube-seconds", type=float, default=600.0)
+    ap.add_argument("--cv-halo", type=int, default=3,
+                    help="the localized control variate's g lives within this many sites of the charges")
+    ap.add_argument("--cv-collect", type=int, default=64,
+                    help="training rounds (every chain contributes one sample per round)")
+    ap.add_argument("--cv-global", action="store_true",
+                    help="also run the whole-lattice control variate on the +-1 system")
     ap.add_argument("--workload", choices=["chains128", "large512", "sweep", "batched", "cv", "cube"],
                     default="chains128", help="secondary workloads print their own line")
     ap.add_argument("--chains", type=int, default=N_CHAINS,
@@ -452,9 +458,112 @@ def run_extra(args):
 
 
 def cv_experiment(args, stream):
-    """Learned Stein control variate on the 128^3 lattice: train on 2048 of the
-    chains' own samples, then compare plain and CV estimators on fresh samples.
-    Runs on the +-1 zero-net N=4096 system and on the paper's q=1 cube (N=8)."""
+    out = [cv_local_cube(args, stream)]
+    if args.cv_global:
+        out.extend(cv_global(args, stream))
+    return out
+
+
+def cv_local_cube(args, stream):
+    """Localized learned Stein control variate on the paper's Fig. 2 geometry
+    (N = 8 charges q = 1 in a cube at the centre of a 128^3 box): g is the net
+    within --cv-halo sites of the charges, evaluated on that sub-box only.
+    Train on the chains' own samples, then sample with the CV recorded on the
+    device every compound sweep until its batch-means error reaches
+    1e-3 |E_lat| (or --cube-seconds), and compare with the plain estimator of
+    the same samples (its time to 1e-3 projected from its error and its own
+    cost per sweep)."""
+    import numpy as np
+    import torch
+
+    from paper_1403_0711_gb300 import coulps, inputs, stein
+    box = (L, L, L)
+    sites, q = inputs.cube(box, 2)
+    e_lat = golden_e_lat("cube_128c_n8_q1")
+    target = 1e-3 * abs(e_lat)
+    lat = coulps.Lattice(box, n_chains=N_CHAINS, precision=coulps.F32, seed=4243, stream=stream)
+    ch = coulps.Charges(lat, sites, q)
+    rho = stein.charge_density(box, sites, q)
+    lo = sites.min(axis=0) - args.cv_halo
+    hi = sites.max(axis=0) + 1 + args.cv_halo
+    cv = stein.LocalSteinCV(box, lo, hi, seed=0, scale=0.3)
+    lat.sweep(300, N_HB, N_OR)
+    lat.sync()
+    t0 = time.perf_counter()
+    phis, Aphis, es = stein.collect_region(cv, lat, ch, rho, n_rounds=args.cv_collect, every=2,
+                                           n_hb=N_HB, n_or=N_OR)
+    t_collect = time.perf_counter() - t0
+    log = []
+    t0 = time.perf_counter()
+    tg_fit = stein.fit_region(cv, phis, Aphis, es, rho, steps=args.cv_steps, batch=128, lr=3e-3,
+                              log=log)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    n_tr = int(len(es) * 0.75)
+    e_ho, t_ho = es[n_tr:].numpy(), tg_fit[n_tr:].cpu().numpy()
+    ratio_holdout = float(np.var(e_ho - cv.c * t_ho) / np.var(e_ho))
+    del phis, Aphis
+    # cost of one compound sweep with and without the CV, on the device
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    tg = torch.empty(N_CHAINS, dtype=torch.float64, device="cuda")
+    ms_plain = ms_cv = 0.0
+    for r in range(20):
+        ev[0].record(stream)
+        ch.run(0, 1, N_HB, N_OR)
+        ev[1].record(stream)
+        cv.evaluate(lat, rho, out=tg)
+        ch.cv_record(tg.data_ptr(), cv.c)
+        ev[2].record(stream)
+        stream.synchronize()
+        if r >= 5:
+            ms_plain += ev[0].elapsed_time(ev[1]) / 15
+            ms_cv += ev[1].elapsed_time(ev[2]) / 15
+    ch.reset_stats()
+    ch.cv_reset()
+    lat.sync()
+    t0 = time.perf_counter()
+    rounds = 0
+    cvest = None
+    while time.perf_counter() - t0 < args.cube_seconds:
+        for _ in range(250):
+            ch.run(0, 1, N_HB, N_OR)
+            cv.evaluate(lat, rho, out=tg)
+            ch.cv_record(tg.data_ptr(), cv.c)
+        rounds += 250
+        cvest = ch.cv_estimate()
+        if cvest["stderr"] == cvest["stderr"] and cvest["stderr"] <= target and rounds >= 2000:
+            break
+    wall = time.perf_counter() - t0
+    plain = ch.estimate()
+    # the plain estimator alone: same samples at its own (lower) cost per sweep
+    plain_wall_same = rounds * ms_plain / 1e3
+    t_plain_proj = plain_wall_same * (plain["stderr"] / target) ** 2
+    r = {"system": "cube8_q1_local_cv", "e_lat": e_lat, "halo": args.cv_halo,
+         "region_lo": [int(v) for v in lo], "region_hi": [int(v) for v in hi],
+         "eval_box": list(cv.edims), "training_samples": int(len(es)), "collect_s": t_collect,
+         "train_s": t_train, "train_steps": args.cv_steps,
+         "loss_first20": float(np.mean(log[:20])), "loss_last20": float(np.mean(log[-20:])),
+         "c": cv.c, "variance_ratio_holdout": ratio_holdout,
+         "ms_compound_sweep": ms_plain, "ms_cv_eval": ms_cv,
+         "rounds": rounds, "samples": cvest["n"], "wall_s_cv": wall,
+         "mean_cv": cvest["mean"], "stderr_cv": cvest["stderr"], "tau_int_cv": cvest["tau_int"],
+         "mean_plain": plain["mean"], "stderr_plain": plain["stderr"],
+         "tau_int_plain": plain["tau_int"],
+         "variance_ratio": (cvest["stderr"] / plain["stderr"]) ** 2,
+         "delta_cv": abs(cvest["mean"] - e_lat) / abs(e_lat),
+         "reached_1e-3_cv": bool(cvest["stderr"] <= target),
+         "s_to_1e-3_cv_incl_training": wall + t_collect + t_train,
+         "projected_s_to_1e-3_plain": t_plain_proj}
+    ch.close()
+    lat.close()
+    torch.cuda.empty_cache()
+    return r
+
+
+def cv_global(args, stream):
+    """Whole-lattice learned Stein control variate on the 128^3 lattice: train on
+    2048 of the chains' own samples, then compare plain and CV estimators on
+    fresh samples.  Runs on the +-1 zero-net N=4096 system."""
     import numpy as np
     import torch
 
@@ -462,8 +571,7 @@ def cv_experiment(args, stream):
     out = []
     box = (L, L, L)
     for name, (sites, q), gold in (
-            ("pm4096", inputs.plus_minus(box, N_CHARGES, seed=1), "bench_128c_n4096_pm"),
-            ("cube8", inputs.cube(box, 2), "cube_128c_n8_q1")):
+            ("pm4096", inputs.plus_minus(box, N_CHARGES, seed=1), "bench_128c_n4096_pm"),):
         lat = coulps.Lattice(box, n_chains=N_CHAINS, precision=coulps.F32, seed=4242, stream=stream)
         ch = coulps.Charges(lat, sites, q, log_capacity=4096)
         rho = stein.charge_density(box, sites, q)

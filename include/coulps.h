@@ -177,7 +177,8 @@ int coulps_charges_update(coulps_charges_t ch, const int32_t *site_xyz, const do
 /* Per-chain estimator state, COULPS_STAT_STRIDE doubles per chain:
  *   [0] samples n, [1] sum e, [2] sum e^2, [3] open batch sum, [4] open batch
  *   count, [5] batch length b, [6] completed batches m (32 <= m < 64 once
- *   n >= 32 b), [7] unused, [8 + j] sum of e over completed batch j.
+ *   n >= 32 b), [7] the most recent sample e, [8 + j] sum of e over completed
+ *   batch j.
  * coulps_chain_stats synchronises and copies n_chains rows into out (cap =
  * doubles available).  coulps_pool_stats is pure host arithmetic: it pools
  * any number of such rows (for example gathered from several processes, each
@@ -319,6 +320,13 @@ int coulps_cv_conv3d_wgrad(const void *a_bf16, const void *dh_bf16, float *dW, i
  * coulps_cv_activate: a = tanh(h), s = 1 - a^2 (BF16) for n floats h. */
 int coulps_cv_pack_field(coulps_lattice_t lat, const float *rho, void *act_bf16, float *Aphi);
 int coulps_cv_activate(const float *h, void *a_bf16, void *s_bf16, int64_t n, void *stream);
+/* coulps_cv_pack_region: the same for the sub-box E = [origin, origin + dims)
+ * (x, y, z order) of every chain, act[chain][ez][ey][ex][16] and
+ * Aphi[chain][ez][ey][ex] in E's own coordinates; A phi is taken from the full
+ * field (neighbours outside E but inside the box count).  rho is the full
+ * box's density.  Errors: EINVAL (E not inside the box), EUNSUPPORTED (FP64). */
+int coulps_cv_pack_region(coulps_lattice_t lat, const float *rho, const int32_t *origin,
+                          const int32_t *dims, void *act_bf16, float *Aphi);
 
 /* coulps_cv_stein_sum: per chain b, the Stein term of the net,
  *   out[b] = sum_x (dg_x/dphi_x - g_x (A phi)_x)
@@ -333,6 +341,40 @@ int coulps_cv_activate(const float *h, void *a_bf16, void *s_bf16, int64_t n, vo
 int coulps_cv_stein_sum(const float *g16, const float *D, const void *s2_bf16, const float *Aphi,
                         const void *s1_bf16, const float *dK, int nb, int Lx, int Ly, int Lz,
                         double *scratch, int64_t scratch_doubles, double *out, void *stream);
+
+/* coulps_cv_stein_region: the Stein term of a net g that is kept inside the
+ * box R = [lo, hi) and set to 0 elsewhere (still a smooth field of phi, so the
+ * term keeps mean 0), evaluated on a sub-box E (edims = x, y, z sizes) that
+ * holds R and its 3-site halo, with R in E's coordinates:
+ *   out[b] = sum_{q in R+1} sum_c2 s2[c2, q] sum_{c1, e} K_q[c2][c1][e] s1[c1, q + e]
+ *            - sum_{x in R} g_x Aphi_x
+ * where K_q is the divergence kernel summed over the offsets f of the last
+ * layer with q - f inside R (per axis a subset of {-1, 0, 1}).  Ktab (device,
+ * 216 x 16 x 16 x 27 floats) holds one K per class ix + 6 iy + 36 iz, the
+ * per-axis index of the allowed set {-1} 0, {0} 1, {-1, 0} 2, {1} 3,
+ * {0, 1} 4, {-1, 0, 1} 5 (f = -1 is bit 0).  g16 [b][E][16] FP32 (channel 0
+ * read), s1, s2 BF16 [b][E][16], Aphi [b][E].  Sums in FP64, fixed order.
+ * scratch >= 64 * nb doubles; out device nb doubles.  Asynchronous.  Errors:
+ * EINVAL, ECUDA. */
+int coulps_cv_stein_region(const float *g16, const void *s1_bf16, const void *s2_bf16,
+                           const float *Aphi, const float *Ktab, int nb, const int32_t *edims,
+                           const int32_t *lo, const int32_t *hi, double *scratch,
+                           int64_t scratch_doubles, double *out, void *stream);
+
+/* Control-variate estimator, kept beside the plain one of a charge set:
+ * coulps_cv_record adds to chain b's CV statistics the sample
+ *   y_b = e_b - c * tg[b],
+ * e_b the chain's most recent Eq. (nsum2) sample (stat [7]) and tg device
+ * n_chains doubles (for example coulps_cv_stein_region's out).  Call it after
+ * each measurement whose field tg was computed from.  coulps_cv_chain_stats,
+ * coulps_cv_estimate and coulps_cv_reset mirror coulps_chain_stats,
+ * coulps_estimate and coulps_reset_stats for these samples (same layout, same
+ * pooling).  Checkpoints do not hold them.  Asynchronous except the readers. */
+int coulps_cv_record(coulps_charges_t ch, const double *tg, double c);
+int coulps_cv_chain_stats(coulps_charges_t ch, double *out, int64_t cap);
+int coulps_cv_estimate(coulps_charges_t ch, double *mean, double *stderr_bm, double *tau_int,
+                       int64_t *n);
+int coulps_cv_reset(coulps_charges_t ch);
 
 /* ---- allocation-free measurement --------------------------------------- */
 /* The paper has no counterpart to this entry point.  It serves callers that

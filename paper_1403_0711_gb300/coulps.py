@@ -37,7 +37,9 @@ EXPORTS = (
     "coulps_batch_run", "coulps_batch_sync", "coulps_batch_estimate", "coulps_batch_samples",
     "coulps_batch_field_get", "coulps_cv_pack_weights", "coulps_cv_conv3d",
     "coulps_cv_conv3d_wgrad", "coulps_cv_pack_field", "coulps_cv_activate", "coulps_cv_stein_sum",
-    "coulps_set_schedule", "coulps_cv_conv3d_tanh",
+    "coulps_set_schedule", "coulps_cv_conv3d_tanh", "coulps_cv_pack_region",
+    "coulps_cv_stein_region", "coulps_cv_record", "coulps_cv_chain_stats", "coulps_cv_estimate",
+    "coulps_cv_reset",
 )
 SCHEDULE_ALIGNED, SCHEDULE_PHASED = 0, 1
 STAT_STRIDE = 72
@@ -116,6 +118,13 @@ def load(path: str | Path | None = None):
         "coulps_cv_stein_sum": (i32, [vp, vp, vp, vp, vp, vp, i32, i32, i32, i32, vp, i64, vp, vp]),
         "coulps_set_schedule": (i32, [vp, i32]),
         "coulps_cv_conv3d_tanh": (i32, [vp, vp, vp, vp, vp, i32, i32, i32, i32, vp, vp]),
+        "coulps_cv_pack_region": (i32, [vp, vp, P(ctypes.c_int32), P(ctypes.c_int32), vp, vp]),
+        "coulps_cv_stein_region": (i32, [vp, vp, vp, vp, vp, i32, P(ctypes.c_int32),
+                                         P(ctypes.c_int32), P(ctypes.c_int32), vp, i64, vp, vp]),
+        "coulps_cv_record": (i32, [vp, vp, f64]),
+        "coulps_cv_chain_stats": (i32, [vp, P(f64), i64]),
+        "coulps_cv_estimate": (i32, [vp, P(f64), P(f64), P(f64), P(i64)]),
+        "coulps_cv_reset": (i32, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -316,6 +325,29 @@ class Charges:
         out = np.empty((nc, STAT_STRIDE), dtype=np.float64)
         _check(self._lib.coulps_chain_stats(self.handle, _f64p(out), out.size), "coulps_chain_stats")
         return out
+
+    # control-variate samples y = e - c * Tg, kept beside the plain ones
+    def cv_record(self, tg_ptr, c):
+        """Record y_b = e_b - c * tg[b] for every chain (tg: device doubles)."""
+        _check(self._lib.coulps_cv_record(self.handle, ctypes.c_void_p(tg_ptr), float(c)),
+               "coulps_cv_record")
+
+    def cv_estimate(self):
+        m, s, t = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        n = ctypes.c_int64()
+        _check(self._lib.coulps_cv_estimate(self.handle, ctypes.byref(m), ctypes.byref(s),
+                                            ctypes.byref(t), ctypes.byref(n)), "coulps_cv_estimate")
+        return {"mean": m.value, "stderr": s.value, "tau_int": t.value, "n": n.value}
+
+    def cv_chain_stats(self):
+        nc = self.lattice.n_chains
+        out = np.empty((nc, STAT_STRIDE), dtype=np.float64)
+        _check(self._lib.coulps_cv_chain_stats(self.handle, _f64p(out), out.size),
+               "coulps_cv_chain_stats")
+        return out
+
+    def cv_reset(self):
+        _check(self._lib.coulps_cv_reset(self.handle), "coulps_cv_reset")
 
 
 def pool_stats(rows):

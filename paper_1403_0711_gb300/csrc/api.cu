@@ -88,6 +88,7 @@ struct coulps_charges {
   int nblk = 1;
   double *d_partials = nullptr;  // scratch: [chain][nblk][2]
   double *d_stats = nullptr;     // [chain][kStatStride]
+  double *d_cvstats = nullptr;   // [chain][kStatStride], control-variate samples
   double *d_log = nullptr;       // [sample][chain][3]
   int64_t log_cap = 0;
   size_t bytes = 0;
@@ -718,9 +719,11 @@ int coulps_charges_create(coulps_lattice_t L, int64_t n, const int32_t *site, co
   C->d_q = (double *)dev_alloc(L->alloc, b_q, L->stream);
   C->d_partials = (double *)dev_alloc(L->alloc, b_part, L->stream);
   C->d_stats = (double *)dev_alloc(L->alloc, b_stats, L->stream);
+  C->d_cvstats = (double *)dev_alloc(L->alloc, b_stats, L->stream);
   if (log_capacity > 0) C->d_log = (double *)dev_alloc(L->alloc, b_log, L->stream);
-  C->bytes = b_idx + b_q + b_part + b_stats + b_log;
-  if (!C->d_idx || !C->d_q || !C->d_partials || !C->d_stats || (log_capacity > 0 && !C->d_log)) {
+  C->bytes = b_idx + b_q + b_part + 2 * b_stats + b_log;
+  if (!C->d_idx || !C->d_q || !C->d_partials || !C->d_stats || !C->d_cvstats ||
+      (log_capacity > 0 && !C->d_log)) {
     coulps_charges_destroy(C);
     return COULPS_ENOMEM;
   }
@@ -734,7 +737,8 @@ int coulps_charges_create(coulps_lattice_t L, int64_t n, const int32_t *site, co
       return COULPS_ECUDA;
     }
   }
-  if (launch_reset_stats(C->d_stats, g.n_chains, L->stream) != cudaSuccess) {
+  if (launch_reset_stats(C->d_stats, g.n_chains, L->stream) != cudaSuccess ||
+      launch_reset_stats(C->d_cvstats, g.n_chains, L->stream) != cudaSuccess) {
     cudaGetLastError();
     coulps_charges_destroy(C);
     return COULPS_ECUDA;
@@ -757,6 +761,7 @@ void coulps_charges_destroy(coulps_charges_t C) {
   dev_free(L->alloc, C->d_q, L->stream);
   dev_free(L->alloc, C->d_partials, L->stream);
   dev_free(L->alloc, C->d_stats, L->stream);
+  dev_free(L->alloc, C->d_cvstats, L->stream);
   dev_free(L->alloc, C->d_log, L->stream);
   if (C->staged) {
     cudaEventSynchronize(C->staged);
@@ -928,6 +933,39 @@ int coulps_reset_stats(coulps_charges_t C) {
   return COULPS_OK;
 }
 
+int coulps_cv_record(coulps_charges_t C, const double *tg, double c) {
+  if (!C || !tg || !std::isfinite(c)) return COULPS_EINVAL;
+  coulps_lattice *L = C->lat;
+  CK(launch_cv_record(C->d_stats, tg, c, C->d_cvstats, L->g.n_chains, L->d_err, L->stream));
+  return COULPS_OK;
+}
+
+int coulps_cv_chain_stats(coulps_charges_t C, double *out, int64_t cap) {
+  if (!C || !out) return COULPS_EINVAL;
+  coulps_lattice *L = C->lat;
+  const int64_t need = (int64_t)L->g.n_chains * kStatStride;
+  if (cap < need) return COULPS_EINVAL;
+  CK(cudaMemcpyAsync(out, C->d_cvstats, need * sizeof(double), cudaMemcpyDeviceToHost,
+                     L->stream));
+  return check_device_error(L);
+}
+
+int coulps_cv_estimate(coulps_charges_t C, double *mean, double *stderr_bm, double *tau_int,
+                       int64_t *n) {
+  if (!C) return COULPS_EINVAL;
+  coulps_lattice *L = C->lat;
+  std::vector<double> st((size_t)L->g.n_chains * kStatStride);
+  int s = coulps_cv_chain_stats(C, st.data(), (int64_t)st.size());
+  if (s) return s;
+  return coulps_pool_stats(st.data(), L->g.n_chains, mean, stderr_bm, tau_int, n);
+}
+
+int coulps_cv_reset(coulps_charges_t C) {
+  if (!C) return COULPS_EINVAL;
+  CK(launch_reset_stats(C->d_cvstats, C->lat->g.n_chains, C->lat->stream));
+  return COULPS_OK;
+}
+
 int coulps_charges_update(coulps_charges_t C, const int32_t *site, const double *q) {
   if (!C) return COULPS_EINVAL;
   if (C->n == 0) return COULPS_OK;
@@ -1000,10 +1038,24 @@ int coulps_kernel_times(coulps_lattice_t L, double out[6]) {
 }
 
 int coulps_cv_pack_field(coulps_lattice_t L, const float *rho, void *act_bf16, float *Aphi) {
-  if (!L || !rho || !act_bf16 || !Aphi) return COULPS_EINVAL;
+  if (!L) return COULPS_EINVAL;
+  const int32_t origin[3] = {0, 0, 0}, dims[3] = {L->g.Lx, L->g.Ly, L->g.Lz};
+  return coulps_cv_pack_region(L, rho, origin, dims, act_bf16, Aphi);
+}
+
+int coulps_cv_pack_region(coulps_lattice_t L, const float *rho, const int32_t *origin,
+                          const int32_t *dims, void *act_bf16, float *Aphi) {
+  if (!L || !rho || !origin || !dims || !act_bf16 || !Aphi) return COULPS_EINVAL;
   if (L->g.precision != COULPS_F32) return COULPS_EUNSUPPORTED;
   if (reinterpret_cast<uintptr_t>(act_bf16) & 15) return COULPS_EINVAL;
-  return coulps_cv_pack_field_impl(L->field, L->g, rho, act_bf16, Aphi, L->stream);
+  const int Ls[3] = {L->g.Lx, L->g.Ly, L->g.Lz};
+  int o[3], d[3];
+  for (int k = 0; k < 3; ++k) {
+    if (origin[k] < 0 || dims[k] < 1 || origin[k] + dims[k] > Ls[k]) return COULPS_EINVAL;
+    o[k] = origin[k];
+    d[k] = dims[k];
+  }
+  return coulps_cv_pack_field_impl(L->field, L->g, rho, act_bf16, Aphi, o, d, L->stream);
 }
 
 // ---- checkpoint ------------------------------------------------------------

@@ -85,6 +85,8 @@ __global__ void __launch_bounds__(kBatchThreads) batch_halfsweep_kernel(const Ba
     if (GATHER) {
       j.g_off = a.g_off + S.goff_base + (size_t)(item.y0 / S.TY) * S.Lz;
       j.g_ent = a.g_ent;
+      j.other = reinterpret_cast<const T *>(a.field) + S.field_off +
+                (long long)(a.colour ^ 1) * S.colour_elems;
       j.g_q = a.g_q;
     }
     double sq = 0.0, sp = 0.0;
@@ -188,10 +190,10 @@ int batch_row_stride(int Lx, int es) {
   return ((4 * ((Lx + 7) / 8) + a - 1) / a) * a;
 }
 
-size_t batch_smem_bytes(const coulps_batch *B, bool orx, bool gather) {
+size_t batch_smem_bytes(const coulps_batch *B, bool orx) {
   size_t m = 0;
   for (const auto &S : B->sys) {
-    const SmemLayout lay = smem_layout(S.TY, S.W, B->es, orx, gather);
+    const SmemLayout lay = smem_layout(S.TY, S.W, B->es, orx);
     m = std::max(m, (size_t)lay.total);
   }
   return m + 128;
@@ -286,7 +288,7 @@ int batch_layout(coulps_batch *B) {
     }
   }
   // persistent grid: as many CTAs as are co-resident at the largest smem need
-  B->smem = batch_smem_bytes(B, true, true);
+  B->smem = batch_smem_bytes(B, true);
   int dev = 0, sms = 0;
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -466,7 +468,7 @@ int coulps_batch_set_tiles(coulps_batch_t B, const int32_t *ty_dz) {
   }
   B->sys = next;
   B->layout_dirty = true;
-  if (batch_smem_bytes(B, true, true) > 227 * 1024) return COULPS_EINVAL;
+  if (batch_smem_bytes(B, true) > 227 * 1024) return COULPS_EINVAL;
   return batch_layout(B);
 }
 

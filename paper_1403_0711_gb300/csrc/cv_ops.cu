@@ -39,14 +39,17 @@ __device__ __forceinline__ float ld_field(const float *f, const Geometry &g, int
            ((size_t)z * g.Ly + y) * g.W + (x >> 1)];
 }
 
+// Packs the sub-box [o, o + e) of every chain (the whole box when o = 0,
+// e = L): rho is the full box's density.
 __global__ void cv_pack_kernel(const float *__restrict__ field, Geometry g,
                                const float *__restrict__ rho, __nv_bfloat16 *__restrict__ act,
-                               float *__restrict__ Aphi) {
-  const int64_t sites = (int64_t)g.Lx * g.Ly * g.Lz;
+                               float *__restrict__ Aphi, int ox, int oy, int oz, int ex, int ey,
+                               int ez) {
+  const int64_t sites = (int64_t)ex * ey * ez;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int chain = blockIdx.y;
   if (i >= sites) return;
-  const int x = (int)(i % g.Lx), y = (int)((i / g.Lx) % g.Ly), z = (int)(i / ((int64_t)g.Lx * g.Ly));
+  const int x = ox + (int)(i % ex), y = oy + (int)((i / ex) % ey), z = oz + (int)(i / ((int64_t)ex * ey));
   const float p = ld_field(field, g, chain, x, y, z);
   const float S = ld_field(field, g, chain, x - 1, y, z) + ld_field(field, g, chain, x + 1, y, z) +
                   ld_field(field, g, chain, x, y - 1, z) + ld_field(field, g, chain, x, y + 1, z) +
@@ -55,7 +58,7 @@ __global__ void cv_pack_kernel(const float *__restrict__ field, Geometry g,
   Aphi[o] = 6.f * p - S;
   __align__(16) __nv_bfloat16 v[16];
   v[0] = __float2bfloat16_rn(p);
-  v[1] = __float2bfloat16_rn(rho[i]);
+  v[1] = __float2bfloat16_rn(rho[((int64_t)z * g.Ly + y) * g.Lx + x]);
 #pragma unroll
   for (int k = 2; k < 16; ++k) v[k] = __float2bfloat16_rn(0.f);
   uint4 *dst = reinterpret_cast<uint4 *>(act + o * 16);
@@ -185,6 +188,73 @@ __global__ void cv_sum_partials_kernel(const double *__restrict__ partials, int 
   out[chain] = accumulate ? out[chain] + s : s;
 }
 
+// Region Stein term: g is the net inside R = [lo, hi) (in E coordinates) and
+// 0 outside.  For q within one site of R the divergence picks the offsets f
+// with q - f inside R: per axis a mask over f in {-1, 0, 1} (bit f + 1),
+// mapped to an index 0..5, class = ix + 6 iy + 36 iz.  K[class][c2][c1][e].
+__device__ __forceinline__ int allowed_index(int q, int lo, int hi) {
+  int m = 0;
+#pragma unroll
+  for (int f = -1; f <= 1; ++f)
+    if (q - f >= lo && q - f < hi) m |= 1 << (f + 1);
+  // masks 1, 2, 3, 4, 6, 7 -> 0..5; 0 (not next to R) -> -1
+  switch (m) {
+    case 1: return 0;
+    case 2: return 1;
+    case 3: return 2;
+    case 4: return 3;
+    case 6: return 4;
+    case 7: return 5;
+    default: return -1;
+  }
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+    cv_region_partial_kernel(const float *__restrict__ g16, const __nv_bfloat16 *__restrict__ s1,
+                             const __nv_bfloat16 *__restrict__ s2, const float *__restrict__ Aphi,
+                             const float *__restrict__ Ktab, int ex, int ey, int ez, int lox,
+                             int loy, int loz, int hix, int hiy, int hiz,
+                             double *__restrict__ partials) {
+  const int chain = blockIdx.y;
+  const int64_t sites = (int64_t)ex * ey * ez;
+  // divergence over q in (R + 1) within E, one thread per (q, c2)
+  const int qx0 = max(lox - 1, 0), qy0 = max(loy - 1, 0), qz0 = max(loz - 1, 0);
+  const int qx1 = min(hix + 1, ex), qy1 = min(hiy + 1, ey), qz1 = min(hiz + 1, ez);
+  const int nqx = qx1 - qx0, nqy = qy1 - qy0, nqz = qz1 - qz0;
+  const int64_t nq = (int64_t)nqx * nqy * nqz;
+  double acc = 0.0;
+  for (int64_t t = (int64_t)blockIdx.x * kRedThreads + threadIdx.x; t < nq * 16;
+       t += (int64_t)gridDim.x * kRedThreads) {
+    const int c2 = (int)(t & 15);
+    const int64_t k = t >> 4;
+    const int x = qx0 + (int)(k % nqx), y = qy0 + (int)((k / nqx) % nqy), z = qz0 + (int)(k / ((int64_t)nqx * nqy));
+    const int ix = allowed_index(x, lox, hix), iy = allowed_index(y, loy, hiy),
+              iz = allowed_index(z, loz, hiz);
+    if (ix < 0 || iy < 0 || iz < 0) continue;
+    const float *kk = Ktab + ((size_t)(ix + 6 * iy + 36 * iz) * 16 + c2) * 16 * 27;
+    float d = 0.f;
+    for (int e = 0; e < 27; ++e) {
+      const int xx = x + e % 3 - 1, yy = y + (e / 3) % 3 - 1, zz = z + e / 9 - 1;
+      if (xx < 0 || yy < 0 || zz < 0 || xx >= ex || yy >= ey || zz >= ez) continue;
+      const __nv_bfloat16 *sp = s1 + ((int64_t)chain * sites + ((int64_t)zz * ey + yy) * ex + xx) * 16;
+#pragma unroll
+      for (int c1 = 0; c1 < 16; ++c1) d = fmaf(kk[c1 * 27 + e], __bfloat162float(sp[c1]), d);
+    }
+    acc += (double)__bfloat162float(s2[((int64_t)chain * sites + ((int64_t)z * ey + y) * ex + x) * 16 + c2]) *
+           (double)d;
+  }
+  // minus sum over x in R of g_x (A phi)_x
+  const int nrx = hix - lox, nry = hiy - loy, nrz = hiz - loz;
+  const int64_t nr = (int64_t)nrx * nry * nrz;
+  for (int64_t k = (int64_t)blockIdx.x * kRedThreads + threadIdx.x; k < nr;
+       k += (int64_t)gridDim.x * kRedThreads) {
+    const int x = lox + (int)(k % nrx), y = loy + (int)((k / nrx) % nry), z = loz + (int)(k / ((int64_t)nrx * nry));
+    const int64_t o = (int64_t)chain * sites + ((int64_t)z * ey + y) * ex + x;
+    acc -= (double)g16[o * 16] * (double)Aphi[o];
+  }
+  block_sum_to(acc, partials + (size_t)chain * gridDim.x + blockIdx.x);
+}
+
 constexpr int kWgTile = 64;  // sites of one x row per shared-memory tile
 
 // Per-CTA partial of dW[co][ci][o] over a contiguous range of x-row tiles
@@ -294,6 +364,25 @@ int coulps_cv_stein_sum(const float *g16, const float *D, const void *s2_bf16, c
   return cudaGetLastError() == cudaSuccess ? COULPS_OK : COULPS_ECUDA;
 }
 
+int coulps_cv_stein_region(const float *g16, const void *s1_bf16, const void *s2_bf16,
+                           const float *Aphi, const float *Ktab, int nb, const int32_t *edims,
+                           const int32_t *lo, const int32_t *hi, double *scratch,
+                           int64_t scratch_doubles, double *out, void *stream) {
+  if (!g16 || !s1_bf16 || !s2_bf16 || !Aphi || !Ktab || !edims || !lo || !hi || !scratch || !out)
+    return COULPS_EINVAL;
+  if (nb < 1) return COULPS_EINVAL;
+  for (int k = 0; k < 3; ++k)
+    if (edims[k] < 1 || lo[k] < 0 || hi[k] > edims[k] || lo[k] >= hi[k]) return COULPS_EINVAL;
+  const int nblk = 64;
+  if (scratch_doubles < (int64_t)nb * nblk) return COULPS_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  cv_region_partial_kernel<<<dim3(nblk, nb), kRedThreads, 0, s>>>(
+      g16, (const __nv_bfloat16 *)s1_bf16, (const __nv_bfloat16 *)s2_bf16, Aphi, Ktab, edims[0],
+      edims[1], edims[2], lo[0], lo[1], lo[2], hi[0], hi[1], hi[2], scratch);
+  cv_sum_partials_kernel<<<(nb + 127) / 128, 128, 0, s>>>(scratch, nblk, nb, out, 0);
+  return cudaGetLastError() == cudaSuccess ? COULPS_OK : COULPS_ECUDA;
+}
+
 int coulps_cv_conv3d_wgrad(const void *a_bf16, const void *dh_bf16, float *dW, int nb, int Lx,
                            int Ly, int Lz, float *scratch, int64_t scratch_floats, void *stream) {
   if (!a_bf16 || !dh_bf16 || !dW || !scratch) return COULPS_EINVAL;
@@ -316,10 +405,12 @@ int coulps_cv_conv3d_wgrad(const void *a_bf16, const void *dh_bf16, float *dW, i
 
 // coulps_cv_pack_field (api.cu) supplies the lattice's geometry and stream.
 int coulps::coulps_cv_pack_field_impl(const void *field, const Geometry &g, const float *rho,
-                              void *act_bf16, float *Aphi, cudaStream_t s) {
-  const int64_t sites = (int64_t)g.Lx * g.Ly * g.Lz;
+                              void *act_bf16, float *Aphi, const int *origin, const int *dims,
+                              cudaStream_t s) {
+  const int64_t sites = (int64_t)dims[0] * dims[1] * dims[2];
   dim3 grid((unsigned)((sites + 255) / 256), g.n_chains);
   cv_pack_kernel<<<grid, 256, 0, s>>>(reinterpret_cast<const float *>(field), g, rho,
-                                      (__nv_bfloat16 *)act_bf16, Aphi);
+                                      (__nv_bfloat16 *)act_bf16, Aphi, origin[0], origin[1],
+                                      origin[2], dims[0], dims[1], dims[2]);
   return cudaGetLastError() == cudaSuccess ? COULPS_OK : COULPS_ECUDA;
 }

@@ -142,15 +142,10 @@ __device__ __forceinline__ double warp_sum(double v) {
 // cancelling difference of Eq. (nsum2)), then the running sums, the batch
 // sums (kBatchMin..2*kBatchMin batches; neighbours merge and the batch length
 // doubles when 2*kBatchMin complete) and, if row != nullptr, the log row.
-__device__ __forceinline__ void record_sample(double *st, double Q, double P, double *row,
-                                              int *err) {
-  const double e = Q * Q - P;
-  if (row != nullptr) {
-    row[0] = Q;
-    row[1] = P;
-    row[2] = e;
-  }
+// Adds the sample e to one chain's running sums and batch means.
+__device__ __forceinline__ void record_value(double *st, double e, int *err) {
   if (!isfinite(e)) atomicOr(err, kErrNonFinite);
+  st[kStatLast] = e;
   st[kStatN] += 1.0;
   st[kStatSum] += e;
   st[kStatSum2] += e * e;
@@ -171,6 +166,18 @@ __device__ __forceinline__ void record_sample(double *st, double Q, double P, do
     }
     st[kStatNBatch] = (double)nb;
   }
+}
+
+// Eq. (nsum2) sample e = Q^2 - P, logged to row when it is not null.
+__device__ __forceinline__ void record_sample(double *st, double Q, double P, double *row,
+                                              int *err) {
+  const double e = Q * Q - P;
+  if (row != nullptr) {
+    row[0] = Q;
+    row[1] = P;
+    row[2] = e;
+  }
+  record_value(st, e, err);
 }
 
 }  // namespace coulps

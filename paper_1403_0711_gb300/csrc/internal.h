@@ -98,7 +98,7 @@ constexpr uint32_t kGatherColourBit = 0x80000000u;
 // Estimator state, per chain, in doubles.
 constexpr int kBatchMin = 32;  // batches kept per chain: between kBatchMin and 2*kBatchMin
 constexpr int kStatN = 0, kStatSum = 1, kStatSum2 = 2, kStatCurSum = 3, kStatCurN = 4,
-              kStatBatchLen = 5, kStatNBatch = 6, kStatBatch0 = 8;
+              kStatBatchLen = 5, kStatNBatch = 6, kStatLast = 7, kStatBatch0 = 8;
 constexpr int kStatStride = kStatBatch0 + 2 * kBatchMin;
 static_assert(kStatStride == COULPS_STAT_STRIDE, "stat layout");
 
@@ -130,11 +130,16 @@ cudaError_t launch_gather(const Geometry &g, const void *field, const uint32_t *
 cudaError_t launch_finalize(const double *partials, int nblk, int n_chains, double *stats,
                             double *log, int64_t log_cap, int *err, cudaStream_t s);
 cudaError_t launch_reset_stats(double *stats, int n_chains, cudaStream_t s);
+// cv[chain] gets the sample y = e_last - c * tg[chain], e_last the chain's
+// most recent Eq. (nsum2) sample in stats
+cudaError_t launch_cv_record(const double *stats, const double *tg, double c, double *cv,
+                             int n_chains, int *err, cudaStream_t s);
 
 int gather_blocks(int64_t n);
 
 // Control variate input packing (cv_ops.cu) for a lattice's FP32 field.
 int coulps_cv_pack_field_impl(const void *field, const Geometry &g, const float *rho,
-                              void *act_bf16, float *Aphi, cudaStream_t s);
+                              void *act_bf16, float *Aphi, const int *origin, const int *dims,
+                              cudaStream_t s);
 
 }  // namespace coulps

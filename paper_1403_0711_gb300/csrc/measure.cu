@@ -87,6 +87,14 @@ __global__ void finalize_group_kernel(const double *__restrict__ partials, int n
   record_sample(st, Q, P, row, err);
 }
 
+__global__ void cv_record_kernel(const double *__restrict__ stats, const double *__restrict__ tg,
+                                 double c, double *__restrict__ cv, int n_chains, int *err) {
+  const int chain = blockIdx.x * blockDim.x + threadIdx.x;
+  if (chain >= n_chains) return;
+  const double e = stats[(size_t)chain * kStatStride + kStatLast];
+  record_value(cv + (size_t)chain * kStatStride, e - c * tg[chain], err);
+}
+
 __global__ void reset_stats_kernel(double *stats, int n_chains) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_chains * kStatStride) return;
@@ -130,6 +138,12 @@ cudaError_t launch_finalize_group(const double *partials, int nblk, int n_chains
   if (count <= 0) return cudaSuccess;
   finalize_group_kernel<<<(count + 127) / 128, 128, 0, s>>>(partials, nblk, n_chains, first, stride,
                                                             stats, log, log_cap, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cv_record(const double *stats, const double *tg, double c, double *cv,
+                             int n_chains, int *err, cudaStream_t s) {
+  cv_record_kernel<<<(n_chains + 127) / 128, 128, 0, s>>>(stats, tg, c, cv, n_chains, err);
   return cudaGetLastError();
 }
 

@@ -27,10 +27,10 @@
 //
 // Fused gather.  On the last half-sweep of a measured compound sweep the
 // kernel also forms the tile's share of Q = sum q_i phi(r_i) and
-// P = sum (q_i phi(r_i))^2 (Eq. (nsum2)): after each plane it reads the new
-// own-colour values from a shared-memory copy and the other colour's from the
-// ring, and each CTA writes one FP64 (Q, P) partial; finalize adds them in a
-// fixed order.
+// P = sum (q_i phi(r_i))^2 (Eq. (nsum2)): once the tile is written it reads
+// the values at the tile's charges back from L2 (one barrier per tile, none
+// per plane), and each CTA writes one FP64 (Q, P) partial; finalize adds them
+// in a fixed order.
 //
 // DRAM traffic per updated site: one read of the other colour, one write
 // (heatbath, 8 B in FP32) plus one read of the old value (over-relaxation,
@@ -71,6 +71,8 @@ __global__ void __launch_bounds__(256)
   if (GATHER) {
     j.g_off = a.g_off + (size_t)blockIdx.x * a.Lz;
     j.g_ent = a.g_ent;
+    j.other = reinterpret_cast<const T *>(a.field) + (size_t)chain * a.chain_elems +
+              (size_t)(a.colour ^ 1) * a.colour_elems;
     j.g_q = a.g_q;
   }
   double sq = 0.0, sp = 0.0;
@@ -116,6 +118,8 @@ __global__ void __launch_bounds__(256)
   j.pass = *a.pass_ptr + m.pass_delta[grp];
   j.g_off = a.g_off + (size_t)blockIdx.x * a.Lz;
   j.g_ent = a.g_ent;
+  j.other = reinterpret_cast<const T *>(a.field) + (size_t)chain * a.chain_elems +
+            (size_t)(a.colour ^ 1) * a.colour_elems;
   j.g_q = a.g_q;
   const PhiloxKeys &K = *reinterpret_cast<const PhiloxKeys *>(a.round_keys);
   double sq = 0.0, sp = 0.0;
@@ -138,7 +142,7 @@ __global__ void __launch_bounds__(256)
 template <typename T>
 cudaError_t launch_mixed_t(const Geometry &g, const Tile &t, const CUtensorMap &tm_halo,
                            const CUtensorMap &tm_own, const MixedArgs &m, cudaStream_t s) {
-  const SmemLayout lay = smem_layout(t.ty, g.W, (int)sizeof(T), true, true);
+  const SmemLayout lay = smem_layout(t.ty, g.W, (int)sizeof(T), true);
   const size_t smem = (size_t)lay.total + 128;
   auto kfn = halfsweep_mixed_kernel<T>;
   static int configured_bytes = 0;
@@ -158,7 +162,7 @@ __global__ void advance_pass_kernel(uint32_t *pass, uint32_t n) { *pass += n; }
 template <typename T, bool OR, bool GATHER>
 cudaError_t launch_t(const Geometry &g, const Tile &t, const CUtensorMap &tm_halo,
                      const CUtensorMap &tm_own, const SweepArgs &a, cudaStream_t s) {
-  const SmemLayout lay = smem_layout(t.ty, g.W, (int)sizeof(T), OR, GATHER);
+  const SmemLayout lay = smem_layout(t.ty, g.W, (int)sizeof(T), OR);
   const size_t smem = (size_t)lay.total + 128;
   auto kfn = halfsweep_kernel<T, OR, GATHER>;
   static int configured_bytes = 0;  // per instantiation
@@ -189,7 +193,7 @@ cudaError_t launch_p(const Geometry &g, const Tile &t, const CUtensorMap &tm_hal
 }  // namespace
 
 size_t halfsweep_smem_bytes(const Geometry &g, const Tile &t, bool overrelax) {
-  return (size_t)smem_layout(t.ty, g.W, g.es, overrelax, true).total + 128;
+  return (size_t)smem_layout(t.ty, g.W, g.es, overrelax).total + 128;
 }
 
 cudaError_t launch_halfsweep(const Geometry &g, const Tile &t, const CUtensorMap &tm_halo,

@@ -16,20 +16,18 @@ struct SmemLayout {
   int halo_bytes;  // exact TMA box bytes of the other colour: (TY + 2) * W * es
   int own_bytes;   // exact TMA box bytes of the own colour: TY * W * es (OR only)
   int slot_bytes;  // one ring slot, both boxes, each rounded to 128 bytes
-  int out_bytes;   // fused gather: this plane's new values, TY * W * es
-  int total;       // header (barriers, flags, reduction) + ring + out, no alignment slack
+  int total;       // header (barriers, flags, reduction) + ring, no alignment slack
 };
 
 // barriers at 0, abort flag at 64, block reduction (2 x 32 doubles) at 128
 constexpr int kHeaderBytes = 1024;
 
-__host__ __device__ inline SmemLayout smem_layout(int TY, int W, int es, bool orx, bool gather) {
+__host__ __device__ inline SmemLayout smem_layout(int TY, int W, int es, bool orx) {
   SmemLayout L;
   L.halo_bytes = (TY + 2) * W * es;
   L.own_bytes = orx ? TY * W * es : 0;
   L.slot_bytes = round_up_int(L.halo_bytes, 128) + round_up_int(L.own_bytes, 128);
-  L.out_bytes = gather ? round_up_int(TY * W * es, 128) : 0;
-  L.total = kHeaderBytes + kStages * L.slot_bytes + L.out_bytes;
+  L.total = kHeaderBytes + kStages * L.slot_bytes;
   return L;
 }
 
@@ -76,6 +74,7 @@ struct TileJob {
   const CUtensorMap *tm_halo, *tm_own;
   int map_other, map_own;  // 4th TMA coordinate of the other / own colour
   T *out;                  // own colour of this chain: element (z*Ly + y)*W + h
+  const T *other;          // the other colour, same indexing (GATHER only)
   int Lx, Ly, Lz, W, Wq, QW, TY;
   int y0, z0, nz;
   int colour;
@@ -107,11 +106,10 @@ __device__ __forceinline__ void ring_init(unsigned char *smem) {
 template <typename T, bool OR, bool GATHER>
 __device__ bool march_tile(const TileJob<T> &j, const PhiloxKeys &K, unsigned char *smem,
                            int *err, int &gbase, double &sq, double &sp) {
-  const SmemLayout lay = smem_layout(j.TY, j.W, (int)sizeof(T), OR, GATHER);
+  const SmemLayout lay = smem_layout(j.TY, j.W, (int)sizeof(T), OR);
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem);  // kStages barriers
   volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 64);
   unsigned char *ring = smem + kHeaderBytes;
-  T *outbuf = reinterpret_cast<T *>(ring + kStages * lay.slot_bytes);
   auto halo_slot = [&](int s) -> T * {
     return reinterpret_cast<T *>(ring + s * lay.slot_bytes);
   };
@@ -216,7 +214,6 @@ __device__ bool march_tile(const TileJob<T> &j, const PhiloxKeys &K, unsigned ch
           for (int i = 0; i < 4; ++i)
             if (2 * (4 * qx + i) + par >= j.Lx) v[i] = T(0);  // keep the row padding at 0
           st_quad(j.out + ((size_t)z * j.Ly + y) * W + 4 * qx, v);
-          if (GATHER) st_quad(outbuf + ty * W + 4 * qx, v);
         }
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -226,23 +223,6 @@ __device__ bool march_tile(const TileJob<T> &j, const PhiloxKeys &K, unsigned ch
       } else {
         atomicOr(err, kErrTimeout);
         *abort_flag = 1;
-      }
-      if (GATHER) {
-        // Q and P over the charges of this plane of the tile: the own colour
-        // from the values just computed, the other colour from the ring.
-        __syncthreads();
-        if (!*abort_flag) {
-          const uint32_t e1 = j.g_off[z + 1];
-          for (uint32_t e = j.g_off[z] + tid; e < e1; e += blockDim.x) {
-            const uint32_t ent = j.g_ent[e];
-            const uint32_t idx = ent & ~kGatherColourBit;
-            const bool own = ((ent >> 31) & 1u) == (uint32_t)c;
-            const T val = own ? outbuf[idx] : Pz[W + idx];
-            const double t = j.g_q[e] * (double)val;
-            sq += t;
-            sp += t * t;
-          }
-        }
       }
       __syncthreads();
       if (*abort_flag) {
@@ -260,6 +240,29 @@ __device__ bool march_tile(const TileJob<T> &j, const PhiloxKeys &K, unsigned ch
       if (!wait_plane(k)) break;
   }
   gbase = gb + n_planes;
+  if (GATHER && !aborted) {
+    // Q and P over the tile's charges, once the whole tile is written: the
+    // barrier makes this CTA's global stores visible to all its threads, and
+    // both colours of the tile are still in L2.  Entry e belongs to plane z
+    // with g_off[z] <= e < g_off[z + 1] (binary search: planes may be empty).
+    __syncthreads();
+    const uint32_t e0 = j.g_off[j.z0], e1 = j.g_off[j.z0 + j.nz];
+    for (uint32_t e = e0 + tid; e < e1; e += blockDim.x) {
+      int lo = j.z0, hi = j.z0 + j.nz;
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (j.g_off[mid] <= e) lo = mid;
+        else hi = mid;
+      }
+      const uint32_t ent = j.g_ent[e];
+      const size_t at = ((size_t)lo * j.Ly + j.y0) * W + (ent & ~kGatherColourBit);
+      const bool own = ((ent >> 31) & 1u) == (uint32_t)c;
+      const T val = own ? j.out[at] : j.other[at];
+      const double t = j.g_q[e] * (double)val;
+      sq += t;
+      sp += t * t;
+    }
+  }
   return !aborted;
 }
 

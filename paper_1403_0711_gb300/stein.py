@@ -348,3 +348,223 @@ def stein_terms(cv: SteinCV, phis, Aphis, rho, batch=16):
     for i in range(0, len(phis), batch):
         out.append(cv.stein_term(inputs_from(phis[i:i + batch], rho), Aphis[i:i + batch]).double())
     return torch.cat(out)
+
+
+# --------------------------------------------------------------------------
+# Localized control variate
+# --------------------------------------------------------------------------
+# T is linear in g, and g = (net inside a box R, 0 elsewhere) is still a smooth
+# field of phi, so its Stein term keeps mean 0.  Around a compact cluster of
+# charges (the q = 1 cube) most of the variance of e comes from the field near
+# the charges, and a g supported there can cancel it.  The net only has to be
+# evaluated on the sub-box E = R + 3 (its receptive field), which costs almost
+# nothing next to a sweep of the whole lattice.
+
+# per-axis allowed sets of the last layer's offset f for q within one site of
+# R, indexed as the library's region kernel expects (f = -1 is bit 0)
+_AXIS_SETS = ((-1,), (0,), (-1, 0), (1,), (0, 1), (-1, 0, 1))
+_MASK_INDEX = {1: 0, 2: 1, 3: 2, 4: 3, 6: 4, 7: 5}
+
+
+def _region_fmasks():
+    """(216, 27) f masks, class ix + 6 iy + 36 iz."""
+    m = torch.zeros(216, 27)
+    for iz, iy, ix in itertools.product(range(6), repeat=3):
+        for fi, f in enumerate(OFFS):  # f = (dz, dy, dx)
+            if f[0] in _AXIS_SETS[iz] and f[1] in _AXIS_SETS[iy] and f[2] in _AXIS_SETS[ix]:
+                m[ix + 6 * iy + 36 * iz, fi] = 1.0
+    return m
+
+
+_REGION_FMASKS = _region_fmasks()
+
+
+def _axis_index(n, lo, hi):
+    """Per coordinate 0..n-1 the allowed-set index, -1 when not next to [lo, hi)."""
+    out = []
+    for q in range(n):
+        m = sum(1 << (f + 1) for f in (-1, 0, 1) if lo <= q - f < hi)
+        out.append(_MASK_INDEX.get(m, -1))
+    return out
+
+
+class LocalSteinCV(SteinCV):
+    """SteinCV whose g is the net inside the box R = [lo, hi) (lattice x, y, z
+    coordinates, half-open) and 0 elsewhere."""
+
+    def __init__(self, L, lo, hi, seed=0, scale=0.3, device="cuda", w3_scale=0.0):
+        super().__init__(seed=seed, scale=scale, device=device, w3_scale=w3_scale)
+        self.L = tuple(int(v) for v in L)
+        lo = tuple(int(v) for v in lo)
+        hi = tuple(int(v) for v in hi)
+        if any(not (0 <= a < b <= n) for a, b, n in zip(lo, hi, self.L)):
+            raise ValueError("region must be a non-empty box inside the lattice")
+        self.e_lo = tuple(max(a - 3, 0) for a in lo)
+        self.e_hi = tuple(min(b + 3, n) for b, n in zip(hi, self.L))
+        self.edims = tuple(b - a for a, b in zip(self.e_lo, self.e_hi))
+        self.r_lo = tuple(a - e for a, e in zip(lo, self.e_lo))  # R in E coordinates
+        self.r_hi = tuple(b - e for b, e in zip(hi, self.e_lo))
+        ex, ey, ez = self.edims
+        ix = _axis_index(ex, self.r_lo[0], self.r_hi[0])
+        iy = _axis_index(ey, self.r_lo[1], self.r_hi[1])
+        iz = _axis_index(ez, self.r_lo[2], self.r_hi[2])
+        # sites q of E next to R and their classes, for the differentiable term
+        qs, cls = [], []
+        for z in range(ez):
+            for y in range(ey):
+                for x in range(ex):
+                    if ix[x] >= 0 and iy[y] >= 0 and iz[z] >= 0:
+                        qs.append((z, y, x))
+                        cls.append(ix[x] + 6 * iy[y] + 36 * iz[z])
+        self._q = torch.tensor(qs, device=device)
+        self._qcls = torch.tensor(cls, device=device)
+        rmask = torch.zeros(ez, ey, ex, device=device)
+        rmask[self.r_lo[2]:self.r_hi[2], self.r_lo[1]:self.r_hi[1], self.r_lo[0]:self.r_hi[0]] = 1
+        self._rmask = rmask
+
+    def region_kernels(self):
+        """(216, 16, 16, 27) divergence kernel per allowed-offset class."""
+        return divergence_kernel(self.W1, self.W2, self.W3, _REGION_FMASKS).reshape(216, 16, 16, 27)
+
+    def rho_region(self, rho):
+        """The density restricted to E, (ez, ey, ex)."""
+        (x0, y0, z0), (x1, y1, z1) = self.e_lo, self.e_hi
+        return rho[z0:z1, y0:y1, x0:x1]
+
+    # -- differentiable T g on E-sized inputs: x0 (n, ez, ey, ex, 16) BF16
+    def stein_term(self, x0, Aphi, faces=True):
+        h1 = Conv3dTC.apply(x0, self._w1p(), self.b1)
+        a1 = torch.tanh(h1)
+        s1 = 1.0 - a1 * a1
+        h2 = Conv3dTC.apply(a1.to(torch.bfloat16), self.W2, self.b2)
+        a2 = torch.tanh(h2)
+        s2 = 1.0 - a2 * a2
+        g = Conv3dTC.apply(a2.to(torch.bfloat16), self._w3p(), self._b3p())[..., 0]
+        # s rounded like the library kernel's BF16 copies (straight-through)
+        s1 = s1 + (s1.to(torch.bfloat16).float() - s1).detach()
+        s2 = s2 + (s2.to(torch.bfloat16).float() - s2).detach()
+        return self.region_divergence(s1, s2) - (g * Aphi * self._rmask).sum(dim=(1, 2, 3))
+
+    def region_divergence(self, s1, s2):
+        """sum_{x in R} dg_x/dphi_x from s1, s2 (n, ez, ey, ex, 16): for each q
+        next to R, s2[q] . (K_class(q) applied to the 27 neighbours of s1)."""
+        s1p = torch.nn.functional.pad(s1, (0, 0, 1, 1, 1, 1, 1, 1))
+        qz, qy, qx = self._q[:, 0], self._q[:, 1], self._q[:, 2]
+        patches = torch.stack([s1p[:, qz + 1 + o[0], qy + 1 + o[1], qx + 1 + o[2]] for o in OFFS],
+                              dim=2)  # (n, m, 27, 16)
+        Kq = self.region_kernels()[self._qcls]  # (m, 16 c2, 16 c1, 27)
+        d = torch.einsum("nmec,mdce->nmd", patches, Kq)
+        return (s2[:, qz, qy, qx] * d).sum(dim=(1, 2))
+
+    @torch.no_grad()
+    def pack(self, lat: "coulps.Lattice", rho: torch.Tensor):
+        """(net input on E (n, ez, ey, ex, 16) BF16, A phi on E FP32) of every
+        chain, by the library's packing kernel on the lattice's stream."""
+        n = lat.n_chains
+        ex, ey, ez = self.edims
+        x0 = torch.empty((n, ez, ey, ex, 16), dtype=torch.bfloat16, device=rho.device)
+        Aphi = torch.empty((n, ez, ey, ex), dtype=torch.float32, device=rho.device)
+        o = (ctypes.c_int32 * 3)(*self.e_lo)
+        d = (ctypes.c_int32 * 3)(*self.edims)
+        coulps._check(coulps.load().coulps_cv_pack_region(lat.handle, _vp(rho), o, d, _vp(x0),
+                                                          _vp(Aphi)), "coulps_cv_pack_region")
+        return x0, Aphi
+
+    def prepare(self):
+        """Pack the weights and class kernels for evaluate (call after fitting)."""
+        with torch.no_grad():
+            dev = self.W1.device
+            self._ev = {
+                "w1": pack_weights(self._w1p()), "w2": pack_weights(self.W2),
+                "w3": pack_weights(self._w3p()),
+                "b1": self.b1.detach().float().contiguous(), "b2": self.b2.detach().float().contiguous(),
+                "b3": self._b3p().detach().float().contiguous(),
+                "K": self.region_kernels().detach().float().contiguous(),
+                "err": torch.zeros(1, dtype=torch.int32, device=dev),
+            }
+
+    # -- evaluation with library kernels only, on the lattice's stream
+    @torch.no_grad()
+    def evaluate(self, lat: "coulps.Lattice", rho: torch.Tensor, out=None) -> torch.Tensor:
+        """T g for every chain (float64 tensor of n_chains, on the device), all
+        in library kernels queued on the lattice's stream; not synchronised."""
+        if not hasattr(self, "_ev"):
+            self.prepare()
+        ev = self._ev
+        lib = coulps.load()
+        n = lat.n_chains
+        ex, ey, ez = self.edims
+        dev = rho.device
+        stream = lat._stream if isinstance(lat._stream, torch.cuda.Stream) else \
+            torch.cuda.current_stream()
+        sp = ctypes.c_void_p(stream.cuda_stream)
+        with torch.cuda.stream(stream):
+            x0, Aphi = self.pack(lat, rho)
+            a1 = torch.empty_like(x0)
+            s1 = torch.empty_like(x0)
+            a2 = torch.empty_like(x0)
+            s2 = torch.empty_like(x0)
+            g16 = torch.empty(x0.shape, dtype=torch.float32, device=dev)
+            for src, w, b, dst in ((x0, "w1", "b1", (a1, s1)), (a1, "w2", "b2", (a2, s2))):
+                coulps._check(lib.coulps_cv_conv3d_tanh(
+                    _vp(src), _vp(ev[w]), _vp(ev[b]), _vp(dst[0]), _vp(dst[1]), n, ex, ey, ez,
+                    _vp(ev["err"]), sp), "coulps_cv_conv3d_tanh")
+            coulps._check(lib.coulps_cv_conv3d(_vp(a2), _vp(ev["w3"]), _vp(ev["b3"]), _vp(g16), n,
+                                               ex, ey, ez, _vp(ev["err"]), sp), "coulps_cv_conv3d")
+            if out is None:
+                out = torch.empty(n, dtype=torch.float64, device=dev)
+            scratch = torch.empty(64 * n, dtype=torch.float64, device=dev)
+            ed = (ctypes.c_int32 * 3)(*self.edims)
+            rl = (ctypes.c_int32 * 3)(*self.r_lo)
+            rh = (ctypes.c_int32 * 3)(*self.r_hi)
+            coulps._check(lib.coulps_cv_stein_region(
+                _vp(g16), _vp(s1), _vp(s2), _vp(Aphi), _vp(ev["K"]), n, ed, rl, rh, _vp(scratch),
+                scratch.numel(), _vp(out), sp), "coulps_cv_stein_region")
+        return out
+
+
+def collect_region(cv: LocalSteinCV, lat, ch, rho, n_rounds, every=1, n_hb=1, n_or=3):
+    """Like collect, on E only: (BF16 phi (k, ez, ey, ex), A phi, e)."""
+    phis, Aphis, es = [], [], []
+    for r in range(n_rounds):
+        ch.run(0, every, n_hb, n_or)
+        x0, a = cv.pack(lat, rho)
+        lat.sync()
+        phis.append(x0[..., 0].clone())
+        Aphis.append(a)
+        es.append(torch.from_numpy(ch.chain_stats()[:, 7].copy()))  # latest sample e
+    return torch.cat(phis), torch.cat(Aphis), torch.cat(es).double()
+
+
+def fit_region(cv: LocalSteinCV, phis, Aphis, es, rho, steps=400, batch=64, lr=3e-3, seed=0,
+               log=None, holdout=0.25):
+    """Minimise Var(e - T g) (Adam, exact region term), then set
+    cv.c = Cov(e, T g) / Var(T g) on held-out samples (the last `holdout`
+    fraction), which keeps the coefficient independent of the weights' fit."""
+    g = torch.Generator().manual_seed(seed)
+    opt = torch.optim.Adam([cv.W1, cv.b1, cv.W2, cv.b2, cv.W3, cv.b3], lr=lr)
+    n = len(es)
+    n_tr = max(2, int(n * (1.0 - holdout)))
+    dev = phis.device
+    es_d = es.to(dev)
+    rho_e = cv.rho_region(rho)
+    var_e = es_d[:n_tr].float().var() + 1e-30
+    for step in range(steps):
+        idx = torch.randint(0, n_tr, (batch,), generator=g).to(dev)
+        tg = cv.stein_term(inputs_from(phis[idx], rho_e), Aphis[idx])
+        r = es_d[idx].float() - tg
+        loss = ((r - r.mean()) ** 2).mean() / var_e
+        opt.zero_grad()
+        loss.backward()
+        opt.step()
+        if log is not None:
+            log.append(float(loss.detach()))
+    with torch.no_grad():
+        tgs = torch.cat([cv.stein_term(inputs_from(phis[i:i + 256], rho_e), Aphis[i:i + 256]).double()
+                         for i in range(0, n, 256)])
+    e, t = es.to(tgs.device)[n_tr:], tgs[n_tr:]
+    if len(e) < 2:
+        e, t = es.to(tgs.device), tgs
+    cv.c = float(((e - e.mean()) * (t - t.mean())).sum() / ((t - t.mean()) ** 2).sum())
+    cv.prepare()
+    return tgs

@@ -118,3 +118,162 @@ def test_training_lowers_loss_and_keeps_mean(env):
     assert abs(float(e_cv.mean() - e2.mean())) < 4 * se
     ch.close()
     lat.close()
+
+
+def test_region_evaluate_matches_oracle(env):
+    """Library kernels on the sub-box E = R + 3 (pack_region, two fused-tanh
+    convs, conv, stein_region) = the oracle's region-restricted Stein term on
+    the whole lattice, and = the differentiable path."""
+    torch, coulps, stream = env
+    from oracle import stein as ost
+    from paper_1403_0711_gb300 import inputs, stein
+    L = (20, 18, 16)
+    lo, hi = (5, 4, 1), (11, 9, 6)  # E clipped at z = 0
+    sites, q = inputs.uniform_q(L, 10, seed=8)
+    sites[:3] = [[6, 5, 2], [9, 7, 4], [7, 8, 3]]  # some charges inside R
+    lat = coulps.Lattice(L, n_chains=3, precision=coulps.F32, seed=15, stream=stream)
+    lat.sweep(20, 1, 1)
+    rho = stein.charge_density(L, sites, q)
+    cv = stein.LocalSteinCV(L, lo, hi, seed=2, scale=0.6, w3_scale=0.1)
+    tg = cv.evaluate(lat, rho)
+    lat.sync()
+    tg = tg.cpu().numpy()
+    x0, Aphi = cv.pack(lat, rho)
+    lat.sync()
+    with torch.no_grad():
+        tg_grad = cv.stein_term(x0, Aphi).double().cpu().numpy()
+    p = {k: getattr(cv, k).detach().double().cpu().numpy() for k in ("W1", "b1", "W2", "b2", "W3", "b3")}
+    r = rho.cpu().numpy().astype(np.float64)
+    region = ((lo[2], hi[2]), (lo[1], hi[1]), (lo[0], hi[0]))
+    mask = ost.region_mask(r.shape, region)
+    for k in range(3):
+        phi = lat.field(k)
+        div = ost.divergence(phi, r, p, region)
+        gA = float(np.sum(ost.forward(phi, r, p)["g"] * mask * ost.apply_A(phi)))
+        scale = abs(div) + abs(gA)
+        assert abs(tg[k] - (div - gA)) < 3e-2 * scale, (k, tg[k], div - gA, scale)
+        assert abs(tg_grad[k] - tg[k]) < 1e-2 * scale, (k, tg_grad[k], tg[k])
+    lat.close()
+
+
+def test_region_pack_matches_field(env):
+    """coulps_cv_pack_region: phi (BF16) and A phi of the sub-box, A phi with
+    the neighbours outside E taken from the full field."""
+    torch, coulps, stream = env
+    from oracle import stein as ost
+    from paper_1403_0711_gb300 import stein
+    L = (17, 12, 10)
+    lat = coulps.Lattice(L, n_chains=2, precision=coulps.F32, seed=3, stream=stream)
+    lat.sweep(10, 1, 0)
+    rho = torch.zeros(L[2], L[1], L[0], device="cuda")
+    rho[4, 5, 6] = 1.0
+    cv = stein.LocalSteinCV(L, (5, 4, 3), (9, 8, 6))
+    x0, Aphi = cv.pack(lat, rho)
+    lat.sync()
+    (x0_, y0_, z0_), (x1_, y1_, z1_) = cv.e_lo, cv.e_hi
+    for k in range(2):
+        phi = lat.field(k)
+        sub = phi[z0_:z1_, y0_:y1_, x0_:x1_]
+        got = x0[k, ..., 0].float().cpu().numpy()
+        assert np.abs(got - sub).max() <= 2 ** -8 * np.abs(sub).max()
+        assert np.abs(Aphi[k].cpu().numpy() - ost.apply_A(phi)[z0_:z1_, y0_:y1_, x0_:x1_]).max() < 1e-5
+        assert np.array_equal(x0[k, ..., 1].float().cpu().numpy(), rho.cpu().numpy()[z0_:z1_, y0_:y1_, x0_:x1_])
+        assert not x0[k, ..., 2:].float().abs().any()
+    lat.close()
+
+
+def test_region_stein_term_has_zero_mean_under_sampler(env):
+    torch, coulps, stream = env
+    from paper_1403_0711_gb300 import inputs, stein
+    L = (10, 10, 10)
+    sites, q = inputs.cube(L, 2)
+    lat = coulps.Lattice(L, n_chains=512, precision=coulps.F32, seed=78, stream=stream)
+    lat.sweep(200, 1, 0)
+    rho = stein.charge_density(L, sites, q)
+    cv = stein.LocalSteinCV(L, (2, 2, 2), (8, 8, 8), seed=4, scale=0.6, w3_scale=0.1)
+    vals = []
+    for _ in range(40):
+        lat.sweep(8, 1, 0)
+        vals.append(cv.evaluate(lat, rho).cpu().numpy())
+    v = np.stack(vals)
+    per_chain = v.mean(axis=0)
+    se = per_chain.std(ddof=1) / math.sqrt(len(per_chain))
+    assert abs(per_chain.mean()) < 4 * se, (per_chain.mean(), se)
+    assert v.std() > 0.0
+    lat.close()
+
+
+def test_cv_record_and_estimate(env):
+    """coulps_cv_record adds y = e - c tg per chain to statistics kept beside
+    the plain ones; c = 0 reproduces the plain estimator exactly."""
+    torch, coulps, stream = env
+    from paper_1403_0711_gb300 import inputs
+    L = (16, 12, 10)
+    sites, q = inputs.plus_minus(L, 20, seed=2)
+    lat = coulps.Lattice(L, n_chains=4, precision=coulps.F32, seed=21, stream=stream)
+    ch = coulps.Charges(lat, sites, q, log_capacity=64)
+    tg = torch.tensor([0.5, -1.0, 2.0, 0.25], dtype=torch.float64, device="cuda")
+    c = 0.75
+    for _ in range(40):
+        ch.run(0, 1, 1, 1)
+        ch.cv_record(tg.data_ptr(), c)
+    lat.sync()
+    e = ch.samples()[:, :, 2]  # (40, 4)
+    y = e - c * tg.cpu().numpy()[None]
+    st = ch.cv_chain_stats()
+    assert np.array_equal(st[:, 0], np.full(4, 40.0))
+    assert np.allclose(st[:, 1], y.sum(axis=0), rtol=1e-12, atol=1e-12)
+    assert np.allclose(st[:, 2], (y * y).sum(axis=0), rtol=1e-12, atol=1e-12)
+    assert np.allclose(st[:, 7], y[-1], rtol=1e-12, atol=1e-12)
+    assert np.array_equal(ch.chain_stats()[:, 7], e[-1])
+    ch.cv_reset()
+    for _ in range(40):
+        ch.run(0, 1, 1, 1)
+        ch.cv_record(tg.data_ptr(), 0.0)
+    ch.reset_stats()
+    ch.cv_reset()
+    for _ in range(80):
+        ch.run(0, 1, 1, 1)
+        ch.cv_record(tg.data_ptr(), 0.0)
+    a, b = ch.estimate(), ch.cv_estimate()
+    assert a == b
+    with pytest.raises(coulps.CoulpsError):
+        ch.cv_record(0, 1.0)
+    ch.close()
+    lat.close()
+
+
+def test_local_cv_reduces_variance_on_cube(env):
+    """Trained on the q = 1 cube (N = 8) with g supported within 3 sites of
+    the charges, the CV estimator keeps the plain mean and has a smaller
+    variance on fresh samples."""
+    torch, coulps, stream = env
+    from paper_1403_0711_gb300 import inputs, stein
+    L = (24, 24, 24)
+    sites, q = inputs.cube(L, 2)
+    lat = coulps.Lattice(L, n_chains=64, precision=coulps.F32, seed=31, stream=stream)
+    ch = coulps.Charges(lat, sites, q)
+    lat.sweep(300, 1, 1)
+    rho = stein.charge_density(L, sites, q)
+    lo, hi = sites.min(axis=0) - 3, sites.max(axis=0) + 4
+    cv = stein.LocalSteinCV(L, lo, hi, seed=0, scale=0.3)
+    phis, Aphis, es = stein.collect_region(cv, lat, ch, rho, n_rounds=48, every=2, n_hb=1, n_or=1)
+    log = []
+    stein.fit_region(cv, phis, Aphis, es, rho, steps=300, batch=128, lr=3e-3, log=log)
+    assert np.mean(log[-20:]) < np.mean(log[:20])
+    ch.reset_stats()
+    ch.cv_reset()
+    tg = torch.empty(64, dtype=torch.float64, device="cuda")
+    for _ in range(400):
+        ch.run(0, 1, 1, 1)
+        cv.evaluate(lat, rho, out=tg)
+        ch.cv_record(tg.data_ptr(), cv.c)
+    plain, cvst = ch.chain_stats(), ch.cv_chain_stats()
+    n = plain[:, 0].sum()
+    var_p = plain[:, 2].sum() / n - (plain[:, 1].sum() / n) ** 2
+    var_c = cvst[:, 2].sum() / n - (cvst[:, 1].sum() / n) ** 2
+    assert var_c < 0.5 * var_p, (var_c, var_p)
+    a, b = ch.estimate(), ch.cv_estimate()
+    assert abs(a["mean"] - b["mean"]) < 4 * math.hypot(a["stderr"], b["stderr"]), (a, b)
+    ch.close()
+    lat.close()
