@@ -10,7 +10,7 @@ so  e - T g,  T g = sum_x (dg_x/dphi_x - g_x (A phi)_x),  has the same mean
 as the Eq. (nsum2) sample e and, for a good g, a smaller variance.
 
 g is a 3-layer 3x3x3 convolutional net with zero padding:
-    psi = (phi, rho)                       (rho = charge density per site)
+    psi = (phi, rho, rho phi)              (rho = charge density per site)
     h1 = b1 + conv(psi, W1),  a1 = tanh(h1)       16 channels
     h2 = b2 + conv(a1,  W2),  a2 = tanh(h2)       16 channels
     g  = b3 + conv(a2,  W3)                        1 channel
@@ -20,7 +20,9 @@ d = (kz-1, ky-1, kx-1) acting on (z, y, x)).
 
 The divergence is computed here by the plain chain rule, site by site:
     dg_x/dphi_x = sum_{c2, f} W3[c2, f] s2[c2, x+f]
-                  sum_{c1, e} W2[c2, c1, e] s1[c1, x+f+e] W1[c1, 0, -(f+e)]
+                  sum_{c1, e} W2[c2, c1, e] s1[c1, x+f+e] w1_x[c1, -(f+e)],
+    w1_x[c1, u] = W1[c1, 0, u] + rho_x W1[c1, 2, u]
+(phi_x enters h1 through the phi channel and through the rho phi channel),
 with s = tanh'(h) = 1 - a^2, every position inside the box and -(f+e) a
 valid kernel offset.  Arrays are (C, Lz, Ly, Lx).
 """
@@ -59,7 +61,7 @@ def conv(a, W, b=None):
 
 
 def forward(phi, rho, p):
-    psi = np.stack([phi, rho])
+    psi = np.stack([phi, rho, rho * phi])
     h1 = conv(psi, p["W1"], p["b1"])
     a1 = np.tanh(h1)
     h2 = conv(a1, p["W2"], p["b2"])
@@ -95,10 +97,12 @@ def divergence(phi, rho, p, region=None):
             if max(abs(v) for v in u) > 1:
                 continue
             w1 = W1[:, 0, u[0] + 1, u[1] + 1, u[2] + 1]  # (c1,)
+            w1r = W1[:, 2, u[0] + 1, u[1] + 1, u[2] + 1]  # (c1,), times rho_x
             w2 = W2[:, :, eo[0] + 1, eo[1] + 1, eo[2] + 1]  # (c2, c1)
             # s1 at x+f+e, defined only where x+f is inside (s2f carries that)
             s1fe = _shift(_shift(s1, eo), fo)
             inner = np.tensordot(w2 * w1[None, :], s1fe, axes=(1, 0))  # (c2, Z, Y, X)
+            inner += rho[None] * np.tensordot(w2 * w1r[None, :], s1fe, axes=(1, 0))
             total += float(np.sum(w3[:, None, None, None] * s2f * inner * mask))
     return total
 
@@ -124,7 +128,7 @@ def stein_term(phi, rho, p, region=None):
 def random_params(seed, scale=0.3):
     rng = np.random.default_rng(seed)
     return {
-        "W1": rng.standard_normal((16, 2, 3, 3, 3)) * scale,
+        "W1": rng.standard_normal((16, 3, 3, 3, 3)) * scale,
         "b1": rng.standard_normal(16) * 0.1,
         "W2": rng.standard_normal((16, 16, 3, 3, 3)) * scale / 4,
         "b2": rng.standard_normal(16) * 0.1,

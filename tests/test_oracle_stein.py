@@ -10,7 +10,13 @@ import math
 import numpy as np
 
 
-def test_divergence_matches_finite_differences():
+import pytest
+
+
+@pytest.mark.parametrize("only_rho_phi", [False, True])
+def test_divergence_matches_finite_differences(only_rho_phi):
+    """With only_rho_phi, phi reaches the net through the rho phi channel
+    alone, so the divergence is entirely the rho_x W1[:, 2] term."""
     from oracle import stein
     rng = np.random.default_rng(0)
     Z, Y, X = 3, 4, 5
@@ -18,6 +24,8 @@ def test_divergence_matches_finite_differences():
     rho = np.zeros((Z, Y, X))
     rho[1, 2, 3], rho[0, 1, 1] = 1.0, -1.0
     p = stein.random_params(1)
+    if only_rho_phi:
+        p["W1"][:, 0] = 0.0
     div = stein.divergence(phi, rho, p)
     h = 1e-5
     fd = 0.0
@@ -67,7 +75,7 @@ def test_region_divergence_matches_finite_differences():
     Z, Y, X = 5, 6, 7
     phi = rng.standard_normal((Z, Y, X))
     rho = np.zeros((Z, Y, X))
-    rho[2, 3, 3] = 1.0
+    rho[2, 3, 3], rho[2, 3, 1] = 1.0, 0.7  # one charge outside the region, one inside
     p = stein.random_params(4)
     region = ((1, 4), (2, 5), (0, 3))
     m = stein.region_mask(phi.shape, region)
