@@ -59,12 +59,12 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--schedule", choices=["phased", "aligned"], default="aligned")
-    ap.add_argument("--cv-steps", type=int, default=300)
+    ap.add_argument("--cv-steps", type=int, default=800)
     ap.add_argument("--cv-rounds", type=int, default=64)
     ap.add_argument("--cube-seconds", type=float, default=600.0)
     ap.add_argument("--cv-halo", type=int, default=3,
                     help="the localized control variate's g lives within this many sites of the charges")
-    ap.add_argument("--cv-collect", type=int, default=64,
+    ap.add_argument("--cv-collect", type=int, default=512,
                     help="training rounds (every chain contributes one sample per round)")
     ap.add_argument("--cv-global", action="store_true",
                     help="also run the whole-lattice control variate on the +-1 system")
@@ -490,12 +490,12 @@ def cv_local_cube(args, stream):
     lat.sweep(300, N_HB, N_OR)
     lat.sync()
     t0 = time.perf_counter()
-    phis, Aphis, es = stein.collect_region(cv, lat, ch, rho, n_rounds=args.cv_collect, every=2,
+    phis, Aphis, es = stein.collect_region(cv, lat, ch, rho, n_rounds=args.cv_collect, every=1,
                                            n_hb=N_HB, n_or=N_OR)
     t_collect = time.perf_counter() - t0
     log = []
     t0 = time.perf_counter()
-    tg_fit = stein.fit_region(cv, phis, Aphis, es, rho, steps=args.cv_steps, batch=128, lr=3e-3,
+    tg_fit = stein.fit_region(cv, phis, Aphis, es, rho, steps=args.cv_steps, batch=256, lr=3e-3,
                               log=log)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
@@ -503,16 +503,21 @@ def cv_local_cube(args, stream):
     e_ho, t_ho = es[n_tr:].numpy(), tg_fit[n_tr:].cpu().numpy()
     ratio_holdout = float(np.var(e_ho - cv.c * t_ho) / np.var(e_ho))
     del phis, Aphis
+    # the CV evaluation and recording as one CUDA graph of library kernels
+    graph, tg = cv.record_graph(lat, ch, rho)
+
+    def cv_step():
+        with torch.cuda.stream(stream):
+            graph.replay()
+
     # cost of one compound sweep with and without the CV, on the device
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-    tg = torch.empty(N_CHAINS, dtype=torch.float64, device="cuda")
     ms_plain = ms_cv = 0.0
     for r in range(20):
         ev[0].record(stream)
         ch.run(0, 1, N_HB, N_OR)
         ev[1].record(stream)
-        cv.evaluate(lat, rho, out=tg)
-        ch.cv_record(tg.data_ptr(), cv.c)
+        cv_step()
         ev[2].record(stream)
         stream.synchronize()
         if r >= 5:
@@ -527,8 +532,7 @@ def cv_local_cube(args, stream):
     while time.perf_counter() - t0 < args.cube_seconds:
         for _ in range(250):
             ch.run(0, 1, N_HB, N_OR)
-            cv.evaluate(lat, rho, out=tg)
-            ch.cv_record(tg.data_ptr(), cv.c)
+            cv_step()
         rounds += 250
         cvest = ch.cv_estimate()
         if cvest["stderr"] == cvest["stderr"] and cvest["stderr"] <= target and rounds >= 2000:

@@ -292,16 +292,20 @@ int coulps_batch_field_get(coulps_batch_t b, int system, double *host_xyz);
  *   in_bf16 device [nb][Lz][Ly][Lx][16] BF16, channels last (16-byte aligned)
  *   wpack   device, the 27 x 256 BF16 of coulps_cv_pack_weights
  *   bias    device, 16 floats;  out device [nb][Lz][Ly][Lx][16] FP32
+ *   x_period 0, or P > 0: the output columns x with x % P == P - 1 are set to
+ *           0 (the gutters of the interleaved box layout, see
+ *           coulps_cv_pack_region, stay 0 from layer to layer)
  *   err     device int; a timed-out wait ORs COULPS_ERR bit 1 into it
  * Asynchronous on stream.  Errors: EINVAL, ECUDA. */
 int coulps_cv_pack_weights(const float *w, uint16_t *wpack);
 int coulps_cv_conv3d(const void *in_bf16, const void *wpack, const float *bias, float *out,
-                     int nb, int Lx, int Ly, int Lz, int *err, void *stream);
+                     int nb, int Lx, int Ly, int Lz, int x_period, int *err, void *stream);
 /* Same convolution with the activation fused into its epilogue: writes
- * a = tanh(h) and s = 1 - a^2 as BF16 [nb][Lz][Ly][Lx][16] (16-byte aligned). */
+ * a = tanh(h) and s = 1 - a^2 as BF16 [nb][Lz][Ly][Lx][16] (16-byte aligned);
+ * gutter columns get a = 0, s = 1. */
 int coulps_cv_conv3d_tanh(const void *in_bf16, const void *wpack, const float *bias,
-                          void *a_bf16, void *s_bf16, int nb, int Lx, int Ly, int Lz, int *err,
-                          void *stream);
+                          void *a_bf16, void *s_bf16, int nb, int Lx, int Ly, int Lz,
+                          int x_period, int *err, void *stream);
 
 /* coulps_cv_conv3d_wgrad: weight gradient of coulps_cv_conv3d,
  *   dW[co][ci][o] = sum_{b, p} dh[b, p, co] a[b, p + o, ci]   (a = 0 outside),
@@ -313,20 +317,25 @@ int coulps_cv_conv3d_wgrad(const void *a_bf16, const void *dh_bf16, float *dW, i
                            int Ly, int Lz, float *scratch, int64_t scratch_floats, void *stream);
 
 /* coulps_cv_pack_field: the net's input for every chain of an FP32 lattice,
- * on the lattice's stream: act[chain][z][y][x][16] BF16 = (phi, rho, 0, ...)
- * and Aphi[chain][z][y][x] = (A phi) = 6 phi - (sum of the six neighbours),
+ * on the lattice's stream: act[chain][z][y][x][16] BF16 = (phi, rho, rho phi,
+ * 0, ...) and Aphi[chain][z][y][x] = (A phi) = 6 phi - (sum of the six neighbours),
  * phi = 0 outside the box (the gradient of H_L).  rho: device Lz*Ly*Lx floats
  * (charge density per site).  act must be 16-byte aligned.
  * coulps_cv_activate: a = tanh(h), s = 1 - a^2 (BF16) for n floats h. */
 int coulps_cv_pack_field(coulps_lattice_t lat, const float *rho, void *act_bf16, float *Aphi);
 int coulps_cv_activate(const float *h, void *a_bf16, void *s_bf16, int64_t n, void *stream);
 /* coulps_cv_pack_region: the same for the sub-box E = [origin, origin + dims)
- * (x, y, z order) of every chain, act[chain][ez][ey][ex][16] and
- * Aphi[chain][ez][ey][ex] in E's own coordinates; A phi is taken from the full
- * field (neighbours outside E but inside the box count).  rho is the full
+ * (x, y, z order) of every chain, in E's own coordinates; A phi is taken from
+ * the full field (neighbours outside E but inside the box count).  interleave
+ * 0: act[chain][ez][ey][ex][16], Aphi[chain][ez][ey][ex].  interleave 1: the
+ * chains' boxes side by side along x, each followed by one zero column:
+ * act[ez][ey][chain][ex + 1][16], Aphi likewise, i.e. one lattice of
+ * n_chains (ex + 1) x ey x ez sites on which coulps_cv_conv3d with
+ * x_period = ex + 1 and nb = 1 convolves every box with its own zero padding
+ * (the small boxes then fill the tensor-core tiles).  rho is the full
  * box's density.  Errors: EINVAL (E not inside the box), EUNSUPPORTED (FP64). */
 int coulps_cv_pack_region(coulps_lattice_t lat, const float *rho, const int32_t *origin,
-                          const int32_t *dims, void *act_bf16, float *Aphi);
+                          const int32_t *dims, int interleave, void *act_bf16, float *Aphi);
 
 /* coulps_cv_stein_sum: per chain b, the Stein term of the net,
  *   out[b] = sum_x (dg_x/dphi_x - g_x (A phi)_x)
@@ -353,13 +362,35 @@ int coulps_cv_stein_sum(const float *g16, const float *D, const void *s2_bf16, c
  * 216 x 16 x 16 x 27 floats) holds one K per class ix + 6 iy + 36 iz, the
  * per-axis index of the allowed set {-1} 0, {0} 1, {-1, 0} 2, {1} 3,
  * {0, 1} 4, {-1, 0, 1} 5 (f = -1 is bit 0).  g16 [b][E][16] FP32 (channel 0
- * read), s1, s2 BF16 [b][E][16], Aphi [b][E].  Sums in FP64, fixed order.
- * scratch >= 64 * nb doubles; out device nb doubles.  Asynchronous.  Errors:
- * EINVAL, ECUDA. */
+ * read), s1, s2 BF16 [b][E][16] (16-byte aligned), Aphi [b][E], all in the
+ * layout `interleave` of coulps_cv_pack_region (gutters are not read).  Each
+ * site's sum over c1, e is FP32; the sums over sites are FP64 in a fixed
+ * order.  scratch >= nb * |(R + 1) within E| doubles; out device nb doubles
+ * (overwritten).  Asynchronous.  Errors: EINVAL, ECUDA. */
 int coulps_cv_stein_region(const float *g16, const void *s1_bf16, const void *s2_bf16,
                            const float *Aphi, const float *Ktab, int nb, const int32_t *edims,
-                           const int32_t *lo, const int32_t *hi, double *scratch,
+                           int interleave, const int32_t *lo, const int32_t *hi, double *scratch,
                            int64_t scratch_doubles, double *out, void *stream);
+
+/* coulps_cv_charge_term: the part of the divergence that comes through the
+ * net's third input channel rho phi (coulps_cv_pack_field writes
+ * act = (phi, rho, rho phi, 0, ...)), which the kernels above leave out:
+ *   out[b] += sum_k rho_k sum_p sum_c2 s2[c2, x_k + f_p]
+ *                         sum_c1 M[p][c2][c1] s1[c1, x_k + f_p + e_p]
+ * with M[p][c2][c1] = W3[c2][f_p] W2[c2][c1][e_p] W1[c1][2][-(f_p + e_p)]
+ * over the 343 pairs p = 49 az + 7 ay + ax, per axis a = 0..6 standing for
+ * (f, e) = (-1,0) (-1,1) (0,-1) (0,0) (0,1) (1,-1) (1,0); positions outside
+ * the box (edims = x, y, z sizes) count as 0.  q_xyz (device, n_q x 3
+ * int32, inside the box, box coordinates) and q_rho (device, n_q floats) are
+ * the charge sites whose g is kept (all of them, or those inside R for
+ * coulps_cv_stein_region) and their density.  M device 343 x 16 x 16 floats;
+ * s1, s2 in the layout `interleave` (s1 and M 16-byte aligned).  Summed in
+ * FP64, charges in order.  scratch >= 7 * nb * n_q doubles.  Asynchronous.
+ * Errors: EINVAL, ECUDA. */
+int coulps_cv_charge_term(const void *s1_bf16, const void *s2_bf16, const float *M,
+                          const int32_t *q_xyz, const float *q_rho, int n_q, int nb,
+                          const int32_t *edims, int interleave, double *scratch,
+                          int64_t scratch_doubles, double *out, void *stream);
 
 /* Control-variate estimator, kept beside the plain one of a charge set:
  * coulps_cv_record adds to chain b's CV statistics the sample

@@ -39,7 +39,7 @@ EXPORTS = (
     "coulps_cv_conv3d_wgrad", "coulps_cv_pack_field", "coulps_cv_activate", "coulps_cv_stein_sum",
     "coulps_set_schedule", "coulps_cv_conv3d_tanh", "coulps_cv_pack_region",
     "coulps_cv_stein_region", "coulps_cv_record", "coulps_cv_chain_stats", "coulps_cv_estimate",
-    "coulps_cv_reset",
+    "coulps_cv_reset", "coulps_cv_charge_term",
 )
 SCHEDULE_ALIGNED, SCHEDULE_PHASED = 0, 1
 STAT_STRIDE = 72
@@ -111,20 +111,23 @@ def load(path: str | Path | None = None):
         "coulps_batch_samples": (i32, [vp, P(f64), i64, P(i64)]),
         "coulps_batch_field_get": (i32, [vp, i32, P(f64)]),
         "coulps_cv_pack_weights": (i32, [P(ctypes.c_float), P(ctypes.c_uint16)]),
-        "coulps_cv_conv3d": (i32, [vp, vp, vp, vp, i32, i32, i32, i32, vp, vp]),
+        "coulps_cv_conv3d": (i32, [vp, vp, vp, vp, i32, i32, i32, i32, i32, vp, vp]),
         "coulps_cv_conv3d_wgrad": (i32, [vp, vp, vp, i32, i32, i32, i32, vp, i64, vp]),
         "coulps_cv_pack_field": (i32, [vp, vp, vp, vp]),
         "coulps_cv_activate": (i32, [vp, vp, vp, i64, vp]),
         "coulps_cv_stein_sum": (i32, [vp, vp, vp, vp, vp, vp, i32, i32, i32, i32, vp, i64, vp, vp]),
         "coulps_set_schedule": (i32, [vp, i32]),
-        "coulps_cv_conv3d_tanh": (i32, [vp, vp, vp, vp, vp, i32, i32, i32, i32, vp, vp]),
-        "coulps_cv_pack_region": (i32, [vp, vp, P(ctypes.c_int32), P(ctypes.c_int32), vp, vp]),
-        "coulps_cv_stein_region": (i32, [vp, vp, vp, vp, vp, i32, P(ctypes.c_int32),
+        "coulps_cv_conv3d_tanh": (i32, [vp, vp, vp, vp, vp, i32, i32, i32, i32, i32, vp, vp]),
+        "coulps_cv_pack_region": (i32, [vp, vp, P(ctypes.c_int32), P(ctypes.c_int32), i32, vp,
+                                        vp]),
+        "coulps_cv_stein_region": (i32, [vp, vp, vp, vp, vp, i32, P(ctypes.c_int32), i32,
                                          P(ctypes.c_int32), P(ctypes.c_int32), vp, i64, vp, vp]),
         "coulps_cv_record": (i32, [vp, vp, f64]),
         "coulps_cv_chain_stats": (i32, [vp, P(f64), i64]),
         "coulps_cv_estimate": (i32, [vp, P(f64), P(f64), P(f64), P(i64)]),
         "coulps_cv_reset": (i32, [vp]),
+        "coulps_cv_charge_term": (i32, [vp, vp, vp, vp, vp, i32, i32, P(ctypes.c_int32), i32, vp,
+                                        i64, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)

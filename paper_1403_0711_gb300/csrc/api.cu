@@ -1040,11 +1040,11 @@ int coulps_kernel_times(coulps_lattice_t L, double out[6]) {
 int coulps_cv_pack_field(coulps_lattice_t L, const float *rho, void *act_bf16, float *Aphi) {
   if (!L) return COULPS_EINVAL;
   const int32_t origin[3] = {0, 0, 0}, dims[3] = {L->g.Lx, L->g.Ly, L->g.Lz};
-  return coulps_cv_pack_region(L, rho, origin, dims, act_bf16, Aphi);
+  return coulps_cv_pack_region(L, rho, origin, dims, 0, act_bf16, Aphi);
 }
 
 int coulps_cv_pack_region(coulps_lattice_t L, const float *rho, const int32_t *origin,
-                          const int32_t *dims, void *act_bf16, float *Aphi) {
+                          const int32_t *dims, int interleave, void *act_bf16, float *Aphi) {
   if (!L || !rho || !origin || !dims || !act_bf16 || !Aphi) return COULPS_EINVAL;
   if (L->g.precision != COULPS_F32) return COULPS_EUNSUPPORTED;
   if (reinterpret_cast<uintptr_t>(act_bf16) & 15) return COULPS_EINVAL;
@@ -1055,7 +1055,8 @@ int coulps_cv_pack_region(coulps_lattice_t L, const float *rho, const int32_t *o
     o[k] = origin[k];
     d[k] = dims[k];
   }
-  return coulps_cv_pack_field_impl(L->field, L->g, rho, act_bf16, Aphi, o, d, L->stream);
+  return coulps_cv_pack_field_impl(L->field, L->g, rho, act_bf16, Aphi, o, d, interleave != 0,
+                                   L->stream);
 }
 
 // ---- checkpoint ------------------------------------------------------------

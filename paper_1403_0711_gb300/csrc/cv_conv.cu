@@ -129,6 +129,7 @@ struct CvConvArgs {
   __nv_bfloat16 *out_a, *out_s;  // mode 1: tanh(h), 1 - tanh(h)^2, BF16
   int mode;
   int Lx, Ly, Lz, nb;
+  int x_period;        // > 0: output columns x with x % x_period == x_period - 1 are 0
   int n_cols;          // nb * Lz * ceil(Lx / 128): one column = all y of (b, z, x tile)
   int *err;
 };
@@ -190,6 +191,10 @@ __global__ void __launch_bounds__(kCvThreads)
     const int x = x0 + 32 * warp + lane;
     if (x < a.Lx) {
       const size_t site = (((size_t)b * a.Lz + z) * a.Ly + y) * a.Lx + x;
+      if (a.x_period > 0 && x % a.x_period == a.x_period - 1) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = -bias[i];  // the gutter column stays 0
+      }
       if (a.mode == 0) {
         float4 *o4 = reinterpret_cast<float4 *>(a.out + site * 16);
 #pragma unroll
@@ -321,8 +326,8 @@ __global__ void __launch_bounds__(kCvThreads)
 }  // namespace
 
 int cv_conv3d_launch(const void *in_bf16, const void *wpack, const float *bias, float *out,
-                     void *out_a, void *out_s, int nb, int Lx, int Ly, int Lz, int *err,
-                     cudaStream_t s) {
+                     void *out_a, void *out_s, int nb, int Lx, int Ly, int Lz, int x_period,
+                     int *err, cudaStream_t s) {
   auto enc = tensor_map_encoder();
   if (!enc) return COULPS_ECUDA;
   CUtensorMap map;
@@ -343,6 +348,7 @@ int cv_conv3d_launch(const void *in_bf16, const void *wpack, const float *bias, 
   a.out_s = reinterpret_cast<__nv_bfloat16 *>(out_s);
   a.mode = out ? 0 : 1;
   a.Lx = Lx; a.Ly = Ly; a.Lz = Lz; a.nb = nb;
+  a.x_period = x_period;
   a.n_cols = nb * Lz * ((Lx + kTileX - 1) / kTileX);
   a.err = err;
   static bool configured = false;
@@ -397,27 +403,27 @@ extern "C" int coulps_cv_pack_weights(const float *w, uint16_t *out) {
 }
 
 extern "C" int coulps_cv_conv3d(const void *in_bf16, const void *wpack, const float *bias,
-                                float *out, int nb, int Lx, int Ly, int Lz, int *err,
-                                void *stream) {
+                                float *out, int nb, int Lx, int Ly, int Lz, int x_period,
+                                int *err, void *stream) {
   if (!in_bf16 || !wpack || !bias || !out || !err) return COULPS_EINVAL;
-  if (nb < 1 || Lx < 1 || Ly < 1 || Lz < 1) return COULPS_EINVAL;
+  if (nb < 1 || Lx < 1 || Ly < 1 || Lz < 1 || x_period < 0) return COULPS_EINVAL;
   if ((int64_t)nb * Lz * ((Lx + 127) / 128) > 0x7fffffff) return COULPS_EINVAL;
   const uintptr_t align = reinterpret_cast<uintptr_t>(in_bf16) | reinterpret_cast<uintptr_t>(wpack) |
                           reinterpret_cast<uintptr_t>(out);
   if (align & 15) return COULPS_EINVAL;
   return coulps::cv_conv3d_launch(in_bf16, wpack, bias, out, nullptr, nullptr, nb, Lx, Ly, Lz,
-                                  err, static_cast<cudaStream_t>(stream));
+                                  x_period, err, static_cast<cudaStream_t>(stream));
 }
 
 extern "C" int coulps_cv_conv3d_tanh(const void *in_bf16, const void *wpack, const float *bias,
                                      void *a_bf16, void *s_bf16, int nb, int Lx, int Ly, int Lz,
-                                     int *err, void *stream) {
+                                     int x_period, int *err, void *stream) {
   if (!in_bf16 || !wpack || !bias || !a_bf16 || !s_bf16 || !err) return COULPS_EINVAL;
-  if (nb < 1 || Lx < 1 || Ly < 1 || Lz < 1) return COULPS_EINVAL;
+  if (nb < 1 || Lx < 1 || Ly < 1 || Lz < 1 || x_period < 0) return COULPS_EINVAL;
   if ((int64_t)nb * Lz * ((Lx + 127) / 128) > 0x7fffffff) return COULPS_EINVAL;
   const uintptr_t align = reinterpret_cast<uintptr_t>(in_bf16) | reinterpret_cast<uintptr_t>(wpack) |
                           reinterpret_cast<uintptr_t>(a_bf16) | reinterpret_cast<uintptr_t>(s_bf16);
   if (align & 15) return COULPS_EINVAL;
   return coulps::cv_conv3d_launch(in_bf16, wpack, bias, nullptr, a_bf16, s_bf16, nb, Lx, Ly, Lz,
-                                  err, static_cast<cudaStream_t>(stream));
+                                  x_period, err, static_cast<cudaStream_t>(stream));
 }

@@ -21,6 +21,7 @@
 //   K_b[c2, c1, e] = W2[c2, c1, e] sum_{f in F_b} W3[c2, f] W1[c1, phi, -(e + f)],
 // where F_b holds the offsets f whose x = q - f lies inside the box; for q
 // off the faces F_b is all 27 offsets and K_b = K.
+#include <algorithm>
 #include <cstdint>
 
 #include <cuda_bf16.h>
@@ -31,6 +32,33 @@
 namespace coulps {
 namespace {
 
+// Site offsets of a batch of nb boxes ex x ey x ez: site (b, z, y, x) at
+// b sb + z sz + y sy + x.  Dense: [b][z][y][x].  Interleaved: the boxes sit
+// side by side along x, each followed by one zero column (a gutter), i.e. one
+// (nb (ex + 1)) x ey x ez lattice whose 3x3x3 convolutions equal the boxes'
+// own with zero padding as long as the gutters stay 0.  xw: columns per box
+// row in memory.
+struct BoxLayout {
+  int64_t sb, sz, sy;
+  int xw;
+};
+
+inline BoxLayout box_layout(int interleave, int nb, int ex, int ey, int ez) {
+  BoxLayout L;
+  if (interleave) {
+    L.xw = ex + 1;
+    L.sb = L.xw;
+    L.sy = (int64_t)nb * L.xw;
+    L.sz = L.sy * ey;
+  } else {
+    L.xw = ex;
+    L.sb = (int64_t)ex * ey * ez;
+    L.sz = (int64_t)ex * ey;
+    L.sy = ex;
+  }
+  return L;
+}
+
 __device__ __forceinline__ float ld_field(const float *f, const Geometry &g, int chain, int x,
                                           int y, int z) {
   if (x < 0 || y < 0 || z < 0 || x >= g.Lx || y >= g.Ly || z >= g.Lz) return 0.f;
@@ -40,28 +68,38 @@ __device__ __forceinline__ float ld_field(const float *f, const Geometry &g, int
 }
 
 // Packs the sub-box [o, o + e) of every chain (the whole box when o = 0,
-// e = L): rho is the full box's density.
+// e = L) into the layout L: rho is the full box's density.  Columns x >= e
+// of a box row (the interleaved layout's gutter) are written as 0.
 __global__ void cv_pack_kernel(const float *__restrict__ field, Geometry g,
                                const float *__restrict__ rho, __nv_bfloat16 *__restrict__ act,
                                float *__restrict__ Aphi, int ox, int oy, int oz, int ex, int ey,
-                               int ez) {
-  const int64_t sites = (int64_t)ex * ey * ez;
+                               int ez, BoxLayout L) {
+  const int64_t n = (int64_t)L.xw * ey * ez;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int chain = blockIdx.y;
-  if (i >= sites) return;
-  const int x = ox + (int)(i % ex), y = oy + (int)((i / ex) % ey), z = oz + (int)(i / ((int64_t)ex * ey));
+  if (i >= n) return;
+  const int xl = (int)(i % L.xw), yl = (int)((i / L.xw) % ey), zl = (int)(i / ((int64_t)L.xw * ey));
+  const int64_t o = (int64_t)chain * L.sb + zl * L.sz + yl * L.sy + xl;
+  __align__(16) __nv_bfloat16 v[16];
+  uint4 *dst = reinterpret_cast<uint4 *>(act + o * 16);
+  if (xl >= ex) {
+    Aphi[o] = 0.f;
+    dst[0] = make_uint4(0, 0, 0, 0);
+    dst[1] = make_uint4(0, 0, 0, 0);
+    return;
+  }
+  const int x = ox + xl, y = oy + yl, z = oz + zl;
   const float p = ld_field(field, g, chain, x, y, z);
   const float S = ld_field(field, g, chain, x - 1, y, z) + ld_field(field, g, chain, x + 1, y, z) +
                   ld_field(field, g, chain, x, y - 1, z) + ld_field(field, g, chain, x, y + 1, z) +
                   ld_field(field, g, chain, x, y, z - 1) + ld_field(field, g, chain, x, y, z + 1);
-  const int64_t o = (int64_t)chain * sites + i;
   Aphi[o] = 6.f * p - S;
-  __align__(16) __nv_bfloat16 v[16];
+  const float r = rho[((int64_t)z * g.Ly + y) * g.Lx + x];
   v[0] = __float2bfloat16_rn(p);
-  v[1] = __float2bfloat16_rn(rho[((int64_t)z * g.Ly + y) * g.Lx + x]);
+  v[1] = __float2bfloat16_rn(r);
+  v[2] = __float2bfloat16_rn(r * p);
 #pragma unroll
-  for (int k = 2; k < 16; ++k) v[k] = __float2bfloat16_rn(0.f);
-  uint4 *dst = reinterpret_cast<uint4 *>(act + o * 16);
+  for (int k = 3; k < 16; ++k) v[k] = __float2bfloat16_rn(0.f);
   dst[0] = reinterpret_cast<const uint4 *>(v)[0];
   dst[1] = reinterpret_cast<const uint4 *>(v)[1];
 }
@@ -191,68 +229,208 @@ __global__ void cv_sum_partials_kernel(const double *__restrict__ partials, int 
 // Region Stein term: g is the net inside R = [lo, hi) (in E coordinates) and
 // 0 outside.  For q within one site of R the divergence picks the offsets f
 // with q - f inside R: per axis a mask over f in {-1, 0, 1} (bit f + 1),
-// mapped to an index 0..5, class = ix + 6 iy + 36 iz.  K[class][c2][c1][e].
-__device__ __forceinline__ int allowed_index(int q, int lo, int hi) {
-  int m = 0;
-#pragma unroll
-  for (int f = -1; f <= 1; ++f)
-    if (q - f >= lo && q - f < hi) m |= 1 << (f + 1);
-  // masks 1, 2, 3, 4, 6, 7 -> 0..5; 0 (not next to R) -> -1
-  switch (m) {
-    case 1: return 0;
-    case 2: return 1;
-    case 3: return 2;
-    case 4: return 3;
-    case 6: return 4;
-    case 7: return 5;
-    default: return -1;
-  }
-}
+// masks 1, 2, 3, 4, 6, 7 mapped to the index 0..5, class = ix + 6 iy + 36 iz;
+// Ktab holds K[class][c2][c1][e].
+// The sites q next to R split, per axis, into at most 5 runs of one class
+// (q = lo-1, q = lo, lo < q < hi-1, q = hi-1, q = hi, clipped to E and merged
+// when R is thin), so R + 1 is a union of at most 125 boxes of one class each.
+// One CTA takes up to kRedThreads (q, chain) items of one box: it stages the
+// box's kernel K[class] in shared memory as [e][c2][c1] and each thread forms
+// D[c2] = sum_{c1, e} K[c2][c1][e] s1[c1, q + e] for its item (K reads are
+// warp-wide broadcasts, four FMAs per 16-byte load), then s2[q] . D.
+struct RegionRuns {
+  int start[3][5], len[3][5], cls[3][5];
+  int nrun[3];
+  int n_box;               // nrun[0] * nrun[1] * nrun[2]
+  int cta_first[126];      // first CTA of each box (prefix over boxes)
+  int ex, ey, ez;          // E
+  int nqx, nqy, nqz;       // R + 1 within E: offsets of the partial buffer
+  int qx0, qy0, qz0;
+  int nb;
+  BoxLayout L;
+};
+
+constexpr int kRegionKFloats = 27 * 16 * 16;
 
 __global__ void __launch_bounds__(kRedThreads)
-    cv_region_partial_kernel(const float *__restrict__ g16, const __nv_bfloat16 *__restrict__ s1,
-                             const __nv_bfloat16 *__restrict__ s2, const float *__restrict__ Aphi,
-                             const float *__restrict__ Ktab, int ex, int ey, int ez, int lox,
-                             int loy, int loz, int hix, int hiy, int hiz,
-                             double *__restrict__ partials) {
-  const int chain = blockIdx.y;
-  const int64_t sites = (int64_t)ex * ey * ez;
-  // divergence over q in (R + 1) within E, one thread per (q, c2)
-  const int qx0 = max(lox - 1, 0), qy0 = max(loy - 1, 0), qz0 = max(loz - 1, 0);
-  const int qx1 = min(hix + 1, ex), qy1 = min(hiy + 1, ey), qz1 = min(hiz + 1, ez);
-  const int nqx = qx1 - qx0, nqy = qy1 - qy0, nqz = qz1 - qz0;
-  const int64_t nq = (int64_t)nqx * nqy * nqz;
-  double acc = 0.0;
-  for (int64_t t = (int64_t)blockIdx.x * kRedThreads + threadIdx.x; t < nq * 16;
-       t += (int64_t)gridDim.x * kRedThreads) {
-    const int c2 = (int)(t & 15);
-    const int64_t k = t >> 4;
-    const int x = qx0 + (int)(k % nqx), y = qy0 + (int)((k / nqx) % nqy), z = qz0 + (int)(k / ((int64_t)nqx * nqy));
-    const int ix = allowed_index(x, lox, hix), iy = allowed_index(y, loy, hiy),
-              iz = allowed_index(z, loz, hiz);
-    if (ix < 0 || iy < 0 || iz < 0) continue;
-    const float *kk = Ktab + ((size_t)(ix + 6 * iy + 36 * iz) * 16 + c2) * 16 * 27;
-    float d = 0.f;
-    for (int e = 0; e < 27; ++e) {
-      const int xx = x + e % 3 - 1, yy = y + (e / 3) % 3 - 1, zz = z + e / 9 - 1;
-      if (xx < 0 || yy < 0 || zz < 0 || xx >= ex || yy >= ey || zz >= ez) continue;
-      const __nv_bfloat16 *sp = s1 + ((int64_t)chain * sites + ((int64_t)zz * ey + yy) * ex + xx) * 16;
-#pragma unroll
-      for (int c1 = 0; c1 < 16; ++c1) d = fmaf(kk[c1 * 27 + e], __bfloat162float(sp[c1]), d);
-    }
-    acc += (double)__bfloat162float(s2[((int64_t)chain * sites + ((int64_t)z * ey + y) * ex + x) * 16 + c2]) *
-           (double)d;
+    cv_region_div_kernel(const __nv_bfloat16 *__restrict__ s1, const __nv_bfloat16 *__restrict__ s2,
+                         const float *__restrict__ Ktab, const RegionRuns r,
+                         double *__restrict__ part) {
+  __shared__ __align__(16) float K[kRegionKFloats];  // [e][c2][c1]
+  int box = 0;
+  while (box + 1 < r.n_box && r.cta_first[box + 1] <= (int)blockIdx.x) ++box;
+  const int bx = box % r.nrun[0], by = (box / r.nrun[0]) % r.nrun[1], bz = box / (r.nrun[0] * r.nrun[1]);
+  const int cls = r.cls[0][bx] + 6 * r.cls[1][by] + 36 * r.cls[2][bz];
+  const float *kg = Ktab + (size_t)cls * kRegionKFloats;  // [c2][c1][e]
+  for (int i = threadIdx.x; i < kRegionKFloats; i += kRedThreads) {
+    const int e = i % 27, c1 = (i / 27) % 16, c2 = i / (27 * 16);
+    K[(e * 16 + c2) * 16 + c1] = kg[i];
   }
-  // minus sum over x in R of g_x (A phi)_x
+  __syncthreads();
+  const int lx = r.len[0][bx], ly = r.len[1][by], lz = r.len[2][bz];
+  const int nq = lx * ly * lz;
+  const int item = (blockIdx.x - r.cta_first[box]) * kRedThreads + threadIdx.x;
+  if (item >= nq * r.nb) return;
+  const int chain = item / nq, k = item % nq;
+  const int x = r.start[0][bx] + k % lx, y = r.start[1][by] + (k / lx) % ly, z = r.start[2][bz] + k / (lx * ly);
+  const __nv_bfloat16 *s1c = s1 + chain * r.L.sb * 16;
+  float D[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) D[c] = 0.f;
+  for (int e = 0; e < 27; ++e) {
+    const int xx = x + e % 3 - 1, yy = y + (e / 3) % 3 - 1, zz = z + e / 9 - 1;
+    if (xx < 0 || yy < 0 || zz < 0 || xx >= r.ex || yy >= r.ey || zz >= r.ez) continue;
+    const uint4 *sp = reinterpret_cast<const uint4 *>(s1c + (zz * r.L.sz + yy * r.L.sy + xx) * 16);
+    const uint4 u0 = sp[0], u1 = sp[1];
+    float v[16];
+    const __nv_bfloat162 *h0 = reinterpret_cast<const __nv_bfloat162 *>(&u0);
+    const __nv_bfloat162 *h1 = reinterpret_cast<const __nv_bfloat162 *>(&u1);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float2 a = __bfloat1622float2(h0[i]), b = __bfloat1622float2(h1[i]);
+      v[2 * i] = a.x; v[2 * i + 1] = a.y; v[8 + 2 * i] = b.x; v[8 + 2 * i + 1] = b.y;
+    }
+    const float4 *ke = reinterpret_cast<const float4 *>(K + e * 256);
+#pragma unroll
+    for (int c2 = 0; c2 < 16; ++c2) {
+      float d = D[c2];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float4 w = ke[c2 * 4 + j];
+        d = fmaf(w.x, v[4 * j], d);
+        d = fmaf(w.y, v[4 * j + 1], d);
+        d = fmaf(w.z, v[4 * j + 2], d);
+        d = fmaf(w.w, v[4 * j + 3], d);
+      }
+      D[c2] = d;
+    }
+  }
+  const uint4 *sq = reinterpret_cast<const uint4 *>(s2 + (chain * r.L.sb + z * r.L.sz + y * r.L.sy + x) * 16);
+  const uint4 w0 = sq[0], w1 = sq[1];
+  const __nv_bfloat162 *g0 = reinterpret_cast<const __nv_bfloat162 *>(&w0);
+  const __nv_bfloat162 *g1 = reinterpret_cast<const __nv_bfloat162 *>(&w1);
+  float acc = 0.f;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float2 a = __bfloat1622float2(g0[i]), b = __bfloat1622float2(g1[i]);
+    acc = fmaf(a.x, D[2 * i], acc);
+    acc = fmaf(a.y, D[2 * i + 1], acc);
+    acc = fmaf(b.x, D[8 + 2 * i], acc);
+    acc = fmaf(b.y, D[8 + 2 * i + 1], acc);
+  }
+  const int qi = ((z - r.qz0) * r.nqy + (y - r.qy0)) * r.nqx + (x - r.qx0);
+  part[(size_t)chain * ((size_t)r.nqx * r.nqy * r.nqz) + qi] = (double)acc;
+}
+
+// out[b] = sum_q part[b][q] - sum_{x in R} g_x (A phi)_x, one CTA per chain
+__global__ void __launch_bounds__(kRedThreads)
+    cv_region_finish_kernel(const double *__restrict__ part, int nq, const float *__restrict__ g16,
+                            const float *__restrict__ Aphi, BoxLayout L, int lox, int loy,
+                            int loz, int hix, int hiy, int hiz, double *__restrict__ out) {
+  const int chain = blockIdx.x;
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < nq; k += kRedThreads) acc += part[(size_t)chain * nq + k];
   const int nrx = hix - lox, nry = hiy - loy, nrz = hiz - loz;
-  const int64_t nr = (int64_t)nrx * nry * nrz;
-  for (int64_t k = (int64_t)blockIdx.x * kRedThreads + threadIdx.x; k < nr;
-       k += (int64_t)gridDim.x * kRedThreads) {
-    const int x = lox + (int)(k % nrx), y = loy + (int)((k / nrx) % nry), z = loz + (int)(k / ((int64_t)nrx * nry));
-    const int64_t o = (int64_t)chain * sites + ((int64_t)z * ey + y) * ex + x;
+  const int nr = nrx * nry * nrz;
+  for (int k = threadIdx.x; k < nr; k += kRedThreads) {
+    const int x = lox + k % nrx, y = loy + (k / nrx) % nry, z = loz + k / (nrx * nry);
+    const int64_t o = chain * L.sb + z * L.sz + y * L.sy + x;
     acc -= (double)g16[o * 16] * (double)Aphi[o];
   }
-  block_sum_to(acc, partials + (size_t)chain * gridDim.x + blockIdx.x);
+  block_sum_to(acc, out + chain);
+}
+
+// Per-axis runs of one class over q in [lo-1, hi] within [0, e).
+static int axis_runs(int lo, int hi, int e, int *start, int *len, int *cls) {
+  int n = 0;
+  for (int q = lo - 1; q <= hi; ++q) {
+    if (q < 0 || q >= e) continue;
+    int m = 0;
+    for (int f = -1; f <= 1; ++f)
+      if (q - f >= lo && q - f < hi) m |= 1 << (f + 1);
+    const int c = m == 1 ? 0 : m == 2 ? 1 : m == 3 ? 2 : m == 4 ? 3 : m == 6 ? 4 : m == 7 ? 5 : -1;
+    if (c < 0) continue;
+    if (n > 0 && cls[n - 1] == c && start[n - 1] + len[n - 1] == q) {
+      ++len[n - 1];
+    } else {
+      if (n == 5) return -1;  // cannot happen for a box
+      start[n] = q;
+      len[n] = 1;
+      cls[n] = c;
+      ++n;
+    }
+  }
+  return n;
+}
+
+// Charge-site term of the divergence: phi_x also enters h1 through the
+// rho phi channel, with weight rho_x W1[c1][2][u].  For a charge at x,
+//   rho_x sum_p sum_c2 s2[c2, x + f_p] sum_c1 M[p][c2][c1] s1[c1, x + f_p + e_p],
+// over the 343 pairs (f, e) with f + e a kernel offset; per axis the pair
+// index a = 0..6 stands for (f, e) = (-1,0) (-1,1) (0,-1) (0,0) (0,1) (1,-1)
+// (1,0) and p = 49 az + 7 ay + ax.  Positions outside the box are 0.
+__device__ __forceinline__ void pair_axis(int a, int &f, int &e) {
+  f = a < 2 ? -1 : (a < 5 ? 0 : 1);
+  e = a < 2 ? a : (a < 5 ? a - 3 : a - 6);
+}
+
+// One CTA per (charge, 16 chains, az): thread (chain, c2) walks the 49 pairs
+// of one z offset class; the 16 chains of a CTA share each M row.
+__global__ void __launch_bounds__(kRedThreads)
+    cv_charge_partial_kernel(const __nv_bfloat16 *__restrict__ s1,
+                             const __nv_bfloat16 *__restrict__ s2, const float *__restrict__ M,
+                             const int32_t *__restrict__ qxyz, const float *__restrict__ qrho,
+                             int n_q, int nb, int ex, int ey, int ez, BoxLayout L,
+                             double *__restrict__ partials) {
+  const int k = blockIdx.x;
+  const int c2 = threadIdx.x & 15;
+  const int chain = blockIdx.y * (kRedThreads / 16) + (threadIdx.x >> 4);
+  const bool live = chain < nb;
+  const int x = qxyz[3 * k], y = qxyz[3 * k + 1], z = qxyz[3 * k + 2];
+  const __nv_bfloat16 *s1c = s1 + (live ? chain : 0) * L.sb * 16;
+  const __nv_bfloat16 *s2c = s2 + (live ? chain : 0) * L.sb * 16;
+  float acc = 0.f;
+  const int p0 = 49 * blockIdx.z;
+  for (int p = p0; p < p0 + 49 && live; ++p) {
+    int fx, fy, fz, exx, eyy, ezz;
+    pair_axis(p % 7, fx, exx);
+    pair_axis((p / 7) % 7, fy, eyy);
+    pair_axis(p / 49, fz, ezz);
+    const int qx = x + fx, qy = y + fy, qz = z + fz;
+    if (qx < 0 || qy < 0 || qz < 0 || qx >= ex || qy >= ey || qz >= ez) continue;
+    const int rx = qx + exx, ry = qy + eyy, rz = qz + ezz;
+    if (rx < 0 || ry < 0 || rz < 0 || rx >= ex || ry >= ey || rz >= ez) continue;
+    const uint4 *sp = reinterpret_cast<const uint4 *>(s1c + (rz * L.sz + ry * L.sy + rx) * 16);
+    const uint4 u0 = sp[0], u1 = sp[1];
+    const __nv_bfloat162 *h0 = reinterpret_cast<const __nv_bfloat162 *>(&u0);
+    const __nv_bfloat162 *h1 = reinterpret_cast<const __nv_bfloat162 *>(&u1);
+    const float4 *m = reinterpret_cast<const float4 *>(M + ((size_t)p * 16 + c2) * 16);
+    float d = 0.f;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const float2 a0 = __bfloat1622float2(h0[2 * i]), a1 = __bfloat1622float2(h0[2 * i + 1]);
+      const float2 b0 = __bfloat1622float2(h1[2 * i]), b1 = __bfloat1622float2(h1[2 * i + 1]);
+      const float4 wa = m[i], wb = m[2 + i];
+      d = fmaf(wa.x, a0.x, d); d = fmaf(wa.y, a0.y, d); d = fmaf(wa.z, a1.x, d); d = fmaf(wa.w, a1.y, d);
+      d = fmaf(wb.x, b0.x, d); d = fmaf(wb.y, b0.y, d); d = fmaf(wb.z, b1.x, d); d = fmaf(wb.w, b1.y, d);
+    }
+    acc = fmaf(__bfloat162float(s2c[(qz * L.sz + qy * L.sy + qx) * 16 + c2]), d, acc);
+  }
+  // sum over the 16 c2 lanes of this chain (xor butterfly within the half-warp)
+  double v = (double)acc;
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (live && c2 == 0) partials[((size_t)chain * n_q + k) * 7 + blockIdx.z] = v * (double)qrho[k];
+}
+
+// out[b] += sum_k partials[b][k], k in order
+__global__ void cv_add_partials_kernel(const double *__restrict__ partials, int n_q, int nb,
+                                       double *__restrict__ out) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  double s = 0.0;
+  for (int k = 0; k < n_q; ++k) s += partials[(size_t)b * n_q + k];
+  out[b] += s;
 }
 
 constexpr int kWgTile = 64;  // sites of one x row per shared-memory tile
@@ -366,20 +544,64 @@ int coulps_cv_stein_sum(const float *g16, const float *D, const void *s2_bf16, c
 
 int coulps_cv_stein_region(const float *g16, const void *s1_bf16, const void *s2_bf16,
                            const float *Aphi, const float *Ktab, int nb, const int32_t *edims,
-                           const int32_t *lo, const int32_t *hi, double *scratch,
+                           int interleave, const int32_t *lo, const int32_t *hi, double *scratch,
                            int64_t scratch_doubles, double *out, void *stream) {
   if (!g16 || !s1_bf16 || !s2_bf16 || !Aphi || !Ktab || !edims || !lo || !hi || !scratch || !out)
     return COULPS_EINVAL;
   if (nb < 1) return COULPS_EINVAL;
   for (int k = 0; k < 3; ++k)
     if (edims[k] < 1 || lo[k] < 0 || hi[k] > edims[k] || lo[k] >= hi[k]) return COULPS_EINVAL;
-  const int nblk = 64;
-  if (scratch_doubles < (int64_t)nb * nblk) return COULPS_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(s1_bf16) | reinterpret_cast<uintptr_t>(s2_bf16)) & 15)
+    return COULPS_EINVAL;
+  RegionRuns r{};
+  r.ex = edims[0]; r.ey = edims[1]; r.ez = edims[2];
+  r.nb = nb;
+  r.L = box_layout(interleave, nb, edims[0], edims[1], edims[2]);
+  for (int k = 0; k < 3; ++k) {
+    r.nrun[k] = axis_runs(lo[k], hi[k], edims[k], r.start[k], r.len[k], r.cls[k]);
+    if (r.nrun[k] < 1) return COULPS_EINVAL;
+  }
+  r.qx0 = std::max(lo[0] - 1, 0); r.nqx = std::min(hi[0] + 1, edims[0]) - r.qx0;
+  r.qy0 = std::max(lo[1] - 1, 0); r.nqy = std::min(hi[1] + 1, edims[1]) - r.qy0;
+  r.qz0 = std::max(lo[2] - 1, 0); r.nqz = std::min(hi[2] + 1, edims[2]) - r.qz0;
+  const int64_t nq = (int64_t)r.nqx * r.nqy * r.nqz;
+  if (scratch_doubles < nq * nb) return COULPS_EINVAL;
+  r.n_box = r.nrun[0] * r.nrun[1] * r.nrun[2];
+  int64_t ctas = 0;
+  for (int b = 0; b < r.n_box; ++b) {
+    const int bx = b % r.nrun[0], by = (b / r.nrun[0]) % r.nrun[1], bz = b / (r.nrun[0] * r.nrun[1]);
+    const int64_t items = (int64_t)r.len[0][bx] * r.len[1][by] * r.len[2][bz] * nb;
+    r.cta_first[b] = (int)ctas;
+    ctas += (items + kRedThreads - 1) / kRedThreads;
+    if (ctas > 0x7fffffff) return COULPS_EINVAL;
+  }
+  r.cta_first[r.n_box] = (int)ctas;
   cudaStream_t s = (cudaStream_t)stream;
-  cv_region_partial_kernel<<<dim3(nblk, nb), kRedThreads, 0, s>>>(
-      g16, (const __nv_bfloat16 *)s1_bf16, (const __nv_bfloat16 *)s2_bf16, Aphi, Ktab, edims[0],
-      edims[1], edims[2], lo[0], lo[1], lo[2], hi[0], hi[1], hi[2], scratch);
-  cv_sum_partials_kernel<<<(nb + 127) / 128, 128, 0, s>>>(scratch, nblk, nb, out, 0);
+  cv_region_div_kernel<<<(unsigned)ctas, kRedThreads, 0, s>>>(
+      (const __nv_bfloat16 *)s1_bf16, (const __nv_bfloat16 *)s2_bf16, Ktab, r, scratch);
+  cv_region_finish_kernel<<<nb, kRedThreads, 0, s>>>(scratch, (int)nq, g16, Aphi, r.L, lo[0],
+                                                     lo[1], lo[2], hi[0], hi[1], hi[2], out);
+  return cudaGetLastError() == cudaSuccess ? COULPS_OK : COULPS_ECUDA;
+}
+
+int coulps_cv_charge_term(const void *s1_bf16, const void *s2_bf16, const float *M,
+                          const int32_t *q_xyz, const float *q_rho, int n_q, int nb,
+                          const int32_t *edims, int interleave, double *scratch,
+                          int64_t scratch_doubles, double *out, void *stream) {
+  if (!s1_bf16 || !s2_bf16 || !M || !edims || !scratch || !out) return COULPS_EINVAL;
+  if (nb < 1 || n_q < 0 || (n_q > 0 && (!q_xyz || !q_rho))) return COULPS_EINVAL;
+  if (edims[0] < 1 || edims[1] < 1 || edims[2] < 1) return COULPS_EINVAL;
+  if (n_q == 0) return COULPS_OK;
+  if (nb > 65535 * 16) return COULPS_EINVAL;
+  if (scratch_doubles < (int64_t)nb * n_q * 7) return COULPS_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((reinterpret_cast<uintptr_t>(s1_bf16) | reinterpret_cast<uintptr_t>(M)) & 15)
+    return COULPS_EINVAL;
+  cv_charge_partial_kernel<<<dim3(n_q, (nb + 15) / 16, 7), kRedThreads, 0, s>>>(
+      (const __nv_bfloat16 *)s1_bf16, (const __nv_bfloat16 *)s2_bf16, M, q_xyz, q_rho, n_q, nb,
+      edims[0], edims[1], edims[2], box_layout(interleave, nb, edims[0], edims[1], edims[2]),
+      scratch);
+  cv_add_partials_kernel<<<(nb + 127) / 128, 128, 0, s>>>(scratch, 7 * n_q, nb, out);
   return cudaGetLastError() == cudaSuccess ? COULPS_OK : COULPS_ECUDA;
 }
 
@@ -406,11 +628,12 @@ int coulps_cv_conv3d_wgrad(const void *a_bf16, const void *dh_bf16, float *dW, i
 // coulps_cv_pack_field (api.cu) supplies the lattice's geometry and stream.
 int coulps::coulps_cv_pack_field_impl(const void *field, const Geometry &g, const float *rho,
                               void *act_bf16, float *Aphi, const int *origin, const int *dims,
-                              cudaStream_t s) {
-  const int64_t sites = (int64_t)dims[0] * dims[1] * dims[2];
-  dim3 grid((unsigned)((sites + 255) / 256), g.n_chains);
+                              int interleave, cudaStream_t s) {
+  const BoxLayout L = box_layout(interleave, g.n_chains, dims[0], dims[1], dims[2]);
+  const int64_t n = (int64_t)L.xw * dims[1] * dims[2];
+  dim3 grid((unsigned)((n + 255) / 256), g.n_chains);
   cv_pack_kernel<<<grid, 256, 0, s>>>(reinterpret_cast<const float *>(field), g, rho,
                                       (__nv_bfloat16 *)act_bf16, Aphi, origin[0], origin[1],
-                                      origin[2], dims[0], dims[1], dims[2]);
+                                      origin[2], dims[0], dims[1], dims[2], L);
   return cudaGetLastError() == cudaSuccess ? COULPS_OK : COULPS_ECUDA;
 }

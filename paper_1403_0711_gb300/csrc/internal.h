@@ -140,6 +140,6 @@ int gather_blocks(int64_t n);
 // Control variate input packing (cv_ops.cu) for a lattice's FP32 field.
 int coulps_cv_pack_field_impl(const void *field, const Geometry &g, const float *rho,
                               void *act_bf16, float *Aphi, const int *origin, const int *dims,
-                              cudaStream_t s);
+                              int interleave, cudaStream_t s);
 
 }  // namespace coulps

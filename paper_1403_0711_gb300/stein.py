@@ -4,8 +4,8 @@ For the lattice measure exp(-H_L) (Eq. (proplat), phi = 0 outside the box)
 and any smooth vector field g(phi) with one component per site,
     E[ T g ] = 0,   T g = sum_x ( dg_x/dphi_x - g_x (A phi)_x ),   A phi = dH_L/dphi,
 so e_CV = e - c T g has the mean of the plain sample e for any fixed c.
-g is a 3-layer 3x3x3 conv net on the input channels (phi, rho), 16 hidden
-channels, tanh, zero padding; c and the weights are fitted to minimise
+g is a 3-layer 3x3x3 conv net on the input channels (phi, rho, rho phi), 16
+hidden channels, tanh, zero padding; c and the weights are fitted to minimise
 Var(e - c T g) on stored samples of the chain.
 
 All convolutions run in libcoulps.so's tcgen05 kernel (BF16 operands, FP32
@@ -15,7 +15,9 @@ weight-gradient kernel.  The divergence uses the identity
     sum_x dg_x/dphi_x = sum_q sum_c2 s2[c2,q] (conv(s1, K) + face corrections)[c2,q],
     K[c2,c1,e] = W2[c2,c1,e] sum_f W3[c2,f] W1[c1,phi,-(e+f)],
 with s = tanh' of the pre-activations: one extra 16 -> 16 conv plus a
-correction on the box's face sites (where some x = q - f fall outside).
+correction on the box's face sites (where some x = q - f fall outside), plus
+the charge-site term of the rho phi channel (phi_x reaches h1 through it with
+weight rho_x W1[c1, 2]), a 343-pair sum at each charge.
 
 Training runs through autograd (the convs are the library's kernels; the
 elementwise glue is PyTorch).  Evaluation inside the sampler (``evaluate``)
@@ -61,7 +63,7 @@ def conv3d_tc(a: torch.Tensor, W: torch.Tensor, b: torch.Tensor) -> torch.Tensor
     err = torch.zeros(1, dtype=torch.int32, device=a.device)
     wp = pack_weights(W)
     bias = b.detach().float().contiguous()
-    st = coulps.load().coulps_cv_conv3d(_vp(a), _vp(wp), _vp(bias), _vp(out), n, X, Y, Z, _vp(err),
+    st = coulps.load().coulps_cv_conv3d(_vp(a), _vp(wp), _vp(bias), _vp(out), n, X, Y, Z, 0, _vp(err),
                                         _stream())
     coulps._check(st, "coulps_cv_conv3d")
     return out
@@ -77,7 +79,7 @@ def conv3d_tanh_tc(a: torch.Tensor, W: torch.Tensor, b: torch.Tensor):
     wp = pack_weights(W)
     bias = b.detach().float().contiguous()
     st = coulps.load().coulps_cv_conv3d_tanh(_vp(a), _vp(wp), _vp(bias), _vp(act), _vp(der), n, X,
-                                             Y, Z, _vp(err), _stream())
+                                             Y, Z, 0, _vp(err), _stream())
     coulps._check(st, "coulps_cv_conv3d_tanh")
     return act, der
 
@@ -147,6 +149,51 @@ def _pair_tensor():
 _P = _pair_tensor()
 
 
+def _charge_pairs():
+    """The 343 (f, e) with f + e a kernel offset, in the library's order
+    p = 49 az + 7 ay + ax, per axis a -> (f, e) as listed in _AXIS_PAIRS."""
+    fi, ei, ui, fo, feo = [], [], [], [], []
+    for az, ay, ax in itertools.product(range(7), repeat=3):
+        (fz, ez), (fy, ey), (fx, ex) = _AXIS_PAIRS[az], _AXIS_PAIRS[ay], _AXIS_PAIRS[ax]
+        f, e = (fz, fy, fx), (ez, ey, ex)
+        u = (-(fz + ez), -(fy + ey), -(fx + ex))
+        fi.append(OFFS.index(f))
+        ei.append(OFFS.index(e))
+        ui.append(OFFS.index(u))
+        fo.append(f)
+        feo.append((fz + ez, fy + ey, fx + ex))
+    return (torch.tensor(fi), torch.tensor(ei), torch.tensor(ui), torch.tensor(fo),
+            torch.tensor(feo))
+
+
+_AXIS_PAIRS = ((-1, 0), (-1, 1), (0, -1), (0, 0), (0, 1), (1, -1), (1, 0))
+_CP_F, _CP_E, _CP_U, _CP_FO, _CP_FEO = _charge_pairs()
+
+
+def charge_matrix(W1, W2, W3):
+    """M[p, c2, c1] = W3[0, c2, f_p] W2[c2, c1, e_p] W1[c1, 2, -(f_p + e_p)]."""
+    dev = W1.device
+    w3 = W3[0].reshape(16, 27)[:, _CP_F.to(dev)].T  # (p, c2)
+    w2 = W2.reshape(16, 16, 27)[:, :, _CP_E.to(dev)].permute(2, 0, 1)  # (p, c2, c1)
+    w1 = W1[:, 2].reshape(16, 27)[:, _CP_U.to(dev)].T  # (p, c1)
+    return w3[:, :, None] * w2 * w1[:, None, :]
+
+
+def charge_term(M, s1, s2, cq, crho):
+    """sum_k crho[k] sum_p s2[x_k + f_p] . M[p] s1[x_k + f_p + e_p] per sample;
+    s1, s2 (n, Z, Y, X, 16), cq (k, 3) sites as (z, y, x), zero outside."""
+    if cq.shape[0] == 0:
+        return torch.zeros(s1.shape[0], dtype=s1.dtype, device=s1.device)
+    dev = s1.device
+    s1p = torch.nn.functional.pad(s1, (0, 0, 2, 2, 2, 2, 2, 2))
+    s2p = torch.nn.functional.pad(s2, (0, 0, 1, 1, 1, 1, 1, 1))
+    fo, feo = _CP_FO.to(dev), _CP_FEO.to(dev)
+    z, y, x = cq[:, 0:1], cq[:, 1:2], cq[:, 2:3]
+    S2 = s2p[:, z + fo[None, :, 0] + 1, y + fo[None, :, 1] + 1, x + fo[None, :, 2] + 1]
+    S1 = s1p[:, z + feo[None, :, 0] + 2, y + feo[None, :, 1] + 2, x + feo[None, :, 2] + 2]
+    return torch.einsum("nkpa,pab,nkpb,k->n", S2, M.to(s1.dtype), S1, crho.to(s1.dtype))
+
+
 def divergence_kernel(W1, W2, W3, fmask=None):
     """K[c2, c1, e] = W2[c2, c1, e] sum_f fmask[f] W3[0, c2, f] W1[c1, 0, -(e+f)];
     with fmask of shape (k, 27) returns (k, 16, 16, 3, 3, 3)."""
@@ -169,7 +216,7 @@ class SteinCV(torch.nn.Module):
         def rnd(*s, sc):
             return torch.nn.Parameter((torch.randn(*s, generator=g) * sc).to(device))
 
-        self.W1 = rnd(16, 2, 3, 3, 3, sc=scale)
+        self.W1 = rnd(16, 3, 3, 3, 3, sc=scale)  # inputs phi, rho, rho phi
         self.b1 = rnd(16, sc=0.1)
         self.W2 = rnd(16, 16, 3, 3, 3, sc=scale / 4)
         self.b2 = rnd(16, sc=0.1)
@@ -178,9 +225,31 @@ class SteinCV(torch.nn.Module):
         self.b3 = rnd(1, sc=0.0)
         self.c = 1.0  # coefficient of T g, set by fit()
 
+    def weights(self):
+        """(W1, W2, W3) rounded to BF16 as the tensor-core convs use them
+        (straight-through for training).  The divergence must be that of the
+        function actually evaluated: with unrounded weights in the divergence
+        the Stein term picks up a bias."""
+        return tuple(w + (w.to(torch.bfloat16).to(w.dtype) - w).detach()
+                     for w in (self.W1, self.W2, self.W3))
+
     # -- parameters in the 16-channel form the kernel takes
     def _w1p(self):
-        return torch.cat([self.W1, torch.zeros(16, 14, 3, 3, 3, device=self.W1.device)], dim=1)
+        return torch.cat([self.W1, torch.zeros(16, 13, 3, 3, 3, device=self.W1.device)], dim=1)
+
+    def set_density(self, rho: torch.Tensor):
+        """The charge density the net sees (Lz, Ly, Lx); its non-zero sites are
+        where the rho phi channel adds to the divergence."""
+        self._rho = rho
+        cq = torch.nonzero(rho)  # (k, 3) as (z, y, x), row-major order
+        self._cq = cq
+        self._crho = rho[cq[:, 0], cq[:, 1], cq[:, 2]].float()
+        self._cq_xyz = cq.flip(1).to(torch.int32).contiguous()
+
+    def _charges_for(self, rho):
+        if getattr(self, "_rho", None) is not rho:
+            self.set_density(rho)
+        return self._cq, self._crho
 
     def _w3p(self):
         return torch.cat([self.W3, torch.zeros(15, 16, 3, 3, 3, device=self.W3.device)], dim=0)
@@ -191,7 +260,7 @@ class SteinCV(torch.nn.Module):
     def face_corrections(self):
         """(64, 16, 16, 27) K_b - K for every face class (zero for class 'inside')."""
         masks = torch.stack([_FACE_MASKS[b] for b in range(64)])
-        Kb = divergence_kernel(self.W1, self.W2, self.W3, masks).reshape(64, 16, 16, 27)
+        Kb = divergence_kernel(*self.weights(), masks).reshape(64, 16, 16, 27)
         return Kb - Kb[_INSIDE][None]
 
     # -- differentiable T g: x0 (n, Z, Y, X, 16) BF16 input, Aphi (n, Z, Y, X).
@@ -199,6 +268,7 @@ class SteinCV(torch.nn.Module):
     # the coefficient c and every evaluation use the exact term, so the
     # estimator stays unbiased whatever the training objective).
     def stein_term(self, x0, Aphi, faces=True):
+        """x0 from inputs_from(phi, rho) with the rho of set_density."""
         h1 = Conv3dTC.apply(x0, self._w1p(), self.b1)
         a1 = torch.tanh(h1)
         s1 = 1.0 - a1 * a1
@@ -206,11 +276,13 @@ class SteinCV(torch.nn.Module):
         a2 = torch.tanh(h2)
         s2 = 1.0 - a2 * a2
         g = Conv3dTC.apply(a2.to(torch.bfloat16), self._w3p(), self._b3p())[..., 0]
-        K = divergence_kernel(self.W1, self.W2, self.W3)
+        K = divergence_kernel(*self.weights())
         D = Conv3dTC.apply(s1.to(torch.bfloat16), K, torch.zeros(16, device=x0.device))
         div = (s2 * D).sum(dim=(1, 2, 3, 4))
         if faces:
             div = div + self._face_term(s1, s2)
+        div = div + charge_term(charge_matrix(*self.weights()), s1, s2, self._cq,
+                                self._crho)
         return div - (g * Aphi).sum(dim=(1, 2, 3))
 
     def _face_term(self, s1, s2):
@@ -250,8 +322,10 @@ class SteinCV(torch.nn.Module):
         dev = rho.device
         stream = lat._stream if isinstance(lat._stream, torch.cuda.Stream) else \
             torch.cuda.current_stream()
-        K = divergence_kernel(self.W1, self.W2, self.W3)
+        K = divergence_kernel(*self.weights())
         dK = self.face_corrections().contiguous()
+        M = charge_matrix(*self.weights()).float().contiguous()
+        self._charges_for(rho)
         torch.cuda.current_stream().synchronize()
         with torch.cuda.stream(stream):
             x0 = torch.empty((n, Lz, Ly, Lx, 16), dtype=torch.bfloat16, device=dev)
@@ -267,6 +341,14 @@ class SteinCV(torch.nn.Module):
             coulps._check(lib.coulps_cv_stein_sum(
                 _vp(g16), _vp(D), _vp(s2), _vp(Aphi), _vp(s1), _vp(dK), n, Lx, Ly, Lz,
                 _vp(scratch), scratch.numel(), _vp(out), _stream()), "coulps_cv_stein_sum")
+            nq = self._cq_xyz.shape[0]
+            if nq:
+                cscr = torch.empty(7 * nq * n, dtype=torch.float64, device=dev)
+                coulps._check(lib.coulps_cv_charge_term(
+                    _vp(s1), _vp(s2), _vp(M), _vp(self._cq_xyz), _vp(self._crho), nq, n,
+                    (ctypes.c_int32 * 3)(Lx, Ly, Lz), 0, _vp(cscr), cscr.numel(), _vp(out),
+                    _stream()),
+                    "coulps_cv_charge_term")
         stream.synchronize()
         return out
 
@@ -297,10 +379,11 @@ def pack_inputs(lat: "coulps.Lattice", rho: torch.Tensor):
 
 
 def inputs_from(phi16: torch.Tensor, rho: torch.Tensor) -> torch.Tensor:
-    """Rebuild the net input (phi, rho, 0, ...) from stored BF16 phi."""
+    """Rebuild the net input (phi, rho, rho phi, 0, ...) from stored BF16 phi."""
     x0 = torch.zeros(phi16.shape + (16,), dtype=torch.bfloat16, device=phi16.device)
     x0[..., 0] = phi16
     x0[..., 1] = rho.to(torch.bfloat16)
+    x0[..., 2] = (rho.float() * phi16.float()).to(torch.bfloat16)
     return x0
 
 
@@ -326,6 +409,7 @@ def fit(cv: SteinCV, phis, Aphis, es, rho, steps=200, batch=16, lr=2e-3, seed=0,
     n = len(es)
     dev = phis.device
     es_d = es.to(dev)
+    cv._charges_for(rho)
     for step in range(steps):
         idx = torch.randperm(n, generator=g)[:batch].to(dev)
         tg = cv.stein_term(inputs_from(phis[idx], rho), Aphis[idx], faces=False)
@@ -344,6 +428,7 @@ def fit(cv: SteinCV, phis, Aphis, es, rho, steps=200, batch=16, lr=2e-3, seed=0,
 
 @torch.no_grad()
 def stein_terms(cv: SteinCV, phis, Aphis, rho, batch=16):
+    cv._charges_for(rho)
     out = []
     for i in range(0, len(phis), batch):
         out.append(cv.stein_term(inputs_from(phis[i:i + batch], rho), Aphis[i:i + batch]).double())
@@ -422,9 +507,20 @@ class LocalSteinCV(SteinCV):
         rmask[self.r_lo[2]:self.r_hi[2], self.r_lo[1]:self.r_hi[1], self.r_lo[0]:self.r_hi[0]] = 1
         self._rmask = rmask
 
+    def set_density(self, rho: torch.Tensor):
+        """rho of the whole box; the charge-site term keeps the charges inside R
+        (in E coordinates)."""
+        self._rho = rho
+        (x0, y0, z0), (x1, y1, z1) = self.e_lo, self.e_hi
+        re = rho[z0:z1, y0:y1, x0:x1] * self._rmask.to(rho.device, rho.dtype)
+        cq = torch.nonzero(re)
+        self._cq = cq
+        self._crho = re[cq[:, 0], cq[:, 1], cq[:, 2]].float()
+        self._cq_xyz = cq.flip(1).to(torch.int32).contiguous()
+
     def region_kernels(self):
         """(216, 16, 16, 27) divergence kernel per allowed-offset class."""
-        return divergence_kernel(self.W1, self.W2, self.W3, _REGION_FMASKS).reshape(216, 16, 16, 27)
+        return divergence_kernel(*self.weights(), _REGION_FMASKS).reshape(216, 16, 16, 27)
 
     def rho_region(self, rho):
         """The density restricted to E, (ez, ey, ex)."""
@@ -443,7 +539,9 @@ class LocalSteinCV(SteinCV):
         # s rounded like the library kernel's BF16 copies (straight-through)
         s1 = s1 + (s1.to(torch.bfloat16).float() - s1).detach()
         s2 = s2 + (s2.to(torch.bfloat16).float() - s2).detach()
-        return self.region_divergence(s1, s2) - (g * Aphi * self._rmask).sum(dim=(1, 2, 3))
+        div = self.region_divergence(s1, s2) + charge_term(
+            charge_matrix(*self.weights()), s1, s2, self._cq, self._crho)
+        return div - (g * Aphi * self._rmask).sum(dim=(1, 2, 3))
 
     def region_divergence(self, s1, s2):
         """sum_{x in R} dg_x/dphi_x from s1, s2 (n, ez, ey, ex, 16): for each q
@@ -457,16 +555,21 @@ class LocalSteinCV(SteinCV):
         return (s2[:, qz, qy, qx] * d).sum(dim=(1, 2))
 
     @torch.no_grad()
-    def pack(self, lat: "coulps.Lattice", rho: torch.Tensor):
-        """(net input on E (n, ez, ey, ex, 16) BF16, A phi on E FP32) of every
-        chain, by the library's packing kernel on the lattice's stream."""
+    def pack(self, lat: "coulps.Lattice", rho: torch.Tensor, interleave=False):
+        """(net input on E BF16, A phi on E FP32) of every chain, by the
+        library's packing kernel on the lattice's stream: (n, ez, ey, ex, 16)
+        and (n, ez, ey, ex), or with interleave the boxes side by side along x
+        with a zero gutter column each, (1, ez, ey, n (ex + 1), 16) and
+        (1, ez, ey, n (ex + 1))."""
         n = lat.n_chains
         ex, ey, ez = self.edims
-        x0 = torch.empty((n, ez, ey, ex, 16), dtype=torch.bfloat16, device=rho.device)
-        Aphi = torch.empty((n, ez, ey, ex), dtype=torch.float32, device=rho.device)
+        shape = (1, ez, ey, n * (ex + 1)) if interleave else (n, ez, ey, ex)
+        x0 = torch.empty(shape + (16,), dtype=torch.bfloat16, device=rho.device)
+        Aphi = torch.empty(shape, dtype=torch.float32, device=rho.device)
         o = (ctypes.c_int32 * 3)(*self.e_lo)
         d = (ctypes.c_int32 * 3)(*self.edims)
-        coulps._check(coulps.load().coulps_cv_pack_region(lat.handle, _vp(rho), o, d, _vp(x0),
+        coulps._check(coulps.load().coulps_cv_pack_region(lat.handle, _vp(rho), o, d,
+                                                          1 if interleave else 0, _vp(x0),
                                                           _vp(Aphi)), "coulps_cv_pack_region")
         return x0, Aphi
 
@@ -480,6 +583,7 @@ class LocalSteinCV(SteinCV):
                 "b1": self.b1.detach().float().contiguous(), "b2": self.b2.detach().float().contiguous(),
                 "b3": self._b3p().detach().float().contiguous(),
                 "K": self.region_kernels().detach().float().contiguous(),
+                "M": charge_matrix(*self.weights()).detach().float().contiguous(),
                 "err": torch.zeros(1, dtype=torch.int32, device=dev),
             }
 
@@ -491,6 +595,7 @@ class LocalSteinCV(SteinCV):
         if not hasattr(self, "_ev"):
             self.prepare()
         ev = self._ev
+        self._charges_for(rho)
         lib = coulps.load()
         n = lat.n_chains
         ex, ey, ez = self.edims
@@ -498,8 +603,12 @@ class LocalSteinCV(SteinCV):
         stream = lat._stream if isinstance(lat._stream, torch.cuda.Stream) else \
             torch.cuda.current_stream()
         sp = ctypes.c_void_p(stream.cuda_stream)
+        # the chains' boxes side by side along x (zero gutters between them), so
+        # the tensor-core tiles (128 sites of x) are filled
+        P = ex + 1
+        X = n * P
         with torch.cuda.stream(stream):
-            x0, Aphi = self.pack(lat, rho)
+            x0, Aphi = self.pack(lat, rho, interleave=True)
             a1 = torch.empty_like(x0)
             s1 = torch.empty_like(x0)
             a2 = torch.empty_like(x0)
@@ -507,20 +616,45 @@ class LocalSteinCV(SteinCV):
             g16 = torch.empty(x0.shape, dtype=torch.float32, device=dev)
             for src, w, b, dst in ((x0, "w1", "b1", (a1, s1)), (a1, "w2", "b2", (a2, s2))):
                 coulps._check(lib.coulps_cv_conv3d_tanh(
-                    _vp(src), _vp(ev[w]), _vp(ev[b]), _vp(dst[0]), _vp(dst[1]), n, ex, ey, ez,
+                    _vp(src), _vp(ev[w]), _vp(ev[b]), _vp(dst[0]), _vp(dst[1]), 1, X, ey, ez, P,
                     _vp(ev["err"]), sp), "coulps_cv_conv3d_tanh")
-            coulps._check(lib.coulps_cv_conv3d(_vp(a2), _vp(ev["w3"]), _vp(ev["b3"]), _vp(g16), n,
-                                               ex, ey, ez, _vp(ev["err"]), sp), "coulps_cv_conv3d")
+            coulps._check(lib.coulps_cv_conv3d(_vp(a2), _vp(ev["w3"]), _vp(ev["b3"]), _vp(g16), 1,
+                                               X, ey, ez, P, _vp(ev["err"]), sp),
+                          "coulps_cv_conv3d")
             if out is None:
                 out = torch.empty(n, dtype=torch.float64, device=dev)
-            scratch = torch.empty(64 * n, dtype=torch.float64, device=dev)
+            scratch = torch.empty(self._q.shape[0] * n, dtype=torch.float64, device=dev)
             ed = (ctypes.c_int32 * 3)(*self.edims)
             rl = (ctypes.c_int32 * 3)(*self.r_lo)
             rh = (ctypes.c_int32 * 3)(*self.r_hi)
             coulps._check(lib.coulps_cv_stein_region(
-                _vp(g16), _vp(s1), _vp(s2), _vp(Aphi), _vp(ev["K"]), n, ed, rl, rh, _vp(scratch),
-                scratch.numel(), _vp(out), sp), "coulps_cv_stein_region")
+                _vp(g16), _vp(s1), _vp(s2), _vp(Aphi), _vp(ev["K"]), n, ed, 1, rl, rh,
+                _vp(scratch), scratch.numel(), _vp(out), sp), "coulps_cv_stein_region")
+            nq = self._cq_xyz.shape[0]
+            if nq:
+                cscr = torch.empty(7 * nq * n, dtype=torch.float64, device=dev)
+                coulps._check(lib.coulps_cv_charge_term(
+                    _vp(s1), _vp(s2), _vp(ev["M"]), _vp(self._cq_xyz), _vp(self._crho), nq, n, ed,
+                    1, _vp(cscr), cscr.numel(), _vp(out), sp), "coulps_cv_charge_term")
         return out
+
+    @torch.no_grad()
+    def record_graph(self, lat: "coulps.Lattice", ch: "coulps.Charges", rho: torch.Tensor):
+        """A CUDA graph of evaluate + coulps_cv_record (y = e - c T g for every
+        chain), to replay on the lattice's stream after each measured sweep:
+        library kernels only, no host work per sample.  Returns (graph, tg)."""
+        if not hasattr(self, "_ev"):
+            self.prepare()
+        stream = lat._stream if isinstance(lat._stream, torch.cuda.Stream) else \
+            torch.cuda.current_stream()
+        tg = torch.zeros(lat.n_chains, dtype=torch.float64, device=rho.device)
+        self.evaluate(lat, rho, out=tg)  # first launches (kernel attributes) outside capture
+        stream.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            self.evaluate(lat, rho, out=tg)
+            ch.cv_record(tg.data_ptr(), self.c)
+        return graph, tg
 
 
 def collect_region(cv: LocalSteinCV, lat, ch, rho, n_rounds, every=1, n_hb=1, n_or=3):
@@ -538,16 +672,19 @@ def collect_region(cv: LocalSteinCV, lat, ch, rho, n_rounds, every=1, n_hb=1, n_
 
 def fit_region(cv: LocalSteinCV, phis, Aphis, es, rho, steps=400, batch=64, lr=3e-3, seed=0,
                log=None, holdout=0.25):
-    """Minimise Var(e - T g) (Adam, exact region term), then set
+    """Minimise Var(e - T g) (Adam with a cosine learning-rate decay, exact
+    region term), then set
     cv.c = Cov(e, T g) / Var(T g) on held-out samples (the last `holdout`
     fraction), which keeps the coefficient independent of the weights' fit."""
     g = torch.Generator().manual_seed(seed)
     opt = torch.optim.Adam([cv.W1, cv.b1, cv.W2, cv.b2, cv.W3, cv.b3], lr=lr)
+    sched = torch.optim.lr_scheduler.CosineAnnealingLR(opt, T_max=max(1, steps), eta_min=lr / 30)
     n = len(es)
     n_tr = max(2, int(n * (1.0 - holdout)))
     dev = phis.device
     es_d = es.to(dev)
     rho_e = cv.rho_region(rho)
+    cv._charges_for(rho)
     var_e = es_d[:n_tr].float().var() + 1e-30
     for step in range(steps):
         idx = torch.randint(0, n_tr, (batch,), generator=g).to(dev)
@@ -557,6 +694,7 @@ def fit_region(cv: LocalSteinCV, phis, Aphis, es, rho, steps=400, batch=64, lr=3
         opt.zero_grad()
         loss.backward()
         opt.step()
+        sched.step()
         if log is not None:
             log.append(float(loss.detach()))
     with torch.no_grad():
