@@ -47,7 +47,7 @@ CONFIG = {
     "l2": "inputs larger than L2 (512 MiB of fields per GPU vs 126 MB L2); no flush",
 }
 PROFILE_TRAFFIC = ROOT / "profiles" / "or_halfsweep_128c_64ch.txt"
-KERNEL_SOURCES = ["sweep.cu", "device_common.cuh", "internal.h"]
+KERNEL_SOURCES = ["sweep.cu", "tile_march.cuh", "device_common.cuh", "internal.h"]
 
 
 def parse():
@@ -68,7 +68,8 @@ def parse():
                     help="training rounds (every chain contributes one sample per round)")
     ap.add_argument("--cv-global", action="store_true",
                     help="also run the whole-lattice control variate on the +-1 system")
-    ap.add_argument("--workload", choices=["chains128", "large512", "sweep", "batched", "cv", "cube"],
+    ap.add_argument("--workload", choices=["chains128", "large512", "sweep", "batched", "cv", "cube",
+                                           "cv_eval"],
                     default="chains128", help="secondary workloads print their own line")
     ap.add_argument("--chains", type=int, default=N_CHAINS,
                     help="chains per GPU (smaller values only for profiler captures)")
@@ -450,6 +451,8 @@ def run_extra(args):
                         "ms_per_step": ms,
                         "algorithmic_GBps": rate / PASSES * (8 + 12 * N_OR) / 1e9})
         b.close()
+    elif args.workload == "cv_eval":
+        results.append(cv_eval_cost(args, stream))
     elif args.workload == "cv":
         results.extend(cv_experiment(args, stream))
     elif args.workload == "cube":
@@ -561,6 +564,46 @@ def cv_local_cube(args, stream):
     ch.close()
     lat.close()
     torch.cuda.empty_cache()
+    return r
+
+
+def cv_eval_cost(args, stream):
+    """Device time of one localized-CV evaluation + recording (the CUDA graph
+    the cv workload replays after every sweep) for 64 chains on the 128^3 q = 1
+    cube, sub-box 14^3: pack, three tensor-core convs, region divergence,
+    charge-site term, record.  Untrained weights (the cost does not depend on
+    them)."""
+    import torch
+
+    from paper_1403_0711_gb300 import coulps, inputs, stein
+    box = (L, L, L)
+    sites, q = inputs.cube(box, 2)
+    lat = coulps.Lattice(box, n_chains=N_CHAINS, precision=coulps.F32, seed=5, stream=stream)
+    ch = coulps.Charges(lat, sites, q)
+    lat.sweep(20, N_HB, N_OR)
+    rho = stein.charge_density(box, sites, q)
+    cv = stein.LocalSteinCV(box, sites.min(axis=0) - args.cv_halo,
+                            sites.max(axis=0) + 1 + args.cv_halo, seed=0, scale=0.3, w3_scale=0.1)
+    cv.c = 1.0
+    graph, tg = cv.record_graph(lat, ch, rho)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    with torch.cuda.stream(stream):
+        for _ in range(5):
+            graph.replay()
+        ev[0].record(stream)
+        for _ in range(args.steps):
+            graph.replay()
+        ev[1].record(stream)
+    stream.synchronize()
+    ms = ev[0].elapsed_time(ev[1]) / args.steps
+    ex, ey, ez = cv.edims
+    conv_sites = N_CHAINS * (ex + 1) * ey * ez  # interleaved boxes with gutters
+    conv_flops = 3 * conv_sites * 16 * 16 * 27 * 2
+    r = {"system": "cube8_q1_local_cv_eval", "eval_box": list(cv.edims), "chains": N_CHAINS,
+         "ms_per_eval": ms, "evals": args.steps, "conv_flops_per_eval": conv_flops,
+         "conv_tflops_if_all_time": conv_flops / (ms / 1e3) / 1e12}
+    ch.close()
+    lat.close()
     return r
 
 
