@@ -44,10 +44,13 @@ CONFIG = {
                 "1 heatbath : 3 over-relaxation, one sample per compound sweep",
     "lattice": [L, L, L], "n_charges": N_CHARGES, "n_chains_per_gpu": N_CHAINS,
     "n_hb": N_HB, "n_or": N_OR,
-    "l2": "inputs larger than L2 (512 MiB of fields per GPU vs 126 MB L2); no flush",
+    "l2": "inputs larger than L2 (512 MiB of fields per GPU, and its second copy, vs 126 MB L2); no flush",
 }
-PROFILE_TRAFFIC = ROOT / "profiles" / "or_halfsweep_128c_64ch.txt"
-KERNEL_SOURCES = ["sweep.cu", "tile_march.cuh", "device_common.cuh", "internal.h"]
+PROFILE_TRAFFIC = {
+    "pass_kernel<float, over-relaxation>": ROOT / "profiles" / "pass_or_128c_64ch.txt",
+    "halfsweep_kernel<float, over-relaxation>": ROOT / "profiles" / "or_halfsweep_128c_64ch.txt",
+}
+KERNEL_SOURCES = ["sweep.cu", "pass_fused.cu", "tile_march.cuh", "device_common.cuh", "internal.h"]
 
 
 def parse():
@@ -59,6 +62,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--schedule", choices=["phased", "aligned"], default="aligned")
+    ap.add_argument("--fused", choices=["on", "all", "off"], default="on",
+                    help="fused passes (one kernel per pass, ping-pong field copies): "
+                         "over-relaxation passes (on), all passes, or none")
     ap.add_argument("--cv-steps", type=int, default=800)
     ap.add_argument("--cv-rounds", type=int, default=64)
     ap.add_argument("--cube-seconds", type=float, default=600.0)
@@ -152,17 +158,19 @@ def kernel_src_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per over-relaxation launch from the committed ncu summary,
-    or None if the kernel sources changed since it was taken."""
-    if not PROFILE_TRAFFIC.exists():
+def profiled_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
+    None if it holds another kernel or the kernel sources changed since it
+    was taken."""
+    path = PROFILE_TRAFFIC.get(kernel)
+    if path is None or not path.exists():
         return None
     kv = {}
-    for ln in PROFILE_TRAFFIC.read_text().splitlines():
+    for ln in path.read_text().splitlines():
         if ":" in ln and not ln.startswith("#"):
             k, v = ln.split(":", 1)
             kv[k.strip()] = v.strip()
-    if kv.get("kernel_src_sha256_16") != kernel_src_hash():
+    if kv.get("kernel_src_sha256_16") != kernel_src_hash() or kv.get("kernel") != kernel:
         return None
     try:
         return float(kv["dram_bytes_per_launch_full"])
@@ -281,6 +289,7 @@ def run_ours(args):
     sites, q = inputs.plus_minus(box, N_CHARGES, seed=1)
     lat = coulps.Lattice(box, n_chains=n_chains, precision=coulps.F32, seed=20140303 + 7919 * rank,
                          stream=stream)
+    lat.set_fused({"off": 0, "on": 1, "all": 2}[args.fused])
     ch = coulps.Charges(lat, sites, q)
 
     # Measured compound sweeps (the sample is gathered by the last half-sweep of
@@ -322,11 +331,20 @@ def run_ours(args):
     tta = time_to_accuracy(est_timed, ms_max / 1e3, world)
 
     # roofline of the dominant kernel.  Algorithmic bytes per updated site:
-    # heatbath 8 (read the other colour, write), over-relaxation 12 (also read
-    # the old value); a compound sweep of one chain moves 44 L^3 bytes.
+    # half-sweeps: heatbath 8 (read the other colour, write), over-relaxation
+    # 12 (also read the old value); fused passes: 8 per site and pass (read
+    # both colours once, write both once)
     peak, peak_kind = measured_peaks()
     sites_per_launch = n_chains * L ** 3 // 2
-    if kt["mixed_n"] > 0:
+    if kt["pass_or_n"] > 0:
+        pass_bytes = 8 * n_chains * L ** 3
+        or_ms = kt["pass_or_ms"] / kt["pass_or_n"]
+        achieved = pass_bytes / (or_ms / 1e3) / 1e9
+        name = "pass_kernel<float, over-relaxation>"
+        dom = {"kernel": name, "algorithmic_bytes_per_launch": pass_bytes, "avg_launch_ms": or_ms,
+               "heatbath_pass_avg_launch_ms": kt["pass_hb_ms"] / max(1, kt["pass_hb_n"])}
+        traffic = profiled_traffic(name)
+    elif kt["mixed_n"] > 0:
         total_bytes = args.steps * n_chains * (8 * N_HB + 12 * N_OR) * L ** 3
         mixed_ms = kt["mixed_ms"] / kt["mixed_n"]
         achieved = total_bytes / (kt["mixed_ms"] / 1e3) / 1e9
@@ -337,10 +355,11 @@ def run_ours(args):
     else:
         or_ms = kt["or_ms"] / max(1, kt["or_n"])
         achieved = 12 * sites_per_launch / (or_ms / 1e3) / 1e9
-        dom = {"kernel": "halfsweep_kernel<float, over-relaxation>",
+        name = "halfsweep_kernel<float, over-relaxation>"
+        dom = {"kernel": name,
                "algorithmic_bytes_per_launch": 12 * sites_per_launch, "avg_launch_ms": or_ms,
                "heatbath_avg_launch_ms": kt["hb_ms"] / max(1, kt["hb_n"])}
-        traffic = profiled_traffic()
+        traffic = profiled_traffic(name)
     roofline = dict({"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": f"{peak_kind} (burst copy)"}, **dom)
@@ -374,12 +393,17 @@ def run_ours(args):
 
     out = None
     if rank == 0:
-        launches = args.steps * (2 * PASSES + 1)  # half-sweeps and finalizes; few advances
+        # per compound sweep: nf fused passes, 2 (PASSES - nf) half-sweeps, a
+        # gather when the sweep ends in a fused pass, finalize, advance
+        nf = {"off": 0, "on": N_OR & ~1, "all": PASSES & ~1}[args.fused]
+        ends_fused = nf > 0 and (args.fused == "all" or nf == N_OR)
+        launches = args.steps * (nf + 2 * (PASSES - nf) + (1 if ends_fused else 0) + 2)
         line = {
             "metric": METRIC, "value": value, "unit": "site-updates/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic", "config": dict(CONFIG, parallelism=f"replicas{world}", n_chains_per_gpu=n_chains),
+            "data": "synthetic", "config": dict(CONFIG, parallelism=f"replicas{world}", n_chains_per_gpu=n_chains,
+                                           fused_passes=args.fused),
             "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "time_to_1e-3": tta, "estimate_after_e2e": est,
         }

@@ -80,7 +80,8 @@ int coulps_set_allocator(coulps_alloc_fn alloc, coulps_free_fn free_fn, void *ct
  *   seed:      Philox key (low word, high word) of every random draw.
  *   stream:    cudaStream_t to queue work on (NULL = legacy default stream).
  * Limits: 1 <= Lx <= 512, 1 <= Ly, Lz <= 65535, 1 <= n_chains <= 65535,
- * and the quad index (z*Ly + y)*ceil(Lx/8) must fit in 32 bits.
+ * and the quad index (z*Ly + y)*ceil(Lx/8) must fit in 32 bits.  Two copies
+ * of the field are allocated (fused passes, see coulps_set_fused).
  * Errors: EINVAL, ENOMEM, ECUDA. */
 int coulps_lattice_create(int Lx, int Ly, int Lz, int n_chains, int precision,
                           uint64_t seed, void *stream, coulps_lattice_t *out);
@@ -92,9 +93,10 @@ void coulps_lattice_destroy(coulps_lattice_t lat);
 /* Change the stream later work is queued on. */
 int coulps_set_stream(coulps_lattice_t lat, void *stream);
 
-/* info[0..9] = Lx, Ly, Lz, n_chains, precision, row stride W (elements),
- * pass counter, device bytes held, tile rows TY, slab depth DZ. */
-int coulps_lattice_info(coulps_lattice_t lat, int64_t info[10]);
+/* info[0..12] = Lx, Ly, Lz, n_chains, precision, row stride W (elements),
+ * pass counter, device bytes held, tile rows TY, slab depth DZ, fused-pass
+ * mode (0, 1, 2), fused-pass tile rows, fused-pass slab depth. */
+int coulps_lattice_info(coulps_lattice_t lat, int64_t info[13]);
 
 /* Tile shape of the half-sweep kernel: ty rows of y per CTA, dz planes of z
  * per CTA (0 = keep).  Used by the autotuner; results do not depend on it.
@@ -202,6 +204,22 @@ int coulps_pool_stats(const double *stats, int64_t n_rows, double *mean, double 
 #define COULPS_SCHEDULE_PHASED 1
 int coulps_set_schedule(coulps_lattice_t lat, int schedule);
 
+/* Fused passes.  A fused pass (both half-sweeps) runs as one kernel that
+ * reads the field once and writes it once (8 bytes per site in FP32 instead
+ * of 12 for over-relaxation), from the field into a second copy of it or
+ * back: the lattice then holds two copies (twice the field memory).  Within
+ * a compound sweep one block of an even number of consecutive passes is
+ * fused, so the sweep starts and ends in the lattice's field: enable = 1
+ * (default) fuses the over-relaxation passes (all of them when n_or is even,
+ * all but the last when it is odd), enable = 2 all passes, enable = 0 none
+ * (and frees the second copy).  Results are bitwise those of the half-sweep
+ * path (same arithmetic per site, same Philox counters).  Not used by the
+ * phased schedule.  coulps_set_pass_tile: ty rows of y per CTA (the CTA also
+ * computes one halo row each side: (ty + 2) * W / 4 threads <= 512), dz
+ * planes of z per CTA (0 = keep).  Errors: EINVAL, ENOMEM, ECUDA. */
+int coulps_set_fused(coulps_lattice_t lat, int enable);
+int coulps_set_pass_tile(coulps_lattice_t lat, int ty, int dz);
+
 /* ---- kernel timing ----------------------------------------------------- */
 /* With profiling on, every half-sweep launched by coulps_sweep (and by
  * coulps_run, which then launches directly instead of replaying its graph)
@@ -210,9 +228,11 @@ int coulps_set_schedule(coulps_lattice_t lat, int schedule);
  *   out[0] total ms of heatbath half-sweeps, out[1] their count,
  *   out[2] total ms of over-relaxation half-sweeps, out[3] their count,
  *   out[4] total ms of mixed half-sweeps (phased schedule), out[5] their count,
+ *   out[6] total ms of fused heatbath passes, out[7] their count,
+ *   out[8] total ms of fused over-relaxation passes, out[9] their count,
  * and restarts the accumulation. */
 int coulps_set_profiling(coulps_lattice_t lat, int enable);
-int coulps_kernel_times(coulps_lattice_t lat, double out[6]);
+int coulps_kernel_times(coulps_lattice_t lat, double out[10]);
 
 /* ---- checkpoint -------------------------------------------------------- */
 /* Save / restore the full sampler state: fields of all chains, the pass

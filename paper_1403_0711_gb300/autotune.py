@@ -1,4 +1,5 @@
-"""Autotuner for the half-sweep tile shape (ty rows x dz planes per CTA).
+"""Autotuner for the tile shapes (ty rows x dz planes per CTA) of the
+half-sweep kernel and of the fused-pass kernel.
 
 The shape changes only the work decomposition, never the results (the tests
 check fields bitwise across shapes), so the tuner may pick freely.  For a box
@@ -8,7 +9,8 @@ sweeps and keeps the fastest.  Results are cached in a JSON file keyed by box,
 chain count, precision, compound-sweep mix and GPU name
 ($COULPS_TUNE_CACHE, default ~/.cache/coulps_tune.json).
 
-tune_lattice(lat)  tunes and applies the shape of a Lattice.
+tune_lattice(lat)  tunes and applies both shapes of a Lattice (the half-sweep
+                   shape serves passes that are not fused).
 tune_batch(batch)  tunes each distinct system shape of a Batch (with as many
                    chains as the batch has systems of that shape, so the tuned
                    lattice carries the same load) and applies them.
@@ -69,19 +71,33 @@ def candidates(L, precision):
     return [(t, d) for t in tys for d in dzs]
 
 
-def _time_shapes(L, n_chains, precision, shapes, n_hb, n_or, reps, stream):
+def pass_candidates(L, precision):
+    """Fused-pass tile shapes: (ty + 2) rows of quads within 512 threads."""
+    Lx, Ly, Lz = L
+    qw = row_stride(Lx, precision) // 4
+    tys = sorted({t for t in (1, 2, 4, 6, 8, 10, 14, 22, 30, 46, 62, 126)
+                  if t <= Ly and qw * (t + 2) <= 512 and t + 4 <= 256} | {1})
+    dzs = sorted({d for d in (8, 16, 32, 64) if d <= Lz} | {Lz})
+    return [(t, d) for t in tys for d in dzs]
+
+
+def _time_shapes(L, n_chains, precision, shapes, n_hb, n_or, reps, stream, fused=False):
     lat = coulps.Lattice(L, n_chains=n_chains, precision=precision, seed=1, stream=stream)
+    lat.set_fused(fused)
     lat.set_profiling(True)
     out = {}
     try:
         lat.sweep(2, n_hb, n_or)
         for ty, dz in shapes:
-            lat.set_tile(ty, dz)
+            if fused:
+                lat.set_pass_tile(ty, dz)
+            else:
+                lat.set_tile(ty, dz)
             lat.sweep(1, n_hb, n_or)
             lat.kernel_times()
             lat.sweep(reps, n_hb, n_or)
             kt = lat.kernel_times()
-            out[(ty, dz)] = kt["hb_ms"] + kt["or_ms"]
+            out[(ty, dz)] = kt["hb_ms"] + kt["or_ms"] + kt["pass_hb_ms"] + kt["pass_or_ms"]
     finally:
         lat.close()
     return out
@@ -104,9 +120,35 @@ def tune_shape(L, n_chains=1, precision=coulps.F32, n_hb=1, n_or=3, reps=3, stre
     return best
 
 
+def tune_pass_shape(L, n_chains=1, precision=coulps.F32, n_hb=1, n_or=3, reps=3, stream=None,
+                    use_cache=True):
+    """Best fused-pass (ty, dz) for a box shape; cached.  Times an even number
+    of passes per compound sweep (all of them fused)."""
+    L = tuple(int(v) for v in L)
+    if (n_hb + n_or) % 2:
+        n_or += 1
+    key = f"pass|{L[0]}x{L[1]}x{L[2]}|{n_chains}|{precision}|{n_hb}:{n_or}|{_gpu_name()}"
+    cache = _load_cache() if use_cache else {}
+    if key in cache:
+        return tuple(cache[key]["tile"])
+    times = _time_shapes(L, n_chains, precision, pass_candidates(L, precision), n_hb, n_or, reps,
+                         stream, fused=True)
+    best = min(times, key=times.get)
+    if use_cache:
+        cache = _load_cache()
+        cache[key] = {"tile": list(best), "ms": times[best]}
+        _save_cache(cache)
+    return best
+
+
 def tune_lattice(lat: "coulps.Lattice", n_hb=1, n_or=3, reps=3, stream=None):
-    best = tune_shape(lat.L, lat.n_chains, lat.precision, n_hb, n_or, reps, stream or lat._stream)
+    """Tunes both shapes; returns the half-sweep shape (the pass shape is
+    applied too and readable from lat.info())."""
+    s = stream or lat._stream
+    best = tune_shape(lat.L, lat.n_chains, lat.precision, n_hb, n_or, reps, s)
     lat.set_tile(*best)
+    pbest = tune_pass_shape(lat.L, lat.n_chains, lat.precision, n_hb, n_or, reps, s)
+    lat.set_pass_tile(*pbest)
     return best
 
 

@@ -39,7 +39,7 @@ EXPORTS = (
     "coulps_cv_conv3d_wgrad", "coulps_cv_pack_field", "coulps_cv_activate", "coulps_cv_stein_sum",
     "coulps_set_schedule", "coulps_cv_conv3d_tanh", "coulps_cv_pack_region",
     "coulps_cv_stein_region", "coulps_cv_record", "coulps_cv_chain_stats", "coulps_cv_estimate",
-    "coulps_cv_reset", "coulps_cv_charge_term",
+    "coulps_cv_reset", "coulps_cv_charge_term", "coulps_set_fused", "coulps_set_pass_tile",
 )
 SCHEDULE_ALIGNED, SCHEDULE_PHASED = 0, 1
 STAT_STRIDE = 72
@@ -126,6 +126,8 @@ def load(path: str | Path | None = None):
         "coulps_cv_chain_stats": (i32, [vp, P(f64), i64]),
         "coulps_cv_estimate": (i32, [vp, P(f64), P(f64), P(f64), P(i64)]),
         "coulps_cv_reset": (i32, [vp]),
+        "coulps_set_fused": (i32, [vp, i32]),
+        "coulps_set_pass_tile": (i32, [vp, i32, i32]),
         "coulps_cv_charge_term": (i32, [vp, vp, vp, vp, vp, i32, i32, P(ctypes.c_int32), i32, vp,
                                         i64, vp, vp]),
     }
@@ -205,9 +207,10 @@ class Lattice:
             pass
 
     def info(self):
-        a = (ctypes.c_int64 * 10)()
+        a = (ctypes.c_int64 * 13)()
         _check(self._lib.coulps_lattice_info(self.handle, a), "coulps_lattice_info")
-        keys = ("Lx", "Ly", "Lz", "n_chains", "precision", "W", "pass", "bytes", "ty", "dz")
+        keys = ("Lx", "Ly", "Lz", "n_chains", "precision", "W", "pass", "bytes", "ty", "dz",
+                "fused", "pass_ty", "pass_dz")
         return dict(zip(keys, list(a)))
 
     def set_stream(self, stream):
@@ -240,14 +243,25 @@ class Lattice:
         _check(self._lib.coulps_set_profiling(self.handle, int(bool(enable))), "coulps_set_profiling")
 
     def kernel_times(self):
-        """{'hb_ms', 'hb_n', 'or_ms', 'or_n', 'mixed_ms', 'mixed_n'} since the last call."""
-        a = (ctypes.c_double * 6)()
+        """{'hb_ms', 'hb_n', 'or_ms', 'or_n', 'mixed_ms', 'mixed_n', 'pass_hb_ms',
+        'pass_hb_n', 'pass_or_ms', 'pass_or_n'} since the last call."""
+        a = (ctypes.c_double * 10)()
         _check(self._lib.coulps_kernel_times(self.handle, a), "coulps_kernel_times")
         return {"hb_ms": a[0], "hb_n": int(a[1]), "or_ms": a[2], "or_n": int(a[3]),
-                "mixed_ms": a[4], "mixed_n": int(a[5])}
+                "mixed_ms": a[4], "mixed_n": int(a[5]), "pass_hb_ms": a[6], "pass_hb_n": int(a[7]),
+                "pass_or_ms": a[8], "pass_or_n": int(a[9])}
 
     def set_schedule(self, schedule):
         _check(self._lib.coulps_set_schedule(self.handle, int(schedule)), "coulps_set_schedule")
+
+    def set_fused(self, mode):
+        """Fused passes (one kernel per pass, two copies of the field): 0/False
+        off, 1/True the over-relaxation passes (default), 2 all passes."""
+        _check(self._lib.coulps_set_fused(self.handle, int(mode)), "coulps_set_fused")
+
+    def set_pass_tile(self, ty, dz=0):
+        _check(self._lib.coulps_set_pass_tile(self.handle, int(ty), int(dz)),
+               "coulps_set_pass_tile")
 
     def checkpoint_save(self, path, charges=None):
         _check(self._lib.coulps_checkpoint_save(self.handle, charges.handle if charges else None,

@@ -56,6 +56,13 @@ struct coulps_lattice {
   int *d_err = nullptr;
   uint64_t pass = 0;  // host mirror of *d_pass
   CUtensorMap tm_halo, tm_own;
+  // fused passes (pass_fused.cu): a second copy of the field; a compound
+  // sweep runs an even number of fused passes, so it starts and ends in
+  // `field`, and field2 is scratch within a compound sweep
+  void *field2 = nullptr;
+  int fused = 0;  // 0 off, 1 over-relaxation passes, 2 all passes
+  Tile ptile = {0, 0};
+  CUtensorMap tm_p1[2], tm_p0[2];  // source field / field2; boxes ty + 4, ty + 2 rows
   size_t bytes = 0;
   int n_charge_sets = 0;
   // measured compound sweep captured as a graph
@@ -67,11 +74,12 @@ struct coulps_lattice {
   bool profiling = false;
   struct Timed {
     cudaEvent_t a, b;
-    int kind;  // 0 heatbath, 1 over-relaxation, 2 mixed (phase-shifted schedule)
+    int kind;  // 0 heatbath, 1 over-relaxation, 2 mixed (phase-shifted schedule),
+               // 3 fused heatbath pass, 4 fused over-relaxation pass
   };
   std::vector<cudaEvent_t> spare_events;
   std::vector<Timed> pending;
-  double times[6] = {0, 0, 0, 0, 0, 0};
+  double times[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   // measured-phase schedule (COULPS_SCHEDULE_*) and its steady-state graph
   int schedule = COULPS_SCHEDULE_ALIGNED;
   cudaGraphExec_t sgraph = nullptr;
@@ -169,6 +177,33 @@ int rebuild_maps(coulps_lattice *L) {
   return make_map(&L->tm_own, L->g, L->field, L->tile.ty);
 }
 
+// Fused-pass tile: rows + 2 halo rows of quads per CTA within 256 threads,
+// an odd row count (measured a little faster at 128^3: 13 rows 0.202 ms, 14
+// rows 0.211 ms per pass of 64 chains); z slabs of 32 planes (several CTAs
+// per column fill the GPU's slots evenly).
+Tile default_pass_tile(const Geometry &g) {
+  const int qw = g.W / 4;
+  int ty = 256 / qw - 2;
+  if (ty > 1 && ty % 2 == 0) --ty;
+  if (ty < 1) ty = 1;
+  if (ty > g.Ly) ty = g.Ly;
+  if (ty > 252) ty = 252;  // TMA box rows ty + 4 <= 256
+  int dz = g.Lz >= 64 ? 32 : g.Lz;
+  return Tile{ty, dz};
+}
+
+int rebuild_pass_maps(coulps_lattice *L) {
+  if (!L->fused) return COULPS_OK;
+  for (int b = 0; b < 2; ++b) {
+    void *base = b ? L->field2 : L->field;
+    int st = make_map(&L->tm_p1[b], L->g, base, L->ptile.ty + 4);
+    if (st) return st;
+    st = make_map(&L->tm_p0[b], L->g, base, L->ptile.ty + 2);
+    if (st) return st;
+  }
+  return COULPS_OK;
+}
+
 Tile default_tile(const Geometry &g) {
   // About 256 threads per CTA (W/4 threads per row), 16 z planes per CTA.
   const int qw = g.W / 4;
@@ -226,13 +261,53 @@ int enqueue_compound(coulps_lattice *L, int n_hb, int n_or, coulps_charges *fuse
   a.g_ent = nullptr;
   a.g_q = nullptr;
   a.g_partials = nullptr;
-  uint32_t off = 0;
-  for (int i = 0; i < n_hb + n_or; ++i, ++off) {
+  const int n_pass = n_hb + n_or;
+  // fused passes: one block of an even number of consecutive passes, run
+  // field -> field2 -> field ...; the others are in-place half-sweeps.
+  // Mode 1: the over-relaxation passes (the heatbath, ALU-bound, gains
+  // nothing from the saved traffic); mode 2: all passes.
+  int f0 = 0, nf = 0;
+  if (L->fused == 1) {
+    f0 = n_hb;
+    nf = n_or & ~1;
+  } else if (L->fused == 2) {
+    nf = n_pass & ~1;
+  }
+  PassArgs p;
+  p.Lx = a.Lx; p.Ly = a.Ly; p.Lz = a.Lz;
+  p.W = a.W; p.Wq = a.Wq; p.QW = a.QW;
+  p.TY = L->ptile.ty; p.DZ = L->ptile.dz;
+  for (int i = 0; i < 20; ++i) p.round_keys[i] = a.round_keys[i];
+  p.pass_ptr = L->d_pass;
+  p.chain_elems = a.chain_elems;
+  p.colour_elems = a.colour_elems;
+  p.err = L->d_err;
+  const bool gather_fused = fuse && !(nf > 0 && f0 + nf == n_pass);
+  for (int i = 0; i < n_pass; ++i) {
     const bool orx = i >= n_hb;
+    const uint32_t off = (uint32_t)i;
+    if (i >= f0 && i < f0 + nf) {
+      const int b = (i - f0) & 1;  // source copy
+      p.dst = b ? L->field : L->field2;
+      p.pass_off = off;
+      cudaEvent_t ea = nullptr, eb = nullptr;
+      if (L->profiling) {
+        ea = take_event(L);
+        eb = take_event(L);
+        if (!ea || !eb) return COULPS_ECUDA;
+        CK(cudaEventRecord(ea, L->stream));
+      }
+      CK(launch_pass(L->g, L->ptile, L->tm_p1[b], L->tm_p0[b], p, orx, L->stream));
+      if (L->profiling) {
+        CK(cudaEventRecord(eb, L->stream));
+        L->pending.push_back({ea, eb, orx ? 4 : 3});
+      }
+      continue;
+    }
     for (int c = 0; c < 2; ++c) {
       a.colour = c;
       a.pass_off = off;
-      if (fuse && i == n_hb + n_or - 1 && c == 1) {
+      if (gather_fused && i == n_pass - 1 && c == 1) {
         // last half-sweep of the compound sweep: gather Q, P in the same pass
         a.g_off = fuse->d_goff;
         a.g_ent = fuse->d_gent;
@@ -254,9 +329,16 @@ int enqueue_compound(coulps_lattice *L, int n_hb, int n_or, coulps_charges *fuse
     }
   }
   if (n_hb + n_or > 0) CK(launch_advance_pass(L->d_pass, (uint32_t)(n_hb + n_or), L->stream));
-  if (fuse)
+  if (gather_fused) {
     CK(launch_finalize(fuse->d_fpart, fuse->fused_nblk, L->g.n_chains, fuse->d_stats, fuse->d_log,
                        fuse->log_cap, L->d_err, L->stream));
+  } else if (fuse) {
+    // the compound sweep ended in a fused pass: the separate gather
+    CK(launch_gather(L->g, L->field, fuse->d_idx, fuse->d_q, fuse->n, fuse->d_partials,
+                     fuse->nblk, L->stream));
+    CK(launch_finalize(fuse->d_partials, fuse->nblk, L->g.n_chains, fuse->d_stats, fuse->d_log,
+                       fuse->log_cap, L->d_err, L->stream));
+  }
   return COULPS_OK;
 }
 
@@ -573,12 +655,49 @@ int coulps_lattice_create(int Lx, int Ly, int Lz, int n_chains, int precision, u
     return COULPS_ECUDA;
   }
   int st = rebuild_maps(L);
+  if (!st) st = coulps_set_fused(L, 1);
   if (st) {
     coulps_lattice_destroy(L);
     return st;
   }
   *out = L;
   return COULPS_OK;
+}
+
+int coulps_set_fused(coulps_lattice_t L, int enable) {
+  if (!L || enable < 0 || enable > 2) return COULPS_EINVAL;
+  const size_t fbytes = L->g.chain_elems * L->g.es * (size_t)L->g.n_chains;
+  drop_graph(L);
+  if (!enable) {
+    if (L->field2) {
+      dev_free(L->alloc, L->field2, L->stream);
+      L->field2 = nullptr;
+      L->bytes -= fbytes;
+    }
+    L->fused = 0;
+    return COULPS_OK;
+  }
+  if (!L->field2) {
+    L->field2 = dev_alloc(L->alloc, fbytes, L->stream);
+    if (!L->field2) return COULPS_ENOMEM;
+    L->bytes += fbytes;
+    // row padding and never-written quads stay 0 in both copies
+    CK(cudaMemsetAsync(L->field2, 0, fbytes, L->stream));
+  }
+  if (L->ptile.ty == 0) L->ptile = default_pass_tile(L->g);
+  L->fused = enable;
+  return rebuild_pass_maps(L);
+}
+
+int coulps_set_pass_tile(coulps_lattice_t L, int ty, int dz) {
+  if (!L || ty < 1 || dz < 0 || ty + 4 > 256) return COULPS_EINVAL;
+  Tile t{ty, dz > 0 ? dz : L->ptile.dz};
+  if (t.dz < 1) t.dz = L->g.Lz;
+  if (pass_threads(L->g, t) > 512) return COULPS_EINVAL;
+  if (pass_smem_bytes(L->g, t, true) > 227 * 1024) return COULPS_EINVAL;
+  drop_graph(L);
+  L->ptile = t;
+  return rebuild_pass_maps(L);
 }
 
 void coulps_lattice_destroy(coulps_lattice_t L) {
@@ -590,6 +709,7 @@ void coulps_lattice_destroy(coulps_lattice_t L) {
   }
   for (auto e : L->spare_events) cudaEventDestroy(e);
   dev_free(L->alloc, L->field, L->stream);
+  dev_free(L->alloc, L->field2, L->stream);
   dev_free(L->alloc, L->d_pass, L->stream);
   dev_free(L->alloc, L->d_err, L->stream);
   delete L;
@@ -602,12 +722,13 @@ int coulps_set_stream(coulps_lattice_t L, void *stream) {
   return COULPS_OK;
 }
 
-int coulps_lattice_info(coulps_lattice_t L, int64_t info[10]) {
+int coulps_lattice_info(coulps_lattice_t L, int64_t info[13]) {
   if (!L || !info) return COULPS_EINVAL;
   info[0] = L->g.Lx; info[1] = L->g.Ly; info[2] = L->g.Lz;
   info[3] = L->g.n_chains; info[4] = L->g.precision; info[5] = L->g.W;
   info[6] = (int64_t)L->pass; info[7] = (int64_t)L->bytes;
   info[8] = L->tile.ty; info[9] = L->tile.dz;
+  info[10] = L->fused; info[11] = L->ptile.ty; info[12] = L->ptile.dz;
   return COULPS_OK;
 }
 
@@ -1018,7 +1139,7 @@ int coulps_set_profiling(coulps_lattice_t L, int enable) {
   return COULPS_OK;
 }
 
-int coulps_kernel_times(coulps_lattice_t L, double out[6]) {
+int coulps_kernel_times(coulps_lattice_t L, double out[10]) {
   if (!L || !out) return COULPS_EINVAL;
   CK(cudaStreamSynchronize(L->stream));
   for (auto &t : L->pending) {
@@ -1030,7 +1151,7 @@ int coulps_kernel_times(coulps_lattice_t L, double out[6]) {
     L->spare_events.push_back(t.b);
   }
   L->pending.clear();
-  for (int i = 0; i < 6; ++i) {
+  for (int i = 0; i < 10; ++i) {
     out[i] = L->times[i];
     L->times[i] = 0;
   }

@@ -74,6 +74,25 @@ struct SweepArgs {
   double *g_partials;  // [chain][y tiles * z slabs][2]
 };
 
+// Fused pass (pass_fused.cu): both half-sweeps of one pass, colour 0 then
+// colour 1, read from src and written to dst (two copies of the field, same
+// layout).  TMA maps are built on src with boxes of TY + 4 rows (colour 1)
+// and TY + 2 rows (colour 0).
+struct PassArgs {
+  void *dst;
+  int Lx, Ly, Lz, W, Wq, QW, TY, DZ;
+  uint32_t round_keys[20];
+  const uint32_t *pass_ptr;
+  uint32_t pass_off;
+  size_t chain_elems, colour_elems;
+  int *err;
+};
+cudaError_t launch_pass(const Geometry &g, const Tile &t, const CUtensorMap &tm_c1,
+                        const CUtensorMap &tm_c0, const PassArgs &a, bool overrelax,
+                        cudaStream_t s);
+int pass_threads(const Geometry &g, const Tile &t);
+size_t pass_smem_bytes(const Geometry &g, const Tile &t, bool overrelax);
+
 // Phase-shifted schedule: chain k belongs to group k % groups; per group the
 // launch does nothing (mode 0), a heatbath (1) or an over-relaxation (2)
 // half-sweep with pass index *pass_ptr + pass_delta, gathering Q, P if

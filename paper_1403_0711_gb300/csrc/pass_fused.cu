@@ -1,0 +1,351 @@
+// Fused pass: both half-sweeps of one pass (colour 0, then colour 1 with the
+// new colour-0 values) in a single z-march, from a source copy of the field
+// to a destination copy.  Per pass each site is read once and written once
+// (8 bytes per site in FP32) instead of 12: the colour-0 half-sweep reads
+// colour 1 and its own old values, the colour-1 half-sweep would read the new
+// colour 0 and its own old values again.
+//
+// Order of work inside one CTA (TY rows of y, slab [z0, z0 + nz) of z, one
+// chain), step s = 0 .. nz + 1:
+//   stage 0: colour 0 at plane p0 = z0 - 1 + s on rows y0 - 1 .. y0 + TY
+//            (one halo row each side, recomputed by both neighbouring CTAs:
+//            same inputs, same Philox counters, same values);
+//   stage 1: colour 1 at plane p1 = p0 - 1 on rows y0 .. y0 + TY - 1.
+// Colour 1's old planes p0 - 1 .. p0 + 1 (rows y0 - 2 .. y0 + TY + 1) and
+// colour 0's old plane p0 (rows y0 - 1 .. y0 + TY) arrive by TMA in a 4-slot
+// ring.  Each thread owns one quad of one row for both stages and carries in
+// registers the three planes of colour 1 (old) and of colour 0 (new) that
+// its quad needs along z; the y +- 1 rows and the x neighbour come from
+// shared memory (the ring, and a 2-plane buffer of the new colour-0 rows).
+// Ghost rows and planes (outside the box) hold 0 in both.
+//
+// Reading the source and writing a separate destination is what makes the
+// halo rows safe: a neighbouring CTA still reads old colour-1 rows that this
+// CTA has already updated.  The arithmetic per site is exactly that of the
+// half-sweep kernel (same sums in the same order, same fma), so a pass gives
+// bitwise the same field as its two half-sweeps.
+#include "device_common.cuh"
+#include "internal.h"
+#include "tile_march.cuh"
+
+namespace coulps {
+namespace {
+
+using namespace tile;
+
+struct PassLayout {
+  int c1_bytes;    // colour-1 box: (TY + 4) rows x W
+  int c0_bytes;    // colour-0 box: (TY + 2) rows x W (over-relaxation only)
+  int slot_bytes;  // both, each rounded to 128 bytes
+  int new_bytes;   // one plane of new colour-0 rows: (TY + 2) x W
+  int total;       // header + 4 slots + 2 new planes
+};
+
+__host__ __device__ inline PassLayout pass_layout(int TY, int W, int es, bool orx) {
+  PassLayout L;
+  L.c1_bytes = (TY + 4) * W * es;
+  L.c0_bytes = orx ? (TY + 2) * W * es : 0;
+  L.slot_bytes = round_up_int(L.c1_bytes, 128) + round_up_int(L.c0_bytes, 128);
+  L.new_bytes = round_up_int((TY + 2) * W * es, 128);
+  L.total = kHeaderBytes + kStages * L.slot_bytes + 2 * L.new_bytes;
+  return L;
+}
+
+template <typename T, bool OR>
+__global__ void __launch_bounds__(512)
+    pass_kernel(const __grid_constant__ CUtensorMap tm_c1, const __grid_constant__ CUtensorMap tm_c0,
+                const PassArgs a) {
+  constexpr int R = 1;  // rows per thread
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *smem = reinterpret_cast<unsigned char *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
+  const PassLayout lay = pass_layout(a.TY, a.W, (int)sizeof(T), OR);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 64);
+  unsigned char *ring = smem + kHeaderBytes;
+  T *newbuf = reinterpret_cast<T *>(ring + kStages * lay.slot_bytes);
+  auto c1_slot = [&](int j) {
+    return reinterpret_cast<T *>(ring + (j & (kStages - 1)) * lay.slot_bytes);
+  };
+  auto c0_slot = [&](int j) {
+    return reinterpret_cast<T *>(ring + (j & (kStages - 1)) * lay.slot_bytes +
+                                 round_up_int(lay.c1_bytes, 128));
+  };
+  auto new_plane = [&](int s) {
+    return reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(newbuf) + (s & 1) * lay.new_bytes);
+  };
+
+  const int chain = blockIdx.z;
+  const int W = a.W, TY = a.TY;
+  const int y0 = blockIdx.x * TY;
+  const int z0 = blockIdx.y * a.DZ;
+  const int nz = min(a.DZ, a.Lz - z0);
+  const int tid = threadIdx.x;
+  // this thread: quad qx of row r0 (y = y0 - 1 + r0; rows 0 and TY + 1 are
+  // the halo of stage 0)
+  const int qx = tid % a.QW, r0 = R * (tid / a.QW);
+  const bool in_tile = r0 < TY + 2;
+  bool live0[R], live1[R];
+  int yk[R];
+#pragma unroll
+  for (int k = 0; k < R; ++k) {
+    yk[k] = y0 - 1 + r0 + k;
+    live0[k] = in_tile && yk[k] >= 0 && yk[k] < a.Ly && qx < a.Wq;
+    live1[k] = live0[k] && r0 + k >= 1 && r0 + k <= TY;
+  }
+  const int n_ring = nz + 4;  // colour-1 planes z0 - 2 .. z0 + nz + 1
+  T *dst0 = reinterpret_cast<T *>(a.dst) + (size_t)chain * a.chain_elems;
+  T *dst1 = dst0 + a.colour_elems;
+  const uint32_t pass = OR ? 0u : (*a.pass_ptr + a.pass_off);
+  const PhiloxKeys &K = *reinterpret_cast<const PhiloxKeys *>(a.round_keys);
+
+  ring_init(smem);
+  if (tid == 0) {
+    prefetch_tensormap(&tm_c1);
+    if (OR) prefetch_tensormap(&tm_c0);
+  }
+  // ring plane j: colour 1 at z0 - 2 + j; with it (j >= 2) colour 0 at z0 - 3 + j
+  auto issue = [&](int j) {
+    const uint32_t bar = smem_addr(&bars[j & (kStages - 1)]);
+    const bool own = OR && j >= 2;
+    mbar_arrive_expect_tx(bar, lay.c1_bytes + (own ? lay.c0_bytes : 0));
+    tma_load_4d(smem_addr(c1_slot(j)), &tm_c1, 0, y0 - 2, z0 - 2 + j, 2 * chain + 1, bar);
+    if (own) tma_load_4d(smem_addr(c0_slot(j)), &tm_c0, 0, y0 - 1, z0 - 3 + j, 2 * chain, bar);
+  };
+  auto wait_plane = [&](int j) -> bool {
+    return mbar_wait_bounded(smem_addr(&bars[j & (kStages - 1)]), (uint32_t)((j / kStages) & 1));
+  };
+  int issued = 0;
+  if (tid == 0)
+    for (; issued < min(kStages, n_ring); ++issued) issue(issued);
+
+  // lanes of the quad past x = Lx - 1 (kept at 0), for row parity 0 and 1
+  uint32_t pad0 = 0u, pad1 = 0u;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    if (2 * (4 * qx + i) >= a.Lx) pad0 |= 1u << i;
+    if (2 * (4 * qx + i) + 1 >= a.Lx) pad1 |= 1u << i;
+  }
+  const bool lo_ok = qx > 0, hi_ok = 4 * qx + 4 < W;
+  const int row = r0 * W + 4 * qx;  // first row of this thread in a box starting at y0 - 1
+  T *out0 = dst0 + (size_t)yk[0] * W + 4 * qx;
+  T *out1 = dst1 + (size_t)yk[0] * W + 4 * qx;
+  const size_t plane = (size_t)a.Ly * W;
+
+  // registers along z, per row: colour 1 old at p0 - 1, p0, p0 + 1; colour 0
+  // new at p1 - 1, p1, p1 + 1 (p1 = p0 - 1)
+  T am[R][4], ac[R][4], ap[R][4], nm[R][4], nc[R][4], np[R][4];
+#pragma unroll
+  for (int k = 0; k < R; ++k)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) am[k][i] = ac[k][i] = ap[k][i] = nm[k][i] = nc[k][i] = np[k][i] = T(0);
+  bool ok = wait_plane(0);
+  if (ok && in_tile)
+#pragma unroll
+    for (int k = 0; k < R; ++k) ld_quad(c1_slot(0) + row + (k + 1) * W, am[k]);
+  ok = ok && wait_plane(1);
+  if (ok && in_tile)
+#pragma unroll
+    for (int k = 0; k < R; ++k) ld_quad(c1_slot(1) + row + (k + 1) * W, ac[k]);
+  if (!ok) {
+    atomicOr(a.err, kErrTimeout);
+    *abort_flag = 1;
+  }
+  __syncthreads();
+  bool aborted = *abort_flag != 0;
+  int done = 1;  // ring planes 0 .. done waited for by every thread
+
+  // One step s: stage 0 at p0 = z0 - 1 + s, then stage 1 at p0 - 1.  The
+  // register triples rotate from step to step (A0 = plane - 1, A1 = plane,
+  // A2 = plane + 1; A2 and N2 written here); the loop below calls it with the
+  // names rotated, so no values are moved.  The y neighbours inside the
+  // thread's rows come from its own registers, the outer two from shared
+  // memory.
+  auto step = [&](int s, T(&A0)[R][4], T(&A1)[R][4], T(&A2)[R][4], T(&N0)[R][4],
+                  T(&N1)[R][4], T(&N2)[R][4]) -> bool {
+    const int j = s + 2;
+    const int p0 = z0 - 1 + s;
+    const bool got = wait_plane(j);
+    T v0[R][4];
+#pragma unroll
+    for (int k = 0; k < R; ++k)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) v0[k][i] = T(0);
+    if (got) {
+      const T *C1 = c1_slot(j) + row;
+#pragma unroll
+      for (int k = 0; k < R; ++k) {
+        if (in_tile) {
+          ld_quad(C1 + (k + 1) * W, A2[k]);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) A2[k][i] = T(0);
+        }
+      }
+      if (in_tile && p0 >= 0 && p0 < a.Lz) {
+        const T *Pz = c1_slot(j - 1) + row;  // colour 1 old, plane p0; row r0 + k at + (k + 1) W
+        T lo[4], hi[4];
+        ld_quad(Pz, lo);                // row r0 - 1
+        ld_quad(Pz + (R + 1) * W, hi);  // row r0 + R
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+          if (!live0[k]) continue;
+          const T *ym = k == 0 ? lo : A1[k - 1];
+          const T *yp = k == R - 1 ? hi : A1[k + 1];
+          T xs[4], S[4];
+          const int par = (yk[k] + p0) & 1;
+          if (par == 0) {
+            xs[0] = lo_ok ? Pz[(k + 1) * W - 1] : T(0);
+            xs[1] = A1[k][0]; xs[2] = A1[k][1]; xs[3] = A1[k][2];
+          } else {
+            xs[0] = A1[k][1]; xs[1] = A1[k][2]; xs[2] = A1[k][3];
+            xs[3] = hi_ok ? Pz[(k + 1) * W + 4] : T(0);
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            S[i] = ((A0[k][i] + A2[k][i]) + (ym[i] + yp[i])) + (A1[k][i] + xs[i]);
+          if (!OR) {
+            const uint32_t quad = ((uint32_t)p0 * (uint32_t)a.Ly + (uint32_t)yk[k]) *
+                                      (uint32_t)a.Wq + (uint32_t)qx;
+            const uint4 w = philox4x32_10(make_uint4(quad, pass, (uint32_t)chain, 0u), K);
+            v0[k][0] = fma(S[0], Coef<T>::sixth, Noise<T>::of(w.x));
+            v0[k][1] = fma(S[1], Coef<T>::sixth, Noise<T>::of(w.y));
+            v0[k][2] = fma(S[2], Coef<T>::sixth, Noise<T>::of(w.z));
+            v0[k][3] = fma(S[3], Coef<T>::sixth, Noise<T>::of(w.w));
+          } else {
+            T old[4];
+            ld_quad(c0_slot(j) + row + k * W, old);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) v0[k][i] = fma(S[i], Coef<T>::third, -old[i]);
+          }
+          const uint32_t pm = par ? pad1 : pad0;
+          if (pm) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+              if ((pm >> i) & 1u) v0[k][i] = T(0);
+          }
+          if (live1[k] && p0 >= z0 && p0 < z0 + nz)
+            st_quad(out0 + (size_t)p0 * plane + (size_t)k * W, v0[k]);
+        }
+      }
+      if (in_tile)
+#pragma unroll
+        for (int k = 0; k < R; ++k) st_quad(new_plane(s) + row + k * W, v0[k]);
+    } else {
+      atomicOr(a.err, kErrTimeout);
+      *abort_flag = 1;
+    }
+#pragma unroll
+    for (int k = 0; k < R; ++k)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) N2[k][i] = v0[k][i];
+    __syncthreads();
+    if (*abort_flag) return false;
+    done = j;
+    // ---- stage 1: colour 1 at plane p1 = p0 - 1 on this tile's rows
+    const int p1 = p0 - 1;
+    if (s >= 2 && (live1[0] || live1[R - 1])) {
+      const T *N = new_plane(s - 1) + row;  // colour 0 new, plane p1
+      T lo[4], hi[4];
+      if (live1[0]) ld_quad(N - W, lo);      // row r0 - 1 (r0 >= 1 here)
+      if (live1[R - 1]) ld_quad(N + R * W, hi);  // row r0 + R (<= TY + 1 here)
+#pragma unroll
+      for (int k = 0; k < R; ++k) {
+        if (!live1[k]) continue;
+        const T *ym = k == 0 ? lo : N1[k - 1];
+        const T *yp = k == R - 1 ? hi : N1[k + 1];
+        T xs[4], S[4], v[4];
+        const int par = (1 + yk[k] + p1) & 1;
+        if (par == 0) {
+          xs[0] = lo_ok ? N[k * W - 1] : T(0);
+          xs[1] = N1[k][0]; xs[2] = N1[k][1]; xs[3] = N1[k][2];
+        } else {
+          xs[0] = N1[k][1]; xs[1] = N1[k][2]; xs[2] = N1[k][3];
+          xs[3] = hi_ok ? N[k * W + 4] : T(0);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          S[i] = ((N0[k][i] + N2[k][i]) + (ym[i] + yp[i])) + (N1[k][i] + xs[i]);
+        if (!OR) {
+          const uint32_t quad = ((uint32_t)p1 * (uint32_t)a.Ly + (uint32_t)yk[k]) *
+                                    (uint32_t)a.Wq + (uint32_t)qx;
+          const uint4 w = philox4x32_10(make_uint4(quad, pass, (uint32_t)chain, 1u), K);
+          v[0] = fma(S[0], Coef<T>::sixth, Noise<T>::of(w.x));
+          v[1] = fma(S[1], Coef<T>::sixth, Noise<T>::of(w.y));
+          v[2] = fma(S[2], Coef<T>::sixth, Noise<T>::of(w.z));
+          v[3] = fma(S[3], Coef<T>::sixth, Noise<T>::of(w.w));
+        } else {
+          // colour 1's own old value at plane p1 = p0 - 1 is A0
+#pragma unroll
+          for (int i = 0; i < 4; ++i) v[i] = fma(S[i], Coef<T>::third, -A0[k][i]);
+        }
+        const uint32_t pm = par ? pad1 : pad0;
+        if (pm) {
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            if ((pm >> i) & 1u) v[i] = T(0);
+        }
+        st_quad(out1 + (size_t)p1 * plane + (size_t)k * W, v);
+      }
+    }
+    __syncthreads();  // new plane s - 1 and ring plane s are free
+    if (tid == 0 && issued < n_ring) issue(issued++);
+    return true;
+  };
+
+  const int n_steps = nz + 2;
+  for (int s = 0; s < n_steps && !aborted; s += 3) {
+    if (!step(s, am, ac, ap, nm, nc, np)) { aborted = true; break; }
+    if (s + 1 >= n_steps) break;
+    if (!step(s + 1, ac, ap, am, nc, np, nm)) { aborted = true; break; }
+    if (s + 2 >= n_steps) break;
+    if (!step(s + 2, ap, am, ac, np, nm, nc)) { aborted = true; break; }
+  }
+  if (aborted && tid == 0) {
+    // leave no copy in flight into this CTA's shared memory
+    for (int k = done + 1; k < issued; ++k)
+      if (!wait_plane(k)) break;
+  }
+}
+
+template <typename T, bool OR>
+cudaError_t launch_pt(const Geometry &g, const Tile &t, const CUtensorMap &tm_c1,
+                      const CUtensorMap &tm_c0, const PassArgs &a, cudaStream_t s) {
+  const PassLayout lay = pass_layout(t.ty, g.W, (int)sizeof(T), OR);
+  const size_t smem = (size_t)lay.total + 128;
+  auto kfn = pass_kernel<T, OR>;
+  static int configured_bytes = 0;  // per instantiation
+  if ((int)smem > configured_bytes) {
+    cudaError_t e =
+        cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured_bytes = (int)smem;
+  }
+  dim3 grid((g.Ly + t.ty - 1) / t.ty, (g.Lz + t.dz - 1) / t.dz, g.n_chains);
+  dim3 block(pass_threads(g, t));
+  kfn<<<grid, block, smem, s>>>(tm_c1, tm_c0, a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int pass_threads(const Geometry &g, const Tile &t) {
+  const int n = (g.W / 4) * (t.ty + 2);
+  return (n + 31) / 32 * 32;
+}
+
+size_t pass_smem_bytes(const Geometry &g, const Tile &t, bool overrelax) {
+  return (size_t)pass_layout(t.ty, g.W, g.es, overrelax).total + 128;
+}
+
+cudaError_t launch_pass(const Geometry &g, const Tile &t, const CUtensorMap &tm_c1,
+                        const CUtensorMap &tm_c0, const PassArgs &a, bool overrelax,
+                        cudaStream_t s) {
+  if (g.precision == COULPS_F32)
+    return overrelax ? launch_pt<float, true>(g, t, tm_c1, tm_c0, a, s)
+                     : launch_pt<float, false>(g, t, tm_c1, tm_c0, a, s);
+  return overrelax ? launch_pt<double, true>(g, t, tm_c1, tm_c0, a, s)
+                   : launch_pt<double, false>(g, t, tm_c1, tm_c0, a, s);
+}
+
+}  // namespace coulps

@@ -1,0 +1,90 @@
+"""Fused passes (one kernel per pass, field copied back and forth between two
+buffers) against the half-sweep path: the fields must be bitwise identical
+(same arithmetic per site, same Philox counters), over heatbath and
+over-relaxation passes, odd and even pass counts, FP32 and FP64, ragged
+boxes, and any fused tile shape.  Samples agree to rounding (the fused path
+gathers with the separate gather kernel, in another summation order)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cl():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1403_0711_gb300 import _build, coulps
+    _build.build()
+    coulps.load()
+    coulps.use_torch_allocator()
+    return coulps
+
+
+@pytest.fixture(scope="module")
+def stream():
+    import torch
+    return torch.cuda.Stream()
+
+
+def _run(cl, stream, L, prec, n_chains, seed, sites, q, n_therm, n_meas, n_hb, n_or, fused,
+         pass_tile=None):
+    lat = cl.Lattice(L, n_chains=n_chains, precision=prec, seed=seed, stream=stream)
+    lat.set_fused(fused)
+    if pass_tile:
+        lat.set_pass_tile(*pass_tile)
+    ch = cl.Charges(lat, sites, q, log_capacity=max(1, n_meas))
+    ch.run(n_therm, n_meas, n_hb, n_or)
+    s = ch.samples()
+    f = [lat.field(k) for k in range(n_chains)]
+    info = lat.info()
+    ch.close()
+    lat.close()
+    return s, f, info
+
+
+def _rel(a, b):
+    den = np.abs(b[..., 0]) ** 2 + np.abs(b[..., 1]) + 1e-300
+    return float(np.max(np.abs(a - b) / den[..., None]))
+
+
+@pytest.mark.parametrize("L,prec,n_hb,n_or,tile,mode", [
+    ((37, 29, 23), "F32", 1, 3, None, 1),   # two OR passes fused, the third as half-sweeps
+    ((37, 29, 23), "F32", 1, 3, (3, 5), 2),  # all four passes fused
+    ((16, 16, 16), "F64", 2, 2, None, 1),
+    ((16, 16, 16), "F64", 2, 2, None, 2),
+    ((10, 9, 8), "F32", 1, 2, None, 2),      # odd pass count: last pass as half-sweeps
+    ((130, 5, 70), "F32", 0, 4, (1, 64), 1),
+    ((64, 64, 64), "F32", 1, 3, (30, 16), 2),
+    ((9, 1, 1), "F64", 1, 1, None, 2),
+    ((25, 40, 3), "F32", 3, 1, (6, 1), 2),
+    ((25, 40, 3), "F32", 1, 5, (6, 1), 1),
+])
+def test_fused_passes_equal_half_sweeps(cl, stream, L, prec, n_hb, n_or, tile, mode):
+    from paper_1403_0711_gb300 import inputs
+    p = getattr(cl, prec)
+    n = min(12, L[0] * L[1] * L[2] // 2) // 2 * 2
+    sites, q = inputs.plus_minus(L, n, seed=3)
+    ref = _run(cl, stream, L, p, 3, 17, sites, q, 2, 4, n_hb, n_or, 0)
+    got = _run(cl, stream, L, p, 3, 17, sites, q, 2, 4, n_hb, n_or, mode, tile)
+    assert got[2]["fused"] == mode and ref[2]["fused"] == 0
+    assert got[2]["pass"] == ref[2]["pass"]
+    for a, b in zip(got[1], ref[1]):
+        assert np.array_equal(a, b)
+    assert _rel(got[0], ref[0]) < 1e-13
+
+
+def test_fused_is_default_and_costs_a_second_copy(cl, stream):
+    L = (32, 32, 32)
+    lat = cl.Lattice(L, n_chains=2, precision=cl.F32, seed=1, stream=stream)
+    info = lat.info()
+    assert info["fused"] == 1 and info["pass_ty"] >= 1 and info["pass_dz"] >= 1
+    b_on = info["bytes"]
+    lat.set_fused(False)
+    b_off = lat.info()["bytes"]
+    field = 2 * 2 * 32 * 32 * 16 * 4  # chains x colours x Lz x Ly x W x 4 B
+    assert b_on - b_off == field
+    with pytest.raises(cl.CoulpsError):
+        lat.set_pass_tile(0, 4)
+    lat.close()

@@ -286,6 +286,7 @@ def test_phased_schedule_is_bitwise_identical(cl, stream, n_hb, n_or, chains, pr
     out = {}
     for sched in (cl.SCHEDULE_ALIGNED, cl.SCHEDULE_PHASED):
         lat = cl.Lattice(L, n_chains=chains, precision=cl.F32, seed=31, stream=stream)
+        lat.set_fused(False)  # the half-sweep path on both sides (fusion has its own tests)
         lat.set_schedule(sched)
         lat.set_profiling(profiling)
         ch = cl.Charges(lat, sites, q, log_capacity=9)
