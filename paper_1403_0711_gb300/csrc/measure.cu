@@ -54,16 +54,31 @@ __global__ void __launch_bounds__(kGatherThreads)
   }
 }
 
-__global__ void finalize_kernel(const double *__restrict__ partials, int nblk, int n_chains,
-                                double *__restrict__ stats, double *__restrict__ log,
-                                int64_t log_cap, int *err) {
-  const int chain = blockIdx.x * blockDim.x + threadIdx.x;
-  if (chain >= n_chains) return;
-  double Q = 0.0, P = 0.0;
-  for (int b = 0; b < nblk; ++b) {
+// One warp per chain: lane l adds the partials l, l + 32, ... in order, then
+// a fixed butterfly adds the lanes (same order every run).
+constexpr int kFinalizeWarps = 8;
+
+__device__ __forceinline__ void chain_QP(const double *__restrict__ partials, int nblk, int chain,
+                                         int lane, double &Q, double &P) {
+  Q = 0.0;
+  P = 0.0;
+  for (int b = lane; b < nblk; b += 32) {
     Q += partials[2 * ((size_t)chain * nblk + b) + 0];
     P += partials[2 * ((size_t)chain * nblk + b) + 1];
   }
+  Q = warp_sum(Q);
+  P = warp_sum(P);
+}
+
+__global__ void finalize_kernel(const double *__restrict__ partials, int nblk, int n_chains,
+                                double *__restrict__ stats, double *__restrict__ log,
+                                int64_t log_cap, int *err) {
+  const int chain = blockIdx.x * kFinalizeWarps + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (chain >= n_chains) return;  // whole warps leave together
+  double Q, P;
+  chain_QP(partials, nblk, chain, lane, Q, P);
+  if (lane != 0) return;
   double *st = stats + (size_t)chain * kStatStride;
   const int64_t s = (int64_t)st[kStatN];
   double *row = (log != nullptr && s < log_cap) ? log + 3 * ((size_t)s * n_chains + chain) : nullptr;
@@ -74,13 +89,12 @@ __global__ void finalize_kernel(const double *__restrict__ partials, int nblk, i
 __global__ void finalize_group_kernel(const double *__restrict__ partials, int nblk, int n_chains,
                                       int first, int stride, double *__restrict__ stats,
                                       double *__restrict__ log, int64_t log_cap, int *err) {
-  const int chain = first + (blockIdx.x * blockDim.x + threadIdx.x) * stride;
-  if (chain >= n_chains) return;
-  double Q = 0.0, P = 0.0;
-  for (int b = 0; b < nblk; ++b) {
-    Q += partials[2 * ((size_t)chain * nblk + b) + 0];
-    P += partials[2 * ((size_t)chain * nblk + b) + 1];
-  }
+  const int chain = first + (blockIdx.x * kFinalizeWarps + (threadIdx.x >> 5)) * stride;
+  const int lane = threadIdx.x & 31;
+  if (chain >= n_chains) return;  // whole warps leave together
+  double Q, P;
+  chain_QP(partials, nblk, chain, lane, Q, P);
+  if (lane != 0) return;
   double *st = stats + (size_t)chain * kStatStride;
   const int64_t s = (int64_t)st[kStatN];
   double *row = (log != nullptr && s < log_cap) ? log + 3 * ((size_t)s * n_chains + chain) : nullptr;
@@ -126,8 +140,8 @@ cudaError_t launch_gather(const Geometry &g, const void *field, const uint32_t *
 
 cudaError_t launch_finalize(const double *partials, int nblk, int n_chains, double *stats,
                             double *log, int64_t log_cap, int *err, cudaStream_t s) {
-  finalize_kernel<<<(n_chains + 127) / 128, 128, 0, s>>>(partials, nblk, n_chains, stats, log,
-                                                          log_cap, err);
+  finalize_kernel<<<(n_chains + kFinalizeWarps - 1) / kFinalizeWarps, 32 * kFinalizeWarps, 0, s>>>(
+      partials, nblk, n_chains, stats, log, log_cap, err);
   return cudaGetLastError();
 }
 
@@ -136,8 +150,8 @@ cudaError_t launch_finalize_group(const double *partials, int nblk, int n_chains
                                   int *err, cudaStream_t s) {
   const int count = (n_chains - first + stride - 1) / stride;
   if (count <= 0) return cudaSuccess;
-  finalize_group_kernel<<<(count + 127) / 128, 128, 0, s>>>(partials, nblk, n_chains, first, stride,
-                                                            stats, log, log_cap, err);
+  finalize_group_kernel<<<(count + kFinalizeWarps - 1) / kFinalizeWarps, 32 * kFinalizeWarps, 0,
+                          s>>>(partials, nblk, n_chains, first, stride, stats, log, log_cap, err);
   return cudaGetLastError();
 }
 
