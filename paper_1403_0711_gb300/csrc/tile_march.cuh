@@ -138,7 +138,7 @@ __device__ bool march_tile(const TileJob<T> &j, const PhiloxKeys &K, unsigned ch
   // Plane k of this tile is other-colour plane z0 - 1 + k; it is ring plane
   // gb + k, in slot (gb + k) % kStages, completed in that slot's phase
   // (gb + k) / kStages.
-  auto slot_of = [&](int k) { return (gb + k) % kStages; };
+  auto slot_of = [&](int k) { return (gb + k) & (kStages - 1); };
   auto issue = [&](int k) {
     const int s = slot_of(k);
     const uint32_t bar = smem_addr(&bars[s]);
@@ -167,71 +167,93 @@ __device__ bool march_tile(const TileJob<T> &j, const PhiloxKeys &K, unsigned ch
   __syncthreads();
   bool aborted = *abort_flag != 0;
   int done = 1;  // planes 0..done completed for every thread
-  if (!aborted) {
-    if (tid == 0 && issued < n_planes) issue(issued++);
-    for (int k = 1; k <= j.nz; ++k) {
-      const bool got = wait_plane(k + 1);
-      const int z = j.z0 + k - 1;
-      const T *Pz = halo_slot(slot_of(k));
-      if (got) {
-        if (in_tile) {
-          ld_quad(halo_slot(slot_of(k + 1)) + (ty + 1) * W + 4 * qx, cp);
+
+  // per-thread constants of the plane loop
+  uint32_t pad0 = 0u, pad1 = 0u;  // quad lanes past x = Lx - 1 (kept at 0), row parity 0 / 1
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    if (2 * (4 * qx + i) >= j.Lx) pad0 |= 1u << i;
+    if (2 * (4 * qx + i) + 1 >= j.Lx) pad1 |= 1u << i;
+  }
+  const bool lo_ok = qx > 0, hi_ok = 4 * qx + 4 < W;
+  const int hrow = (ty + 1) * W + 4 * qx;  // this quad in a halo box (first row y0 - 1)
+  const int orow = ty * W + 4 * qx;        // this quad in an own box (first row y0)
+  T *outp = j.out + ((size_t)j.z0 * j.Ly + y) * W + 4 * qx;  // plane z0; one plane per step
+  const size_t pstride = (size_t)j.Ly * W;
+  int par = (c + y + j.z0) & 1;  // the row (y, z) holds x = 2h + par; flips with z
+
+  // Plane k (z = z0 + k - 1): M, C, P are the other colour's quads of planes
+  // z - 1, z, z + 1 (P loaded here).  The loop calls it with the names
+  // rotated, so no register is copied from plane to plane.
+  auto step = [&](int k, T(&M)[4], T(&C)[4], T(&P)[4]) -> bool {
+    const bool got = wait_plane(k + 1);
+    const T *Pz = halo_slot(slot_of(k)) + hrow;  // row y of plane z
+    if (got) {
+      if (in_tile) {
+        ld_quad(halo_slot(slot_of(k + 1)) + hrow, P);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) P[i] = T(0);
+      }
+      if (live) {
+        T ym[4], yp[4], xs[4], S[4], v[4];
+        ld_quad(Pz - W, ym);
+        ld_quad(Pz + W, yp);
+        if (par == 0) {
+          // x - 1 of h lies at h - 1 in the other colour, x + 1 at h
+          xs[0] = lo_ok ? Pz[-1] : T(0);
+          xs[1] = C[0]; xs[2] = C[1]; xs[3] = C[2];
         } else {
-#pragma unroll
-          for (int i = 0; i < 4; ++i) cp[i] = T(0);
+          // x - 1 of h lies at h, x + 1 at h + 1
+          xs[0] = C[1]; xs[1] = C[2]; xs[2] = C[3];
+          xs[3] = hi_ok ? Pz[4] : T(0);
         }
-        if (live) {
-          T ym[4], yp[4], xs[4], S[4], v[4];
-          ld_quad(Pz + ty * W + 4 * qx, ym);
-          ld_quad(Pz + (ty + 2) * W + 4 * qx, yp);
-          const int par = (c + y + z) & 1;  // row holds x = 2h + par
-          if (par == 0) {
-            // x - 1 of h lies at h - 1 in the other colour, x + 1 at h
-            xs[0] = qx > 0 ? Pz[(ty + 1) * W + 4 * qx - 1] : T(0);
-            xs[1] = c0[0]; xs[2] = c0[1]; xs[3] = c0[2];
-          } else {
-            // x - 1 of h lies at h, x + 1 at h + 1
-            xs[0] = c0[1]; xs[1] = c0[2]; xs[2] = c0[3];
-            xs[3] = (4 * qx + 4 < W) ? Pz[(ty + 1) * W + 4 * qx + 4] : T(0);
-          }
 #pragma unroll
-          for (int i = 0; i < 4; ++i) S[i] = ((cm[i] + cp[i]) + (ym[i] + yp[i])) + (c0[i] + xs[i]);
-          if (!OR) {
-            const uint32_t quad = ((uint32_t)z * (uint32_t)j.Ly + (uint32_t)y) * (uint32_t)j.Wq +
-                                  (uint32_t)qx;
-            const uint4 w = philox4x32_10(make_uint4(quad, j.pass, j.rng_id, (uint32_t)c), K);
-            v[0] = fma(S[0], Coef<T>::sixth, Noise<T>::of(w.x));
-            v[1] = fma(S[1], Coef<T>::sixth, Noise<T>::of(w.y));
-            v[2] = fma(S[2], Coef<T>::sixth, Noise<T>::of(w.z));
-            v[3] = fma(S[3], Coef<T>::sixth, Noise<T>::of(w.w));
-          } else {
-            T old[4];
-            ld_quad(own_slot(slot_of(k)) + ty * W + 4 * qx, old);
+        for (int i = 0; i < 4; ++i) S[i] = ((M[i] + P[i]) + (ym[i] + yp[i])) + (C[i] + xs[i]);
+        if (!OR) {
+          const uint32_t z = (uint32_t)(j.z0 + k - 1);
+          const uint32_t quad = (z * (uint32_t)j.Ly + (uint32_t)y) * (uint32_t)j.Wq + (uint32_t)qx;
+          const uint4 w = philox4x32_10(make_uint4(quad, j.pass, j.rng_id, (uint32_t)c), K);
+          v[0] = fma(S[0], Coef<T>::sixth, Noise<T>::of(w.x));
+          v[1] = fma(S[1], Coef<T>::sixth, Noise<T>::of(w.y));
+          v[2] = fma(S[2], Coef<T>::sixth, Noise<T>::of(w.z));
+          v[3] = fma(S[3], Coef<T>::sixth, Noise<T>::of(w.w));
+        } else {
+          T old[4];
+          ld_quad(own_slot(slot_of(k)) + orow, old);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) v[i] = fma(S[i], Coef<T>::third, -old[i]);
-          }
+          for (int i = 0; i < 4; ++i) v[i] = fma(S[i], Coef<T>::third, -old[i]);
+        }
+        const uint32_t pm = par ? pad1 : pad0;
+        if (pm) {
 #pragma unroll
           for (int i = 0; i < 4; ++i)
-            if (2 * (4 * qx + i) + par >= j.Lx) v[i] = T(0);  // keep the row padding at 0
-          st_quad(j.out + ((size_t)z * j.Ly + y) * W + 4 * qx, v);
+            if ((pm >> i) & 1u) v[i] = T(0);  // keep the row padding at 0
         }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          cm[i] = c0[i];
-          c0[i] = cp[i];
-        }
-      } else {
-        atomicOr(err, kErrTimeout);
-        *abort_flag = 1;
+        st_quad(outp, v);
       }
-      __syncthreads();
-      if (*abort_flag) {
-        aborted = true;
-        break;
-      }
-      done = k + 1;
-      // plane k is no longer read: refill its slot with plane k + kStages
-      if (tid == 0 && issued < n_planes) issue(issued++);
+    } else {
+      atomicOr(err, kErrTimeout);
+      *abort_flag = 1;
+    }
+    __syncthreads();
+    if (*abort_flag) return false;
+    done = k + 1;
+    // plane k is no longer read: refill its slot with plane k + kStages
+    if (tid == 0 && issued < n_planes) issue(issued++);
+    outp += pstride;
+    par ^= 1;
+    return true;
+  };
+
+  if (!aborted) {
+    if (tid == 0 && issued < n_planes) issue(issued++);
+    for (int k = 1; k <= j.nz; k += 3) {
+      if (!step(k, cm, c0, cp)) { aborted = true; break; }
+      if (k + 1 > j.nz) break;
+      if (!step(k + 1, c0, cp, cm)) { aborted = true; break; }
+      if (k + 2 > j.nz) break;
+      if (!step(k + 2, cp, cm, c0)) { aborted = true; break; }
     }
   }
   if (aborted && tid == 0) {
