@@ -75,7 +75,7 @@ def parse():
     ap.add_argument("--cv-global", action="store_true",
                     help="also run the whole-lattice control variate on the +-1 system")
     ap.add_argument("--workload", choices=["chains128", "large512", "sweep", "batched", "cv", "cube",
-                                           "cv_eval"],
+                                           "cv_eval", "paper"],
                     default="chains128", help="secondary workloads print their own line")
     ap.add_argument("--chains", type=int, default=N_CHAINS,
                     help="chains per GPU (smaller values only for profiler captures)")
@@ -178,13 +178,62 @@ def profiled_traffic(kernel):
         return None
 
 
-def golden_e_lat(name):
+def golden_e_lat(name, column=8):
     """Exact lattice energy of a seeded workload (tests/golden/e_lat.txt, written
-    by tests/golden/make_golden.py from the FP64 oracle)."""
+    by tests/golden/make_golden.py from the FP64 oracle); column 9 is the
+    continuum Eq. (s1) of the same charges."""
     for ln in (ROOT / "tests" / "golden" / "e_lat.txt").read_text().splitlines():
         if ln.startswith(name + " "):
-            return float(ln.split()[8])
+            return float(ln.split()[column])
     return None
+
+
+def paper_figures(args, stream):
+    """The paper's Fig. 1 and Fig. 2 workloads on one set of samples (every
+    charge set is measured on every sample: the samples depend only on the box):
+    128^3, 64 chains, 1 HB : 3 OR.  Fig. 2: q = 1 cubes of N = 2^3 .. 32^3 at
+    the box centre; Fig. 1: two charges q = 1, one at the centre, the other at
+    (n_x, L/2, L/2).  For M = 10^2 .. 10^6 samples (M = 64 x compound sweeps)
+    reports delta = |MC - E| / |E| against the exact lattice value and against
+    the continuum Coulomb sum Eq. (s1), with the batch-means error."""
+    import math
+
+    import torch
+
+    from paper_1403_0711_gb300 import coulps, inputs
+    box = (L, L, L)
+    lat = coulps.Lattice(box, n_chains=N_CHAINS, precision=coulps.F32, seed=2014, stream=stream)
+    sets = [(f"fig2_cube_N{s ** 3}", f"cube_128c_n{s ** 3}_q1", inputs.cube(box, s))
+            for s in (2, 4, 8, 16, 32)]
+    sets += [(f"fig1_pair_nx{nx}", f"twobody_128c_nx{nx}", inputs.two_body(box, nx))
+             for nx in (65, 66, 68, 72, 80, 96, 112, 127)]
+    chs = [coulps.Charges(lat, s, q) for _, _, (s, q) in sets]
+    lat.sweep(300, N_HB, N_OR)
+    torch.cuda.synchronize()
+    rows = {name: {"set": name, "n_charges": len(q), "e_lat": golden_e_lat(gold),
+                   "e_continuum": golden_e_lat(gold, 9), "by_M": []}
+            for name, gold, (_, q) in sets}
+    done = 0
+    t0 = time.perf_counter()
+    for M in (10 ** 2, 10 ** 3, 10 ** 4, 10 ** 5, 10 ** 6):
+        k = math.ceil(M / N_CHAINS) - done
+        if k > 0:
+            coulps.run_sets(lat, chs, 0, k, N_HB, N_OR)
+            done += k
+        lat.sync()
+        wall = time.perf_counter() - t0
+        for (name, _, _), ch in zip(sets, chs):
+            est = ch.estimate()
+            r = rows[name]
+            r["by_M"].append({
+                "M": est["n"], "wall_s": wall, "mean": est["mean"], "stderr": est["stderr"],
+                "delta_lat": abs(est["mean"] - r["e_lat"]) / abs(r["e_lat"]),
+                "delta_continuum": abs(est["mean"] - r["e_continuum"]) / abs(r["e_continuum"]),
+                "rel_stderr": est["stderr"] / abs(r["e_lat"])})
+    for ch in chs:
+        ch.close()
+    lat.close()
+    return list(rows.values())
 
 
 def time_to_accuracy(est, seconds, world, eps=1e-3, name="bench_128c_n4096_pm"):
@@ -475,6 +524,8 @@ def run_extra(args):
                         "ms_per_step": ms,
                         "algorithmic_GBps": rate / PASSES * (8 + 12 * N_OR) / 1e9})
         b.close()
+    elif args.workload == "paper":
+        results.extend(paper_figures(args, stream))
     elif args.workload == "cv_eval":
         results.append(cv_eval_cost(args, stream))
     elif args.workload == "cv":

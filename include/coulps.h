@@ -169,6 +169,20 @@ int coulps_samples(coulps_charges_t ch, double *QPe, int64_t cap, int64_t *n);
 /* Forget all samples (running sums, batches and log). Asynchronous. */
 int coulps_reset_stats(coulps_charges_t ch);
 
+/* Several charge sets on the same samples.  A sample of the field does not
+ * depend on where the charges sit (the paper's argument for reusing one
+ * sample set), so any number of charge sets of one lattice can be measured
+ * on every sample: coulps_measure_sets takes one sample of every set from the
+ * current fields (one gather launch and one finalize launch per 32 sets);
+ * coulps_run_sets runs n_therm unmeasured and n_meas measured compound
+ * sweeps, each measured one followed by a sample of every set (captured once
+ * per call as a CUDA graph when n_meas >= 4).  Each set keeps its own
+ * statistics and log (coulps_estimate etc. per set).  Asynchronous.
+ * Errors: EINVAL (no sets, a set of another lattice), ECUDA. */
+int coulps_measure_sets(coulps_lattice_t lat, const coulps_charges_t *sets, int n_sets);
+int coulps_run_sets(coulps_lattice_t lat, const coulps_charges_t *sets, int n_sets, int n_therm,
+                    int n_meas, int n_hb, int n_or);
+
 /* Replace the positions and values of the ch's n charges (same n as at
  * creation) from host arrays, asynchronously: the arrays are converted and
  * staged in library-owned pinned memory before the call returns, so the

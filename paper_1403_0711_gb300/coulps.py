@@ -40,6 +40,7 @@ EXPORTS = (
     "coulps_set_schedule", "coulps_cv_conv3d_tanh", "coulps_cv_pack_region",
     "coulps_cv_stein_region", "coulps_cv_record", "coulps_cv_chain_stats", "coulps_cv_estimate",
     "coulps_cv_reset", "coulps_cv_charge_term", "coulps_set_fused", "coulps_set_pass_tile",
+    "coulps_measure_sets", "coulps_run_sets",
 )
 SCHEDULE_ALIGNED, SCHEDULE_PHASED = 0, 1
 STAT_STRIDE = 72
@@ -127,6 +128,8 @@ def load(path: str | Path | None = None):
         "coulps_cv_estimate": (i32, [vp, P(f64), P(f64), P(f64), P(i64)]),
         "coulps_cv_reset": (i32, [vp]),
         "coulps_set_fused": (i32, [vp, i32]),
+        "coulps_measure_sets": (i32, [vp, P(vp), i32]),
+        "coulps_run_sets": (i32, [vp, P(vp), i32, i32, i32, i32, i32]),
         "coulps_set_pass_tile": (i32, [vp, i32, i32]),
         "coulps_cv_charge_term": (i32, [vp, vp, vp, vp, vp, i32, i32, P(ctypes.c_int32), i32, vp,
                                         i64, vp, vp]),
@@ -365,6 +368,25 @@ class Charges:
 
     def cv_reset(self):
         _check(self._lib.coulps_cv_reset(self.handle), "coulps_cv_reset")
+
+
+def _set_array(sets):
+    arr = (ctypes.c_void_p * len(sets))(*[c.handle for c in sets])
+    return arr
+
+
+def measure_sets(lattice, sets):
+    """One sample of every charge set (all of `lattice`) from the current fields."""
+    sets = list(sets)
+    _check(load().coulps_measure_sets(lattice.handle, _set_array(sets), len(sets)),
+           "coulps_measure_sets")
+
+
+def run_sets(lattice, sets, n_therm, n_meas, n_hb=1, n_or=0):
+    """n_therm + n_meas compound sweeps; every measured one samples every set."""
+    sets = list(sets)
+    _check(load().coulps_run_sets(lattice.handle, _set_array(sets), len(sets), int(n_therm),
+                                  int(n_meas), int(n_hb), int(n_or)), "coulps_run_sets")
 
 
 def pool_stats(rows):

@@ -7,6 +7,7 @@
 // (the host-side counterpart of the paper's final mpi_reduce).
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -86,6 +87,10 @@ struct coulps_lattice {
   const void *sgraph_key = nullptr;
   int sgraph_hb = -1, sgraph_or = -1;
   Tile sgraph_tile = {0, 0};
+  // measured compound sweep + multi-set gather (coulps_run_sets) as a graph
+  cudaGraphExec_t mgraph = nullptr;
+  std::vector<const void *> mgraph_key;
+  int mgraph_hb = -1, mgraph_or = -1;
 };
 
 struct coulps_charges {
@@ -434,7 +439,33 @@ int enqueue_measure(coulps_lattice *L, coulps_charges *C) {
   return COULPS_OK;
 }
 
+// Every set samples the current fields: kMaxSets per gather launch.
+int enqueue_measure_sets(coulps_lattice *L, coulps_charges *const *sets, int n_sets) {
+  for (int k0 = 0; k0 < n_sets; k0 += kMaxSets) {
+    SetTable t;
+    t.n_sets = n_sets - k0 < kMaxSets ? n_sets - k0 : kMaxSets;
+    for (int k = 0; k < t.n_sets; ++k) {
+      coulps_charges *C = sets[k0 + k];
+      t.idx[k] = C->d_idx;
+      t.q[k] = C->d_q;
+      t.n[k] = C->n;
+      t.partials[k] = C->d_partials;
+      t.nblk[k] = C->nblk;
+      t.stats[k] = C->d_stats;
+      t.log[k] = C->d_log;
+      t.log_cap[k] = C->log_cap;
+    }
+    CK(launch_measure_sets(L->g, L->field, t, L->d_err, L->stream));
+  }
+  return COULPS_OK;
+}
+
 void drop_graph(coulps_lattice *L) {
+  // launches of these graphs may still be queued: let them finish first
+  if (L->graph || L->sgraph || L->mgraph) cudaStreamSynchronize(L->stream);
+  if (L->mgraph) cudaGraphExecDestroy(L->mgraph);
+  L->mgraph = nullptr;
+  L->mgraph_key.clear();
   if (L->graph) cudaGraphExecDestroy(L->graph);
   L->graph = nullptr;
   L->graph_key = nullptr;
@@ -877,7 +908,9 @@ int coulps_charges_create(coulps_lattice_t L, int64_t n, const int32_t *site, co
 void coulps_charges_destroy(coulps_charges_t C) {
   if (!C) return;
   coulps_lattice *L = C->lat;
-  if (L->graph_key == C) drop_graph(L);
+  if (L->graph_key == C ||
+      std::find(L->mgraph_key.begin(), L->mgraph_key.end(), (const void *)C) != L->mgraph_key.end())
+    drop_graph(L);
   dev_free(L->alloc, C->d_idx, L->stream);
   dev_free(L->alloc, C->d_q, L->stream);
   dev_free(L->alloc, C->d_partials, L->stream);
@@ -967,6 +1000,70 @@ int coulps_run(coulps_lattice_t L, coulps_charges_t C, int n_therm, int n_meas, 
     L->pass += (uint64_t)(n_hb + n_or);
   }
   return COULPS_OK;
+}
+
+static int check_sets(coulps_lattice *L, const coulps_charges_t *sets, int n_sets) {
+  if (!L || !sets || n_sets < 1) return COULPS_EINVAL;
+  for (int k = 0; k < n_sets; ++k)
+    if (!sets[k] || sets[k]->lat != L) return COULPS_EINVAL;
+  return COULPS_OK;
+}
+
+int coulps_measure_sets(coulps_lattice_t L, const coulps_charges_t *sets, int n_sets) {
+  int st = check_sets(L, sets, n_sets);
+  if (st) return st;
+  return enqueue_measure_sets(L, sets, n_sets);
+}
+
+int coulps_run_sets(coulps_lattice_t L, const coulps_charges_t *sets, int n_sets, int n_therm,
+                    int n_meas, int n_hb, int n_or) {
+  int st = check_sets(L, sets, n_sets);
+  if (st) return st;
+  if (n_therm < 0 || n_meas < 0 || n_hb < 0 || n_or < 0) return COULPS_EINVAL;
+  st = coulps_sweep(L, n_therm, n_hb, n_or);
+  if (st || n_meas == 0) return st;
+  // one measured compound sweep + the multi-set gather as a graph, kept for
+  // later calls with the same sets and mix (tile changes drop it)
+  std::vector<const void *> key(sets, sets + n_sets);
+  const bool capturable = L->stream != nullptr && !L->profiling && n_meas >= 4;
+  if (capturable && (!L->mgraph || L->mgraph_key != key || L->mgraph_hb != n_hb ||
+                     L->mgraph_or != n_or)) {
+    drop_graph(L);
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t gr = nullptr;
+    CK(cudaStreamBeginCapture(L->stream, cudaStreamCaptureModeThreadLocal));
+    int s1 = enqueue_compound(L, n_hb, n_or, nullptr);
+    int s2 = s1 ? s1 : enqueue_measure_sets(L, sets, n_sets);
+    cudaError_t e = cudaStreamEndCapture(L->stream, &gr);
+    if (s2 || e != cudaSuccess) {
+      cudaGetLastError();
+      if (gr) cudaGraphDestroy(gr);
+      return s2 ? s2 : COULPS_ECUDA;
+    }
+    e = cudaGraphInstantiate(&exec, gr, 0);
+    cudaGraphDestroy(gr);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return COULPS_ECUDA;
+    }
+    L->mgraph = exec;
+    L->mgraph_key = key;
+    L->mgraph_hb = n_hb;
+    L->mgraph_or = n_or;
+  }
+  for (int k = 0; k < n_meas && !st; ++k) {
+    if (capturable) {
+      if (cudaGraphLaunch(L->mgraph, L->stream) != cudaSuccess) {
+        cudaGetLastError();
+        st = COULPS_ECUDA;
+      }
+    } else {
+      st = enqueue_compound(L, n_hb, n_or, nullptr);
+      if (!st) st = enqueue_measure_sets(L, sets, n_sets);
+    }
+    if (!st) L->pass += (uint64_t)(n_hb + n_or);
+  }
+  return st;
 }
 
 int coulps_pool_stats(const double *st, int64_t n_rows, double *mean, double *stderr_bm,

@@ -111,6 +111,24 @@ cudaError_t launch_finalize_group(const double *partials, int nblk, int n_chains
                                   int stride, double *stats, double *log, int64_t log_cap,
                                   int *err, cudaStream_t s);
 
+// Several charge sets measured on the same fields in one gather launch and one
+// finalize launch (per set: its storage offsets, charges, CTA partials,
+// blocks per chain, estimator state and optional log).
+constexpr int kMaxSets = 32;
+struct SetTable {
+  const uint32_t *idx[kMaxSets];
+  const double *q[kMaxSets];
+  int64_t n[kMaxSets];
+  double *partials[kMaxSets];
+  int nblk[kMaxSets];
+  double *stats[kMaxSets];
+  double *log[kMaxSets];
+  int64_t log_cap[kMaxSets];
+  int n_sets;
+};
+cudaError_t launch_measure_sets(const Geometry &g, const void *field, const SetTable &t,
+                                int *err, cudaStream_t s);
+
 // Entry packing of the fused gather.
 constexpr uint32_t kGatherColourBit = 0x80000000u;
 

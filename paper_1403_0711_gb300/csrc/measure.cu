@@ -115,7 +115,83 @@ __global__ void reset_stats_kernel(double *stats, int n_chains) {
   stats[i] = (i % kStatStride == kStatBatchLen) ? 1.0 : 0.0;
 }
 
+// Several charge sets on the same fields (the samples do not depend on where
+// the charges sit): CTA (b, chain, s) does block b of set s; sets with fewer
+// blocks leave early.  Same per-CTA arithmetic as gather_kernel.
+template <typename T>
+__global__ void __launch_bounds__(kGatherThreads)
+    gather_sets_kernel(const T *__restrict__ field, size_t chain_elems, const SetTable t) {
+  const int set = blockIdx.z;
+  const int nblk = t.nblk[set];
+  if ((int)blockIdx.x >= nblk) return;
+  const int chain = blockIdx.y;
+  const T *f = field + (size_t)chain * chain_elems;
+  const uint32_t *idx = t.idx[set];
+  const double *q = t.q[set];
+  const int64_t n = t.n[set];
+  double sq = 0.0, sp = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * kGatherThreads + threadIdx.x; i < n;
+       i += (int64_t)nblk * kGatherThreads) {
+    const double v = q[i] * (double)f[idx[i]];
+    sq += v;
+    sp += v * v;
+  }
+  sq = warp_sum(sq);
+  sp = warp_sum(sp);
+  __shared__ double red[2][kGatherThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][wid] = sq;
+    red[1][wid] = sp;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    sq = lane < kGatherThreads / 32 ? red[0][lane] : 0.0;
+    sp = lane < kGatherThreads / 32 ? red[1][lane] : 0.0;
+    sq = warp_sum(sq);
+    sp = warp_sum(sp);
+    if (lane == 0) {
+      t.partials[set][2 * ((size_t)chain * nblk + blockIdx.x) + 0] = sq;
+      t.partials[set][2 * ((size_t)chain * nblk + blockIdx.x) + 1] = sp;
+    }
+  }
+}
+
+// warp per (chain, set)
+__global__ void finalize_sets_kernel(const SetTable t, int n_chains, int *err) {
+  const int set = blockIdx.y;
+  const int chain = blockIdx.x * kFinalizeWarps + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (chain >= n_chains) return;
+  double Q, P;
+  chain_QP(t.partials[set], t.nblk[set], chain, lane, Q, P);
+  if (lane != 0) return;
+  double *st = t.stats[set] + (size_t)chain * kStatStride;
+  const int64_t s = (int64_t)st[kStatN];
+  double *log = t.log[set];
+  double *row = (log != nullptr && s < t.log_cap[set]) ? log + 3 * ((size_t)s * n_chains + chain)
+                                                        : nullptr;
+  record_sample(st, Q, P, row, err);
+}
+
 }  // namespace
+
+cudaError_t launch_measure_sets(const Geometry &g, const void *field, const SetTable &t,
+                                int *err, cudaStream_t s) {
+  if (t.n_sets < 1) return cudaSuccess;
+  int max_nblk = 1;
+  for (int k = 0; k < t.n_sets; ++k) max_nblk = t.nblk[k] > max_nblk ? t.nblk[k] : max_nblk;
+  dim3 grid(max_nblk, g.n_chains, t.n_sets);
+  if (g.precision == COULPS_F32)
+    gather_sets_kernel<float><<<grid, kGatherThreads, 0, s>>>(
+        reinterpret_cast<const float *>(field), g.chain_elems, t);
+  else
+    gather_sets_kernel<double><<<grid, kGatherThreads, 0, s>>>(
+        reinterpret_cast<const double *>(field), g.chain_elems, t);
+  dim3 fgrid((g.n_chains + kFinalizeWarps - 1) / kFinalizeWarps, t.n_sets);
+  finalize_sets_kernel<<<fgrid, 32 * kFinalizeWarps, 0, s>>>(t, g.n_chains, err);
+  return cudaGetLastError();
+}
 
 int gather_blocks(int64_t n) {
   // about 4 charges per thread, at least one CTA, at most 64 per chain

@@ -14,11 +14,20 @@ from oracle import oracle  # noqa: E402
 from paper_1403_0711_gb300 import inputs  # noqa: E402
 
 CASES = [
-    # name, L, generator, N, seed, method
+    # name, L, generator, N, seed, method  (two_body: the seed column holds n_x)
     ("plain_16c_n8_pm", (16, 16, 16), "plus_minus", 8, 1, "dense"),
     ("bench_128c_n4096_pm", (128, 128, 128), "plus_minus", 4096, 1, "dst"),
     ("cube_16c_n8_q1", (16, 16, 16), "cube", 8, 0, "dense"),
     ("cube_128c_n8_q1", (128, 128, 128), "cube", 8, 0, "dst"),
+    # the paper's Fig. 2 cubes (q = 1, N = 2^3 .. 32^3 at the centre of 128^3)
+    ("cube_128c_n64_q1", (128, 128, 128), "cube", 64, 0, "dst"),
+    ("cube_128c_n512_q1", (128, 128, 128), "cube", 512, 0, "dst"),
+    ("cube_128c_n4096_q1", (128, 128, 128), "cube", 4096, 0, "dst"),
+    ("cube_128c_n32768_q1", (128, 128, 128), "cube", 32768, 0, "dst"),
+] + [
+    # the paper's Fig. 1 pairs: one charge at (L/2, L/2, L/2), the other at (n_x, L/2, L/2)
+    (f"twobody_128c_nx{nx}", (128, 128, 128), "two_body", 2, nx, "dst")
+    for nx in (65, 66, 68, 72, 80, 96, 112, 127)
 ]
 
 
@@ -28,6 +37,8 @@ def charges(gen, L, n, seed):
     if gen == "cube":
         side = round(n ** (1 / 3))
         return inputs.cube(L, side)
+    if gen == "two_body":
+        return inputs.two_body(L, seed)
     raise ValueError(gen)
 
 
@@ -37,7 +48,7 @@ def main():
     for name, L, gen, n, seed, method in CASES:
         sites, q = charges(gen, L, n, seed)
         e = oracle.e_lat(L, sites, q, method)
-        cont = oracle.coulomb_direct(sites, q) if n <= 4096 else float("nan")
+        cont = oracle.coulomb_direct(sites, q)
         lines.append(f"{name} {L[0]} {L[1]} {L[2]} {gen} {n} {seed} {method} {e:.15e} {cont:.15e}")
         print(lines[-1], flush=True)
     (Path(__file__).resolve().parent / "e_lat.txt").write_text("\n".join(lines) + "\n")
