@@ -135,3 +135,13 @@ def random_params(seed, scale=0.3):
         "W3": rng.standard_normal((1, 16, 3, 3, 3)) * scale / 4,
         "b3": rng.standard_normal(1) * 0.1,
     }
+
+
+def global_stein_term(phi, rho, h):
+    """T g for the global control variate g_x = Q(phi) h_x, Q = sum_x rho_x phi_x
+    and h a fixed field: dg_x/dphi_x = rho_x h_x, so
+        T g = sum_x rho_x h_x - Q sum_x h_x (A phi)_x = h . rho - Q (A h) . phi
+    (A symmetric).  Mean 0 under exp(-H_L) for any h; with h = -G rho it equals
+    Q^2 - rho . G rho for every phi."""
+    Q = float(np.sum(rho * phi))
+    return float(np.sum(h * rho) - Q * np.sum(apply_A(h) * phi))

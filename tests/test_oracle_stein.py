@@ -88,3 +88,55 @@ def test_region_divergence_matches_finite_differences():
         b[z, y, x] -= h
         fd += (stein.forward(a, rho, p)["g"][z, y, x] - stein.forward(b, rho, p)["g"][z, y, x]) / (2 * h)
     assert abs(div - fd) < 1e-7 * max(1.0, abs(div))
+
+
+def test_global_stein_term_matches_finite_differences_and_closed_form(orc):
+    """Global control variate g = Q h: the divergence by finite differences of g,
+    and with h = -G rho (dense inverse) the closed form T g = Q^2 - rho.G.rho
+    for an arbitrary phi."""
+    from oracle import stein
+    L = (4, 3, 5)
+    rng = np.random.default_rng(11)
+    phi = rng.standard_normal((L[2], L[1], L[0]))
+    rho = np.zeros_like(phi)
+    rho[1, 1, 2], rho[3, 0, 0], rho[4, 2, 3] = 1.0, -1.0, 0.5
+    h = rng.standard_normal(phi.shape)
+    # T g from its definition: divergence by central differences of g_x = Q h_x
+    eps = 1e-6
+    div = 0.0
+    for idx in np.ndindex(phi.shape):
+        a, b = phi.copy(), phi.copy()
+        a[idx] += eps
+        b[idx] -= eps
+        div += (np.sum(rho * a) * h[idx] - np.sum(rho * b) * h[idx]) / (2 * eps)
+    g = np.sum(rho * phi) * h
+    tg_def = div - float(np.sum(g * stein.apply_A(phi)))
+    tg = stein.global_stein_term(phi, rho, h)
+    assert abs(tg - tg_def) < 1e-7 * max(1.0, abs(tg)), (tg, tg_def)
+    # closed form with h = -G rho
+    G = orc.green_dense(L)
+    r = rho.reshape(-1)
+    hG = -(G @ r).reshape(phi.shape)
+    Q = float(np.sum(rho * phi))
+    assert abs(stein.global_stein_term(phi, rho, hG) - (Q * Q - r @ G @ r)) < 1e-12 * (1 + Q * Q)
+
+
+def test_global_stein_term_has_zero_mean_under_exact_samples(orc):
+    from oracle import stein
+    L = (3, 4, 3)
+    A = orc.laplacian_dense(L)
+    C = np.linalg.cholesky(A)
+    rng = np.random.default_rng(12)
+    rho = np.zeros((L[2], L[1], L[0]))
+    rho[1, 1, 1], rho[0, 3, 2], rho[2, 0, 0] = 1.0, -1.0, 0.7
+    h = rng.standard_normal(rho.shape) + 2.0 * rho  # h . rho clearly non-zero
+    n = 20000
+    z = rng.standard_normal((n, A.shape[0]))
+    phis = np.linalg.solve(C.T, z.T).T.reshape(n, L[2], L[1], L[0])
+    tg = np.array([stein.global_stein_term(p, rho, h) for p in phis])
+    se = tg.std(ddof=1) / math.sqrt(n)
+    assert abs(tg.mean()) < 4 * se, (tg.mean(), se)
+    # the second part alone averages to h . rho, not 0 (the test has power)
+    qa = np.array([np.sum(rho * p) * np.sum(stein.apply_A(h) * p) for p in phis])
+    assert abs(qa.mean()) > 8 * qa.std(ddof=1) / math.sqrt(n)
+    assert abs(qa.mean() - np.sum(h * rho)) < 4 * qa.std(ddof=1) / math.sqrt(n)
