@@ -65,7 +65,9 @@ def parse():
     ap.add_argument("--fused", choices=["on", "all", "off"], default="on",
                     help="fused passes (one kernel per pass, ping-pong field copies): "
                          "over-relaxation passes (on), all passes, or none")
-    ap.add_argument("--cv-steps", type=int, default=800)
+    ap.add_argument("--cv-steps", type=int, default=800, help="training steps of the learned CV")
+    ap.add_argument("--gcv-steps", type=int, default=3000,
+                    help="headline run: compound sweeps with the global control variate (0: skip)")
     ap.add_argument("--cv-rounds", type=int, default=64)
     ap.add_argument("--cube-seconds", type=float, default=600.0)
     ap.add_argument("--cv-halo", type=int, default=3,
@@ -75,7 +77,7 @@ def parse():
     ap.add_argument("--cv-global", action="store_true",
                     help="also run the whole-lattice control variate on the +-1 system")
     ap.add_argument("--workload", choices=["chains128", "large512", "sweep", "batched", "cv", "cube",
-                                           "cv_eval", "paper"],
+                                           "cv_eval", "paper", "gcv"],
                     default="chains128", help="secondary workloads print their own line")
     ap.add_argument("--chains", type=int, default=N_CHAINS,
                     help="chains per GPU (smaller values only for profiler captures)")
@@ -186,6 +188,74 @@ def golden_e_lat(name, column=8):
         if ln.startswith(name + " "):
             return float(ln.split()[column])
     return None
+
+
+def gcv_time_to_accuracy(args, stream):
+    """Time to 1e-3 |E_lat| on the headline system (128^3, 64 chains, N = 4096
+    charges +-1, 1 HB : 3 OR) with the global control variate g = Q h (h from
+    SOR on A h = -rho, set up on the device), measured directly: sample with
+    the control variate recorded every compound sweep until its batch-means
+    error reaches 1e-3 |E_lat| (or --cube-seconds).  The plain estimator of the
+    same samples gives the variance ratio and its own projected time."""
+    import torch
+
+    from paper_1403_0711_gb300 import coulps, inputs
+    box = (L, L, L)
+    sites, q = inputs.plus_minus(box, N_CHARGES, seed=1)
+    e_lat = golden_e_lat("bench_128c_n4096_pm")
+    target = 1e-3 * abs(e_lat)
+    lat = coulps.Lattice(box, n_chains=N_CHAINS, precision=coulps.F32, seed=20140303, stream=stream)
+    ch = coulps.Charges(lat, sites, q)
+    lat.sweep(300, N_HB, N_OR)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g = coulps.GlobalCV(ch)
+    t_setup = time.perf_counter() - t0
+    info = g.info()
+    # cost per compound sweep with and without the control variate
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ch.run(0, 20, N_HB, N_OR)
+    ev[0].record(stream)
+    ch.run(0, 200, N_HB, N_OR)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    ms_plain = ev[0].elapsed_time(ev[1]) / 200
+    g.run(20, N_HB, N_OR, 1.0)
+    ev[0].record(stream)
+    g.run(200, N_HB, N_OR, 1.0)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    ms_cv = ev[0].elapsed_time(ev[1]) / 200
+    ch.reset_stats()
+    ch.cv_reset()
+    t0 = time.perf_counter()
+    rounds = 0
+    est = None
+    while time.perf_counter() - t0 < args.cube_seconds:
+        g.run(2000, N_HB, N_OR, 1.0)
+        rounds += 2000
+        est = ch.cv_estimate()
+        if est["stderr"] == est["stderr"] and est["stderr"] <= target:
+            break
+    wall = time.perf_counter() - t0
+    plain = ch.estimate()
+    t_plain_proj = rounds * ms_plain / 1e3 * (plain["stderr"] / target) ** 2
+    r = {"system": "pm4096_128c_global_cv", "e_lat": e_lat, "sor_iterations": 6 * L + 50,
+         "solve_residual": info["residual"], "setup_s": t_setup,
+         "ms_compound_sweep_plain": ms_plain, "ms_compound_sweep_with_cv": ms_cv,
+         "rounds": rounds, "samples": est["n"], "wall_s_cv": wall,
+         "mean_cv": est["mean"], "stderr_cv": est["stderr"], "tau_int_cv": est["tau_int"],
+         "delta_cv": abs(est["mean"] - e_lat) / abs(e_lat),
+         "mean_plain": plain["mean"], "stderr_plain": plain["stderr"],
+         "tau_int_plain": plain["tau_int"],
+         "error_variance_ratio": (est["stderr"] / plain["stderr"]) ** 2,
+         "reached_1e-3_cv": bool(est["stderr"] <= target),
+         "s_to_1e-3_cv_incl_setup": wall + t_setup,
+         "projected_s_to_1e-3_plain": t_plain_proj}
+    g.close()
+    ch.close()
+    lat.close()
+    return r
 
 
 def paper_figures(args, stream):
@@ -440,6 +510,36 @@ def run_ours(args):
            "steps": args.e2e_steps,
            "path": "coulps_charges_update + coulps_run(0, 1, 1, 3) + coulps_estimate"}
 
+    # time to 1e-3 with the global control variate g = Q h (projected from a
+    # short run; bench.py --workload gcv measures it directly)
+    tta_cv = None
+    if args.gcv_steps > 0:
+        ch.reset_stats()
+        ch.cv_reset()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        gcv = coulps.GlobalCV(ch)
+        setup = time.perf_counter() - t0
+        ev0.record(stream)
+        gcv.run(args.gcv_steps, N_HB, N_OR, 1.0)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        cv_s = ev0.elapsed_time(ev1) / 1e3
+        est_cv, est_pl = ch.cv_estimate(), ch.estimate()
+        e_lat = golden_e_lat("bench_128c_n4096_pm")
+        if est_cv["stderr"] > 0 and est_pl["stderr"] > 0:
+            t_cv = cv_s * (est_cv["stderr"] / (1e-3 * abs(e_lat))) ** 2
+            tta_cv = {"eps": 1e-3, "estimator": "global control variate g = Q h (h by SOR), c = 1",
+                      "setup_s": setup, "samples": est_cv["n"] * world,
+                      "ms_per_step_with_cv": 1e3 * cv_s / args.gcv_steps,
+                      "mean": est_cv["mean"], "stderr": est_cv["stderr"],
+                      "tau_int": est_cv["tau_int"],
+                      "delta": abs(est_cv["mean"] - e_lat) / abs(e_lat),
+                      "error_variance_ratio_vs_plain_same_samples":
+                          (est_cv["stderr"] / est_pl["stderr"]) ** 2,
+                      "projected_seconds": t_cv + setup, "projected_hours": (t_cv + setup) / 3600}
+        gcv.close()
+
     out = None
     if rank == 0:
         # per compound sweep: nf fused passes, 2 (PASSES - nf) half-sweeps, a
@@ -454,7 +554,7 @@ def run_ours(args):
             "data": "synthetic", "config": dict(CONFIG, parallelism=f"replicas{world}", n_chains_per_gpu=n_chains,
                                            fused_passes=args.fused),
             "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-            "time_to_1e-3": tta, "estimate_after_e2e": est,
+            "time_to_1e-3": tta, "time_to_1e-3_cv": tta_cv, "estimate_after_e2e": est,
         }
         if world == 1:
             rate, cores, n = cpu_oracle_rate(args.cpu_seconds)
@@ -524,6 +624,8 @@ def run_extra(args):
                         "ms_per_step": ms,
                         "algorithmic_GBps": rate / PASSES * (8 + 12 * N_OR) / 1e9})
         b.close()
+    elif args.workload == "gcv":
+        results.append(gcv_time_to_accuracy(args, stream))
     elif args.workload == "paper":
         results.extend(paper_figures(args, stream))
     elif args.workload == "cv_eval":

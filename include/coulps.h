@@ -441,6 +441,36 @@ int coulps_cv_estimate(coulps_charges_t ch, double *mean, double *stderr_bm, dou
                        int64_t *n);
 int coulps_cv_reset(coulps_charges_t ch);
 
+/* ---- global control variate ------------------------------------------- */
+/* Not in the paper.  g_x = Q(phi) h_x with Q = sum_i q_i phi(r_i) and a fixed
+ * field h of the charge set: its Stein term
+ *   T g = h . rho - Q (A h) . phi            (rho = charge density)
+ * has mean 0 under exp(-H_L) for any h, and with h = -G rho it equals
+ * Q^2 - rho.G.rho, which removes from e = Q^2 - P all of its variance except
+ * that of P.  coulps_gcv_create solves A u = -rho by n_iter red/black SOR
+ * iterations (FP64, the optimal factor of the box) on the lattice's stream,
+ * rounds u to the fixed-point grid 2^-k with 13 max|u| 2^k < 2^24 (h), so
+ * that v = A h is exact in FP32 (kept in the field's layout) and h . rho is
+ * formed in FP64: E[T g] = 0 holds for the h actually used.  Per sample
+ * v . phi adds FP32 products in FP32 over 16 sites and those in FP64.
+ * Synchronises.  The object reads the charge set's positions at creation
+ * (re-create it after coulps_charges_update; destroy it before the set).
+ * coulps_gcv_info: out[0] = h . rho, out[1] = |A u + rho| / |rho| (synchronises).
+ * coulps_gcv_h: h (fp32) in natural order (synchronises).
+ * coulps_gcv_eval: per chain T g of the current fields into tg (device,
+ *   n_chains doubles; NULL = internal buffer); asynchronous.
+ * coulps_gcv_run: n_meas measured compound sweeps; each records the plain
+ *   Eq. (nsum2) sample and the control-variate sample e - c T g
+ *   (coulps_cv_estimate reads the latter).  Synchronises at the end.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+typedef struct coulps_gcv *coulps_gcv_t;
+int coulps_gcv_create(coulps_charges_t ch, int n_iter, coulps_gcv_t *out);
+void coulps_gcv_destroy(coulps_gcv_t gcv);
+int coulps_gcv_info(coulps_gcv_t gcv, double out[2]);
+int coulps_gcv_h(coulps_gcv_t gcv, float *host_xyz);
+int coulps_gcv_eval(coulps_gcv_t gcv, double *tg);
+int coulps_gcv_run(coulps_gcv_t gcv, int n_meas, int n_hb, int n_or, double c);
+
 /* ---- allocation-free measurement --------------------------------------- */
 /* The paper has no counterpart to this entry point.  It serves callers that
  * cannot allocate device memory when they measure: code running while a CUDA

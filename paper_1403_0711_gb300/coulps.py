@@ -40,7 +40,8 @@ EXPORTS = (
     "coulps_set_schedule", "coulps_cv_conv3d_tanh", "coulps_cv_pack_region",
     "coulps_cv_stein_region", "coulps_cv_record", "coulps_cv_chain_stats", "coulps_cv_estimate",
     "coulps_cv_reset", "coulps_cv_charge_term", "coulps_set_fused", "coulps_set_pass_tile",
-    "coulps_measure_sets", "coulps_run_sets",
+    "coulps_measure_sets", "coulps_run_sets", "coulps_gcv_create", "coulps_gcv_destroy",
+    "coulps_gcv_info", "coulps_gcv_h", "coulps_gcv_eval", "coulps_gcv_run",
 )
 SCHEDULE_ALIGNED, SCHEDULE_PHASED = 0, 1
 STAT_STRIDE = 72
@@ -129,6 +130,12 @@ def load(path: str | Path | None = None):
         "coulps_cv_reset": (i32, [vp]),
         "coulps_set_fused": (i32, [vp, i32]),
         "coulps_measure_sets": (i32, [vp, P(vp), i32]),
+        "coulps_gcv_create": (i32, [vp, i32, P(vp)]),
+        "coulps_gcv_destroy": (None, [vp]),
+        "coulps_gcv_info": (i32, [vp, P(f64)]),
+        "coulps_gcv_h": (i32, [vp, P(ctypes.c_float)]),
+        "coulps_gcv_eval": (i32, [vp, vp]),
+        "coulps_gcv_run": (i32, [vp, i32, i32, i32, f64]),
         "coulps_run_sets": (i32, [vp, P(vp), i32, i32, i32, i32, i32]),
         "coulps_set_pass_tile": (i32, [vp, i32, i32]),
         "coulps_cv_charge_term": (i32, [vp, vp, vp, vp, vp, i32, i32, P(ctypes.c_int32), i32, vp,
@@ -368,6 +375,54 @@ class Charges:
 
     def cv_reset(self):
         _check(self._lib.coulps_cv_reset(self.handle), "coulps_cv_reset")
+
+
+class GlobalCV:
+    """Global control variate g = Q h of a charge set (coulps_gcv_*): h from
+    n_iter SOR iterations on A h = -rho."""
+
+    def __init__(self, charges, n_iter=None):
+        self.charges = charges
+        self._lib = load()
+        L = charges.lattice.L
+        if n_iter is None:
+            n_iter = 6 * max(L) + 50
+        h = ctypes.c_void_p()
+        _check(self._lib.coulps_gcv_create(charges.handle, int(n_iter), ctypes.byref(h)),
+               "coulps_gcv_create")
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            self._lib.coulps_gcv_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        a = (ctypes.c_double * 2)()
+        _check(self._lib.coulps_gcv_info(self.handle, a), "coulps_gcv_info")
+        return {"h_dot_rho": a[0], "residual": a[1]}
+
+    def h(self):
+        Lx, Ly, Lz = self.charges.lattice.L
+        out = np.empty((Lz, Ly, Lx), dtype=np.float32)
+        _check(self._lib.coulps_gcv_h(self.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+               "coulps_gcv_h")
+        return out
+
+    def eval(self, tg_ptr=None):
+        """T g of the current fields into device doubles at tg_ptr (None: internal)."""
+        _check(self._lib.coulps_gcv_eval(self.handle, ctypes.c_void_p(tg_ptr) if tg_ptr else None),
+               "coulps_gcv_eval")
+
+    def run(self, n_meas, n_hb=1, n_or=0, c=1.0):
+        _check(self._lib.coulps_gcv_run(self.handle, int(n_meas), int(n_hb), int(n_or), float(c)),
+               "coulps_gcv_run")
 
 
 def _set_array(sets):

@@ -1184,6 +1184,158 @@ int coulps_cv_reset(coulps_charges_t C) {
   return COULPS_OK;
 }
 
+// ---- global control variate (gcv.cu) ---------------------------------------
+struct coulps_gcv {
+  coulps_charges *ch = nullptr;
+  double *d_rho = nullptr, *d_u = nullptr, *d_scratch = nullptr;
+  double *d_c0res = nullptr, *d_partials = nullptr, *d_tg = nullptr;
+  float *d_h32 = nullptr, *d_v = nullptr;
+  int nblk_red = 64, nblk = 1;
+  size_t bytes = 0;
+};
+
+void coulps_gcv_destroy(coulps_gcv_t G) {
+  if (!G) return;
+  coulps_lattice *L = G->ch->lat;
+  for (void *p : {(void *)G->d_rho, (void *)G->d_u, (void *)G->d_v, (void *)G->d_scratch,
+                  (void *)G->d_c0res, (void *)G->d_partials, (void *)G->d_tg, (void *)G->d_h32})
+    dev_free(L->alloc, p, L->stream);
+  delete G;
+}
+
+int coulps_gcv_create(coulps_charges_t C, int n_iter, coulps_gcv_t *out) {
+  if (!C || !out || n_iter < 0) return COULPS_EINVAL;
+  *out = nullptr;
+  coulps_lattice *L = C->lat;
+  const Geometry &g = L->g;
+  coulps_gcv *G = new (std::nothrow) coulps_gcv();
+  if (!G) return COULPS_ENOMEM;
+  G->ch = C;
+  G->nblk = gcv_blocks(g);
+  const size_t n = (size_t)g.Lx * g.Ly * g.Lz;
+  G->d_rho = (double *)dev_alloc(L->alloc, n * sizeof(double), L->stream);
+  G->d_u = (double *)dev_alloc(L->alloc, n * sizeof(double), L->stream);
+  G->d_h32 = (float *)dev_alloc(L->alloc, n * sizeof(float), L->stream);
+  G->d_v = (float *)dev_alloc(L->alloc, g.chain_elems * sizeof(float), L->stream);
+  G->d_scratch = (double *)dev_alloc(L->alloc, 4 * G->nblk_red * sizeof(double), L->stream);
+  G->d_c0res = (double *)dev_alloc(L->alloc, 4 * sizeof(double), L->stream);
+  G->d_partials =
+      (double *)dev_alloc(L->alloc, 2 * (size_t)G->nblk * g.n_chains * sizeof(double), L->stream);
+  G->d_tg = (double *)dev_alloc(L->alloc, (size_t)g.n_chains * sizeof(double), L->stream);
+  G->bytes = n * (2 * sizeof(double) + sizeof(float)) + g.chain_elems * sizeof(float);
+  if (!G->d_rho || !G->d_u || !G->d_h32 || !G->d_v || !G->d_scratch || !G->d_c0res ||
+      !G->d_partials || !G->d_tg) {
+    coulps_gcv_destroy(G);
+    return COULPS_ENOMEM;
+  }
+  // the charge density from the set's host copy (natural order)
+  std::vector<double> rho;
+  try {
+    rho.assign(n, 0.0);
+  } catch (...) {
+    coulps_gcv_destroy(G);
+    return COULPS_ENOMEM;
+  }
+  for (size_t i = 0; i < C->qv.size(); ++i) {
+    const int32_t *s = &C->sites[3 * i];
+    rho[((size_t)s[2] * g.Ly + s[1]) * g.Lx + s[0]] += C->qv[i];
+  }
+  if (cudaMemcpyAsync(G->d_rho, rho.data(), n * sizeof(double), cudaMemcpyHostToDevice,
+                      L->stream) != cudaSuccess ||
+      gcv_solve(g, G->d_rho, G->d_u, G->d_h32, G->d_v, G->d_scratch, G->nblk_red, n_iter,
+                G->d_c0res, L->stream) != cudaSuccess ||
+      cudaStreamSynchronize(L->stream) != cudaSuccess) {  // rho is pageable host memory
+    cudaGetLastError();
+    coulps_gcv_destroy(G);
+    return COULPS_ECUDA;
+  }
+  *out = G;
+  return COULPS_OK;
+}
+
+int coulps_gcv_info(coulps_gcv_t G, double out[2]) {
+  if (!G || !out) return COULPS_EINVAL;
+  coulps_lattice *L = G->ch->lat;
+  CK(cudaMemcpyAsync(out, G->d_c0res, 2 * sizeof(double), cudaMemcpyDeviceToHost, L->stream));
+  CK(cudaStreamSynchronize(L->stream));
+  return COULPS_OK;
+}
+
+int coulps_gcv_h(coulps_gcv_t G, float *host_xyz) {
+  if (!G || !host_xyz) return COULPS_EINVAL;
+  coulps_lattice *L = G->ch->lat;
+  const size_t n = (size_t)L->g.Lx * L->g.Ly * L->g.Lz;
+  CK(cudaMemcpyAsync(host_xyz, G->d_h32, n * sizeof(float), cudaMemcpyDeviceToHost, L->stream));
+  CK(cudaStreamSynchronize(L->stream));
+  return COULPS_OK;
+}
+
+int coulps_gcv_eval(coulps_gcv_t G, double *tg) {
+  if (!G) return COULPS_EINVAL;
+  coulps_charges *C = G->ch;
+  coulps_lattice *L = C->lat;
+  CK(gcv_eval(L->g, L->field, G->d_v, C->d_idx, C->d_q, C->n, G->d_partials, G->nblk,
+              G->d_c0res, tg ? tg : G->d_tg, L->stream));
+  return COULPS_OK;
+}
+
+int coulps_gcv_run(coulps_gcv_t G, int n_meas, int n_hb, int n_or, double c) {
+  if (!G || n_meas < 0 || n_hb < 0 || n_or < 0 || !std::isfinite(c)) return COULPS_EINVAL;
+  coulps_charges *C = G->ch;
+  coulps_lattice *L = C->lat;
+  if (n_meas == 0) return COULPS_OK;
+  const bool fused = n_hb + n_or > 0;
+  if (fused) {
+    int st = stage_gather(L, C);
+    if (st) return st;
+  }
+  auto one = [&]() -> int {
+    int st = enqueue_compound(L, n_hb, n_or, fused ? C : nullptr);
+    if (!st && !fused) st = enqueue_measure(L, C);
+    if (st) return st;
+    CK(gcv_eval(L->g, L->field, G->d_v, C->d_idx, C->d_q, C->n, G->d_partials, G->nblk,
+                G->d_c0res, G->d_tg, L->stream));
+    CK(launch_cv_record(C->d_stats, G->d_tg, c, C->d_cvstats, L->g.n_chains, L->d_err,
+                        L->stream));
+    return COULPS_OK;
+  };
+  cudaGraphExec_t exec = nullptr;
+  if (L->stream != nullptr && !L->profiling && n_meas >= 8) {
+    cudaGraph_t gr = nullptr;
+    CK(cudaStreamBeginCapture(L->stream, cudaStreamCaptureModeThreadLocal));
+    const int s1 = one();
+    cudaError_t e = cudaStreamEndCapture(L->stream, &gr);
+    if (s1 || e != cudaSuccess) {
+      cudaGetLastError();
+      if (gr) cudaGraphDestroy(gr);
+      return s1 ? s1 : COULPS_ECUDA;
+    }
+    e = cudaGraphInstantiate(&exec, gr, 0);
+    cudaGraphDestroy(gr);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return COULPS_ECUDA;
+    }
+  }
+  int st = COULPS_OK;
+  for (int k = 0; k < n_meas && !st; ++k) {
+    if (exec) {
+      if (cudaGraphLaunch(exec, L->stream) != cudaSuccess) {
+        cudaGetLastError();
+        st = COULPS_ECUDA;
+      }
+    } else {
+      st = one();
+    }
+    if (!st) L->pass += (uint64_t)(n_hb + n_or);
+  }
+  if (exec) {
+    cudaStreamSynchronize(L->stream);  // the replays are done before the graph goes
+    cudaGraphExecDestroy(exec);
+  }
+  return st;
+}
+
 int coulps_charges_update(coulps_charges_t C, const int32_t *site, const double *q) {
   if (!C) return COULPS_EINVAL;
   if (C->n == 0) return COULPS_OK;

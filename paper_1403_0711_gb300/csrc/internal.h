@@ -129,6 +129,22 @@ struct SetTable {
 cudaError_t launch_measure_sets(const Geometry &g, const void *field, const SetTable &t,
                                 int *err, cudaStream_t s);
 
+// Global control variate (gcv.cu).  gcv_solve: red/black SOR on A u = -rho
+// (natural order, FP64, u_nat and rho_nat Lx*Ly*Lz doubles), h32 = u rounded
+// to a fixed-point grid (exact FP32), v_layout = A h32 (exact in FP32) in one
+// chain's field layout (chain_elems floats), res[0] = h32 . rho,
+// res[1] = |A u + rho| / |rho|, res[2] = max |u| (res: 3 doubles); scratch
+// >= 4 * nblk_red doubles; synchronises once.  gcv_eval: per chain
+// T g = res[0] - Q (v . phi) into tg; partials >= 2 * nblk * n_chains
+// doubles, nblk = gcv_blocks(g).
+int gcv_blocks(const Geometry &g);
+cudaError_t gcv_solve(const Geometry &g, const double *rho_nat, double *u_nat, float *h32,
+                      float *v_layout, double *scratch, int nblk_red, int n_iter, double *res,
+                      cudaStream_t s);
+cudaError_t gcv_eval(const Geometry &g, const void *field, const float *v_layout,
+                     const uint32_t *idx, const double *q, int64_t n_q, double *partials,
+                     int nblk, const double *c0, double *tg, cudaStream_t s);
+
 // Entry packing of the fused gather.
 constexpr uint32_t kGatherColourBit = 0x80000000u;
 

@@ -1,0 +1,91 @@
+"""Global control variate g = Q h (coulps_gcv_*): the SOR solution h against
+the oracle's spectral solve of A h = -rho, the per-chain Stein term against
+the oracle's formula with the same h, zero mean under the sampler, and the
+variance it removes from the +-1 estimator."""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cl():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1403_0711_gb300 import _build, coulps
+    _build.build()
+    coulps.load()
+    coulps.use_torch_allocator()
+    return coulps
+
+
+@pytest.fixture(scope="module")
+def stream():
+    import torch
+    return torch.cuda.Stream()
+
+
+def test_h_and_stein_term_match_oracle(cl, stream):
+    import torch
+    from oracle import oracle as O
+    from oracle import stein as ost
+    from paper_1403_0711_gb300 import inputs
+    L = (23, 18, 15)
+    sites, q = inputs.uniform_q(L, 30, seed=4)
+    lat = cl.Lattice(L, n_chains=3, precision=cl.F32, seed=8, stream=stream)
+    ch = cl.Charges(lat, sites, q, log_capacity=4)
+    lat.sweep(30, 1, 2)
+    g = cl.GlobalCV(ch, n_iter=400)
+    info = g.info()
+    assert info["residual"] < 1e-9
+    rho = O.charge_density(L, sites, q)
+    u = O.solve_dst(rho)  # A^-1 rho
+    h = g.h().astype(np.float64)
+    assert np.abs(h + u).max() < 1e-6 * np.abs(u).max()
+    assert abs(info["h_dot_rho"] - float(np.sum(h * rho))) < 1e-12 * abs(info["h_dot_rho"])
+    tg = torch.zeros(3, dtype=torch.float64, device="cuda")
+    g.eval(tg.data_ptr())
+    lat.sync()
+    tg = tg.cpu().numpy()
+    for k in range(3):
+        phi = lat.field(k)
+        ref = ost.global_stein_term(phi, rho, h)
+        Q = float(np.sum(rho * phi))
+        scale = abs(info["h_dot_rho"]) + abs(Q) * float(np.abs(ost.apply_A(h) * phi).sum())
+        # v . phi: FP32 partial sums of 16 products, FP64 across them
+        assert abs(tg[k] - ref) < 1e-6 * scale, (k, tg[k], ref)
+    g.close()
+    ch.close()
+    lat.close()
+
+
+def test_gcv_unbiased_and_removes_the_far_pair_variance(cl, stream):
+    from oracle import oracle as O
+    from paper_1403_0711_gb300 import inputs
+    L = (32, 32, 32)
+    sites, q = inputs.plus_minus(L, 64, seed=6)
+    e_lat = O.e_lat(L, sites, q, "dst")
+    lat = cl.Lattice(L, n_chains=64, precision=cl.F32, seed=10, stream=stream)
+    ch = cl.Charges(lat, sites, q)
+    lat.sweep(200, 1, 3)
+    g = cl.GlobalCV(ch)
+    ch.reset_stats()
+    ch.cv_reset()
+    g.run(1500, 1, 3, 1.0)
+    plain, cvst = ch.chain_stats(), ch.cv_chain_stats()
+    n = plain[:, 0].sum()
+    var_p = plain[:, 2].sum() / n - (plain[:, 1].sum() / n) ** 2
+    var_c = cvst[:, 2].sum() / n - (cvst[:, 1].sum() / n) ** 2
+    assert var_c < 0.05 * var_p, (var_c, var_p)
+    a, b = ch.estimate(), ch.cv_estimate()
+    assert abs(b["mean"] - e_lat) < 4 * b["stderr"], (b, e_lat)
+    assert abs(a["mean"] - e_lat) < 4 * a["stderr"], (a, e_lat)
+    # per-chain means of T g (c = 1): e - y, zero within errors
+    tg_chain = (plain[:, 1] - cvst[:, 1]) / plain[:, 0]
+    assert abs(tg_chain.mean()) < 4 * tg_chain.std(ddof=1) / math.sqrt(len(tg_chain))
+    g.close()
+    ch.close()
+    lat.close()
