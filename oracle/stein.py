@@ -145,3 +145,32 @@ def global_stein_term(phi, rho, h):
     Q^2 - rho . G rho for every phi."""
     Q = float(np.sum(rho * phi))
     return float(np.sum(h * rho) - Q * np.sum(apply_A(h) * phi))
+
+
+def cube_green(R):
+    """Dirichlet Green function of the (2R+1)^3 cube at its centre, (dz, dy, dx)
+    from -R to R: the column of the dense inverse of the cube's A."""
+    from oracle import oracle
+    m = 2 * R + 1
+    G = oracle.green_dense((m, m, m))
+    return G[:, (R * m + R) * m + R].reshape(m, m, m)
+
+
+def local_p_stein_term(phi, sites, q, k):
+    """T g for g_x = sum_i q_i^2 phi(r_i) k(x - r_i) (x in the box, k of radius
+    R = (len(k) - 1) / 2 indexed [dz + R, dy + R, dx + R]):
+        T g = k(0) sum_i q_i^2 - sum_i q_i^2 phi(r_i) w_i,
+        w_i = sum_d k(d) (A phi)(r_i + d)   over r_i + d in the box.
+    Mean 0 under exp(-H_L) for any k; sites are (x, y, z)."""
+    R = (k.shape[0] - 1) // 2
+    Lz, Ly, Lx = phi.shape
+    Ap = apply_A(phi)
+    q = np.asarray(q, dtype=np.float64)
+    t = float(k[R, R, R] * np.sum(q * q))
+    for (x, y, z), qi in zip(np.asarray(sites).reshape(-1, 3), q):
+        z0, z1 = max(z - R, 0), min(z + R + 1, Lz)
+        y0, y1 = max(y - R, 0), min(y + R + 1, Ly)
+        x0, x1 = max(x - R, 0), min(x + R + 1, Lx)
+        kk = k[z0 - (z - R):z1 - (z - R), y0 - (y - R):y1 - (y - R), x0 - (x - R):x1 - (x - R)]
+        t -= qi * qi * phi[z, y, x] * float(np.sum(kk * Ap[z0:z1, y0:y1, x0:x1]))
+    return t

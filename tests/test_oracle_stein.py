@@ -140,3 +140,50 @@ def test_global_stein_term_has_zero_mean_under_exact_samples(orc):
     qa = np.array([np.sum(rho * p) * np.sum(stein.apply_A(h) * p) for p in phis])
     assert abs(qa.mean()) > 8 * qa.std(ddof=1) / math.sqrt(n)
     assert abs(qa.mean() - np.sum(h * rho)) < 4 * qa.std(ddof=1) / math.sqrt(n)
+
+
+def test_local_p_term_matches_definition_and_has_zero_mean(orc):
+    """Local term of P: g_x = sum_i q_i^2 phi(r_i) k(x - r_i).  Its Stein term
+    equals the definition (divergence by central differences, g . A phi by
+    hand) with charges at the box faces, and averages to 0 under exact
+    samples; with k the cube Green function A k = e_centre inside the cube."""
+    from oracle import stein
+    k = stein.cube_green(1)
+    # A k = delta inside the cube (k = 0 outside it)
+    Ak = stein.apply_A(k)
+    assert abs(Ak[1, 1, 1] - 1.0) < 1e-12 and np.abs(np.delete(Ak.reshape(-1), 13)).max() < 1e-12
+    L = (5, 4, 3)
+    rng = np.random.default_rng(3)
+    phi = rng.standard_normal((L[2], L[1], L[0]))
+    sites = np.array([[0, 0, 0], [2, 1, 1], [4, 3, 2], [3, 1, 1]])
+    q = np.array([1.0, -0.5, 0.8, 1.0])
+
+    def g_of(p):
+        g = np.zeros_like(p)
+        for (x, y, z), qi in zip(sites, q):
+            for dz in range(-1, 2):
+                for dy in range(-1, 2):
+                    for dx in range(-1, 2):
+                        xx, yy, zz = x + dx, y + dy, z + dz
+                        if 0 <= xx < L[0] and 0 <= yy < L[1] and 0 <= zz < L[2]:
+                            g[zz, yy, xx] += qi * qi * p[z, y, x] * k[dz + 1, dy + 1, dx + 1]
+        return g
+
+    eps = 1e-6
+    div = 0.0
+    for idx in np.ndindex(phi.shape):
+        a, b = phi.copy(), phi.copy()
+        a[idx] += eps
+        b[idx] -= eps
+        div += (g_of(a)[idx] - g_of(b)[idx]) / (2 * eps)
+    tg_def = div - float(np.sum(g_of(phi) * stein.apply_A(phi)))
+    tg = stein.local_p_stein_term(phi, sites, q, k)
+    assert abs(tg - tg_def) < 1e-7 * max(1.0, abs(tg)), (tg, tg_def)
+    # zero mean under exact samples
+    A = orc.laplacian_dense(L)
+    C = np.linalg.cholesky(A)
+    n = 20000
+    z = rng.standard_normal((n, A.shape[0]))
+    phis = np.linalg.solve(C.T, z.T).T.reshape(n, L[2], L[1], L[0])
+    t = np.array([stein.local_p_stein_term(p, sites, q, k) for p in phis])
+    assert abs(t.mean()) < 4 * t.std(ddof=1) / math.sqrt(n), (t.mean(), t.std())
