@@ -453,6 +453,11 @@ int coulps_cv_reset(coulps_charges_t ch);
  * that v = A h is exact in FP32 (kept in the field's layout) and h . rho is
  * formed in FP64: E[T g] = 0 holds for the h actually used.  Per sample
  * v . phi adds FP32 products in FP32 over 16 sites and those in FP64.
+ * R in 1..4 adds the local term of P: g^P_x = sum_i q_i^2 phi(r_i) k(x - r_i)
+ * with k the Dirichlet Green function of the (2R+1)^3 cube at its centre
+ * (FP32), whose Stein term k(0) sum q^2 - sum_i q_i^2 phi(r_i) w_i,
+ * w_i = sum_d k(d) (A phi)(r_i + d), also has mean 0 and removes most of the
+ * variance of P; T g then denotes the sum of both terms.  R = 0: Q term only.
  * Synchronises.  The object reads the charge set's positions at creation
  * (re-create it after coulps_charges_update; destroy it before the set).
  * coulps_gcv_info: out[0] = h . rho, out[1] = |A u + rho| / |rho| (synchronises).
@@ -464,7 +469,7 @@ int coulps_cv_reset(coulps_charges_t ch);
  *   (coulps_cv_estimate reads the latter).  Synchronises at the end.
  * Errors: EINVAL, ENOMEM, ECUDA. */
 typedef struct coulps_gcv *coulps_gcv_t;
-int coulps_gcv_create(coulps_charges_t ch, int n_iter, coulps_gcv_t *out);
+int coulps_gcv_create(coulps_charges_t ch, int n_iter, int R, coulps_gcv_t *out);
 void coulps_gcv_destroy(coulps_gcv_t gcv);
 int coulps_gcv_info(coulps_gcv_t gcv, double out[2]);
 int coulps_gcv_h(coulps_gcv_t gcv, float *host_xyz);

@@ -130,7 +130,7 @@ def load(path: str | Path | None = None):
         "coulps_cv_reset": (i32, [vp]),
         "coulps_set_fused": (i32, [vp, i32]),
         "coulps_measure_sets": (i32, [vp, P(vp), i32]),
-        "coulps_gcv_create": (i32, [vp, i32, P(vp)]),
+        "coulps_gcv_create": (i32, [vp, i32, i32, P(vp)]),
         "coulps_gcv_destroy": (None, [vp]),
         "coulps_gcv_info": (i32, [vp, P(f64)]),
         "coulps_gcv_h": (i32, [vp, P(ctypes.c_float)]),
@@ -379,16 +379,17 @@ class Charges:
 
 class GlobalCV:
     """Global control variate g = Q h of a charge set (coulps_gcv_*): h from
-    n_iter SOR iterations on A h = -rho."""
+    n_iter SOR iterations on A h = -rho; with R > 0 also the local term of P
+    (kernel radius R)."""
 
-    def __init__(self, charges, n_iter=None):
+    def __init__(self, charges, n_iter=None, R=2):
         self.charges = charges
         self._lib = load()
         L = charges.lattice.L
         if n_iter is None:
             n_iter = 6 * max(L) + 50
         h = ctypes.c_void_p()
-        _check(self._lib.coulps_gcv_create(charges.handle, int(n_iter), ctypes.byref(h)),
+        _check(self._lib.coulps_gcv_create(charges.handle, int(n_iter), int(R), ctypes.byref(h)),
                "coulps_gcv_create")
         self.handle = h
 

@@ -1192,19 +1192,63 @@ struct coulps_gcv {
   float *d_h32 = nullptr, *d_v = nullptr;
   int nblk_red = 64, nblk = 1;
   size_t bytes = 0;
+  // local term of P: kernel of radius R, its centre value times sum q^2
+  int R = 0;
+  float *d_k = nullptr;
+  double cP = 0.0;
+  double *d_ppart = nullptr;
 };
+
+// Dirichlet Green function of the (2R+1)^3 cube at its centre: A k = e_centre
+// by Gaussian elimination (at most 729 unknowns), in FP64, rounded to FP32.
+static std::vector<float> cube_green(int R) {
+  const int m = 2 * R + 1, n = m * m * m;
+  std::vector<double> A((size_t)n * n, 0.0), b(n, 0.0);
+  auto id = [&](int x, int y, int z) { return (z * m + y) * m + x; };
+  for (int z = 0; z < m; ++z)
+    for (int y = 0; y < m; ++y)
+      for (int x = 0; x < m; ++x) {
+        const int i = id(x, y, z);
+        A[(size_t)i * n + i] = 6.0;
+        const int nb[6][3] = {{x - 1, y, z}, {x + 1, y, z}, {x, y - 1, z},
+                              {x, y + 1, z}, {x, y, z - 1}, {x, y, z + 1}};
+        for (auto &p : nb)
+          if (p[0] >= 0 && p[1] >= 0 && p[2] >= 0 && p[0] < m && p[1] < m && p[2] < m)
+            A[(size_t)i * n + id(p[0], p[1], p[2])] = -1.0;
+      }
+  b[id(R, R, R)] = 1.0;
+  for (int c = 0; c < n; ++c) {  // SPD: no pivoting needed
+    const double d = A[(size_t)c * n + c];
+    for (int r = c + 1; r < n; ++r) {
+      const double f = A[(size_t)r * n + c] / d;
+      if (f == 0.0) continue;
+      for (int k = c; k < n; ++k) A[(size_t)r * n + k] -= f * A[(size_t)c * n + k];
+      b[r] -= f * b[c];
+    }
+  }
+  std::vector<double> x(n, 0.0);
+  for (int r = n - 1; r >= 0; --r) {
+    double s = b[r];
+    for (int k = r + 1; k < n; ++k) s -= A[(size_t)r * n + k] * x[k];
+    x[r] = s / A[(size_t)r * n + r];
+  }
+  std::vector<float> out(n);
+  for (int i = 0; i < n; ++i) out[i] = (float)x[i];
+  return out;
+}
 
 void coulps_gcv_destroy(coulps_gcv_t G) {
   if (!G) return;
   coulps_lattice *L = G->ch->lat;
   for (void *p : {(void *)G->d_rho, (void *)G->d_u, (void *)G->d_v, (void *)G->d_scratch,
-                  (void *)G->d_c0res, (void *)G->d_partials, (void *)G->d_tg, (void *)G->d_h32})
+                  (void *)G->d_c0res, (void *)G->d_partials, (void *)G->d_tg, (void *)G->d_h32,
+                  (void *)G->d_k, (void *)G->d_ppart})
     dev_free(L->alloc, p, L->stream);
   delete G;
 }
 
-int coulps_gcv_create(coulps_charges_t C, int n_iter, coulps_gcv_t *out) {
-  if (!C || !out || n_iter < 0) return COULPS_EINVAL;
+int coulps_gcv_create(coulps_charges_t C, int n_iter, int R, coulps_gcv_t *out) {
+  if (!C || !out || n_iter < 0 || R < 0 || R > 4) return COULPS_EINVAL;
   *out = nullptr;
   coulps_lattice *L = C->lat;
   const Geometry &g = L->g;
@@ -1222,6 +1266,22 @@ int coulps_gcv_create(coulps_charges_t C, int n_iter, coulps_gcv_t *out) {
   G->d_partials =
       (double *)dev_alloc(L->alloc, 2 * (size_t)G->nblk * g.n_chains * sizeof(double), L->stream);
   G->d_tg = (double *)dev_alloc(L->alloc, (size_t)g.n_chains * sizeof(double), L->stream);
+  G->R = C->n > 0 ? R : 0;
+  std::vector<float> kt;
+  if (G->R > 0) {
+    kt = cube_green(G->R);
+    const int m = 2 * G->R + 1;
+    double q2 = 0.0;
+    for (double v : C->qv) q2 += v * v;
+    G->cP = (double)kt[(G->R * m + G->R) * m + G->R] * q2;
+    G->d_k = (float *)dev_alloc(L->alloc, kt.size() * sizeof(float), L->stream);
+    G->d_ppart = (double *)dev_alloc(
+        L->alloc, (size_t)((C->n + 7) / 8) * g.n_chains * sizeof(double), L->stream);
+    if (!G->d_k || !G->d_ppart) {
+      coulps_gcv_destroy(G);
+      return COULPS_ENOMEM;
+    }
+  }
   G->bytes = n * (2 * sizeof(double) + sizeof(float)) + g.chain_elems * sizeof(float);
   if (!G->d_rho || !G->d_u || !G->d_h32 || !G->d_v || !G->d_scratch || !G->d_c0res ||
       !G->d_partials || !G->d_tg) {
@@ -1242,6 +1302,8 @@ int coulps_gcv_create(coulps_charges_t C, int n_iter, coulps_gcv_t *out) {
   }
   if (cudaMemcpyAsync(G->d_rho, rho.data(), n * sizeof(double), cudaMemcpyHostToDevice,
                       L->stream) != cudaSuccess ||
+      (G->R > 0 && cudaMemcpyAsync(G->d_k, kt.data(), kt.size() * sizeof(float),
+                                   cudaMemcpyHostToDevice, L->stream) != cudaSuccess) ||
       gcv_solve(g, G->d_rho, G->d_u, G->d_h32, G->d_v, G->d_scratch, G->nblk_red, n_iter,
                 G->d_c0res, L->stream) != cudaSuccess ||
       cudaStreamSynchronize(L->stream) != cudaSuccess) {  // rho is pageable host memory
@@ -1275,7 +1337,7 @@ int coulps_gcv_eval(coulps_gcv_t G, double *tg) {
   coulps_charges *C = G->ch;
   coulps_lattice *L = C->lat;
   CK(gcv_eval(L->g, L->field, G->d_v, C->d_idx, C->d_q, C->n, G->d_partials, G->nblk,
-              G->d_c0res, tg ? tg : G->d_tg, L->stream));
+              G->d_c0res, G->d_k, G->R, G->cP, G->d_ppart, tg ? tg : G->d_tg, L->stream));
   return COULPS_OK;
 }
 
@@ -1294,7 +1356,7 @@ int coulps_gcv_run(coulps_gcv_t G, int n_meas, int n_hb, int n_or, double c) {
     if (!st && !fused) st = enqueue_measure(L, C);
     if (st) return st;
     CK(gcv_eval(L->g, L->field, G->d_v, C->d_idx, C->d_q, C->n, G->d_partials, G->nblk,
-                G->d_c0res, G->d_tg, L->stream));
+                G->d_c0res, G->d_k, G->R, G->cP, G->d_ppart, G->d_tg, L->stream));
     CK(launch_cv_record(C->d_stats, G->d_tg, c, C->d_cvstats, L->g.n_chains, L->d_err,
                         L->stream));
     return COULPS_OK;

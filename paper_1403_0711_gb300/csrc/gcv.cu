@@ -8,6 +8,15 @@
 // A h = -rho (once per charge set); the estimator stays unbiased whatever the
 // solver's residual, which only sets how much variance is removed.
 //
+// A second, local term removes most of the variance of P: g^P_x =
+// sum_i q_i^2 phi(r_i) k(x - r_i), k a fixed kernel of radius R (the
+// Dirichlet Green function of the (2R+1)^3 cube at its centre, restricted to
+// the box), has Stein term
+//   T g^P = k(0) sum_i q_i^2 - sum_i q_i^2 phi(r_i) w_i,
+//   w_i = sum_d k(d) (A phi)(r_i + d)   (d over the cube, r_i + d in the box);
+// with k = G(., r_i) it would equal sum q^2 G_ii - P, so e - T g - T g^P would
+// be E_lat exactly.  Mean 0 for any k, like T g.
+//
 // Exactness: h is rounded to the fixed-point grid 2^-k (h~, k as large as lets
 // 13 max|h~| 2^k stay below 2^24), so v = A h~ is a multiple of 2^-k below
 // 2^24 2^-k in magnitude and exact in FP32; h~ . rho is formed in FP64.  Thus
@@ -192,20 +201,77 @@ __global__ void __launch_bounds__(kGcvThreads)
   block_sum2(s, Q, partials + 2 * ((size_t)chain * gridDim.x + blockIdx.x));
 }
 
-// warp per chain: fixed-order sums, then T g = h~ . rho - Q s
-__global__ void gcv_finish_kernel(const double *__restrict__ partials, int nblk, int n_chains,
-                                  const double *__restrict__ c0, double *__restrict__ tg) {
+// phi at (x, y, z) of one chain in the field layout (0 outside the box)
+template <typename T>
+__device__ __forceinline__ double phi_at(const T *f, const Geometry &g, int x, int y, int z) {
+  if (x < 0 || y < 0 || z < 0 || x >= g.Lx || y >= g.Ly || z >= g.Lz) return 0.0;
+  const int c = (x + y + z) & 1;
+  return (double)f[(size_t)c * g.colour_elems + ((size_t)z * g.Ly + y) * g.W + (x >> 1)];
+}
+
+// warp per (charge, chain): q_i^2 phi(r_i) w_i; per block of 8 charges one
+// partial per chain
+template <typename T>
+__global__ void __launch_bounds__(256)
+    gcv_p_kernel(const T *__restrict__ field, const Geometry g, const uint32_t *__restrict__ idx,
+                 const double *__restrict__ q, int64_t n_q, const float *__restrict__ kt, int R,
+                 double *__restrict__ partials) {
+  const int chain = blockIdx.y;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t i = (int64_t)blockIdx.x * 8 + wid;
+  const T *f = field + (size_t)chain * g.chain_elems;
+  double contrib = 0.0;
+  if (i < n_q) {
+    // site of charge i from its storage offset
+    const uint32_t e = idx[i];
+    const int c = (int)(e / g.colour_elems);
+    const uint32_t r = e - (uint32_t)c * (uint32_t)g.colour_elems;
+    const int h = (int)(r % g.W), y = (int)((r / g.W) % g.Ly), z = (int)(r / ((uint32_t)g.W * g.Ly));
+    const int x = 2 * h + ((c + y + z) & 1);
+    const int m = 2 * R + 1, m3 = m * m * m;
+    double w = 0.0;
+    for (int t = lane; t < m3; t += 32) {
+      const int dx = t % m - R, dy = (t / m) % m - R, dz = t / (m * m) - R;
+      const int xx = x + dx, yy = y + dy, zz = z + dz;
+      if (xx < 0 || yy < 0 || zz < 0 || xx >= g.Lx || yy >= g.Ly || zz >= g.Lz) continue;
+      const double Ap = 6.0 * phi_at(f, g, xx, yy, zz) - phi_at(f, g, xx - 1, yy, zz) -
+                        phi_at(f, g, xx + 1, yy, zz) - phi_at(f, g, xx, yy - 1, zz) -
+                        phi_at(f, g, xx, yy + 1, zz) - phi_at(f, g, xx, yy, zz - 1) -
+                        phi_at(f, g, xx, yy, zz + 1);
+      w += (double)kt[t] * Ap;
+    }
+    w = warp_sum(w);
+    contrib = q[i] * q[i] * (double)f[e] * w;
+  }
+  __shared__ double red[8];
+  if (lane == 0) red[wid] = contrib;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sum = 0.0;
+    for (int k = 0; k < 8; ++k) sum += red[k];
+    partials[(size_t)chain * gridDim.x + blockIdx.x] = sum;
+  }
+}
+
+// warp per chain: fixed-order sums, then
+// T g + T g^P = h~ . rho - Q s + cP - sum_i q_i^2 phi_i w_i
+__global__ void gcv_finish_kernel(const double *__restrict__ partials, int nblk,
+                                  const double *__restrict__ ppart, int nblk_p, int n_chains,
+                                  const double *__restrict__ c0, double cP,
+                                  double *__restrict__ tg) {
   const int chain = blockIdx.x * 8 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (chain >= n_chains) return;
-  double s = 0.0, Q = 0.0;
+  double s = 0.0, Q = 0.0, p = 0.0;
   for (int b = lane; b < nblk; b += 32) {
     s += partials[2 * ((size_t)chain * nblk + b) + 0];
     Q += partials[2 * ((size_t)chain * nblk + b) + 1];
   }
+  for (int b = lane; b < nblk_p; b += 32) p += ppart[(size_t)chain * nblk_p + b];
   s = warp_sum(s);
   Q = warp_sum(Q);
-  if (lane == 0) tg[chain] = *c0 - Q * s;
+  p = warp_sum(p);
+  if (lane == 0) tg[chain] = *c0 - Q * s + cP - p;
 }
 
 }  // namespace
@@ -256,7 +322,8 @@ cudaError_t gcv_solve(const Geometry &g, const double *rho_nat, double *u_nat, f
 
 cudaError_t gcv_eval(const Geometry &g, const void *field, const float *v_layout,
                      const uint32_t *idx, const double *q, int64_t n_q, double *partials,
-                     int nblk, const double *c0, double *tg, cudaStream_t s) {
+                     int nblk, const double *c0, const float *kt, int R, double cP,
+                     double *ppart, double *tg, cudaStream_t s) {
   dim3 grid(nblk, g.n_chains);
   if (g.precision == COULPS_F32)
     gcv_sample_kernel<float><<<grid, kGcvThreads, 0, s>>>(
@@ -264,7 +331,18 @@ cudaError_t gcv_eval(const Geometry &g, const void *field, const float *v_layout
   else
     gcv_sample_kernel<double><<<grid, kGcvThreads, 0, s>>>(
         reinterpret_cast<const double *>(field), g.chain_elems, v_layout, idx, q, n_q, partials);
-  gcv_finish_kernel<<<(g.n_chains + 7) / 8, 256, 0, s>>>(partials, nblk, g.n_chains, c0, tg);
+  const int nblk_p = R > 0 && n_q > 0 ? (int)((n_q + 7) / 8) : 0;
+  if (nblk_p > 0) {
+    dim3 pgrid(nblk_p, g.n_chains);
+    if (g.precision == COULPS_F32)
+      gcv_p_kernel<float><<<pgrid, 256, 0, s>>>(reinterpret_cast<const float *>(field), g, idx, q,
+                                               n_q, kt, R, ppart);
+    else
+      gcv_p_kernel<double><<<pgrid, 256, 0, s>>>(reinterpret_cast<const double *>(field), g, idx,
+                                                q, n_q, kt, R, ppart);
+  }
+  gcv_finish_kernel<<<(g.n_chains + 7) / 8, 256, 0, s>>>(partials, nblk, ppart, nblk_p,
+                                                        g.n_chains, c0, nblk_p > 0 ? cP : 0.0, tg);
   return cudaGetLastError();
 }
 

@@ -141,9 +141,13 @@ int gcv_blocks(const Geometry &g);
 cudaError_t gcv_solve(const Geometry &g, const double *rho_nat, double *u_nat, float *h32,
                       float *v_layout, double *scratch, int nblk_red, int n_iter, double *res,
                       cudaStream_t s);
+// With R > 0 also the local term of P (kt: (2R+1)^3 floats, index
+// (dz + R)(2R+1)^2 + (dy + R)(2R+1) + dx + R; cP = kt[centre] sum q^2; ppart
+// >= ceil(n_q / 8) * n_chains doubles).
 cudaError_t gcv_eval(const Geometry &g, const void *field, const float *v_layout,
                      const uint32_t *idx, const double *q, int64_t n_q, double *partials,
-                     int nblk, const double *c0, double *tg, cudaStream_t s);
+                     int nblk, const double *c0, const float *kt, int R, double cP,
+                     double *ppart, double *tg, cudaStream_t s);
 
 // Entry packing of the fused gather.
 constexpr uint32_t kGatherColourBit = 0x80000000u;

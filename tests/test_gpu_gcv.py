@@ -38,7 +38,7 @@ def test_h_and_stein_term_match_oracle(cl, stream):
     lat = cl.Lattice(L, n_chains=3, precision=cl.F32, seed=8, stream=stream)
     ch = cl.Charges(lat, sites, q, log_capacity=4)
     lat.sweep(30, 1, 2)
-    g = cl.GlobalCV(ch, n_iter=400)
+    g = cl.GlobalCV(ch, n_iter=400, R=2)
     info = g.info()
     assert info["residual"] < 1e-9
     rho = O.charge_density(L, sites, q)
@@ -50,12 +50,13 @@ def test_h_and_stein_term_match_oracle(cl, stream):
     g.eval(tg.data_ptr())
     lat.sync()
     tg = tg.cpu().numpy()
+    kc = ost.cube_green(2)
     for k in range(3):
         phi = lat.field(k)
-        ref = ost.global_stein_term(phi, rho, h)
+        ref = ost.global_stein_term(phi, rho, h) + ost.local_p_stein_term(phi, sites, q, kc)
         Q = float(np.sum(rho * phi))
         scale = abs(info["h_dot_rho"]) + abs(Q) * float(np.abs(ost.apply_A(h) * phi).sum())
-        # v . phi: FP32 partial sums of 16 products, FP64 across them
+        # v . phi: FP32 partial sums of 16 products, FP64 across them; k in FP32
         assert abs(tg[k] - ref) < 1e-6 * scale, (k, tg[k], ref)
     g.close()
     ch.close()
@@ -71,7 +72,7 @@ def test_gcv_unbiased_and_removes_the_far_pair_variance(cl, stream):
     lat = cl.Lattice(L, n_chains=64, precision=cl.F32, seed=10, stream=stream)
     ch = cl.Charges(lat, sites, q)
     lat.sweep(200, 1, 3)
-    g = cl.GlobalCV(ch)
+    g = cl.GlobalCV(ch, R=0)  # the Q term alone first
     ch.reset_stats()
     ch.cv_reset()
     g.run(1500, 1, 3, 1.0)
@@ -84,6 +85,21 @@ def test_gcv_unbiased_and_removes_the_far_pair_variance(cl, stream):
     assert abs(b["mean"] - e_lat) < 4 * b["stderr"], (b, e_lat)
     assert abs(a["mean"] - e_lat) < 4 * a["stderr"], (a, e_lat)
     # per-chain means of T g (c = 1): e - y, zero within errors
+    tg_chain = (plain[:, 1] - cvst[:, 1]) / plain[:, 0]
+    assert abs(tg_chain.mean()) < 4 * tg_chain.std(ddof=1) / math.sqrt(len(tg_chain))
+    g.close()
+    # with the local term of P the variance drops much further, still unbiased
+    g = cl.GlobalCV(ch, R=2)
+    ch.reset_stats()
+    ch.cv_reset()
+    g.run(1500, 1, 3, 1.0)
+    plain, cvst = ch.chain_stats(), ch.cv_chain_stats()
+    n = plain[:, 0].sum()
+    var_p = plain[:, 2].sum() / n - (plain[:, 1].sum() / n) ** 2
+    var_c2 = cvst[:, 2].sum() / n - (cvst[:, 1].sum() / n) ** 2
+    assert var_c2 < 0.2 * var_c and var_c2 < 0.005 * var_p, (var_c2, var_c, var_p)
+    b = ch.cv_estimate()
+    assert abs(b["mean"] - e_lat) < 4 * b["stderr"], (b, e_lat)
     tg_chain = (plain[:, 1] - cvst[:, 1]) / plain[:, 0]
     assert abs(tg_chain.mean()) < 4 * tg_chain.std(ddof=1) / math.sqrt(len(tg_chain))
     g.close()
