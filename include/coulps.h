@@ -190,6 +190,41 @@ int coulps_run_sets(coulps_lattice_t lat, const coulps_charges_t *sets, int n_se
  * (site outside the box, non-finite q), ECUDA. */
 int coulps_charges_update(coulps_charges_t ch, const int32_t *site_xyz, const double *q);
 
+/* Off-lattice charges (the paper's closing remarks: a particle between sites
+ * is modelled through the eight sites around it, and forces follow by the
+ * same interpolation).  Particle i sits at pos_xyz[3i..3i+2] (doubles,
+ * 0 <= x <= Lx - 1 etc.; every dimension of the lattice >= 2) with charge
+ * q[i].  With base b = floor(r) clipped to L - 2 and f = r - b, the eight
+ * corners b + c (c in {0,1}^3) carry the trilinear weights
+ *   w_c = prod_mu (c_mu ? f_mu : 1 - f_mu),
+ * so a sample reads phi~_i = sum_c w_c phi(b + c) and takes, as Eq. (nsum2)
+ * does for lattice charges, Q = sum_i q_i phi~_i, P = sum_i (q_i phi~_i)^2,
+ * e = Q^2 - P (all in FP64; mean = sum_{i != j} q_i q_j G~(r_i, r_j) with the
+ * interpolated Green function).  With forces != 0 every sample also adds, per
+ * chain and particle,
+ *   f_i = -de/dr_i = -2 q_i (Q - q_i phi~_i) grad phi~_i,
+ *   grad phi~_i = sum_c (grad w_c) phi(b + c),
+ * to running sums (the measure does not depend on the positions, so their
+ * mean is the force on particle i).  Weights and gradients are formed once
+ * on the host in FP64.  The set works with coulps_measure, coulps_run (the
+ * gather is a separate launch after the sweep), coulps_measure_sets,
+ * coulps_run_sets, coulps_estimate, coulps_samples, coulps_chain_stats and
+ * coulps_reset_stats (which also clears the force sums); coulps_charges_update
+ * and coulps_gcv_create return EUNSUPPORTED.  Errors: EINVAL (a position
+ * outside the box or not finite, a dimension < 2, non-finite q, n < 0),
+ * ENOMEM, ECUDA. */
+int coulps_charges_create_off(coulps_lattice_t lat, int64_t n, const double *pos_xyz,
+                              const double *q, int64_t log_capacity, int forces,
+                              coulps_charges_t *out);
+
+/* Synchronise and return the mean force on each particle of an off-lattice
+ * set created with forces != 0: mean[3i + mu] = (sum over all chains' samples
+ * of f_i,mu) / (number of samples), and, if stderr_chains is not NULL, the
+ * standard error from the spread of the chains' own means (chains are
+ * independent).  Errors: EINVAL, EUNSUPPORTED (not an off-lattice set with
+ * forces), ECUDA, ETIMEOUT. */
+int coulps_forces(coulps_charges_t ch, double *mean, double *stderr_chains);
+
 /* Per-chain estimator state, COULPS_STAT_STRIDE doubles per chain:
  *   [0] samples n, [1] sum e, [2] sum e^2, [3] open batch sum, [4] open batch
  *   count, [5] batch length b, [6] completed batches m (32 <= m < 64 once

@@ -42,6 +42,7 @@ EXPORTS = (
     "coulps_cv_reset", "coulps_cv_charge_term", "coulps_set_fused", "coulps_set_pass_tile",
     "coulps_measure_sets", "coulps_run_sets", "coulps_gcv_create", "coulps_gcv_destroy",
     "coulps_gcv_info", "coulps_gcv_h", "coulps_gcv_eval", "coulps_gcv_run",
+    "coulps_charges_create_off", "coulps_forces",
 )
 SCHEDULE_ALIGNED, SCHEDULE_PHASED = 0, 1
 STAT_STRIDE = 72
@@ -86,6 +87,8 @@ def load(path: str | Path | None = None):
         "coulps_sweep": (i32, [vp, i32, i32, i32]),
         "coulps_sync": (i32, [vp]),
         "coulps_charges_create": (i32, [vp, i64, P(ctypes.c_int32), P(f64), i64, P(vp)]),
+        "coulps_charges_create_off": (i32, [vp, i64, P(f64), P(f64), i64, ctypes.c_int, P(vp)]),
+        "coulps_forces": (i32, [vp, P(f64), P(f64)]),
         "coulps_charges_destroy": (None, [vp]),
         "coulps_measure": (i32, [vp, vp]),
         "coulps_run": (i32, [vp, vp, i32, i32, i32, i32]),
@@ -285,9 +288,13 @@ class Lattice:
 class Charges:
     """A charge set measured on every chain of a lattice."""
 
-    def __init__(self, lattice: Lattice, sites, q, log_capacity=0):
+    def __init__(self, lattice: Lattice, sites, q, log_capacity=0, _handle=None):
         self._lib = load()
         self.lattice = lattice
+        if _handle is not None:
+            self.n = len(q)
+            self.handle = _handle
+            return
         s = np.ascontiguousarray(np.asarray(sites, dtype=np.int32).reshape(-1, 3))
         qq = np.ascontiguousarray(np.asarray(q, dtype=np.float64).reshape(-1))
         assert len(s) == len(qq)
@@ -297,6 +304,28 @@ class Charges:
             lattice.handle, self.n, s.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _f64p(qq),
             int(log_capacity), ctypes.byref(h)), "coulps_charges_create")
         self.handle = h
+
+    @classmethod
+    def off_lattice(cls, lattice: Lattice, pos, q, log_capacity=0, forces=False):
+        """Particles at real positions pos (n, 3) as (x, y, z), each read
+        through the trilinear weights of its eight surrounding sites
+        (coulps_charges_create_off); forces=True keeps the force sums."""
+        lib = load()
+        p = np.ascontiguousarray(np.asarray(pos, dtype=np.float64).reshape(-1, 3))
+        qq = np.ascontiguousarray(np.asarray(q, dtype=np.float64).reshape(-1))
+        assert len(p) == len(qq)
+        h = ctypes.c_void_p()
+        _check(lib.coulps_charges_create_off(lattice.handle, len(qq), _f64p(p), _f64p(qq),
+                                             int(log_capacity), int(bool(forces)),
+                                             ctypes.byref(h)), "coulps_charges_create_off")
+        return cls(lattice, None, qq, _handle=h)
+
+    def forces(self):
+        """(mean (n, 3), stderr over chains (n, 3)) of -de/dr_i."""
+        m = np.empty((self.n, 3), dtype=np.float64)
+        e = np.empty((self.n, 3), dtype=np.float64)
+        _check(self._lib.coulps_forces(self.handle, _f64p(m), _f64p(e)), "coulps_forces")
+        return m, e
 
     def close(self):
         if getattr(self, "handle", None):
@@ -561,6 +590,14 @@ def coulps_lattice_create(Lx, Ly, Lz, n_chains, precision, seed, stream=None):
 
 def coulps_charges_create(lattice, sites, q, log_capacity=0):
     return Charges(lattice, sites, q, log_capacity)
+
+
+def coulps_charges_create_off(lattice, pos, q, log_capacity=0, forces=False):
+    return Charges.off_lattice(lattice, pos, q, log_capacity, forces)
+
+
+def coulps_forces(charges):
+    return charges.forces()
 
 
 def coulps_sweep(lattice, n_compound, n_hb, n_or):

@@ -102,6 +102,11 @@ struct coulps_charges {
   double *d_partials = nullptr;  // scratch: [chain][nblk][2]
   double *d_stats = nullptr;     // [chain][kStatStride]
   double *d_cvstats = nullptr;   // [chain][kStatStride], control-variate samples
+  // off-lattice set: per particle 8 corner offsets, weights, weight gradients;
+  // the last sample's Q per chain; running force sums [chain][particle][3]
+  bool off = false;
+  uint32_t *d_oidx = nullptr;
+  double *d_ow = nullptr, *d_og = nullptr, *d_lastQ = nullptr, *d_fsum = nullptr;
   double *d_log = nullptr;       // [sample][chain][3]
   int64_t log_cap = 0;
   size_t bytes = 0;
@@ -433,6 +438,16 @@ int stage_gather(coulps_lattice *L, coulps_charges *C) {
 }
 
 int enqueue_measure(coulps_lattice *L, coulps_charges *C) {
+  if (C->off) {
+    CK(launch_gather_off(L->g, L->field, C->d_oidx, C->d_ow, C->d_q, C->n, C->d_partials, C->nblk,
+                         L->stream));
+    CK(launch_finalize(C->d_partials, C->nblk, L->g.n_chains, C->d_stats, C->d_log, C->log_cap,
+                       L->d_err, L->stream, C->d_lastQ));
+    if (C->d_fsum)
+      CK(launch_force_off(L->g, L->field, C->d_oidx, C->d_ow, C->d_og, C->d_q, C->n, C->d_lastQ,
+                          C->d_fsum, L->stream));
+    return COULPS_OK;
+  }
   CK(launch_gather(L->g, L->field, C->d_idx, C->d_q, C->n, C->d_partials, C->nblk, L->stream));
   CK(launch_finalize(C->d_partials, C->nblk, L->g.n_chains, C->d_stats, C->d_log, C->log_cap,
                      L->d_err, L->stream));
@@ -441,11 +456,22 @@ int enqueue_measure(coulps_lattice *L, coulps_charges *C) {
 
 // Every set samples the current fields: kMaxSets per gather launch.
 int enqueue_measure_sets(coulps_lattice *L, coulps_charges *const *sets, int n_sets) {
+  // off-lattice sets one by one, the others kMaxSets per launch
+  std::vector<coulps_charges *> on;
+  for (int k = 0; k < n_sets; ++k) {
+    if (sets[k]->off) {
+      int st = enqueue_measure(L, sets[k]);
+      if (st) return st;
+    } else {
+      on.push_back(sets[k]);
+    }
+  }
+  n_sets = (int)on.size();
   for (int k0 = 0; k0 < n_sets; k0 += kMaxSets) {
     SetTable t;
     t.n_sets = n_sets - k0 < kMaxSets ? n_sets - k0 : kMaxSets;
     for (int k = 0; k < t.n_sets; ++k) {
-      coulps_charges *C = sets[k0 + k];
+      coulps_charges *C = on[k0 + k];
       t.idx[k] = C->d_idx;
       t.q[k] = C->d_q;
       t.n[k] = C->n;
@@ -917,6 +943,9 @@ void coulps_charges_destroy(coulps_charges_t C) {
   dev_free(L->alloc, C->d_stats, L->stream);
   dev_free(L->alloc, C->d_cvstats, L->stream);
   dev_free(L->alloc, C->d_log, L->stream);
+  for (void *p : {(void *)C->d_oidx, (void *)C->d_ow, (void *)C->d_og, (void *)C->d_lastQ,
+                  (void *)C->d_fsum})
+    dev_free(L->alloc, p, L->stream);
   if (C->staged) {
     cudaEventSynchronize(C->staged);
     cudaEventDestroy(C->staged);
@@ -950,14 +979,15 @@ int coulps_run(coulps_lattice_t L, coulps_charges_t C, int n_therm, int n_meas, 
   int st = coulps_sweep(L, n_therm, n_hb, n_or);
   if (st) return st;
   if (n_meas == 0) return COULPS_OK;
-  // The measured sweeps gather Q, P inside their last half-sweep.
-  const bool fused = n_hb + n_or > 0;
+  // The measured sweeps gather Q, P inside their last half-sweep (on-lattice
+  // sets; off-lattice ones use their own gather after the sweep).
+  const bool fused = n_hb + n_or > 0 && !C->off;
   if (fused) {
     st = stage_gather(L, C);
     if (st) return st;
   }
   const int P = n_hb + n_or;
-  if (L->schedule == COULPS_SCHEDULE_PHASED && n_hb > 0 && n_or > 0 && P <= kMaxGroups &&
+  if (L->schedule == COULPS_SCHEDULE_PHASED && !C->off && n_hb > 0 && n_or > 0 && P <= kMaxGroups &&
       n_meas >= 2 && L->g.n_chains >= P) {
     st = run_staggered(L, C, n_meas, n_hb, n_or);
     if (!st) L->pass += (uint64_t)n_meas * P;
@@ -1148,6 +1178,140 @@ int coulps_samples(coulps_charges_t C, double *QPe, int64_t cap, int64_t *n) {
 int coulps_reset_stats(coulps_charges_t C) {
   if (!C) return COULPS_EINVAL;
   CK(launch_reset_stats(C->d_stats, C->lat->g.n_chains, C->lat->stream));
+  if (C->d_fsum)
+    CK(cudaMemsetAsync(C->d_fsum, 0, sizeof(double) * 3 * (size_t)C->n * C->lat->g.n_chains,
+                       C->lat->stream));
+  return COULPS_OK;
+}
+
+int coulps_charges_create_off(coulps_lattice_t L, int64_t n, const double *pos, const double *q,
+                              int64_t log_capacity, int forces, coulps_charges_t *out) {
+  if (!L || !out || n < 0 || log_capacity < 0) return COULPS_EINVAL;
+  *out = nullptr;
+  if (n > 0 && (!pos || !q)) return COULPS_EINVAL;
+  if (n > ((int64_t)1 << 28)) return COULPS_EINVAL;
+  const Geometry &g = L->g;
+  if (g.Lx < 2 || g.Ly < 2 || g.Lz < 2) return COULPS_EINVAL;
+  const int Ls[3] = {g.Lx, g.Ly, g.Lz};
+  // corners, trilinear weights and their gradients, in FP64 on the host
+  std::vector<uint32_t> oidx((size_t)8 * n);
+  std::vector<double> ow((size_t)8 * n), og((size_t)24 * n);
+  for (int64_t i = 0; i < n; ++i) {
+    int b[3];
+    double f[3];
+    for (int mu = 0; mu < 3; ++mu) {
+      const double r = pos[3 * i + mu];
+      if (!(r >= 0.0 && r <= (double)(Ls[mu] - 1))) return COULPS_EINVAL;
+      int bi = (int)std::floor(r);
+      if (bi > Ls[mu] - 2) bi = Ls[mu] - 2;
+      b[mu] = bi;
+      f[mu] = r - bi;
+    }
+    if (!std::isfinite(q[i])) return COULPS_EINVAL;
+    for (int c = 0; c < 8; ++c) {
+      const int cx = (c >> 2) & 1, cy = (c >> 1) & 1, cz = c & 1;  // x slowest
+      const int cc[3] = {cx, cy, cz};
+      double fac[3], dfac[3];
+      for (int mu = 0; mu < 3; ++mu) {
+        fac[mu] = cc[mu] ? f[mu] : 1.0 - f[mu];
+        dfac[mu] = cc[mu] ? 1.0 : -1.0;
+      }
+      const int x = b[0] + cx, y = b[1] + cy, z = b[2] + cz;
+      const int col = (x + y + z) & 1;
+      oidx[8 * i + c] =
+          (uint32_t)((size_t)col * g.colour_elems + ((size_t)z * g.Ly + y) * g.W + (x >> 1));
+      ow[8 * i + c] = fac[0] * fac[1] * fac[2];
+      og[3 * (8 * i + c) + 0] = dfac[0] * fac[1] * fac[2];
+      og[3 * (8 * i + c) + 1] = fac[0] * dfac[1] * fac[2];
+      og[3 * (8 * i + c) + 2] = fac[0] * fac[1] * dfac[2];
+    }
+  }
+  // the common parts of a charge set (statistics, log) with no lattice charges
+  coulps_charges_t C = nullptr;
+  int st = coulps_charges_create(L, 0, nullptr, nullptr, log_capacity, &C);
+  if (st) return st;
+  C->off = true;
+  C->n = n;
+  C->nblk = gather_blocks(n);
+  dev_free(L->alloc, C->d_partials, L->stream);
+  dev_free(L->alloc, C->d_q, L->stream);
+  const size_t nc = (size_t)g.n_chains;
+  C->d_partials = (double *)dev_alloc(L->alloc, sizeof(double) * 2 * (size_t)C->nblk * nc, L->stream);
+  C->d_q = (double *)dev_alloc(L->alloc, sizeof(double) * (size_t)(n > 0 ? n : 1), L->stream);
+  C->d_oidx = (uint32_t *)dev_alloc(L->alloc, sizeof(uint32_t) * 8 * (size_t)(n > 0 ? n : 1), L->stream);
+  C->d_ow = (double *)dev_alloc(L->alloc, sizeof(double) * 8 * (size_t)(n > 0 ? n : 1), L->stream);
+  C->d_og = (double *)dev_alloc(L->alloc, sizeof(double) * 24 * (size_t)(n > 0 ? n : 1), L->stream);
+  C->d_lastQ = (double *)dev_alloc(L->alloc, sizeof(double) * nc, L->stream);
+  if (forces && n > 0)
+    C->d_fsum = (double *)dev_alloc(L->alloc, sizeof(double) * 3 * (size_t)n * nc, L->stream);
+  if (!C->d_partials || !C->d_q || !C->d_oidx || !C->d_ow || !C->d_og || !C->d_lastQ ||
+      (forces && n > 0 && !C->d_fsum)) {
+    coulps_charges_destroy(C);
+    return COULPS_ENOMEM;
+  }
+  C->qv.assign(q, q + n);
+  C->bytes += (size_t)n * (sizeof(double) + 8 * (sizeof(uint32_t) + 4 * sizeof(double))) +
+              sizeof(double) * nc * (1 + (C->d_fsum ? 3 * (size_t)n : 0));
+  if (n > 0 &&
+      (cudaMemcpyAsync(C->d_q, q, sizeof(double) * n, cudaMemcpyHostToDevice, L->stream) !=
+           cudaSuccess ||
+       cudaMemcpyAsync(C->d_oidx, oidx.data(), sizeof(uint32_t) * oidx.size(),
+                       cudaMemcpyHostToDevice, L->stream) != cudaSuccess ||
+       cudaMemcpyAsync(C->d_ow, ow.data(), sizeof(double) * ow.size(), cudaMemcpyHostToDevice,
+                       L->stream) != cudaSuccess ||
+       cudaMemcpyAsync(C->d_og, og.data(), sizeof(double) * og.size(), cudaMemcpyHostToDevice,
+                       L->stream) != cudaSuccess ||
+       (C->d_fsum && cudaMemsetAsync(C->d_fsum, 0, sizeof(double) * 3 * (size_t)n * nc,
+                                     L->stream) != cudaSuccess) ||
+       cudaStreamSynchronize(L->stream) != cudaSuccess)) {  // pageable host arrays
+    cudaGetLastError();
+    coulps_charges_destroy(C);
+    return COULPS_ECUDA;
+  }
+  *out = C;
+  return COULPS_OK;
+}
+
+int coulps_forces(coulps_charges_t C, double *mean, double *stderr_chains) {
+  if (!C || !mean) return COULPS_EINVAL;
+  if (!C->off || !C->d_fsum) return COULPS_EUNSUPPORTED;
+  coulps_lattice *L = C->lat;
+  const int nc = L->g.n_chains;
+  const size_t n = (size_t)C->n;
+  std::vector<double> fs(3 * n * nc), st((size_t)kStatStride * nc);
+  CK(cudaMemcpyAsync(fs.data(), C->d_fsum, sizeof(double) * fs.size(), cudaMemcpyDeviceToHost,
+                     L->stream));
+  CK(cudaMemcpyAsync(st.data(), C->d_stats, sizeof(double) * st.size(), cudaMemcpyDeviceToHost,
+                     L->stream));
+  int s = check_device_error(L);
+  if (s) return s;
+  double N = 0.0;
+  for (int b = 0; b < nc; ++b) N += st[(size_t)b * kStatStride + kStatN];
+  for (size_t k = 0; k < 3 * n; ++k) {
+    double sum = 0.0;
+    for (int b = 0; b < nc; ++b) sum += fs[(size_t)b * 3 * n + k];
+    mean[k] = N > 0 ? sum / N : NAN;
+    if (stderr_chains) {
+      // spread of the chains' own means (independent chains)
+      double m1 = 0.0, m2 = 0.0;
+      int used = 0;
+      for (int b = 0; b < nc; ++b) {
+        const double nb = st[(size_t)b * kStatStride + kStatN];
+        if (nb <= 0) continue;
+        const double m = fs[(size_t)b * 3 * n + k] / nb;
+        m1 += m;
+        m2 += m * m;
+        ++used;
+      }
+      if (used >= 2) {
+        const double mu = m1 / used;
+        const double var = (m2 - used * mu * mu) / (used - 1);
+        stderr_chains[k] = std::sqrt(var > 0 ? var / used : 0.0);
+      } else {
+        stderr_chains[k] = NAN;
+      }
+    }
+  }
   return COULPS_OK;
 }
 
@@ -1249,6 +1413,7 @@ void coulps_gcv_destroy(coulps_gcv_t G) {
 
 int coulps_gcv_create(coulps_charges_t C, int n_iter, int R, coulps_gcv_t *out) {
   if (!C || !out || n_iter < 0 || R < 0 || R > 4) return COULPS_EINVAL;
+  if (C->off) return COULPS_EUNSUPPORTED;
   *out = nullptr;
   coulps_lattice *L = C->lat;
   const Geometry &g = L->g;
@@ -1400,6 +1565,7 @@ int coulps_gcv_run(coulps_gcv_t G, int n_meas, int n_hb, int n_or, double c) {
 
 int coulps_charges_update(coulps_charges_t C, const int32_t *site, const double *q) {
   if (!C) return COULPS_EINVAL;
+  if (C->off) return COULPS_EUNSUPPORTED;
   if (C->n == 0) return COULPS_OK;
   if (!site || !q) return COULPS_EINVAL;
   coulps_lattice *L = C->lat;

@@ -184,8 +184,17 @@ cudaError_t launch_advance_pass(uint32_t *pass, uint32_t n, cudaStream_t s);
 cudaError_t launch_gather(const Geometry &g, const void *field, const uint32_t *idx,
                           const double *q, int64_t n, double *partials, int nblk,
                           cudaStream_t s);
+// Off-lattice charge sets (trilinear weights over eight corner sites; per
+// particle 8 storage offsets, 8 weights, 8 x 3 weight gradients).
+cudaError_t launch_gather_off(const Geometry &g, const void *field, const uint32_t *oidx,
+                              const double *ow, const double *q, int64_t n, double *partials,
+                              int nblk, cudaStream_t s);
+cudaError_t launch_force_off(const Geometry &g, const void *field, const uint32_t *oidx,
+                             const double *ow, const double *og, const double *q, int64_t n,
+                             const double *Qc, double *fsum, cudaStream_t s);
 cudaError_t launch_finalize(const double *partials, int nblk, int n_chains, double *stats,
-                            double *log, int64_t log_cap, int *err, cudaStream_t s);
+                            double *log, int64_t log_cap, int *err, cudaStream_t s,
+                            double *Qout = nullptr);
 cudaError_t launch_reset_stats(double *stats, int n_chains, cudaStream_t s);
 // cv[chain] gets the sample y = e_last - c * tg[chain], e_last the chain's
 // most recent Eq. (nsum2) sample in stats

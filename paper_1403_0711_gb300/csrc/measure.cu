@@ -72,13 +72,14 @@ __device__ __forceinline__ void chain_QP(const double *__restrict__ partials, in
 
 __global__ void finalize_kernel(const double *__restrict__ partials, int nblk, int n_chains,
                                 double *__restrict__ stats, double *__restrict__ log,
-                                int64_t log_cap, int *err) {
+                                int64_t log_cap, int *err, double *__restrict__ Qout) {
   const int chain = blockIdx.x * kFinalizeWarps + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (chain >= n_chains) return;  // whole warps leave together
   double Q, P;
   chain_QP(partials, nblk, chain, lane, Q, P);
   if (lane != 0) return;
+  if (Qout != nullptr) Qout[chain] = Q;
   double *st = stats + (size_t)chain * kStatStride;
   const int64_t s = (int64_t)st[kStatN];
   double *row = (log != nullptr && s < log_cap) ? log + 3 * ((size_t)s * n_chains + chain) : nullptr;
@@ -113,6 +114,77 @@ __global__ void reset_stats_kernel(double *stats, int n_chains) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_chains * kStatStride) return;
   stats[i] = (i % kStatStride == kStatBatchLen) ? 1.0 : 0.0;
+}
+
+// Off-lattice charges: particle i sees phi~_i = sum_c w_ic phi(corner c)
+// (trilinear weights, eight corners given as storage offsets).  Per CTA the
+// same (Q, P) partials as gather_kernel, with t_i = q_i phi~_i.
+template <typename T>
+__global__ void __launch_bounds__(kGatherThreads)
+    gather_off_kernel(const T *__restrict__ field, size_t chain_elems,
+                      const uint32_t *__restrict__ oidx, const double *__restrict__ ow,
+                      const double *__restrict__ q, int64_t n, double *__restrict__ partials,
+                      int nblk) {
+  const int chain = blockIdx.y;
+  const T *f = field + (size_t)chain * chain_elems;
+  double sq = 0.0, sp = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * kGatherThreads + threadIdx.x; i < n;
+       i += (int64_t)nblk * kGatherThreads) {
+    double p = 0.0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) p += ow[8 * i + c] * (double)f[oidx[8 * i + c]];
+    const double t = q[i] * p;
+    sq += t;
+    sp += t * t;
+  }
+  sq = warp_sum(sq);
+  sp = warp_sum(sp);
+  __shared__ double red[2][kGatherThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][wid] = sq;
+    red[1][wid] = sp;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    sq = lane < kGatherThreads / 32 ? red[0][lane] : 0.0;
+    sp = lane < kGatherThreads / 32 ? red[1][lane] : 0.0;
+    sq = warp_sum(sq);
+    sp = warp_sum(sp);
+    if (lane == 0) {
+      partials[2 * ((size_t)chain * nblk + blockIdx.x) + 0] = sq;
+      partials[2 * ((size_t)chain * nblk + blockIdx.x) + 1] = sp;
+    }
+  }
+}
+
+// Force sample of particle i in chain b (thread per (i, b)), added to the
+// chain's running sums: -de/dr_i = -2 q_i (Q - q_i phi~_i) grad phi~_i with
+// grad phi~_i = sum_c grad w_ic phi(corner c) and Q of the same sample.
+template <typename T>
+__global__ void force_off_kernel(const T *__restrict__ field, size_t chain_elems,
+                                 const uint32_t *__restrict__ oidx, const double *__restrict__ ow,
+                                 const double *__restrict__ og, const double *__restrict__ q,
+                                 int64_t n, const double *__restrict__ Qc,
+                                 double *__restrict__ fsum) {
+  const int chain = blockIdx.y;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const T *f = field + (size_t)chain * chain_elems;
+  double p = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const double v = (double)f[oidx[8 * i + c]];
+    p += ow[8 * i + c] * v;
+    gx += og[3 * (8 * i + c) + 0] * v;
+    gy += og[3 * (8 * i + c) + 1] * v;
+    gz += og[3 * (8 * i + c) + 2] * v;
+  }
+  const double a = -2.0 * q[i] * (Qc[chain] - q[i] * p);
+  double *o = fsum + 3 * ((size_t)chain * n + i);
+  o[0] += a * gx;
+  o[1] += a * gy;
+  o[2] += a * gz;
 }
 
 // Several charge sets on the same fields (the samples do not depend on where
@@ -176,6 +248,33 @@ __global__ void finalize_sets_kernel(const SetTable t, int n_chains, int *err) {
 
 }  // namespace
 
+cudaError_t launch_gather_off(const Geometry &g, const void *field, const uint32_t *oidx,
+                              const double *ow, const double *q, int64_t n, double *partials,
+                              int nblk, cudaStream_t s) {
+  dim3 grid(nblk, g.n_chains);
+  if (g.precision == COULPS_F32)
+    gather_off_kernel<float><<<grid, kGatherThreads, 0, s>>>(
+        reinterpret_cast<const float *>(field), g.chain_elems, oidx, ow, q, n, partials, nblk);
+  else
+    gather_off_kernel<double><<<grid, kGatherThreads, 0, s>>>(
+        reinterpret_cast<const double *>(field), g.chain_elems, oidx, ow, q, n, partials, nblk);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_force_off(const Geometry &g, const void *field, const uint32_t *oidx,
+                             const double *ow, const double *og, const double *q, int64_t n,
+                             const double *Qc, double *fsum, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  dim3 grid((unsigned)((n + 127) / 128), g.n_chains);
+  if (g.precision == COULPS_F32)
+    force_off_kernel<float><<<grid, 128, 0, s>>>(reinterpret_cast<const float *>(field),
+                                                  g.chain_elems, oidx, ow, og, q, n, Qc, fsum);
+  else
+    force_off_kernel<double><<<grid, 128, 0, s>>>(reinterpret_cast<const double *>(field),
+                                                   g.chain_elems, oidx, ow, og, q, n, Qc, fsum);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_measure_sets(const Geometry &g, const void *field, const SetTable &t,
                                 int *err, cudaStream_t s) {
   if (t.n_sets < 1) return cudaSuccess;
@@ -215,9 +314,10 @@ cudaError_t launch_gather(const Geometry &g, const void *field, const uint32_t *
 }
 
 cudaError_t launch_finalize(const double *partials, int nblk, int n_chains, double *stats,
-                            double *log, int64_t log_cap, int *err, cudaStream_t s) {
+                            double *log, int64_t log_cap, int *err, cudaStream_t s,
+                            double *Qout) {
   finalize_kernel<<<(n_chains + kFinalizeWarps - 1) / kFinalizeWarps, 32 * kFinalizeWarps, 0, s>>>(
-      partials, nblk, n_chains, stats, log, log_cap, err);
+      partials, nblk, n_chains, stats, log, log_cap, err, Qout);
   return cudaGetLastError();
 }
 

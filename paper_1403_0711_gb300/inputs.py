@@ -91,6 +91,20 @@ def uniform_q(L, n, seed, qmax=1.0):
     return sites, q
 
 
+def off_lattice(L, n, seed, qmax=1.0):
+    """n particles at real positions uniform in [0, L - 1] per axis (x, y, z),
+    charges uniform in [-qmax, qmax]; a few are put on exact lattice points,
+    box faces and the far corner (the edge cases of the corner choice)."""
+    rng = _rng(seed)
+    hi = np.asarray(L, dtype=np.float64) - 1.0
+    pos = rng.uniform(0.0, 1.0, size=(n, 3)) * hi
+    special = [hi, np.zeros(3), np.floor(hi / 2), np.array([hi[0], 0.0, hi[2] / 3])]
+    for k in range(min(n // 2, len(special))):
+        pos[k] = special[k]
+    q = rng.uniform(-qmax, qmax, size=n)
+    return pos, q
+
+
 def blobs(L, n, seed, n_blob=200, sigma=6.0, qmax=0.8):
     Lx, Ly, Lz = L
     rng = _rng(seed)

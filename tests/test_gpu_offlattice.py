@@ -1,0 +1,147 @@
+"""Off-lattice charges (coulps_charges_create_off) against the FP64 oracle.
+
+Per sample: the CUDA path's (Q, P, e) of trilinearly interpolated charges and
+its force sums -de/dr_i equal the oracle's (oracle/offlattice.py) on the
+oracle chain's own fields (same seed, chain ids and Philox counters, FP64),
+to 1e-12 relative.  In distribution: the pooled mean of e and the mean forces
+over many chains match the exact interpolated-Green-function values on a
+small box within a few standard errors."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+
+
+@pytest.fixture(scope="module")
+def cl():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1403_0711_gb300 import _build, coulps
+    _build.build()
+    coulps.load()
+    coulps.use_torch_allocator()
+    return coulps
+
+
+@pytest.fixture(scope="module")
+def stream():
+    import torch
+    return torch.cuda.Stream()
+
+
+def _oracle_steps(orc, L, seed, chain, n_therm, n_meas, n_hb, n_or, pos, q):
+    from oracle import offlattice as off
+    c = orc.Chain(L, seed=seed, chain=chain)
+    c.run(n_therm, n_hb, n_or)
+    qpe, forces = [], []
+    for _ in range(n_meas):
+        c.run(1, n_hb, n_or)
+        qpe.append(off.sample(c.phi, L, pos, q))
+        forces.append(off.force_sample(c.phi, L, pos, q))
+    return np.array(qpe), np.array(forces)
+
+
+def _rel(got, ref):
+    Q, P = ref[:, 0], ref[:, 1]
+    den = np.maximum(Q * Q + P, 1e-300)
+    eq = np.abs(got[:, 0] - Q) / np.sqrt(np.maximum(P, 1e-300))
+    return max(eq.max(), (np.abs(got[:, 1] - P) / den).max(), (np.abs(got[:, 2] - ref[:, 2]) / den).max())
+
+
+@pytest.mark.parametrize("L,n,path", [((13, 7, 5), 9, "run"), ((9, 2, 17), 5, "measure"),
+                                      ((2, 2, 2), 3, "run"), ((33, 17, 9), 40, "sets")])
+def test_off_lattice_samples_and_forces_match_oracle(cl, stream, orc, L, n, path):
+    from paper_1403_0711_gb300 import inputs
+    pos, q = inputs.off_lattice(L, n, seed=sum(L))
+    n_chains, n_therm, n_meas, n_hb, n_or, seed = 2, 2, 5, 1, 2, 11
+    lat = cl.Lattice(L, n_chains=n_chains, precision=cl.F64, seed=seed, stream=stream)
+    ch = cl.Charges.off_lattice(lat, pos, q, log_capacity=n_meas, forces=True)
+    if path == "run":
+        ch.run(n_therm, n_meas, n_hb, n_or)
+    elif path == "measure":
+        lat.sweep(n_therm, n_hb, n_or)
+        for _ in range(n_meas):
+            lat.sweep(1, n_hb, n_or)
+            ch.measure()
+    else:  # beside an on-lattice set, through the multi-set path
+        sites, qq = inputs.uniform_q(L, 7, seed=3)
+        on = cl.Charges(lat, sites, qq, log_capacity=n_meas)
+        cl.run_sets(lat, [on, ch], n_therm, n_meas, n_hb, n_or)
+        ref_on = orc.Chain(L, seed=seed, chain=1)
+        ref_on.run(n_therm, n_hb, n_or)
+        want = ref_on.run(n_meas, n_hb, n_or, sites, qq)
+        assert _rel(on.samples()[:, 1], want) < TOL64
+        on.close()
+    s = ch.samples()
+    assert s.shape == (n_meas, n_chains, 3)
+    fsum = np.zeros((n, 3))
+    for k in range(n_chains):
+        ref, f = _oracle_steps(orc, L, seed, k, n_therm, n_meas, n_hb, n_or, pos, q)
+        assert _rel(s[:, k], ref) < TOL64, k
+        fsum += f.sum(axis=0)
+    mean, err = ch.forces()
+    want = fsum / (n_chains * n_meas)
+    scale = np.abs(want).max() + 1e-300
+    assert np.abs(mean - want).max() < 1e-11 * scale
+    assert np.all(np.isfinite(err))
+    # reset clears the samples and the force sums
+    ch.reset_stats()
+    ch.measure()
+    m1, _ = ch.forces()
+    assert ch.estimate()["n"] == n_chains
+    assert np.all(np.isfinite(m1))
+    ch.close()
+    lat.close()
+
+
+def test_off_lattice_mean_and_forces_match_exact(cl, stream, orc):
+    """8 x 7 x 6 box, 4 particles: pooled mean of e against E = sum_{i!=j}
+    q_i q_j G~(r_i, r_j) and mean forces against -2 q_i sum_j q_j grad G~,
+    both from the dense lattice Green function, within 5 standard errors."""
+    from oracle import offlattice as off
+    L = (8, 7, 6)
+    pos = np.array([[2.3, 3.1, 2.7], [4.6, 3.4, 2.2], [3.5, 1.2, 3.9], [5.2, 5.5, 1.4]])
+    q = np.array([1.0, -1.0, 0.7, -0.4])
+    G = orc.green_dense(L)
+    E = off.energy_exact(G, L, pos, q)
+    F = off.force_exact(G, L, pos, q)
+    lat = cl.Lattice(L, n_chains=256, precision=cl.F32, seed=77, stream=stream)
+    ch = cl.Charges.off_lattice(lat, pos, q, forces=True)
+    ch.run(100, 2000, 1, 1)
+    est = ch.estimate()
+    mean, err = ch.forces()
+    ch.close()
+    lat.close()
+    assert abs(est["mean"] - E) < 5 * est["stderr"], (est, E)
+    z = np.abs(mean - F) / err
+    assert z.max() < 5, (mean, F, err)
+    assert np.abs(mean - F).max() < 0.15 * np.abs(F).max()
+
+
+def test_off_lattice_rejects_bad_input(cl, stream):
+    L = (6, 5, 4)
+    lat = cl.Lattice(L, n_chains=1, precision=cl.F32, seed=1, stream=stream)
+    for pos in ([[5.01, 1, 1]], [[-0.01, 1, 1]], [[1, 1, np.nan]]):
+        with pytest.raises(cl.CoulpsError):
+            cl.Charges.off_lattice(lat, pos, [1.0])
+    flat = cl.Lattice((6, 1, 4), n_chains=1, precision=cl.F32, seed=1, stream=stream)
+    with pytest.raises(cl.CoulpsError):
+        cl.Charges.off_lattice(flat, [[1, 0, 1]], [1.0])
+    ch = cl.Charges.off_lattice(lat, [[1.5, 2.5, 0.5]], [1.0])
+    with pytest.raises(cl.CoulpsError):
+        ch.forces()  # created without forces
+    with pytest.raises(cl.CoulpsError):
+        ch.update([[1, 1, 1]], [1.0])
+    with pytest.raises(cl.CoulpsError):
+        cl.GlobalCV(ch)
+    ch.close()
+    # an empty set samples zeros
+    e = cl.Charges.off_lattice(lat, np.zeros((0, 3)), np.zeros(0), log_capacity=2, forces=True)
+    e.run(1, 2, 1, 1)
+    assert np.all(e.samples() == 0)
+    e.close()
+    flat.close()
+    lat.close()
