@@ -93,3 +93,97 @@ def force_exact(G, L, pos, q):
     n = len(q)
     mask = 1.0 - np.eye(n)
     return -2.0 * q[:, None] * np.einsum("ijm,j,ij->im", dGt, q, mask)
+
+
+# --------------------------------------------------------------------------
+# Near-field direct correction
+# --------------------------------------------------------------------------
+# The paper's closing remarks propose computing close particles directly,
+# because the lattice Green function misrepresents the steep core of the
+# Coulomb potential.  Reading used here: the near set N = {(i, j): i < j,
+# |r_i - r_j| < r_c} is fixed when the set is built; its pairs are removed
+# from every sample,
+#     e_far = Q^2 - P - s_N,   s_N = 2 sum_{(i,j) in N} q_i q_j phi~_i phi~_j,
+# (the mean of e_far is the lattice energy of the far pairs) and added back
+# with the continuum kernel of Eq. (s1),
+#     E_N^direct = 2 sum_{(i,j) in N} q_i q_j / (4 pi |r_i - r_j|),
+# so that E ~ <e_far> + E_N^direct.  Forces follow in the same way.
+
+
+def near_pairs(pos, rc):
+    """All pairs i < j with |r_i - r_j| < rc, shape (m, 2), by brute force."""
+    pos = np.asarray(pos, dtype=np.float64).reshape(-1, 3)
+    out = []
+    for i in range(len(pos)):
+        for j in range(i + 1, len(pos)):
+            if np.sqrt(np.sum((pos[i] - pos[j]) ** 2)) < rc:
+                out.append((i, j))
+    return np.array(out, dtype=np.int64).reshape(-1, 2)
+
+
+def near_sample(phi, L, pos, q, pairs):
+    """(Q, P + s_N, e_far) of one field: s_N moves into the subtracted part
+    so that e_far = Q^2 - (P + s_N)."""
+    q = np.asarray(q, dtype=np.float64)
+    t = q * interpolate(phi, L, pos)[0]
+    Q, P = float(t.sum()), float((t * t).sum())
+    s = 0.0
+    for i, j in pairs:
+        s += 2.0 * t[i] * t[j]
+    return Q, P + s, Q * Q - P - s
+
+
+def near_force_sample(phi, L, pos, q, pairs):
+    """-de_far/dr_i = -2 q_i (Q - q_i phi~_i - sum_{j near i} q_j phi~_j) grad phi~_i."""
+    q = np.asarray(q, dtype=np.float64)
+    pt, gr = interpolate(phi, L, pos)
+    t = q * pt
+    u = np.zeros(len(q))
+    for i, j in pairs:
+        u[i] += t[j]
+        u[j] += t[i]
+    Q = float(t.sum())
+    return -2.0 * (q * (Q - t - u))[:, None] * gr
+
+
+def near_direct_energy(pos, q, pairs):
+    """E_N^direct = 2 sum_{(i,j) in N} q_i q_j / (4 pi r_ij)."""
+    pos = np.asarray(pos, dtype=np.float64).reshape(-1, 3)
+    tot = 0.0
+    for i, j in pairs:
+        tot += 2.0 * q[i] * q[j] / np.sqrt(np.sum((pos[i] - pos[j]) ** 2))
+    return tot / (4.0 * np.pi)
+
+
+def near_direct_forces(pos, q, pairs):
+    """-dE_N^direct/dr_i = 2 q_i sum_{j near i} q_j (r_i - r_j) / (4 pi r_ij^3)."""
+    pos = np.asarray(pos, dtype=np.float64).reshape(-1, 3)
+    F = np.zeros_like(pos)
+    for i, j in pairs:
+        d = pos[i] - pos[j]
+        r = np.sqrt(np.sum(d * d))
+        f = 2.0 * q[i] * q[j] * d / (4.0 * np.pi * r ** 3)
+        F[i] += f
+        F[j] -= f
+    return F
+
+
+def far_energy_exact(G, L, pos, q, pairs):
+    """Mean of e_far: the exact interpolated-lattice energy without the pairs of N."""
+    q = np.asarray(q, dtype=np.float64)
+    Gt, _ = _green_tilde(G, L, pos)
+    E = float(q @ Gt @ q - np.sum(q * q * np.diag(Gt)))
+    for i, j in pairs:
+        E -= 2.0 * q[i] * q[j] * Gt[i, j]
+    return E
+
+
+def far_force_exact(G, L, pos, q, pairs):
+    """Mean of -de_far/dr_i: -2 q_i sum_{j != i, (i,j) not in N} q_j grad_r G~(r_i, r_j)."""
+    q = np.asarray(q, dtype=np.float64)
+    _, dGt = _green_tilde(G, L, pos)
+    n = len(q)
+    mask = 1.0 - np.eye(n)
+    for i, j in pairs:
+        mask[i, j] = mask[j, i] = 0.0
+    return -2.0 * q[:, None] * np.einsum("ijm,j,ij->im", dGt, q, mask)

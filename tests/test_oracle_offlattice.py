@@ -77,3 +77,92 @@ def test_estimators_average_to_the_exact_energy_and_forces(orc):
     assert abs(e.mean() - E) < 4 * e.std(ddof=1) / math.sqrt(n), (e.mean(), E)
     se = f.std(axis=0, ddof=1) / math.sqrt(n)
     assert (np.abs(f.mean(axis=0) - F) < 4 * se + 1e-12).all(), (f.mean(axis=0), F, se)
+
+
+def test_near_pairs_against_cell_free_enumeration():
+    from oracle import offlattice as off
+    pos = _pos((9, 8, 7), 60, 7)
+    rc = 2.2
+    pairs = off.near_pairs(pos, rc)
+    d = np.linalg.norm(pos[:, None, :] - pos[None, :, :], axis=2)
+    want = {(i, j) for i in range(60) for j in range(i + 1, 60) if d[i, j] < rc}
+    assert {tuple(p) for p in pairs} == want and len(pairs) == len(want) > 0
+
+
+def test_near_correction_limits(orc):
+    """No pairs: the plain estimator.  All pairs near: e_far == 0 for every
+    field (Q^2 = P + s_N identically) and the direct part is Eq. (s1)."""
+    from oracle import offlattice as off
+    L = (7, 6, 5)
+    pos = _pos(L, 6, 8)
+    q = np.array([1.0, -0.5, 0.8, -1.2, 0.3, 1.0])
+    rng = np.random.default_rng(9)
+    phi = rng.standard_normal((L[2], L[1], L[0]))
+    none = off.near_pairs(pos, 0.0)
+    assert len(none) == 0
+    assert np.allclose(off.near_sample(phi, L, pos, q, none), off.sample(phi, L, pos, q), rtol=0, atol=0)
+    assert np.array_equal(off.near_force_sample(phi, L, pos, q, none), off.force_sample(phi, L, pos, q))
+    allp = off.near_pairs(pos, 1e9)
+    assert len(allp) == 15
+    Q, Pn, e = off.near_sample(phi, L, pos, q, allp)
+    assert abs(e) < 1e-12 * Q * Q + 1e-14
+    assert np.abs(off.near_force_sample(phi, L, pos, q, allp)).max() < 1e-12
+    assert abs(off.near_direct_energy(pos, q, allp) - orc.coulomb_direct(pos, q)) < 1e-13
+    G = orc.green_dense(L)
+    assert abs(off.far_energy_exact(G, L, pos, q, allp)) < 1e-13
+
+
+def test_near_forces_are_minus_gradients():
+    """Per-sample far force = -d e_far/dr_i at a fixed field and direct force
+    = -dE_direct/dr_i, both against central differences."""
+    from oracle import offlattice as off
+    L = (6, 7, 5)
+    pos = _pos(L, 5, 10)
+    pos = np.floor(pos) + np.clip(pos - np.floor(pos), 0.1, 0.9)
+    q = np.array([1.0, -1.0, 0.6, 0.9, -0.7])
+    pairs = off.near_pairs(pos, 3.0)
+    assert 0 < len(pairs) < 10
+    rng = np.random.default_rng(11)
+    phi = rng.standard_normal((L[2], L[1], L[0]))
+    f = off.near_force_sample(phi, L, pos, q, pairs)
+    fd_ = off.near_direct_forces(pos, q, pairs)
+    h = 1e-6
+    for i in range(len(q)):
+        for mu in range(3):
+            a, b = pos.copy(), pos.copy()
+            a[i, mu] += h
+            b[i, mu] -= h
+            fd = -(off.near_sample(phi, L, a, q, pairs)[2] - off.near_sample(phi, L, b, q, pairs)[2]) / (2 * h)
+            assert abs(f[i, mu] - fd) < 1e-6 * max(1.0, abs(fd)), (i, mu)
+            fd = -(off.near_direct_energy(a, q, pairs) - off.near_direct_energy(b, q, pairs)) / (2 * h)
+            assert abs(fd_[i, mu] - fd) < 1e-7 * max(1.0, abs(fd)), (i, mu)
+
+
+def test_far_estimators_average_to_exact_far_values(orc):
+    from oracle import offlattice as off
+    L = (5, 4, 4)
+    pos = _pos(L, 5, 12)
+    q = np.array([1.0, -1.0, 1.0, -0.5, 0.5])
+    pairs = off.near_pairs(pos, 1.8)
+    assert 0 < len(pairs) < 10
+    G = orc.green_dense(L)
+    C = np.linalg.cholesky(orc.laplacian_dense(L))
+    rng = np.random.default_rng(13)
+    n = 20000
+    z = rng.standard_normal((n, C.shape[0]))
+    phis = np.linalg.solve(C.T, z.T).T.reshape(n, L[2], L[1], L[0])
+    e = np.array([off.near_sample(p, L, pos, q, pairs)[2] for p in phis])
+    f = np.array([off.near_force_sample(p, L, pos, q, pairs) for p in phis])
+    E = off.far_energy_exact(G, L, pos, q, pairs)
+    F = off.far_force_exact(G, L, pos, q, pairs)
+    assert abs(e.mean() - E) < 4 * e.std(ddof=1) / math.sqrt(n), (e.mean(), E)
+    se = f.std(axis=0, ddof=1) / math.sqrt(n)
+    assert (np.abs(f.mean(axis=0) - F) < 4 * se + 1e-12).all()
+    # the far force is the gradient of the far energy
+    h = 1e-6
+    for i, mu in ((0, 0), (2, 1), (4, 2)):
+        a, b = pos.copy(), pos.copy()
+        a[i, mu] += h
+        b[i, mu] -= h
+        fd = -(off.far_energy_exact(G, L, a, q, pairs) - off.far_energy_exact(G, L, b, q, pairs)) / (2 * h)
+        assert abs(F[i, mu] - fd) < 1e-6 * max(1.0, abs(fd))
