@@ -217,6 +217,28 @@ int coulps_charges_create_off(coulps_lattice_t lat, int64_t n, const double *pos
                               const double *q, int64_t log_capacity, int forces,
                               coulps_charges_t *out);
 
+/* Near-field direct correction of an off-lattice set (the paper's closing
+ * remarks: close particles are better computed directly than through the
+ * lattice, whose Green function misses the steep core of the potential).
+ * The near set N = {(i, j): i < j, |r_i - r_j| < rc} is fixed by this call
+ * (rc = 0: none).  From then on every sample leaves N's pairs out,
+ *   s_N = 2 sum_{(i,j) in N} q_i q_j phi~_i phi~_j,
+ *   P -> P + s_N, e = Q^2 - P - s_N  (the logged P includes s_N),
+ * and, with forces on, f_i = -2 q_i (Q - q_i phi~_i - sum_{j near i} q_j
+ * phi~_j) grad phi~_i; the pairs come back with the continuum kernel of
+ * Eq. (s1), returned here in FP64:
+ *   *e_direct = 2 sum_{(i,j) in N} q_i q_j / (4 pi r_ij),
+ *   f_direct[3i + mu] = 2 q_i sum_{j near i} q_j (r_i - r_j)_mu / (4 pi r_ij^3)
+ * (any of the three outputs may be NULL; f_direct holds 3 n doubles).  The
+ * energy is then coulps_estimate's mean + *e_direct and the force
+ * coulps_forces' mean + f_direct.  Pairs are found on the host by a cell grid;
+ * the list is kept on the device as CSR (both directions, ascending).
+ * Synchronises; drops the set's samples, force sums and captured graphs.
+ * Errors: EINVAL (rc < 0 or not finite), EUNSUPPORTED (not an off-lattice
+ * set), ENOMEM, ECUDA. */
+int coulps_charges_near(coulps_charges_t ch, double rc, int64_t *n_pairs, double *e_direct,
+                        double *f_direct);
+
 /* Synchronise and return the mean force on each particle of an off-lattice
  * set created with forces != 0: mean[3i + mu] = (sum over all chains' samples
  * of f_i,mu) / (number of samples), and, if stderr_chains is not NULL, the

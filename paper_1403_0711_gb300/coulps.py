@@ -42,7 +42,7 @@ EXPORTS = (
     "coulps_cv_reset", "coulps_cv_charge_term", "coulps_set_fused", "coulps_set_pass_tile",
     "coulps_measure_sets", "coulps_run_sets", "coulps_gcv_create", "coulps_gcv_destroy",
     "coulps_gcv_info", "coulps_gcv_h", "coulps_gcv_eval", "coulps_gcv_run",
-    "coulps_charges_create_off", "coulps_forces",
+    "coulps_charges_create_off", "coulps_forces", "coulps_charges_near",
 )
 SCHEDULE_ALIGNED, SCHEDULE_PHASED = 0, 1
 STAT_STRIDE = 72
@@ -89,6 +89,7 @@ def load(path: str | Path | None = None):
         "coulps_charges_create": (i32, [vp, i64, P(ctypes.c_int32), P(f64), i64, P(vp)]),
         "coulps_charges_create_off": (i32, [vp, i64, P(f64), P(f64), i64, ctypes.c_int, P(vp)]),
         "coulps_forces": (i32, [vp, P(f64), P(f64)]),
+        "coulps_charges_near": (i32, [vp, ctypes.c_double, P(i64), P(f64), P(f64)]),
         "coulps_charges_destroy": (None, [vp]),
         "coulps_measure": (i32, [vp, vp]),
         "coulps_run": (i32, [vp, vp, i32, i32, i32, i32]),
@@ -319,6 +320,16 @@ class Charges:
                                              int(log_capacity), int(bool(forces)),
                                              ctypes.byref(h)), "coulps_charges_create_off")
         return cls(lattice, None, qq, _handle=h)
+
+    def near(self, rc):
+        """Leave the pairs closer than rc out of every sample; returns their
+        direct (continuum Eq. (s1)) energy and forces to add back."""
+        npairs = ctypes.c_int64()
+        e = ctypes.c_double()
+        f = np.zeros((self.n, 3), dtype=np.float64)
+        _check(self._lib.coulps_charges_near(self.handle, float(rc), ctypes.byref(npairs),
+                                             ctypes.byref(e), _f64p(f)), "coulps_charges_near")
+        return {"n_pairs": npairs.value, "e_direct": e.value, "f_direct": f}
 
     def forces(self):
         """(mean (n, 3), stderr over chains (n, 3)) of -de/dr_i."""
@@ -598,6 +609,10 @@ def coulps_charges_create_off(lattice, pos, q, log_capacity=0, forces=False):
 
 def coulps_forces(charges):
     return charges.forces()
+
+
+def coulps_charges_near(charges, rc):
+    return charges.near(rc)
 
 
 def coulps_sweep(lattice, n_compound, n_hb, n_or):

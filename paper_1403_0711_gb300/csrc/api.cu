@@ -107,6 +107,14 @@ struct coulps_charges {
   bool off = false;
   uint32_t *d_oidx = nullptr;
   double *d_ow = nullptr, *d_og = nullptr, *d_lastQ = nullptr, *d_fsum = nullptr;
+  std::vector<double> pos;  // off-lattice positions (x, y, z) per particle
+  // near pairs (CSR over particles, both directions); gather blocks nblk_g,
+  // near-pair blocks after them (nblk = row length of the partials)
+  int nblk_g = 0;
+  int64_t n_pairs = 0;
+  int64_t *d_nptr = nullptr;
+  uint32_t *d_nbr = nullptr;
+  double *d_t = nullptr, *d_u = nullptr;
   double *d_log = nullptr;       // [sample][chain][3]
   int64_t log_cap = 0;
   size_t bytes = 0;
@@ -439,13 +447,17 @@ int stage_gather(coulps_lattice *L, coulps_charges *C) {
 
 int enqueue_measure(coulps_lattice *L, coulps_charges *C) {
   if (C->off) {
-    CK(launch_gather_off(L->g, L->field, C->d_oidx, C->d_ow, C->d_q, C->n, C->d_partials, C->nblk,
-                         L->stream));
+    const bool near = C->n_pairs > 0;
+    CK(launch_gather_off(L->g, L->field, C->d_oidx, C->d_ow, C->d_q, C->n, C->d_partials,
+                         C->nblk_g, C->nblk, near ? C->d_t : nullptr, L->stream));
+    if (near)
+      CK(launch_near(C->d_t, C->d_nptr, C->d_nbr, C->n, L->g.n_chains, C->d_u, C->d_partials,
+                     C->nblk, C->nblk_g, L->stream));
     CK(launch_finalize(C->d_partials, C->nblk, L->g.n_chains, C->d_stats, C->d_log, C->log_cap,
                        L->d_err, L->stream, C->d_lastQ));
     if (C->d_fsum)
       CK(launch_force_off(L->g, L->field, C->d_oidx, C->d_ow, C->d_og, C->d_q, C->n, C->d_lastQ,
-                          C->d_fsum, L->stream));
+                          near ? C->d_u : nullptr, C->d_fsum, L->stream));
     return COULPS_OK;
   }
   CK(launch_gather(L->g, L->field, C->d_idx, C->d_q, C->n, C->d_partials, C->nblk, L->stream));
@@ -944,7 +956,8 @@ void coulps_charges_destroy(coulps_charges_t C) {
   dev_free(L->alloc, C->d_cvstats, L->stream);
   dev_free(L->alloc, C->d_log, L->stream);
   for (void *p : {(void *)C->d_oidx, (void *)C->d_ow, (void *)C->d_og, (void *)C->d_lastQ,
-                  (void *)C->d_fsum})
+                  (void *)C->d_fsum, (void *)C->d_nptr, (void *)C->d_nbr, (void *)C->d_t,
+                  (void *)C->d_u})
     dev_free(L->alloc, p, L->stream);
   if (C->staged) {
     cudaEventSynchronize(C->staged);
@@ -1232,7 +1245,8 @@ int coulps_charges_create_off(coulps_lattice_t L, int64_t n, const double *pos, 
   if (st) return st;
   C->off = true;
   C->n = n;
-  C->nblk = gather_blocks(n);
+  C->nblk = C->nblk_g = gather_blocks(n);
+  C->pos.assign(pos, pos + 3 * n);
   dev_free(L->alloc, C->d_partials, L->stream);
   dev_free(L->alloc, C->d_q, L->stream);
   const size_t nc = (size_t)g.n_chains;
@@ -1269,6 +1283,127 @@ int coulps_charges_create_off(coulps_lattice_t L, int64_t n, const double *pos, 
     return COULPS_ECUDA;
   }
   *out = C;
+  return COULPS_OK;
+}
+
+int coulps_charges_near(coulps_charges_t C, double rc, int64_t *n_pairs, double *e_direct,
+                        double *f_direct) {
+  if (!C || !std::isfinite(rc) || rc < 0.0) return COULPS_EINVAL;
+  if (!C->off) return COULPS_EUNSUPPORTED;
+  coulps_lattice *L = C->lat;
+  const int64_t n = C->n;
+  const double *p = C->pos.data();
+  // neighbour lists by a cell grid of edge >= rc (a particle's near partners
+  // are in its own or the 26 adjacent cells), each list in ascending order
+  std::vector<int64_t> ptr((size_t)n + 1, 0);
+  std::vector<uint32_t> nbr;
+  if (rc > 0.0 && n > 1) {
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = 0; i < n; ++i)
+      for (int mu = 0; mu < 3; ++mu) {
+        lo[mu] = std::min(lo[mu], p[3 * i + mu]);
+        hi[mu] = std::max(hi[mu], p[3 * i + mu]);
+      }
+    double cs = rc;
+    int64_t nd[3];
+    for (;;) {
+      for (int mu = 0; mu < 3; ++mu) nd[mu] = (int64_t)std::floor((hi[mu] - lo[mu]) / cs) + 1;
+      if ((double)nd[0] * nd[1] * nd[2] <= 8.0 * (double)n + 64.0) break;
+      cs *= 1.5;
+    }
+    auto cell_of = [&](int64_t i, int mu) {
+      int64_t c = (int64_t)std::floor((p[3 * i + mu] - lo[mu]) / cs);
+      return c < 0 ? 0 : (c >= nd[mu] ? nd[mu] - 1 : c);
+    };
+    const int64_t ncell = nd[0] * nd[1] * nd[2];
+    std::vector<int64_t> cstart((size_t)ncell + 1, 0), cell((size_t)n), order((size_t)n);
+    for (int64_t i = 0; i < n; ++i) {
+      cell[i] = (cell_of(i, 2) * nd[1] + cell_of(i, 1)) * nd[0] + cell_of(i, 0);
+      cstart[cell[i] + 1]++;
+    }
+    for (int64_t c = 0; c < ncell; ++c) cstart[c + 1] += cstart[c];
+    {
+      std::vector<int64_t> fill(cstart.begin(), cstart.end() - 1);
+      for (int64_t i = 0; i < n; ++i) order[fill[cell[i]]++] = i;
+    }
+    std::vector<uint32_t> mine;
+    for (int64_t i = 0; i < n; ++i) {
+      mine.clear();
+      const int64_t cx = cell_of(i, 0), cy = cell_of(i, 1), cz = cell_of(i, 2);
+      for (int64_t z = std::max<int64_t>(cz - 1, 0); z <= std::min(cz + 1, nd[2] - 1); ++z)
+        for (int64_t y = std::max<int64_t>(cy - 1, 0); y <= std::min(cy + 1, nd[1] - 1); ++y)
+          for (int64_t x = std::max<int64_t>(cx - 1, 0); x <= std::min(cx + 1, nd[0] - 1); ++x) {
+            const int64_t c = (z * nd[1] + y) * nd[0] + x;
+            for (int64_t k = cstart[c]; k < cstart[c + 1]; ++k) {
+              const int64_t j = order[k];
+              if (j == i) continue;
+              const double dx = p[3 * i] - p[3 * j], dy = p[3 * i + 1] - p[3 * j + 1],
+                           dz = p[3 * i + 2] - p[3 * j + 2];
+              if (std::sqrt(dx * dx + dy * dy + dz * dz) < rc) mine.push_back((uint32_t)j);
+            }
+          }
+      std::sort(mine.begin(), mine.end());
+      nbr.insert(nbr.end(), mine.begin(), mine.end());
+      ptr[i + 1] = (int64_t)nbr.size();
+    }
+  }
+  const int64_t pairs = (int64_t)nbr.size() / 2;
+  // the direct part with the continuum kernel of Eq. (s1), in FP64
+  double E = 0.0;
+  if (f_direct)
+    for (int64_t k = 0; k < 3 * n; ++k) f_direct[k] = 0.0;
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k) {
+      const int64_t j = nbr[k];
+      const double d[3] = {p[3 * i] - p[3 * j], p[3 * i + 1] - p[3 * j + 1],
+                           p[3 * i + 2] - p[3 * j + 2]};
+      const double r = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      const double qq = C->qv[i] * C->qv[j];
+      if (j > i) E += 2.0 * qq / r;
+      if (f_direct)
+        for (int mu = 0; mu < 3; ++mu) f_direct[3 * i + mu] += 2.0 * qq * d[mu] / (r * r * r);
+    }
+  const double inv4pi = 1.0 / (4.0 * M_PI);
+  E *= inv4pi;
+  if (f_direct)
+    for (int64_t k = 0; k < 3 * n; ++k) f_direct[k] *= inv4pi;
+  if (n_pairs) *n_pairs = pairs;
+  if (e_direct) *e_direct = E;
+  // device side: the graphs that measure this set are rebuilt, the samples
+  // taken under the previous list are dropped
+  if (L->graph_key == C ||
+      std::find(L->mgraph_key.begin(), L->mgraph_key.end(), (const void *)C) != L->mgraph_key.end())
+    drop_graph(L);
+  CK(cudaStreamSynchronize(L->stream));
+  for (void **q : {(void **)&C->d_nptr, (void **)&C->d_nbr, (void **)&C->d_t, (void **)&C->d_u}) {
+    dev_free(L->alloc, *q, L->stream);
+    *q = nullptr;
+  }
+  C->n_pairs = 0;
+  const int nc = L->g.n_chains;
+  const int row = C->nblk_g + (pairs > 0 ? near_blocks(n) : 0);
+  if (row != C->nblk) {
+    dev_free(L->alloc, C->d_partials, L->stream);
+    C->d_partials = (double *)dev_alloc(L->alloc, sizeof(double) * 2 * (size_t)row * nc, L->stream);
+    C->nblk = row;
+    if (!C->d_partials) return COULPS_ENOMEM;
+  }
+  if (pairs > 0) {
+    C->d_nptr = (int64_t *)dev_alloc(L->alloc, sizeof(int64_t) * ptr.size(), L->stream);
+    C->d_nbr = (uint32_t *)dev_alloc(L->alloc, sizeof(uint32_t) * nbr.size(), L->stream);
+    C->d_t = (double *)dev_alloc(L->alloc, sizeof(double) * (size_t)n * nc, L->stream);
+    C->d_u = (double *)dev_alloc(L->alloc, sizeof(double) * (size_t)n * nc, L->stream);
+    if (!C->d_nptr || !C->d_nbr || !C->d_t || !C->d_u) return COULPS_ENOMEM;
+    CK(cudaMemcpyAsync(C->d_nptr, ptr.data(), sizeof(int64_t) * ptr.size(),
+                       cudaMemcpyHostToDevice, L->stream));
+    CK(cudaMemcpyAsync(C->d_nbr, nbr.data(), sizeof(uint32_t) * nbr.size(),
+                       cudaMemcpyHostToDevice, L->stream));
+    C->n_pairs = pairs;
+  }
+  int st = coulps_reset_stats(C);
+  if (st) return st;
+  CK(launch_reset_stats(C->d_cvstats, nc, L->stream));
+  CK(cudaStreamSynchronize(L->stream));  // pageable host arrays
   return COULPS_OK;
 }
 

@@ -186,12 +186,19 @@ cudaError_t launch_gather(const Geometry &g, const void *field, const uint32_t *
                           cudaStream_t s);
 // Off-lattice charge sets (trilinear weights over eight corner sites; per
 // particle 8 storage offsets, 8 weights, 8 x 3 weight gradients).
+// off-lattice sets: partial blocks of a chain are `row` apart; the gather
+// fills blocks [0, nblk) and (tout != NULL) keeps t_i = q_i phi~_i per chain;
+// launch_near fills blocks [first, first + near_blocks(n)) with (0, s_N).
 cudaError_t launch_gather_off(const Geometry &g, const void *field, const uint32_t *oidx,
                               const double *ow, const double *q, int64_t n, double *partials,
-                              int nblk, cudaStream_t s);
+                              int nblk, int row, double *tout, cudaStream_t s);
+int near_blocks(int64_t n);
+cudaError_t launch_near(const double *t, const int64_t *nptr, const uint32_t *nbr, int64_t n,
+                        int n_chains, double *u, double *partials, int row, int first,
+                        cudaStream_t s);
 cudaError_t launch_force_off(const Geometry &g, const void *field, const uint32_t *oidx,
                              const double *ow, const double *og, const double *q, int64_t n,
-                             const double *Qc, double *fsum, cudaStream_t s);
+                             const double *Qc, const double *u, double *fsum, cudaStream_t s);
 cudaError_t launch_finalize(const double *partials, int nblk, int n_chains, double *stats,
                             double *log, int64_t log_cap, int *err, cudaStream_t s,
                             double *Qout = nullptr);

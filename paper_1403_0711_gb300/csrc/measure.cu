@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(kGatherThreads)
     gather_off_kernel(const T *__restrict__ field, size_t chain_elems,
                       const uint32_t *__restrict__ oidx, const double *__restrict__ ow,
                       const double *__restrict__ q, int64_t n, double *__restrict__ partials,
-                      int nblk) {
+                      int nblk, int row, double *__restrict__ tout) {
   const int chain = blockIdx.y;
   const T *f = field + (size_t)chain * chain_elems;
   double sq = 0.0, sp = 0.0;
@@ -134,6 +134,7 @@ __global__ void __launch_bounds__(kGatherThreads)
 #pragma unroll
     for (int c = 0; c < 8; ++c) p += ow[8 * i + c] * (double)f[oidx[8 * i + c]];
     const double t = q[i] * p;
+    if (tout) tout[(size_t)chain * n + i] = t;
     sq += t;
     sp += t * t;
   }
@@ -152,8 +153,42 @@ __global__ void __launch_bounds__(kGatherThreads)
     sq = warp_sum(sq);
     sp = warp_sum(sp);
     if (lane == 0) {
-      partials[2 * ((size_t)chain * nblk + blockIdx.x) + 0] = sq;
-      partials[2 * ((size_t)chain * nblk + blockIdx.x) + 1] = sp;
+      partials[2 * ((size_t)chain * row + blockIdx.x) + 0] = sq;
+      partials[2 * ((size_t)chain * row + blockIdx.x) + 1] = sp;
+    }
+  }
+}
+
+// Near pairs of an off-lattice set (CSR, both directions): thread per
+// particle i, u_i = sum_{j near i} t_j with t = q phi~ of the same sample;
+// the CTA's s_N part sum_i t_i u_i (= 2 sum over pairs) goes into the P slot
+// of partial block `first + blockIdx.x`, so the finalize forms
+// e = Q^2 - P - s_N.  u is kept for the force kernel.
+__global__ void __launch_bounds__(kGatherThreads)
+    near_kernel(const double *__restrict__ t, const int64_t *__restrict__ nptr,
+                const uint32_t *__restrict__ nbr, int64_t n, double *__restrict__ u,
+                double *__restrict__ partials, int row, int first) {
+  const int chain = blockIdx.y;
+  const double *tc = t + (size_t)chain * n;
+  const int64_t i = (int64_t)blockIdx.x * kGatherThreads + threadIdx.x;
+  double s = 0.0;
+  if (i < n) {
+    double ui = 0.0;
+    for (int64_t k = nptr[i]; k < nptr[i + 1]; ++k) ui += tc[nbr[k]];
+    u[(size_t)chain * n + i] = ui;
+    s = tc[i] * ui;
+  }
+  s = warp_sum(s);
+  __shared__ double red[kGatherThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = s;
+  __syncthreads();
+  if (wid == 0) {
+    s = lane < kGatherThreads / 32 ? red[lane] : 0.0;
+    s = warp_sum(s);
+    if (lane == 0) {
+      partials[2 * ((size_t)chain * row + first + blockIdx.x) + 0] = 0.0;
+      partials[2 * ((size_t)chain * row + first + blockIdx.x) + 1] = s;
     }
   }
 }
@@ -166,7 +201,7 @@ __global__ void force_off_kernel(const T *__restrict__ field, size_t chain_elems
                                  const uint32_t *__restrict__ oidx, const double *__restrict__ ow,
                                  const double *__restrict__ og, const double *__restrict__ q,
                                  int64_t n, const double *__restrict__ Qc,
-                                 double *__restrict__ fsum) {
+                                 const double *__restrict__ u, double *__restrict__ fsum) {
   const int chain = blockIdx.y;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -180,7 +215,9 @@ __global__ void force_off_kernel(const T *__restrict__ field, size_t chain_elems
     gy += og[3 * (8 * i + c) + 1] * v;
     gz += og[3 * (8 * i + c) + 2] * v;
   }
-  const double a = -2.0 * q[i] * (Qc[chain] - q[i] * p);
+  // near pairs (u) are left out of the sample's energy, so of its derivative
+  const double un = u ? u[(size_t)chain * n + i] : 0.0;
+  const double a = -2.0 * q[i] * (Qc[chain] - q[i] * p - un);
   double *o = fsum + 3 * ((size_t)chain * n + i);
   o[0] += a * gx;
   o[1] += a * gy;
@@ -250,28 +287,41 @@ __global__ void finalize_sets_kernel(const SetTable t, int n_chains, int *err) {
 
 cudaError_t launch_gather_off(const Geometry &g, const void *field, const uint32_t *oidx,
                               const double *ow, const double *q, int64_t n, double *partials,
-                              int nblk, cudaStream_t s) {
+                              int nblk, int row, double *tout, cudaStream_t s) {
   dim3 grid(nblk, g.n_chains);
   if (g.precision == COULPS_F32)
     gather_off_kernel<float><<<grid, kGatherThreads, 0, s>>>(
-        reinterpret_cast<const float *>(field), g.chain_elems, oidx, ow, q, n, partials, nblk);
+        reinterpret_cast<const float *>(field), g.chain_elems, oidx, ow, q, n, partials, nblk,
+        row, tout);
   else
     gather_off_kernel<double><<<grid, kGatherThreads, 0, s>>>(
-        reinterpret_cast<const double *>(field), g.chain_elems, oidx, ow, q, n, partials, nblk);
+        reinterpret_cast<const double *>(field), g.chain_elems, oidx, ow, q, n, partials, nblk,
+        row, tout);
+  return cudaGetLastError();
+}
+
+int near_blocks(int64_t n) { return (int)((n + kGatherThreads - 1) / kGatherThreads); }
+
+cudaError_t launch_near(const double *t, const int64_t *nptr, const uint32_t *nbr, int64_t n,
+                        int n_chains, double *u, double *partials, int row, int first,
+                        cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  dim3 grid(near_blocks(n), n_chains);
+  near_kernel<<<grid, kGatherThreads, 0, s>>>(t, nptr, nbr, n, u, partials, row, first);
   return cudaGetLastError();
 }
 
 cudaError_t launch_force_off(const Geometry &g, const void *field, const uint32_t *oidx,
                              const double *ow, const double *og, const double *q, int64_t n,
-                             const double *Qc, double *fsum, cudaStream_t s) {
+                             const double *Qc, const double *u, double *fsum, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   dim3 grid((unsigned)((n + 127) / 128), g.n_chains);
   if (g.precision == COULPS_F32)
     force_off_kernel<float><<<grid, 128, 0, s>>>(reinterpret_cast<const float *>(field),
-                                                  g.chain_elems, oidx, ow, og, q, n, Qc, fsum);
+                                                  g.chain_elems, oidx, ow, og, q, n, Qc, u, fsum);
   else
     force_off_kernel<double><<<grid, 128, 0, s>>>(reinterpret_cast<const double *>(field),
-                                                   g.chain_elems, oidx, ow, og, q, n, Qc, fsum);
+                                                   g.chain_elems, oidx, ow, og, q, n, Qc, u, fsum);
   return cudaGetLastError();
 }
 

@@ -145,3 +145,107 @@ def test_off_lattice_rejects_bad_input(cl, stream):
     e.close()
     flat.close()
     lat.close()
+
+
+@pytest.mark.parametrize("L,n,rc,path", [((13, 7, 5), 30, 2.5, "run"), ((9, 8, 17), 60, 1.7, "measure"),
+                                         ((5, 4, 3), 6, 1e9, "run")])
+def test_near_correction_matches_oracle(cl, stream, orc, L, n, rc, path):
+    """Near pairs found on the host (cell grid) = the oracle's brute-force
+    set; direct energy and forces; per-sample (Q, P + s_N, e_far) and far
+    force sums equal to the oracle's on the oracle chain's fields."""
+    from oracle import offlattice as off
+    from paper_1403_0711_gb300 import inputs
+    pos, q = inputs.off_lattice(L, n, seed=n)
+    pairs = off.near_pairs(pos, rc)
+    n_chains, n_therm, n_meas, n_hb, n_or, seed = 2, 2, 4, 1, 1, 21
+    lat = cl.Lattice(L, n_chains=n_chains, precision=cl.F64, seed=seed, stream=stream)
+    ch = cl.Charges.off_lattice(lat, pos, q, log_capacity=n_meas, forces=True)
+    info = ch.near(rc)
+    assert info["n_pairs"] == len(pairs) > 0
+    ed = off.near_direct_energy(pos, q, pairs)
+    assert abs(info["e_direct"] - ed) < 1e-12 * max(1.0, abs(ed))
+    fd = off.near_direct_forces(pos, q, pairs)
+    assert np.abs(info["f_direct"] - fd).max() < 1e-12 * max(1.0, np.abs(fd).max())
+    if path == "run":
+        ch.run(n_therm, n_meas, n_hb, n_or)
+    else:
+        lat.sweep(n_therm, n_hb, n_or)
+        for _ in range(n_meas):
+            lat.sweep(1, n_hb, n_or)
+            ch.measure()
+    s = ch.samples()
+    fsum = np.zeros((n, 3))
+    for k in range(n_chains):
+        c = orc.Chain(L, seed=seed, chain=k)
+        c.run(n_therm, n_hb, n_or)
+        ref = []
+        for _ in range(n_meas):
+            c.run(1, n_hb, n_or)
+            ref.append(off.near_sample(c.phi, L, pos, q, pairs))
+            fsum += off.near_force_sample(c.phi, L, pos, q, pairs)
+        ref = np.array(ref)
+        den = ref[:, 0] ** 2 + np.abs(ref[:, 1]) + 1e-300
+        assert np.abs(s[:, k, 0] - ref[:, 0]).max() < TOL64 * np.sqrt(den).max()
+        assert (np.abs(s[:, k, 1:] - ref[:, 1:]) / den[:, None]).max() < TOL64
+    mean, _ = ch.forces()
+    want = fsum / (n_chains * n_meas)
+    # (all pairs near: the force is 0 up to rounding of O(1) terms)
+    assert np.abs(mean - want).max() < 1e-11 * (np.abs(want).max() + 1e-3)
+    if rc > 100:  # every pair near: e_far vanishes identically
+        assert np.abs(s[:, :, 2]).max() < 1e-12 * (s[:, :, 0] ** 2).max()
+    ch.close()
+    lat.close()
+
+
+def test_near_correction_off_again_is_bitwise_plain(cl, stream):
+    from paper_1403_0711_gb300 import inputs
+    L = (12, 10, 9)
+    pos, q = inputs.off_lattice(L, 50, seed=4)
+    out = []
+    for near in (False, True):
+        lat = cl.Lattice(L, n_chains=3, precision=cl.F32, seed=8, stream=stream)
+        ch = cl.Charges.off_lattice(lat, pos, q, log_capacity=6, forces=True)
+        if near:
+            assert ch.near(2.0)["n_pairs"] > 0
+            ch.run(1, 3, 1, 1)
+            assert ch.near(0.0)["n_pairs"] == 0
+            assert ch.estimate()["n"] == 0
+            ch.close()
+            lat.close()
+            lat = cl.Lattice(L, n_chains=3, precision=cl.F32, seed=8, stream=stream)
+            ch = cl.Charges.off_lattice(lat, pos, q, log_capacity=6, forces=True)
+            ch.near(2.0)
+            ch.near(0.0)
+        ch.run(2, 6, 1, 2)
+        out.append((ch.samples(), ch.forces()[0]))
+        ch.close()
+        lat.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+
+
+def test_near_far_mean_matches_exact(cl, stream, orc):
+    """8 x 7 x 6 box, 6 particles, near pairs within 2.2: pooled mean of e_far
+    against the exact far lattice energy and far forces against their exact
+    values, within 5 standard errors."""
+    from oracle import offlattice as off
+    L = (8, 7, 6)
+    pos = np.array([[2.3, 3.1, 2.7], [4.6, 3.4, 2.2], [3.5, 1.2, 3.9], [5.2, 5.5, 1.4],
+                    [3.1, 3.9, 3.3], [6.0, 2.5, 4.1]])
+    q = np.array([1.0, -1.0, 0.7, -0.4, 0.9, -0.6])
+    pairs = off.near_pairs(pos, 2.2)
+    assert 0 < len(pairs) < 15
+    G = orc.green_dense(L)
+    E = off.far_energy_exact(G, L, pos, q, pairs)
+    F = off.far_force_exact(G, L, pos, q, pairs)
+    lat = cl.Lattice(L, n_chains=256, precision=cl.F32, seed=78, stream=stream)
+    ch = cl.Charges.off_lattice(lat, pos, q, forces=True)
+    info = ch.near(2.2)
+    assert info["n_pairs"] == len(pairs)
+    ch.run(100, 2000, 1, 1)
+    est = ch.estimate()
+    mean, err = ch.forces()
+    ch.close()
+    lat.close()
+    assert abs(est["mean"] - E) < 5 * est["stderr"], (est, E)
+    assert (np.abs(mean - F) / err).max() < 5, (mean, F, err)
