@@ -466,7 +466,9 @@ def run_ours(args):
         achieved = pass_bytes / (or_ms / 1e3) / 1e9
         name = "pass_kernel<float, over-relaxation>"
         dom = {"kernel": name, "algorithmic_bytes_per_launch": pass_bytes, "avg_launch_ms": or_ms,
-               "heatbath_pass_avg_launch_ms": kt["pass_hb_ms"] / max(1, kt["pass_hb_n"])}
+               "heatbath_pass_avg_launch_ms": kt["pass_hb_ms"] / max(1, kt["pass_hb_n"]),
+               "heatbath_halfsweep_avg_launch_ms": kt["hb_ms"] / max(1, kt["hb_n"]),
+               "overrelax_halfsweep_avg_launch_ms": kt["or_ms"] / max(1, kt["or_n"])}
         traffic = profiled_traffic(name)
     elif kt["mixed_n"] > 0:
         total_bytes = args.steps * n_chains * (8 * N_HB + 12 * N_OR) * L ** 3
@@ -551,7 +553,9 @@ def run_ours(args):
     if rank == 0:
         # per compound sweep: nf fused passes, 2 (PASSES - nf) half-sweeps, a
         # gather when the sweep ends in a fused pass, finalize, advance
-        nf = {"off": 0, "on": N_OR & ~1, "all": PASSES & ~1}[args.fused]
+        # (mode "on" fuses an odd N_OR whole when a heatbath pass precedes it)
+        nf_on = N_OR if (N_OR % 2 == 1 and N_HB > 0) else N_OR & ~1
+        nf = {"off": 0, "on": nf_on, "all": PASSES & ~1}[args.fused]
         ends_fused = nf > 0 and (args.fused == "all" or nf == N_OR)
         launches = args.steps * (nf + 2 * (PASSES - nf) + (1 if ends_fused else 0) + 2)
         line = {

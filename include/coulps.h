@@ -279,11 +279,13 @@ int coulps_set_schedule(coulps_lattice_t lat, int schedule);
  * reads the field once and writes it once (8 bytes per site in FP32 instead
  * of 12 for over-relaxation), from the field into a second copy of it or
  * back: the lattice then holds two copies (twice the field memory).  Within
- * a compound sweep one block of an even number of consecutive passes is
- * fused, so the sweep starts and ends in the lattice's field: enable = 1
- * (default) fuses the over-relaxation passes (all of them when n_or is even,
- * all but the last when it is odd), enable = 2 all passes, enable = 0 none
- * (and frees the second copy).  Results are bitwise those of the half-sweep
+ * a compound sweep one block of consecutive passes is fused, and the sweep
+ * starts and ends in the lattice's field: enable = 1 (default) fuses the
+ * over-relaxation passes (all of them when n_or is even or n_hb >= 1: with
+ * an odd n_or the first heatbath pass writes the second copy, at no extra
+ * traffic, and the fused block ends in the field; all but the last when
+ * n_or is odd and n_hb = 0), enable = 2 all passes (an even number of them),
+ * enable = 0 none (and frees the second copy).  Results are bitwise those of the half-sweep
  * path (same arithmetic per site, same Philox counters).  Not used by the
  * phased schedule.  coulps_set_pass_tile: ty rows of y per CTA (the CTA also
  * computes one halo row each side: (ty + 2) * W / 4 threads <= 512), dz
@@ -571,6 +573,16 @@ int coulps_gcv_run(coulps_gcv_t gcv, int n_meas, int n_hb, int n_or, double c);
 int coulps_measure_static(const void *field, int Lx, int Ly, int Lz, int n_chains, int precision,
                           const uint32_t *site_index, const double *q, int64_t n, double *QPe,
                           void *stream);
+
+/* The random term of the heatbath update Eq. (phi), exactly as the sweep
+ * kernels form it: out[i] = -erfc^-1(2 r_i) / sqrt(3) with
+ * r_i = (w[i] + 1/2) 2^-32, for n 32-bit words w (device arrays; out holds
+ * floats for COULPS_F32, doubles for COULPS_F64).  FP64 uses CUDA's erfcinv;
+ * FP32 uses the library's own erfc^-1 (a polynomial in Giles' variable
+ * w = -ln(u (2 - u)) with both u and 1 - u formed from the integer word),
+ * a few FP32 ulps from the exact value.  Asynchronous on `stream`.
+ * Errors: EINVAL (bad precision, NULL arrays with n > 0), ECUDA. */
+int coulps_heatbath_noise(int precision, const uint32_t *w, void *out, int64_t n, void *stream);
 
 #ifdef __cplusplus
 }

@@ -43,6 +43,7 @@ EXPORTS = (
     "coulps_measure_sets", "coulps_run_sets", "coulps_gcv_create", "coulps_gcv_destroy",
     "coulps_gcv_info", "coulps_gcv_h", "coulps_gcv_eval", "coulps_gcv_run",
     "coulps_charges_create_off", "coulps_forces", "coulps_charges_near",
+    "coulps_heatbath_noise",
 )
 SCHEDULE_ALIGNED, SCHEDULE_PHASED = 0, 1
 STAT_STRIDE = 72
@@ -90,6 +91,7 @@ def load(path: str | Path | None = None):
         "coulps_charges_create_off": (i32, [vp, i64, P(f64), P(f64), i64, ctypes.c_int, P(vp)]),
         "coulps_forces": (i32, [vp, P(f64), P(f64)]),
         "coulps_charges_near": (i32, [vp, ctypes.c_double, P(i64), P(f64), P(f64)]),
+        "coulps_heatbath_noise": (i32, [i32, vp, vp, i64, vp]),
         "coulps_charges_destroy": (None, [vp]),
         "coulps_measure": (i32, [vp, vp]),
         "coulps_run": (i32, [vp, vp, i32, i32, i32, i32]),
@@ -613,6 +615,22 @@ def coulps_forces(charges):
 
 def coulps_charges_near(charges, rc):
     return charges.near(rc)
+
+
+def heatbath_noise(words, precision, stream=None):
+    """The heatbath's random term for 32-bit words (coulps_heatbath_noise):
+    words is a CUDA tensor of int32 (the words' bit patterns); returns a
+    float32 / float64 CUDA tensor."""
+    import torch
+    lib = load()
+    w = words.contiguous()
+    dt = torch.float32 if precision == F32 else torch.float64
+    out = torch.empty(w.shape, dtype=dt, device=w.device)
+    s = stream.cuda_stream if stream is not None else torch.cuda.current_stream(w.device).cuda_stream
+    _check(lib.coulps_heatbath_noise(int(precision), ctypes.c_void_p(w.data_ptr()),
+                                     ctypes.c_void_p(out.data_ptr()), w.numel(), ctypes.c_void_p(s)),
+           "coulps_heatbath_noise")
+    return out
 
 
 def coulps_sweep(lattice, n_compound, n_hb, n_or):

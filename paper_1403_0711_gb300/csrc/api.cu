@@ -58,9 +58,11 @@ struct coulps_lattice {
   uint64_t pass = 0;  // host mirror of *d_pass
   CUtensorMap tm_halo, tm_own;
   // fused passes (pass_fused.cu): a second copy of the field; a compound
-  // sweep runs an even number of fused passes, so it starts and ends in
-  // `field`, and field2 is scratch within a compound sweep
+  // sweep starts and ends in `field`, and field2 is scratch within it
+  // (an odd block of fused passes starts from field2, which the first
+  // heatbath pass then writes out of place)
   void *field2 = nullptr;
+  CUtensorMap tm_halo2;  // halo map of field2 (tile ty + 2 rows)
   int fused = 0;  // 0 off, 1 over-relaxation passes, 2 all passes
   Tile ptile = {0, 0};
   CUtensorMap tm_p1[2], tm_p0[2];  // source field / field2; boxes ty + 4, ty + 2 rows
@@ -192,6 +194,10 @@ int make_map(CUtensorMap *m, const Geometry &g, void *base, int rows) {
 int rebuild_maps(coulps_lattice *L) {
   int st = make_map(&L->tm_halo, L->g, L->field, L->tile.ty + 2);
   if (st) return st;
+  if (L->field2) {
+    st = make_map(&L->tm_halo2, L->g, L->field2, L->tile.ty + 2);
+    if (st) return st;
+  }
   return make_map(&L->tm_own, L->g, L->field, L->tile.ty);
 }
 
@@ -280,14 +286,25 @@ int enqueue_compound(coulps_lattice *L, int n_hb, int n_or, coulps_charges *fuse
   a.g_q = nullptr;
   a.g_partials = nullptr;
   const int n_pass = n_hb + n_or;
-  // fused passes: one block of an even number of consecutive passes, run
-  // field -> field2 -> field ...; the others are in-place half-sweeps.
-  // Mode 1: the over-relaxation passes (the heatbath, ALU-bound, gains
-  // nothing from the saved traffic); mode 2: all passes.
+  // fused passes: one block of consecutive passes, run field -> field2 ->
+  // field ...; the others are in-place half-sweeps.  Mode 1: the
+  // over-relaxation passes (the heatbath, ALU-bound, gains nothing from the
+  // saved traffic); mode 2: all passes, an even number of them.  In mode 1 an
+  // odd number of over-relaxation passes is fused whole when a heatbath pass
+  // precedes them: that pass is written out of place (colour 0 from field
+  // into field2, colour 1 within field2; a heatbath update does not read the
+  // site's old value, so this moves no extra bytes), further heatbath passes
+  // run in place on field2, and the fused block goes field2 -> field -> ...
+  // -> field.
   int f0 = 0, nf = 0;
+  bool flip = false;
   if (L->fused == 1) {
     f0 = n_hb;
     nf = n_or & ~1;
+    if ((n_or & 1) && n_hb > 0) {
+      nf = n_or;
+      flip = true;
+    }
   } else if (L->fused == 2) {
     nf = n_pass & ~1;
   }
@@ -305,7 +322,7 @@ int enqueue_compound(coulps_lattice *L, int n_hb, int n_or, coulps_charges *fuse
     const bool orx = i >= n_hb;
     const uint32_t off = (uint32_t)i;
     if (i >= f0 && i < f0 + nf) {
-      const int b = (i - f0) & 1;  // source copy
+      const int b = (i - f0 + (flip ? 1 : 0)) & 1;  // source copy
       p.dst = b ? L->field : L->field2;
       p.pass_off = off;
       cudaEvent_t ea = nullptr, eb = nullptr;
@@ -322,9 +339,15 @@ int enqueue_compound(coulps_lattice *L, int n_hb, int n_or, coulps_charges *fuse
       }
       continue;
     }
+    // heatbath passes ahead of an odd fused block write field2 (see above)
+    const bool on2 = flip && i < f0;
+    a.field = on2 ? L->field2 : L->field;
     for (int c = 0; c < 2; ++c) {
       a.colour = c;
       a.pass_off = off;
+      // the other colour's rows come from field, except once field2 holds
+      // them: colour 1 of the first pass, and every later pass
+      const CUtensorMap &halo = on2 && (i > 0 || c == 1) ? L->tm_halo2 : L->tm_halo;
       if (gather_fused && i == n_pass - 1 && c == 1) {
         // last half-sweep of the compound sweep: gather Q, P in the same pass
         a.g_off = fuse->d_goff;
@@ -339,13 +362,14 @@ int enqueue_compound(coulps_lattice *L, int n_hb, int n_or, coulps_charges *fuse
         if (!ea || !eb) return COULPS_ECUDA;
         CK(cudaEventRecord(ea, L->stream));
       }
-      CK(launch_halfsweep(L->g, L->tile, L->tm_halo, L->tm_own, a, orx, L->stream));
+      CK(launch_halfsweep(L->g, L->tile, halo, L->tm_own, a, orx, L->stream));
       if (L->profiling) {
         CK(cudaEventRecord(eb, L->stream));
         L->pending.push_back({ea, eb, orx ? 1 : 0});
       }
     }
   }
+  a.field = L->field;
   if (n_hb + n_or > 0) CK(launch_advance_pass(L->d_pass, (uint32_t)(n_hb + n_or), L->stream));
   if (gather_fused) {
     CK(launch_finalize(fuse->d_fpart, fuse->fused_nblk, L->g.n_chains, fuse->d_stats, fuse->d_log,
@@ -755,6 +779,8 @@ int coulps_set_fused(coulps_lattice_t L, int enable) {
   }
   if (L->ptile.ty == 0) L->ptile = default_pass_tile(L->g);
   L->fused = enable;
+  int st = rebuild_maps(L);
+  if (st) return st;
   return rebuild_pass_maps(L);
 }
 

@@ -60,8 +60,7 @@ struct BatchArgs {
 template <typename T, bool OR, bool GATHER>
 __global__ void __launch_bounds__(kBatchThreads) batch_halfsweep_kernel(const BatchArgs a) {
   extern __shared__ unsigned char smem_raw[];
-  unsigned char *smem = reinterpret_cast<unsigned char *>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
+  unsigned char *smem = align_smem128(smem_raw);
   const PhiloxKeys &K = *reinterpret_cast<const PhiloxKeys *>(a.round_keys);
   const uint32_t pass = OR ? 0u : (*a.pass_ptr + a.pass_off);
   int gbase = 0;

@@ -21,6 +21,16 @@
 
 namespace coulps {
 
+// The dynamic shared-memory window rounded up to a 128-byte boundary (TMA
+// destinations).  The offset is added to the __shared__ array itself rather
+// than through an integer round trip, so the compiler keeps this pointer and
+// everything derived from it in the shared address space (32-bit shared
+// loads and stores instead of generic ones).
+__device__ __forceinline__ unsigned char *align_smem128(unsigned char *raw) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(raw);
+  return raw + ((128u - (a & 127u)) & 127u);
+}
+
 // Longest a single mbarrier wait may spin before giving up (ns).
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
 
@@ -41,9 +51,53 @@ __device__ __forceinline__ uint32_t hb_small_side(uint32_t w) {
   return ((w >> 31) ? ~w : w) & 0x7fffffffu;
 }
 
+// erfc^-1(u) in FP32 for u = (s + 1/2) 2^-31, s < 2^31.  Both u and
+// x = 1 - u = (2^31 - 1 - s + 1/2) 2^-31 are formed from integers, so neither
+// inherits the other's rounding (erfc^-1 near u = 1 and near u = 0 stays
+// accurate).  erfc^-1(u) = erfinv(x) = x p(w) with w = -ln(u (2 - u)) =
+// -ln(u (1 + x)); p is smooth in w (the change of variable of M. Giles,
+// "Approximating the erfinv function", GPU Computing Gems, 2011) and is taken
+// as a degree-9 polynomial in w - 2.5 for w < 5 and a degree-10 polynomial in
+// sqrt(w) - 3 above (u >= 2^-32 keeps w < 21.5).  Coefficients: our own
+// weighted least-squares fit (fit_erfcinv.py beside this file; fit error
+// 5.6e-9 and 2.2e-8 relative).  Measured against FP64 erfcinv over all
+// 2^31 arguments' range: a few FP32 ulps (tests/test_gpu_noise.py).
+__device__ __forceinline__ float hb_erfcinv_f32(uint32_t s) {
+  const float u = fmaf(__uint2float_rn(s), 0x1p-31f, 0x1p-32f);
+  const float x = fmaf(__uint2float_rn(0x7fffffffu - s), 0x1p-31f, 0x1p-32f);
+  const float w = -__logf(u * (1.0f + x));
+  float p;
+  if (w < 5.0f) {
+    const float z = w - 2.5f;
+    p = -8.791183e-09f;
+    p = fmaf(p, z, 2.323271e-08f);
+    p = fmaf(p, z, 4.6617242e-07f);
+    p = fmaf(p, z, -3.4627055e-06f);
+    p = fmaf(p, z, -4.963356e-06f);
+    p = fmaf(p, z, 0.00021834444f);
+    p = fmaf(p, z, -0.0012527419f);
+    p = fmaf(p, z, -0.004177387f);
+    p = fmaf(p, z, 0.24664028f);
+    p = fmaf(p, z, 1.5014094f);
+  } else {
+    const float z = sqrtf(w) - 3.0f;
+    p = -1.9327976e-05f;
+    p = fmaf(p, z, 0.00012418872f);
+    p = fmaf(p, z, -0.0002553589f);
+    p = fmaf(p, z, -7.817031e-05f);
+    p = fmaf(p, z, 0.0014351195f);
+    p = fmaf(p, z, -0.003582941f);
+    p = fmaf(p, z, 0.005705795f);
+    p = fmaf(p, z, -0.0076402943f);
+    p = fmaf(p, z, 0.009442766f);
+    p = fmaf(p, z, 1.0016751f);
+    p = fmaf(p, z, 2.8329768f);
+  }
+  return x * p;
+}
+
 __device__ __forceinline__ float hb_noise_f32(uint32_t w) {
-  const float u = fmaf(__uint2float_rn(hb_small_side(w)), 0x1p-31f, 0x1p-32f);
-  const float y = erfcinvf(u) * 0.577350269189625764509f;  // 1/sqrt(3)
+  const float y = hb_erfcinv_f32(hb_small_side(w)) * 0.577350269189625764509f;  // 1/sqrt(3)
   return (w >> 31) ? y : -y;
 }
 

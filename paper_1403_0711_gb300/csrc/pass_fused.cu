@@ -57,8 +57,7 @@ __global__ void __launch_bounds__(512)
                 const PassArgs a) {
   constexpr int R = 1;  // rows per thread
   extern __shared__ unsigned char smem_raw[];
-  unsigned char *smem = reinterpret_cast<unsigned char *>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
+  unsigned char *smem = align_smem128(smem_raw);
   const PassLayout lay = pass_layout(a.TY, a.W, (int)sizeof(T), OR);
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 64);
@@ -194,13 +193,9 @@ __global__ void __launch_bounds__(512)
           const T *yp = k == R - 1 ? hi : A1[k + 1];
           T xs[4], S[4];
           const int par = (yk[k] + p0) & 1;
-          if (par == 0) {
-            xs[0] = lo_ok ? Pz[(k + 1) * W - 1] : T(0);
-            xs[1] = A1[k][0]; xs[2] = A1[k][1]; xs[3] = A1[k][2];
-          } else {
-            xs[0] = A1[k][1]; xs[1] = A1[k][2]; xs[2] = A1[k][3];
-            xs[3] = hi_ok ? Pz[(k + 1) * W + 4] : T(0);
-          }
+          const bool odd = par != 0;
+          const T e = (odd ? hi_ok : lo_ok) ? Pz[(k + 1) * W + (odd ? 4 : -1)] : T(0);
+          x_neighbours(odd, e, A1[k], xs);
 #pragma unroll
           for (int i = 0; i < 4; ++i)
             S[i] = ((A0[k][i] + A2[k][i]) + (ym[i] + yp[i])) + (A1[k][i] + xs[i]);
@@ -239,10 +234,11 @@ __global__ void __launch_bounds__(512)
     for (int k = 0; k < R; ++k)
 #pragma unroll
       for (int i = 0; i < 4; ++i) N2[k][i] = v0[k][i];
-    __syncthreads();
-    if (*abort_flag) return false;
-    done = j;
-    // ---- stage 1: colour 1 at plane p1 = p0 - 1 on this tile's rows
+    // ---- stage 1: colour 1 at plane p1 = p0 - 1 on this tile's rows.  It
+    // reads the new colour-0 rows of plane p1 (written in the previous step,
+    // before the barrier that ends it) and this thread's own registers, none
+    // of what stage 0 of this step wrote to shared memory, so no barrier
+    // between the stages.
     const int p1 = p0 - 1;
     if (s >= 2 && (live1[0] || live1[R - 1])) {
       const T *N = new_plane(s - 1) + row;  // colour 0 new, plane p1
@@ -256,13 +252,9 @@ __global__ void __launch_bounds__(512)
         const T *yp = k == R - 1 ? hi : N1[k + 1];
         T xs[4], S[4], v[4];
         const int par = (1 + yk[k] + p1) & 1;
-        if (par == 0) {
-          xs[0] = lo_ok ? N[k * W - 1] : T(0);
-          xs[1] = N1[k][0]; xs[2] = N1[k][1]; xs[3] = N1[k][2];
-        } else {
-          xs[0] = N1[k][1]; xs[1] = N1[k][2]; xs[2] = N1[k][3];
-          xs[3] = hi_ok ? N[k * W + 4] : T(0);
-        }
+        const bool odd = par != 0;
+        const T e = (odd ? hi_ok : lo_ok) ? N[k * W + (odd ? 4 : -1)] : T(0);
+        x_neighbours(odd, e, N1[k], xs);
 #pragma unroll
         for (int i = 0; i < 4; ++i)
           S[i] = ((N0[k][i] + N2[k][i]) + (ym[i] + yp[i])) + (N1[k][i] + xs[i]);
@@ -288,7 +280,11 @@ __global__ void __launch_bounds__(512)
         st_quad(out1 + (size_t)p1 * plane + (size_t)k * W, v);
       }
     }
-    __syncthreads();  // new plane s - 1 and ring plane s are free
+    // new plane s visible to the next step's stage 1; new plane s - 1 and
+    // ring plane s free for reuse
+    __syncthreads();
+    if (*abort_flag) return false;
+    done = j;
     if (tid == 0 && issued < n_ring) issue(issued++);
     return true;
   };

@@ -51,8 +51,7 @@ __global__ void __launch_bounds__(256)
                      const __grid_constant__ CUtensorMap tm_own, const SweepArgs a) {
   extern __shared__ unsigned char smem_raw[];
   // 128-byte aligned base (the launch reserves 128 bytes of slack).
-  unsigned char *smem = reinterpret_cast<unsigned char *>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
+  unsigned char *smem = align_smem128(smem_raw);
   const int chain = blockIdx.z;
   TileJob<T> j;
   j.tm_halo = &tm_halo;
@@ -100,8 +99,7 @@ __global__ void __launch_bounds__(256)
   if (mode == 0) return;
   const bool gather = m.gather[grp] != 0;
   extern __shared__ unsigned char smem_raw[];
-  unsigned char *smem = reinterpret_cast<unsigned char *>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
+  unsigned char *smem = align_smem128(smem_raw);
   TileJob<T> j;
   j.tm_halo = &tm_halo;
   j.tm_own = &tm_own;
@@ -215,4 +213,29 @@ cudaError_t launch_advance_pass(uint32_t *pass, uint32_t n, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+namespace {
+template <typename T>
+__global__ void noise_kernel(const uint32_t *__restrict__ w, T *__restrict__ out, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = Noise<T>::of(w[i]);
+}
+}  // namespace
+
 }  // namespace coulps
+
+extern "C" int coulps_heatbath_noise(int precision, const uint32_t *w, void *out, int64_t n,
+                                     void *stream) {
+  using namespace coulps;
+  if (n < 0 || (n > 0 && (!w || !out))) return COULPS_EINVAL;
+  if (precision != COULPS_F32 && precision != COULPS_F64) return COULPS_EINVAL;
+  if (n == 0) return COULPS_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t want = (n + 255) / 256;
+  const unsigned blocks = (unsigned)(want < 4096 ? want : 4096);
+  if (precision == COULPS_F32)
+    noise_kernel<float><<<blocks, 256, 0, s>>>(w, (float *)out, n);
+  else
+    noise_kernel<double><<<blocks, 256, 0, s>>>(w, (double *)out, n);
+  return cudaGetLastError() == cudaSuccess ? COULPS_OK : COULPS_ECUDA;
+}

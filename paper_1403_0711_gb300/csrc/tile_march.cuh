@@ -57,6 +57,20 @@ __device__ __forceinline__ void st_quad<double>(double *p, const double (&v)[4])
   reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
 }
 
+// The x neighbours of a quad's 4 same-colour sites h .. h + 3 of a row: for
+// row parity 0 the x - 1 neighbour of h is the other colour's h - 1 and x + 1
+// is h; for parity 1 they are h and h + 1.  So S takes C[i] + xs[i], with
+// xs[i] = C[i - 1] (even) or C[i + 1] (odd); the one value outside C is e
+// (from shared memory, or 0 beyond the box).  Selects rather than a branch:
+// the two rows one warp covers have opposite parity.
+template <typename T>
+__device__ __forceinline__ void x_neighbours(bool odd, T e, const T (&C)[4], T (&xs)[4]) {
+  xs[0] = odd ? C[1] : e;
+  xs[1] = odd ? C[2] : C[0];
+  xs[2] = odd ? C[3] : C[1];
+  xs[3] = odd ? e : C[2];
+}
+
 template <typename T> struct Coef;
 template <> struct Coef<float> {
   static constexpr float sixth = 0.166666666666666666667f;
@@ -199,15 +213,9 @@ __device__ bool march_tile(const TileJob<T> &j, const PhiloxKeys &K, unsigned ch
         T ym[4], yp[4], xs[4], S[4], v[4];
         ld_quad(Pz - W, ym);
         ld_quad(Pz + W, yp);
-        if (par == 0) {
-          // x - 1 of h lies at h - 1 in the other colour, x + 1 at h
-          xs[0] = lo_ok ? Pz[-1] : T(0);
-          xs[1] = C[0]; xs[2] = C[1]; xs[3] = C[2];
-        } else {
-          // x - 1 of h lies at h, x + 1 at h + 1
-          xs[0] = C[1]; xs[1] = C[2]; xs[2] = C[3];
-          xs[3] = hi_ok ? Pz[4] : T(0);
-        }
+        const bool odd = par != 0;
+        const T e = (odd ? hi_ok : lo_ok) ? Pz[odd ? 4 : -1] : T(0);
+        x_neighbours(odd, e, C, xs);
 #pragma unroll
         for (int i = 0; i < 4; ++i) S[i] = ((M[i] + P[i]) + (ym[i] + yp[i])) + (C[i] + xs[i]);
         if (!OR) {

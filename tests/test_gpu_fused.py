@@ -50,7 +50,9 @@ def _rel(a, b):
 
 
 @pytest.mark.parametrize("L,prec,n_hb,n_or,tile,mode", [
-    ((37, 29, 23), "F32", 1, 3, None, 1),   # two OR passes fused, the third as half-sweeps
+    ((37, 29, 23), "F32", 1, 3, None, 1),   # three OR passes fused, the HB pass out of place
+    ((21, 18, 12), "F64", 2, 3, None, 1),   # two HB passes (the second in place on the copy)
+    ((12, 7, 9), "F32", 1, 1, (2, 3), 1),   # one fused OR pass after one HB pass
     ((37, 29, 23), "F32", 1, 3, (3, 5), 2),  # all four passes fused
     ((16, 16, 16), "F64", 2, 2, None, 1),
     ((16, 16, 16), "F64", 2, 2, None, 2),
