@@ -578,9 +578,9 @@ int coulps_measure_static(const void *field, int Lx, int Ly, int Lz, int n_chain
  * kernels form it: out[i] = -erfc^-1(2 r_i) / sqrt(3) with
  * r_i = (w[i] + 1/2) 2^-32, for n 32-bit words w (device arrays; out holds
  * floats for COULPS_F32, doubles for COULPS_F64).  FP64 uses CUDA's erfcinv;
- * FP32 uses the library's own erfc^-1 (a polynomial in Giles' variable
- * w = -ln(u (2 - u)) with both u and 1 - u formed from the integer word),
- * a few FP32 ulps from the exact value.  Asynchronous on `stream`.
+ * FP32 uses the library's own erfc^-1 (polynomials in Giles' variable, in
+ * base 2: v = -log2(u (2 - u)), with both u and 1 - u formed from the
+ * integer word), a few FP32 ulps from the exact value.  Asynchronous on `stream`.
  * Errors: EINVAL (bad precision, NULL arrays with n > 0), ECUDA. */
 int coulps_heatbath_noise(int precision, const uint32_t *w, void *out, int64_t n, void *stream);
 

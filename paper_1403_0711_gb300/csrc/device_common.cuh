@@ -51,54 +51,53 @@ __device__ __forceinline__ uint32_t hb_small_side(uint32_t w) {
   return ((w >> 31) ? ~w : w) & 0x7fffffffu;
 }
 
-// erfc^-1(u) in FP32 for u = (s + 1/2) 2^-31, s < 2^31.  Both u and
+// The heatbath deviate in FP32: erfc^-1(u) / sqrt(3) for u = (s + 1/2) 2^-31,
+// s < 2^31, with the sign of the word's top bit.  Both u and
 // x = 1 - u = (2^31 - 1 - s + 1/2) 2^-31 are formed from integers, so neither
-// inherits the other's rounding (erfc^-1 near u = 1 and near u = 0 stays
-// accurate).  erfc^-1(u) = erfinv(x) = x p(w) with w = -ln(u (2 - u)) =
-// -ln(u (1 + x)); p is smooth in w (the change of variable of M. Giles,
-// "Approximating the erfinv function", GPU Computing Gems, 2011) and is taken
-// as a degree-9 polynomial in w - 2.5 for w < 5 and a degree-10 polynomial in
-// sqrt(w) - 3 above (u >= 2^-32 keeps w < 21.5).  Coefficients: our own
-// weighted least-squares fit (fit_erfcinv.py beside this file; fit error
-// 5.6e-9 and 2.2e-8 relative).  Measured against FP64 erfcinv over all
-// 2^31 arguments' range: a few FP32 ulps (tests/test_gpu_noise.py).
-__device__ __forceinline__ float hb_erfcinv_f32(uint32_t s) {
+// inherits the other's rounding (accurate near u = 1 and near u = 0).
+// erfc^-1(u) / sqrt(3) = x q(v) with v = -log2(u (2 - u)) = -log2(u + u x);
+// q is smooth in v (the change of variable of M. Giles, "Approximating the
+// erfinv function", GPU Computing Gems, 2011, here in base 2) and is taken
+// as a degree-9 polynomial in v - 3.5 for v < 7 and a degree-10 polynomial in
+// sqrt(v) - 3.6 above (u >= 2^-32 keeps v < 32); 1/sqrt(3) is folded into
+// the coefficients.  Coefficients: our own weighted least-squares fit
+// (fit_erfcinv.py beside this file; fit error 3.6e-9 and 2.9e-8 relative).
+// Measured against FP64 erfc^-1 over the whole range: a few FP32 ulps.
+__device__ __forceinline__ float hb_noise_f32(uint32_t w) {
+  const uint32_t s = hb_small_side(w);
   const float u = fmaf(__uint2float_rn(s), 0x1p-31f, 0x1p-32f);
   const float x = fmaf(__uint2float_rn(0x7fffffffu - s), 0x1p-31f, 0x1p-32f);
-  const float w = -__logf(u * (1.0f + x));
-  float p;
-  if (w < 5.0f) {
-    const float z = w - 2.5f;
-    p = -8.791183e-09f;
-    p = fmaf(p, z, 2.323271e-08f);
-    p = fmaf(p, z, 4.6617242e-07f);
-    p = fmaf(p, z, -3.4627055e-06f);
-    p = fmaf(p, z, -4.963356e-06f);
-    p = fmaf(p, z, 0.00021834444f);
-    p = fmaf(p, z, -0.0012527419f);
-    p = fmaf(p, z, -0.004177387f);
-    p = fmaf(p, z, 0.24664028f);
-    p = fmaf(p, z, 1.5014094f);
+  const float v = -__log2f(fmaf(u, x, u));
+  float q;
+  if (v < 7.0f) {
+    const float z = v - 3.5f;
+    q = -1.9502296e-10f;
+    q = fmaf(q, z, 8.8274743e-10f);
+    q = fmaf(q, z, 2.0195072e-08f);
+    q = fmaf(q, z, -2.3665939e-07f);
+    q = fmaf(q, z, -3.1320127e-07f);
+    q = fmaf(q, z, 2.9303386e-05f);
+    q = fmaf(q, z, -0.00025333301f);
+    q = fmaf(q, z, -0.0010796369f);
+    q = fmaf(q, z, 0.098941647f);
+    q = fmaf(q, z, 0.85629088f);
   } else {
-    const float z = sqrtf(w) - 3.0f;
-    p = -1.9327976e-05f;
-    p = fmaf(p, z, 0.00012418872f);
-    p = fmaf(p, z, -0.0002553589f);
-    p = fmaf(p, z, -7.817031e-05f);
-    p = fmaf(p, z, 0.0014351195f);
-    p = fmaf(p, z, -0.003582941f);
-    p = fmaf(p, z, 0.005705795f);
-    p = fmaf(p, z, -0.0076402943f);
-    p = fmaf(p, z, 0.009442766f);
-    p = fmaf(p, z, 1.0016751f);
-    p = fmaf(p, z, 2.8329768f);
+    const float z = sqrtf(v) - 3.6f;
+    q = -1.7354193e-06f;
+    q = fmaf(q, z, 1.368092e-05f);
+    q = fmaf(q, z, -3.4650988e-05f);
+    q = fmaf(q, z, -1.0538802e-05f);
+    q = fmaf(q, z, 0.00027573694f);
+    q = fmaf(q, z, -0.00083418511f);
+    q = fmaf(q, z, 0.0015974527f);
+    q = fmaf(q, z, -0.0025665793f);
+    q = fmaf(q, z, 0.003804483f);
+    q = fmaf(q, z, 0.48145521f);
+    q = fmaf(q, z, 1.6339988f);
   }
-  return x * p;
-}
-
-__device__ __forceinline__ float hb_noise_f32(uint32_t w) {
-  const float y = hb_erfcinv_f32(hb_small_side(w)) * 0.577350269189625764509f;  // 1/sqrt(3)
-  return (w >> 31) ? y : -y;
+  // w < 2^31 (2r < 1): a negative term; the sign goes onto x (exact)
+  const float xs = __uint_as_float(__float_as_uint(x) | ((~w) & 0x80000000u));
+  return xs * q;
 }
 
 __device__ __forceinline__ double hb_noise_f64(uint32_t w) {
