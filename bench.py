@@ -48,7 +48,6 @@ CONFIG = {
 }
 PROFILE_TRAFFIC = {
     "pass_kernel<float, over-relaxation>": ROOT / "profiles" / "pass_or_128c_64ch.txt",
-    "halfsweep_kernel<float, over-relaxation>": ROOT / "profiles" / "or_halfsweep_128c_64ch.txt",
 }
 KERNEL_SOURCES = ["sweep.cu", "pass_fused.cu", "tile_march.cuh", "device_common.cuh", "internal.h"]
 
