@@ -80,8 +80,10 @@ def parse():
     ap.add_argument("--cv-global", action="store_true",
                     help="also run the whole-lattice control variate on the +-1 system")
     ap.add_argument("--workload", choices=["chains128", "large512", "sweep", "batched", "cv", "cube",
-                                           "cv_eval", "paper", "gcv"],
+                                           "cv_eval", "paper", "gcv", "offlattice"],
                     default="chains128", help="secondary workloads print their own line")
+    ap.add_argument("--off-seconds", type=float, default=120.0,
+                    help="sampling time limit of the off-lattice workload")
     ap.add_argument("--chains", type=int, default=N_CHAINS,
                     help="chains per GPU (smaller values only for profiler captures)")
     return ap.parse_args()
@@ -644,6 +646,8 @@ def run_extra(args):
         results.extend(cv_experiment(args, stream))
     elif args.workload == "cube":
         results.append(cube_time_to_accuracy(args, stream))
+    elif args.workload == "offlattice":
+        results.append(offlattice_cube(args, stream))
     print(json.dumps({"workload": args.workload, "metric": METRIC, "results": results}), flush=True)
 
 
@@ -897,6 +901,92 @@ def cube_time_to_accuracy(args, stream):
          "delta": abs(est["mean"] - e_lat) / abs(e_lat),
          "reached_1e-3": bool(est["stderr"] <= 1e-3 * abs(e_lat))}
     ch.close()
+    lat.close()
+    return r
+
+
+def golden_offlattice(name):
+    """Exact energies of the off-lattice cube (tests/golden/offlattice.txt,
+    written by tests/golden/make_golden.py from the FP64 oracle)."""
+    keys = ["n_pairs", "e_far", "e_direct", "e_plain", "continuum"]
+    for ln in (ROOT / "tests" / "golden" / "offlattice.txt").read_text().splitlines():
+        if ln.startswith(name + " "):
+            v = ln.split()
+            return dict(zip(keys, [int(v[8])] + [float(x) for x in v[9:13]]))
+    return None
+
+
+def offlattice_cube(args, stream):
+    """The paper's closing remarks on the Fig. 2 cube: the 8 charges q = 1
+    moved off their sites (uniform offsets in [-0.3, 0.3] per axis) and read
+    through trilinear weights, with forces, and with the pairs closer than
+    r_c = 1.5 computed directly (continuum Eq. (s1) terms).  Both estimators
+    (near pairs left out, and plain interpolated lattice) are measured on the
+    same samples, with forces, until the near-field estimate's error reaches
+    1e-3 of the total or --off-seconds; reported against the oracle's exact
+    values."""
+    import numpy as np
+    import torch
+
+    from paper_1403_0711_gb300 import coulps, inputs
+    box = (L, L, L)
+    pos, q = inputs.off_lattice_cube(box, 2, 0, 0.3)
+    gold = golden_offlattice("offcube_128c_n8_q1")
+    rc = 1.5
+    lat = coulps.Lattice(box, n_chains=N_CHAINS, precision=coulps.F32, seed=123, stream=stream)
+    near = coulps.Charges.off_lattice(lat, pos, q, forces=True)
+    plain = coulps.Charges.off_lattice(lat, pos, q, forces=True)
+    info = near.near(rc)
+    lat.sweep(300, N_HB, N_OR)
+    # cost of a measured compound sweep with both sets against the sweep alone
+    coulps.run_sets(lat, [near, plain], 0, 50, N_HB, N_OR)
+    lat.sweep(50, N_HB, N_OR)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record(stream)
+    lat.sweep(200, N_HB, N_OR)
+    ev[1].record(stream)
+    coulps.run_sets(lat, [near, plain], 0, 200, N_HB, N_OR)
+    ev[2].record(stream)
+    torch.cuda.synchronize()
+    ms_sweep = ev[0].elapsed_time(ev[1]) / 200
+    ms_meas = ev[1].elapsed_time(ev[2]) / 200
+    near.reset_stats()
+    plain.reset_stats()
+    e_total = gold["e_far"] + info["e_direct"]
+    t0 = time.perf_counter()
+    est = None
+    while time.perf_counter() - t0 < args.off_seconds:
+        coulps.run_sets(lat, [near, plain], 0, 500, N_HB, N_OR)
+        est = near.estimate()
+        if est["stderr"] == est["stderr"] and est["stderr"] <= 1e-3 * abs(e_total) and \
+                est["n"] > N_CHAINS * 2000:
+            break
+    wall = time.perf_counter() - t0
+    est_p = plain.estimate()
+    f_near, f_err = near.forces()
+    f_tot = f_near + info["f_direct"]
+    r = {"system": "off-lattice cube, 8 charges q=1 (jitter 0.3), 128^3, 64 chains",
+         "r_c": rc, "near_pairs": info["n_pairs"], "golden_pairs": gold["n_pairs"],
+         "ms_per_compound_sweep": ms_sweep,
+         "ms_per_compound_sweep_with_two_offlattice_sets_and_forces": ms_meas,
+         "wall_s": wall, "samples": est["n"], "tau_int": est["tau_int"],
+         "near": {"mean_far": est["mean"], "stderr": est["stderr"], "exact_far": gold["e_far"],
+                  "e_direct": info["e_direct"], "total": est["mean"] + info["e_direct"],
+                  "delta_vs_exact_total": abs(est["mean"] - gold["e_far"]) / abs(e_total),
+                  "rel_stderr": est["stderr"] / abs(e_total)},
+         "plain": {"mean": est_p["mean"], "stderr": est_p["stderr"], "exact": gold["e_plain"],
+                   "delta": abs(est_p["mean"] - gold["e_plain"]) / abs(gold["e_plain"])},
+         "continuum_Eq_s1": gold["continuum"],
+         "gap_to_continuum": {"plain_lattice": abs(gold["e_plain"] - gold["continuum"])
+                              / gold["continuum"],
+                              "near_field_corrected": abs(e_total - gold["continuum"])
+                              / gold["continuum"]},
+         "forces": {"max_abs": float(np.abs(f_tot).max()),
+                    "max_stderr": float(np.abs(f_err).max()),
+                    "net_force_norm": float(np.linalg.norm(f_tot.sum(axis=0)))}}
+    for c in (near, plain):
+        c.close()
     lat.close()
     return r
 

@@ -187,3 +187,47 @@ def far_force_exact(G, L, pos, q, pairs):
     for i, j in pairs:
         mask[i, j] = mask[j, i] = 0.0
     return -2.0 * q[:, None] * np.einsum("ijm,j,ij->im", dGt, q, mask)
+
+
+def _corner_pairs(L, pos_a, pos_b):
+    """Flattened corner-site pairs and weight products of particle pairs
+    (a_k, b_k): returns sites_a (m*64, 3), sites_b (m*64, 3), weights (m*64,)."""
+    sa, wa, _ = corners(L, pos_a)
+    sb, wb, _ = corners(L, pos_b)
+    m = len(sa)
+    A = np.repeat(sa, 8, axis=1).reshape(m * 64, 3)
+    B = np.tile(sb, (1, 8, 1)).reshape(m * 64, 3)
+    W = (wa[:, :, None] * wb[:, None, :]).reshape(m * 64)
+    return A, B, W
+
+
+def far_energy_solve(L, pos, q, pairs, chunk=2048):
+    """far_energy_exact for large boxes without a dense G:
+        rho~^T G rho~ - sum_i q_i^2 G~(r_i, r_i) - 2 sum_{(i,j) in N} q_i q_j G~(r_i, r_j),
+    rho~ = sum_i q_i w_i (the particles' weights spread on the lattice), G rho~
+    by the oracle's DST-I solve, G~ of particle pairs as weighted sums of
+    lattice G entries by heat-kernel quadrature."""
+    from . import oracle
+    pos = np.asarray(pos, dtype=np.float64).reshape(-1, 3)
+    q = np.asarray(q, dtype=np.float64)
+    Lx, Ly, Lz = L
+    s, w, _ = corners(L, pos)
+    rho = np.zeros((Lz, Ly, Lx))
+    np.add.at(rho, (s[..., 2].ravel(), s[..., 1].ravel(), s[..., 0].ravel()),
+              (q[:, None] * w).ravel())
+    E = float(np.vdot(rho, oracle.solve_dst(rho)))
+
+    def gtilde(ia, ib):
+        out = np.empty(len(ia))
+        for k0 in range(0, len(ia), chunk):
+            a, b = ia[k0:k0 + chunk], ib[k0:k0 + chunk]
+            A, B, W = _corner_pairs(L, pos[a], pos[b])
+            out[k0:k0 + chunk] = (oracle.green_pairs(L, A, B) * W).reshape(len(a), 64).sum(axis=1)
+        return out
+
+    idx = np.arange(len(q))
+    E -= float(np.sum(q * q * gtilde(idx, idx)))
+    pairs = np.asarray(pairs, dtype=np.int64).reshape(-1, 2)
+    if len(pairs):
+        E -= 2.0 * float(np.sum(q[pairs[:, 0]] * q[pairs[:, 1]] * gtilde(pairs[:, 0], pairs[:, 1])))
+    return E

@@ -105,6 +105,16 @@ def off_lattice(L, n, seed, qmax=1.0):
     return pos, q
 
 
+def off_lattice_cube(L, n_side, seed, jitter=0.3, q=1.0):
+    """The paper's Fig. 2 cube of n_side^3 charges q at the centre of the box,
+    each moved off its site by a uniform offset in [-jitter, jitter] per axis
+    (real positions (x, y, z))."""
+    sites, qq = cube(L, n_side, q)
+    rng = _rng(seed)
+    pos = sites.astype(np.float64) + rng.uniform(-jitter, jitter, size=sites.shape)
+    return pos, qq
+
+
 def blobs(L, n, seed, n_blob=200, sigma=6.0, qmax=0.8):
     Lx, Ly, Lz = L
     rng = _rng(seed)

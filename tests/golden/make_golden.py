@@ -1,8 +1,10 @@
 """Write tests/golden/e_lat.txt: exact lattice energies E_lat of the seeded
 workloads, computed by the FP64 oracle only (DST-I spectral solve for G rho,
-heat-kernel quadrature for G_ii; dense Cholesky where the box is small).
+heat-kernel quadrature for G_ii; dense Cholesky where the box is small), and
+tests/golden/offlattice.txt: the off-lattice cube's exact energies (trilinear
+weights, near pairs within r_c left out and their continuum terms).
 
-Run from the repository root:  python tests/golden/make_golden.py
+Run from the repository root:  python tests/golden/make_golden.py [--offlattice-only]
 """
 import sys
 from pathlib import Path
@@ -10,8 +12,13 @@ from pathlib import Path
 ROOT = Path(__file__).resolve().parents[2]
 sys.path.insert(0, str(ROOT))
 
-from oracle import oracle  # noqa: E402
+from oracle import offlattice, oracle  # noqa: E402
 from paper_1403_0711_gb300 import inputs  # noqa: E402
+
+OFF_CASES = [
+    # name, L, cube side, seed, jitter, r_c
+    ("offcube_128c_n8_q1", (128, 128, 128), 2, 0, 0.3, 1.5),
+]
 
 CASES = [
     # name, L, generator, N, seed, method  (two_body: the seed column holds n_x)
@@ -42,7 +49,28 @@ def charges(gen, L, n, seed):
     raise ValueError(gen)
 
 
+def main_offlattice():
+    lines = ["# name Lx Ly Lz side seed jitter r_c n_pairs E_far E_direct E_plain continuum_Eq_s1",
+             "# E_far: mean of the sample with the near pairs left out; E_direct: their",
+             "# continuum terms; E_plain: the interpolated lattice energy with no pairs left out",
+             "# written by tests/golden/make_golden.py (FP64 oracle only)"]
+    for name, L, side, seed, jitter, rc in OFF_CASES:
+        pos, q = inputs.off_lattice_cube(L, side, seed, jitter)
+        pairs = offlattice.near_pairs(pos, rc)
+        e_far = offlattice.far_energy_solve(L, pos, q, pairs)
+        e_dir = offlattice.near_direct_energy(pos, q, pairs)
+        e_plain = offlattice.far_energy_solve(L, pos, q, pairs[:0])
+        cont = oracle.coulomb_direct(pos, q)
+        lines.append(f"{name} {L[0]} {L[1]} {L[2]} {side} {seed} {jitter} {rc} {len(pairs)} "
+                     f"{e_far:.15e} {e_dir:.15e} {e_plain:.15e} {cont:.15e}")
+        print(lines[-1], flush=True)
+    (Path(__file__).resolve().parent / "offlattice.txt").write_text("\n".join(lines) + "\n")
+
+
 def main():
+    main_offlattice()
+    if "--offlattice-only" in sys.argv:
+        return
     lines = ["# name Lx Ly Lz generator N seed method E_lat continuum_Eq_s1",
              "# written by tests/golden/make_golden.py (FP64 oracle only)"]
     for name, L, gen, n, seed, method in CASES:

@@ -166,3 +166,17 @@ def test_far_estimators_average_to_exact_far_values(orc):
         b[i, mu] -= h
         fd = -(off.far_energy_exact(G, L, a, q, pairs) - off.far_energy_exact(G, L, b, q, pairs)) / (2 * h)
         assert abs(F[i, mu] - fd) < 1e-6 * max(1.0, abs(fd))
+
+
+def test_far_energy_by_solve_equals_dense(orc):
+    """The large-box route (DST solve + heat-kernel quadrature) against the
+    dense-G definition on small boxes, with and without near pairs."""
+    from oracle import offlattice as off
+    for L, n, rc, seed in (((7, 6, 5), 6, 2.0, 14), ((9, 4, 6), 9, 0.0, 15)):
+        pos = _pos(L, n, seed)
+        q = np.random.default_rng(seed).uniform(-1, 1, n)
+        pairs = off.near_pairs(pos, rc)
+        G = orc.green_dense(L)
+        want = off.far_energy_exact(G, L, pos, q, pairs)
+        got = off.far_energy_solve(L, pos, q, pairs)
+        assert abs(got - want) < 1e-10 * max(1.0, abs(want)), (got, want)
