@@ -45,7 +45,7 @@ namespace {
 
 using namespace tile;
 
-template <typename T, bool OR, bool GATHER>
+template <typename T, bool OR, bool GATHER, int V>
 __global__ void __launch_bounds__(256)
     halfsweep_kernel(const __grid_constant__ CUtensorMap tm_halo,
                      const __grid_constant__ CUtensorMap tm_own, const SweepArgs a) {
@@ -77,8 +77,8 @@ __global__ void __launch_bounds__(256)
   double sq = 0.0, sp = 0.0;
   int gbase = 0;
   ring_init(smem);
-  march_tile<T, OR, GATHER>(j, *reinterpret_cast<const PhiloxKeys *>(a.round_keys), smem, a.err,
-                            gbase, sq, sp);
+  march_tile<T, OR, GATHER, V>(j, *reinterpret_cast<const PhiloxKeys *>(a.round_keys), smem,
+                               a.err, gbase, sq, sp);
   if (GATHER) {
     const size_t cta = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
     block_partials(sq, sp, smem,
@@ -157,12 +157,20 @@ cudaError_t launch_mixed_t(const Geometry &g, const Tile &t, const CUtensorMap &
 
 __global__ void advance_pass_kernel(uint32_t *pass, uint32_t n) { *pass += n; }
 
+// The heatbath half-sweep in FP32 (issue-bound: Philox and the deviate) runs
+// two quads per thread; the others one.
+template <typename T, bool OR, bool GATHER>
+constexpr int quads_per_thread() {
+  return (sizeof(T) == 4 && !OR && !GATHER) ? 2 : 1;
+}
+
 template <typename T, bool OR, bool GATHER>
 cudaError_t launch_t(const Geometry &g, const Tile &t, const CUtensorMap &tm_halo,
                      const CUtensorMap &tm_own, const SweepArgs &a, cudaStream_t s) {
   const SmemLayout lay = smem_layout(t.ty, g.W, (int)sizeof(T), OR);
   const size_t smem = (size_t)lay.total + 128;
-  auto kfn = halfsweep_kernel<T, OR, GATHER>;
+  constexpr int V = quads_per_thread<T, OR, GATHER>();
+  auto kfn = halfsweep_kernel<T, OR, GATHER, V>;
   static int configured_bytes = 0;  // per instantiation
   if ((int)smem > configured_bytes) {
     cudaError_t e =
@@ -171,7 +179,7 @@ cudaError_t launch_t(const Geometry &g, const Tile &t, const CUtensorMap &tm_hal
     configured_bytes = (int)smem;
   }
   dim3 grid((g.Ly + t.ty - 1) / t.ty, (g.Lz + t.dz - 1) / t.dz, g.n_chains);
-  dim3 block((g.W / 4) * t.ty);
+  dim3 block((g.W / 4 + V - 1) / V * t.ty);
   kfn<<<grid, block, smem, s>>>(tm_halo, tm_own, a);
   return cudaGetLastError();
 }

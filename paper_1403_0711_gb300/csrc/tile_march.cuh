@@ -117,7 +117,13 @@ __device__ __forceinline__ void ring_init(unsigned char *smem) {
 // (the ring position and barrier phases continue from there) and is advanced
 // past this tile's planes.  Returns false if a bounded wait gave up (the error
 // word is set and no copy is left in flight).
-template <typename T, bool OR, bool GATHER>
+//
+// V quads per thread (V consecutive quads of a row, 4 V same-colour sites):
+// V = 2 halves the per-site share of the loop's fixed work (waits, barrier,
+// addresses, predicates) at the cost of registers; the sites' arithmetic is
+// unchanged, so the results are bitwise those of V = 1.  The block has
+// ceil(QW / V) threads per row.
+template <typename T, bool OR, bool GATHER, int V = 1>
 __device__ bool march_tile(const TileJob<T> &j, const PhiloxKeys &K, unsigned char *smem,
                            int *err, int &gbase, double &sq, double &sp) {
   const SmemLayout lay = smem_layout(j.TY, j.W, (int)sizeof(T), OR);
@@ -133,7 +139,8 @@ __device__ bool march_tile(const TileJob<T> &j, const PhiloxKeys &K, unsigned ch
 
   const int tid = threadIdx.x;
   const int W = j.W;
-  const int qx = tid % j.QW, ty = tid / j.QW;
+  const int qwv = (j.QW + V - 1) / V;  // threads per row
+  const int qx = (tid % qwv) * V, ty = tid / qwv;  // this thread's first quad
   const int n_planes = j.nz + 2;  // other-colour planes z0-1 .. z0+nz
   const int c = j.colour;
   const int y = j.y0 + ty;
@@ -142,6 +149,13 @@ __device__ bool march_tile(const TileJob<T> &j, const PhiloxKeys &K, unsigned ch
   // row TY - 1 touch no shared or global memory of the tile.
   const bool in_tile = ty < j.TY;
   const bool live = in_tile && (y < j.Ly) && (qx < j.Wq);
+  // quad v of this thread: inside the row's storage (loads), holds sites (updates)
+  bool qmem[V], qlive[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    qmem[v] = in_tile && qx + v < j.QW;
+    qlive[v] = live && qx + v < j.Wq;
+  }
 
   const int gb = gbase;
   if (tid == 0) {
@@ -169,11 +183,21 @@ __device__ bool march_tile(const TileJob<T> &j, const PhiloxKeys &K, unsigned ch
   if (tid == 0)
     for (; issued < min(kStages, n_planes); ++issued) issue(issued);
 
-  T cm[4] = {T(0), T(0), T(0), T(0)}, c0[4] = {T(0), T(0), T(0), T(0)}, cp[4];
+  T cm[V][4], c0[V][4], cp[V][4];
+#pragma unroll
+  for (int v = 0; v < V; ++v)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) cm[v][i] = c0[v][i] = cp[v][i] = T(0);
   bool ok = wait_plane(0);
-  if (ok && in_tile) ld_quad(halo_slot(slot_of(0)) + (ty + 1) * W + 4 * qx, cm);
+  if (ok)
+#pragma unroll
+    for (int v = 0; v < V; ++v)
+      if (qmem[v]) ld_quad(halo_slot(slot_of(0)) + (ty + 1) * W + 4 * (qx + v), cm[v]);
   ok = ok && wait_plane(1);
-  if (ok && in_tile) ld_quad(halo_slot(slot_of(1)) + (ty + 1) * W + 4 * qx, c0);
+  if (ok)
+#pragma unroll
+    for (int v = 0; v < V; ++v)
+      if (qmem[v]) ld_quad(halo_slot(slot_of(1)) + (ty + 1) * W + 4 * (qx + v), c0[v]);
   if (!ok) {
     atomicOr(err, kErrTimeout);
     *abort_flag = 1;
@@ -183,13 +207,18 @@ __device__ bool march_tile(const TileJob<T> &j, const PhiloxKeys &K, unsigned ch
   int done = 1;  // planes 0..done completed for every thread
 
   // per-thread constants of the plane loop
-  uint32_t pad0 = 0u, pad1 = 0u;  // quad lanes past x = Lx - 1 (kept at 0), row parity 0 / 1
+  // quad lanes past x = Lx - 1 (kept at 0), row parity 0 / 1, per quad
+  uint32_t pad0[V], pad1[V];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    if (2 * (4 * qx + i) >= j.Lx) pad0 |= 1u << i;
-    if (2 * (4 * qx + i) + 1 >= j.Lx) pad1 |= 1u << i;
+  for (int v = 0; v < V; ++v) {
+    pad0[v] = pad1[v] = 0u;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (2 * (4 * (qx + v) + i) >= j.Lx) pad0[v] |= 1u << i;
+      if (2 * (4 * (qx + v) + i) + 1 >= j.Lx) pad1[v] |= 1u << i;
+    }
   }
-  const bool lo_ok = qx > 0, hi_ok = 4 * qx + 4 < W;
+  const bool lo_ok = qx > 0, hi_ok = 4 * qx + 4 * V < W;
   const int hrow = (ty + 1) * W + 4 * qx;  // this quad in a halo box (first row y0 - 1)
   const int orow = ty * W + 4 * qx;        // this quad in an own box (first row y0)
   T *outp = j.out + ((size_t)j.z0 * j.Ly + y) * W + 4 * qx;  // plane z0; one plane per step
@@ -199,46 +228,59 @@ __device__ bool march_tile(const TileJob<T> &j, const PhiloxKeys &K, unsigned ch
   // Plane k (z = z0 + k - 1): M, C, P are the other colour's quads of planes
   // z - 1, z, z + 1 (P loaded here).  The loop calls it with the names
   // rotated, so no register is copied from plane to plane.
-  auto step = [&](int k, T(&M)[4], T(&C)[4], T(&P)[4]) -> bool {
+  auto step = [&](int k, T(&M)[V][4], T(&C)[V][4], T(&P)[V][4]) -> bool {
     const bool got = wait_plane(k + 1);
     const T *Pz = halo_slot(slot_of(k)) + hrow;  // row y of plane z
     if (got) {
-      if (in_tile) {
-        ld_quad(halo_slot(slot_of(k + 1)) + hrow, P);
-      } else {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) P[i] = T(0);
+      for (int v = 0; v < V; ++v) {
+        if (qmem[v]) {
+          ld_quad(halo_slot(slot_of(k + 1)) + hrow + 4 * v, P[v]);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) P[v][i] = T(0);
+        }
       }
       if (live) {
-        T ym[4], yp[4], xs[4], S[4], v[4];
-        ld_quad(Pz - W, ym);
-        ld_quad(Pz + W, yp);
         const bool odd = par != 0;
-        const T e = (odd ? hi_ok : lo_ok) ? Pz[odd ? 4 : -1] : T(0);
-        x_neighbours(odd, e, C, xs);
+        // the x neighbour beyond this thread's quads (left end when even,
+        // right end when odd); between its own quads it is in registers
+        const T edge = (odd ? hi_ok : lo_ok) ? Pz[odd ? 4 * V : -1] : T(0);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) S[i] = ((M[i] + P[i]) + (ym[i] + yp[i])) + (C[i] + xs[i]);
-        if (!OR) {
-          const uint32_t z = (uint32_t)(j.z0 + k - 1);
-          const uint32_t quad = (z * (uint32_t)j.Ly + (uint32_t)y) * (uint32_t)j.Wq + (uint32_t)qx;
-          const uint4 w = philox4x32_10(make_uint4(quad, j.pass, j.rng_id, (uint32_t)c), K);
-          v[0] = fma(S[0], Coef<T>::sixth, Noise<T>::of(w.x));
-          v[1] = fma(S[1], Coef<T>::sixth, Noise<T>::of(w.y));
-          v[2] = fma(S[2], Coef<T>::sixth, Noise<T>::of(w.z));
-          v[3] = fma(S[3], Coef<T>::sixth, Noise<T>::of(w.w));
-        } else {
-          T old[4];
-          ld_quad(own_slot(slot_of(k)) + orow, old);
-#pragma unroll
-          for (int i = 0; i < 4; ++i) v[i] = fma(S[i], Coef<T>::third, -old[i]);
-        }
-        const uint32_t pm = par ? pad1 : pad0;
-        if (pm) {
+        for (int v = 0; v < V; ++v) {
+          if (!qlive[v]) continue;
+          T ym[4], yp[4], xs[4], S[4], u[4];
+          ld_quad(Pz + 4 * v - W, ym);
+          ld_quad(Pz + 4 * v + W, yp);
+          const T e = odd ? (v + 1 < V ? C[v + 1 < V ? v + 1 : v][0] : edge)
+                          : (v > 0 ? C[v > 0 ? v - 1 : v][3] : edge);
+          x_neighbours(odd, e, C[v], xs);
 #pragma unroll
           for (int i = 0; i < 4; ++i)
-            if ((pm >> i) & 1u) v[i] = T(0);  // keep the row padding at 0
+            S[i] = ((M[v][i] + P[v][i]) + (ym[i] + yp[i])) + (C[v][i] + xs[i]);
+          if (!OR) {
+            const uint32_t z = (uint32_t)(j.z0 + k - 1);
+            const uint32_t quad =
+                (z * (uint32_t)j.Ly + (uint32_t)y) * (uint32_t)j.Wq + (uint32_t)(qx + v);
+            const uint4 w = philox4x32_10(make_uint4(quad, j.pass, j.rng_id, (uint32_t)c), K);
+            u[0] = fma(S[0], Coef<T>::sixth, Noise<T>::of(w.x));
+            u[1] = fma(S[1], Coef<T>::sixth, Noise<T>::of(w.y));
+            u[2] = fma(S[2], Coef<T>::sixth, Noise<T>::of(w.z));
+            u[3] = fma(S[3], Coef<T>::sixth, Noise<T>::of(w.w));
+          } else {
+            T old[4];
+            ld_quad(own_slot(slot_of(k)) + orow + 4 * v, old);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) u[i] = fma(S[i], Coef<T>::third, -old[i]);
+          }
+          const uint32_t pm = par ? pad1[v] : pad0[v];
+          if (pm) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+              if ((pm >> i) & 1u) u[i] = T(0);  // keep the row padding at 0
+          }
+          st_quad(outp + 4 * v, u);
         }
-        st_quad(outp, v);
       }
     } else {
       atomicOr(err, kErrTimeout);
