@@ -310,9 +310,14 @@ int coulps_kernel_times(coulps_lattice_t lat, double out[10]);
 /* ---- checkpoint -------------------------------------------------------- */
 /* Save / restore the full sampler state: fields of all chains, the pass
  * counter, seed and shape, and (if ch != NULL) the estimator state of the
- * charge set, with a checksum.  Restoring then continuing gives bitwise the
- * same samples as an uninterrupted run.  Synchronises.
- * Errors: EIO, ECORRUPT (checksum or shape mismatch), ECUDA. */
+ * charge set (statistics, sample log, control-variate statistics and, for an
+ * off-lattice set with forces, the force sums), with a checksum.  Restoring
+ * then continuing gives bitwise the same samples as an uninterrupted run.
+ * The charge set itself (sites or positions, near pairs) is not stored: load
+ * into a set created the same way.  Files of the first format (no
+ * control-variate state or force sums) still load.  Synchronises.
+ * Errors: EIO, ECORRUPT (checksum or shape mismatch, or force sums present in
+ * only one of file and set), ECUDA. */
 int coulps_checkpoint_save(coulps_lattice_t lat, coulps_charges_t ch, const char *path);
 int coulps_checkpoint_load(coulps_lattice_t lat, coulps_charges_t ch, const char *path);
 

@@ -1835,7 +1835,7 @@ int coulps_checkpoint_save(coulps_lattice_t L, coulps_charges_t C, const char *p
   CkptHeader h;
   std::memset(&h, 0, sizeof(h));
   std::memcpy(h.magic, "COULPS1", 8);
-  h.version = 1;
+  h.version = 2;
   h.Lx = g.Lx; h.Ly = g.Ly; h.Lz = g.Lz; h.n_chains = g.n_chains;
   h.precision = g.precision; h.W = g.W;
   h.seed = L->seed;
@@ -1845,7 +1845,10 @@ int coulps_checkpoint_save(coulps_lattice_t L, coulps_charges_t C, const char *p
   h.stat_stride = kStatStride;
   h.log_cap = C ? C->log_cap : 0;
   std::vector<unsigned char> field(g.chain_elems * g.es * (size_t)g.n_chains);
-  std::vector<double> stats, log;
+  std::vector<double> stats, log, cvstats, fsum;
+  // version 2: after the log, {has control-variate state, has force sums}
+  // and those blocks
+  int64_t ex[2] = {C ? 1 : 0, (C && C->d_fsum) ? 1 : 0};
   CK(cudaMemcpyAsync(field.data(), L->field, field.size(), cudaMemcpyDeviceToHost, L->stream));
   if (C) {
     stats.resize((size_t)kStatStride * g.n_chains);
@@ -1855,6 +1858,14 @@ int coulps_checkpoint_save(coulps_lattice_t L, coulps_charges_t C, const char *p
     if (!log.empty())
       CK(cudaMemcpyAsync(log.data(), C->d_log, log.size() * sizeof(double),
                          cudaMemcpyDeviceToHost, L->stream));
+    cvstats.resize(stats.size());
+    CK(cudaMemcpyAsync(cvstats.data(), C->d_cvstats, cvstats.size() * sizeof(double),
+                       cudaMemcpyDeviceToHost, L->stream));
+    if (ex[1]) {
+      fsum.resize((size_t)3 * C->n * g.n_chains);
+      CK(cudaMemcpyAsync(fsum.data(), C->d_fsum, fsum.size() * sizeof(double),
+                         cudaMemcpyDeviceToHost, L->stream));
+    }
   }
   uint32_t dpass = 0;
   CK(cudaMemcpyAsync(&dpass, L->d_pass, sizeof(dpass), cudaMemcpyDeviceToHost, L->stream));
@@ -1866,12 +1877,18 @@ int coulps_checkpoint_save(coulps_lattice_t L, coulps_charges_t C, const char *p
   sum = fnv1a(sum, field.data(), field.size());
   sum = fnv1a(sum, stats.data(), stats.size() * sizeof(double));
   sum = fnv1a(sum, log.data(), log.size() * sizeof(double));
+  sum = fnv1a(sum, ex, sizeof(ex));
+  sum = fnv1a(sum, cvstats.data(), cvstats.size() * sizeof(double));
+  sum = fnv1a(sum, fsum.data(), fsum.size() * sizeof(double));
   FILE *f = std::fopen(path, "wb");
   if (!f) return COULPS_EIO;
   bool ok = std::fwrite(&h, sizeof(h), 1, f) == 1 &&
             std::fwrite(field.data(), 1, field.size(), f) == field.size() &&
             std::fwrite(stats.data(), sizeof(double), stats.size(), f) == stats.size() &&
             std::fwrite(log.data(), sizeof(double), log.size(), f) == log.size() &&
+            std::fwrite(ex, sizeof(ex), 1, f) == 1 &&
+            std::fwrite(cvstats.data(), sizeof(double), cvstats.size(), f) == cvstats.size() &&
+            std::fwrite(fsum.data(), sizeof(double), fsum.size(), f) == fsum.size() &&
             std::fwrite(&sum, sizeof(sum), 1, f) == 1;
   ok = (std::fclose(f) == 0) && ok;
   return ok ? COULPS_OK : COULPS_EIO;
@@ -1887,7 +1904,8 @@ int coulps_checkpoint_load(coulps_lattice_t L, coulps_charges_t C, const char *p
     std::fclose(f);
     return COULPS_ECORRUPT;
   }
-  if (std::memcmp(h.magic, "COULPS1", 8) != 0 || h.version != 1 || h.Lx != g.Lx ||
+  if (std::memcmp(h.magic, "COULPS1", 8) != 0 || (h.version != 1 && h.version != 2) ||
+      h.Lx != g.Lx ||
       h.Ly != g.Ly || h.Lz != g.Lz || h.n_chains != g.n_chains || h.precision != g.precision ||
       h.W != g.W || h.seed != L->seed || h.stat_stride != kStatStride ||
       (C && (!h.has_charges || h.n_charges != C->n || h.log_cap != C->log_cap))) {
@@ -1900,8 +1918,21 @@ int coulps_checkpoint_load(coulps_lattice_t L, coulps_charges_t C, const char *p
   uint64_t sum_file = 0;
   bool ok = std::fread(field.data(), 1, field.size(), f) == field.size() &&
             std::fread(stats.data(), sizeof(double), stats.size(), f) == stats.size() &&
-            std::fread(log.data(), sizeof(double), log.size(), f) == log.size() &&
-            std::fread(&sum_file, sizeof(sum_file), 1, f) == 1;
+            std::fread(log.data(), sizeof(double), log.size(), f) == log.size();
+  // version 2 extras: control-variate state and force sums (version 1: none)
+  int64_t ex[2] = {0, 0};
+  std::vector<double> cvstats, fsum;
+  if (ok && h.version == 2) {
+    ok = std::fread(ex, sizeof(ex), 1, f) == 1 && ex[0] == h.has_charges &&
+         (ex[1] == 0 || ex[1] == 1) && (!ex[1] || h.has_charges);
+    if (ok) {
+      cvstats.resize(ex[0] ? stats.size() : 0);
+      fsum.resize(ex[1] ? (size_t)3 * h.n_charges * g.n_chains : 0);
+      ok = std::fread(cvstats.data(), sizeof(double), cvstats.size(), f) == cvstats.size() &&
+           std::fread(fsum.data(), sizeof(double), fsum.size(), f) == fsum.size();
+    }
+  }
+  ok = ok && std::fread(&sum_file, sizeof(sum_file), 1, f) == 1;
   std::fclose(f);
   if (!ok) return COULPS_ECORRUPT;
   uint64_t sum = 1469598103934665603ull;
@@ -1909,7 +1940,14 @@ int coulps_checkpoint_load(coulps_lattice_t L, coulps_charges_t C, const char *p
   sum = fnv1a(sum, field.data(), field.size());
   sum = fnv1a(sum, stats.data(), stats.size() * sizeof(double));
   sum = fnv1a(sum, log.data(), log.size() * sizeof(double));
+  if (h.version == 2) {
+    sum = fnv1a(sum, ex, sizeof(ex));
+    sum = fnv1a(sum, cvstats.data(), cvstats.size() * sizeof(double));
+    sum = fnv1a(sum, fsum.data(), fsum.size() * sizeof(double));
+  }
   if (sum != sum_file) return COULPS_ECORRUPT;
+  // a set that keeps force sums needs them from the file, and only such a set takes them
+  if (C && ((C->d_fsum != nullptr) != (ex[1] != 0))) return COULPS_ECORRUPT;
   const uint32_t dpass = (uint32_t)h.pass;
   CK(cudaMemcpyAsync(L->field, field.data(), field.size(), cudaMemcpyHostToDevice, L->stream));
   CK(cudaMemcpyAsync(L->d_pass, &dpass, sizeof(dpass), cudaMemcpyHostToDevice, L->stream));
@@ -1918,6 +1956,14 @@ int coulps_checkpoint_load(coulps_lattice_t L, coulps_charges_t C, const char *p
                        cudaMemcpyHostToDevice, L->stream));
     if (!log.empty())
       CK(cudaMemcpyAsync(C->d_log, log.data(), log.size() * sizeof(double),
+                         cudaMemcpyHostToDevice, L->stream));
+    if (!cvstats.empty())
+      CK(cudaMemcpyAsync(C->d_cvstats, cvstats.data(), cvstats.size() * sizeof(double),
+                         cudaMemcpyHostToDevice, L->stream));
+    else
+      CK(launch_reset_stats(C->d_cvstats, g.n_chains, L->stream));
+    if (!fsum.empty())
+      CK(cudaMemcpyAsync(C->d_fsum, fsum.data(), fsum.size() * sizeof(double),
                          cudaMemcpyHostToDevice, L->stream));
   }
   CK(cudaStreamSynchronize(L->stream));
