@@ -239,6 +239,27 @@ int coulps_charges_create_off(coulps_lattice_t lat, int64_t n, const double *pos
 int coulps_charges_near(coulps_charges_t ch, double rc, int64_t *n_pairs, double *e_direct,
                         double *f_direct);
 
+/* Pure host helpers behind coulps_charges_create_off and coulps_charges_near
+ * (no device, no lattice; host arrays owned by the caller).
+ * coulps_near_pairs: for n particles at pos_xyz, the near partners
+ * (|r_i - r_j| < rc, j != i) as CSR, both directions, each list ascending:
+ * ptr[0..n] and nbr[0..ptr[n]).  *n_entries always receives ptr[n]; if it
+ * exceeds cap (nbr may then be NULL) nothing else is written and EINVAL is
+ * returned, so a first call with cap = 0 sizes the array.
+ * coulps_offlattice_corners: for each particle its eight corner sites
+ * (c = 4 cx + 2 cy + cz, base site floor(r) clipped to L - 2) as offsets in
+ * one chain's field of a lattice of this shape and precision
+ * (colour * colour_elems + (z * Ly + y) * W + x / 2, the layout of
+ * coulps_field_get's storage), their trilinear weights (8 n doubles) and
+ * weight gradients (24 n doubles, [8 i + c][mu]).
+ * Errors: EINVAL (bad sizes or pointers, non-finite or out-of-box positions,
+ * a dimension < 2), ENOMEM. */
+int coulps_near_pairs(int64_t n, const double *pos_xyz, double rc, int64_t *ptr, uint32_t *nbr,
+                      int64_t cap, int64_t *n_entries);
+int coulps_offlattice_corners(int Lx, int Ly, int Lz, int precision, int64_t n,
+                              const double *pos_xyz, uint32_t *offset, double *weight,
+                              double *grad);
+
 /* Synchronise and return the mean force on each particle of an off-lattice
  * set created with forces != 0: mean[3i + mu] = (sum over all chains' samples
  * of f_i,mu) / (number of samples), and, if stderr_chains is not NULL, the

@@ -43,7 +43,7 @@ EXPORTS = (
     "coulps_measure_sets", "coulps_run_sets", "coulps_gcv_create", "coulps_gcv_destroy",
     "coulps_gcv_info", "coulps_gcv_h", "coulps_gcv_eval", "coulps_gcv_run",
     "coulps_charges_create_off", "coulps_forces", "coulps_charges_near",
-    "coulps_heatbath_noise",
+    "coulps_heatbath_noise", "coulps_near_pairs", "coulps_offlattice_corners",
 )
 SCHEDULE_ALIGNED, SCHEDULE_PHASED = 0, 1
 STAT_STRIDE = 72
@@ -92,6 +92,10 @@ def load(path: str | Path | None = None):
         "coulps_forces": (i32, [vp, P(f64), P(f64)]),
         "coulps_charges_near": (i32, [vp, ctypes.c_double, P(i64), P(f64), P(f64)]),
         "coulps_heatbath_noise": (i32, [i32, vp, vp, i64, vp]),
+        "coulps_near_pairs": (i32, [i64, P(f64), ctypes.c_double, P(i64), P(ctypes.c_uint32), i64,
+                                    P(i64)]),
+        "coulps_offlattice_corners": (i32, [i32, i32, i32, i32, i64, P(f64),
+                                            P(ctypes.c_uint32), P(f64), P(f64)]),
         "coulps_charges_destroy": (None, [vp]),
         "coulps_measure": (i32, [vp, vp]),
         "coulps_run": (i32, [vp, vp, i32, i32, i32, i32]),
@@ -615,6 +619,40 @@ def coulps_forces(charges):
 
 def coulps_charges_near(charges, rc):
     return charges.near(rc)
+
+
+def near_pairs(pos, rc):
+    """CSR (ptr, nbr) of the near partners of particles at pos (n, 3)
+    (coulps_near_pairs; host only)."""
+    lib = load()
+    p = np.ascontiguousarray(np.asarray(pos, dtype=np.float64).reshape(-1, 3))
+    n = len(p)
+    ptr = np.zeros(n + 1, dtype=np.int64)
+    need = ctypes.c_int64()
+    st = lib.coulps_near_pairs(n, _f64p(p), float(rc), ptr.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                               None, 0, ctypes.byref(need))
+    if st == 0:
+        return ptr, np.zeros(0, dtype=np.uint32)
+    nbr = np.zeros(need.value, dtype=np.uint32)
+    _check(lib.coulps_near_pairs(n, _f64p(p), float(rc),
+                                 ptr.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                 nbr.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), len(nbr),
+                                 ctypes.byref(need)), "coulps_near_pairs")
+    return ptr, nbr
+
+
+def offlattice_corners(L, precision, pos):
+    """(offset (n, 8), weight (n, 8), grad (n, 8, 3)) of coulps_offlattice_corners."""
+    lib = load()
+    p = np.ascontiguousarray(np.asarray(pos, dtype=np.float64).reshape(-1, 3))
+    n = len(p)
+    off = np.zeros((n, 8), dtype=np.uint32)
+    w = np.zeros((n, 8))
+    g = np.zeros((n, 8, 3))
+    _check(lib.coulps_offlattice_corners(int(L[0]), int(L[1]), int(L[2]), int(precision), n,
+                                         _f64p(p), off.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                                         _f64p(w), _f64p(g)), "coulps_offlattice_corners")
+    return off, w, g
 
 
 def heatbath_noise(words, precision, stream=None):

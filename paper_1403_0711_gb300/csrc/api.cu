@@ -668,6 +668,106 @@ int run_staggered(coulps_lattice *L, coulps_charges *C, int n_meas, int n_hb, in
   return COULPS_OK;
 }
 
+// Corner storage offsets (in a chain's field), trilinear weights and weight
+// gradients of n particles at real positions pos (x, y, z): base site
+// b = floor(r) clipped to L - 2, f = r - b, corner c = (cx, cy, cz) with cx
+// slowest, weight prod_mu (c_mu ? f_mu : 1 - f_mu).  False if a position is
+// outside [0, L - 1] or not finite, or a dimension is < 2.
+bool offlattice_corners(int Lx, int Ly, int Lz, int W, size_t colour_elems, int64_t n,
+                        const double *pos, uint32_t *oidx, double *ow, double *og) {
+  const int Ls[3] = {Lx, Ly, Lz};
+  if (Lx < 2 || Ly < 2 || Lz < 2) return false;
+  for (int64_t i = 0; i < n; ++i) {
+    int b[3];
+    double f[3];
+    for (int mu = 0; mu < 3; ++mu) {
+      const double r = pos[3 * i + mu];
+      if (!(r >= 0.0 && r <= (double)(Ls[mu] - 1))) return false;
+      int bi = (int)std::floor(r);
+      if (bi > Ls[mu] - 2) bi = Ls[mu] - 2;
+      b[mu] = bi;
+      f[mu] = r - bi;
+    }
+    for (int c = 0; c < 8; ++c) {
+      const int cc[3] = {(c >> 2) & 1, (c >> 1) & 1, c & 1};
+      double fac[3], dfac[3];
+      for (int mu = 0; mu < 3; ++mu) {
+        fac[mu] = cc[mu] ? f[mu] : 1.0 - f[mu];
+        dfac[mu] = cc[mu] ? 1.0 : -1.0;
+      }
+      const int x = b[0] + cc[0], y = b[1] + cc[1], z = b[2] + cc[2];
+      const int col = (x + y + z) & 1;
+      oidx[8 * i + c] =
+          (uint32_t)((size_t)col * colour_elems + ((size_t)z * Ly + y) * W + (x >> 1));
+      ow[8 * i + c] = fac[0] * fac[1] * fac[2];
+      og[3 * (8 * i + c) + 0] = dfac[0] * fac[1] * fac[2];
+      og[3 * (8 * i + c) + 1] = fac[0] * dfac[1] * fac[2];
+      og[3 * (8 * i + c) + 2] = fac[0] * fac[1] * dfac[2];
+    }
+  }
+  return true;
+}
+
+// Near partners of n particles (|r_i - r_j| < rc, j != i) as CSR, both
+// directions, each list ascending: ptr (n + 1 entries) and nbr.  Pairs are
+// found through a grid of cells of edge >= rc (a particle's partners lie in
+// its own or the 26 adjacent cells); the grid is coarsened until it has at
+// most 8 n + 64 cells.
+void near_csr(const double *p, int64_t n, double rc, std::vector<int64_t> &ptr,
+              std::vector<uint32_t> &nbr) {
+  ptr.assign((size_t)n + 1, 0);
+  nbr.clear();
+  if (!(rc > 0.0) || n < 2) return;
+  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int64_t i = 0; i < n; ++i)
+    for (int mu = 0; mu < 3; ++mu) {
+      lo[mu] = std::min(lo[mu], p[3 * i + mu]);
+      hi[mu] = std::max(hi[mu], p[3 * i + mu]);
+    }
+  double cs = rc;
+  int64_t nd[3];
+  for (;;) {
+    for (int mu = 0; mu < 3; ++mu) nd[mu] = (int64_t)std::floor((hi[mu] - lo[mu]) / cs) + 1;
+    if ((double)nd[0] * nd[1] * nd[2] <= 8.0 * (double)n + 64.0) break;
+    cs *= 1.5;
+  }
+  auto cell_of = [&](int64_t i, int mu) {
+    int64_t c = (int64_t)std::floor((p[3 * i + mu] - lo[mu]) / cs);
+    return c < 0 ? 0 : (c >= nd[mu] ? nd[mu] - 1 : c);
+  };
+  const int64_t ncell = nd[0] * nd[1] * nd[2];
+  std::vector<int64_t> cstart((size_t)ncell + 1, 0), cell((size_t)n), order((size_t)n);
+  for (int64_t i = 0; i < n; ++i) {
+    cell[i] = (cell_of(i, 2) * nd[1] + cell_of(i, 1)) * nd[0] + cell_of(i, 0);
+    cstart[cell[i] + 1]++;
+  }
+  for (int64_t c = 0; c < ncell; ++c) cstart[c + 1] += cstart[c];
+  {
+    std::vector<int64_t> fill(cstart.begin(), cstart.end() - 1);
+    for (int64_t i = 0; i < n; ++i) order[fill[cell[i]]++] = i;
+  }
+  std::vector<uint32_t> mine;
+  for (int64_t i = 0; i < n; ++i) {
+    mine.clear();
+    const int64_t cx = cell_of(i, 0), cy = cell_of(i, 1), cz = cell_of(i, 2);
+    for (int64_t z = std::max<int64_t>(cz - 1, 0); z <= std::min(cz + 1, nd[2] - 1); ++z)
+      for (int64_t y = std::max<int64_t>(cy - 1, 0); y <= std::min(cy + 1, nd[1] - 1); ++y)
+        for (int64_t x = std::max<int64_t>(cx - 1, 0); x <= std::min(cx + 1, nd[0] - 1); ++x) {
+          const int64_t c = (z * nd[1] + y) * nd[0] + x;
+          for (int64_t k = cstart[c]; k < cstart[c + 1]; ++k) {
+            const int64_t j = order[k];
+            if (j == i) continue;
+            const double dx = p[3 * i] - p[3 * j], dy = p[3 * i + 1] - p[3 * j + 1],
+                         dz = p[3 * i + 2] - p[3 * j + 2];
+            if (std::sqrt(dx * dx + dy * dy + dz * dz) < rc) mine.push_back((uint32_t)j);
+          }
+        }
+    std::sort(mine.begin(), mine.end());
+    nbr.insert(nbr.end(), mine.begin(), mine.end());
+    ptr[i + 1] = (int64_t)nbr.size();
+  }
+}
+
 uint64_t fnv1a(uint64_t h, const void *p, size_t n) {
   const unsigned char *b = static_cast<const unsigned char *>(p);
   for (size_t i = 0; i < n; ++i) {
@@ -1231,40 +1331,14 @@ int coulps_charges_create_off(coulps_lattice_t L, int64_t n, const double *pos, 
   if (n > ((int64_t)1 << 28)) return COULPS_EINVAL;
   const Geometry &g = L->g;
   if (g.Lx < 2 || g.Ly < 2 || g.Lz < 2) return COULPS_EINVAL;
-  const int Ls[3] = {g.Lx, g.Ly, g.Lz};
+  for (int64_t i = 0; i < n; ++i)
+    if (!std::isfinite(q[i])) return COULPS_EINVAL;
   // corners, trilinear weights and their gradients, in FP64 on the host
   std::vector<uint32_t> oidx((size_t)8 * n);
   std::vector<double> ow((size_t)8 * n), og((size_t)24 * n);
-  for (int64_t i = 0; i < n; ++i) {
-    int b[3];
-    double f[3];
-    for (int mu = 0; mu < 3; ++mu) {
-      const double r = pos[3 * i + mu];
-      if (!(r >= 0.0 && r <= (double)(Ls[mu] - 1))) return COULPS_EINVAL;
-      int bi = (int)std::floor(r);
-      if (bi > Ls[mu] - 2) bi = Ls[mu] - 2;
-      b[mu] = bi;
-      f[mu] = r - bi;
-    }
-    if (!std::isfinite(q[i])) return COULPS_EINVAL;
-    for (int c = 0; c < 8; ++c) {
-      const int cx = (c >> 2) & 1, cy = (c >> 1) & 1, cz = c & 1;  // x slowest
-      const int cc[3] = {cx, cy, cz};
-      double fac[3], dfac[3];
-      for (int mu = 0; mu < 3; ++mu) {
-        fac[mu] = cc[mu] ? f[mu] : 1.0 - f[mu];
-        dfac[mu] = cc[mu] ? 1.0 : -1.0;
-      }
-      const int x = b[0] + cx, y = b[1] + cy, z = b[2] + cz;
-      const int col = (x + y + z) & 1;
-      oidx[8 * i + c] =
-          (uint32_t)((size_t)col * g.colour_elems + ((size_t)z * g.Ly + y) * g.W + (x >> 1));
-      ow[8 * i + c] = fac[0] * fac[1] * fac[2];
-      og[3 * (8 * i + c) + 0] = dfac[0] * fac[1] * fac[2];
-      og[3 * (8 * i + c) + 1] = fac[0] * dfac[1] * fac[2];
-      og[3 * (8 * i + c) + 2] = fac[0] * fac[1] * dfac[2];
-    }
-  }
+  if (!offlattice_corners(g.Lx, g.Ly, g.Lz, g.W, g.colour_elems, n, pos, oidx.data(), ow.data(),
+                          og.data()))
+    return COULPS_EINVAL;
   // the common parts of a charge set (statistics, log) with no lattice charges
   coulps_charges_t C = nullptr;
   int st = coulps_charges_create(L, 0, nullptr, nullptr, log_capacity, &C);
@@ -1319,60 +1393,9 @@ int coulps_charges_near(coulps_charges_t C, double rc, int64_t *n_pairs, double 
   coulps_lattice *L = C->lat;
   const int64_t n = C->n;
   const double *p = C->pos.data();
-  // neighbour lists by a cell grid of edge >= rc (a particle's near partners
-  // are in its own or the 26 adjacent cells), each list in ascending order
-  std::vector<int64_t> ptr((size_t)n + 1, 0);
+  std::vector<int64_t> ptr;
   std::vector<uint32_t> nbr;
-  if (rc > 0.0 && n > 1) {
-    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int64_t i = 0; i < n; ++i)
-      for (int mu = 0; mu < 3; ++mu) {
-        lo[mu] = std::min(lo[mu], p[3 * i + mu]);
-        hi[mu] = std::max(hi[mu], p[3 * i + mu]);
-      }
-    double cs = rc;
-    int64_t nd[3];
-    for (;;) {
-      for (int mu = 0; mu < 3; ++mu) nd[mu] = (int64_t)std::floor((hi[mu] - lo[mu]) / cs) + 1;
-      if ((double)nd[0] * nd[1] * nd[2] <= 8.0 * (double)n + 64.0) break;
-      cs *= 1.5;
-    }
-    auto cell_of = [&](int64_t i, int mu) {
-      int64_t c = (int64_t)std::floor((p[3 * i + mu] - lo[mu]) / cs);
-      return c < 0 ? 0 : (c >= nd[mu] ? nd[mu] - 1 : c);
-    };
-    const int64_t ncell = nd[0] * nd[1] * nd[2];
-    std::vector<int64_t> cstart((size_t)ncell + 1, 0), cell((size_t)n), order((size_t)n);
-    for (int64_t i = 0; i < n; ++i) {
-      cell[i] = (cell_of(i, 2) * nd[1] + cell_of(i, 1)) * nd[0] + cell_of(i, 0);
-      cstart[cell[i] + 1]++;
-    }
-    for (int64_t c = 0; c < ncell; ++c) cstart[c + 1] += cstart[c];
-    {
-      std::vector<int64_t> fill(cstart.begin(), cstart.end() - 1);
-      for (int64_t i = 0; i < n; ++i) order[fill[cell[i]]++] = i;
-    }
-    std::vector<uint32_t> mine;
-    for (int64_t i = 0; i < n; ++i) {
-      mine.clear();
-      const int64_t cx = cell_of(i, 0), cy = cell_of(i, 1), cz = cell_of(i, 2);
-      for (int64_t z = std::max<int64_t>(cz - 1, 0); z <= std::min(cz + 1, nd[2] - 1); ++z)
-        for (int64_t y = std::max<int64_t>(cy - 1, 0); y <= std::min(cy + 1, nd[1] - 1); ++y)
-          for (int64_t x = std::max<int64_t>(cx - 1, 0); x <= std::min(cx + 1, nd[0] - 1); ++x) {
-            const int64_t c = (z * nd[1] + y) * nd[0] + x;
-            for (int64_t k = cstart[c]; k < cstart[c + 1]; ++k) {
-              const int64_t j = order[k];
-              if (j == i) continue;
-              const double dx = p[3 * i] - p[3 * j], dy = p[3 * i + 1] - p[3 * j + 1],
-                           dz = p[3 * i + 2] - p[3 * j + 2];
-              if (std::sqrt(dx * dx + dy * dy + dz * dz) < rc) mine.push_back((uint32_t)j);
-            }
-          }
-      std::sort(mine.begin(), mine.end());
-      nbr.insert(nbr.end(), mine.begin(), mine.end());
-      ptr[i + 1] = (int64_t)nbr.size();
-    }
-  }
+  near_csr(p, n, rc, ptr, nbr);
   const int64_t pairs = (int64_t)nbr.size() / 2;
   // the direct part with the continuum kernel of Eq. (s1), in FP64
   double E = 0.0;
@@ -1431,6 +1454,42 @@ int coulps_charges_near(coulps_charges_t C, double rc, int64_t *n_pairs, double 
   CK(launch_reset_stats(C->d_cvstats, nc, L->stream));
   CK(cudaStreamSynchronize(L->stream));  // pageable host arrays
   return COULPS_OK;
+}
+
+int coulps_near_pairs(int64_t n, const double *pos, double rc, int64_t *ptr, uint32_t *nbr,
+                      int64_t cap, int64_t *n_entries) {
+  if (n < 0 || (n > 0 && (!pos || !ptr)) || !n_entries || !std::isfinite(rc) || rc < 0.0 ||
+      cap < 0 || n > ((int64_t)1 << 31))
+    return COULPS_EINVAL;
+  for (int64_t k = 0; k < 3 * n; ++k)
+    if (!std::isfinite(pos[k])) return COULPS_EINVAL;
+  std::vector<int64_t> p;
+  std::vector<uint32_t> b;
+  try {
+    near_csr(pos, n, rc, p, b);
+  } catch (...) {
+    return COULPS_ENOMEM;
+  }
+  *n_entries = (int64_t)b.size();
+  if ((int64_t)b.size() > cap || (!b.empty() && !nbr)) return COULPS_EINVAL;
+  std::copy(p.begin(), p.end(), ptr);
+  std::copy(b.begin(), b.end(), nbr);
+  return COULPS_OK;
+}
+
+int coulps_offlattice_corners(int Lx, int Ly, int Lz, int precision, int64_t n, const double *pos,
+                              uint32_t *offset, double *weight, double *grad) {
+  if (n < 0 || (n > 0 && (!pos || !offset || !weight || !grad))) return COULPS_EINVAL;
+  if (precision != COULPS_F32 && precision != COULPS_F64) return COULPS_EINVAL;
+  if (Lx < 2 || Ly < 2 || Lz < 2 || Lx > 512 || Ly > 65535 || Lz > 65535) return COULPS_EINVAL;
+  // the row stride and colour size of a lattice of this shape and precision
+  const int es = precision == COULPS_F32 ? 4 : 8;
+  const int Wq = (Lx + 7) / 8, align_elems = 32 / es;
+  const int W = ((4 * Wq + align_elems - 1) / align_elems) * align_elems;
+  const size_t colour_elems = (size_t)Lz * Ly * W;
+  return offlattice_corners(Lx, Ly, Lz, W, colour_elems, n, pos, offset, weight, grad)
+             ? COULPS_OK
+             : COULPS_EINVAL;
 }
 
 int coulps_forces(coulps_charges_t C, double *mean, double *stderr_chains) {
