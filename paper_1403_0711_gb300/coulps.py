@@ -44,6 +44,7 @@ EXPORTS = (
     "coulps_gcv_info", "coulps_gcv_h", "coulps_gcv_eval", "coulps_gcv_run",
     "coulps_charges_create_off", "coulps_forces", "coulps_charges_near",
     "coulps_heatbath_noise", "coulps_near_pairs", "coulps_offlattice_corners",
+    "coulps_set_streams",
 )
 SCHEDULE_ALIGNED, SCHEDULE_PHASED = 0, 1
 STAT_STRIDE = 72
@@ -92,6 +93,7 @@ def load(path: str | Path | None = None):
         "coulps_forces": (i32, [vp, P(f64), P(f64)]),
         "coulps_charges_near": (i32, [vp, ctypes.c_double, P(i64), P(f64), P(f64)]),
         "coulps_heatbath_noise": (i32, [i32, vp, vp, i64, vp]),
+        "coulps_set_streams": (i32, [vp, i32]),
         "coulps_near_pairs": (i32, [i64, P(f64), ctypes.c_double, P(i64), P(ctypes.c_uint32), i64,
                                     P(i64)]),
         "coulps_offlattice_corners": (i32, [i32, i32, i32, i32, i64, P(f64),
@@ -270,6 +272,10 @@ class Lattice:
         return {"hb_ms": a[0], "hb_n": int(a[1]), "or_ms": a[2], "or_n": int(a[3]),
                 "mixed_ms": a[4], "mixed_n": int(a[5]), "pass_hb_ms": a[6], "pass_hb_n": int(a[7]),
                 "pass_or_ms": a[8], "pass_or_n": int(a[9])}
+
+    def set_streams(self, n):
+        """1 or 2 streams per compound sweep (coulps_set_streams)."""
+        _check(self._lib.coulps_set_streams(self.handle, int(n)), "coulps_set_streams")
 
     def set_schedule(self, schedule):
         _check(self._lib.coulps_set_schedule(self.handle, int(schedule)), "coulps_set_schedule")

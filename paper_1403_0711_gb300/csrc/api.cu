@@ -63,6 +63,10 @@ struct coulps_lattice {
   // heatbath pass then writes out of place)
   void *field2 = nullptr;
   CUtensorMap tm_halo2;  // halo map of field2 (tile ty + 2 rows)
+  // two streams: odd chains on stream2 (coulps_set_streams)
+  int split = 1;
+  cudaStream_t stream2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int fused = 0;  // 0 off, 1 over-relaxation passes, 2 all passes
   Tile ptile = {0, 0};
   CUtensorMap tm_p1[2], tm_p0[2];  // source field / field2; boxes ty + 4, ty + 2 rows
@@ -267,8 +271,14 @@ cudaEvent_t take_event(coulps_lattice *L) {
   return e;
 }
 
-int enqueue_compound(coulps_lattice *L, int n_hb, int n_or, coulps_charges *fuse = nullptr) {
+// The passes of one compound sweep for the chains chain0, chain0 + stride,
+// ... on stream `st`, with their measurement when `fuse` is given (the pass
+// counter is advanced by the caller).
+int enqueue_part(coulps_lattice *L, cudaStream_t st, int n_hb, int n_or, coulps_charges *fuse,
+                 int chain0, int stride) {
   SweepArgs a;
+  a.chain0 = chain0;
+  a.chain_stride = stride;
   a.field = L->field;
   a.Lx = L->g.Lx; a.Ly = L->g.Ly; a.Lz = L->g.Lz;
   a.W = L->g.W; a.Wq = L->g.Wq; a.QW = L->g.W / 4;
@@ -309,6 +319,8 @@ int enqueue_compound(coulps_lattice *L, int n_hb, int n_or, coulps_charges *fuse
     nf = n_pass & ~1;
   }
   PassArgs p;
+  p.chain0 = chain0;
+  p.chain_stride = stride;
   p.Lx = a.Lx; p.Ly = a.Ly; p.Lz = a.Lz;
   p.W = a.W; p.Wq = a.Wq; p.QW = a.QW;
   p.TY = L->ptile.ty; p.DZ = L->ptile.dz;
@@ -330,11 +342,11 @@ int enqueue_compound(coulps_lattice *L, int n_hb, int n_or, coulps_charges *fuse
         ea = take_event(L);
         eb = take_event(L);
         if (!ea || !eb) return COULPS_ECUDA;
-        CK(cudaEventRecord(ea, L->stream));
+        CK(cudaEventRecord(ea, st));
       }
-      CK(launch_pass(L->g, L->ptile, L->tm_p1[b], L->tm_p0[b], p, orx, L->stream));
+      CK(launch_pass(L->g, L->ptile, L->tm_p1[b], L->tm_p0[b], p, orx, st));
       if (L->profiling) {
-        CK(cudaEventRecord(eb, L->stream));
+        CK(cudaEventRecord(eb, st));
         L->pending.push_back({ea, eb, orx ? 4 : 3});
       }
       continue;
@@ -360,29 +372,63 @@ int enqueue_compound(coulps_lattice *L, int n_hb, int n_or, coulps_charges *fuse
         ea = take_event(L);
         eb = take_event(L);
         if (!ea || !eb) return COULPS_ECUDA;
-        CK(cudaEventRecord(ea, L->stream));
+        CK(cudaEventRecord(ea, st));
       }
-      CK(launch_halfsweep(L->g, L->tile, halo, L->tm_own, a, orx, L->stream));
+      CK(launch_halfsweep(L->g, L->tile, halo, L->tm_own, a, orx, st));
       if (L->profiling) {
-        CK(cudaEventRecord(eb, L->stream));
+        CK(cudaEventRecord(eb, st));
         L->pending.push_back({ea, eb, orx ? 1 : 0});
       }
     }
   }
   a.field = L->field;
-  if (n_hb + n_or > 0) CK(launch_advance_pass(L->d_pass, (uint32_t)(n_hb + n_or), L->stream));
+  const bool all = chain0 == 0 && stride == 1;
   if (gather_fused) {
-    CK(launch_finalize(fuse->d_fpart, fuse->fused_nblk, L->g.n_chains, fuse->d_stats, fuse->d_log,
-                       fuse->log_cap, L->d_err, L->stream));
+    if (all)
+      CK(launch_finalize(fuse->d_fpart, fuse->fused_nblk, L->g.n_chains, fuse->d_stats,
+                         fuse->d_log, fuse->log_cap, L->d_err, st));
+    else
+      CK(launch_finalize_group(fuse->d_fpart, fuse->fused_nblk, L->g.n_chains, chain0, stride,
+                               fuse->d_stats, fuse->d_log, fuse->log_cap, L->d_err, st));
   } else if (fuse) {
     // the compound sweep ended in a fused pass: the separate gather
-    CK(launch_gather(L->g, L->field, fuse->d_idx, fuse->d_q, fuse->n, fuse->d_partials,
-                     fuse->nblk, L->stream));
-    CK(launch_finalize(fuse->d_partials, fuse->nblk, L->g.n_chains, fuse->d_stats, fuse->d_log,
-                       fuse->log_cap, L->d_err, L->stream));
+    CK(launch_gather_group(L->g, L->field, fuse->d_idx, fuse->d_q, fuse->n, fuse->d_partials,
+                           fuse->nblk, chain0, stride, st));
+    if (all)
+      CK(launch_finalize(fuse->d_partials, fuse->nblk, L->g.n_chains, fuse->d_stats,
+                         fuse->d_log, fuse->log_cap, L->d_err, st));
+    else
+      CK(launch_finalize_group(fuse->d_partials, fuse->nblk, L->g.n_chains, chain0, stride,
+                               fuse->d_stats, fuse->d_log, fuse->log_cap, L->d_err, st));
   }
   return COULPS_OK;
 }
+
+// One compound sweep of every chain (and its sample when `fuse` is given).
+// With two streams the even chains run on the lattice's stream and the odd
+// ones on the second stream (forked from and joined back into the lattice's
+// stream, also under graph capture), so the two halves' heatbath and
+// over-relaxation kernels can share the GPU; each chain's passes, draws and
+// sample are unchanged.
+int enqueue_compound(coulps_lattice *L, int n_hb, int n_or, coulps_charges *fuse = nullptr) {
+  if (L->split == 2 && L->g.n_chains >= 2) {
+    CK(cudaEventRecord(L->ev_fork, L->stream));
+    CK(cudaStreamWaitEvent(L->stream2, L->ev_fork, 0));
+    int r = enqueue_part(L, L->stream2, n_hb, n_or, fuse, 1, 2);
+    if (!r) r = enqueue_part(L, L->stream, n_hb, n_or, fuse, 0, 2);
+    // join whatever was queued on the second stream, also on failure
+    CK(cudaEventRecord(L->ev_join, L->stream2));
+    CK(cudaStreamWaitEvent(L->stream, L->ev_join, 0));
+    if (r) return r;
+  } else {
+    int r = enqueue_part(L, L->stream, n_hb, n_or, fuse, 0, 1);
+    if (r) return r;
+  }
+  if (n_hb + n_or > 0) CK(launch_advance_pass(L->d_pass, (uint32_t)(n_hb + n_or), L->stream));
+  return COULPS_OK;
+}
+
+
 
 void drop_graph(coulps_lattice *L);
 
@@ -552,6 +598,8 @@ int enqueue_slot(coulps_lattice *L, coulps_charges *C, int n_hb, int n_or, int64
   MixedArgs m;
   std::memset(&m, 0, sizeof(m));
   SweepArgs &a = m.base;
+  a.chain0 = 0;
+  a.chain_stride = 1;
   a.field = L->field;
   a.Lx = L->g.Lx; a.Ly = L->g.Ly; a.Lz = L->g.Lz;
   a.W = L->g.W; a.Wq = L->g.Wq; a.QW = L->g.W / 4;
@@ -903,6 +951,12 @@ void coulps_lattice_destroy(coulps_lattice_t L) {
     cudaEventDestroy(t.b);
   }
   for (auto e : L->spare_events) cudaEventDestroy(e);
+  if (L->stream2) {
+    cudaStreamSynchronize(L->stream2);
+    cudaStreamDestroy(L->stream2);
+  }
+  if (L->ev_fork) cudaEventDestroy(L->ev_fork);
+  if (L->ev_join) cudaEventDestroy(L->ev_join);
   dev_free(L->alloc, L->field, L->stream);
   dev_free(L->alloc, L->field2, L->stream);
   dev_free(L->alloc, L->d_pass, L->stream);
@@ -1818,6 +1872,22 @@ int coulps_charges_update(coulps_charges_t C, const int32_t *site, const double 
   CK(cudaMemcpyAsync(C->d_q, C->h_q, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice,
                      L->stream));
   CK(cudaEventRecord(C->staged, L->stream));
+  return COULPS_OK;
+}
+
+int coulps_set_streams(coulps_lattice_t L, int n) {
+  if (!L || n < 1 || n > 2) return COULPS_EINVAL;
+  if (n == L->split) return COULPS_OK;
+  drop_graph(L);
+  if (n == 2 && !L->stream2) {
+    if (cudaStreamCreateWithFlags(&L->stream2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&L->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&L->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return COULPS_ECUDA;
+    }
+  }
+  L->split = n;
   return COULPS_OK;
 }
 

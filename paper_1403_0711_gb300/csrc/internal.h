@@ -54,10 +54,18 @@ __host__ __device__ inline PhiloxKeys philox_keys(uint32_t k0, uint32_t k1) {
   return K;
 }
 
+// Number of chains chain0, chain0 + stride, ... below n_chains (grid z).
+inline unsigned launch_chains(int n_chains, int chain0, int stride) {
+  return chain0 >= n_chains || stride < 1 ? 0u : (unsigned)((n_chains - chain0 + stride - 1) / stride);
+}
+
 struct SweepArgs {
   void *field;
   int Lx, Ly, Lz, W, Wq, QW, TY, DZ;
   int colour;
+  // chains of the launch: chain0, chain0 + chain_stride, ... < n_chains
+  // (grid z runs over them)
+  int chain0, chain_stride;
   uint32_t round_keys[20];  // Philox round keys of the lattice's seed
   const uint32_t *pass_ptr;  // device pass counter
   uint32_t pass_off;         // added to *pass_ptr
@@ -81,6 +89,7 @@ struct SweepArgs {
 struct PassArgs {
   void *dst;
   int Lx, Ly, Lz, W, Wq, QW, TY, DZ;
+  int chain0, chain_stride;  // chains of the launch, as in SweepArgs
   uint32_t round_keys[20];
   const uint32_t *pass_ptr;
   uint32_t pass_off;
@@ -107,6 +116,10 @@ struct MixedArgs {
 };
 cudaError_t launch_halfsweep_mixed(const Geometry &g, const Tile &t, const CUtensorMap &tm_halo,
                                    const CUtensorMap &tm_own, const MixedArgs &a, cudaStream_t s);
+// the gather for the chains first, first + stride, ... only
+cudaError_t launch_gather_group(const Geometry &g, const void *field, const uint32_t *idx,
+                                const double *q, int64_t n, double *partials, int nblk, int first,
+                                int stride, cudaStream_t s);
 cudaError_t launch_finalize_group(const double *partials, int nblk, int n_chains, int first,
                                   int stride, double *stats, double *log, int64_t log_cap,
                                   int *err, cudaStream_t s);

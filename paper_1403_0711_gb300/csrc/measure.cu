@@ -23,8 +23,8 @@ template <typename T>
 __global__ void __launch_bounds__(kGatherThreads)
     gather_kernel(const T *__restrict__ field, size_t chain_elems,
                   const uint32_t *__restrict__ idx, const double *__restrict__ q, int64_t n,
-                  double *__restrict__ partials, int nblk) {
-  const int chain = blockIdx.y;
+                  double *__restrict__ partials, int nblk, int first, int stride) {
+  const int chain = first + (int)blockIdx.y * stride;
   const T *f = field + (size_t)chain * chain_elems;
   double sq = 0.0, sp = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * kGatherThreads + threadIdx.x; i < n;
@@ -350,17 +350,27 @@ int gather_blocks(int64_t n) {
   return (int)b;
 }
 
+cudaError_t launch_gather_group(const Geometry &g, const void *field, const uint32_t *idx,
+                                const double *q, int64_t n, double *partials, int nblk, int first,
+                                int stride, cudaStream_t s) {
+  const unsigned count = launch_chains(g.n_chains, first, stride);
+  if (count == 0) return cudaSuccess;
+  dim3 grid(nblk, count);
+  if (g.precision == COULPS_F32)
+    gather_kernel<float><<<grid, kGatherThreads, 0, s>>>(
+        reinterpret_cast<const float *>(field), g.chain_elems, idx, q, n, partials, nblk, first,
+        stride);
+  else
+    gather_kernel<double><<<grid, kGatherThreads, 0, s>>>(
+        reinterpret_cast<const double *>(field), g.chain_elems, idx, q, n, partials, nblk, first,
+        stride);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_gather(const Geometry &g, const void *field, const uint32_t *idx,
                           const double *q, int64_t n, double *partials, int nblk,
                           cudaStream_t s) {
-  dim3 grid(nblk, g.n_chains);
-  if (g.precision == COULPS_F32)
-    gather_kernel<float><<<grid, kGatherThreads, 0, s>>>(
-        reinterpret_cast<const float *>(field), g.chain_elems, idx, q, n, partials, nblk);
-  else
-    gather_kernel<double><<<grid, kGatherThreads, 0, s>>>(
-        reinterpret_cast<const double *>(field), g.chain_elems, idx, q, n, partials, nblk);
-  return cudaGetLastError();
+  return launch_gather_group(g, field, idx, q, n, partials, nblk, 0, 1, s);
 }
 
 cudaError_t launch_finalize(const double *partials, int nblk, int n_chains, double *stats,

@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(512)
     return reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(newbuf) + (s & 1) * lay.new_bytes);
   };
 
-  const int chain = blockIdx.z;
+  const int chain = a.chain0 + (int)blockIdx.z * a.chain_stride;
   const int W = a.W, TY = a.TY;
   const int y0 = blockIdx.x * TY;
   const int z0 = blockIdx.y * a.DZ;
@@ -317,7 +317,8 @@ cudaError_t launch_pt(const Geometry &g, const Tile &t, const CUtensorMap &tm_c1
     if (e != cudaSuccess) return e;
     configured_bytes = (int)smem;
   }
-  dim3 grid((g.Ly + t.ty - 1) / t.ty, (g.Lz + t.dz - 1) / t.dz, g.n_chains);
+  dim3 grid((g.Ly + t.ty - 1) / t.ty, (g.Lz + t.dz - 1) / t.dz,
+            launch_chains(g.n_chains, a.chain0, a.chain_stride));
   dim3 block(pass_threads(g, t));
   kfn<<<grid, block, smem, s>>>(tm_c1, tm_c0, a);
   return cudaGetLastError();

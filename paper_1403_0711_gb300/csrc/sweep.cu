@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(256)
   extern __shared__ unsigned char smem_raw[];
   // 128-byte aligned base (the launch reserves 128 bytes of slack).
   unsigned char *smem = align_smem128(smem_raw);
-  const int chain = blockIdx.z;
+  const int chain = a.chain0 + (int)blockIdx.z * a.chain_stride;
   TileJob<T> j;
   j.tm_halo = &tm_halo;
   j.tm_own = &tm_own;
@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(256)
     halfsweep_mixed_kernel(const __grid_constant__ CUtensorMap tm_halo,
                            const __grid_constant__ CUtensorMap tm_own, const MixedArgs m) {
   const SweepArgs &a = m.base;
-  const int chain = blockIdx.z;
+  const int chain = a.chain0 + (int)blockIdx.z * a.chain_stride;
   const int grp = chain % m.groups;
   const int mode = m.mode[grp];
   if (mode == 0) return;
@@ -150,7 +150,8 @@ cudaError_t launch_mixed_t(const Geometry &g, const Tile &t, const CUtensorMap &
     if (e != cudaSuccess) return e;
     configured_bytes = (int)smem;
   }
-  dim3 grid((g.Ly + t.ty - 1) / t.ty, (g.Lz + t.dz - 1) / t.dz, g.n_chains);
+  dim3 grid((g.Ly + t.ty - 1) / t.ty, (g.Lz + t.dz - 1) / t.dz,
+            launch_chains(g.n_chains, m.base.chain0, m.base.chain_stride));
   kfn<<<grid, dim3((g.W / 4) * t.ty), smem, s>>>(tm_halo, tm_own, m);
   return cudaGetLastError();
 }
@@ -178,7 +179,8 @@ cudaError_t launch_t(const Geometry &g, const Tile &t, const CUtensorMap &tm_hal
     if (e != cudaSuccess) return e;
     configured_bytes = (int)smem;
   }
-  dim3 grid((g.Ly + t.ty - 1) / t.ty, (g.Lz + t.dz - 1) / t.dz, g.n_chains);
+  dim3 grid((g.Ly + t.ty - 1) / t.ty, (g.Lz + t.dz - 1) / t.dz,
+            launch_chains(g.n_chains, a.chain0, a.chain_stride));
   dim3 block((g.W / 4 + V - 1) / V * t.ty);
   kfn<<<grid, block, smem, s>>>(tm_halo, tm_own, a);
   return cudaGetLastError();
