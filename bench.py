@@ -61,8 +61,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--schedule", choices=["phased", "aligned"], default="aligned")
-    ap.add_argument("--streams", type=int, choices=[1, 2], default=2,
-                    help="2: odd chains on a second stream (coulps_set_streams)")
+    ap.add_argument("--streams", type=int, choices=[1, 2, 3, 4], default=2,
+                    help="chain k on stream k %% n (coulps_set_streams)")
     ap.add_argument("--fused", choices=["on", "all", "off"], default="on",
                     help="fused passes (one kernel per pass, ping-pong field copies): "
                          "over-relaxation passes (on), all passes, or none")

@@ -292,15 +292,15 @@ int coulps_pool_stats(const double *stats, int64_t n_rows, double *mean, double 
  * (memory-bound) of the others.  Every chain does exactly the same passes,
  * Philox draws and samples as with the aligned schedule (results are
  * bitwise identical); only the order across chains changes. */
-/* Two streams (n = 2): every compound sweep runs the even chains on the
- * lattice's stream and the odd chains on a second stream of the library's
- * own, forked from the lattice's stream at the start of the sweep and joined
- * back at its end (also inside captured graphs), so that the two halves'
- * heatbath (instruction-bound) and over-relaxation (memory-bound) kernels
- * can run at the same time.  Every chain's passes, Philox draws and samples
- * are unchanged (bitwise identical results); all work still completes in
- * order on the lattice's stream.  n = 1 (default): one stream.  Lattices of
- * one chain ignore it.  Not used by the phased schedule.
+/* Several streams (n = 2 .. 4): every compound sweep runs chain k on stream
+ * k % n, stream 0 being the lattice's and the others the library's own,
+ * forked from the lattice's stream at the start of the sweep and joined back
+ * at its end (also inside captured graphs), so that the groups' heatbath
+ * (instruction-bound) and over-relaxation (memory-bound) kernels can run at
+ * the same time.  Every chain's passes, Philox draws and samples are
+ * unchanged (bitwise identical results); all work still completes in order
+ * on the lattice's stream.  n = 1 (default): one stream.  At most n_chains
+ * streams are used.  Not used by the phased schedule.
  * Errors: EINVAL, ECUDA. */
 int coulps_set_streams(coulps_lattice_t lat, int n);
 

@@ -63,10 +63,11 @@ struct coulps_lattice {
   // heatbath pass then writes out of place)
   void *field2 = nullptr;
   CUtensorMap tm_halo2;  // halo map of field2 (tile ty + 2 rows)
-  // two streams: odd chains on stream2 (coulps_set_streams)
+  // split > 1 streams: chains k with k % split == j on stream j (stream 0 is
+  // the lattice's own; xstream[j - 1] the library's; coulps_set_streams)
   int split = 1;
-  cudaStream_t stream2 = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaStream_t xstream[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t ev_fork = nullptr, ev_join[3] = {nullptr, nullptr, nullptr};
   int fused = 0;  // 0 off, 1 over-relaxation passes, 2 all passes
   Tile ptile = {0, 0};
   CUtensorMap tm_p1[2], tm_p0[2];  // source field / field2; boxes ty + 4, ty + 2 rows
@@ -411,14 +412,20 @@ int enqueue_part(coulps_lattice *L, cudaStream_t st, int n_hb, int n_or, coulps_
 // over-relaxation kernels can share the GPU; each chain's passes, draws and
 // sample are unchanged.
 int enqueue_compound(coulps_lattice *L, int n_hb, int n_or, coulps_charges *fuse = nullptr) {
-  if (L->split == 2 && L->g.n_chains >= 2) {
+  const int k = L->split < L->g.n_chains ? L->split : L->g.n_chains;
+  if (k >= 2) {
     CK(cudaEventRecord(L->ev_fork, L->stream));
-    CK(cudaStreamWaitEvent(L->stream2, L->ev_fork, 0));
-    int r = enqueue_part(L, L->stream2, n_hb, n_or, fuse, 1, 2);
-    if (!r) r = enqueue_part(L, L->stream, n_hb, n_or, fuse, 0, 2);
-    // join whatever was queued on the second stream, also on failure
-    CK(cudaEventRecord(L->ev_join, L->stream2));
-    CK(cudaStreamWaitEvent(L->stream, L->ev_join, 0));
+    int r = COULPS_OK;
+    for (int j = 1; j < k; ++j) {
+      CK(cudaStreamWaitEvent(L->xstream[j - 1], L->ev_fork, 0));
+      if (!r) r = enqueue_part(L, L->xstream[j - 1], n_hb, n_or, fuse, j, k);
+    }
+    if (!r) r = enqueue_part(L, L->stream, n_hb, n_or, fuse, 0, k);
+    // join whatever was queued on the other streams, also on failure
+    for (int j = 1; j < k; ++j) {
+      CK(cudaEventRecord(L->ev_join[j - 1], L->xstream[j - 1]));
+      CK(cudaStreamWaitEvent(L->stream, L->ev_join[j - 1], 0));
+    }
     if (r) return r;
   } else {
     int r = enqueue_part(L, L->stream, n_hb, n_or, fuse, 0, 1);
@@ -951,12 +958,14 @@ void coulps_lattice_destroy(coulps_lattice_t L) {
     cudaEventDestroy(t.b);
   }
   for (auto e : L->spare_events) cudaEventDestroy(e);
-  if (L->stream2) {
-    cudaStreamSynchronize(L->stream2);
-    cudaStreamDestroy(L->stream2);
+  for (int j = 0; j < 3; ++j) {
+    if (L->xstream[j]) {
+      cudaStreamSynchronize(L->xstream[j]);
+      cudaStreamDestroy(L->xstream[j]);
+    }
+    if (L->ev_join[j]) cudaEventDestroy(L->ev_join[j]);
   }
   if (L->ev_fork) cudaEventDestroy(L->ev_fork);
-  if (L->ev_join) cudaEventDestroy(L->ev_join);
   dev_free(L->alloc, L->field, L->stream);
   dev_free(L->alloc, L->field2, L->stream);
   dev_free(L->alloc, L->d_pass, L->stream);
@@ -1876,13 +1885,18 @@ int coulps_charges_update(coulps_charges_t C, const int32_t *site, const double 
 }
 
 int coulps_set_streams(coulps_lattice_t L, int n) {
-  if (!L || n < 1 || n > 2) return COULPS_EINVAL;
+  if (!L || n < 1 || n > 4) return COULPS_EINVAL;
   if (n == L->split) return COULPS_OK;
   drop_graph(L);
-  if (n == 2 && !L->stream2) {
-    if (cudaStreamCreateWithFlags(&L->stream2, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&L->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&L->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+  if (n > 1 && !L->ev_fork &&
+      cudaEventCreateWithFlags(&L->ev_fork, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    return COULPS_ECUDA;
+  }
+  for (int j = 0; j < n - 1; ++j) {
+    if (!L->xstream[j] &&
+        (cudaStreamCreateWithFlags(&L->xstream[j], cudaStreamNonBlocking) != cudaSuccess ||
+         cudaEventCreateWithFlags(&L->ev_join[j], cudaEventDisableTiming) != cudaSuccess)) {
       cudaGetLastError();
       return COULPS_ECUDA;
     }

@@ -1,5 +1,6 @@
-"""Two streams per compound sweep (coulps_set_streams): the odd chains run on
-a second stream forked from and joined into the lattice's stream.  Fields,
+"""Several streams per compound sweep (coulps_set_streams): chain k runs on
+stream k % n, the extra streams forked from and joined into the lattice's
+stream.  Fields,
 samples and estimates must be bitwise those of the one-stream path, with
 graph replay and direct launches, every fused mode, multi-set measurement
 and the global control variate."""
@@ -39,7 +40,7 @@ def test_two_streams_bitwise(cl, stream, L, prec, chains, fused, n_hb, n_or, pro
     from paper_1403_0711_gb300 import inputs
     sites, q = inputs.uniform_q(L, 30, seed=5)
     out = []
-    for n in (1, 2):
+    for n in (1, 2, 3, 4):
         lat = cl.Lattice(L, n_chains=chains, precision=getattr(cl, prec), seed=41, stream=stream)
         lat.set_fused(fused)
         lat.set_streams(n)
@@ -52,11 +53,12 @@ def test_two_streams_bitwise(cl, stream, L, prec, chains, fused, n_hb, n_or, pro
                     lat.info()["pass"]))
         ch.close()
         lat.close()
-    a, b = out
-    assert np.array_equal(a[0], b[0])
-    for fa, fb in zip(a[1], b[1]):
-        assert np.array_equal(fa, fb)
-    assert a[2] == b[2] and a[3] == b[3]
+    a = out[0]
+    for b in out[1:]:
+        assert np.array_equal(a[0], b[0])
+        for fa, fb in zip(a[1], b[1]):
+            assert np.array_equal(fa, fb)
+        assert a[2] == b[2] and a[3] == b[3]
 
 
 def test_two_streams_sets_and_global_cv_bitwise(cl, stream):
@@ -64,7 +66,7 @@ def test_two_streams_sets_and_global_cv_bitwise(cl, stream):
     L = (20, 18, 16)
     sets = [inputs.plus_minus(L, 20, seed=1), inputs.uniform_q(L, 33, seed=2)]
     out = []
-    for n in (1, 2):
+    for n in (1, 2, 4):
         lat = cl.Lattice(L, n_chains=4, precision=cl.F32, seed=43, stream=stream)
         lat.set_streams(n)
         cs = [cl.Charges(lat, s, q, log_capacity=6) for s, q in sets]
@@ -76,7 +78,8 @@ def test_two_streams_sets_and_global_cv_bitwise(cl, stream):
         for c in cs:
             c.close()
         lat.close()
-    a, b = out
-    for x, y in zip(a[0], b[0]):
-        assert np.array_equal(x, y)
-    assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+    a = out[0]
+    for b in out[1:]:
+        for x, y in zip(a[0], b[0]):
+            assert np.array_equal(x, y)
+        assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
