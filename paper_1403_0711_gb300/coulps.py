@@ -434,7 +434,7 @@ class GlobalCV:
     n_iter SOR iterations on A h = -rho; with R > 0 also the local term of P
     (kernel radius R)."""
 
-    def __init__(self, charges, n_iter=None, R=2):
+    def __init__(self, charges, n_iter=None, R=1):
         self.charges = charges
         self._lib = load()
         L = charges.lattice.L
