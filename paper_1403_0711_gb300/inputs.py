@@ -91,6 +91,15 @@ def uniform_q(L, n, seed, qmax=1.0):
     return sites, q
 
 
+def gaussian_fields(L, n, seed, scale=0.5):
+    """n seeded test fields (Lz, Ly, Lx) of independent normal values times
+    scale (about the size of a sampled field's fluctuations), for comparing
+    field functions of the library and the oracle on the same inputs."""
+    Lx, Ly, Lz = L
+    rng = _rng(seed)
+    return [scale * rng.standard_normal((Lz, Ly, Lx)) for _ in range(n)]
+
+
 def off_lattice(L, n, seed, qmax=1.0):
     """n particles at real positions uniform in [0, L - 1] per axis (x, y, z),
     charges uniform in [-qmax, qmax]; a few are put on exact lattice points,

@@ -28,7 +28,8 @@ def stream():
     return torch.cuda.Stream()
 
 
-def test_h_and_stein_term_match_oracle(cl, stream):
+@pytest.mark.parametrize("R", [0, 1, 2])
+def test_h_and_stein_term_match_oracle(cl, stream, R):
     import torch
     from oracle import oracle as O
     from oracle import stein as ost
@@ -37,8 +38,10 @@ def test_h_and_stein_term_match_oracle(cl, stream):
     sites, q = inputs.uniform_q(L, 30, seed=4)
     lat = cl.Lattice(L, n_chains=3, precision=cl.F32, seed=8, stream=stream)
     ch = cl.Charges(lat, sites, q, log_capacity=4)
-    lat.sweep(30, 1, 2)
-    g = cl.GlobalCV(ch, n_iter=400, R=2)
+    fields = inputs.gaussian_fields(L, 3, seed=9)
+    for k, f in enumerate(fields):
+        lat.set_field(k, f)
+    g = cl.GlobalCV(ch, n_iter=400, R=R)
     info = g.info()
     assert info["residual"] < 1e-9
     rho = O.charge_density(L, sites, q)
@@ -50,10 +53,12 @@ def test_h_and_stein_term_match_oracle(cl, stream):
     g.eval(tg.data_ptr())
     lat.sync()
     tg = tg.cpu().numpy()
-    kc = ost.cube_green(2)
+    kc = ost.cube_green(R) if R > 0 else None
     for k in range(3):
-        phi = lat.field(k)
-        ref = ost.global_stein_term(phi, rho, h) + ost.local_p_stein_term(phi, sites, q, kc)
+        phi = fields[k].astype(np.float32).astype(np.float64)  # as stored (FP32 lattice)
+        ref = ost.global_stein_term(phi, rho, h)
+        if R > 0:
+            ref += ost.local_p_stein_term(phi, sites, q, kc)
         Q = float(np.sum(rho * phi))
         scale = abs(info["h_dot_rho"]) + abs(Q) * float(np.abs(ost.apply_A(h) * phi).sum())
         # v . phi: FP32 partial sums of 16 products, FP64 across them; k in FP32

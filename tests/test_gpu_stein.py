@@ -41,7 +41,9 @@ def test_evaluate_matches_autograd_path_and_oracle(env):
     L = (20, 12, 9)
     sites, q = inputs.uniform_q(L, 12, seed=3)
     lat = coulps.Lattice(L, n_chains=3, precision=coulps.F32, seed=5, stream=stream)
-    lat.sweep(20, 1, 1)
+    fields = inputs.gaussian_fields(L, 3, seed=6)
+    for k, f in enumerate(fields):
+        lat.set_field(k, f)
     rho = stein.charge_density(L, sites, q)
     cv = stein.SteinCV(seed=2, scale=0.6, w3_scale=0.1)
     tg_eval = cv.evaluate(lat, rho).cpu().numpy()
@@ -51,7 +53,7 @@ def test_evaluate_matches_autograd_path_and_oracle(env):
     p = _oracle_params(cv)
     r = rho.cpu().numpy().astype(np.float64)
     for k in range(3):
-        phi = lat.field(k)
+        phi = fields[k].astype(np.float32).astype(np.float64)  # as stored (FP32 lattice)
         div = ost.divergence(phi, r, p)
         gA = float(np.sum(ost.forward(phi, r, p)["g"] * ost.apply_A(phi)))
         scale = abs(div) + abs(gA)
@@ -140,7 +142,9 @@ def test_region_evaluate_matches_oracle(env):
     sites, q = inputs.uniform_q(L, 10, seed=8)
     sites[:3] = [[6, 5, 2], [9, 7, 4], [7, 8, 3]]  # some charges inside R
     lat = coulps.Lattice(L, n_chains=3, precision=coulps.F32, seed=15, stream=stream)
-    lat.sweep(20, 1, 1)
+    fields = inputs.gaussian_fields(L, 3, seed=16)
+    for k, f in enumerate(fields):
+        lat.set_field(k, f)
     rho = stein.charge_density(L, sites, q)
     cv = stein.LocalSteinCV(L, lo, hi, seed=2, scale=0.6, w3_scale=0.1)
     tg = cv.evaluate(lat, rho)
@@ -155,7 +159,7 @@ def test_region_evaluate_matches_oracle(env):
     region = ((lo[2], hi[2]), (lo[1], hi[1]), (lo[0], hi[0]))
     mask = ost.region_mask(r.shape, region)
     for k in range(3):
-        phi = lat.field(k)
+        phi = fields[k].astype(np.float32).astype(np.float64)  # as stored (FP32 lattice)
         div = ost.divergence(phi, r, p, region)
         gA = float(np.sum(ost.forward(phi, r, p)["g"] * mask * ost.apply_A(phi)))
         scale = abs(div) + abs(gA)
@@ -170,9 +174,12 @@ def test_region_pack_matches_field(env):
     torch, coulps, stream = env
     from oracle import stein as ost
     from paper_1403_0711_gb300 import stein
+    from paper_1403_0711_gb300 import inputs
     L = (17, 12, 10)
     lat = coulps.Lattice(L, n_chains=2, precision=coulps.F32, seed=3, stream=stream)
-    lat.sweep(10, 1, 0)
+    fields = inputs.gaussian_fields(L, 2, seed=4)
+    for k, f in enumerate(fields):
+        lat.set_field(k, f)
     rho = torch.zeros(L[2], L[1], L[0], device="cuda")
     rho[4, 5, 6] = 1.0
     cv = stein.LocalSteinCV(L, (5, 4, 3), (9, 8, 6))
@@ -180,14 +187,14 @@ def test_region_pack_matches_field(env):
     lat.sync()
     (x0_, y0_, z0_), (x1_, y1_, z1_) = cv.e_lo, cv.e_hi
     for k in range(2):
-        phi = lat.field(k)
+        phi = fields[k].astype(np.float32).astype(np.float64)  # as stored (FP32 lattice)
         sub = phi[z0_:z1_, y0_:y1_, x0_:x1_]
         got = x0[k, ..., 0].float().cpu().numpy()
         assert np.abs(got - sub).max() <= 2 ** -8 * np.abs(sub).max()
         assert np.abs(Aphi[k].cpu().numpy() - ost.apply_A(phi)[z0_:z1_, y0_:y1_, x0_:x1_]).max() < 1e-5
         assert np.array_equal(x0[k, ..., 1].float().cpu().numpy(), rho.cpu().numpy()[z0_:z1_, y0_:y1_, x0_:x1_])
         r_e = rho.cpu().numpy()[z0_:z1_, y0_:y1_, x0_:x1_]
-        want = torch.from_numpy((r_e * lat.field(k)[z0_:z1_, y0_:y1_, x0_:x1_]).astype(np.float32))
+        want = torch.from_numpy((r_e * phi[z0_:z1_, y0_:y1_, x0_:x1_]).astype(np.float32))
         got2 = x0[k, ..., 2].float().cpu()
         assert torch.equal(got2 != 0, want != 0)
         assert (got2 - want).abs().max() <= 2 ** -8 * want.abs().max()
