@@ -1487,31 +1487,56 @@ int coulps_charges_near(coulps_charges_t C, double rc, int64_t *n_pairs, double 
       std::find(L->mgraph_key.begin(), L->mgraph_key.end(), (const void *)C) != L->mgraph_key.end())
     drop_graph(L);
   CK(cudaStreamSynchronize(L->stream));
+  const int nc = L->g.n_chains;
+  const int row = C->nblk_g + (pairs > 0 ? near_blocks(n) : 0);
+  // the new device buffers first: if one cannot be had, the set keeps its
+  // previous near list and buffers unchanged
+  double *part = nullptr, *t = nullptr, *u = nullptr;
+  int64_t *dptr = nullptr;
+  uint32_t *dnbr = nullptr;
+  auto release = [&]() {
+    for (void *q : {(void *)part, (void *)t, (void *)u, (void *)dptr, (void *)dnbr})
+      dev_free(L->alloc, q, L->stream);
+  };
+  bool ok = true;
+  if (row != C->nblk) {
+    part = (double *)dev_alloc(L->alloc, sizeof(double) * 2 * (size_t)row * nc, L->stream);
+    ok = part != nullptr;
+  }
+  if (ok && pairs > 0) {
+    dptr = (int64_t *)dev_alloc(L->alloc, sizeof(int64_t) * ptr.size(), L->stream);
+    dnbr = (uint32_t *)dev_alloc(L->alloc, sizeof(uint32_t) * nbr.size(), L->stream);
+    t = (double *)dev_alloc(L->alloc, sizeof(double) * (size_t)n * nc, L->stream);
+    u = (double *)dev_alloc(L->alloc, sizeof(double) * (size_t)n * nc, L->stream);
+    ok = dptr && dnbr && t && u;
+    if (ok && (cudaMemcpyAsync(dptr, ptr.data(), sizeof(int64_t) * ptr.size(),
+                               cudaMemcpyHostToDevice, L->stream) != cudaSuccess ||
+               cudaMemcpyAsync(dnbr, nbr.data(), sizeof(uint32_t) * nbr.size(),
+                               cudaMemcpyHostToDevice, L->stream) != cudaSuccess)) {
+      cudaGetLastError();
+      release();
+      return COULPS_ECUDA;
+    }
+  }
+  if (!ok) {
+    release();
+    return COULPS_ENOMEM;
+  }
+  // swap in the new list
   for (void **q : {(void **)&C->d_nptr, (void **)&C->d_nbr, (void **)&C->d_t, (void **)&C->d_u}) {
     dev_free(L->alloc, *q, L->stream);
     *q = nullptr;
   }
-  C->n_pairs = 0;
-  const int nc = L->g.n_chains;
-  const int row = C->nblk_g + (pairs > 0 ? near_blocks(n) : 0);
   if (row != C->nblk) {
     dev_free(L->alloc, C->d_partials, L->stream);
-    C->d_partials = (double *)dev_alloc(L->alloc, sizeof(double) * 2 * (size_t)row * nc, L->stream);
+    C->d_partials = part;
     C->nblk = row;
-    if (!C->d_partials) return COULPS_ENOMEM;
   }
-  if (pairs > 0) {
-    C->d_nptr = (int64_t *)dev_alloc(L->alloc, sizeof(int64_t) * ptr.size(), L->stream);
-    C->d_nbr = (uint32_t *)dev_alloc(L->alloc, sizeof(uint32_t) * nbr.size(), L->stream);
-    C->d_t = (double *)dev_alloc(L->alloc, sizeof(double) * (size_t)n * nc, L->stream);
-    C->d_u = (double *)dev_alloc(L->alloc, sizeof(double) * (size_t)n * nc, L->stream);
-    if (!C->d_nptr || !C->d_nbr || !C->d_t || !C->d_u) return COULPS_ENOMEM;
-    CK(cudaMemcpyAsync(C->d_nptr, ptr.data(), sizeof(int64_t) * ptr.size(),
-                       cudaMemcpyHostToDevice, L->stream));
-    CK(cudaMemcpyAsync(C->d_nbr, nbr.data(), sizeof(uint32_t) * nbr.size(),
-                       cudaMemcpyHostToDevice, L->stream));
-    C->n_pairs = pairs;
-  }
+  C->d_nptr = dptr;
+  C->d_nbr = dnbr;
+  C->d_t = t;
+  C->d_u = u;
+  C->n_pairs = pairs;
   int st = coulps_reset_stats(C);
   if (st) return st;
   CK(launch_reset_stats(C->d_cvstats, nc, L->stream));
