@@ -304,6 +304,7 @@ class Charges:
     def __init__(self, lattice: Lattice, sites, q, log_capacity=0, _handle=None):
         self._lib = load()
         self.lattice = lattice
+        self.log_capacity = int(log_capacity)
         if _handle is not None:
             self.n = len(q)
             self.handle = _handle
@@ -331,7 +332,7 @@ class Charges:
         _check(lib.coulps_charges_create_off(lattice.handle, len(qq), _f64p(p), _f64p(qq),
                                              int(log_capacity), int(bool(forces)),
                                              ctypes.byref(h)), "coulps_charges_create_off")
-        return cls(lattice, None, qq, _handle=h)
+        return cls(lattice, None, qq, log_capacity=log_capacity, _handle=h)
 
     def near(self, rc):
         """Leave the pairs closer than rc out of every sample; returns their
@@ -379,7 +380,7 @@ class Charges:
         """(n_samples, n_chains, 3) array of logged (Q, P, e)."""
         nc = self.lattice.n_chains
         if cap is None:
-            cap = 1 << 20
+            cap = max(1, self.log_capacity)
         buf = np.empty((cap, nc, 3), dtype=np.float64)
         n = ctypes.c_int64()
         _check(self._lib.coulps_samples(self.handle, _f64p(buf), int(cap), ctypes.byref(n)),
