@@ -121,6 +121,20 @@ int coulps_sweep(coulps_lattice_t lat, int n_compound, int n_hb, int n_or);
 /* Wait for the lattice's stream and report any recorded device error. */
 int coulps_sync(coulps_lattice_t lat);
 
+/* Failure detection.  Every wait inside the library's kernels (mbarrier
+ * phases of the TMA rings) is bounded by %globaltimer time; a wait that
+ * gives up records COULPS_ETIMEOUT in the lattice's error word, lets its
+ * copies in flight land and returns, so the context stays usable and the
+ * next coulps_sync / coulps_estimate reports the error.  The word stays set
+ * (the fields may be partly updated) until coulps_clear_error, typically after
+ * restoring a checkpoint.
+ * coulps_selftest_wait queues, on the lattice's stream, a kernel that waits
+ * for a flag nothing sets and gives up after limit_ns (1 us .. 1 s) exactly
+ * like those waits: it exercises the failure path without touching the
+ * fields.  Errors: EINVAL, ECUDA. */
+int coulps_selftest_wait(coulps_lattice_t lat, int64_t limit_ns);
+int coulps_clear_error(coulps_lattice_t lat);
+
 /* ---- charge sets and the estimator ------------------------------------- */
 /* Register n point charges q[i] at sites site_xyz[3i..3i+2] of lattice `lat`
  * (copied; the arrays are the caller's).  All chains of the lattice are

@@ -44,7 +44,7 @@ EXPORTS = (
     "coulps_gcv_info", "coulps_gcv_h", "coulps_gcv_eval", "coulps_gcv_run",
     "coulps_charges_create_off", "coulps_forces", "coulps_charges_near",
     "coulps_heatbath_noise", "coulps_near_pairs", "coulps_offlattice_corners",
-    "coulps_set_streams",
+    "coulps_set_streams", "coulps_selftest_wait", "coulps_clear_error",
 )
 SCHEDULE_ALIGNED, SCHEDULE_PHASED = 0, 1
 STAT_STRIDE = 72
@@ -94,6 +94,8 @@ def load(path: str | Path | None = None):
         "coulps_charges_near": (i32, [vp, ctypes.c_double, P(i64), P(f64), P(f64)]),
         "coulps_heatbath_noise": (i32, [i32, vp, vp, i64, vp]),
         "coulps_set_streams": (i32, [vp, i32]),
+        "coulps_selftest_wait": (i32, [vp, i64]),
+        "coulps_clear_error": (i32, [vp]),
         "coulps_near_pairs": (i32, [i64, P(f64), ctypes.c_double, P(i64), P(ctypes.c_uint32), i64,
                                     P(i64)]),
         "coulps_offlattice_corners": (i32, [i32, i32, i32, i32, i64, P(f64),
@@ -260,6 +262,13 @@ class Lattice:
 
     def sync(self):
         _check(self._lib.coulps_sync(self.handle), "coulps_sync")
+
+    def selftest_wait(self, limit_ns):
+        """Queue a bounded wait that times out (coulps_selftest_wait)."""
+        _check(self._lib.coulps_selftest_wait(self.handle, int(limit_ns)), "coulps_selftest_wait")
+
+    def clear_error(self):
+        _check(self._lib.coulps_clear_error(self.handle), "coulps_clear_error")
 
     def set_profiling(self, enable=True):
         _check(self._lib.coulps_set_profiling(self.handle, int(bool(enable))), "coulps_set_profiling")

@@ -14,6 +14,7 @@
 #include <new>
 #include <vector>
 
+#include "device_common.cuh"
 #include "internal.h"
 
 using namespace coulps;
@@ -243,6 +244,25 @@ Tile default_tile(const Geometry &g) {
   while (ty > 1 && qw * ty > 1024) --ty;
   int dz = g.Lz < 16 ? g.Lz : 16;
   return Tile{ty, dz};
+}
+
+// Self-test of the failure path of a bounded device wait: one thread polls a
+// word that nothing ever sets, gives up after limit_ns of %globaltimer time
+// and records a timeout in the lattice's error word, as every sweep kernel's
+// bounded mbarrier wait does.
+__device__ int g_never_set = 0;
+
+__global__ void selftest_wait_kernel(int *err, uint64_t limit_ns) {
+  if (threadIdx.x != 0) return;
+  volatile int *flag = &g_never_set;
+  const uint64_t t0 = global_timer_ns();
+  while (*flag == 0) {
+    if (global_timer_ns() - t0 > limit_ns) {
+      atomicOr(err, kErrTimeout);
+      return;
+    }
+    __nanosleep(1000);
+  }
 }
 
 int check_device_error(coulps_lattice *L) {
@@ -1006,6 +1026,20 @@ int coulps_set_tile(coulps_lattice_t L, int ty, int dz) {
 int coulps_sync(coulps_lattice_t L) {
   if (!L) return COULPS_EINVAL;
   return check_device_error(L);
+}
+
+int coulps_selftest_wait(coulps_lattice_t L, int64_t limit_ns) {
+  if (!L || limit_ns < 1000 || limit_ns > 1000000000) return COULPS_EINVAL;
+  selftest_wait_kernel<<<1, 32, 0, L->stream>>>(L->d_err, (uint64_t)limit_ns);
+  CK(cudaGetLastError());
+  return COULPS_OK;
+}
+
+int coulps_clear_error(coulps_lattice_t L) {
+  if (!L) return COULPS_EINVAL;
+  CK(cudaMemsetAsync(L->d_err, 0, sizeof(int), L->stream));
+  CK(cudaStreamSynchronize(L->stream));
+  return COULPS_OK;
 }
 
 int coulps_field_get(coulps_lattice_t L, int chain, double *host) {
