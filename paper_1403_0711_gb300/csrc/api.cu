@@ -426,11 +426,11 @@ int enqueue_part(coulps_lattice *L, cudaStream_t st, int n_hb, int n_or, coulps_
 }
 
 // One compound sweep of every chain (and its sample when `fuse` is given).
-// With two streams the even chains run on the lattice's stream and the odd
-// ones on the second stream (forked from and joined back into the lattice's
-// stream, also under graph capture), so the two halves' heatbath and
-// over-relaxation kernels can share the GPU; each chain's passes, draws and
-// sample are unchanged.
+// With k > 1 streams chain c runs on stream c % k: stream 0 is the lattice's,
+// the others are forked from it at the start and joined back at the end
+// (also under graph capture), so the groups' heatbath and over-relaxation
+// kernels can share the GPU; each chain's passes, draws and sample are
+// unchanged.  The pass counter is advanced once, after the join.
 int enqueue_compound(coulps_lattice *L, int n_hb, int n_or, coulps_charges *fuse = nullptr) {
   const int k = L->split < L->g.n_chains ? L->split : L->g.n_chains;
   if (k >= 2) {
