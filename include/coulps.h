@@ -141,7 +141,8 @@ int coulps_clear_error(coulps_lattice_t lat);
  * measured against this set.  Coincident sites are allowed.  log_capacity
  * samples of (Q, P, e) per chain are kept on the device for
  * coulps_samples (0 = keep none).  Errors: EINVAL (site outside the box,
- * n < 0, non-finite q), ENOMEM, ECUDA. */
+ * n < 0, non-finite q), EUNSUPPORTED (a chain's field holds more than 2^32
+ * elements: sites are kept as 32-bit offsets), ENOMEM, ECUDA. */
 int coulps_charges_create(coulps_lattice_t lat, int64_t n, const int32_t *site_xyz,
                           const double *q, int64_t log_capacity, coulps_charges_t *out);
 
@@ -226,7 +227,8 @@ int coulps_charges_update(coulps_charges_t ch, const int32_t *site_xyz, const do
  * coulps_reset_stats (which also clears the force sums); coulps_charges_update
  * and coulps_gcv_create return EUNSUPPORTED.  Errors: EINVAL (a position
  * outside the box or not finite, a dimension < 2, non-finite q, n < 0),
- * ENOMEM, ECUDA. */
+ * EUNSUPPORTED (a chain's field holds more than 2^32 elements), ENOMEM,
+ * ECUDA. */
 int coulps_charges_create_off(coulps_lattice_t lat, int64_t n, const double *pos_xyz,
                               const double *q, int64_t log_capacity, int forces,
                               coulps_charges_t *out);

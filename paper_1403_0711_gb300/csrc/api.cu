@@ -1103,6 +1103,8 @@ int coulps_charges_create(coulps_lattice_t L, int64_t n, const int32_t *site, co
   if (n > 0 && (!site || !q)) return COULPS_EINVAL;
   if (n > (int64_t)1 << 31) return COULPS_EINVAL;
   const Geometry &g = L->g;
+  // charge sites are kept as 32-bit offsets within one chain's field
+  if (g.chain_elems > 0xffffffffull) return COULPS_EUNSUPPORTED;
   std::vector<uint32_t> idx((size_t)n);
   for (int64_t i = 0; i < n; ++i) {
     const int x = site[3 * i], y = site[3 * i + 1], z = site[3 * i + 2];
@@ -1428,6 +1430,7 @@ int coulps_charges_create_off(coulps_lattice_t L, int64_t n, const double *pos, 
   if (n > ((int64_t)1 << 28)) return COULPS_EINVAL;
   const Geometry &g = L->g;
   if (g.Lx < 2 || g.Ly < 2 || g.Lz < 2) return COULPS_EINVAL;
+  if (g.chain_elems > 0xffffffffull) return COULPS_EUNSUPPORTED;  // 32-bit corner offsets
   for (int64_t i = 0; i < n; ++i)
     if (!std::isfinite(q[i])) return COULPS_EINVAL;
   // corners, trilinear weights and their gradients, in FP64 on the host
