@@ -343,9 +343,12 @@ int coulps_set_fused(coulps_lattice_t lat, int enable);
 int coulps_set_pass_tile(coulps_lattice_t lat, int ty, int dz);
 
 /* ---- kernel timing ----------------------------------------------------- */
-/* With profiling on, every half-sweep launched by coulps_sweep (and by
- * coulps_run, which then launches directly instead of replaying its graph)
- * is bracketed by CUDA events on the lattice stream.  coulps_kernel_times
+/* With profiling on, every half-sweep and fused pass launched by
+ * coulps_sweep (and by coulps_run, which then launches directly instead of
+ * replaying its graph) is bracketed by CUDA events on the stream it runs on
+ * (the lattice's, or with coulps_set_streams the chain group's; launches of
+ * different groups then overlap, so their durations do not isolate one
+ * kernel: time kernels on one stream).  coulps_kernel_times
  * synchronises and returns, since profiling was enabled or last read:
  *   out[0] total ms of heatbath half-sweeps, out[1] their count,
  *   out[2] total ms of over-relaxation half-sweeps, out[3] their count,
