@@ -49,7 +49,9 @@ CONFIG = {
 PROFILE_TRAFFIC = {
     "pass_kernel<float, over-relaxation>": ROOT / "profiles" / "pass_or_128c_64ch.txt",
 }
-KERNEL_SOURCES = ["sweep.cu", "pass_fused.cu", "tile_march.cuh", "device_common.cuh", "internal.h"]
+KERNEL_SOURCES = ["sweep.cu", "pass_fused.cu", "pass_pair.cu", "tile_march.cuh",
+                  "device_common.cuh", "internal.h"]
+FUSED_MODES = {"off": 0, "on": 1, "all": 2, "pairs": 3, "allpairs": 4}
 
 
 def parse():
@@ -63,9 +65,16 @@ def parse():
     ap.add_argument("--schedule", choices=["phased", "aligned"], default="aligned")
     ap.add_argument("--streams", type=int, choices=[1, 2, 3, 4], default=2,
                     help="chain k on stream k %% n (coulps_set_streams)")
-    ap.add_argument("--fused", choices=["on", "all", "off"], default="on",
-                    help="fused passes (one kernel per pass, ping-pong field copies): "
-                         "over-relaxation passes (on), all passes, or none")
+    ap.add_argument("--fused", choices=["pairs", "allpairs", "on", "all", "off"], default="pairs",
+                    help="fused passes (ping-pong field copies): over-relaxation passes two per "
+                         "kernel (pairs, the default), all passes two per kernel (allpairs), "
+                         "over-relaxation passes one per kernel (on), all passes one per kernel "
+                         "(all), or none")
+    ap.add_argument("--repeats", type=int, default=5,
+                    help="timed repetitions of the step loop after the timed region (spread)")
+    ap.add_argument("--extras", choices=["on", "off"], default="on",
+                    help="secondary configurations in the headline line (256 systems, 512^3, "
+                         "learned control variate on the q = 1 cube)")
     ap.add_argument("--cv-steps", type=int, default=800, help="training steps of the learned CV")
     ap.add_argument("--gcv-radius", type=int, default=1,
                     help="local term of P in the global control variate, kernel radius "
@@ -416,7 +425,7 @@ def run_ours(args):
     sites, q = inputs.plus_minus(box, N_CHARGES, seed=1)
     lat = coulps.Lattice(box, n_chains=n_chains, precision=coulps.F32, seed=20140303 + 7919 * rank,
                          stream=stream)
-    lat.set_fused({"off": 0, "on": 1, "all": 2}[args.fused])
+    lat.set_fused(FUSED_MODES[args.fused])
     ch = coulps.Charges(lat, sites, q)
 
     # Measured compound sweeps (the sample is gathered by the last half-sweep of
@@ -434,22 +443,28 @@ def run_ours(args):
     lat.sync()
     ch.reset_stats()  # the timed samples alone feed the time-to-accuracy projection
 
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
+    # the K timed steps in up to five chunks, an event at each boundary: the
+    # whole region gives the value, the chunks its spread
+    n_chunks = max(1, min(5, args.steps))
+    bounds = [round(args.steps * i / n_chunks) for i in range(n_chunks + 1)]
+    evs = [torch.cuda.Event(enable_timing=True) for _ in bounds]
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks = Clocks(local)
     clocks.start()
     time.sleep(0.3)  # let the sampler start
-    ev0.record(stream)
-    ch.run(0, args.steps, N_HB, N_OR)
-    ev1.record(stream)
+    evs[0].record(stream)
+    for i in range(n_chunks):
+        ch.run(0, bounds[i + 1] - bounds[i], N_HB, N_OR)
+        evs[i + 1].record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
     if world > 1:
         torch.distributed.barrier()
-    ms = ev0.elapsed_time(ev1)
+    ms = evs[0].elapsed_time(evs[-1])
+    chunk_ms = [evs[i].elapsed_time(evs[i + 1]) / (bounds[i + 1] - bounds[i])
+                for i in range(n_chunks) if bounds[i + 1] > bounds[i]]
     lat.sync()
     t = torch.tensor([ms], dtype=torch.float64, device="cuda")
     if world > 1:
@@ -457,7 +472,6 @@ def run_ours(args):
     ms_max = float(t.item())
     value = world * sites_per_step * args.steps / (ms_max / 1e3)
     est_timed = ch.estimate()
-    tta = time_to_accuracy(est_timed, ms_max / 1e3, world)
 
     # Per-kernel durations: CUDA events around every launch, on one stream
     # (with two streams the halves' kernels overlap, so a launch's duration
@@ -473,43 +487,63 @@ def run_ours(args):
     lat.set_profiling(False)
     lat.set_streams(args.streams)
 
-    # roofline of the dominant kernel.  Algorithmic bytes per updated site:
-    # half-sweeps: heatbath 8 (read the other colour, write), over-relaxation
-    # 12 (also read the old value); fused passes: 8 per site and pass (read
-    # both colours once, write both once)
+    # roofline of the dominant kernel (largest share of the device time of a
+    # step).  Algorithmic bytes per launch: a half-sweep reads the other
+    # colour and writes its own (heatbath, 8 B per updated site) and also
+    # reads its old value (over-relaxation, 12 B); a fused pass and a pass pair
+    # read every site once and write it once (8 B per site, for one pass or
+    # for two); the mixed half-sweep of the phased schedule is counted as its
+    # share of 8 / 12 B per updated site.
     peak, peak_kind = measured_peaks()
-    sites_per_launch = n_chains * L ** 3 // 2
-    if kt["pass_or_n"] > 0:
-        pass_bytes = 8 * n_chains * L ** 3
-        or_ms = kt["pass_or_ms"] / kt["pass_or_n"]
-        achieved = pass_bytes / (or_ms / 1e3) / 1e9
-        name = "pass_kernel<float, over-relaxation>"
-        dom = {"kernel": name, "algorithmic_bytes_per_launch": pass_bytes, "avg_launch_ms": or_ms,
-               "heatbath_pass_avg_launch_ms": kt["pass_hb_ms"] / max(1, kt["pass_hb_n"]),
-               "heatbath_halfsweep_avg_launch_ms": kt["hb_ms"] / max(1, kt["hb_n"]),
-               "overrelax_halfsweep_avg_launch_ms": kt["or_ms"] / max(1, kt["or_n"])}
-        traffic = profiled_traffic(name)
-    elif kt["mixed_n"] > 0:
-        total_bytes = n_rf * n_chains * (8 * N_HB + 12 * N_OR) * L ** 3
-        mixed_ms = kt["mixed_ms"] / kt["mixed_n"]
-        achieved = total_bytes / (kt["mixed_ms"] / 1e3) / 1e9
-        dom = {"kernel": "halfsweep_mixed_kernel<float> (phase-shifted heatbath + over-relaxation)",
-               "algorithmic_bytes_per_launch": total_bytes / kt["mixed_n"],
-               "avg_launch_ms": mixed_ms, "launches": kt["mixed_n"]}
-        traffic = None
-    else:
-        or_ms = kt["or_ms"] / max(1, kt["or_n"])
-        achieved = 12 * sites_per_launch / (or_ms / 1e3) / 1e9
-        name = "halfsweep_kernel<float, over-relaxation>"
-        dom = {"kernel": name,
-               "algorithmic_bytes_per_launch": 12 * sites_per_launch, "avg_launch_ms": or_ms,
-               "heatbath_avg_launch_ms": kt["hb_ms"] / max(1, kt["hb_n"])}
-        traffic = profiled_traffic(name)
+    n_sites = n_chains * L ** 3
+    kinds = {
+        "hb": ("halfsweep_kernel<float, heatbath>", 8 * n_sites // 2),
+        "or": ("halfsweep_kernel<float, over-relaxation>", 12 * n_sites // 2),
+        "pass_hb": ("pass_kernel<float, heatbath>", 8 * n_sites),
+        "pass_or": ("pass_kernel<float, over-relaxation>", 8 * n_sites),
+        "pair_hb": ("pair_kernel<float, heatbath pass in the pair>", 8 * n_sites),
+        "pair_or": ("pair_kernel<float, over-relaxation, over-relaxation>", 8 * n_sites),
+        "mixed": ("halfsweep_mixed_kernel<float> (phase-shifted heatbath + over-relaxation)",
+                  n_sites // 2 * (8 * N_HB + 12 * N_OR) // PASSES),
+    }
+    total_ms = sum(kt[k + "_ms"] for k in kinds)
+    dom_kind = max(kinds, key=lambda k: kt[k + "_ms"])
+    name, bytes_per_launch = kinds[dom_kind]
+    avg_ms = kt[dom_kind + "_ms"] / max(1, kt[dom_kind + "_n"])
+    achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
+    dom = {"kernel": name, "algorithmic_bytes_per_launch": bytes_per_launch,
+           "avg_launch_ms": avg_ms,
+           "share_of_sweep_kernel_time": kt[dom_kind + "_ms"] / total_ms if total_ms else None,
+           "launches_per_compound_sweep": {k: kt[k + "_n"] / n_rf for k in kinds if kt[k + "_n"]},
+           "avg_launch_ms_by_kind": {k: kt[k + "_ms"] / kt[k + "_n"] for k in kinds
+                                     if kt[k + "_n"]},
+           "sweep_kernel_ms_per_compound_sweep": total_ms / n_rf}
+    traffic = profiled_traffic(name)
     roofline = dict({"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": f"{peak_kind} (burst copy)",
                      "timing": f"CUDA events around every launch, one stream, {n_rf} compound "
                                "sweeps after the timed region"}, **dom)
+    sweep_launches = sum(kt[k + "_n"] for k in kinds) / n_rf  # all chains, one stream
+
+    # spread: the step loop timed again, --repeats times, right after the
+    # timed region (same graph, same streams)
+    rep_ms = []
+    n_rep_steps = max(args.steps, 100)
+    for _ in range(max(0, args.repeats)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ch.run(0, n_rep_steps, N_HB, N_OR)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rep_ms.append(e0.elapsed_time(e1) / n_rep_steps)
+    repeats = None
+    if rep_ms:
+        repeats = {"steps_each": n_rep_steps, "ms_per_step": rep_ms,
+                   "median_ms_per_step": statistics.median(rep_ms),
+                   "min_ms_per_step": min(rep_ms), "max_ms_per_step": max(rep_ms),
+                   "median_site_updates_per_s": world * sites_per_step /
+                   (statistics.median(rep_ms) / 1e3)}
 
     # end to end through the C ABI with host buffers: upload the charge set
     # from host memory, one measured compound sweep (graph replay), read back
@@ -538,9 +572,14 @@ def run_ours(args):
            "steps": args.e2e_steps,
            "path": "coulps_charges_update + coulps_run(0, 1, 1, 3) + coulps_estimate"}
 
-    # time to 1e-3 with the global control variate g = Q h (projected from a
-    # short run; bench.py --workload gcv measures it directly)
-    tta_cv = None
+    # time to 1e-3, plain and with the global control variate g = Q h, both
+    # projected from the same args.gcv_steps compound sweeps of every chain
+    # (bench.py --workload gcv measures the latter directly): the plain
+    # estimator of those samples at the plain cost per sweep of the timed
+    # region, the control variate at its own measured cost
+    tta, tta_cv = None, None
+    if args.gcv_steps <= 0:
+        tta = time_to_accuracy(est_timed, ms_max / 1e3, world)
     if args.gcv_steps > 0:
         ch.reset_stats()
         ch.cv_reset()
@@ -548,6 +587,8 @@ def run_ours(args):
         t0 = time.perf_counter()
         gcv = coulps.GlobalCV(ch, R=args.gcv_radius)
         setup = time.perf_counter() - t0
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
         gcv.run(args.gcv_steps, N_HB, N_OR, 1.0)
         ev1.record(stream)
@@ -555,6 +596,11 @@ def run_ours(args):
         cv_s = ev0.elapsed_time(ev1) / 1e3
         est_cv, est_pl = ch.cv_estimate(), ch.estimate()
         e_lat = golden_e_lat("bench_128c_n4096_pm")
+        tta = time_to_accuracy(est_pl, args.gcv_steps * (ms_max / args.steps) / 1e3, world)
+        if tta:
+            tta["estimator"] = ("plain Eq. (nsum2), batch means over all chains, on the "
+                                f"{est_pl['n'] * world} samples of the control-variate run, "
+                                "timed at the plain cost per compound sweep")
         if est_cv["stderr"] > 0 and est_pl["stderr"] > 0:
             t_cv = cv_s * (est_cv["stderr"] / (1e-3 * abs(e_lat))) ** 2
             tta_cv = {"eps": 1e-3,
@@ -568,20 +614,26 @@ def run_ours(args):
                       "error_variance_ratio_vs_plain_same_samples":
                           (est_cv["stderr"] / est_pl["stderr"]) ** 2,
                       "projected_seconds": t_cv + setup, "projected_hours": (t_cv + setup) / 3600}
+            if tta:
+                tta_cv["plain_over_cv_time"] = tta["projected_seconds"] / tta_cv["projected_seconds"]
         gcv.close()
+
+    extras = None
+    if rank == 0 and world == 1 and args.extras == "on":
+        ch.close()
+        lat.close()
+        ch = lat = None
+        torch.cuda.empty_cache()
+        extras = {"batched_256_systems": batched_throughput(args, stream, steps=50),
+                  "large_512_1e6_charges": large_throughput(args, stream, 512, steps=20),
+                  "learned_cv_q1_cube": cv_local_cube(args, stream, seconds=60.0)}
 
     out = None
     if rank == 0:
-        # per compound sweep: nf fused passes, 2 (PASSES - nf) half-sweeps, a
-        # gather when the sweep ends in a fused pass, finalize, advance
-        # (mode "on" fuses an odd N_OR whole when a heatbath pass precedes it)
-        nf_on = N_OR if (N_OR % 2 == 1 and N_HB > 0) else N_OR & ~1
-        nf = {"off": 0, "on": nf_on, "all": PASSES & ~1}[args.fused]
-        ends_fused = nf > 0 and (args.fused == "all" or nf == N_OR)
-        # (with two streams each half of the chains has its own sweep kernels,
-        # gather and finalize; one pass-counter advance per sweep)
-        per_half = nf + 2 * (PASSES - nf) + (1 if ends_fused else 0) + 1
-        launches = args.steps * (args.streams * per_half + 1)
+        # per step and half of the chains (two streams: each half has its own
+        # sweep kernels and finalize): the sweep kernels counted by the
+        # profiled sweeps above, one finalize; one pass-counter advance per step
+        launches = int(round(args.steps * (args.streams * (sweep_launches + 1) + 1)))
         line = {
             "metric": METRIC, "value": value, "unit": "site-updates/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
@@ -589,7 +641,11 @@ def run_ours(args):
             "data": "synthetic", "config": dict(CONFIG, parallelism=f"replicas{world}", n_chains_per_gpu=n_chains,
                                            fused_passes=args.fused, streams=args.streams),
             "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+            "timed_chunks": {"ms_per_step": chunk_ms, "median": statistics.median(chunk_ms),
+                             "min": min(chunk_ms), "max": max(chunk_ms)},
+            "repeats": repeats,
             "time_to_1e-3": tta, "time_to_1e-3_cv": tta_cv, "estimate_after_e2e": est,
+            "secondary_configs": extras,
         }
         if world == 1:
             rate, cores, n = cpu_oracle_rate(args.cpu_seconds)
@@ -598,12 +654,72 @@ def run_ours(args):
                 "sample": f"{n} compound sweeps (1 HB + 3 OR) + samples of one 128^3 chain, "
                           "FP64 oracle, OpenMP over z planes"}
         out = line
-    ch.close()
-    lat.close()
+    if ch is not None:
+        ch.close()
+        lat.close()
     if world > 1:
         torch.distributed.destroy_process_group()
     if out is not None:
         print(json.dumps(out), flush=True)
+
+
+def batched_throughput(args, stream, steps):
+    """256 independent systems in one persistent launch per half-sweep (one
+    CUDA graph per measured compound sweep): edges from {32,48,64,80,96}, N
+    log-uniform in [64, 2048], q in [-1, 1] shifted to zero net, FP32,
+    1 HB : 3 OR, the sample of every system each compound sweep."""
+    import torch
+
+    from paper_1403_0711_gb300 import coulps, inputs
+    systems = inputs.batch_systems(256, seed=7)
+    b = coulps.Batch([L_ for L_, _, _ in systems], precision=coulps.F32, seed=77, stream=stream)
+    b.set_charges([(s_, q_) for _, s_, q_ in systems])
+    info = b.info()
+    rate, ms = _timed(stream, lambda: b.run(0, 1, N_HB, N_OR), info["sites"] * PASSES, steps, 10)
+    r = {"systems": 256, "sites": info["sites"], "tiles": info["tiles"],
+         "persistent_ctas": info["grid"], "site_updates_per_s": rate, "ms_per_step": ms,
+         "steps": steps,
+         "algorithmic_GBps_halfsweep_bytes": rate / PASSES * (8 + 12 * N_OR) / 1e9}
+    b.close()
+    torch.cuda.empty_cache()
+    return r
+
+
+def large_throughput(args, stream, n, steps):
+    """One n^3 chain (FP32 field, FP64 sums), charges in 200 Gaussian blobs
+    (sigma = 6 sites), q in [-0.8, 0.8] shifted to zero net: 10^6 charges at
+    512^3, else the same density N / L^3 = 0.00745; 1 HB : 3 OR measured
+    compound sweeps on the default schedule."""
+    import torch
+
+    from paper_1403_0711_gb300 import coulps, inputs
+    box = (n, n, n)
+    nq = 1_000_000 if n == 512 else int(round(0.00745 * n ** 3))
+    sites, q = inputs.blobs(box, nq, seed=3)
+    lat = coulps.Lattice(box, n_chains=1, precision=coulps.F32, seed=77, stream=stream)
+    ch = coulps.Charges(lat, sites, q)
+    rate, ms = _timed(stream, lambda: ch.run(0, 1, N_HB, N_OR), n ** 3 * PASSES, steps, 5)
+    r = {"L": n, "n_charges": nq, "site_updates_per_s": rate, "ms_per_step": ms, "steps": steps,
+         "fused_mode": lat.info()["fused"]}
+    ch.close()
+    lat.close()
+    torch.cuda.empty_cache()
+    return r
+
+
+def _timed(stream, step, sites_per_step, steps, warmup):
+    import torch
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    return sites_per_step * steps / (ms / 1e3), ms / steps
 
 
 def run_extra(args):
@@ -619,46 +735,13 @@ def run_extra(args):
     coulps.use_torch_allocator()
     stream = torch.cuda.Stream()
     results = []
-
-    def timed(step, sites_per_step, steps, warmup):
-        for _ in range(warmup):
-            step()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(steps):
-            step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        return sites_per_step * steps / (ms / 1e3), ms / steps
-
     if args.workload in ("large512", "sweep"):
         sizes = [512] if args.workload == "large512" else [128, 256, 384, 512]
         for n in sizes:
-            box = (n, n, n)
-            nq = 1_000_000 if n == 512 else int(round(0.00745 * n ** 3))
-            sites, q = inputs.blobs(box, nq, seed=3)
-            lat = coulps.Lattice(box, n_chains=1, precision=coulps.F32, seed=77, stream=stream)
-            ch = coulps.Charges(lat, sites, q)
-            steps = max(20, min(args.steps, int(2e10 / n ** 3)))
-            rate, ms = timed(lambda: ch.run(0, 1, N_HB, N_OR), n ** 3 * PASSES, steps, 5)
-            results.append({"L": n, "n_charges": nq, "site_updates_per_s": rate, "ms_per_step": ms,
-                            "algorithmic_GBps": rate / PASSES * (8 + 12 * N_OR) / N_HB / 1e9
-                            if N_HB == 1 else None})
-            ch.close()
-            lat.close()
+            results.append(large_throughput(args, stream, n,
+                                            max(20, min(args.steps, int(2e10 / n ** 3)))))
     elif args.workload == "batched":
-        systems = inputs.batch_systems(256, seed=7)
-        b = coulps.Batch([L_ for L_, _, _ in systems], precision=coulps.F32, seed=77, stream=stream)
-        b.set_charges([(s_, q_) for _, s_, q_ in systems])
-        info = b.info()
-        rate, ms = timed(lambda: b.run(0, 1, N_HB, N_OR), info["sites"] * PASSES, args.steps, 10)
-        results.append({"systems": 256, "sites": info["sites"], "tiles": info["tiles"],
-                        "persistent_ctas": info["grid"], "site_updates_per_s": rate,
-                        "ms_per_step": ms,
-                        "algorithmic_GBps": rate / PASSES * (8 + 12 * N_OR) / 1e9})
-        b.close()
+        results.append(batched_throughput(args, stream, args.steps))
     elif args.workload == "gcv":
         results.append(gcv_time_to_accuracy(args, stream))
     elif args.workload == "paper":
@@ -681,7 +764,7 @@ def cv_experiment(args, stream):
     return out
 
 
-def cv_local_cube(args, stream):
+def cv_local_cube(args, stream, seconds=None):
     """Localized learned Stein control variate on the paper's Fig. 2 geometry
     (N = 8 charges q = 1 in a cube at the centre of a 128^3 box): g is the net
     within --cv-halo sites of the charges, evaluated on that sub-box only.
@@ -746,7 +829,8 @@ def cv_local_cube(args, stream):
     t0 = time.perf_counter()
     rounds = 0
     cvest = None
-    while time.perf_counter() - t0 < args.cube_seconds:
+    limit = args.cube_seconds if seconds is None else seconds
+    while time.perf_counter() - t0 < limit:
         for _ in range(250):
             ch.run(0, 1, N_HB, N_OR)
             cv_step()

@@ -329,18 +329,40 @@ int coulps_set_schedule(coulps_lattice_t lat, int schedule);
  * of 12 for over-relaxation), from the field into a second copy of it or
  * back: the lattice then holds two copies (twice the field memory).  Within
  * a compound sweep one block of consecutive passes is fused, and the sweep
- * starts and ends in the lattice's field: enable = 1 (default) fuses the
+ * starts and ends in the lattice's field: enable = 1 fuses the
  * over-relaxation passes (all of them when n_or is even or n_hb >= 1: with
  * an odd n_or the first heatbath pass writes the second copy, at no extra
  * traffic, and the fused block ends in the field; all but the last when
  * n_or is odd and n_hb = 0), enable = 2 all passes (an even number of them),
- * enable = 0 none (and frees the second copy).  Results are bitwise those of the half-sweep
- * path (same arithmetic per site, same Philox counters).  Not used by the
- * phased schedule.  coulps_set_pass_tile: ty rows of y per CTA (the CTA also
- * computes one halo row each side: (ty + 2) * W / 4 threads <= 512), dz
- * planes of z per CTA (0 = keep).  Errors: EINVAL, ENOMEM, ECUDA. */
+ * enable = 3 (default) over-relaxation pass pairs: two consecutive passes in one
+ * kernel that reads the field once and writes it once for both (4 bytes per
+ * site and pass in FP32); the heatbath passes run as half-sweeps, the
+ * over-relaxation passes as n_or / 2 pairs and n_or mod 2 single fused
+ * passes (an odd number of these kernels after a heatbath pass: that pass
+ * writes the second copy as in enable = 1; with no heatbath pass one pair
+ * becomes two single passes, and a lone pass runs as half-sweeps).
+ * enable = 4 all passes as pairs, heatbath ones included, followed by single
+ * fused passes so that the number of kernels is even (n = 1 pass: two
+ * half-sweeps; n mod 4 = 0: n / 2 pairs; 1: (n - 3) / 2 pairs + 3 singles;
+ * 2: n / 2 - 1 pairs + 2 singles; 3: (n - 1) / 2 pairs + 1 single).  Rows
+ * too wide for a pair CTA (fewer than 4 rows fit) run enable = 3 as 1 and
+ * 4 as 2.  enable = 0 none (and frees the second copy).  Results are bitwise those of
+ * the half-sweep path (same arithmetic per site, same Philox counters).  The
+ * sample of a measured compound sweep is gathered by its last kernel.  Not
+ * used by the phased schedule.  coulps_set_pass_tile: ty rows of y per CTA
+ * (the CTA also computes one halo row each side: (ty + 2) * W / 4 threads
+ * <= 512), dz planes of z per CTA (0 = keep).  Errors: EINVAL, ENOMEM,
+ * ECUDA. */
 int coulps_set_fused(coulps_lattice_t lat, int enable);
 int coulps_set_pass_tile(coulps_lattice_t lat, int ty, int dz);
+
+/* Pass-pair tile (enable = 3, 4): ty rows of y per CTA, which also computes
+ * three halo rows each side ((ty + 6) * W / 4 threads <= 512 in FP32, 256 in
+ * FP64; ty + 8 <= 256; shared memory within 227 KiB), dz planes of z per CTA
+ * (0 = keep).  coulps_pair_tile writes the current (ty, dz), (0, 0) when the
+ * lattice has no pair tile.  Errors: EINVAL. */
+int coulps_set_pair_tile(coulps_lattice_t lat, int ty, int dz);
+int coulps_pair_tile(coulps_lattice_t lat, int32_t out[2]);
 
 /* ---- kernel timing ----------------------------------------------------- */
 /* With profiling on, every half-sweep and fused pass launched by
@@ -355,9 +377,13 @@ int coulps_set_pass_tile(coulps_lattice_t lat, int ty, int dz);
  *   out[4] total ms of mixed half-sweeps (phased schedule), out[5] their count,
  *   out[6] total ms of fused heatbath passes, out[7] their count,
  *   out[8] total ms of fused over-relaxation passes, out[9] their count,
- * and restarts the accumulation. */
+ * and restarts the accumulation.  coulps_kernel_times_n writes the first n
+ * of these and further kinds, zero past the last one:
+ *   out[10] total ms of pass pairs with a heatbath pass, out[11] their count,
+ *   out[12] total ms of over-relaxation pass pairs, out[13] their count. */
 int coulps_set_profiling(coulps_lattice_t lat, int enable);
 int coulps_kernel_times(coulps_lattice_t lat, double out[10]);
+int coulps_kernel_times_n(coulps_lattice_t lat, double *out, int n);
 
 /* ---- checkpoint -------------------------------------------------------- */
 /* Save / restore the full sampler state: fields of all chains, the pass

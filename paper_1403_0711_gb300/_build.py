@@ -21,7 +21,7 @@ BUILD = PKG.parent / "_build"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",
            "-I", str(CSRC), "-I", str(INCLUDE)]
-SOURCES = ["sweep.cu", "pass_fused.cu", "measure.cu", "api.cu", "measure_static.cu", "batch.cu",
+SOURCES = ["sweep.cu", "pass_fused.cu", "pass_pair.cu", "measure.cu", "api.cu", "measure_static.cu", "batch.cu",
            "cv_conv.cu", "cv_ops.cu", "gcv.cu"]
 
 

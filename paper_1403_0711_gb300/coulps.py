@@ -45,6 +45,7 @@ EXPORTS = (
     "coulps_charges_create_off", "coulps_forces", "coulps_charges_near",
     "coulps_heatbath_noise", "coulps_near_pairs", "coulps_offlattice_corners",
     "coulps_set_streams", "coulps_selftest_wait", "coulps_clear_error",
+    "coulps_set_pair_tile", "coulps_pair_tile", "coulps_kernel_times_n",
 )
 SCHEDULE_ALIGNED, SCHEDULE_PHASED = 0, 1
 STAT_STRIDE = 72
@@ -152,6 +153,9 @@ def load(path: str | Path | None = None):
         "coulps_gcv_run": (i32, [vp, i32, i32, i32, f64]),
         "coulps_run_sets": (i32, [vp, P(vp), i32, i32, i32, i32, i32]),
         "coulps_set_pass_tile": (i32, [vp, i32, i32]),
+        "coulps_set_pair_tile": (i32, [vp, i32, i32]),
+        "coulps_pair_tile": (i32, [vp, P(i32)]),
+        "coulps_kernel_times_n": (i32, [vp, P(f64), i32]),
         "coulps_cv_charge_term": (i32, [vp, vp, vp, vp, vp, i32, i32, P(ctypes.c_int32), i32, vp,
                                         i64, vp, vp]),
     }
@@ -275,12 +279,14 @@ class Lattice:
 
     def kernel_times(self):
         """{'hb_ms', 'hb_n', 'or_ms', 'or_n', 'mixed_ms', 'mixed_n', 'pass_hb_ms',
-        'pass_hb_n', 'pass_or_ms', 'pass_or_n'} since the last call."""
-        a = (ctypes.c_double * 10)()
-        _check(self._lib.coulps_kernel_times(self.handle, a), "coulps_kernel_times")
+        'pass_hb_n', 'pass_or_ms', 'pass_or_n', 'pair_hb_ms', 'pair_hb_n', 'pair_or_ms',
+        'pair_or_n'} since the last call (coulps_kernel_times_n)."""
+        a = (ctypes.c_double * 14)()
+        _check(self._lib.coulps_kernel_times_n(self.handle, a, 14), "coulps_kernel_times_n")
         return {"hb_ms": a[0], "hb_n": int(a[1]), "or_ms": a[2], "or_n": int(a[3]),
                 "mixed_ms": a[4], "mixed_n": int(a[5]), "pass_hb_ms": a[6], "pass_hb_n": int(a[7]),
-                "pass_or_ms": a[8], "pass_or_n": int(a[9])}
+                "pass_or_ms": a[8], "pass_or_n": int(a[9]), "pair_hb_ms": a[10],
+                "pair_hb_n": int(a[11]), "pair_or_ms": a[12], "pair_or_n": int(a[13])}
 
     def set_streams(self, n):
         """1 or 2 streams per compound sweep (coulps_set_streams)."""
@@ -290,13 +296,24 @@ class Lattice:
         _check(self._lib.coulps_set_schedule(self.handle, int(schedule)), "coulps_set_schedule")
 
     def set_fused(self, mode):
-        """Fused passes (one kernel per pass, two copies of the field): 0/False
-        off, 1/True the over-relaxation passes (default), 2 all passes."""
+        """Fused passes (two copies of the field): 0/False off, 1/True the
+        over-relaxation passes one kernel per pass, 2 all passes one kernel per
+        pass, 3 over-relaxation passes two per kernel (pass pairs), 4 all
+        passes as pass pairs (coulps_set_fused)."""
         _check(self._lib.coulps_set_fused(self.handle, int(mode)), "coulps_set_fused")
 
     def set_pass_tile(self, ty, dz=0):
         _check(self._lib.coulps_set_pass_tile(self.handle, int(ty), int(dz)),
                "coulps_set_pass_tile")
+
+    def set_pair_tile(self, ty, dz=0):
+        _check(self._lib.coulps_set_pair_tile(self.handle, int(ty), int(dz)),
+               "coulps_set_pair_tile")
+
+    def pair_tile(self):
+        a = (ctypes.c_int32 * 2)()
+        _check(self._lib.coulps_pair_tile(self.handle, a), "coulps_pair_tile")
+        return int(a[0]), int(a[1])
 
     def checkpoint_save(self, path, charges=None):
         _check(self._lib.coulps_checkpoint_save(self.handle, charges.handle if charges else None,

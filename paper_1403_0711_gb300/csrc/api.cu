@@ -69,9 +69,14 @@ struct coulps_lattice {
   int split = 1;
   cudaStream_t xstream[3] = {nullptr, nullptr, nullptr};
   cudaEvent_t ev_fork = nullptr, ev_join[3] = {nullptr, nullptr, nullptr};
-  int fused = 0;  // 0 off, 1 over-relaxation passes, 2 all passes
+  int fused = 0;  // 0 off, 1 over-relaxation passes, 2 all passes, 3 over-relaxation
+                  // pass pairs, 4 all passes as pairs (pass_plan)
   Tile ptile = {0, 0};
   CUtensorMap tm_p1[2], tm_p0[2];  // source field / field2; boxes ty + 4, ty + 2 rows
+  // pass pairs (pass_pair.cu): tile ({0, 0} when the row is too wide for a
+  // pair CTA) and maps on field / field2 with boxes ty + 8 and ty + 6 rows
+  Tile qtile = {0, 0};
+  CUtensorMap tm_q1[2], tm_q0[2];
   size_t bytes = 0;
   int n_charge_sets = 0;
   // measured compound sweep captured as a graph
@@ -84,11 +89,13 @@ struct coulps_lattice {
   struct Timed {
     cudaEvent_t a, b;
     int kind;  // 0 heatbath, 1 over-relaxation, 2 mixed (phase-shifted schedule),
-               // 3 fused heatbath pass, 4 fused over-relaxation pass
+               // 3 fused heatbath pass, 4 fused over-relaxation pass,
+               // 5 pass pair with a heatbath pass, 6 over-relaxation pass pair
   };
   std::vector<cudaEvent_t> spare_events;
   std::vector<Timed> pending;
-  double times[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  static constexpr int kTimeSlots = 14;
+  double times[kTimeSlots] = {0};
   // measured-phase schedule (COULPS_SCHEDULE_*) and its steady-state graph
   int schedule = COULPS_SCHEDULE_ALIGNED;
   cudaGraphExec_t sgraph = nullptr;
@@ -222,6 +229,24 @@ Tile default_pass_tile(const Geometry &g) {
   return Tile{ty, dz};
 }
 
+// Pass-pair tile: the CTA computes ty + 6 rows (3 halo rows each side) of
+// W / 4 quads, one thread per quad, within 512 threads (FP32) or 256 (FP64);
+// {0, 0} when fewer than 4 rows fit (the halo would dominate).  z slabs of
+// 64 planes from Lz = 128 (measured at 128^3 x 64 chains, two streams: 0.802
+// ms per 1 HB : 3 OR compound sweep against 0.828 with 32 planes).
+Tile default_pair_tile(const Geometry &g) {
+  const int qw = g.W / 4;
+  const int max_threads = g.precision == COULPS_F32 ? kPairMaxThreads32 : kPairMaxThreads64;
+  int ty = max_threads / qw - 6;
+  if (ty > g.Ly) ty = g.Ly;
+  if (ty > 248) ty = 248;  // TMA box rows ty + 8 <= 256
+  const int dz = g.Lz >= 128 ? 64 : (g.Lz >= 64 ? 32 : g.Lz);
+  while (ty >= 1 && pair_smem_bytes(g, Tile{ty, dz}, true) > 227 * 1024) --ty;
+  if (ty < 4 && ty < g.Ly) return Tile{0, 0};
+  if (ty < 1) return Tile{0, 0};
+  return Tile{ty, dz};
+}
+
 int rebuild_pass_maps(coulps_lattice *L) {
   if (!L->fused) return COULPS_OK;
   for (int b = 0; b < 2; ++b) {
@@ -230,8 +255,80 @@ int rebuild_pass_maps(coulps_lattice *L) {
     if (st) return st;
     st = make_map(&L->tm_p0[b], L->g, base, L->ptile.ty + 2);
     if (st) return st;
+    if (L->fused >= 3 && L->qtile.ty > 0) {
+      st = make_map(&L->tm_q1[b], L->g, base, L->qtile.ty + 8);
+      if (st) return st;
+      st = make_map(&L->tm_q0[b], L->g, base, L->qtile.ty + 6);
+      if (st) return st;
+    }
   }
   return COULPS_OK;
+}
+
+// Trips of n >= 2 passes run as pass pairs: `pairs` pass pairs, then
+// `singles` fused single passes, with pairs + singles even so that the
+// passes, which flip between the two copies on every trip, end in the copy
+// they started from.
+void pair_plan(int n, int &pairs, int &singles) {
+  switch (n % 4) {
+    case 0: pairs = n / 2; singles = 0; break;
+    case 1: pairs = (n - 3) / 2; singles = 3; break;
+    case 2: pairs = n / 2 - 1; singles = 2; break;
+    default: pairs = (n - 1) / 2; singles = 1; break;
+  }
+}
+
+// How the passes of one compound sweep run: passes [0, head) as
+// half-sweeps (in place on the field, or, with flip, the first one out of
+// place into field2 and the rest in place there), then `pairs` pass pairs and
+// `singles` fused single passes (the trips, alternating between the copies,
+// from field2 with flip and from the field otherwise, ending in the field),
+// then the remaining passes as in-place half-sweeps on the field.
+struct PassPlan {
+  int head = 0;
+  bool flip = false;
+  int pairs = 0, singles = 0;
+};
+
+PassPlan pass_plan(const coulps_lattice *L, int n_hb, int n_or) {
+  const int n = n_hb + n_or;
+  PassPlan P;
+  const bool pairs_ok = L->qtile.ty > 0;
+  int mode = L->fused;
+  if (mode == 3 && !pairs_ok) mode = 1;
+  if (mode == 4 && !pairs_ok) mode = 2;
+  if (mode == 1 || mode == 3) {
+    // heatbath passes as half-sweeps, the over-relaxation block as trips
+    P.head = n_hb;
+    int d = mode == 3 ? n_or / 2 : 0, s = mode == 3 ? n_or % 2 : n_or;
+    if ((d + s) % 2 == 1) {
+      if (n_hb > 0) {
+        P.flip = true;  // the heatbath passes write field2: an odd trip count ends in the field
+      } else if (d >= 1) {
+        d -= 1;
+        s += 2;
+      } else {
+        s -= 1;  // one pass left: it runs as half-sweeps after the trips
+      }
+    }
+    P.pairs = d;
+    P.singles = s;
+  } else if (mode == 2) {
+    P.singles = n & ~1;
+  } else if (mode == 4 && n >= 2) {
+    pair_plan(n, P.pairs, P.singles);
+  }
+  return P;
+}
+
+// The tile by which the last kernel of a measured compound sweep (aligned
+// schedule) gathers Q and P: the pass pair's, the fused pass's, or the
+// half-sweep's.
+Tile fused_gather_tile(const coulps_lattice *L, int n_hb, int n_or) {
+  const int n = n_hb + n_or;
+  const PassPlan P = pass_plan(L, n_hb, n_or);
+  if (P.head + 2 * P.pairs + P.singles < n || P.pairs + P.singles == 0) return L->tile;
+  return P.singles > 0 ? L->ptile : L->qtile;
 }
 
 Tile default_tile(const Geometry &g) {
@@ -293,8 +390,9 @@ cudaEvent_t take_event(coulps_lattice *L) {
 }
 
 // The passes of one compound sweep for the chains chain0, chain0 + stride,
-// ... on stream `st`, with their measurement when `fuse` is given (the pass
-// counter is advanced by the caller).
+// ... on stream `st`, with their measurement when `fuse` is given: its Q, P
+// are gathered by the sweep's last kernel, by the tile fused_gather_tile
+// names (the pass counter is advanced by the caller).
 int enqueue_part(coulps_lattice *L, cudaStream_t st, int n_hb, int n_or, coulps_charges *fuse,
                  int chain0, int stride) {
   SweepArgs a;
@@ -317,109 +415,117 @@ int enqueue_part(coulps_lattice *L, cudaStream_t st, int n_hb, int n_or, coulps_
   a.g_q = nullptr;
   a.g_partials = nullptr;
   const int n_pass = n_hb + n_or;
-  // fused passes: one block of consecutive passes, run field -> field2 ->
-  // field ...; the others are in-place half-sweeps.  Mode 1: the
-  // over-relaxation passes (the heatbath, ALU-bound, gains nothing from the
-  // saved traffic); mode 2: all passes, an even number of them.  In mode 1 an
-  // odd number of over-relaxation passes is fused whole when a heatbath pass
-  // precedes them: that pass is written out of place (colour 0 from field
-  // into field2, colour 1 within field2; a heatbath update does not read the
-  // site's old value, so this moves no extra bytes), further heatbath passes
-  // run in place on field2, and the fused block goes field2 -> field -> ...
-  // -> field.
-  int f0 = 0, nf = 0;
-  bool flip = false;
-  if (L->fused == 1) {
-    f0 = n_hb;
-    nf = n_or & ~1;
-    if ((n_or & 1) && n_hb > 0) {
-      nf = n_or;
-      flip = true;
-    }
-  } else if (L->fused == 2) {
-    nf = n_pass & ~1;
+  if (fuse) {
+    // the charges must be grouped by the tile of the kernel that gathers
+    const Tile gt = fused_gather_tile(L, n_hb, n_or);
+    if (fuse->gather_dirty || fuse->gather_tile.ty != gt.ty || fuse->gather_tile.dz != gt.dz)
+      return COULPS_EINVAL;
   }
   PassArgs p;
   p.chain0 = chain0;
   p.chain_stride = stride;
   p.Lx = a.Lx; p.Ly = a.Ly; p.Lz = a.Lz;
   p.W = a.W; p.Wq = a.Wq; p.QW = a.QW;
-  p.TY = L->ptile.ty; p.DZ = L->ptile.dz;
   for (int i = 0; i < 20; ++i) p.round_keys[i] = a.round_keys[i];
   p.pass_ptr = L->d_pass;
   p.chain_elems = a.chain_elems;
   p.colour_elems = a.colour_elems;
   p.err = L->d_err;
-  const bool gather_fused = fuse && !(nf > 0 && f0 + nf == n_pass);
-  for (int i = 0; i < n_pass; ++i) {
-    const bool orx = i >= n_hb;
-    const uint32_t off = (uint32_t)i;
-    if (i >= f0 && i < f0 + nf) {
-      const int b = (i - f0 + (flip ? 1 : 0)) & 1;  // source copy
-      p.dst = b ? L->field : L->field2;
-      p.pass_off = off;
-      cudaEvent_t ea = nullptr, eb = nullptr;
-      if (L->profiling) {
-        ea = take_event(L);
-        eb = take_event(L);
-        if (!ea || !eb) return COULPS_ECUDA;
-        CK(cudaEventRecord(ea, st));
-      }
-      CK(launch_pass(L->g, L->ptile, L->tm_p1[b], L->tm_p0[b], p, orx, st));
-      if (L->profiling) {
-        CK(cudaEventRecord(eb, st));
-        L->pending.push_back({ea, eb, orx ? 4 : 3});
-      }
-      continue;
+  p.g_off = nullptr;
+  p.g_ent = nullptr;
+  p.g_q = nullptr;
+  p.g_partials = nullptr;
+  auto set_gather = [&](PassArgs &q) {
+    q.g_off = fuse->d_goff;
+    q.g_ent = fuse->d_gent;
+    q.g_q = fuse->d_gq;
+    q.g_partials = fuse->d_fpart;
+  };
+  auto timed = [&](int kind, auto &&launch) -> int {
+    cudaEvent_t ea = nullptr, eb = nullptr;
+    if (L->profiling) {
+      ea = take_event(L);
+      eb = take_event(L);
+      if (!ea || !eb) return COULPS_ECUDA;
+      CK(cudaEventRecord(ea, st));
     }
-    // heatbath passes ahead of an odd fused block write field2 (see above)
-    const bool on2 = flip && i < f0;
+    CK(launch());
+    if (L->profiling) {
+      CK(cudaEventRecord(eb, st));
+      L->pending.push_back({ea, eb, kind});
+    }
+    return COULPS_OK;
+  };
+
+  const PassPlan plan = pass_plan(L, n_hb, n_or);
+  const int trips = plan.pairs + plan.singles;
+  const int tail0 = plan.head + 2 * plan.pairs + plan.singles;  // first pass of the tail
+  // one pass as two half-sweeps: on2 -- the pass runs on field2 (heatbath
+  // passes ahead of trips that start from field2: the first of them reads
+  // colour 1 from the field and writes colour 0 into field2, a heatbath update
+  // does not read the site's old value, so this moves no extra bytes)
+  auto half_sweeps = [&](int i, bool on2, bool gather) -> int {
+    const bool orx = i >= n_hb;
     a.field = on2 ? L->field2 : L->field;
     for (int c = 0; c < 2; ++c) {
       a.colour = c;
-      a.pass_off = off;
+      a.pass_off = (uint32_t)i;
       // the other colour's rows come from field, except once field2 holds
       // them: colour 1 of the first pass, and every later pass
       const CUtensorMap &halo = on2 && (i > 0 || c == 1) ? L->tm_halo2 : L->tm_halo;
-      if (gather_fused && i == n_pass - 1 && c == 1) {
-        // last half-sweep of the compound sweep: gather Q, P in the same pass
+      if (gather && c == 1) {
         a.g_off = fuse->d_goff;
         a.g_ent = fuse->d_gent;
         a.g_q = fuse->d_gq;
         a.g_partials = fuse->d_fpart;
       }
-      cudaEvent_t ea = nullptr, eb = nullptr;
-      if (L->profiling) {
-        ea = take_event(L);
-        eb = take_event(L);
-        if (!ea || !eb) return COULPS_ECUDA;
-        CK(cudaEventRecord(ea, st));
-      }
-      CK(launch_halfsweep(L->g, L->tile, halo, L->tm_own, a, orx, st));
-      if (L->profiling) {
-        CK(cudaEventRecord(eb, st));
-        L->pending.push_back({ea, eb, orx ? 1 : 0});
-      }
+      const int r = timed(orx ? 1 : 0, [&]() {
+        return launch_halfsweep(L->g, L->tile, halo, L->tm_own, a, orx, st);
+      });
+      if (r) return r;
     }
+    a.field = L->field;
+    return COULPS_OK;
+  };
+  for (int i = 0; i < plan.head; ++i) {
+    const int r = half_sweeps(i, plan.flip, fuse && trips == 0 && tail0 == n_pass && i == n_pass - 1);
+    if (r) return r;
   }
-  a.field = L->field;
-  const bool all = chain0 == 0 && stride == 1;
-  if (gather_fused) {
-    if (all)
+  // trips: pass pairs, then single fused passes, each from one copy to the other
+  int i = plan.head;
+  for (int t = 0; t < trips; ++t) {
+    const int b = (t + (plan.flip ? 1 : 0)) & 1;  // source copy: 0 the field, 1 field2
+    p.dst = b ? L->field : L->field2;
+    p.pass_off = (uint32_t)i;
+    if (fuse && t == trips - 1 && tail0 == n_pass) set_gather(p);
+    int r;
+    if (t < plan.pairs) {
+      const bool a_or = i >= n_hb, b_or = i + 1 >= n_hb;
+      p.TY = L->qtile.ty; p.DZ = L->qtile.dz;
+      r = timed(a_or && b_or ? 6 : 5, [&]() {
+        return launch_pair(L->g, L->qtile, L->tm_q1[b], L->tm_q0[b], p, a_or, b_or, st);
+      });
+      i += 2;
+    } else {
+      const bool orx = i >= n_hb;
+      p.TY = L->ptile.ty; p.DZ = L->ptile.dz;
+      r = timed(orx ? 4 : 3, [&]() {
+        return launch_pass(L->g, L->ptile, L->tm_p1[b], L->tm_p0[b], p, orx, st);
+      });
+      i += 1;
+    }
+    if (r) return r;
+  }
+  for (; i < n_pass; ++i) {
+    const int r = half_sweeps(i, false, fuse && i == n_pass - 1);
+    if (r) return r;
+  }
+  if (fuse && n_pass > 0) {
+    if (chain0 == 0 && stride == 1)
       CK(launch_finalize(fuse->d_fpart, fuse->fused_nblk, L->g.n_chains, fuse->d_stats,
                          fuse->d_log, fuse->log_cap, L->d_err, st));
     else
       CK(launch_finalize_group(fuse->d_fpart, fuse->fused_nblk, L->g.n_chains, chain0, stride,
-                               fuse->d_stats, fuse->d_log, fuse->log_cap, L->d_err, st));
-  } else if (fuse) {
-    // the compound sweep ended in a fused pass: the separate gather
-    CK(launch_gather_group(L->g, L->field, fuse->d_idx, fuse->d_q, fuse->n, fuse->d_partials,
-                           fuse->nblk, chain0, stride, st));
-    if (all)
-      CK(launch_finalize(fuse->d_partials, fuse->nblk, L->g.n_chains, fuse->d_stats,
-                         fuse->d_log, fuse->log_cap, L->d_err, st));
-    else
-      CK(launch_finalize_group(fuse->d_partials, fuse->nblk, L->g.n_chains, chain0, stride,
                                fuse->d_stats, fuse->d_log, fuse->log_cap, L->d_err, st));
   }
   return COULPS_OK;
@@ -459,12 +565,12 @@ int enqueue_compound(coulps_lattice *L, int n_hb, int n_or, coulps_charges *fuse
 
 void drop_graph(coulps_lattice *L);
 
-// Group the charge set by (y tile, z plane) of the lattice's current tile and
-// queue the upload of the lists the fused gather reads.  Buffers are reused
-// when their sizes do not change, so a captured graph stays valid.
-int stage_gather(coulps_lattice *L, coulps_charges *C) {
+// Group the charge set by (y tile, z plane) of tile t (that of the kernel
+// that gathers) and queue the upload of the lists the fused gather reads.
+// Buffers are reused when their sizes do not change, so a captured graph
+// stays valid.
+int stage_gather(coulps_lattice *L, coulps_charges *C, Tile t) {
   const Geometry &g = L->g;
-  const Tile t = L->tile;
   if (!C->gather_dirty && C->gather_tile.ty == t.ty && C->gather_tile.dz == t.dz) return COULPS_OK;
   const int ytiles = (g.Ly + t.ty - 1) / t.ty, zslabs = (g.Lz + t.dz - 1) / t.dz;
   const size_t goff_n = (size_t)ytiles * g.Lz + 1;
@@ -526,7 +632,7 @@ int stage_gather(coulps_lattice *L, coulps_charges *C) {
     const int yt = y / t.ty;
     const uint32_t pos = count[(size_t)yt * g.Lz + z]++;
     const uint32_t colour = (uint32_t)((x + y + z) & 1);
-    C->h_gent[pos] = (colour << 31) | (uint32_t)((y - yt * t.ty) * g.W + (x >> 1));
+    C->h_gent[pos] = (colour << 31) | (uint32_t)(((size_t)z * g.Ly + y) * g.W + (x >> 1));
     C->h_gq[pos] = C->qv[i];
   }
   CK(cudaMemcpyAsync(C->d_goff, C->h_goff, goff_n * sizeof(uint32_t), cudaMemcpyHostToDevice,
@@ -923,7 +1029,7 @@ int coulps_lattice_create(int Lx, int Ly, int Lz, int n_chains, int precision, u
     return COULPS_ECUDA;
   }
   int st = rebuild_maps(L);
-  if (!st) st = coulps_set_fused(L, 1);
+  if (!st) st = coulps_set_fused(L, 3);
   if (st) {
     coulps_lattice_destroy(L);
     return st;
@@ -933,7 +1039,7 @@ int coulps_lattice_create(int Lx, int Ly, int Lz, int n_chains, int precision, u
 }
 
 int coulps_set_fused(coulps_lattice_t L, int enable) {
-  if (!L || enable < 0 || enable > 2) return COULPS_EINVAL;
+  if (!L || enable < 0 || enable > 4) return COULPS_EINVAL;
   const size_t fbytes = L->g.chain_elems * L->g.es * (size_t)L->g.n_chains;
   drop_graph(L);
   if (!enable) {
@@ -953,10 +1059,29 @@ int coulps_set_fused(coulps_lattice_t L, int enable) {
     CK(cudaMemsetAsync(L->field2, 0, fbytes, L->stream));
   }
   if (L->ptile.ty == 0) L->ptile = default_pass_tile(L->g);
+  if (enable >= 3 && L->qtile.ty == 0) L->qtile = default_pair_tile(L->g);
   L->fused = enable;
   int st = rebuild_maps(L);
   if (st) return st;
   return rebuild_pass_maps(L);
+}
+
+int coulps_set_pair_tile(coulps_lattice_t L, int ty, int dz) {
+  if (!L || ty < 1 || dz < 0 || ty + 8 > 256) return COULPS_EINVAL;
+  Tile t{ty, dz > 0 ? dz : (L->qtile.dz > 0 ? L->qtile.dz : L->g.Lz)};
+  const int max_threads = L->g.precision == COULPS_F32 ? kPairMaxThreads32 : kPairMaxThreads64;
+  if (pair_threads(L->g, t) > max_threads) return COULPS_EINVAL;
+  if (pair_smem_bytes(L->g, t, true) > 227 * 1024) return COULPS_EINVAL;
+  drop_graph(L);
+  L->qtile = t;
+  return rebuild_pass_maps(L);
+}
+
+int coulps_pair_tile(coulps_lattice_t L, int32_t out[2]) {
+  if (!L || !out) return COULPS_EINVAL;
+  out[0] = L->qtile.ty;
+  out[1] = L->qtile.dz;
+  return COULPS_OK;
 }
 
 int coulps_set_pass_tile(coulps_lattice_t L, int ty, int dz) {
@@ -1217,16 +1342,17 @@ int coulps_run(coulps_lattice_t L, coulps_charges_t C, int n_therm, int n_meas, 
   int st = coulps_sweep(L, n_therm, n_hb, n_or);
   if (st) return st;
   if (n_meas == 0) return COULPS_OK;
-  // The measured sweeps gather Q, P inside their last half-sweep (on-lattice
+  // The measured sweeps gather Q, P inside their last kernel (on-lattice
   // sets; off-lattice ones use their own gather after the sweep).
   const bool fused = n_hb + n_or > 0 && !C->off;
+  const int P = n_hb + n_or;
+  const bool phased = L->schedule == COULPS_SCHEDULE_PHASED && !C->off && n_hb > 0 && n_or > 0 &&
+                      P <= kMaxGroups && n_meas >= 2 && L->g.n_chains >= P;
   if (fused) {
-    st = stage_gather(L, C);
+    st = stage_gather(L, C, phased ? L->tile : fused_gather_tile(L, n_hb, n_or));
     if (st) return st;
   }
-  const int P = n_hb + n_or;
-  if (L->schedule == COULPS_SCHEDULE_PHASED && !C->off && n_hb > 0 && n_or > 0 && P <= kMaxGroups &&
-      n_meas >= 2 && L->g.n_chains >= P) {
+  if (phased) {
     st = run_staggered(L, C, n_meas, n_hb, n_or);
     if (!st) L->pass += (uint64_t)n_meas * P;
     return st;
@@ -1858,7 +1984,7 @@ int coulps_gcv_run(coulps_gcv_t G, int n_meas, int n_hb, int n_or, double c) {
   if (n_meas == 0) return COULPS_OK;
   const bool fused = n_hb + n_or > 0;
   if (fused) {
-    int st = stage_gather(L, C);
+    int st = stage_gather(L, C, fused_gather_tile(L, n_hb, n_or));
     if (st) return st;
   }
   auto one = [&]() -> int {
@@ -1982,8 +2108,8 @@ int coulps_set_profiling(coulps_lattice_t L, int enable) {
   return COULPS_OK;
 }
 
-int coulps_kernel_times(coulps_lattice_t L, double out[10]) {
-  if (!L || !out) return COULPS_EINVAL;
+int coulps_kernel_times_n(coulps_lattice_t L, double *out, int n) {
+  if (!L || !out || n < 0) return COULPS_EINVAL;
   CK(cudaStreamSynchronize(L->stream));
   for (auto &t : L->pending) {
     float ms = 0.f;
@@ -1994,11 +2120,16 @@ int coulps_kernel_times(coulps_lattice_t L, double out[10]) {
     L->spare_events.push_back(t.b);
   }
   L->pending.clear();
-  for (int i = 0; i < 10; ++i) {
-    out[i] = L->times[i];
+  for (int i = 0; i < coulps_lattice::kTimeSlots; ++i) {
+    if (i < n) out[i] = L->times[i];
     L->times[i] = 0;
   }
+  for (int i = coulps_lattice::kTimeSlots; i < n; ++i) out[i] = 0.0;
   return COULPS_OK;
+}
+
+int coulps_kernel_times(coulps_lattice_t L, double out[10]) {
+  return coulps_kernel_times_n(L, out, 10);
 }
 
 int coulps_cv_pack_field(coulps_lattice_t L, const float *rho, void *act_bf16, float *Aphi) {

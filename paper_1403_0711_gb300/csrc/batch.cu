@@ -266,7 +266,8 @@ int batch_layout(coulps_batch *B) {
         const int x = B->sites[3 * i], y = B->sites[3 * i + 1], z = B->sites[3 * i + 2];
         const int yt = y / S.TY;
         const uint32_t p = pos[(size_t)S.goff_base + (size_t)yt * S.Lz + z]++;
-        ent[p] = ((uint32_t)((x + y + z) & 1) << 31) | (uint32_t)((y - yt * S.TY) * S.W + (x >> 1));
+        ent[p] = ((uint32_t)((x + y + z) & 1) << 31) |
+                 (uint32_t)(((size_t)z * S.Ly + y) * S.W + (x >> 1));
         gq[p] = B->q[i];
       }
     }

@@ -51,6 +51,46 @@ __device__ __forceinline__ uint32_t hb_small_side(uint32_t w) {
   return ((w >> 31) ? ~w : w) & 0x7fffffffu;
 }
 
+// The two polynomials of q in FP32 Horner form; V is float or float2 (two
+// sites in one packed FP32 instruction, each lane rounded exactly as the
+// scalar form).
+__device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+template <typename V> __device__ __forceinline__ V bcast(float c);
+template <> __device__ __forceinline__ float bcast<float>(float c) { return c; }
+template <> __device__ __forceinline__ float2 bcast<float2>(float c) { return make_float2(c, c); }
+
+template <typename V>
+__device__ __forceinline__ V erfcinv_q_main(V z) {  // z = v - 3.5, v < 7
+  V q = bcast<V>(-1.9502296e-10f);
+  q = vfma(q, z, bcast<V>(8.8274743e-10f));
+  q = vfma(q, z, bcast<V>(2.0195072e-08f));
+  q = vfma(q, z, bcast<V>(-2.3665939e-07f));
+  q = vfma(q, z, bcast<V>(-3.1320127e-07f));
+  q = vfma(q, z, bcast<V>(2.9303386e-05f));
+  q = vfma(q, z, bcast<V>(-0.00025333301f));
+  q = vfma(q, z, bcast<V>(-0.0010796369f));
+  q = vfma(q, z, bcast<V>(0.098941647f));
+  q = vfma(q, z, bcast<V>(0.85629088f));
+  return q;
+}
+
+template <typename V>
+__device__ __forceinline__ V erfcinv_q_tail(V z) {  // z = sqrt(v) - 3.6, v >= 7
+  V q = bcast<V>(-1.7354193e-06f);
+  q = vfma(q, z, bcast<V>(1.368092e-05f));
+  q = vfma(q, z, bcast<V>(-3.4650988e-05f));
+  q = vfma(q, z, bcast<V>(-1.0538802e-05f));
+  q = vfma(q, z, bcast<V>(0.00027573694f));
+  q = vfma(q, z, bcast<V>(-0.00083418511f));
+  q = vfma(q, z, bcast<V>(0.0015974527f));
+  q = vfma(q, z, bcast<V>(-0.0025665793f));
+  q = vfma(q, z, bcast<V>(0.003804483f));
+  q = vfma(q, z, bcast<V>(0.48145521f));
+  q = vfma(q, z, bcast<V>(1.6339988f));
+  return q;
+}
+
 // The heatbath deviate in FP32: erfc^-1(u) / sqrt(3) for u = (s + 1/2) 2^-31,
 // s < 2^31, with the sign of the word's top bit.  Both u and
 // x = 1 - u = (2^31 - 1 - s + 1/2) 2^-31 are formed from integers, so neither
@@ -69,35 +109,52 @@ __device__ __forceinline__ float hb_noise_f32(uint32_t w) {
   const float x = fmaf(__uint2float_rn(0x7fffffffu - s), 0x1p-31f, 0x1p-32f);
   const float v = -__log2f(fmaf(u, x, u));
   float q;
-  if (v < 7.0f) {
-    const float z = v - 3.5f;
-    q = -1.9502296e-10f;
-    q = fmaf(q, z, 8.8274743e-10f);
-    q = fmaf(q, z, 2.0195072e-08f);
-    q = fmaf(q, z, -2.3665939e-07f);
-    q = fmaf(q, z, -3.1320127e-07f);
-    q = fmaf(q, z, 2.9303386e-05f);
-    q = fmaf(q, z, -0.00025333301f);
-    q = fmaf(q, z, -0.0010796369f);
-    q = fmaf(q, z, 0.098941647f);
-    q = fmaf(q, z, 0.85629088f);
-  } else {
-    const float z = sqrtf(v) - 3.6f;
-    q = -1.7354193e-06f;
-    q = fmaf(q, z, 1.368092e-05f);
-    q = fmaf(q, z, -3.4650988e-05f);
-    q = fmaf(q, z, -1.0538802e-05f);
-    q = fmaf(q, z, 0.00027573694f);
-    q = fmaf(q, z, -0.00083418511f);
-    q = fmaf(q, z, 0.0015974527f);
-    q = fmaf(q, z, -0.0025665793f);
-    q = fmaf(q, z, 0.003804483f);
-    q = fmaf(q, z, 0.48145521f);
-    q = fmaf(q, z, 1.6339988f);
-  }
+  if (v < 7.0f)
+    q = erfcinv_q_main(v - 3.5f);
+  else
+    q = erfcinv_q_tail(sqrtf(v) - 3.6f);
   // w < 2^31 (2r < 1): a negative term; the sign goes onto x (exact)
   const float xs = __uint_as_float(__float_as_uint(x) | ((~w) & 0x80000000u));
   return xs * q;
+}
+
+// hb_noise_f32 of 2 NP words (pairs (w[0], w[1]), (w[2], w[3]), ...) with one
+// vote of the warp's active lanes for the tail over all of them, so the words'
+// independent chains can interleave; bitwise the same per word.
+template <int NP>
+__device__ __forceinline__ void hb_noise_pairs_f32(const uint32_t (&w)[2 * NP], float2 (&out)[NP]) {
+  const float2 scale = make_float2(0x1p-31f, 0x1p-31f), half = make_float2(0x1p-32f, 0x1p-32f);
+  float2 x[NP], v[NP], q[NP];
+  bool tail = false;
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    const uint32_t s0 = hb_small_side(w[2 * p]), s1 = hb_small_side(w[2 * p + 1]);
+    const float2 u =
+        __ffma2_rn(make_float2(__uint2float_rn(s0), __uint2float_rn(s1)), scale, half);
+    x[p] = __ffma2_rn(
+        make_float2(__uint2float_rn(0x7fffffffu - s0), __uint2float_rn(0x7fffffffu - s1)), scale,
+        half);
+    const float2 t = __ffma2_rn(u, x[p], u);
+    v[p] = make_float2(-__log2f(t.x), -__log2f(t.y));
+    q[p] = erfcinv_q_main(__fadd2_rn(v[p], make_float2(-3.5f, -3.5f)));
+    tail = tail || !(v[p].x < 7.0f) || !(v[p].y < 7.0f);
+  }
+  if (__any_sync(__activemask(), tail)) {
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      const float2 qt = erfcinv_q_tail(
+          __fadd2_rn(make_float2(sqrtf(v[p].x), sqrtf(v[p].y)), make_float2(-3.6f, -3.6f)));
+      q[p].x = v[p].x < 7.0f ? q[p].x : qt.x;
+      q[p].y = v[p].y < 7.0f ? q[p].y : qt.y;
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    const float2 xs =
+        make_float2(__uint_as_float(__float_as_uint(x[p].x) | ((~w[2 * p]) & 0x80000000u)),
+                    __uint_as_float(__float_as_uint(x[p].y) | ((~w[2 * p + 1]) & 0x80000000u)));
+    out[p] = __fmul2_rn(xs, q[p]);
+  }
 }
 
 __device__ __forceinline__ double hb_noise_f64(uint32_t w) {

@@ -75,7 +75,8 @@ struct SweepArgs {
   // null otherwise).  Charges are grouped by (y tile, z plane) of the launch's
   // tile shape: entries of tile column ty_idx and plane z are
   // [g_off[ty_idx*Lz + z], g_off[ty_idx*Lz + z + 1]).  An entry packs the
-  // colour in bit 31 and r*W + h in bits 0..30 (r = y - y0, h = x >> 1).
+  // colour in bit 31 and the site's offset within its colour's array,
+  // (z*Ly + y)*W + h (h = x >> 1), in bits 0..30.
   const uint32_t *g_off;
   const uint32_t *g_ent;
   const double *g_q;
@@ -95,12 +96,31 @@ struct PassArgs {
   uint32_t pass_off;
   size_t chain_elems, colour_elems;
   int *err;
+  // Fused gather on the last kernel of a measured compound sweep (null
+  // otherwise), grouped by (y tile, z plane) of this kernel's tile as in
+  // SweepArgs; both colours are read from dst.
+  const uint32_t *g_off;
+  const uint32_t *g_ent;
+  const double *g_q;
+  double *g_partials;  // [chain][y tiles * z slabs][2]
 };
 cudaError_t launch_pass(const Geometry &g, const Tile &t, const CUtensorMap &tm_c1,
                         const CUtensorMap &tm_c0, const PassArgs &a, bool overrelax,
                         cudaStream_t s);
 int pass_threads(const Geometry &g, const Tile &t);
 size_t pass_smem_bytes(const Geometry &g, const Tile &t, bool overrelax);
+
+// Pass pair (pass_pair.cu): two consecutive passes A (pass index
+// *pass_ptr + pass_off) and B (the next) in one z-march from src to dst, each
+// site read and written once for both.  TMA maps on src with boxes of TY + 8
+// rows (colour 1) and TY + 6 rows (colour 0, read when A is over-relaxation).
+cudaError_t launch_pair(const Geometry &g, const Tile &t, const CUtensorMap &tm_c1,
+                        const CUtensorMap &tm_c0, const PassArgs &a, bool a_or, bool b_or,
+                        cudaStream_t s);
+int pair_threads(const Geometry &g, const Tile &t);
+size_t pair_smem_bytes(const Geometry &g, const Tile &t, bool a_or);
+// largest thread count of a pair CTA (FP32 / FP64)
+constexpr int kPairMaxThreads32 = 512, kPairMaxThreads64 = 256;
 
 // Phase-shifted schedule: chain k belongs to group k % groups; per group the
 // launch does nothing (mode 0), a heatbath (1) or an over-relaxation (2)

@@ -24,6 +24,10 @@
 // CTA has already updated.  The arithmetic per site is exactly that of the
 // half-sweep kernel (same sums in the same order, same fma), so a pass gives
 // bitwise the same field as its two half-sweeps.
+//
+// With a gather (the last kernel of a measured compound sweep) each CTA then
+// adds up Q = sum q phi and P = sum (q phi)^2 (Eq. (nsum2)) over the charges
+// of its own rows and planes, read back from dst, into one FP64 partial.
 #include "device_common.cuh"
 #include "internal.h"
 #include "tile_march.cuh"
@@ -51,7 +55,7 @@ __host__ __device__ inline PassLayout pass_layout(int TY, int W, int es, bool or
   return L;
 }
 
-template <typename T, bool OR>
+template <typename T, bool OR, bool GATHER>
 __global__ void __launch_bounds__(512)
     pass_kernel(const __grid_constant__ CUtensorMap tm_c1, const __grid_constant__ CUtensorMap tm_c0,
                 const PassArgs a) {
@@ -117,6 +121,19 @@ __global__ void __launch_bounds__(512)
   int issued = 0;
   if (tid == 0)
     for (; issued < min(kStages, n_ring); ++issued) issue(issued);
+  // fused gather: this CTA's charge range, and this thread's first entry,
+  // loaded while the first planes arrive (used once the tile is written)
+  uint32_t g_e = 0u, g_e1 = 0u, g_ent0 = 0u;
+  double g_q0 = 0.0;
+  if (GATHER) {
+    const uint32_t *g_off = a.g_off + (size_t)blockIdx.x * a.Lz;
+    g_e = g_off[z0] + (uint32_t)tid;
+    g_e1 = g_off[z0 + nz];
+    if (g_e < g_e1) {
+      g_ent0 = a.g_ent[g_e];
+      g_q0 = a.g_q[g_e];
+    }
+  }
 
   // lanes of the quad past x = Lx - 1 (kept at 0), for row parity 0 and 1
   uint32_t pad0 = 0u, pad1 = 0u;
@@ -302,14 +319,33 @@ __global__ void __launch_bounds__(512)
     for (int k = done + 1; k < issued; ++k)
       if (!wait_plane(k)) break;
   }
+  if (GATHER) {
+    double sq = 0.0, sp = 0.0;
+    __syncthreads();  // this CTA's stores of the last step are visible to all its threads
+    if (!aborted) {
+      // both colours of the tile are still in L2; an entry holds its site's
+      // colour and offset within the colour's array
+      for (uint32_t e = g_e; e < g_e1; e += blockDim.x) {
+        const uint32_t ent = e == g_e ? g_ent0 : a.g_ent[e];
+        const double qe = e == g_e ? g_q0 : a.g_q[e];
+        const uint32_t at = ent & ~kGatherColourBit;
+        const T val = (ent & kGatherColourBit) ? dst1[at] : dst0[at];
+        const double t = qe * (double)val;
+        sq += t;
+        sp += t * t;
+      }
+    }
+    const size_t cta = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+    block_partials(sq, sp, smem, a.g_partials + 2 * ((size_t)chain * gridDim.x * gridDim.y + cta));
+  }
 }
 
-template <typename T, bool OR>
+template <typename T, bool OR, bool GATHER>
 cudaError_t launch_pt(const Geometry &g, const Tile &t, const CUtensorMap &tm_c1,
                       const CUtensorMap &tm_c0, const PassArgs &a, cudaStream_t s) {
   const PassLayout lay = pass_layout(t.ty, g.W, (int)sizeof(T), OR);
   const size_t smem = (size_t)lay.total + 128;
-  auto kfn = pass_kernel<T, OR>;
+  auto kfn = pass_kernel<T, OR, GATHER>;
   static int configured_bytes = 0;  // per instantiation
   if ((int)smem > configured_bytes) {
     cudaError_t e =
@@ -338,11 +374,19 @@ size_t pass_smem_bytes(const Geometry &g, const Tile &t, bool overrelax) {
 cudaError_t launch_pass(const Geometry &g, const Tile &t, const CUtensorMap &tm_c1,
                         const CUtensorMap &tm_c0, const PassArgs &a, bool overrelax,
                         cudaStream_t s) {
-  if (g.precision == COULPS_F32)
-    return overrelax ? launch_pt<float, true>(g, t, tm_c1, tm_c0, a, s)
-                     : launch_pt<float, false>(g, t, tm_c1, tm_c0, a, s);
-  return overrelax ? launch_pt<double, true>(g, t, tm_c1, tm_c0, a, s)
-                   : launch_pt<double, false>(g, t, tm_c1, tm_c0, a, s);
+  const bool gather = a.g_partials != nullptr;
+  if (g.precision == COULPS_F32) {
+    if (overrelax)
+      return gather ? launch_pt<float, true, true>(g, t, tm_c1, tm_c0, a, s)
+                    : launch_pt<float, true, false>(g, t, tm_c1, tm_c0, a, s);
+    return gather ? launch_pt<float, false, true>(g, t, tm_c1, tm_c0, a, s)
+                  : launch_pt<float, false, false>(g, t, tm_c1, tm_c0, a, s);
+  }
+  if (overrelax)
+    return gather ? launch_pt<double, true, true>(g, t, tm_c1, tm_c0, a, s)
+                  : launch_pt<double, true, false>(g, t, tm_c1, tm_c0, a, s);
+  return gather ? launch_pt<double, false, true>(g, t, tm_c1, tm_c0, a, s)
+                : launch_pt<double, false, false>(g, t, tm_c1, tm_c0, a, s);
 }
 
 }  // namespace coulps

@@ -315,19 +315,13 @@ __device__ bool march_tile(const TileJob<T> &j, const PhiloxKeys &K, unsigned ch
   if (GATHER && !aborted) {
     // Q and P over the tile's charges, once the whole tile is written: the
     // barrier makes this CTA's global stores visible to all its threads, and
-    // both colours of the tile are still in L2.  Entry e belongs to plane z
-    // with g_off[z] <= e < g_off[z + 1] (binary search: planes may be empty).
+    // both colours of the tile are still in L2.  An entry holds its site's
+    // colour and offset within the colour's array.
     __syncthreads();
     const uint32_t e0 = j.g_off[j.z0], e1 = j.g_off[j.z0 + j.nz];
     for (uint32_t e = e0 + tid; e < e1; e += blockDim.x) {
-      int lo = j.z0, hi = j.z0 + j.nz;
-      while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (j.g_off[mid] <= e) lo = mid;
-        else hi = mid;
-      }
       const uint32_t ent = j.g_ent[e];
-      const size_t at = ((size_t)lo * j.Ly + j.y0) * W + (ent & ~kGatherColourBit);
+      const size_t at = ent & ~kGatherColourBit;
       const bool own = ((ent >> 31) & 1u) == (uint32_t)c;
       const T val = own ? j.out[at] : j.other[at];
       const double t = j.g_q[e] * (double)val;

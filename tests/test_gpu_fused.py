@@ -29,11 +29,17 @@ def stream():
 
 
 def _run(cl, stream, L, prec, n_chains, seed, sites, q, n_therm, n_meas, n_hb, n_or, fused,
-         pass_tile=None):
+         pass_tile=None, pair_tile=None):
+    from paper_1403_0711_gb300 import inputs
     lat = cl.Lattice(L, n_chains=n_chains, precision=prec, seed=seed, stream=stream)
     lat.set_fused(fused)
     if pass_tile:
         lat.set_pass_tile(*pass_tile)
+    if pair_tile:
+        lat.set_pair_tile(*pair_tile)
+    # seeded Gaussian start (an over-relaxation-only run from phi = 0 stays 0)
+    for k, f in enumerate(inputs.gaussian_fields(L, n_chains, seed=seed)):
+        lat.set_field(k, f)
     ch = cl.Charges(lat, sites, q, log_capacity=max(1, n_meas))
     ch.run(n_therm, n_meas, n_hb, n_or)
     s = ch.samples()
@@ -77,11 +83,73 @@ def test_fused_passes_equal_half_sweeps(cl, stream, L, prec, n_hb, n_or, tile, m
     assert _rel(got[0], ref[0]) < 1e-13
 
 
+# Pass pairs: mode 3 (heatbath passes as half-sweeps, over-relaxation passes
+# as pairs + one single for an odd count, the heatbath pass out of place when
+# the count of these kernels is odd) and mode 4 (all passes as pairs + single
+# fused passes: n = 4: two pairs; 5: one pair + three singles; 6: two pairs +
+# two singles; 3: one pair + one single; 2: two singles, pairs of every kind),
+# pair tiles from one row to the default, slabs of one plane to the whole box,
+# rows narrower than a tile and boxes thinner than the pipeline (Lz < 4).
+@pytest.mark.parametrize("mode", [3, 4])
+@pytest.mark.parametrize("L,prec,n_hb,n_or,pair_tile", [
+    ((37, 29, 23), "F32", 1, 3, None),
+    ((37, 29, 23), "F32", 1, 3, (3, 5)),
+    ((21, 18, 12), "F64", 2, 3, None),
+    ((16, 16, 16), "F64", 2, 2, None),
+    ((16, 16, 16), "F32", 2, 2, (4, 3)),
+    ((10, 9, 8), "F32", 1, 2, None),
+    ((12, 7, 9), "F32", 1, 1, None),
+    ((130, 5, 70), "F32", 0, 4, (1, 64)),
+    ((64, 64, 64), "F32", 1, 3, (26, 16)),
+    ((128, 64, 40), "F32", 1, 3, None),
+    ((9, 1, 1), "F64", 1, 1, None),
+    ((25, 40, 3), "F32", 3, 1, (6, 1)),
+    ((25, 40, 3), "F32", 1, 5, (6, 1)),
+    ((8, 8, 200), "F32", 1, 3, (8, 7)),
+    ((100, 3, 50), "F64", 1, 3, (2, 9)),
+    ((2, 3, 4), "F32", 1, 3, None),
+    ((1, 1, 1), "F32", 1, 3, None),
+])
+def test_pass_pairs_equal_half_sweeps(cl, stream, L, prec, n_hb, n_or, pair_tile, mode):
+    from paper_1403_0711_gb300 import inputs
+    p = getattr(cl, prec)
+    n = max(2, min(12, L[0] * L[1] * L[2] // 2) // 2 * 2)
+    if L == (1, 1, 1):
+        n = 1
+    sites, q = (inputs.plus_minus(L, n, seed=3) if n > 1 else
+                (np.zeros((1, 3), np.int32), np.ones(1)))
+    ref = _run(cl, stream, L, p, 3, 17, sites, q, 2, 4, n_hb, n_or, 0)
+    got = _run(cl, stream, L, p, 3, 17, sites, q, 2, 4, n_hb, n_or, mode, pair_tile=pair_tile)
+    assert got[2]["fused"] == mode
+    assert got[2]["pass"] == ref[2]["pass"]
+    for a, b in zip(got[1], ref[1]):
+        assert np.array_equal(a, b)
+    assert _rel(got[0], ref[0]) < 1e-13
+
+
+def test_pair_tile_limits(cl, stream):
+    lat = cl.Lattice((128, 128, 128), n_chains=1, precision=cl.F32, seed=1, stream=stream)
+    lat.set_fused(3)
+    ty, dz = lat.pair_tile()
+    assert (ty + 6) * 16 <= 512 and ty >= 4 and dz >= 1
+    with pytest.raises(cl.CoulpsError):
+        lat.set_pair_tile(27, 8)  # 33 rows x 16 quads > 512 threads
+    lat.set_pair_tile(26, 128)
+    assert lat.pair_tile() == (26, 128)
+    lat.close()
+    # rows of 512 sites: no pair tile, the pair modes run single fused passes
+    wide = cl.Lattice((512, 4, 4), n_chains=1, precision=cl.F32, seed=1, stream=stream)
+    wide.set_fused(4)
+    assert wide.pair_tile() == (0, 0)
+    wide.close()
+
+
 def test_fused_is_default_and_costs_a_second_copy(cl, stream):
     L = (32, 32, 32)
     lat = cl.Lattice(L, n_chains=2, precision=cl.F32, seed=1, stream=stream)
     info = lat.info()
-    assert info["fused"] == 1 and info["pass_ty"] >= 1 and info["pass_dz"] >= 1
+    assert info["fused"] == 3 and info["pass_ty"] >= 1 and info["pass_dz"] >= 1
+    assert lat.pair_tile()[0] >= 4
     b_on = info["bytes"]
     lat.set_fused(False)
     b_off = lat.info()["bytes"]

@@ -39,10 +39,12 @@ def stream():
 
 
 def gpu_run(cl, stream, L, n_chains, prec, seed, sites, q, n_therm, n_meas, n_hb, n_or,
-            tile=None, fields=()):
+            tile=None, fields=(), fused=None):
     lat = cl.Lattice(L, n_chains=n_chains, precision=prec, seed=seed, stream=stream)
     if tile:
         lat.set_tile(*tile)
+    if fused is not None:
+        lat.set_fused(fused)
     ch = cl.Charges(lat, sites, q, log_capacity=max(1, n_meas))
     ch.run(n_therm, n_meas, n_hb, n_or)
     s = ch.samples()
@@ -127,13 +129,17 @@ def test_fp32_window_64cubed(cl, stream, orc):
     assert field_err(f[0], phi) < TOL32
 
 
-def test_fp32_full_size_sampled_chains(cl, stream, orc):
-    """128^3, 4096 charges +-1, 64 chains, 1 HB : 3 OR, default tile (the benchmark
-    launch configuration); chains 0, 37 and 63 checked against the oracle."""
+@pytest.mark.parametrize("fused", [1, 3, 4])
+def test_fp32_full_size_sampled_chains(cl, stream, orc, fused):
+    """128^3, 4096 charges +-1, 64 chains, 1 HB : 3 OR, default tiles, on the
+    fused-pass (1), the over-relaxation pass-pair (3, the benchmark launch
+    configuration) and the all-pairs (4) schedules, the sample gathered by the
+    sweep's last kernel; chains 0, 37 and 63 checked against the oracle."""
     from paper_1403_0711_gb300 import inputs
     L = (128, 128, 128)
     sites, q = inputs.plus_minus(L, 4096, seed=1)
-    s, f, _ = gpu_run(cl, stream, L, 64, cl.F32, 1, sites, q, 1, 3, 1, 3, fields=(0, 37, 63))
+    s, f, _ = gpu_run(cl, stream, L, 64, cl.F32, 1, sites, q, 1, 3, 1, 3, fields=(0, 37, 63),
+                      fused=fused)
     for k in (0, 37, 63):
         ref, phi = orc_run(orc, L, 1, k, sites, q, 1, 3, 1, 3)
         assert sample_err(s[:, k], ref) < TOL32, k
@@ -154,14 +160,18 @@ def test_tile_shape_does_not_change_results(cl, stream, tile):
         assert sample_err(got[:, k], base[:, k]) < 1e-13
 
 
-def test_fused_and_separate_gather_agree(cl, stream):
-    """coulps_run gathers inside the last half-sweep; coulps_measure runs the
-    separate gather kernel on the same fields: same samples."""
+@pytest.mark.parametrize("mode", [0, 1, 2, 3, 4])
+def test_fused_and_separate_gather_agree(cl, stream, mode):
+    """coulps_run gathers inside the sweep's last kernel (a half-sweep with
+    mode 0, a fused pass with modes 1, 2 and 3, a pass pair with mode 4);
+    coulps_measure runs the separate gather kernel on the same fields: same
+    samples."""
     from paper_1403_0711_gb300 import inputs
     L = (48, 33, 29)
     sites, q = inputs.uniform_q(L, 700, seed=12)
-    fused, _, _ = gpu_run(cl, stream, L, 3, cl.F32, 13, sites, q, 1, 5, 1, 3)
+    fused, _, _ = gpu_run(cl, stream, L, 3, cl.F32, 13, sites, q, 1, 5, 1, 3, fused=mode)
     lat = cl.Lattice(L, n_chains=3, precision=cl.F32, seed=13, stream=stream)
+    lat.set_fused(mode)
     ch = cl.Charges(lat, sites, q, log_capacity=5)
     lat.sweep(1, 1, 3)
     for _ in range(5):

@@ -42,7 +42,9 @@ def _h_l(phi):
 
 @pytest.mark.parametrize("L,prec,fused,n_or", [((13, 7, 5), "F64", 0, 3), ((13, 7, 5), "F64", 1, 4),
                                                ((24, 17, 9), "F32", 1, 2), ((31, 8, 12), "F32", 0, 1),
-                                               ((16, 16, 16), "F64", 2, 2)])
+                                               ((16, 16, 16), "F64", 2, 2),
+                                               ((24, 17, 9), "F32", 3, 2), ((13, 7, 5), "F64", 3, 4),
+                                               ((24, 17, 9), "F32", 4, 3)])
 def test_over_relaxation_conserves_action(cl, stream, L, prec, fused, n_or):
     from paper_1403_0711_gb300 import inputs
     fields = inputs.gaussian_fields(L, 2, seed=sum(L))

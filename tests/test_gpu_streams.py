@@ -35,6 +35,11 @@ def stream():
     ((20, 16, 8), "F32", 3, 2, 1, 3, False),
     ((16, 16, 16), "F32", 1, 1, 1, 3, False),
     ((33, 10, 6), "F32", 6, 1, 2, 2, False),
+    ((24, 13, 11), "F32", 5, 3, 1, 3, False),
+    ((24, 13, 11), "F32", 5, 3, 1, 3, True),
+    ((17, 9, 12), "F64", 4, 4, 1, 3, False),
+    ((33, 10, 6), "F32", 6, 3, 2, 2, False),
+    ((33, 10, 6), "F32", 6, 4, 2, 3, False),
 ])
 def test_two_streams_bitwise(cl, stream, L, prec, chains, fused, n_hb, n_or, profiling):
     from paper_1403_0711_gb300 import inputs
