@@ -62,7 +62,11 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--schedule", choices=["phased", "aligned"], default="aligned")
+    ap.add_argument("--schedule", choices=["aligned", "shifted", "phased"], default="aligned",
+                    help="shifted: with two streams the odd chains run half a compound sweep "
+                         "behind (coulps_set_schedule; measured 0.748 against 0.735 ms per "
+                         "step aligned: a pass-pair CTA leaves no room for a heatbath CTA "
+                         "on its SM)")
     ap.add_argument("--streams", type=int, choices=[1, 2, 3, 4], default=2,
                     help="chain k on stream k %% n (coulps_set_streams)")
     ap.add_argument("--fused", choices=["pairs", "allpairs", "on", "all", "off"], default="pairs",
@@ -432,8 +436,8 @@ def run_ours(args):
     # each).  A step is one measured compound sweep of every chain; all K timed
     # steps are one call.  --schedule phased runs chain k mod 4 passes behind
     # (launches mix heatbath and over-relaxation tiles; measured no faster).
-    lat.set_schedule(coulps.SCHEDULE_PHASED if args.schedule == "phased"
-                     else coulps.SCHEDULE_ALIGNED)
+    lat.set_schedule({"phased": coulps.SCHEDULE_PHASED, "aligned": coulps.SCHEDULE_ALIGNED,
+                      "shifted": coulps.SCHEDULE_SHIFTED}[args.schedule])
     # The timed steps run as the library runs them: the measured compound
     # sweep captured once as a CUDA graph and replayed, with the odd chains on
     # a second stream (--streams 2).  Per-kernel CUDA-event timing (which
@@ -443,9 +447,11 @@ def run_ours(args):
     lat.sync()
     ch.reset_stats()  # the timed samples alone feed the time-to-accuracy projection
 
-    # the K timed steps in up to five chunks, an event at each boundary: the
-    # whole region gives the value, the chunks its spread
-    n_chunks = max(1, min(5, args.steps))
+    # the K timed steps in one call, or from K = 100 on in five calls with an
+    # event at each boundary: the whole region gives the value, the chunks its
+    # spread (each call of the shifted schedule has its own prologue and
+    # epilogue, so short chunks would time them more often than a run does)
+    n_chunks = 5 if args.steps >= 100 else 1
     bounds = [round(args.steps * i / n_chunks) for i in range(n_chunks + 1)]
     evs = [torch.cuda.Event(enable_timing=True) for _ in bounds]
     if world > 1:

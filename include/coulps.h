@@ -320,8 +320,21 @@ int coulps_pool_stats(const double *stats, int64_t n_rows, double *mean, double 
  * Errors: EINVAL, ECUDA. */
 int coulps_set_streams(coulps_lattice_t lat, int n);
 
+/* COULPS_SCHEDULE_SHIFTED: with two streams (coulps_set_streams(lat, 2)),
+ * fused modes 1 and 3, n_hb >= 1 and n_or >= 1, coulps_run's measured phase
+ * (n_meas >= 2, on-lattice charge set) runs the odd chains half a compound
+ * sweep behind the even ones: a prologue (even chains: the first sweep; odd
+ * chains: its heatbath passes), n_meas - 1 steady steps (even: the next
+ * sweep; odd: the over-relaxation passes and sample of their previous sweep,
+ * then the heatbath passes of the next), an epilogue (odd: the rest of their
+ * last sweep), each captured as a CUDA graph.  One group's heatbath
+ * half-sweeps then run beside the other's over-relaxation kernels.  Every
+ * chain does exactly the passes, Philox draws and samples of the aligned
+ * schedule (bitwise identical results); after the call all chains have
+ * finished the same sweeps.  Otherwise it runs as ALIGNED. */
 #define COULPS_SCHEDULE_ALIGNED 0
 #define COULPS_SCHEDULE_PHASED 1
+#define COULPS_SCHEDULE_SHIFTED 2
 int coulps_set_schedule(coulps_lattice_t lat, int schedule);
 
 /* Fused passes.  A fused pass (both half-sweeps) runs as one kernel that

@@ -47,7 +47,7 @@ EXPORTS = (
     "coulps_set_streams", "coulps_selftest_wait", "coulps_clear_error",
     "coulps_set_pair_tile", "coulps_pair_tile", "coulps_kernel_times_n",
 )
-SCHEDULE_ALIGNED, SCHEDULE_PHASED = 0, 1
+SCHEDULE_ALIGNED, SCHEDULE_PHASED, SCHEDULE_SHIFTED = 0, 1, 2
 STAT_STRIDE = 72
 
 

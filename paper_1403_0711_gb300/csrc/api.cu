@@ -102,6 +102,10 @@ struct coulps_lattice {
   const void *sgraph_key = nullptr;
   int sgraph_hb = -1, sgraph_or = -1;
   Tile sgraph_tile = {0, 0};
+  // shifted schedule: prologue, steady step and epilogue graphs
+  cudaGraphExec_t hgraph[3] = {nullptr, nullptr, nullptr};
+  const void *hgraph_key = nullptr;
+  int hgraph_hb = -1, hgraph_or = -1;
   // measured compound sweep + multi-set gather (coulps_run_sets) as a graph
   cudaGraphExec_t mgraph = nullptr;
   std::vector<const void *> mgraph_key;
@@ -393,8 +397,13 @@ cudaEvent_t take_event(coulps_lattice *L) {
 // ... on stream `st`, with their measurement when `fuse` is given: its Q, P
 // are gathered by the sweep's last kernel, by the tile fused_gather_tile
 // names (the pass counter is advanced by the caller).
+// Which passes of the plan enqueue_part queues: all of them, the head only
+// (the heatbath half-sweeps of modes 1 and 3), or the rest only (the trips
+// and tail, with their gather), the rest's pass indices offset by `shift`.
+enum PartRange { kPartAll = 0, kPartHead = 1, kPartRest = 2 };
+
 int enqueue_part(coulps_lattice *L, cudaStream_t st, int n_hb, int n_or, coulps_charges *fuse,
-                 int chain0, int stride) {
+                 int chain0, int stride, int range = kPartAll, uint32_t shift = 0u) {
   SweepArgs a;
   a.chain0 = chain0;
   a.chain_stride = stride;
@@ -469,7 +478,7 @@ int enqueue_part(coulps_lattice *L, cudaStream_t st, int n_hb, int n_or, coulps_
     a.field = on2 ? L->field2 : L->field;
     for (int c = 0; c < 2; ++c) {
       a.colour = c;
-      a.pass_off = (uint32_t)i;
+      a.pass_off = (uint32_t)i + (i >= plan.head ? shift : 0u);
       // the other colour's rows come from field, except once field2 holds
       // them: colour 1 of the first pass, and every later pass
       const CUtensorMap &halo = on2 && (i > 0 || c == 1) ? L->tm_halo2 : L->tm_halo;
@@ -487,16 +496,19 @@ int enqueue_part(coulps_lattice *L, cudaStream_t st, int n_hb, int n_or, coulps_
     a.field = L->field;
     return COULPS_OK;
   };
-  for (int i = 0; i < plan.head; ++i) {
-    const int r = half_sweeps(i, plan.flip, fuse && trips == 0 && tail0 == n_pass && i == n_pass - 1);
-    if (r) return r;
-  }
+  if (range != kPartRest)
+    for (int i = 0; i < plan.head; ++i) {
+      const int r =
+          half_sweeps(i, plan.flip, fuse && trips == 0 && tail0 == n_pass && i == n_pass - 1);
+      if (r) return r;
+    }
+  if (range == kPartHead) return COULPS_OK;
   // trips: pass pairs, then single fused passes, each from one copy to the other
   int i = plan.head;
   for (int t = 0; t < trips; ++t) {
     const int b = (t + (plan.flip ? 1 : 0)) & 1;  // source copy: 0 the field, 1 field2
     p.dst = b ? L->field : L->field2;
-    p.pass_off = (uint32_t)i;
+    p.pass_off = (uint32_t)i + shift;
     if (fuse && t == trips - 1 && tail0 == n_pass) set_gather(p);
     int r;
     if (t < plan.pairs) {
@@ -520,7 +532,7 @@ int enqueue_part(coulps_lattice *L, cudaStream_t st, int n_hb, int n_or, coulps_
     const int r = half_sweeps(i, false, fuse && i == n_pass - 1);
     if (r) return r;
   }
-  if (fuse && n_pass > 0) {
+  if (fuse && n_pass > 0) {  // (range is kPartAll or kPartRest here)
     if (chain0 == 0 && stride == 1)
       CK(launch_finalize(fuse->d_fpart, fuse->fused_nblk, L->g.n_chains, fuse->d_stats,
                          fuse->d_log, fuse->log_cap, L->d_err, st));
@@ -558,6 +570,45 @@ int enqueue_compound(coulps_lattice *L, int n_hb, int n_or, coulps_charges *fuse
     if (r) return r;
   }
   if (n_hb + n_or > 0) CK(launch_advance_pass(L->d_pass, (uint32_t)(n_hb + n_or), L->stream));
+  return COULPS_OK;
+}
+
+
+// The shifted schedule (coulps_set_schedule): with two streams, the odd
+// chains run half a compound sweep behind the even ones, so that one group's
+// heatbath half-sweeps (instruction-bound) meet the other's over-relaxation
+// kernels (memory-bound) throughout.  A run of n >= 2 measured compound
+// sweeps is a prologue (even chains: sweep 0; odd chains: the heatbath
+// passes of sweep 0), n - 1 steady steps (even: sweep k; odd: the
+// over-relaxation passes and the sample of sweep k - 1, then the heatbath
+// passes of sweep k) and an epilogue (odd: the over-relaxation passes and
+// sample of the last sweep).  Every chain does exactly the passes, draws and
+// samples of the aligned schedule; the pass counter advances by one sweep per
+// prologue and steady step.
+bool shifted_ok(const coulps_lattice *L, int n_hb, int n_or) {
+  if (L->schedule != COULPS_SCHEDULE_SHIFTED || L->split != 2 || L->g.n_chains < 2) return false;
+  if (n_hb < 1 || n_or < 1) return false;
+  const PassPlan P = pass_plan(L, n_hb, n_or);
+  return P.head == n_hb && P.head < n_hb + n_or;
+}
+
+int enqueue_shifted(coulps_lattice *L, int n_hb, int n_or, coulps_charges *fuse, int phase) {
+  const int n = n_hb + n_or;
+  const uint32_t back = (uint32_t)(-(int64_t)n);  // pass offsets of the previous sweep
+  CK(cudaEventRecord(L->ev_fork, L->stream));
+  CK(cudaStreamWaitEvent(L->xstream[0], L->ev_fork, 0));
+  int r = COULPS_OK;
+  if (phase == 0) {
+    r = enqueue_part(L, L->xstream[0], n_hb, n_or, nullptr, 1, 2, kPartHead);
+  } else {
+    r = enqueue_part(L, L->xstream[0], n_hb, n_or, fuse, 1, 2, kPartRest, back);
+    if (!r && phase == 1) r = enqueue_part(L, L->xstream[0], n_hb, n_or, nullptr, 1, 2, kPartHead);
+  }
+  if (!r && phase != 2) r = enqueue_part(L, L->stream, n_hb, n_or, fuse, 0, 2);
+  CK(cudaEventRecord(L->ev_join[0], L->xstream[0]));
+  CK(cudaStreamWaitEvent(L->stream, L->ev_join[0], 0));
+  if (r) return r;
+  if (phase != 2) CK(launch_advance_pass(L->d_pass, (uint32_t)n, L->stream));
   return COULPS_OK;
 }
 
@@ -703,7 +754,12 @@ int enqueue_measure_sets(coulps_lattice *L, coulps_charges *const *sets, int n_s
 
 void drop_graph(coulps_lattice *L) {
   // launches of these graphs may still be queued: let them finish first
-  if (L->graph || L->sgraph || L->mgraph) cudaStreamSynchronize(L->stream);
+  if (L->graph || L->sgraph || L->mgraph || L->hgraph[0]) cudaStreamSynchronize(L->stream);
+  for (auto &h : L->hgraph) {
+    if (h) cudaGraphExecDestroy(h);
+    h = nullptr;
+  }
+  L->hgraph_key = nullptr;
   if (L->mgraph) cudaGraphExecDestroy(L->mgraph);
   L->mgraph = nullptr;
   L->mgraph_key.clear();
@@ -713,6 +769,51 @@ void drop_graph(coulps_lattice *L) {
   if (L->sgraph) cudaGraphExecDestroy(L->sgraph);
   L->sgraph = nullptr;
   L->sgraph_key = nullptr;
+}
+
+// The measured phase of coulps_run on the shifted schedule (see
+// enqueue_shifted): prologue, n_meas - 1 steady steps, epilogue, each a
+// cached CUDA graph when the stream can be captured.
+int run_shifted(coulps_lattice *L, coulps_charges *C, int n_meas, int n_hb, int n_or) {
+  const bool capturable = L->stream != nullptr && !L->profiling;
+  if (capturable &&
+      (L->hgraph_key != C || L->hgraph_hb != n_hb || L->hgraph_or != n_or || !L->hgraph[0])) {
+    drop_graph(L);
+    for (int ph = 0; ph < 3; ++ph) {
+      cudaGraph_t gr = nullptr;
+      CK(cudaStreamBeginCapture(L->stream, cudaStreamCaptureModeThreadLocal));
+      const int s1 = enqueue_shifted(L, n_hb, n_or, C, ph);
+      cudaError_t e = cudaStreamEndCapture(L->stream, &gr);
+      if (s1 || e != cudaSuccess) {
+        cudaGetLastError();
+        if (gr) cudaGraphDestroy(gr);
+        drop_graph(L);
+        return s1 ? s1 : COULPS_ECUDA;
+      }
+      e = cudaGraphInstantiate(&L->hgraph[ph], gr, 0);
+      cudaGraphDestroy(gr);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        L->hgraph[ph] = nullptr;
+        drop_graph(L);
+        return COULPS_ECUDA;
+      }
+    }
+    L->hgraph_key = C;
+    L->hgraph_hb = n_hb;
+    L->hgraph_or = n_or;
+  }
+  auto phase = [&](int ph) -> int {
+    if (capturable) {
+      CK(cudaGraphLaunch(L->hgraph[ph], L->stream));
+      return COULPS_OK;
+    }
+    return enqueue_shifted(L, n_hb, n_or, C, ph);
+  };
+  int st = phase(0);
+  for (int k = 1; k < n_meas && !st; ++k) st = phase(1);
+  if (!st) st = phase(2);
+  return st;
 }
 
 // ---- phase-shifted schedule ------------------------------------------------
@@ -1354,6 +1455,11 @@ int coulps_run(coulps_lattice_t L, coulps_charges_t C, int n_therm, int n_meas, 
   }
   if (phased) {
     st = run_staggered(L, C, n_meas, n_hb, n_or);
+    if (!st) L->pass += (uint64_t)n_meas * P;
+    return st;
+  }
+  if (fused && n_meas >= 2 && shifted_ok(L, n_hb, n_or)) {
+    st = run_shifted(L, C, n_meas, n_hb, n_or);
     if (!st) L->pass += (uint64_t)n_meas * P;
     return st;
   }
@@ -2094,7 +2200,8 @@ int coulps_set_streams(coulps_lattice_t L, int n) {
 }
 
 int coulps_set_schedule(coulps_lattice_t L, int schedule) {
-  if (!L || (schedule != COULPS_SCHEDULE_ALIGNED && schedule != COULPS_SCHEDULE_PHASED))
+  if (!L || (schedule != COULPS_SCHEDULE_ALIGNED && schedule != COULPS_SCHEDULE_PHASED &&
+             schedule != COULPS_SCHEDULE_SHIFTED))
     return COULPS_EINVAL;
   if (schedule != L->schedule) drop_graph(L);
   L->schedule = schedule;

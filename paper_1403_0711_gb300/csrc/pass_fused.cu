@@ -12,9 +12,10 @@
 //            same inputs, same Philox counters, same values);
 //   stage 1: colour 1 at plane p1 = p0 - 1 on rows y0 .. y0 + TY - 1.
 // Colour 1's old planes p0 - 1 .. p0 + 1 (rows y0 - 2 .. y0 + TY + 1) and
-// colour 0's old plane p0 (rows y0 - 1 .. y0 + TY) arrive by TMA in a 4-slot
-// ring.  Each thread owns one quad of one row for both stages and carries in
-// registers the three planes of colour 1 (old) and of colour 0 (new) that
+// colour 0's old plane p0 (rows y0 - 1 .. y0 + TY) arrive by TMA in a
+// kPassStages-slot ring.  Each thread owns one quad of one row for both
+// stages and carries in registers the three planes of colour 1 (old) and of
+// colour 0 (new) that
 // its quad needs along z; the y +- 1 rows and the x neighbour come from
 // shared memory (the ring, and a 2-plane buffer of the new colour-0 rows).
 // Ghost rows and planes (outside the box) hold 0 in both.
@@ -37,6 +38,13 @@ namespace {
 
 using namespace tile;
 
+// Ring depth of the fused pass (slots of one colour-1 box and one colour-0
+// box); at most 8 (mbarriers at 0 .. 63 of the header, abort flag at 64).
+// Measured at 128^3 x 64 chains: 0.203 ms per over-relaxation pass with 4
+// slots, 0.194 with 6, 0.196 with 8.
+constexpr int kPassStages = 6;
+static_assert(kPassStages <= 8, "mbarriers must end before the abort flag");
+
 struct PassLayout {
   int c1_bytes;    // colour-1 box: (TY + 4) rows x W
   int c0_bytes;    // colour-0 box: (TY + 2) rows x W (over-relaxation only)
@@ -51,7 +59,7 @@ __host__ __device__ inline PassLayout pass_layout(int TY, int W, int es, bool or
   L.c0_bytes = orx ? (TY + 2) * W * es : 0;
   L.slot_bytes = round_up_int(L.c1_bytes, 128) + round_up_int(L.c0_bytes, 128);
   L.new_bytes = round_up_int((TY + 2) * W * es, 128);
-  L.total = kHeaderBytes + kStages * L.slot_bytes + 2 * L.new_bytes;
+  L.total = kHeaderBytes + kPassStages * L.slot_bytes + 2 * L.new_bytes;
   return L;
 }
 
@@ -66,12 +74,12 @@ __global__ void __launch_bounds__(512)
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 64);
   unsigned char *ring = smem + kHeaderBytes;
-  T *newbuf = reinterpret_cast<T *>(ring + kStages * lay.slot_bytes);
+  T *newbuf = reinterpret_cast<T *>(ring + kPassStages * lay.slot_bytes);
   auto c1_slot = [&](int j) {
-    return reinterpret_cast<T *>(ring + (j & (kStages - 1)) * lay.slot_bytes);
+    return reinterpret_cast<T *>(ring + (j % kPassStages) * lay.slot_bytes);
   };
   auto c0_slot = [&](int j) {
-    return reinterpret_cast<T *>(ring + (j & (kStages - 1)) * lay.slot_bytes +
+    return reinterpret_cast<T *>(ring + (j % kPassStages) * lay.slot_bytes +
                                  round_up_int(lay.c1_bytes, 128));
   };
   auto new_plane = [&](int s) {
@@ -102,25 +110,31 @@ __global__ void __launch_bounds__(512)
   const uint32_t pass = OR ? 0u : (*a.pass_ptr + a.pass_off);
   const PhiloxKeys &K = *reinterpret_cast<const PhiloxKeys *>(a.round_keys);
 
-  ring_init(smem);
+  if (tid == 0) {
+    for (int k = 0; k < kPassStages; ++k) mbar_init(smem_addr(&bars[k]), 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
   if (tid == 0) {
     prefetch_tensormap(&tm_c1);
     if (OR) prefetch_tensormap(&tm_c0);
   }
   // ring plane j: colour 1 at z0 - 2 + j; with it (j >= 2) colour 0 at z0 - 3 + j
   auto issue = [&](int j) {
-    const uint32_t bar = smem_addr(&bars[j & (kStages - 1)]);
+    const uint32_t bar = smem_addr(&bars[j % kPassStages]);
     const bool own = OR && j >= 2;
     mbar_arrive_expect_tx(bar, lay.c1_bytes + (own ? lay.c0_bytes : 0));
     tma_load_4d(smem_addr(c1_slot(j)), &tm_c1, 0, y0 - 2, z0 - 2 + j, 2 * chain + 1, bar);
     if (own) tma_load_4d(smem_addr(c0_slot(j)), &tm_c0, 0, y0 - 1, z0 - 3 + j, 2 * chain, bar);
   };
   auto wait_plane = [&](int j) -> bool {
-    return mbar_wait_bounded(smem_addr(&bars[j & (kStages - 1)]), (uint32_t)((j / kStages) & 1));
+    return mbar_wait_bounded(smem_addr(&bars[j % kPassStages]),
+                             (uint32_t)((j / kPassStages) & 1));
   };
   int issued = 0;
   if (tid == 0)
-    for (; issued < min(kStages, n_ring); ++issued) issue(issued);
+    for (; issued < min(kPassStages, n_ring); ++issued) issue(issued);
   // fused gather: this CTA's charge range, and this thread's first entry,
   // loaded while the first planes arrive (used once the tile is written)
   uint32_t g_e = 0u, g_e1 = 0u, g_ent0 = 0u;
