@@ -640,7 +640,8 @@ int coulps_gcv_run(coulps_gcv_t gcv, int n_meas, int n_hb, int n_or, double c);
  * each of n_chains fields the caller owns, the same (Q, P, e) as
  * coulps_measure, and allocates nothing: no cudaMalloc, no cudaFree, no
  * allocating library call.  Its only working memory is a file-scope device
- * array of COULPS_STATIC_SCRATCH_DOUBLES doubles (512 KiB) that every GPU
+ * array of COULPS_STATIC_SCRATCH_DOUBLES doubles (512 KiB) and a one-word
+ * counter of out-of-range offsets (cleared by each call) that every GPU
  * loading this library holds until the process exits.
  *   field      device pointer to n_chains fields in the library's storage
  *              layout: field[chain][colour][z][y][h] with colour (x+y+z)&1,
@@ -649,11 +650,16 @@ int coulps_gcv_run(coulps_gcv_t gcv, int n_meas, int n_hb, int n_or, double c);
  *              0; one chain is 2*Lz*Ly*W elements (float or double by
  *              precision).  This is the layout coulps_lattice_create uses.
  *   site_index device pointer to n uint32 offsets within one chain's field:
- *              colour*(Lz*Ly*W) + (z*Ly + y)*W + (x>>1).
+ *              colour*(Lz*Ly*W) + (z*Ly + y)*W + (x>>1).  An offset of
+ *              2*Lz*Ly*W or more is not read: it makes every chain's
+ *              (Q, P, e) NaN.
  *   q          device pointer to n doubles.
  *   QPe        device pointer to 3*n_chains doubles, written as
- *              (Q, P, e) of chain k at QPe[3k..3k+2].
- *   stream     cudaStream_t the work is queued on (asynchronous).
+ *              (Q, P, e) of chain k at QPe[3k..3k+2], bitwise the values
+ *              coulps_measure gives for the same fields and charges.
+ *   stream     cudaStream_t the work is queued on (asynchronous); it must
+ *              belong to the current device (EINVAL otherwise; checked when
+ *              the stream is not being captured into a graph).
  * Limit: n_chains * b * 2 <= COULPS_STATIC_SCRATCH_DOUBLES, where
  * b = min(64, max(1, ceil(n / 1024))) CTAs per chain; e.g. any n with up to
  * 512 chains, or up to 32768 chains when n <= 1024.  Larger requests return
@@ -664,7 +670,8 @@ int coulps_gcv_run(coulps_gcv_t gcv, int n_meas, int n_hb, int n_or, double c);
  * last call's contents; every slot a call reads is first written by that same
  * call, so nothing needs clearing, but calls that overlap on the GPU (for
  * example on two streams at once) race on it and must be serialised by the
- * caller.  Errors: EINVAL, ECUDA, EUNSUPPORTED (device ordinal >= 64). */
+ * caller.  A device reset while the library is loaded is not supported.
+ * Errors: EINVAL, ECUDA, EUNSUPPORTED (device ordinal >= 64). */
 #define COULPS_STATIC_SCRATCH_DOUBLES 65536
 int coulps_measure_static(const void *field, int Lx, int Ly, int Lz, int n_chains, int precision,
                           const uint32_t *site_index, const double *q, int64_t n, double *QPe,

@@ -1,5 +1,5 @@
 """Autotuner for the tile shapes (ty rows x dz planes per CTA) of the
-half-sweep kernel and of the fused-pass kernel.
+half-sweep kernel, the fused-pass kernel and the pass-pair kernel.
 
 The shape changes only the work decomposition, never the results (the tests
 check fields bitwise across shapes), so the tuner may pick freely.  For a box
@@ -9,8 +9,8 @@ sweeps and keeps the fastest.  Results are cached in a JSON file keyed by box,
 chain count, precision, compound-sweep mix and GPU name
 ($COULPS_TUNE_CACHE, default ~/.cache/coulps_tune.json).
 
-tune_lattice(lat)  tunes and applies both shapes of a Lattice (the half-sweep
-                   shape serves passes that are not fused).
+tune_lattice(lat)  tunes and applies the three shapes of a Lattice (the
+                   half-sweep shape serves passes that are not fused).
 tune_batch(batch)  tunes each distinct system shape of a Batch (with as many
                    chains as the batch has systems of that shape, so the tuned
                    lattice carries the same load) and applies them.
@@ -85,16 +85,35 @@ def pass_candidates(L, precision):
     return [(t, d) for t in tys for d in dzs]
 
 
-def _time_shapes(L, n_chains, precision, shapes, n_hb, n_or, reps, stream, fused=False):
+def pair_candidates(L, precision):
+    """Pass-pair tile shapes: (ty + 6) rows of quads within 512 threads (FP32)
+    or 256 (FP64), colour-1 boxes of ty + 8 <= 256 rows."""
+    Lx, Ly, Lz = L
+    qw = row_stride(Lx, precision) // 4
+    max_threads = 512 if precision == coulps.F32 else 256
+    tys = sorted({t for t in (4, 6, 8, 10, 14, 18, 22, 26, 42, 58, 122)
+                  if t <= Ly and qw * (t + 6) <= max_threads and t + 8 <= 256} |
+                 ({min(Ly, max_threads // qw - 6, 248)} if max_threads // qw - 6 >= 1 else set()))
+    dzs = sorted({d for d in (16, 32, 64, 128) if d <= Lz} | {Lz})
+    return [(t, d) for t in tys for d in dzs]
+
+
+def _time_shapes(L, n_chains, precision, shapes, n_hb, n_or, reps, stream, fused=False,
+                 pair=False):
+    """Device time of the sweep kernels per `reps` compound sweeps for each
+    shape: half-sweep tiles (default), fused-pass tiles (fused=True, all
+    passes fused) or pass-pair tiles (pair=True, over-relaxation pairs)."""
     lat = coulps.Lattice(L, n_chains=n_chains, precision=precision, seed=1, stream=stream)
-    lat.set_fused(fused)
+    lat.set_fused(3 if pair else (2 if fused else 0))
     lat.set_profiling(True)
     out = {}
     try:
         lat.sweep(2, n_hb, n_or)
         for ty, dz in shapes:
             try:
-                if fused:
+                if pair:
+                    lat.set_pair_tile(ty, dz)
+                elif fused:
                     lat.set_pass_tile(ty, dz)
                 else:
                     lat.set_tile(ty, dz)
@@ -104,10 +123,19 @@ def _time_shapes(L, n_chains, precision, shapes, n_hb, n_or, reps, stream, fused
             lat.kernel_times()
             lat.sweep(reps, n_hb, n_or)
             kt = lat.kernel_times()
-            out[(ty, dz)] = kt["hb_ms"] + kt["or_ms"] + kt["pass_hb_ms"] + kt["pass_or_ms"]
+            out[(ty, dz)] = sum(v for k, v in kt.items() if k.endswith("_ms"))
     finally:
         lat.close()
     return out
+
+
+def _best(times, L, what):
+    """The fastest shape; an error naming the box when the library refused
+    every candidate."""
+    if not times:
+        raise coulps.CoulpsError(
+            coulps.EINVAL, f"autotune: the library refused every {what} tile shape for box {L}")
+    return min(times, key=times.get)
 
 
 def tune_shape(L, n_chains=1, precision=coulps.F32, n_hb=1, n_or=3, reps=3, stream=None,
@@ -119,7 +147,7 @@ def tune_shape(L, n_chains=1, precision=coulps.F32, n_hb=1, n_or=3, reps=3, stre
     if key in cache:
         return tuple(cache[key]["tile"])
     times = _time_shapes(L, n_chains, precision, candidates(L, precision), n_hb, n_or, reps, stream)
-    best = min(times, key=times.get)
+    best = _best(times, L, "half-sweep")
     if use_cache:
         cache = _load_cache()
         cache[key] = {"tile": list(best), "ms": times[best]}
@@ -140,7 +168,29 @@ def tune_pass_shape(L, n_chains=1, precision=coulps.F32, n_hb=1, n_or=3, reps=3,
         return tuple(cache[key]["tile"])
     times = _time_shapes(L, n_chains, precision, pass_candidates(L, precision), n_hb, n_or, reps,
                          stream, fused=True)
-    best = min(times, key=times.get)
+    best = _best(times, L, "fused-pass")
+    if use_cache:
+        cache = _load_cache()
+        cache[key] = {"tile": list(best), "ms": times[best]}
+        _save_cache(cache)
+    return best
+
+
+def tune_pair_shape(L, n_chains=1, precision=coulps.F32, n_hb=1, n_or=3, reps=3, stream=None,
+                    use_cache=True):
+    """Best pass-pair (ty, dz) for a box shape (the schedule of fused mode 3:
+    heatbath half-sweeps, over-relaxation pairs); cached.  None when the row
+    is too wide for a pair CTA."""
+    L = tuple(int(v) for v in L)
+    cands = pair_candidates(L, precision)
+    if not cands:
+        return None
+    key = f"pair|{L[0]}x{L[1]}x{L[2]}|{n_chains}|{precision}|{n_hb}:{n_or}|{_gpu_name()}"
+    cache = _load_cache() if use_cache else {}
+    if key in cache:
+        return tuple(cache[key]["tile"])
+    times = _time_shapes(L, n_chains, precision, cands, n_hb, n_or, reps, stream, pair=True)
+    best = _best(times, L, "pass-pair")
     if use_cache:
         cache = _load_cache()
         cache[key] = {"tile": list(best), "ms": times[best]}
@@ -149,13 +199,16 @@ def tune_pass_shape(L, n_chains=1, precision=coulps.F32, n_hb=1, n_or=3, reps=3,
 
 
 def tune_lattice(lat: "coulps.Lattice", n_hb=1, n_or=3, reps=3, stream=None):
-    """Tunes both shapes; returns the half-sweep shape (the pass shape is
-    applied too and readable from lat.info())."""
+    """Tunes the half-sweep, fused-pass and pass-pair shapes; returns the
+    half-sweep shape (the others are applied too: lat.info(), lat.pair_tile())."""
     s = stream or lat._stream
     best = tune_shape(lat.L, lat.n_chains, lat.precision, n_hb, n_or, reps, s)
     lat.set_tile(*best)
     pbest = tune_pass_shape(lat.L, lat.n_chains, lat.precision, n_hb, n_or, reps, s)
     lat.set_pass_tile(*pbest)
+    qbest = tune_pair_shape(lat.L, lat.n_chains, lat.precision, n_hb, n_or, reps, s)
+    if qbest is not None and lat.pair_tile()[0] > 0:
+        lat.set_pair_tile(*qbest)
     return best
 
 

@@ -265,6 +265,21 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// One chain's (Q, P) from its nblk CTA partials [chain][nblk][2], in a fixed
+// order: lane l of a warp adds blocks l, l + 32, ..., then the warp's
+// butterfly sum.  Every lane of the warp must call it.
+__device__ __forceinline__ void chain_QP(const double *__restrict__ partials, int nblk, int chain,
+                                         int lane, double &Q, double &P) {
+  Q = 0.0;
+  P = 0.0;
+  for (int b = lane; b < nblk; b += 32) {
+    Q += partials[2 * ((size_t)chain * nblk + b) + 0];
+    P += partials[2 * ((size_t)chain * nblk + b) + 1];
+  }
+  Q = warp_sum(Q);
+  P = warp_sum(P);
+}
+
 // One sample of one chain (or system): e = Q^2 - P formed in FP64 (the
 // cancelling difference of Eq. (nsum2)), then the running sums, the batch
 // sums (kBatchMin..2*kBatchMin batches; neighbours merge and the batch length

@@ -217,6 +217,11 @@ cudaError_t launch_advance_pass(uint32_t *pass, uint32_t n, cudaStream_t s);
 cudaError_t launch_gather(const Geometry &g, const void *field, const uint32_t *idx,
                           const double *q, int64_t n, double *partials, int nblk,
                           cudaStream_t s);
+// The same gather over all chains with offsets checked on the device: an
+// offset >= chain_elems is skipped and counted in *bad (device memory).
+cudaError_t launch_gather_checked(const Geometry &g, const void *field, const uint32_t *idx,
+                                  const double *q, int64_t n, double *partials, int nblk,
+                                  unsigned *bad, cudaStream_t s);
 // Off-lattice charge sets (trilinear weights over eight corner sites; per
 // particle 8 storage offsets, 8 weights, 8 x 3 weight gradients).
 // off-lattice sets: partial blocks of a chain are `row` apart; the gather

@@ -19,17 +19,26 @@ namespace {
 
 constexpr int kGatherThreads = 256;
 
-template <typename T>
+// CHECKED (offsets from the caller's device memory, coulps_measure_static):
+// an offset >= chain_elems is skipped and counted in *bad; the sums of valid
+// offsets are formed in the same order as unchecked.
+template <typename T, bool CHECKED>
 __global__ void __launch_bounds__(kGatherThreads)
     gather_kernel(const T *__restrict__ field, size_t chain_elems,
                   const uint32_t *__restrict__ idx, const double *__restrict__ q, int64_t n,
-                  double *__restrict__ partials, int nblk, int first, int stride) {
+                  double *__restrict__ partials, int nblk, int first, int stride,
+                  unsigned *__restrict__ bad) {
   const int chain = first + (int)blockIdx.y * stride;
   const T *f = field + (size_t)chain * chain_elems;
   double sq = 0.0, sp = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * kGatherThreads + threadIdx.x; i < n;
        i += (int64_t)nblk * kGatherThreads) {
-    const double t = q[i] * (double)f[idx[i]];
+    const uint32_t at = idx[i];
+    if (CHECKED && at >= chain_elems) {
+      atomicAdd(bad, 1u);
+      continue;
+    }
+    const double t = q[i] * (double)f[at];
     sq += t;
     sp += t * t;
   }
@@ -57,18 +66,6 @@ __global__ void __launch_bounds__(kGatherThreads)
 // One warp per chain: lane l adds the partials l, l + 32, ... in order, then
 // a fixed butterfly adds the lanes (same order every run).
 constexpr int kFinalizeWarps = 8;
-
-__device__ __forceinline__ void chain_QP(const double *__restrict__ partials, int nblk, int chain,
-                                         int lane, double &Q, double &P) {
-  Q = 0.0;
-  P = 0.0;
-  for (int b = lane; b < nblk; b += 32) {
-    Q += partials[2 * ((size_t)chain * nblk + b) + 0];
-    P += partials[2 * ((size_t)chain * nblk + b) + 1];
-  }
-  Q = warp_sum(Q);
-  P = warp_sum(P);
-}
 
 __global__ void finalize_kernel(const double *__restrict__ partials, int nblk, int n_chains,
                                 double *__restrict__ stats, double *__restrict__ log,
@@ -357,13 +354,28 @@ cudaError_t launch_gather_group(const Geometry &g, const void *field, const uint
   if (count == 0) return cudaSuccess;
   dim3 grid(nblk, count);
   if (g.precision == COULPS_F32)
-    gather_kernel<float><<<grid, kGatherThreads, 0, s>>>(
+    gather_kernel<float, false><<<grid, kGatherThreads, 0, s>>>(
         reinterpret_cast<const float *>(field), g.chain_elems, idx, q, n, partials, nblk, first,
-        stride);
+        stride, nullptr);
   else
-    gather_kernel<double><<<grid, kGatherThreads, 0, s>>>(
+    gather_kernel<double, false><<<grid, kGatherThreads, 0, s>>>(
         reinterpret_cast<const double *>(field), g.chain_elems, idx, q, n, partials, nblk, first,
-        stride);
+        stride, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_checked(const Geometry &g, const void *field, const uint32_t *idx,
+                                  const double *q, int64_t n, double *partials, int nblk,
+                                  unsigned *bad, cudaStream_t s) {
+  dim3 grid(nblk, g.n_chains);
+  if (g.precision == COULPS_F32)
+    gather_kernel<float, true><<<grid, kGatherThreads, 0, s>>>(
+        reinterpret_cast<const float *>(field), g.chain_elems, idx, q, n, partials, nblk, 0, 1,
+        bad);
+  else
+    gather_kernel<double, true><<<grid, kGatherThreads, 0, s>>>(
+        reinterpret_cast<const double *>(field), g.chain_elems, idx, q, n, partials, nblk, 0, 1,
+        bad);
   return cudaGetLastError();
 }
 

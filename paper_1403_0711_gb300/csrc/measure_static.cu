@@ -13,7 +13,8 @@
 // there until the process exits.  Its device address is looked up once per
 // device (with that device current) by cudaGetSymbolAddress; host code never
 // hands the array's name itself to a kernel, because on the host that name
-// denotes a host-side stand-in, not device memory.
+// denotes a host-side stand-in, not device memory.  A device reset while the
+// library is loaded is not supported: the looked-up address would be stale.
 #include <mutex>
 
 #include "device_common.cuh"
@@ -21,16 +22,20 @@
 
 // Per-CTA (Q, P) partial sums of every call on this device.
 static __device__ __align__(256) double g_static_scratch[COULPS_STATIC_SCRATCH_DOUBLES];
+// Count of charge offsets of the current call that lie outside a chain's field.
+static __device__ __align__(256) unsigned g_static_bad[1];
 
 namespace coulps {
 namespace {
 
 constexpr int kMaxDevices = 64;
 double *g_scratch_ptr[kMaxDevices] = {};
+unsigned *g_bad_ptr[kMaxDevices] = {};
 std::mutex g_scratch_mutex;
 
-// Device address of g_static_scratch on the current device (looked up once).
-int static_scratch(double **out) {
+// Device addresses of g_static_scratch and g_static_bad on the current device
+// (looked up once per device).
+int static_scratch(double **out, unsigned **bad) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
@@ -39,28 +44,33 @@ int static_scratch(double **out) {
   if (dev < 0 || dev >= kMaxDevices) return COULPS_EUNSUPPORTED;
   std::lock_guard<std::mutex> lock(g_scratch_mutex);
   if (!g_scratch_ptr[dev]) {
-    void *p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess || p == nullptr) {
+    void *p = nullptr, *b = nullptr;
+    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || p == nullptr ||
+        cudaGetSymbolAddress(&b, g_static_bad) != cudaSuccess || b == nullptr) {
       cudaGetLastError();
       return COULPS_ECUDA;
     }
+    g_bad_ptr[dev] = static_cast<unsigned *>(b);
     g_scratch_ptr[dev] = static_cast<double *>(p);
   }
   *out = g_scratch_ptr[dev];
+  *bad = g_bad_ptr[dev];
   return COULPS_OK;
 }
 
-// Fixed-order sum of each chain's CTA partials into (Q, P, e = Q^2 - P).
+// Each chain's CTA partials added in the order of coulps_measure's finalize
+// (one warp per chain, chain_QP), so both return bitwise the same (Q, P, e);
+// NaN for every chain when an offset was out of range.
+constexpr int kQpeWarps = 8;
 __global__ void static_qpe_kernel(const double *__restrict__ partials, int nblk, int n_chains,
-                                  double *__restrict__ QPe) {
-  const int chain = blockIdx.x * blockDim.x + threadIdx.x;
-  if (chain >= n_chains) return;
-  double Q = 0.0, P = 0.0;
-  for (int b = 0; b < nblk; ++b) {
-    Q += partials[2 * ((size_t)chain * nblk + b) + 0];
-    P += partials[2 * ((size_t)chain * nblk + b) + 1];
-  }
+                                  const unsigned *__restrict__ bad, double *__restrict__ QPe) {
+  const int chain = blockIdx.x * kQpeWarps + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (chain >= n_chains) return;  // whole warps leave together
+  double Q, P;
+  chain_QP(partials, nblk, chain, lane, Q, P);
+  if (lane != 0) return;
+  if (*bad != 0u) Q = P = __longlong_as_double(0x7ff8000000000000ll);
   QPe[3 * (size_t)chain + 0] = Q;
   QPe[3 * (size_t)chain + 1] = P;
   QPe[3 * (size_t)chain + 2] = Q * Q - P;
@@ -91,15 +101,38 @@ extern "C" int coulps_measure_static(const void *field, int Lx, int Ly, int Lz, 
   g.chain_elems = 2 * g.colour_elems;
   const int nblk = gather_blocks(n);
   if ((int64_t)n_chains * nblk * 2 > COULPS_STATIC_SCRATCH_DOUBLES) return COULPS_EINVAL;
-  double *scratch = nullptr;
-  const int st = static_scratch(&scratch);
-  if (st) return st;
+  if (g.chain_elems > 0xffffffffull) return COULPS_EINVAL;  // 32-bit offsets
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (launch_gather(g, field, site_index, q, n, scratch, nblk, s) != cudaSuccess) {
+  // The work must go to the current device, whose array address is used.
+  // The stream's device is queried only outside a stream capture (the query
+  // would invalidate a capture in global mode); the legacy default stream is
+  // always the current device's.
+  if (s != nullptr) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+      cudaGetLastError();
+      return COULPS_ECUDA;
+    }
+    if (cs == cudaStreamCaptureStatusNone) {
+      int dev = 0, sdev = 0;
+      if (cudaGetDevice(&dev) != cudaSuccess || cudaStreamGetDevice(s, &sdev) != cudaSuccess) {
+        cudaGetLastError();
+        return COULPS_ECUDA;
+      }
+      if (sdev != dev) return COULPS_EINVAL;
+    }
+  }
+  double *scratch = nullptr;
+  unsigned *bad = nullptr;
+  const int st = static_scratch(&scratch, &bad);
+  if (st) return st;
+  if (cudaMemsetAsync(bad, 0, sizeof(unsigned), s) != cudaSuccess ||
+      launch_gather_checked(g, field, site_index, q, n, scratch, nblk, bad, s) != cudaSuccess) {
     cudaGetLastError();
     return COULPS_ECUDA;
   }
-  static_qpe_kernel<<<(n_chains + 127) / 128, 128, 0, s>>>(scratch, nblk, n_chains, QPe);
+  static_qpe_kernel<<<(n_chains + kQpeWarps - 1) / kQpeWarps, 32 * kQpeWarps, 0, s>>>(
+      scratch, nblk, n_chains, bad, QPe);
   if (cudaGetLastError() != cudaSuccess) return COULPS_ECUDA;
   return COULPS_OK;
 }
