@@ -1,8 +1,9 @@
 """The learned Stein control variate on the GPU.
 
 - Library-kernel evaluation = autograd path = FP64 oracle (BF16 tolerance).
-- The tensor-core conv's autograd gradients = PyTorch FP32 conv3d gradients
-  of the same BF16 operands.
+- The tensor-core conv's autograd gradients = finite differences of its own
+  forward (exact on a binary grid) and = PyTorch FP32 conv3d gradients of
+  the same BF16 operands.
 - The Stein term has zero mean under the library's own sampler.
 - Training lowers the loss and the fitted estimator keeps the plain mean.
 """
@@ -34,6 +35,17 @@ def _oracle_params(cv):
     return p
 
 
+# Tolerances of the BF16 evaluation against the FP64 oracle, relative to
+# |div| + |g . A phi|.  Inputs and activations are BF16 (relative rounding
+# 2^-9 each, through three layers), so the Stein term's two parts each carry
+# errors of a few 1e-3 of their size.  Measured on the GPU (4 nets x 3
+# fields each): whole lattice max 3.3e-3 (mean 1.3e-3), autograd path vs
+# library kernels max 7.0e-4; sub-box max 1.18e-2 (mean 2.3e-3), autograd
+# path vs kernels max 7.1e-7.  Bounds: about 2-3x the measured maxima.
+TOL_GLOBAL, TOL_GLOBAL_GRAD = 1e-2, 3e-3
+TOL_REGION, TOL_REGION_GRAD = 2.5e-2, 1e-5
+
+
 def test_evaluate_matches_autograd_path_and_oracle(env):
     torch, coulps, stream = env
     from oracle import stein as ost
@@ -57,9 +69,51 @@ def test_evaluate_matches_autograd_path_and_oracle(env):
         div = ost.divergence(phi, r, p)
         gA = float(np.sum(ost.forward(phi, r, p)["g"] * ost.apply_A(phi)))
         scale = abs(div) + abs(gA)
-        assert abs(tg_eval[k] - (div - gA)) < 3e-2 * scale, (k, tg_eval[k], div - gA, scale)
-        assert abs(tg_grad[k] - tg_eval[k]) < 1e-2 * scale, (k, tg_grad[k], tg_eval[k])
+        assert abs(tg_eval[k] - (div - gA)) < TOL_GLOBAL * scale, (k, tg_eval[k], div - gA, scale)
+        assert abs(tg_grad[k] - tg_eval[k]) < TOL_GLOBAL_GRAD * scale, (k, tg_grad[k], tg_eval[k])
     lat.close()
+
+
+def test_conv_autograd_matches_finite_differences(env):
+    """The three gradients of the tensor-core conv (Conv3dTC: data gradient by
+    the transposed tcgen05 conv, weight gradient by the library's reduction,
+    bias gradient) against finite differences of f = sum(R * conv(a, W, b)).
+    f is linear in each argument, so a difference quotient is the directional
+    derivative for any step.  Every operand sits on a coarse binary grid, so
+    the BF16 operands are exact, each FP32 accumulation is exact and the outer
+    sums are taken in FP64: the differences are exact, and so are the weight
+    and bias gradients.  The data gradient is returned in BF16 (the dtype of
+    a), so it agrees to its own rounding, 2^-8 relative per element."""
+    torch, coulps, stream = env
+    from paper_1403_0711_gb300 import stein
+    g = torch.Generator().manual_seed(11)
+
+    def grid(shape, m, den):
+        return torch.randint(-m, m + 1, shape, generator=g).float() / den
+
+    shape = (2, 5, 6, 37, 16)
+    a = grid(shape, 8, 8).to(torch.bfloat16).cuda()
+    d = grid(shape, 4, 16).to(torch.bfloat16).cuda()
+    W = grid((16, 16, 3, 3, 3), 8, 64).cuda()
+    D = grid((16, 16, 3, 3, 3), 4, 128).cuda()
+    b = grid((16,), 8, 8).cuda()
+    db = grid((16,), 4, 16).cuda()
+    R = grid(shape, 8, 8).cuda()
+
+    def f(a_, W_, b_):
+        return float((stein.Conv3dTC.apply(a_, W_, b_).double() * R.double()).sum())
+
+    a1, W1, b1 = a.clone().requires_grad_(), W.clone().requires_grad_(), b.clone().requires_grad_()
+    (stein.Conv3dTC.apply(a1, W1, b1) * R).sum().backward()
+    f0 = f(a, W, b)
+    # weight and bias: exact
+    assert f(a, W + D, b) - f0 == float((W1.grad.double() * D.double()).sum())
+    assert f(a, W, b + db) - f0 == float((b1.grad.double() * db.double()).sum())
+    # data: the gradient's own BF16 rounding
+    fd = f((a.float() + d.float()).to(torch.bfloat16), W, b) - f0
+    gd = a1.grad.double() * d.double()
+    assert abs(fd - float(gd.sum())) <= 2 ** -8 * float(gd.abs().sum()), (fd, float(gd.sum()))
+    assert fd != 0.0
 
 
 def test_conv_autograd_matches_torch(env):
@@ -163,8 +217,8 @@ def test_region_evaluate_matches_oracle(env):
         div = ost.divergence(phi, r, p, region)
         gA = float(np.sum(ost.forward(phi, r, p)["g"] * mask * ost.apply_A(phi)))
         scale = abs(div) + abs(gA)
-        assert abs(tg[k] - (div - gA)) < 3e-2 * scale, (k, tg[k], div - gA, scale)
-        assert abs(tg_grad[k] - tg[k]) < 1e-2 * scale, (k, tg_grad[k], tg[k])
+        assert abs(tg[k] - (div - gA)) < TOL_REGION * scale, (k, tg[k], div - gA, scale)
+        assert abs(tg_grad[k] - tg[k]) < TOL_REGION_GRAD * scale, (k, tg_grad[k], tg[k])
     lat.close()
 
 
@@ -302,7 +356,8 @@ def test_local_cv_reduces_variance_on_cube(env):
     n = plain[:, 0].sum()
     var_p = plain[:, 2].sum() / n - (plain[:, 1].sum() / n) ** 2
     var_c = cvst[:, 2].sum() / n - (cvst[:, 1].sum() / n) ** 2
-    assert var_c < 0.6 * var_p, (var_c, var_p)
+    # measured 0.31-0.34 over four training seeds on the GPU
+    assert var_c < 0.5 * var_p, (var_c, var_p)
     # per-chain means of c T g = e - y: chains are independent
     ctg = (plain[:, 1] - cvst[:, 1]) / plain[:, 0]
     se = ctg.std(ddof=1) / math.sqrt(len(ctg))
