@@ -48,6 +48,9 @@ CONFIG = {
 }
 PROFILE_TRAFFIC = {
     "pass_kernel<float, over-relaxation>": ROOT / "profiles" / "pass_or_128c_64ch.txt",
+    "pair_kernel<float, over-relaxation, over-relaxation>":
+        ROOT / "profiles" / "pair_or_128c_64ch.txt",
+    "halfsweep_kernel<float, heatbath>": ROOT / "profiles" / "heatbath_halfsweep_128c_64ch.txt",
 }
 KERNEL_SOURCES = ["sweep.cu", "pass_fused.cu", "pass_pair.cu", "tile_march.cuh",
                   "device_common.cuh", "internal.h"]
