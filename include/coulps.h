@@ -420,7 +420,8 @@ int coulps_checkpoint_load(coulps_lattice_t lat, coulps_charges_t ch, const char
  * word 2 = s (its "chain" id), so each system reproduces a one-chain lattice
  * with that chain id.  Storage, boundary, update rules and estimator are those
  * of the lattice API above; the measured compound sweep gathers Q, P in its
- * last half-sweep and is replayed as one CUDA graph. */
+ * last kernel and is replayed as one CUDA graph.  By default the
+ * over-relaxation passes run as fused passes (coulps_batch_set_fused). */
 typedef struct coulps_batch *coulps_batch_t;
 
 /* dims[3s..3s+2] = (Lx, Ly, Lz) of system s, limits as coulps_lattice_create.
@@ -438,6 +439,23 @@ int coulps_batch_system_tile(coulps_batch_t b, int system, int32_t *ty_dz);
 /* info[0..6] = n_systems, work-list tiles, persistent CTAs, shared memory
  * bytes per CTA, pass counter, field bytes, total sites. */
 int coulps_batch_info(coulps_batch_t b, int64_t *info);
+
+/* Fused over-relaxation passes (enable = 1, the default): the
+ * over-relaxation passes of a compound sweep run as fused passes (both
+ * half-sweeps of a pass in one z-march, each site read and written once, 8
+ * bytes per site in FP32 instead of 12) by one persistent launch per pass
+ * that walks a list of pass tiles, between the fields and a second copy of
+ * them (twice the field memory); the heatbath passes stay half-sweeps, the
+ * first written into the second copy when n_or is odd (with no heatbath
+ * pass, the last of an odd block runs as half-sweeps); the sweep ends in the
+ * fields.  enable = 0: half-sweeps only (frees the copy).  Results are
+ * bitwise those of the half-sweeps.  Pass tile of every system:
+ * ty_dz[2s] rows, ty_dz[2s+1] planes (0 = keep; (ty + 2) * W / 4 <= 256
+ * threads, ty + 4 <= 256, shared memory <= 227 KiB).
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+int coulps_batch_set_fused(coulps_batch_t b, int enable);
+int coulps_batch_set_pass_tiles(coulps_batch_t b, const int32_t *ty_dz);
+int coulps_batch_system_pass_tile(coulps_batch_t b, int system, int32_t *ty_dz);
 
 /* Charges of all systems: those of system s are entries offsets[s] ..
  * offsets[s+1]-1 of site_xyz (3 per charge, inside that system's box) and q.

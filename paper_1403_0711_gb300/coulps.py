@@ -46,6 +46,7 @@ EXPORTS = (
     "coulps_heatbath_noise", "coulps_near_pairs", "coulps_offlattice_corners",
     "coulps_set_streams", "coulps_selftest_wait", "coulps_clear_error",
     "coulps_set_pair_tile", "coulps_pair_tile", "coulps_kernel_times_n",
+    "coulps_batch_set_fused", "coulps_batch_set_pass_tiles", "coulps_batch_system_pass_tile",
 )
 SCHEDULE_ALIGNED, SCHEDULE_PHASED, SCHEDULE_SHIFTED = 0, 1, 2
 STAT_STRIDE = 72
@@ -119,6 +120,9 @@ def load(path: str | Path | None = None):
         "coulps_batch_destroy": (None, [vp]),
         "coulps_batch_set_tiles": (i32, [vp, P(ctypes.c_int32)]),
         "coulps_batch_system_tile": (i32, [vp, i32, P(ctypes.c_int32)]),
+        "coulps_batch_set_fused": (i32, [vp, i32]),
+        "coulps_batch_set_pass_tiles": (i32, [vp, P(ctypes.c_int32)]),
+        "coulps_batch_system_pass_tile": (i32, [vp, i32, P(ctypes.c_int32)]),
         "coulps_batch_info": (i32, [vp, P(i64)]),
         "coulps_batch_charges": (i32, [vp, P(i64), P(ctypes.c_int32), P(f64), i64]),
         "coulps_batch_sweep": (i32, [vp, i32, i32, i32]),
@@ -578,6 +582,25 @@ class Batch:
         for s in range(self.n):
             a = (ctypes.c_int32 * 2)()
             _check(self._lib.coulps_batch_system_tile(self.handle, s, a), "coulps_batch_system_tile")
+            out.append((a[0], a[1]))
+        return out
+
+    def set_fused(self, enable):
+        """Fused over-relaxation passes (1, default) or half-sweeps only (0)."""
+        _check(self._lib.coulps_batch_set_fused(self.handle, int(enable)), "coulps_batch_set_fused")
+
+    def set_pass_tiles(self, ty_dz):
+        t = np.ascontiguousarray(np.asarray(ty_dz, dtype=np.int32).reshape(-1, 2))
+        assert len(t) == self.n
+        _check(self._lib.coulps_batch_set_pass_tiles(self.handle, t.ctypes.data_as(
+            ctypes.POINTER(ctypes.c_int32))), "coulps_batch_set_pass_tiles")
+
+    def pass_tiles(self):
+        out = []
+        for s in range(self.n):
+            a = (ctypes.c_int32 * 2)()
+            _check(self._lib.coulps_batch_system_pass_tile(self.handle, s, a),
+                   "coulps_batch_system_pass_tile")
             out.append((a[0], a[1]))
         return out
 

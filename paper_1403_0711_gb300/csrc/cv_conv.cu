@@ -17,9 +17,11 @@
 // K-major core-matrix layout without swizzle (8 rows x 16 bytes per core
 // matrix, next 8 rows at +128 bytes, the second 8 channels at +plane): a shift
 // by dx is just a +16 byte start address.  Out-of-box rows, planes and x are
-// zero-filled by the TMA unit.  A CTA walks all y of a column (b, z, x tile)
-// keeping 4 rows per input plane in a ring, so each tile loads one new row per
-// plane, one tile ahead.  Weights sit in shared memory in the same layout
+// zero-filled by the TMA unit.  A CTA walks the y range of a work item (a
+// chunk of y_chunk rows of a column (b, z, x tile)), keeping 4 rows per input
+// plane in a ring, so each tile loads one new row per plane, one tile ahead;
+// the chunk length is chosen so that there are enough items to fill the GPU
+// (short chunks re-load two halo rows per chunk).  Weights sit in shared memory in the same layout
 // (prepared on the host), loaded once per CTA.  One elected thread issues the
 // MMAs of tile y into one of two TMEM accumulators and commits them to an
 // mbarrier while the warps read tile y-1 from the other (tcgen05.ld: 32 lanes
@@ -131,14 +133,17 @@ struct CvConvArgs {
   int Lx, Ly, Lz, nb;
   int x_period;        // > 0: output columns x with x % x_period == x_period - 1 are 0
   int n_cols;          // nb * Lz * ceil(Lx / 128): one column = all y of (b, z, x tile)
+  int y_chunk;         // rows of y per work item
+  int n_items;         // n_cols * ceil(Ly / y_chunk)
   int *err;
 };
 
-// One CTA walks columns (b, z, x tile) and, within a column, the tiles y =
-// 0 .. Ly-1.  Tile y needs input rows y-1, y, y+1 of planes z-1, z, z+1; the
-// rows of each plane sit in a 4-row ring, so each tile loads one new row per
-// plane (row y+2, one tile ahead).  Tile y's 27 MMAs go to TMEM buffer
-// (count & 1) while the warps read tile y-1 from the other buffer.
+// One CTA walks work items (a column (b, z, x tile) and a chunk of rows
+// y0 .. y1-1) and, within an item, the tiles y = y0 .. y1-1.  Tile y needs
+// input rows y-1, y, y+1 of planes z-1, z, z+1; the rows of each plane sit in
+// a 4-row ring, so each tile loads one new row per plane (row y+2, one tile
+// ahead).  Tile y's 27 MMAs go to TMEM buffer (count & 1) while the warps read
+// tile y-1 from the other buffer.
 __global__ void __launch_bounds__(kCvThreads)
     cv_conv3d_kernel(const __grid_constant__ CUtensorMap tm_in, const CvConvArgs a) {
   extern __shared__ unsigned char smem_raw[];
@@ -219,20 +224,23 @@ __global__ void __launch_bounds__(kCvThreads)
     }
   };
 
-  for (int col = blockIdx.x; col < a.n_cols && !aborted; col += gridDim.x) {
-    int r = col;
+  const int n_chunks = (a.Ly + a.y_chunk - 1) / a.y_chunk;
+  for (int item = blockIdx.x; item < a.n_items && !aborted; item += gridDim.x) {
+    int r = item / n_chunks;
+    const int ylo = (item % n_chunks) * a.y_chunk;
+    const int ny = min(a.y_chunk, a.Ly - ylo);
     const int x0 = (r % xt) * kTileX;
     r /= xt;
     const int z = r % a.Lz;
     const int b = r / a.Lz;
-    const int nrows = a.Ly + 2;
+    const int nrows = ny + 2;  // row k of the item is input row ylo - 1 + k
     auto issue_row = [&](int k) {  // thread 0
       const int64_t g = grow + k;
       const uint32_t bar = smem_addr(&bars[row_slot(g)]);
       mbar_arrive_expect_tx(bar, 6 * kRowSites * 16);
       for (int dzi = 0; dzi < 3; ++dzi)
         for (int h = 0; h < 2; ++h)
-          tma_load_5d(row_base(dzi, g) + h * kPlaneBytes, &tm_in, 8 * h, x0 - 1, k - 1,
+          tma_load_5d(row_base(dzi, g) + h * kPlaneBytes, &tm_in, 8 * h, x0 - 1, ylo + k - 1,
                       z + dzi - 1, b, bar);
       ++rows_issued;
     };
@@ -244,7 +252,7 @@ __global__ void __launch_bounds__(kCvThreads)
       for (int k = 0; k < kRing && k < nrows; ++k) issue_row(k);
     bool ok = wait_row(0) && wait_row(1);
     if (tid == 0 && ok) rows_waited += 2;
-    for (int y = 0; y < a.Ly; ++y) {
+    for (int y = 0; y < ny; ++y) {  // tile ylo + y
       ok = ok && wait_row(y + 2);
       if (tid == 0 && ok) {
         ++rows_waited;
@@ -280,7 +288,7 @@ __global__ void __launch_bounds__(kCvThreads)
         aborted = true;
         break;
       }
-      if (y > 0) epilogue(gtile - 1, b, z, y - 1, x0);
+      if (y > 0) epilogue(gtile - 1, b, z, ylo + y - 1, x0);
       fence_before_sync();
       __syncthreads();  // the TMEM buffer read above is free for tile y + 1
       fence_after_sync();
@@ -303,7 +311,7 @@ __global__ void __launch_bounds__(kCvThreads)
         aborted = true;
         break;
       }
-      epilogue(tp, b, z, a.Ly - 1, x0);
+      epilogue(tp, b, z, ylo + ny - 1, x0);
       fence_before_sync();
       __syncthreads();
       fence_after_sync();
@@ -371,8 +379,15 @@ int cv_conv3d_launch(const void *in_bf16, const void *wpack, const float *bias, 
     per_sm = 1;
   }
   if (per_sm > 8) per_sm = 8;  // 8 x 32 TMEM columns of 512
-  int grid = sms * per_sm;
-  if (grid > a.n_cols) grid = a.n_cols;
+  // rows per item: whole columns when there are enough of them, else chunks
+  // of at least 2 rows, so that about two items per resident CTA exist
+  const int slots = sms * per_sm;
+  a.y_chunk = Ly;
+  while (a.y_chunk > 2 && (int64_t)a.n_cols * ((Ly + a.y_chunk - 1) / a.y_chunk) < 2 * slots)
+    a.y_chunk = (a.y_chunk + 1) / 2;
+  a.n_items = a.n_cols * ((Ly + a.y_chunk - 1) / a.y_chunk);
+  int grid = slots;
+  if (grid > a.n_items) grid = a.n_items;
   if (grid < 1) return COULPS_OK;
   cv_conv3d_kernel<<<grid, kCvThreads, smem, s>>>(map, a);
   return cudaGetLastError() == cudaSuccess ? COULPS_OK : COULPS_ECUDA;

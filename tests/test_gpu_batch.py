@@ -76,6 +76,51 @@ def test_batch_tiles_do_not_change_fields(cl, stream):
     b.close()
 
 
+@pytest.mark.parametrize("prec,n_hb,n_or", [(0, 1, 3), (0, 1, 2), (1, 2, 2), (0, 0, 3), (0, 0, 2),
+                                           (1, 1, 1), (0, 2, 3), (0, 1, 0)])
+def test_batch_fused_passes_equal_half_sweeps(cl, stream, prec, n_hb, n_or):
+    """Fused over-relaxation passes (the default) against half-sweeps only: the
+    fields bitwise, the samples to FP64 summation order (the last kernel
+    gathers over other tiles), for odd and even over-relaxation counts with
+    and without heatbath passes, uneven boxes down to one site."""
+    systems = _charges(DIMS, 21)
+    out = []
+    for fused in (0, 1):
+        b = cl.Batch(DIMS, precision=prec, seed=29, stream=stream)
+        b.set_fused(fused)
+        b.set_charges(systems, log_capacity=5)
+        b.sweep(3, 1, 1)  # a non-zero field for over-relaxation-only mixes
+        b.run(1, 5, n_hb, n_or)
+        out.append((b.samples(), [b.field(k) for k in range(len(DIMS))], b.info()["pass"]))
+        b.close()
+    (sa, fa, pa), (sb, fb, pb) = out
+    assert pa == pb
+    for k in range(len(DIMS)):
+        assert np.array_equal(fa[k], fb[k]), k
+        if n_hb + n_or > 0:
+            assert sample_err(sb[:, k], sa[:, k]) < 1e-13, k
+
+
+def test_batch_pass_tiles_do_not_change_fields(cl, stream):
+    systems = _charges(DIMS, 23)
+    a = cl.Batch(DIMS, precision=0, seed=31, stream=stream)
+    a.set_charges(systems, log_capacity=4)
+    a.run(1, 4, 1, 3)
+    b = cl.Batch(DIMS, precision=0, seed=31, stream=stream)
+    b.set_pass_tiles([(max(1, min(3, L[1])), 2) for L in DIMS])
+    assert b.pass_tiles()[0] == (3, 2)
+    b.set_charges(systems, log_capacity=4)
+    b.run(1, 4, 1, 3)
+    sa, sb = a.samples(), b.samples()
+    for k in range(len(DIMS)):
+        assert np.array_equal(a.field(k), b.field(k)), k
+        assert sample_err(sb[:, k], sa[:, k]) < 1e-13, k
+    with pytest.raises(cl.CoulpsError):
+        b.set_pass_tiles([(300, 0)] * len(DIMS))
+    a.close()
+    b.close()
+
+
 def test_batch_system0_equals_single_lattice(cl, stream):
     from paper_1403_0711_gb300 import inputs
     L = (20, 18, 16)
