@@ -52,7 +52,8 @@ PROFILE_TRAFFIC = {
         ROOT / "profiles" / "pair_or_128c_64ch.txt",
     "halfsweep_kernel<float, heatbath>": ROOT / "profiles" / "heatbath_halfsweep_128c_64ch.txt",
 }
-KERNEL_SOURCES = ["sweep.cu", "pass_fused.cu", "pass_pair.cu", "tile_march.cuh",
+KERNEL_SOURCES = ["sweep.cu", "pass_fused.cu", "pass_pair.cu", "tile_march.cuh", "pass_march.cuh",
+                  "pair_march.cuh",
                   "device_common.cuh", "internal.h"]
 FUSED_MODES = {"off": 0, "on": 1, "all": 2, "pairs": 3, "allpairs": 4}
 
@@ -97,6 +98,8 @@ def parse():
                     help="training rounds (every chain contributes one sample per round)")
     ap.add_argument("--cv-global", action="store_true",
                     help="also run the whole-lattice control variate on the +-1 system")
+    ap.add_argument("--batch-fused", type=int, choices=[0, 1, 2, 3], default=None,
+                    help="many-system fused mode (coulps_batch_set_fused; default: the library's)")
     ap.add_argument("--workload", choices=["chains128", "large512", "sweep", "batched", "cv", "cube",
                                            "cv_eval", "paper", "gcv", "offlattice"],
                     default="chains128", help="secondary workloads print their own line")
@@ -682,10 +685,12 @@ def batched_throughput(args, stream, steps):
     from paper_1403_0711_gb300 import coulps, inputs
     systems = inputs.batch_systems(256, seed=7)
     b = coulps.Batch([L_ for L_, _, _ in systems], precision=coulps.F32, seed=77, stream=stream)
+    if getattr(args, "batch_fused", None) is not None:
+        b.set_fused(args.batch_fused)
     b.set_charges([(s_, q_) for _, s_, q_ in systems])
     info = b.info()
     rate, ms = _timed(stream, lambda: b.run(0, 1, N_HB, N_OR), info["sites"] * PASSES, steps, 10)
-    r = {"systems": 256, "sites": info["sites"], "tiles": info["tiles"],
+    r = {"systems": 256, "sites": info["sites"], "tiles": info["tiles"], "fused_mode": b.fused(),
          "persistent_ctas": info["grid"], "site_updates_per_s": rate, "ms_per_step": ms,
          "steps": steps,
          "algorithmic_GBps_halfsweep_bytes": rate / PASSES * (8 + 12 * N_OR) / 1e9}

@@ -421,7 +421,7 @@ int coulps_checkpoint_load(coulps_lattice_t lat, coulps_charges_t ch, const char
  * with that chain id.  Storage, boundary, update rules and estimator are those
  * of the lattice API above; the measured compound sweep gathers Q, P in its
  * last kernel and is replayed as one CUDA graph.  By default the
- * over-relaxation passes run as fused passes (coulps_batch_set_fused). */
+ * over-relaxation passes run as pass pairs (coulps_batch_set_fused). */
 typedef struct coulps_batch *coulps_batch_t;
 
 /* dims[3s..3s+2] = (Lx, Ly, Lz) of system s, limits as coulps_lattice_create.
@@ -436,26 +436,43 @@ void coulps_batch_destroy(coulps_batch_t b);
 int coulps_batch_set_tiles(coulps_batch_t b, const int32_t *ty_dz);
 int coulps_batch_system_tile(coulps_batch_t b, int system, int32_t *ty_dz);
 
-/* info[0..6] = n_systems, work-list tiles, persistent CTAs, shared memory
- * bytes per CTA, pass counter, field bytes, total sites. */
+/* info[0..9] = n_systems, work-list tiles, persistent CTAs, shared memory
+ * bytes per CTA, pass counter, field bytes, total sites, fused-pass CTAs,
+ * pass-pair CTAs and threads per pair CTA (0 without pass pairs). */
 int coulps_batch_info(coulps_batch_t b, int64_t *info);
 
-/* Fused over-relaxation passes (enable = 1, the default): the
- * over-relaxation passes of a compound sweep run as fused passes (both
- * half-sweeps of a pass in one z-march, each site read and written once, 8
- * bytes per site in FP32 instead of 12) by one persistent launch per pass
- * that walks a list of pass tiles, between the fields and a second copy of
- * them (twice the field memory); the heatbath passes stay half-sweeps, the
- * first written into the second copy when n_or is odd (with no heatbath
- * pass, the last of an odd block runs as half-sweeps); the sweep ends in the
- * fields.  enable = 0: half-sweeps only (frees the copy).  Results are
- * bitwise those of the half-sweeps.  Pass tile of every system:
- * ty_dz[2s] rows, ty_dz[2s+1] planes (0 = keep; (ty + 2) * W / 4 <= 256
- * threads, ty + 4 <= 256, shared memory <= 227 KiB).
+/* Fused over-relaxation passes, between the fields and a second copy of
+ * them (twice the field memory).  enable = 1: the over-relaxation passes of
+ * a compound sweep run as fused passes (both half-sweeps of a pass in one
+ * z-march, each site read and written once, 8 bytes per site in FP32
+ * instead of 12), one persistent launch per pass over a list of pass tiles.
+ * enable = 2 (the default when every system admits a pair tile): they run
+ * as pass pairs (two passes in one z-march, 4 bytes per site and pass), one
+ * persistent launch per pair over a list of pair tiles, largest first, and
+ * a fused pass for an odd remainder.  The heatbath passes stay half-sweeps,
+ * written into the second copy when the number of out-of-place kernels is
+ * odd (with no heatbath pass, a pair becomes two fused passes, or the last
+ * pass runs as half-sweeps); the sweep ends in the fields.  enable = 3: all
+ * passes, heatbath ones included, as pass pairs and fused passes (an even
+ * number of kernels: by n = n_hb + n_or mod 4, n / 2 pairs; (n - 3) / 2
+ * pairs and 3 fused passes; n / 2 - 1 and 2; (n - 1) / 2 and 1; a single
+ * pass as half-sweeps).  enable = 0:
+ * half-sweeps only (frees the copy).  Results are bitwise those of the
+ * half-sweeps in every mode.  EINVAL for enable >= 2 if some system admits no
+ * pair tile.
+ * Pass tile of every system: ty_dz[2s] rows, ty_dz[2s+1] planes (0 = keep;
+ * (ty + 2) * W / 4 <= 256 threads, ty + 4 <= 256, shared memory <= 227 KiB).
+ * Pair tile of every system: the same form ((ty + 6) * W / 4 <= 512
+ * threads in FP32, 256 in FP64, ty + 8 <= 256, shared memory <= 227 KiB;
+ * ty = 0 in coulps_batch_system_pair_tile: no pair tile fits).
+ * coulps_batch_fused returns the mode (-1 for a null handle).
  * Errors: EINVAL, ENOMEM, ECUDA. */
 int coulps_batch_set_fused(coulps_batch_t b, int enable);
+int coulps_batch_fused(coulps_batch_t b);
 int coulps_batch_set_pass_tiles(coulps_batch_t b, const int32_t *ty_dz);
 int coulps_batch_system_pass_tile(coulps_batch_t b, int system, int32_t *ty_dz);
+int coulps_batch_set_pair_tiles(coulps_batch_t b, const int32_t *ty_dz);
+int coulps_batch_system_pair_tile(coulps_batch_t b, int system, int32_t *ty_dz);
 
 /* Charges of all systems: those of system s are entries offsets[s] ..
  * offsets[s+1]-1 of site_xyz (3 per charge, inside that system's box) and q.

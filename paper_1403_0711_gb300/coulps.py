@@ -47,6 +47,7 @@ EXPORTS = (
     "coulps_set_streams", "coulps_selftest_wait", "coulps_clear_error",
     "coulps_set_pair_tile", "coulps_pair_tile", "coulps_kernel_times_n",
     "coulps_batch_set_fused", "coulps_batch_set_pass_tiles", "coulps_batch_system_pass_tile",
+    "coulps_batch_fused", "coulps_batch_set_pair_tiles", "coulps_batch_system_pair_tile",
 )
 SCHEDULE_ALIGNED, SCHEDULE_PHASED, SCHEDULE_SHIFTED = 0, 1, 2
 STAT_STRIDE = 72
@@ -123,6 +124,9 @@ def load(path: str | Path | None = None):
         "coulps_batch_set_fused": (i32, [vp, i32]),
         "coulps_batch_set_pass_tiles": (i32, [vp, P(ctypes.c_int32)]),
         "coulps_batch_system_pass_tile": (i32, [vp, i32, P(ctypes.c_int32)]),
+        "coulps_batch_fused": (i32, [vp]),
+        "coulps_batch_set_pair_tiles": (i32, [vp, P(ctypes.c_int32)]),
+        "coulps_batch_system_pair_tile": (i32, [vp, i32, P(ctypes.c_int32)]),
         "coulps_batch_info": (i32, [vp, P(i64)]),
         "coulps_batch_charges": (i32, [vp, P(i64), P(ctypes.c_int32), P(f64), i64]),
         "coulps_batch_sweep": (i32, [vp, i32, i32, i32]),
@@ -566,9 +570,10 @@ class Batch:
             pass
 
     def info(self):
-        a = (ctypes.c_int64 * 7)()
+        a = (ctypes.c_int64 * 10)()
         _check(self._lib.coulps_batch_info(self.handle, a), "coulps_batch_info")
-        keys = ("n_systems", "tiles", "grid", "smem", "pass", "field_bytes", "sites")
+        keys = ("n_systems", "tiles", "grid", "smem", "pass", "field_bytes", "sites",
+                "pass_grid", "pair_grid", "pair_threads")
         return dict(zip(keys, list(a)))
 
     def set_tiles(self, ty_dz):
@@ -585,9 +590,29 @@ class Batch:
             out.append((a[0], a[1]))
         return out
 
-    def set_fused(self, enable):
-        """Fused over-relaxation passes (1, default) or half-sweeps only (0)."""
-        _check(self._lib.coulps_batch_set_fused(self.handle, int(enable)), "coulps_batch_set_fused")
+    def set_fused(self, mode):
+        """Over-relaxation passes as half-sweeps only (0), fused passes (1) or
+        pass pairs (2, the default where every system admits a pair tile); 3:
+        all passes, heatbath ones included, as pass pairs and fused passes."""
+        _check(self._lib.coulps_batch_set_fused(self.handle, int(mode)), "coulps_batch_set_fused")
+
+    def fused(self):
+        return int(self._lib.coulps_batch_fused(self.handle))
+
+    def set_pair_tiles(self, ty_dz):
+        t = np.ascontiguousarray(np.asarray(ty_dz, dtype=np.int32).reshape(-1, 2))
+        assert len(t) == self.n
+        _check(self._lib.coulps_batch_set_pair_tiles(self.handle, t.ctypes.data_as(
+            ctypes.POINTER(ctypes.c_int32))), "coulps_batch_set_pair_tiles")
+
+    def pair_tiles(self):
+        out = []
+        for s in range(self.n):
+            a = (ctypes.c_int32 * 2)()
+            _check(self._lib.coulps_batch_system_pair_tile(self.handle, s, a),
+                   "coulps_batch_system_pair_tile")
+            out.append((a[0], a[1]))
+        return out
 
     def set_pass_tiles(self, ty_dz):
         t = np.ascontiguousarray(np.asarray(ty_dz, dtype=np.int32).reshape(-1, 2))

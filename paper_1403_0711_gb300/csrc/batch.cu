@@ -13,14 +13,19 @@
 // system's partials in tile order.  The whole measured compound sweep is one
 // CUDA graph.
 //
-// Fused over-relaxation passes (coulps_batch_set_fused, on by default): the
-// over-relaxation passes run as fused passes (both half-sweeps of a pass in
-// one z-march, pass_march.cuh) from one copy of the fields to a second one
-// and back, by a persistent kernel that walks a list of pass tiles (each
-// system with its own pass tile shape and tensor maps on both copies); the
-// heatbath passes stay half-sweeps, the first written out of place into the
-// second copy when the over-relaxation count is odd, so that the compound
-// sweep ends in the first copy.  The sample is gathered by the last kernel.
+// Fused over-relaxation passes (coulps_batch_set_fused): the
+// over-relaxation passes run from one copy of the fields to a second one and
+// back, either as fused passes (both half-sweeps of a pass in one z-march,
+// pass_march.cuh; mode 1) or as pass pairs (two passes in one z-march,
+// pair_march.cuh) with a fused pass for an odd remainder (mode 2, the
+// default where every system admits a pair tile), by persistent kernels that
+// walk lists of tiles (each system with its own tile shapes and tensor maps
+// on both copies).  The heatbath passes stay half-sweeps, written out of
+// place into the second copy when the count of out-of-place kernels is odd,
+// so that the compound sweep ends in the first copy.  The sample is gathered
+// by the last kernel.  Pair tiles vary about tenfold in size between
+// systems, so the pair kernel takes them largest first from an atomic
+// counter rather than by a fixed stride.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -29,6 +34,7 @@
 
 #include "device_common.cuh"
 #include "internal.h"
+#include "pair_march.cuh"
 #include "pass_march.cuh"
 #include "tile_march.cuh"
 
@@ -49,11 +55,42 @@ struct BatchSystem {
   int PTY, PDZ;            // fused-pass tile: rows, planes
   int pgoff_base;          // first pass-tile gather offset of the system
   int pitem_begin;         // first pass tile of the system in the pass work list
+  int QTY, QDZ;            // pass-pair tile: rows, planes (QTY = 0: no pair tile fits)
+  int qgoff_base;          // first pair-tile gather offset of the system
+  int qitem_begin;         // first pair tile of the system in the pair work list
 };
+
+// Tilings of one system's lattice: half-sweep, fused-pass, pass-pair tiles.
+enum Tiling { kTileHalf = 0, kTilePass = 1, kTilePair = 2 };
 
 struct BatchItem {
   int sys, y0, z0, nz;
 };
+
+// Dynamic tile scheduler of the persistent kernels: a CTA takes the next
+// tile of the launch's list (tiles ordered largest first) from ctr[0]; after
+// its last fetch it counts itself in ctr[1], and the last CTA of the grid
+// sets both back to 0 for the next launch (launches on the batch's stream
+// never overlap).  Partials are stored by tile index, so sums do not depend
+// on which CTA ran a tile.
+__device__ __forceinline__ int next_tile(int *ctr, const int *order, int n_items) {
+  __shared__ int slot;
+  if (threadIdx.x == 0) slot = atomicAdd(&ctr[0], 1);
+  __syncthreads();
+  const int k = slot;
+  __syncthreads();  // every thread has read slot before the next fetch
+  return k < n_items ? order[k] : -1;
+}
+
+__device__ __forceinline__ void tiles_done(int *ctr) {
+  if (threadIdx.x == 0) {
+    __threadfence();  // this CTA's last fetch comes before its count
+    if (atomicAdd(&ctr[1], 1) == (int)gridDim.x - 1) {
+      ctr[0] = 0;
+      ctr[1] = 0;
+    }
+  }
+}
 
 struct BatchArgs {
   void *field;  // written: the own colour of each tile
@@ -61,6 +98,8 @@ struct BatchArgs {
   const BatchItem *items;
   int n_items;
   const CUtensorMap *maps;  // 2 per system: other-colour box (TY+2 rows), own box (TY rows)
+  const int *order;         // tile indices, largest tile first
+  int *ctr;                 // scheduler counters (next_tile)
   int colour;
   uint32_t round_keys[20];
   const uint32_t *pass_ptr;
@@ -71,7 +110,14 @@ struct BatchArgs {
   double *g_partials;  // [item][2]
 };
 
+// V quads per thread (march_tile): 2 for the FP32 heatbath half-sweep
+// without a gather (issue-bound, as in the single-lattice kernel), else 1.
 template <typename T, bool OR, bool GATHER>
+constexpr int batch_quads_per_thread() {
+  return (sizeof(T) == 4 && !OR && !GATHER) ? 2 : 1;
+}
+
+template <typename T, bool OR, bool GATHER, int V>
 __global__ void __launch_bounds__(kBatchThreads) batch_halfsweep_kernel(const BatchArgs a) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem = align_smem128(smem_raw);
@@ -79,34 +125,35 @@ __global__ void __launch_bounds__(kBatchThreads) batch_halfsweep_kernel(const Ba
   const uint32_t pass = OR ? 0u : (*a.pass_ptr + a.pass_off);
   int gbase = 0;
   ring_init(smem);
-  for (int it = blockIdx.x; it < a.n_items; it += gridDim.x) {
+  for (int it; (it = next_tile(a.ctr, a.order, a.n_items)) >= 0;) {
     const BatchItem item = a.items[it];
     const BatchSystem S = a.sys[item.sys];
     TileJob<T> j;
-    j.tm_halo = &a.maps[2 * item.sys];
-    j.tm_own = &a.maps[2 * item.sys + 1];
-    j.colour = a.colour;
-    j.map_other = a.colour ^ 1;
-    j.map_own = a.colour;
-    j.out = reinterpret_cast<T *>(a.field) + S.field_off + (long long)a.colour * S.colour_elems;
-    j.Lx = S.Lx; j.Ly = S.Ly; j.Lz = S.Lz; j.W = S.W; j.Wq = S.Wq; j.QW = S.QW; j.TY = S.TY;
-    j.y0 = item.y0;
-    j.z0 = item.z0;
-    j.nz = item.nz;
-    j.rng_id = (uint32_t)item.sys;
-    j.pass = pass;
+    j.tm_halo_ = &a.maps[2 * item.sys];
+    j.tm_own_ = &a.maps[2 * item.sys + 1];
+    j.colour_ = a.colour;
+    j.map_other_ = a.colour ^ 1;
+    j.map_own_ = a.colour;
+    j.out_ = reinterpret_cast<T *>(a.field) + S.field_off + (long long)a.colour * S.colour_elems;
+    j.Lx_ = S.Lx; j.Ly_ = S.Ly; j.Lz_ = S.Lz; j.W_ = S.W; j.Wq_ = S.Wq; j.QW_ = S.QW; j.TY_ = S.TY;
+    j.y0_ = item.y0;
+    j.z0_ = item.z0;
+    j.nz_ = item.nz;
+    j.rng_id_ = (uint32_t)item.sys;
+    j.pass_ = pass;
     if (GATHER) {
-      j.g_off = a.g_off + S.goff_base + (size_t)(item.y0 / S.TY) * S.Lz;
-      j.g_ent = a.g_ent;
-      j.other = reinterpret_cast<const T *>(a.field) + S.field_off +
+      j.g_off_ = a.g_off + S.goff_base + (size_t)(item.y0 / S.TY) * S.Lz;
+      j.g_ent_ = a.g_ent;
+      j.other_ = reinterpret_cast<const T *>(a.field) + S.field_off +
                 (long long)(a.colour ^ 1) * S.colour_elems;
-      j.g_q = a.g_q;
+      j.g_q_ = a.g_q;
     }
     double sq = 0.0, sp = 0.0;
-    const bool ok = march_tile<T, OR, GATHER>(j, K, smem, a.err, gbase, sq, sp);
+    const bool ok = march_tile<T, OR, GATHER, V>(j, K, smem, a.err, gbase, sq, sp);
     if (GATHER) block_partials(sq, sp, smem, a.g_partials + 2 * (size_t)it);
     if (!ok) break;
   }
+  tiles_done(a.ctr);
 }
 
 // Fused passes over all systems: a persistent grid walks the pass tiles
@@ -117,6 +164,8 @@ struct BatchPassArgs {
   void *dst;
   const BatchSystem *sys;
   const BatchItem *items;
+  const int *order;  // tile indices, largest tile first
+  int *ctr;          // scheduler counters (next_tile)
   int n_items;
   const CUtensorMap *maps;
   uint32_t round_keys[20];
@@ -136,48 +185,116 @@ __global__ void __launch_bounds__(kBatchPassThreads) batch_pass_kernel(const Bat
   const uint32_t pass = OR ? 0u : (*a.pass_ptr + a.pass_off);
   int gbase = 0;
   pass_ring_init(smem);
-  for (int it = blockIdx.x; it < a.n_items; it += gridDim.x) {
+  for (int it; (it = next_tile(a.ctr, a.order, a.n_items)) >= 0;) {
     const BatchItem item = a.items[it];
     const BatchSystem S = a.sys[item.sys];
-    PassJob<T> j;
-    j.tm_c1 = &a.maps[2 * item.sys];
-    j.tm_c0 = &a.maps[2 * item.sys + 1];
-    j.map_c1 = 1;
-    j.map_c0 = 0;
-    j.dst0 = reinterpret_cast<T *>(a.dst) + S.field_off;
-    j.dst1 = j.dst0 + S.colour_elems;
-    j.Lx = S.Lx; j.Ly = S.Ly; j.Lz = S.Lz; j.W = S.W; j.Wq = S.Wq; j.QW = S.QW; j.TY = S.PTY;
-    j.y0 = item.y0;
-    j.z0 = item.z0;
-    j.nz = item.nz;
-    j.rng_id = (uint32_t)item.sys;
-    j.pass = pass;
-    j.g_off = GATHER ? a.g_off + S.pgoff_base + (size_t)(item.y0 / S.PTY) * S.Lz : nullptr;
-    j.g_ent = a.g_ent;
-    j.g_q = a.g_q;
+    PassTile<T> j;
+    j.tm_c1_ = &a.maps[2 * item.sys];
+    j.tm_c0_ = &a.maps[2 * item.sys + 1];
+    j.map_c1_ = 1;
+    j.map_c0_ = 0;
+    j.dst_ = reinterpret_cast<T *>(a.dst) + S.field_off;
+    j.colour_elems_ = S.colour_elems;
+    j.Lx_ = S.Lx; j.Ly_ = S.Ly; j.Lz_ = S.Lz; j.W_ = S.W; j.Wq_ = S.Wq; j.QW_ = S.QW; j.TY_ = S.PTY;
+    j.y0_ = item.y0;
+    j.z0_ = item.z0;
+    j.nz_ = item.nz;
+    j.rng_id_ = (uint32_t)item.sys;
+    j.pass_ = pass;
+    j.g_off_ = GATHER ? a.g_off + S.pgoff_base + (size_t)(item.y0 / S.PTY) * S.Lz : nullptr;
+    j.g_ent_ = a.g_ent;
+    j.g_q_ = a.g_q;
     double sq = 0.0, sp = 0.0;
     const bool ok = march_pass<T, OR, GATHER>(j, K, smem, a.err, gbase, sq, sp);
     if (GATHER) block_partials(sq, sp, smem, a.g_partials + 2 * (size_t)it);
     if (!ok) break;
   }
+  tiles_done(a.ctr);
 }
 
-// Each system's tile partials added in tile order: the half-sweep tiles, or
-// (pass_tiles) the fused-pass tiles.
+// Over-relaxation pass pairs over all systems: a persistent grid (one CTA
+// per SM) takes pair tiles (system, y0, z0, nz) in order of decreasing size
+// from an atomic counter, each CTA running march_pair tile after tile with
+// its ring phases carried over; the source copy's tensor maps are 2 per
+// system (colour-1 box QTY + 8 rows, colour-0 box QTY + 6 rows), dst the
+// other copy.  Partials are stored by tile index, so the gathered sums do
+// not depend on which CTA ran a tile.
+struct BatchPairArgs {
+  void *dst;
+  const uint32_t *pass_ptr;  // Philox pass of pass A: *pass_ptr + pass_off
+  uint32_t pass_off;
+  const BatchSystem *sys;
+  const BatchItem *items;  // pair tiles in system order
+  const int *order;        // tile indices, largest tile first
+  int n_items;
+  const CUtensorMap *maps;
+  uint32_t round_keys[20];
+  int *err;
+  int *ctr;  // scheduler counters (next_tile)
+  const uint32_t *g_off, *g_ent;  // grouped by (pair y tile, z) per system
+  const double *g_q;
+  double *g_partials;  // [pair tile][2]
+};
+
+template <typename T, bool A_OR, bool B_OR, bool GATHER>
+__global__ void __launch_bounds__(sizeof(T) == 4 ? kPairMaxThreads32 : kPairMaxThreads64, 1)
+    batch_pair_kernel(const BatchPairArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *smem = align_smem128(smem_raw);
+  const PhiloxKeys &K = *reinterpret_cast<const PhiloxKeys *>(a.round_keys);
+  int gbase = 0;
+  pair_ring_init(smem);
+  for (int it; (it = next_tile(a.ctr, a.order, a.n_items)) >= 0;) {
+    const BatchItem item = a.items[it];
+    const BatchSystem S = a.sys[item.sys];
+    PairTile<T> j;
+    j.tm_c1_ = &a.maps[2 * item.sys];
+    j.tm_c0_ = &a.maps[2 * item.sys + 1];
+    j.map_c1_ = 1;
+    j.map_c0_ = 0;
+    j.dst_ = reinterpret_cast<T *>(a.dst) + S.field_off;
+    j.colour_elems_ = S.colour_elems;
+    j.Lx_ = S.Lx; j.Ly_ = S.Ly; j.Lz_ = S.Lz; j.W_ = S.W; j.Wq_ = S.Wq; j.QW_ = S.QW; j.TY_ = S.QTY;
+    j.y0_ = item.y0;
+    j.z0_ = item.z0;
+    j.nz_ = item.nz;
+    j.rng_id_ = (uint32_t)item.sys;
+    j.pass_ = (A_OR && B_OR) ? 0u : (*a.pass_ptr + a.pass_off);
+    j.g_off_ = GATHER ? a.g_off + S.qgoff_base + (size_t)(item.y0 / S.QTY) * S.Lz : nullptr;
+    j.g_ent_ = a.g_ent;
+    j.g_q_ = a.g_q;
+    double sq = 0.0, sp = 0.0;
+    const bool ok = march_pair<T, A_OR, B_OR, GATHER>(j, K, smem, a.err, gbase, sq, sp);
+    if (GATHER) block_partials(sq, sp, smem, a.g_partials + 2 * (size_t)it);
+    if (!ok) break;
+  }
+  tiles_done(a.ctr);
+}
+
+// Each system's tile partials added up by one warp (lane l takes tiles
+// l, l + 32, ... of the system, then a fixed butterfly), for the tiling of
+// the kernel that gathered; lane 0 records the sample.
 __global__ void batch_finalize_kernel(const double *__restrict__ partials,
                                       const BatchSystem *__restrict__ sys, int n_sys, int n_items,
-                                      bool pass_tiles, double *__restrict__ stats,
+                                      int tiling, double *__restrict__ stats,
                                       double *__restrict__ log, int64_t log_cap, int *err) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n_sys) return;
-  const int b0 = pass_tiles ? sys[s].pitem_begin : sys[s].item_begin;
-  const int b1 = s + 1 < n_sys ? (pass_tiles ? sys[s + 1].pitem_begin : sys[s + 1].item_begin)
-                               : n_items;
+  const int s = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (s >= n_sys) return;  // whole warps
+  auto begin = [&](int t) {
+    return tiling == kTilePair ? sys[t].qitem_begin
+                               : (tiling == kTilePass ? sys[t].pitem_begin : sys[t].item_begin);
+  };
+  const int b0 = begin(s);
+  const int b1 = s + 1 < n_sys ? begin(s + 1) : n_items;
   double Q = 0.0, P = 0.0;
-  for (int b = b0; b < b1; ++b) {
+  for (int b = b0 + lane; b < b1; b += 32) {
     Q += partials[2 * (size_t)b];
     P += partials[2 * (size_t)b + 1];
   }
+  Q = warp_sum(Q);
+  P = warp_sum(P);
+  if (lane != 0) return;
   double *st = stats + (size_t)s * kStatStride;
   const int64_t k = (int64_t)st[kStatN];
   double *row = (log != nullptr && k < log_cap) ? log + 3 * ((size_t)k * n_sys + s) : nullptr;
@@ -216,9 +333,11 @@ struct coulps_batch {
   size_t field_bytes = 0;
   BatchSystem *d_sys = nullptr;
   BatchItem *d_items = nullptr;
+  int *d_order = nullptr, *d_porder = nullptr;  // tile lists largest first
   CUtensorMap *d_maps = nullptr;  // half-sweep maps: [copy][system][2]
-  // fused over-relaxation passes (fused = 1): a second copy of the fields,
-  // the pass tiles, their maps [copy][system][2] and gather lists
+  // fused over-relaxation passes (fused >= 1): a second copy of the fields,
+  // the pass tiles, their maps [copy][system][2] and gather lists; with
+  // fused = 2 also the pair tiles
   int fused = 0;
   void *field2 = nullptr;
   std::vector<BatchItem> pitems;
@@ -228,11 +347,21 @@ struct coulps_batch {
   double *d_pgq = nullptr, *d_ppart = nullptr;
   int pgrid = 0;
   size_t psmem = 0;
+  std::vector<BatchItem> qitems;
+  BatchItem *d_qitems = nullptr;
+  int *d_qorder = nullptr;
+  CUtensorMap *d_qmaps = nullptr;
+  uint32_t *d_qgoff = nullptr, *d_qgent = nullptr;
+  double *d_qgq = nullptr, *d_qpart = nullptr;
+  int *d_ctr = nullptr;
+  int qgrid = 0, qthreads = 0;
+  size_t qsmem = 0;
   uint32_t *d_pass = nullptr;
   int *d_err = nullptr;
   uint64_t pass = 0;
   int grid = 0;        // persistent CTAs
   size_t smem = 0;     // dynamic shared memory per CTA (largest system)
+  int grid2 = 0, threads2 = 0;  // the same with two quads per thread
   bool layout_dirty = true;
   // charges and estimator
   bool has_charges = false;
@@ -301,18 +430,19 @@ int batch_map(const coulps_batch *B, const BatchSystem &S, void *field, int rows
 }
 
 // Gather lists of the charges grouped by (y tile, z) per system for the tile
-// rows of `pass` (fused-pass tiles) or of the half-sweep tiles: offsets
-// `off` (system base + y tile * Lz + z) and entries (colour bit 31, offset
-// within the colour's array).
-void batch_gather_lists(const coulps_batch *B, bool pass, int n_off, std::vector<uint32_t> &off,
+// rows of one tiling: offsets `off` (system base + y tile * Lz + z) and
+// entries (colour bit 31, offset within the colour's array).
+void batch_gather_lists(const coulps_batch *B, int tiling, int n_off, std::vector<uint32_t> &off,
                         std::vector<uint32_t> &ent, std::vector<double> &gq) {
   off.assign((size_t)n_off + 1, 0);
   const int64_t ntot = B->offsets[B->n_sys];
   ent.assign((size_t)ntot, 0);
   gq.assign((size_t)ntot, 0.0);
   auto key = [&](const BatchSystem &S, int y, int z) {
-    const int ty = pass ? S.PTY : S.TY;
-    return (size_t)(pass ? S.pgoff_base : S.goff_base) + (size_t)(y / ty) * S.Lz + z;
+    const int ty = tiling == kTilePair ? S.QTY : (tiling == kTilePass ? S.PTY : S.TY);
+    const int base = tiling == kTilePair ? S.qgoff_base
+                                         : (tiling == kTilePass ? S.pgoff_base : S.goff_base);
+    return (size_t)base + (size_t)(y / ty) * S.Lz + z;
   };
   for (int s = 0; s < B->n_sys; ++s)
     for (int64_t i = B->offsets[s]; i < B->offsets[s + 1]; ++i)
@@ -361,13 +491,37 @@ size_t batch_pass_smem_bytes(const coulps_batch *B) {
   return m + 128;
 }
 
+int batch_pair_threads(int es) { return es == 4 ? kPairMaxThreads32 : kPairMaxThreads64; }
+
+// A pair tile of ty rows fits: (ty + 6) rows of quads in one CTA, colour-1
+// box rows <= 256, shared memory <= 227 KiB.
+bool batch_pair_fits(const BatchSystem &S, int ty, int es) {
+  return ty >= 1 && ty <= S.Ly && S.QW * (ty + 6) <= batch_pair_threads(es) && ty + 8 <= 256 &&
+         pair_layout(ty, S.W, es, true).total + 128 <= 227 * 1024;
+}
+
+bool batch_pairs_ok(const coulps_batch *B) {
+  for (const auto &S : B->sys)
+    if (!batch_pair_fits(S, S.QTY, B->es)) return false;
+  return true;
+}
+
+size_t batch_pair_smem_bytes(const coulps_batch *B) {
+  size_t m = 0;
+  for (const auto &S : B->sys)
+    m = std::max(m, (size_t)pair_layout(S.QTY, S.W, B->es, true).total);
+  return m + 128;
+}
+
 // Tile lists, tensor maps and gather lists for the current tile shapes.
 int batch_layout(coulps_batch *B) {
   if (!B->layout_dirty) return COULPS_OK;
   batch_drop_graph(B);
   B->items.clear();
   B->pitems.clear();
-  int goff = 0, pgoff = 0;
+  B->qitems.clear();
+  const bool pairs = B->fused >= 2;
+  int goff = 0, pgoff = 0, qgoff = 0;
   for (int s = 0; s < B->n_sys; ++s) {
     BatchSystem &S = B->sys[s];
     S.item_begin = (int)B->items.size();
@@ -382,10 +536,35 @@ int batch_layout(coulps_batch *B) {
     for (int z0 = 0; z0 < S.Lz; z0 += S.PDZ)
       for (int y0 = 0; y0 < S.Ly; y0 += S.PTY)
         B->pitems.push_back(BatchItem{s, y0, z0, std::min(S.PDZ, S.Lz - z0)});
+    S.qitem_begin = (int)B->qitems.size();
+    S.qgoff_base = qgoff;
+    if (pairs) {
+      qgoff += ((S.Ly + S.QTY - 1) / S.QTY) * S.Lz;
+      for (int z0 = 0; z0 < S.Lz; z0 += S.QDZ)
+        for (int y0 = 0; y0 < S.Ly; y0 += S.QTY)
+          B->qitems.push_back(BatchItem{s, y0, z0, std::min(S.QDZ, S.Lz - z0)});
+    }
   }
+  // each tile list largest first (sites of the tile, ties in list order)
+  auto largest_first = [&](const std::vector<BatchItem> &items, int tiling) {
+    std::vector<int> order(items.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    auto sites = [&](int i) {
+      const BatchItem &t = items[i];
+      const BatchSystem &S = B->sys[t.sys];
+      const int ty = tiling == kTilePair ? S.QTY : (tiling == kTilePass ? S.PTY : S.TY);
+      return (long long)std::min(ty, S.Ly - t.y0) * t.nz * S.Lx;
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return sites(x) > sites(y); });
+    return order;
+  };
+  const std::vector<int> order = largest_first(B->items, kTileHalf);
+  const std::vector<int> porder = largest_first(B->pitems, kTilePass);
+  const std::vector<int> qorder = largest_first(B->qitems, kTilePair);
   // half-sweep maps on both copies (the second only with fused passes)
   std::vector<CUtensorMap> maps(4 * (size_t)B->n_sys);
   std::vector<CUtensorMap> pmaps(4 * (size_t)B->n_sys);
+  std::vector<CUtensorMap> qmaps(4 * (size_t)B->n_sys);
   for (int c = 0; c < (B->field2 ? 2 : 1); ++c) {
     void *f = c ? B->field2 : B->field;
     for (int s = 0; s < B->n_sys; ++s) {
@@ -398,6 +577,11 @@ int batch_layout(coulps_batch *B) {
         st = batch_map(B, S, f, S.PTY + 4, &pm[0]);
         if (!st) st = batch_map(B, S, f, S.PTY + 2, &pm[1]);
       }
+      if (!st && pairs) {
+        CUtensorMap *qm = &qmaps[2 * ((size_t)c * B->n_sys + s)];
+        st = batch_map(B, S, f, S.QTY + 8, &qm[0]);
+        if (!st) st = batch_map(B, S, f, S.QTY + 6, &qm[1]);
+      }
       if (st) return st;
     }
   }
@@ -409,7 +593,31 @@ int batch_layout(coulps_batch *B) {
   B->d_part = (double *)dev_alloc(B->alloc, B->items.size() * 2 * sizeof(double), B->stream);
   B->d_pitems = (BatchItem *)dev_alloc(B->alloc, B->pitems.size() * sizeof(BatchItem), B->stream);
   B->d_ppart = (double *)dev_alloc(B->alloc, B->pitems.size() * 2 * sizeof(double), B->stream);
-  if (!B->d_items || !B->d_part || !B->d_pitems || !B->d_ppart) return COULPS_ENOMEM;
+  release(B, B->d_order);
+  release(B, B->d_porder);
+  B->d_order = (int *)dev_alloc(B->alloc, order.size() * sizeof(int), B->stream);
+  B->d_porder = (int *)dev_alloc(B->alloc, porder.size() * sizeof(int), B->stream);
+  if (!B->d_items || !B->d_part || !B->d_pitems || !B->d_ppart || !B->d_order || !B->d_porder)
+    return COULPS_ENOMEM;
+  CK(cudaMemcpyAsync(B->d_order, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice,
+                     B->stream));
+  CK(cudaMemcpyAsync(B->d_porder, porder.data(), porder.size() * sizeof(int),
+                     cudaMemcpyHostToDevice, B->stream));
+  release(B, B->d_qitems);
+  release(B, B->d_qorder);
+  release(B, B->d_qpart);
+  if (pairs) {
+    B->d_qitems = (BatchItem *)dev_alloc(B->alloc, B->qitems.size() * sizeof(BatchItem), B->stream);
+    B->d_qorder = (int *)dev_alloc(B->alloc, qorder.size() * sizeof(int), B->stream);
+    B->d_qpart = (double *)dev_alloc(B->alloc, B->qitems.size() * 2 * sizeof(double), B->stream);
+    if (!B->d_qitems || !B->d_qorder || !B->d_qpart) return COULPS_ENOMEM;
+    CK(cudaMemcpyAsync(B->d_qitems, B->qitems.data(), B->qitems.size() * sizeof(BatchItem),
+                       cudaMemcpyHostToDevice, B->stream));
+    CK(cudaMemcpyAsync(B->d_qorder, qorder.data(), qorder.size() * sizeof(int),
+                       cudaMemcpyHostToDevice, B->stream));
+    CK(cudaMemcpyAsync(B->d_qmaps, qmaps.data(), qmaps.size() * sizeof(CUtensorMap),
+                       cudaMemcpyHostToDevice, B->stream));
+  }
   CK(cudaMemcpyAsync(B->d_sys, B->sys.data(), B->sys.size() * sizeof(BatchSystem),
                      cudaMemcpyHostToDevice, B->stream));
   CK(cudaMemcpyAsync(B->d_items, B->items.data(), B->items.size() * sizeof(BatchItem),
@@ -420,16 +628,21 @@ int batch_layout(coulps_batch *B) {
                      cudaMemcpyHostToDevice, B->stream));
   CK(cudaMemcpyAsync(B->d_pmaps, pmaps.data(), pmaps.size() * sizeof(CUtensorMap),
                      cudaMemcpyHostToDevice, B->stream));
-  // gather lists for both tilings
-  std::vector<uint32_t> off, ent, poff, pent;
-  std::vector<double> gq, pgq;
+  // gather lists for every tiling in use
+  std::vector<uint32_t> off, ent, poff, pent, qoff, qent;
+  std::vector<double> gq, pgq, qgq;
   if (B->has_charges) {
-    batch_gather_lists(B, false, goff, off, ent, gq);
+    batch_gather_lists(B, kTileHalf, goff, off, ent, gq);
     int st = batch_upload_lists(B, off, ent, gq, B->d_goff, B->d_gent, B->d_gq);
     if (st) return st;
-    batch_gather_lists(B, true, pgoff, poff, pent, pgq);
+    batch_gather_lists(B, kTilePass, pgoff, poff, pent, pgq);
     st = batch_upload_lists(B, poff, pent, pgq, B->d_pgoff, B->d_pgent, B->d_pgq);
     if (st) return st;
+    if (pairs) {
+      batch_gather_lists(B, kTilePair, qgoff, qoff, qent, qgq);
+      st = batch_upload_lists(B, qoff, qent, qgq, B->d_qgoff, B->d_qgent, B->d_qgq);
+      if (st) return st;
+    }
   }
   // persistent grids: as many CTAs as are co-resident at the largest smem need
   B->smem = batch_smem_bytes(B, true);
@@ -439,6 +652,25 @@ int batch_layout(coulps_batch *B) {
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int per_sm = std::max(1, std::min(8, (int)((200 * 1024) / B->smem)));
   B->grid = std::max(1, std::min((int)B->items.size(), sms * per_sm));
+  // two quads per thread: ceil(QW / 2) threads a row, the widest tile's count
+  B->threads2 = 32;
+  for (const auto &S : B->sys)
+    B->threads2 = std::max(B->threads2, (S.QW + 1) / 2 * S.TY);
+  B->threads2 = (B->threads2 + 31) / 32 * 32;
+  {
+    int per_sm2 = 0;
+    auto hk = B->precision == COULPS_F32 ? batch_halfsweep_kernel<float, false, false, 2>
+                                         : batch_halfsweep_kernel<double, false, false, 2>;
+    if (cudaFuncSetAttribute(hk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B->smem) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, hk, B->threads2, B->smem) !=
+            cudaSuccess ||
+        per_sm2 < 1) {
+      cudaGetLastError();
+      per_sm2 = per_sm;
+    }
+    B->grid2 = std::max(1, std::min((int)B->items.size(), sms * per_sm2));
+  }
   // pass CTAs per SM: as many as registers, threads and shared memory allow
   int pper_sm = 0;
   auto pk = B->precision == COULPS_F32 ? batch_pass_kernel<float, true, false>
@@ -452,6 +684,37 @@ int batch_layout(coulps_batch *B) {
     pper_sm = 1;
   }
   B->pgrid = std::max(1, std::min((int)B->pitems.size(), sms * pper_sm));
+  // pair CTAs: one per SM (512 threads of over 100 registers each)
+  if (pairs) {
+    B->qsmem = batch_pair_smem_bytes(B);
+    // the block: the widest pair tile's (QTY + 6) rows of quads, whole warps
+    B->qthreads = 32;
+    for (const auto &S : B->sys) B->qthreads = std::max(B->qthreads, S.QW * (S.QTY + 6));
+    B->qthreads = (B->qthreads + 31) / 32 * 32;
+    // CTAs per SM: the fewest over the pair kinds the mode runs
+    auto per_sm_of = [&](const void *k) {
+      int n = 0;
+      if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B->qsmem) !=
+              cudaSuccess ||
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, B->qthreads, B->qsmem) !=
+              cudaSuccess ||
+          n < 1) {
+        cudaGetLastError();
+        n = 1;
+      }
+      return n;
+    };
+    const bool f32 = B->precision == COULPS_F32;
+    int qper_sm = per_sm_of(f32 ? (const void *)batch_pair_kernel<float, true, true, false>
+                                : (const void *)batch_pair_kernel<double, true, true, false>);
+    if (B->fused == 3) {
+      qper_sm = std::min(qper_sm, per_sm_of(f32 ? (const void *)batch_pair_kernel<float, false, true, false>
+                                                : (const void *)batch_pair_kernel<double, false, true, false>));
+      qper_sm = std::min(qper_sm, per_sm_of(f32 ? (const void *)batch_pair_kernel<float, false, false, false>
+                                                : (const void *)batch_pair_kernel<double, false, false, false>));
+    }
+    B->qgrid = std::max(1, std::min((int)B->qitems.size(), sms * qper_sm));
+  }
   CK(cudaStreamSynchronize(B->stream));  // host vectors leave scope
   B->layout_dirty = false;
   return COULPS_OK;
@@ -459,7 +722,8 @@ int batch_layout(coulps_batch *B) {
 
 template <typename T, bool OR, bool GATHER>
 cudaError_t launch_batch_t(coulps_batch *B, const BatchArgs &a) {
-  auto kfn = batch_halfsweep_kernel<T, OR, GATHER>;
+  constexpr int V = batch_quads_per_thread<T, OR, GATHER>();
+  auto kfn = batch_halfsweep_kernel<T, OR, GATHER, V>;
   static size_t configured = 0;
   if (B->smem > configured) {
     cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -467,7 +731,10 @@ cudaError_t launch_batch_t(coulps_batch *B, const BatchArgs &a) {
     if (e != cudaSuccess) return e;
     configured = B->smem;
   }
-  kfn<<<B->grid, kBatchThreads, B->smem, B->stream>>>(a);
+  if (V == 2)
+    kfn<<<B->grid2, B->threads2, B->smem, B->stream>>>(a);
+  else
+    kfn<<<B->grid, kBatchThreads, B->smem, B->stream>>>(a);
   return cudaGetLastError();
 }
 
@@ -499,29 +766,85 @@ cudaError_t launch_bpass_p(coulps_batch *B, const BatchPassArgs &a, bool orx) {
   return gather ? launch_bpass_t<T, false, true>(B, a) : launch_bpass_t<T, false, false>(B, a);
 }
 
-// One compound sweep of every system (and its sample when `measure`).  With
-// fused passes the over-relaxation block runs as fused passes between the
-// two copies: all of it after the heatbath passes when n_or is even, or when
-// it is odd and a heatbath pass precedes it (then the heatbath passes write
-// the second copy, the first of them reading colour 1 from the first copy);
-// otherwise all but the last, which runs as in-place half-sweeps.  The
-// sweep ends in the first copy.
+template <typename T, bool A_OR, bool B_OR, bool GATHER>
+cudaError_t launch_bpair_t(coulps_batch *B, const BatchPairArgs &a) {
+  auto kfn = batch_pair_kernel<T, A_OR, B_OR, GATHER>;
+  static size_t configured = 0;
+  if (B->qsmem > configured) {
+    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)B->qsmem);
+    if (e != cudaSuccess) return e;
+    configured = B->qsmem;
+  }
+  kfn<<<B->qgrid, B->qthreads, B->qsmem, B->stream>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_bpair_p(coulps_batch *B, const BatchPairArgs &a, bool a_or, bool b_or) {
+  const bool gather = a.g_partials != nullptr;
+  if (a_or)  // over-relaxation passes come after the heatbath passes: B too
+    return gather ? launch_bpair_t<T, true, true, true>(B, a)
+                  : launch_bpair_t<T, true, true, false>(B, a);
+  if (b_or)
+    return gather ? launch_bpair_t<T, false, true, true>(B, a)
+                  : launch_bpair_t<T, false, true, false>(B, a);
+  return gather ? launch_bpair_t<T, false, false, true>(B, a)
+                : launch_bpair_t<T, false, false, false>(B, a);
+}
+
+cudaError_t launch_bpair(coulps_batch *B, const BatchPairArgs &a, bool a_or, bool b_or) {
+  return B->precision == COULPS_F32 ? launch_bpair_p<float>(B, a, a_or, b_or)
+                                    : launch_bpair_p<double>(B, a, a_or, b_or);
+}
+
+// One compound sweep of every system (and its sample when `measure`).  The
+// passes [0, head) run as half-sweeps, then d pass pairs and s fused passes
+// between the two copies, then the rest as in-place half-sweeps on the
+// first copy.  fused = 1, 2: head = n_hb and the over-relaxation block runs
+// as d = n_or / 2 pairs (fused = 2, else d = 0) and s = n_or - 2 d fused
+// passes.  Every such kernel changes copy, so when d + s is odd the heatbath
+// passes write the second copy (the first of them reading colour 1 from the
+// first copy); with no heatbath pass one pair becomes two fused passes, or
+// (no pair) the last pass runs as in-place half-sweeps.  fused = 3: all n
+// passes as pairs and fused passes (head = 0; an even count of kernels, by
+// n mod 4: n / 2 pairs; (n - 3) / 2 and 3; n / 2 - 1 and 2; (n - 1) / 2 and 1),
+// half-sweeps only for n = 1.  The sweep ends in the first copy.
 int batch_enqueue_compound(coulps_batch *B, int n_hb, int n_or, bool measure) {
   const int n = n_hb + n_or;
-  int nf = 0;
+  int head = n_hb, d = 0, s = 0;
   bool flip = false;
-  if (B->fused && B->field2) {
-    nf = n_or & ~1;
-    if ((n_or & 1) && n_hb > 0) {
-      nf = n_or;
-      flip = true;
+  if (B->fused == 3 && B->field2 && n >= 2) {
+    head = 0;
+    switch (n % 4) {
+      case 0: d = n / 2; s = 0; break;
+      case 1: d = (n - 3) / 2; s = 3; break;
+      case 2: d = n / 2 - 1; s = 2; break;
+      default: d = (n - 1) / 2; s = 1; break;
+    }
+  } else if (B->fused && B->field2) {
+    d = B->fused >= 2 ? n_or / 2 : 0;
+    s = n_or - 2 * d;
+    if ((d + s) % 2 == 1) {
+      if (n_hb > 0) {
+        flip = true;
+      } else if (d >= 1) {
+        d -= 1;
+        s += 2;
+      } else {
+        s -= 1;
+      }
     }
   }
-  const bool gather_pass = measure && nf > 0 && n_hb + nf == n;
+  const int nf = 2 * d + s;  // passes run out of place
+  const bool gather_fused = measure && nf > 0 && head + nf == n;
+  const int gather_tiling = !gather_fused ? kTileHalf : (s > 0 ? kTilePass : kTilePair);
   BatchArgs a;
   std::memset(&a, 0, sizeof(a));
   a.sys = B->d_sys;
   a.items = B->d_items;
+  a.order = B->d_order;
+  a.ctr = B->d_ctr;
   a.n_items = (int)B->items.size();
   const PhiloxKeys K = philox_keys((uint32_t)(B->seed & 0xffffffffu), (uint32_t)(B->seed >> 32));
   for (int i = 0; i < 20; ++i) a.round_keys[i] = K.k[i];
@@ -546,42 +869,72 @@ int batch_enqueue_compound(coulps_batch *B, int n_hb, int n_or, bool measure) {
     }
     return COULPS_OK;
   };
-  for (int i = 0; i < n_hb; ++i) {
+  for (int i = 0; i < head; ++i) {
     const int r = half_sweeps(i, flip, measure && nf == 0 && i == n - 1);
     if (r) return r;
+  }
+  int src = flip ? 1 : 0;  // copy the next out-of-place kernel reads
+  BatchPairArgs q;
+  std::memset(&q, 0, sizeof(q));
+  q.sys = B->d_sys;
+  q.items = B->d_qitems;
+  q.order = B->d_qorder;
+  q.n_items = (int)B->qitems.size();
+  for (int i = 0; i < 20; ++i) q.round_keys[i] = K.k[i];
+  q.err = B->d_err;
+  q.ctr = B->d_ctr;
+  q.pass_ptr = B->d_pass;
+  for (int t = 0; t < d; ++t, src ^= 1) {
+    const int i = head + 2 * t;  // passes i (A) and i + 1 (B)
+    q.pass_off = (uint32_t)i;
+    q.dst = src ? B->field : B->field2;
+    q.maps = B->d_qmaps + 2 * (size_t)src * B->n_sys;
+    const bool last = gather_fused && s == 0 && t == d - 1;
+    q.g_off = last ? B->d_qgoff : nullptr;
+    q.g_ent = last ? B->d_qgent : nullptr;
+    q.g_q = last ? B->d_qgq : nullptr;
+    q.g_partials = last ? B->d_qpart : nullptr;
+    CK(launch_bpair(B, q, i >= n_hb, i + 1 >= n_hb));
   }
   BatchPassArgs p;
   std::memset(&p, 0, sizeof(p));
   p.sys = B->d_sys;
   p.items = B->d_pitems;
+  p.order = B->d_porder;
+  p.ctr = B->d_ctr;
   p.n_items = (int)B->pitems.size();
   for (int i = 0; i < 20; ++i) p.round_keys[i] = K.k[i];
   p.pass_ptr = B->d_pass;
   p.err = B->d_err;
-  for (int t = 0; t < nf; ++t) {
-    const int i = n_hb + t;
-    const int b = (t + (flip ? 1 : 0)) & 1;  // source copy
+  for (int t = 0; t < s; ++t, src ^= 1) {
+    const int i = head + 2 * d + t;
+    const int b = src;
     p.dst = b ? B->field : B->field2;
     p.maps = B->d_pmaps + 2 * (size_t)b * B->n_sys;
     p.pass_off = (uint32_t)i;
-    const bool last = gather_pass && t == nf - 1;
+    const bool last = gather_fused && t == s - 1;
     p.g_off = last ? B->d_pgoff : nullptr;
     p.g_ent = last ? B->d_pgent : nullptr;
     p.g_q = last ? B->d_pgq : nullptr;
     p.g_partials = last ? B->d_ppart : nullptr;
-    CK(B->precision == COULPS_F32 ? launch_bpass_p<float>(B, p, true)
-                                  : launch_bpass_p<double>(B, p, true));
+    CK(B->precision == COULPS_F32 ? launch_bpass_p<float>(B, p, i >= n_hb)
+                                  : launch_bpass_p<double>(B, p, i >= n_hb));
   }
-  for (int i = n_hb + nf; i < n; ++i) {
+  for (int i = head + nf; i < n; ++i) {
     const int r = half_sweeps(i, false, measure && i == n - 1);
     if (r) return r;
   }
   if (n > 0) CK(launch_advance_pass(B->d_pass, (uint32_t)n, B->stream));
   if (measure) {
-    batch_finalize_kernel<<<(B->n_sys + 127) / 128, 128, 0, B->stream>>>(
-        gather_pass ? B->d_ppart : B->d_part, B->d_sys, B->n_sys,
-        gather_pass ? (int)B->pitems.size() : (int)B->items.size(), gather_pass, B->d_stats,
-        B->d_log, B->log_cap, B->d_err);
+    const double *part = gather_tiling == kTilePair
+                             ? B->d_qpart
+                             : (gather_tiling == kTilePass ? B->d_ppart : B->d_part);
+    const int n_items = (int)(gather_tiling == kTilePair
+                                  ? B->qitems.size()
+                                  : (gather_tiling == kTilePass ? B->pitems.size() : B->items.size()));
+    batch_finalize_kernel<<<(B->n_sys + 3) / 4, 128, 0, B->stream>>>(
+        part, B->d_sys, B->n_sys, n_items, gather_tiling, B->d_stats, B->d_log, B->log_cap,
+        B->d_err);
     CK(cudaGetLastError());
   }
   return COULPS_OK;
@@ -637,6 +990,12 @@ int coulps_batch_create(int n_systems, const int32_t *dims, int precision, uint6
     if (S.PTY > 1 && S.PTY % 2 == 0) --S.PTY;
     S.PTY = std::max(1, std::min(std::min(S.PTY, S.Ly), 252));
     S.PDZ = S.Lz >= 64 ? 32 : S.Lz;
+    // pass-pair tile: (QTY + 6) rows of quads within one CTA of the pair
+    // kernel's width, whole z up to 127 planes (the ring's 8 halo planes
+    // are then outside the box and cost no DRAM traffic), else 64
+    S.QTY = std::min(std::min(batch_pair_threads(B->es) / S.QW - 6, S.Ly), 248);
+    if (!batch_pair_fits(S, S.QTY, B->es)) S.QTY = 0;
+    S.QDZ = S.Lz < 128 ? S.Lz : 64;
     S.colour_elems = (long long)S.Lz * S.Ly * S.W;
     S.field_off = off;
     off += 2 * S.colour_elems;
@@ -649,18 +1008,22 @@ int coulps_batch_create(int n_systems, const int32_t *dims, int precision, uint6
                                        B->stream);
   B->d_pmaps = (CUtensorMap *)dev_alloc(B->alloc, 4 * (size_t)n_systems * sizeof(CUtensorMap),
                                         B->stream);
+  B->d_qmaps = (CUtensorMap *)dev_alloc(B->alloc, 4 * (size_t)n_systems * sizeof(CUtensorMap),
+                                        B->stream);
+  B->d_ctr = (int *)dev_alloc(B->alloc, 64, B->stream);
   B->d_pass = (uint32_t *)dev_alloc(B->alloc, 64, B->stream);
   B->d_err = (int *)dev_alloc(B->alloc, 64, B->stream);
   B->d_stats = (double *)dev_alloc(B->alloc, (size_t)n_systems * kStatStride * sizeof(double),
                                    B->stream);
-  if (!B->field || !B->d_sys || !B->d_maps || !B->d_pmaps || !B->d_pass || !B->d_err ||
-      !B->d_stats) {
+  if (!B->field || !B->d_sys || !B->d_maps || !B->d_pmaps || !B->d_qmaps || !B->d_ctr ||
+      !B->d_pass || !B->d_err || !B->d_stats) {
     coulps_batch_destroy(B);
     return COULPS_ENOMEM;
   }
   B->bytes = B->field_bytes;
   if (cudaMemsetAsync(B->field, 0, B->field_bytes, B->stream) != cudaSuccess ||
       cudaMemsetAsync(B->d_pass, 0, 64, B->stream) != cudaSuccess ||
+      cudaMemsetAsync(B->d_ctr, 0, 64, B->stream) != cudaSuccess ||
       cudaMemsetAsync(B->d_err, 0, 64, B->stream) != cudaSuccess) {
     cudaGetLastError();
     coulps_batch_destroy(B);
@@ -668,7 +1031,7 @@ int coulps_batch_create(int n_systems, const int32_t *dims, int precision, uint6
   }
   batch_reset_stats_kernel<<<(n_systems * kStatStride + 255) / 256, 256, 0, B->stream>>>(
       B->d_stats, n_systems);
-  int st = coulps_batch_set_fused(B, 1);
+  int st = coulps_batch_set_fused(B, batch_pairs_ok(B) ? 2 : 1);
   if (!st) st = batch_layout(B);
   if (st) {
     coulps_batch_destroy(B);
@@ -679,7 +1042,8 @@ int coulps_batch_create(int n_systems, const int32_t *dims, int precision, uint6
 }
 
 int coulps_batch_set_fused(coulps_batch_t B, int enable) {
-  if (!B || enable < 0 || enable > 1) return COULPS_EINVAL;
+  if (!B || enable < 0 || enable > 3) return COULPS_EINVAL;
+  if (enable >= 2 && !batch_pairs_ok(B)) return COULPS_EINVAL;
   batch_drop_graph(B);
   if (!enable) {
     if (B->field2) {
@@ -695,7 +1059,7 @@ int coulps_batch_set_fused(coulps_batch_t B, int enable) {
       // row padding and never-written quads stay 0 in both copies
       CK(cudaMemsetAsync(B->field2, 0, B->field_bytes, B->stream));
     }
-    B->fused = 1;
+    B->fused = enable;
   }
   B->layout_dirty = true;
   return batch_layout(B);
@@ -725,6 +1089,31 @@ int coulps_batch_system_pass_tile(coulps_batch_t B, int system, int32_t *ty_dz) 
   return COULPS_OK;
 }
 
+int coulps_batch_set_pair_tiles(coulps_batch_t B, const int32_t *ty_dz) {
+  if (!B || !ty_dz) return COULPS_EINVAL;
+  std::vector<BatchSystem> next = B->sys;
+  for (int s = 0; s < B->n_sys; ++s) {
+    BatchSystem &S = next[s];
+    const int ty = ty_dz[2 * s], dz = ty_dz[2 * s + 1];
+    if (ty < 0 || dz < 0) return COULPS_EINVAL;
+    if (ty > 0) S.QTY = ty;
+    if (dz > 0) S.QDZ = dz;
+    if (!batch_pair_fits(S, S.QTY, B->es)) return COULPS_EINVAL;
+  }
+  B->sys = next;
+  B->layout_dirty = true;
+  return batch_layout(B);
+}
+
+int coulps_batch_system_pair_tile(coulps_batch_t B, int system, int32_t *ty_dz) {
+  if (!B || !ty_dz || system < 0 || system >= B->n_sys) return COULPS_EINVAL;
+  ty_dz[0] = B->sys[system].QTY;
+  ty_dz[1] = B->sys[system].QDZ;
+  return COULPS_OK;
+}
+
+int coulps_batch_fused(coulps_batch_t B) { return B ? B->fused : -1; }
+
 void coulps_batch_destroy(coulps_batch_t B) {
   if (!B) return;
   batch_drop_graph(B);
@@ -739,6 +1128,16 @@ void coulps_batch_destroy(coulps_batch_t B) {
   release(B, B->d_pgent);
   release(B, B->d_pgq);
   release(B, B->d_ppart);
+  release(B, B->d_qmaps);
+  release(B, B->d_qitems);
+  release(B, B->d_qorder);
+  release(B, B->d_order);
+  release(B, B->d_porder);
+  release(B, B->d_qgoff);
+  release(B, B->d_qgent);
+  release(B, B->d_qgq);
+  release(B, B->d_qpart);
+  release(B, B->d_ctr);
   release(B, B->d_pass);
   release(B, B->d_err);
   release(B, B->d_goff);
@@ -778,6 +1177,9 @@ int coulps_batch_info(coulps_batch_t B, int64_t *info) {
   int64_t sites = 0;
   for (const auto &S : B->sys) sites += (int64_t)S.Lx * S.Ly * S.Lz;
   info[6] = sites;
+  info[7] = B->pgrid;
+  info[8] = B->fused >= 2 ? B->qgrid : 0;
+  info[9] = B->fused >= 2 ? B->qthreads : 0;
   return COULPS_OK;
 }
 

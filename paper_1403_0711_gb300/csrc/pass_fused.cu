@@ -40,29 +40,48 @@ namespace {
 
 using namespace tile;
 
+// The tile of one CTA: y tile blockIdx.x, z slab blockIdx.y, chain chain0 +
+// blockIdx.z * chain_stride; every quantity read from the kernel's
+// parameters where the march uses it.
+template <typename T, bool OR>
+struct GridPass {
+  const CUtensorMap &m1, &m0;
+  const PassArgs &p;
+  __device__ __forceinline__ int chain() const { return p.chain0 + (int)blockIdx.z * p.chain_stride; }
+  __device__ __forceinline__ const CUtensorMap *tm_c1() const { return &m1; }
+  __device__ __forceinline__ const CUtensorMap *tm_c0() const { return &m0; }
+  __device__ __forceinline__ int map_c1() const { return 2 * chain() + 1; }
+  __device__ __forceinline__ int map_c0() const { return 2 * chain(); }
+  __device__ __forceinline__ T *dst() const {
+    return reinterpret_cast<T *>(p.dst) + (size_t)chain() * p.chain_elems;
+  }
+  __device__ __forceinline__ size_t colour_elems() const { return p.colour_elems; }
+  __device__ __forceinline__ int Lx() const { return p.Lx; }
+  __device__ __forceinline__ int Ly() const { return p.Ly; }
+  __device__ __forceinline__ int Lz() const { return p.Lz; }
+  __device__ __forceinline__ int W() const { return p.W; }
+  __device__ __forceinline__ int Wq() const { return p.Wq; }
+  __device__ __forceinline__ int QW() const { return p.QW; }
+  __device__ __forceinline__ int TY() const { return p.TY; }
+  __device__ __forceinline__ int y0() const { return (int)blockIdx.x * p.TY; }
+  __device__ __forceinline__ int z0() const { return (int)blockIdx.y * p.DZ; }
+  __device__ __forceinline__ int nz() const { return min(p.DZ, p.Lz - z0()); }
+  __device__ __forceinline__ uint32_t rng_id() const { return (uint32_t)chain(); }
+  __device__ __forceinline__ uint32_t pass() const { return OR ? 0u : (*p.pass_ptr + p.pass_off); }
+  __device__ __forceinline__ const uint32_t *g_off() const {
+    return p.g_off + (size_t)blockIdx.x * p.Lz;
+  }
+  __device__ __forceinline__ const uint32_t *g_ent() const { return p.g_ent; }
+  __device__ __forceinline__ const double *g_q() const { return p.g_q; }
+};
+
 template <typename T, bool OR, bool GATHER>
 __global__ void __launch_bounds__(512)
     pass_kernel(const __grid_constant__ CUtensorMap tm_c1, const __grid_constant__ CUtensorMap tm_c0,
                 const PassArgs a) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem = align_smem128(smem_raw);
-  const int chain = a.chain0 + (int)blockIdx.z * a.chain_stride;
-  PassJob<T> j;
-  j.tm_c1 = &tm_c1;
-  j.tm_c0 = &tm_c0;
-  j.map_c1 = 2 * chain + 1;
-  j.map_c0 = 2 * chain;
-  j.dst0 = reinterpret_cast<T *>(a.dst) + (size_t)chain * a.chain_elems;
-  j.dst1 = j.dst0 + a.colour_elems;
-  j.Lx = a.Lx; j.Ly = a.Ly; j.Lz = a.Lz; j.W = a.W; j.Wq = a.Wq; j.QW = a.QW; j.TY = a.TY;
-  j.y0 = blockIdx.x * a.TY;
-  j.z0 = blockIdx.y * a.DZ;
-  j.nz = min(a.DZ, a.Lz - j.z0);
-  j.rng_id = (uint32_t)chain;
-  j.pass = OR ? 0u : (*a.pass_ptr + a.pass_off);
-  j.g_off = GATHER ? a.g_off + (size_t)blockIdx.x * a.Lz : nullptr;
-  j.g_ent = a.g_ent;
-  j.g_q = a.g_q;
+  const GridPass<T, OR> j{tm_c1, tm_c0, a};
   double sq = 0.0, sp = 0.0;
   int gbase = 0;
   pass_ring_init(smem);
@@ -70,7 +89,8 @@ __global__ void __launch_bounds__(512)
                             gbase, sq, sp);
   if (GATHER) {
     const size_t cta = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
-    block_partials(sq, sp, smem, a.g_partials + 2 * ((size_t)chain * gridDim.x * gridDim.y + cta));
+    block_partials(sq, sp, smem,
+                   a.g_partials + 2 * ((size_t)j.chain() * gridDim.x * gridDim.y + cta));
   }
 }
 

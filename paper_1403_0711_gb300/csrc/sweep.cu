@@ -54,25 +54,25 @@ __global__ void __launch_bounds__(256)
   unsigned char *smem = align_smem128(smem_raw);
   const int chain = a.chain0 + (int)blockIdx.z * a.chain_stride;
   TileJob<T> j;
-  j.tm_halo = &tm_halo;
-  j.tm_own = &tm_own;
-  j.colour = a.colour;
-  j.map_other = 2 * chain + (a.colour ^ 1);
-  j.map_own = 2 * chain + a.colour;
-  j.out = reinterpret_cast<T *>(a.field) + (size_t)chain * a.chain_elems +
+  j.tm_halo_ = &tm_halo;
+  j.tm_own_ = &tm_own;
+  j.colour_ = a.colour;
+  j.map_other_ = 2 * chain + (a.colour ^ 1);
+  j.map_own_ = 2 * chain + a.colour;
+  j.out_ = reinterpret_cast<T *>(a.field) + (size_t)chain * a.chain_elems +
           (size_t)a.colour * a.colour_elems;
-  j.Lx = a.Lx; j.Ly = a.Ly; j.Lz = a.Lz; j.W = a.W; j.Wq = a.Wq; j.QW = a.QW; j.TY = a.TY;
-  j.y0 = blockIdx.x * a.TY;
-  j.z0 = blockIdx.y * a.DZ;
-  j.nz = min(a.DZ, a.Lz - j.z0);
-  j.rng_id = (uint32_t)chain;
-  j.pass = OR ? 0u : (*a.pass_ptr + a.pass_off);
+  j.Lx_ = a.Lx; j.Ly_ = a.Ly; j.Lz_ = a.Lz; j.W_ = a.W; j.Wq_ = a.Wq; j.QW_ = a.QW; j.TY_ = a.TY;
+  j.y0_ = blockIdx.x * a.TY;
+  j.z0_ = blockIdx.y * a.DZ;
+  j.nz_ = min(a.DZ, a.Lz - j.z0_);
+  j.rng_id_ = (uint32_t)chain;
+  j.pass_ = OR ? 0u : (*a.pass_ptr + a.pass_off);
   if (GATHER) {
-    j.g_off = a.g_off + (size_t)blockIdx.x * a.Lz;
-    j.g_ent = a.g_ent;
-    j.other = reinterpret_cast<const T *>(a.field) + (size_t)chain * a.chain_elems +
+    j.g_off_ = a.g_off + (size_t)blockIdx.x * a.Lz;
+    j.g_ent_ = a.g_ent;
+    j.other_ = reinterpret_cast<const T *>(a.field) + (size_t)chain * a.chain_elems +
               (size_t)(a.colour ^ 1) * a.colour_elems;
-    j.g_q = a.g_q;
+    j.g_q_ = a.g_q;
   }
   double sq = 0.0, sp = 0.0;
   int gbase = 0;
@@ -101,24 +101,24 @@ __global__ void __launch_bounds__(256)
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem = align_smem128(smem_raw);
   TileJob<T> j;
-  j.tm_halo = &tm_halo;
-  j.tm_own = &tm_own;
-  j.colour = a.colour;
-  j.map_other = 2 * chain + (a.colour ^ 1);
-  j.map_own = 2 * chain + a.colour;
-  j.out = reinterpret_cast<T *>(a.field) + (size_t)chain * a.chain_elems +
+  j.tm_halo_ = &tm_halo;
+  j.tm_own_ = &tm_own;
+  j.colour_ = a.colour;
+  j.map_other_ = 2 * chain + (a.colour ^ 1);
+  j.map_own_ = 2 * chain + a.colour;
+  j.out_ = reinterpret_cast<T *>(a.field) + (size_t)chain * a.chain_elems +
           (size_t)a.colour * a.colour_elems;
-  j.Lx = a.Lx; j.Ly = a.Ly; j.Lz = a.Lz; j.W = a.W; j.Wq = a.Wq; j.QW = a.QW; j.TY = a.TY;
-  j.y0 = blockIdx.x * a.TY;
-  j.z0 = blockIdx.y * a.DZ;
-  j.nz = min(a.DZ, a.Lz - j.z0);
-  j.rng_id = (uint32_t)chain;
-  j.pass = *a.pass_ptr + m.pass_delta[grp];
-  j.g_off = a.g_off + (size_t)blockIdx.x * a.Lz;
-  j.g_ent = a.g_ent;
-  j.other = reinterpret_cast<const T *>(a.field) + (size_t)chain * a.chain_elems +
+  j.Lx_ = a.Lx; j.Ly_ = a.Ly; j.Lz_ = a.Lz; j.W_ = a.W; j.Wq_ = a.Wq; j.QW_ = a.QW; j.TY_ = a.TY;
+  j.y0_ = blockIdx.x * a.TY;
+  j.z0_ = blockIdx.y * a.DZ;
+  j.nz_ = min(a.DZ, a.Lz - j.z0_);
+  j.rng_id_ = (uint32_t)chain;
+  j.pass_ = *a.pass_ptr + m.pass_delta[grp];
+  j.g_off_ = a.g_off + (size_t)blockIdx.x * a.Lz;
+  j.g_ent_ = a.g_ent;
+  j.other_ = reinterpret_cast<const T *>(a.field) + (size_t)chain * a.chain_elems +
             (size_t)(a.colour ^ 1) * a.colour_elems;
-  j.g_q = a.g_q;
+  j.g_q_ = a.g_q;
   const PhiloxKeys &K = *reinterpret_cast<const PhiloxKeys *>(a.round_keys);
   double sq = 0.0, sp = 0.0;
   int gbase = 0;

@@ -106,21 +106,44 @@ template <> struct Coef<double> {
   static constexpr double third = 0.333333333333333333333;
 };
 
+// Accessors of a stored tile job: `name()` returns field `name_`.  The
+// marches read their tile through such accessors, so that a kernel with one
+// tile per CTA can instead answer each from its own parameters and block
+// index at the point of use (see GridPass in pass_fused.cu).
+#define COULPS_FIELD(type, name) \
+  __device__ __forceinline__ type name() const { return name##_; }
+
 // One tile of one half-sweep: TY rows (all of x) of one chain, planes
-// z0 .. z0+nz-1, streamed as described at the top of this file.
+// z0 .. z0+nz-1, streamed as described at the top of this file: read through
+// tm_halo / tm_own (4th coordinates map_other / map_own), the own colour
+// written to out (element (z*Ly + y)*W + h), the other colour at `other`
+// (GATHER only); Philox counter words quad, pass, rng_id (chain), colour;
+// the fused gather of the tile column at g_off (GATHER only).  march_tile
+// reads a tile through accessors of these names; TileJob stores them.  (For
+// this march a stored job measured as fast as reading the kernel's
+// parameters at each use, unlike the fused pass and the pair.)
 template <typename T>
 struct TileJob {
-  const CUtensorMap *tm_halo, *tm_own;
-  int map_other, map_own;  // 4th TMA coordinate of the other / own colour
-  T *out;                  // own colour of this chain: element (z*Ly + y)*W + h
-  const T *other;          // the other colour, same indexing (GATHER only)
-  int Lx, Ly, Lz, W, Wq, QW, TY;
-  int y0, z0, nz;
-  int colour;
-  uint32_t rng_id;  // Philox counter word 2 (chain)
-  uint32_t pass;    // Philox counter word 1
-  const uint32_t *g_off, *g_ent;  // fused gather of this tile column (GATHER only)
-  const double *g_q;
+  const CUtensorMap *tm_halo_, *tm_own_;
+  int map_other_, map_own_;
+  T *out_;
+  const T *other_;
+  int Lx_, Ly_, Lz_, W_, Wq_, QW_, TY_;
+  int y0_, z0_, nz_;
+  int colour_;
+  uint32_t rng_id_, pass_;
+  const uint32_t *g_off_, *g_ent_;
+  const double *g_q_;
+  COULPS_FIELD(const CUtensorMap *, tm_halo) COULPS_FIELD(const CUtensorMap *, tm_own)
+  COULPS_FIELD(int, map_other) COULPS_FIELD(int, map_own)
+  COULPS_FIELD(T *, out) COULPS_FIELD(const T *, other)
+  COULPS_FIELD(int, Lx) COULPS_FIELD(int, Ly) COULPS_FIELD(int, Lz) COULPS_FIELD(int, W)
+  COULPS_FIELD(int, Wq) COULPS_FIELD(int, QW) COULPS_FIELD(int, TY)
+  COULPS_FIELD(int, y0) COULPS_FIELD(int, z0) COULPS_FIELD(int, nz)
+  COULPS_FIELD(int, colour)
+  COULPS_FIELD(uint32_t, rng_id) COULPS_FIELD(uint32_t, pass)
+  COULPS_FIELD(const uint32_t *, g_off) COULPS_FIELD(const uint32_t *, g_ent)
+  COULPS_FIELD(const double *, g_q)
 };
 
 // Shared-memory ring header: kStages mbarriers and the abort flag.  Done
@@ -148,10 +171,10 @@ __device__ __forceinline__ void ring_init(unsigned char *smem) {
 // addresses, predicates) at the cost of registers; the sites' arithmetic is
 // unchanged, so the results are bitwise those of V = 1.  The block has
 // ceil(QW / V) threads per row.
-template <typename T, bool OR, bool GATHER, int V = 1>
-__device__ bool march_tile(const TileJob<T> &j, const PhiloxKeys &K, unsigned char *smem,
+template <typename T, bool OR, bool GATHER, int V = 1, typename Job>
+__device__ bool march_tile(const Job &j, const PhiloxKeys &K, unsigned char *smem,
                            int *err, int &gbase, double &sq, double &sp) {
-  const SmemLayout lay = smem_layout(j.TY, j.W, (int)sizeof(T), OR);
+  const SmemLayout lay = smem_layout(j.TY(), j.W(), (int)sizeof(T), OR);
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem);  // kStages barriers
   volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 64);
   unsigned char *ring = smem + kHeaderBytes;
@@ -163,29 +186,29 @@ __device__ bool march_tile(const TileJob<T> &j, const PhiloxKeys &K, unsigned ch
   };
 
   const int tid = threadIdx.x;
-  const int W = j.W;
-  const int qwv = (j.QW + V - 1) / V;  // threads per row
+  const int W = j.W();
+  const int qwv = (j.QW() + V - 1) / V;  // threads per row
   const int qx = (tid % qwv) * V, ty = tid / qwv;  // this thread's first quad
-  const int n_planes = j.nz + 2;  // other-colour planes z0-1 .. z0+nz
-  const int c = j.colour;
-  const int y = j.y0 + ty;
+  const int n_planes = j.nz() + 2;  // other-colour planes z0-1 .. z0+nz
+  const int c = j.colour();
+  const int y = j.y0() + ty;
   // A CTA may have more threads than the tile has quads (the many-system
   // kernel runs tiles of different shapes with one block size): threads past
   // row TY - 1 touch no shared or global memory of the tile.
-  const bool in_tile = ty < j.TY;
-  const bool live = in_tile && (y < j.Ly) && (qx < j.Wq);
+  const bool in_tile = ty < j.TY();
+  const bool live = in_tile && (y < j.Ly()) && (qx < j.Wq());
   // quad v of this thread: inside the row's storage (loads), holds sites (updates)
   bool qmem[V], qlive[V];
 #pragma unroll
   for (int v = 0; v < V; ++v) {
-    qmem[v] = in_tile && qx + v < j.QW;
-    qlive[v] = live && qx + v < j.Wq;
+    qmem[v] = in_tile && qx + v < j.QW();
+    qlive[v] = live && qx + v < j.Wq();
   }
 
   const int gb = gbase;
   if (tid == 0) {
-    prefetch_tensormap(j.tm_halo);
-    if (OR) prefetch_tensormap(j.tm_own);
+    prefetch_tensormap(j.tm_halo());
+    if (OR) prefetch_tensormap(j.tm_own());
   }
 
   // Plane k of this tile is other-colour plane z0 - 1 + k; it is ring plane
@@ -195,10 +218,10 @@ __device__ bool march_tile(const TileJob<T> &j, const PhiloxKeys &K, unsigned ch
   auto issue = [&](int k) {
     const int s = slot_of(k);
     const uint32_t bar = smem_addr(&bars[s]);
-    const bool own = OR && k >= 1 && k <= j.nz;
+    const bool own = OR && k >= 1 && k <= j.nz();
     mbar_arrive_expect_tx(bar, lay.halo_bytes + (own ? lay.own_bytes : 0));
-    tma_load_4d(smem_addr(halo_slot(s)), j.tm_halo, 0, j.y0 - 1, j.z0 - 1 + k, j.map_other, bar);
-    if (own) tma_load_4d(smem_addr(own_slot(s)), j.tm_own, 0, j.y0, j.z0 - 1 + k, j.map_own, bar);
+    tma_load_4d(smem_addr(halo_slot(s)), j.tm_halo(), 0, j.y0() - 1, j.z0() - 1 + k, j.map_other(), bar);
+    if (own) tma_load_4d(smem_addr(own_slot(s)), j.tm_own(), 0, j.y0(), j.z0() - 1 + k, j.map_own(), bar);
   };
   auto wait_plane = [&](int k) -> bool {
     return mbar_wait_bounded(smem_addr(&bars[slot_of(k)]), (uint32_t)(((gb + k) / kStages) & 1));
@@ -239,16 +262,16 @@ __device__ bool march_tile(const TileJob<T> &j, const PhiloxKeys &K, unsigned ch
     pad0[v] = pad1[v] = 0u;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      if (2 * (4 * (qx + v) + i) >= j.Lx) pad0[v] |= 1u << i;
-      if (2 * (4 * (qx + v) + i) + 1 >= j.Lx) pad1[v] |= 1u << i;
+      if (2 * (4 * (qx + v) + i) >= j.Lx()) pad0[v] |= 1u << i;
+      if (2 * (4 * (qx + v) + i) + 1 >= j.Lx()) pad1[v] |= 1u << i;
     }
   }
   const bool lo_ok = qx > 0, hi_ok = 4 * qx + 4 * V < W;
   const int hrow = (ty + 1) * W + 4 * qx;  // this quad in a halo box (first row y0 - 1)
   const int orow = ty * W + 4 * qx;        // this quad in an own box (first row y0)
-  T *outp = j.out + ((size_t)j.z0 * j.Ly + y) * W + 4 * qx;  // plane z0; one plane per step
-  const size_t pstride = (size_t)j.Ly * W;
-  int par = (c + y + j.z0) & 1;  // the row (y, z) holds x = 2h + par; flips with z
+  T *outp = j.out() + ((size_t)j.z0() * j.Ly() + y) * W + 4 * qx;  // plane z0; one plane per step
+  const size_t pstride = (size_t)j.Ly() * W;
+  int par = (c + y + j.z0()) & 1;  // the row (y, z) holds x = 2h + par; flips with z
 
   // Plane k (z = z0 + k - 1): M, C, P are the other colour's quads of planes
   // z - 1, z, z + 1 (P loaded here).  The loop calls it with the names
@@ -284,10 +307,10 @@ __device__ bool march_tile(const TileJob<T> &j, const PhiloxKeys &K, unsigned ch
           for (int i = 0; i < 4; ++i)
             S[i] = ((M[v][i] + P[v][i]) + (ym[i] + yp[i])) + (C[v][i] + xs[i]);
           if (!OR) {
-            const uint32_t z = (uint32_t)(j.z0 + k - 1);
+            const uint32_t z = (uint32_t)(j.z0() + k - 1);
             const uint32_t quad =
-                (z * (uint32_t)j.Ly + (uint32_t)y) * (uint32_t)j.Wq + (uint32_t)(qx + v);
-            const uint4 w = philox4x32_10(make_uint4(quad, j.pass, j.rng_id, (uint32_t)c), K);
+                (z * (uint32_t)j.Ly() + (uint32_t)y) * (uint32_t)j.Wq() + (uint32_t)(qx + v);
+            const uint4 w = philox4x32_10(make_uint4(quad, j.pass(), j.rng_id(), (uint32_t)c), K);
             T n4[4];
             QuadNoise1<T>::of(w, n4);
             u[0] = fma(S[0], Coef<T>::sixth, n4[0]);
@@ -325,11 +348,11 @@ __device__ bool march_tile(const TileJob<T> &j, const PhiloxKeys &K, unsigned ch
 
   if (!aborted) {
     if (tid == 0 && issued < n_planes) issue(issued++);
-    for (int k = 1; k <= j.nz; k += 3) {
+    for (int k = 1; k <= j.nz(); k += 3) {
       if (!step(k, cm, c0, cp)) { aborted = true; break; }
-      if (k + 1 > j.nz) break;
+      if (k + 1 > j.nz()) break;
       if (!step(k + 1, c0, cp, cm)) { aborted = true; break; }
-      if (k + 2 > j.nz) break;
+      if (k + 2 > j.nz()) break;
       if (!step(k + 2, cp, cm, c0)) { aborted = true; break; }
     }
   }
@@ -345,13 +368,13 @@ __device__ bool march_tile(const TileJob<T> &j, const PhiloxKeys &K, unsigned ch
     // both colours of the tile are still in L2.  An entry holds its site's
     // colour and offset within the colour's array.
     __syncthreads();
-    const uint32_t e0 = j.g_off[j.z0], e1 = j.g_off[j.z0 + j.nz];
+    const uint32_t e0 = j.g_off()[j.z0()], e1 = j.g_off()[j.z0() + j.nz()];
     for (uint32_t e = e0 + tid; e < e1; e += blockDim.x) {
-      const uint32_t ent = j.g_ent[e];
+      const uint32_t ent = j.g_ent()[e];
       const size_t at = ent & ~kGatherColourBit;
       const bool own = ((ent >> 31) & 1u) == (uint32_t)c;
-      const T val = own ? j.out[at] : j.other[at];
-      const double t = j.g_q[e] * (double)val;
+      const T val = own ? j.out()[at] : j.other()[at];
+      const double t = j.g_q()[e] * (double)val;
       sq += t;
       sp += t * t;
     }

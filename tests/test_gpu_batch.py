@@ -79,26 +79,78 @@ def test_batch_tiles_do_not_change_fields(cl, stream):
 @pytest.mark.parametrize("prec,n_hb,n_or", [(0, 1, 3), (0, 1, 2), (1, 2, 2), (0, 0, 3), (0, 0, 2),
                                            (1, 1, 1), (0, 2, 3), (0, 1, 0)])
 def test_batch_fused_passes_equal_half_sweeps(cl, stream, prec, n_hb, n_or):
-    """Fused over-relaxation passes (the default) against half-sweeps only: the
-    fields bitwise, the samples to FP64 summation order (the last kernel
-    gathers over other tiles), for odd and even over-relaxation counts with
-    and without heatbath passes, uneven boxes down to one site."""
+    """Fused over-relaxation passes and pass pairs (the default) against
+    half-sweeps only: the fields bitwise, the samples to FP64 summation order
+    (the last kernel gathers over other tiles), for odd and even
+    over-relaxation counts with and without heatbath passes, uneven boxes
+    down to one site."""
     systems = _charges(DIMS, 21)
     out = []
-    for fused in (0, 1):
+    for fused in (0, 1, 2, 3):
         b = cl.Batch(DIMS, precision=prec, seed=29, stream=stream)
-        b.set_fused(fused)
+        if fused != 2:
+            b.set_fused(fused)
+        assert b.fused() == fused
         b.set_charges(systems, log_capacity=5)
         b.sweep(3, 1, 1)  # a non-zero field for over-relaxation-only mixes
         b.run(1, 5, n_hb, n_or)
         out.append((b.samples(), [b.field(k) for k in range(len(DIMS))], b.info()["pass"]))
         b.close()
-    (sa, fa, pa), (sb, fb, pb) = out
-    assert pa == pb
-    for k in range(len(DIMS)):
-        assert np.array_equal(fa[k], fb[k]), k
-        if n_hb + n_or > 0:
-            assert sample_err(sb[:, k], sa[:, k]) < 1e-13, k
+    sa, fa, pa = out[0]
+    for sb, fb, pb in out[1:]:
+        assert pa == pb
+        for k in range(len(DIMS)):
+            assert np.array_equal(fa[k], fb[k]), k
+            if n_hb + n_or > 0:
+                assert sample_err(sb[:, k], sa[:, k]) < 1e-13, k
+
+
+PAIR_DIMS = [(8, 6, 130), (64, 40, 20), (13, 7, 5), (1, 1, 1), (40, 23, 19), (96, 9, 11)]
+
+
+@pytest.mark.parametrize("mode", [2, 3])
+@pytest.mark.parametrize("n_hb,n_or", [(1, 3), (1, 4), (0, 5), (0, 4), (2, 2), (3, 2), (1, 0),
+                                       (2, 0)])
+def test_batch_pair_tiles_equal_half_sweeps(cl, stream, mode, n_hb, n_or):
+    """Pass pairs (over-relaxation only, or with heatbath passes: mode 3) on
+    small tiles (several y tiles and z slabs per system, a slab split at
+    Lz >= 128 by default) against half-sweeps only: fields bitwise, samples
+    to summation order; many pair launches in a row (the tile counter resets
+    itself)."""
+    systems = _charges(PAIR_DIMS, 41)
+    a = cl.Batch(PAIR_DIMS, precision=0, seed=5, stream=stream)
+    a.set_fused(0)
+    b = cl.Batch(PAIR_DIMS, precision=0, seed=5, stream=stream)
+    b.set_fused(mode)
+    assert b.pair_tiles()[0] == (6, 64)  # whole y (2 quads a row), z split at 64
+    c = cl.Batch(PAIR_DIMS, precision=0, seed=5, stream=stream)
+    c.set_fused(mode)
+    c.set_pair_tiles([(max(1, min(2, L[1])), 3) for L in PAIR_DIMS])
+    assert c.pair_tiles()[1] == (2, 3)
+    for x in (a, b, c):
+        x.set_charges(systems, log_capacity=6)
+        x.sweep(2, 1, 1)
+        x.run(2, 6, n_hb, n_or)
+    for x in (b, c):
+        assert x.fused() == mode
+        for k in range(len(PAIR_DIMS)):
+            assert np.array_equal(a.field(k), x.field(k)), k
+            assert sample_err(x.samples()[:, k], a.samples()[:, k]) < 1e-13, k
+    with pytest.raises(cl.CoulpsError):
+        c.set_pair_tiles([(300, 0)] * len(PAIR_DIMS))
+    for x in (a, b, c):
+        x.close()
+
+
+def test_batch_without_pair_tile_uses_fused_passes(cl, stream):
+    """A system whose rows are too wide for a pair tile (FP64, Lx = 512: 64
+    quads a row, 7 rows > 256 threads) keeps fused passes; pairs are refused."""
+    b = cl.Batch([(512, 3, 4), (8, 8, 8)], precision=1, seed=1, stream=stream)
+    assert b.fused() == 1 and b.pair_tiles()[0][0] == 0
+    for mode in (2, 3):
+        with pytest.raises(cl.CoulpsError):
+            b.set_fused(mode)
+    b.close()
 
 
 def test_batch_pass_tiles_do_not_change_fields(cl, stream):
