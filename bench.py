@@ -100,7 +100,8 @@ def parse():
                     help="also run the whole-lattice control variate on the +-1 system")
     ap.add_argument("--batch-fused", type=int, choices=[0, 1, 2, 3], default=None,
                     help="many-system fused mode (coulps_batch_set_fused; default: the library's)")
-    ap.add_argument("--workload", choices=["chains128", "large512", "sweep", "batched", "cv", "cube",
+    ap.add_argument("--workload", choices=["chains128", "large512", "sweep", "batched", "batched_tta",
+                                           "cv", "cube",
                                            "cv_eval", "paper", "gcv", "offlattice"],
                     default="chains128", help="secondary workloads print their own line")
     ap.add_argument("--off-seconds", type=float, default=120.0,
@@ -637,6 +638,7 @@ def run_ours(args):
         ch = lat = None
         torch.cuda.empty_cache()
         extras = {"batched_256_systems": batched_throughput(args, stream, steps=50),
+                  "batched_256_time_to_1e-3": batched_time_to_accuracy(args, stream, steps=2000),
                   "large_512_1e6_charges": large_throughput(args, stream, 512, steps=20),
                   "learned_cv_q1_cube": cv_local_cube(args, stream, seconds=60.0)}
 
@@ -699,6 +701,65 @@ def batched_throughput(args, stream, steps):
     return r
 
 
+def batched_time_to_accuracy(args, stream, steps, eps=1e-3):
+    """Time until every one of the 256 systems of the batched workload has its
+    E_N to a batch-means standard error of eps: plain Eq. (nsum2) samples
+    against the global control variate of every system (coulps_batch_gcv,
+    h by SOR, local P term R = 1, c = 1).  Each arm samples `steps` measured
+    compound sweeps (1 HB : 3 OR) of all systems after 100 unmeasured ones,
+    timed with CUDA events; a system needing n_s = n (se_s / eps)^2 samples,
+    all systems advance together, so the projected time is max_s n_s times the
+    measured time per compound sweep (CV setup added to the CV arm)."""
+    import numpy as np
+    import torch
+
+    from paper_1403_0711_gb300 import coulps, inputs
+    systems = inputs.batch_systems(256, seed=7)
+    b = coulps.Batch([L_ for L_, _, _ in systems], precision=coulps.F32, seed=77, stream=stream)
+    b.set_charges([(s_, q_) for _, s_, q_ in systems])
+    b.sweep(100, N_HB, N_OR)
+
+    def project(est, ms):
+        need = est["n"] * (est["stderr"] / eps) ** 2
+        worst = float(np.max(need))
+        return {"ms_per_step": ms, "samples": int(est["n"][0]),
+                "max_stderr": float(np.max(est["stderr"])),
+                "median_stderr": float(np.median(est["stderr"])),
+                "median_tau_int": float(np.median(est["tau_int"])),
+                "steps_needed_worst_system": worst,
+                "steps_needed_median_system": float(np.median(need)),
+                "projected_seconds": worst * ms / 1e3}
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b.reset_stats()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    b.run(0, steps, N_HB, N_OR)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain = project(b.estimate(), e0.elapsed_time(e1) / steps)
+    t0 = time.perf_counter()
+    g = coulps.BatchGlobalCV(b, R=1)
+    b.sync()
+    setup = time.perf_counter() - t0
+    g.run(10, N_HB, N_OR, 1.0)  # graph capture and warm-up
+    g.reset()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    g.run(steps, N_HB, N_OR, 1.0)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    cv = project(g.estimate(), e0.elapsed_time(e1) / steps)
+    cv["setup_s"] = setup
+    cv["projected_seconds"] += setup
+    g.close()
+    b.close()
+    torch.cuda.empty_cache()
+    return {"systems": 256, "eps": eps, "estimator_cv": "global CV per system, R = 1, c = 1",
+            "plain": plain, "cv": cv,
+            "plain_over_cv_time": plain["projected_seconds"] / cv["projected_seconds"]}
+
+
 def large_throughput(args, stream, n, steps):
     """One n^3 chain (FP32 field, FP64 sums), charges in 200 Gaussian blobs
     (sigma = 6 sites), q in [-0.8, 0.8] shifted to zero net: 10^6 charges at
@@ -756,6 +817,8 @@ def run_extra(args):
                                             max(20, min(args.steps, int(2e10 / n ** 3)))))
     elif args.workload == "batched":
         results.append(batched_throughput(args, stream, args.steps))
+    elif args.workload == "batched_tta":
+        results.append(batched_time_to_accuracy(args, stream, max(args.steps, 500)))
     elif args.workload == "gcv":
         results.append(gcv_time_to_accuracy(args, stream))
     elif args.workload == "paper":

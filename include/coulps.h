@@ -501,6 +501,43 @@ int coulps_batch_samples(coulps_batch_t b, double *QPe, int64_t cap, int64_t *n)
 
 /* System s's field as Lx*Ly*Lz doubles in natural order.  Synchronises. */
 int coulps_batch_field_get(coulps_batch_t b, int system, double *host_xyz);
+/* Sets system s's field from host_xyz (natural order x fastest, Lx Ly Lz
+ * doubles; rounded to the precision).  Synchronises. */
+int coulps_batch_field_set(coulps_batch_t b, int system, const double *host_xyz);
+/* Raw per-system statistics of the plain samples: out[s * COULPS_STAT_STRIDE
+ * + k] as coulps_chain_stats (cap >= n_systems * COULPS_STAT_STRIDE);
+ * coulps_batch_reset_stats clears them (asynchronous).  Errors: EINVAL, ECUDA. */
+int coulps_batch_stats(coulps_batch_t b, double *out, int64_t cap);
+int coulps_batch_reset_stats(coulps_batch_t b);
+
+/* ---- global control variate of every system of a batch ---------------- */
+/* Not in the paper.  The control variate of coulps_gcv_create for each
+ * system s of a batch: g = Q_s h_s (h_s = -G rho_s by n_iter red/black SOR
+ * iterations of the system's box, rounded so that A h_s is exact in FP32),
+ * plus for R in 1..4 the local term of P; T g = h_s . rho_s - Q_s (A h_s) .
+ * phi_s (+ k(0) sum q^2 - sum_i q_i^2 phi_i w_i), mean 0 for any h and kernel.
+ * h_s is bitwise the one coulps_gcv_create makes for the same box, charges
+ * and n_iter.  create reads the batch's charges (re-create it after
+ * coulps_batch_charges) and synchronises; it needs charges (EINVAL).
+ * info: out[2 s] = h_s . rho_s, out[2 s + 1] = |A u_s + rho_s| / |rho_s|.
+ * h: h_s (FP32, natural order) of one system.  eval: T g of every system's
+ * current field into tg (device, n_systems doubles; NULL = internal),
+ * asynchronous.  run: n_meas measured compound sweeps of all systems (one
+ * CUDA graph each on a non-default stream), each recording the plain sample
+ * (coulps_batch_estimate) and e - c T g per system (coulps_batch_gcv_estimate,
+ * raw sums by coulps_batch_gcv_stats, cleared by coulps_batch_gcv_reset).
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+typedef struct coulps_batch_gcv *coulps_batch_gcv_t;
+int coulps_batch_gcv_create(coulps_batch_t b, int n_iter, int R, coulps_batch_gcv_t *out);
+void coulps_batch_gcv_destroy(coulps_batch_gcv_t g);
+int coulps_batch_gcv_info(coulps_batch_gcv_t g, double *out);
+int coulps_batch_gcv_h(coulps_batch_gcv_t g, int system, float *host_xyz);
+int coulps_batch_gcv_eval(coulps_batch_gcv_t g, double *tg);
+int coulps_batch_gcv_run(coulps_batch_gcv_t g, int n_meas, int n_hb, int n_or, double c);
+int coulps_batch_gcv_reset(coulps_batch_gcv_t g);
+int coulps_batch_gcv_stats(coulps_batch_gcv_t g, double *out, int64_t cap);
+int coulps_batch_gcv_estimate(coulps_batch_gcv_t g, double *mean, double *stderr_bm,
+                              double *tau_int, int64_t *n);
 
 /* ---- Stein control variate kernels -------------------------------------- */
 /* Building blocks of the learned control variate (not in the paper): a small

@@ -22,7 +22,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",
            "-I", str(CSRC), "-I", str(INCLUDE)]
 SOURCES = ["sweep.cu", "pass_fused.cu", "pass_pair.cu", "measure.cu", "api.cu", "measure_static.cu", "batch.cu",
-           "cv_conv.cu", "cv_ops.cu", "gcv.cu"]
+           "cv_conv.cu", "cv_ops.cu", "gcv.cu", "batch_gcv.cu"]
 
 
 def nvcc() -> str:

@@ -42,6 +42,10 @@ EXPORTS = (
     "coulps_cv_reset", "coulps_cv_charge_term", "coulps_set_fused", "coulps_set_pass_tile",
     "coulps_measure_sets", "coulps_run_sets", "coulps_gcv_create", "coulps_gcv_destroy",
     "coulps_gcv_info", "coulps_gcv_h", "coulps_gcv_eval", "coulps_gcv_run",
+    "coulps_batch_field_set", "coulps_batch_stats", "coulps_batch_reset_stats",
+    "coulps_batch_gcv_create", "coulps_batch_gcv_destroy", "coulps_batch_gcv_info",
+    "coulps_batch_gcv_h", "coulps_batch_gcv_eval", "coulps_batch_gcv_run", "coulps_batch_gcv_reset",
+    "coulps_batch_gcv_stats", "coulps_batch_gcv_estimate",
     "coulps_charges_create_off", "coulps_forces", "coulps_charges_near",
     "coulps_heatbath_noise", "coulps_near_pairs", "coulps_offlattice_corners",
     "coulps_set_streams", "coulps_selftest_wait", "coulps_clear_error",
@@ -159,6 +163,18 @@ def load(path: str | Path | None = None):
         "coulps_gcv_h": (i32, [vp, P(ctypes.c_float)]),
         "coulps_gcv_eval": (i32, [vp, vp]),
         "coulps_gcv_run": (i32, [vp, i32, i32, i32, f64]),
+        "coulps_batch_field_set": (i32, [vp, i32, P(f64)]),
+        "coulps_batch_stats": (i32, [vp, P(f64), i64]),
+        "coulps_batch_reset_stats": (i32, [vp]),
+        "coulps_batch_gcv_create": (i32, [vp, i32, i32, P(vp)]),
+        "coulps_batch_gcv_destroy": (None, [vp]),
+        "coulps_batch_gcv_info": (i32, [vp, P(f64)]),
+        "coulps_batch_gcv_h": (i32, [vp, i32, P(ctypes.c_float)]),
+        "coulps_batch_gcv_eval": (i32, [vp, vp]),
+        "coulps_batch_gcv_run": (i32, [vp, i32, i32, i32, f64]),
+        "coulps_batch_gcv_reset": (i32, [vp]),
+        "coulps_batch_gcv_stats": (i32, [vp, P(f64), i64]),
+        "coulps_batch_gcv_estimate": (i32, [vp, P(f64), P(f64), P(f64), P(i64)]),
         "coulps_run_sets": (i32, [vp, P(vp), i32, i32, i32, i32, i32]),
         "coulps_set_pass_tile": (i32, [vp, i32, i32]),
         "coulps_set_pair_tile": (i32, [vp, i32, i32]),
@@ -679,6 +695,89 @@ class Batch:
         _check(self._lib.coulps_batch_field_get(self.handle, int(system), _f64p(out)),
                "coulps_batch_field_get")
         return out
+
+    def set_field(self, system, phi):
+        """phi: (Lz, Ly, Lx) array, x fastest."""
+        Lx, Ly, Lz = self.dims[system]
+        a = np.ascontiguousarray(np.asarray(phi, dtype=np.float64).reshape(Lz, Ly, Lx))
+        _check(self._lib.coulps_batch_field_set(self.handle, int(system), _f64p(a)),
+               "coulps_batch_field_set")
+
+    def stats(self):
+        """(n_systems, COULPS_STAT_STRIDE) raw statistics of the plain samples."""
+        out = np.empty((self.n, STAT_STRIDE))
+        _check(self._lib.coulps_batch_stats(self.handle, _f64p(out), out.size), "coulps_batch_stats")
+        return out
+
+    def reset_stats(self):
+        _check(self._lib.coulps_batch_reset_stats(self.handle), "coulps_batch_reset_stats")
+
+
+class BatchGlobalCV:
+    """Global control variate of every system of a Batch (coulps_batch_gcv_*):
+    per system h from n_iter SOR iterations on A h = -rho; with R > 0 also
+    the local term of P (kernel radius R)."""
+
+    def __init__(self, batch, n_iter=None, R=1):
+        self.batch = batch
+        self._lib = load()
+        if n_iter is None:
+            n_iter = 6 * max(max(L) for L in batch.dims) + 50
+        h = ctypes.c_void_p()
+        _check(self._lib.coulps_batch_gcv_create(batch.handle, int(n_iter), int(R), ctypes.byref(h)),
+               "coulps_batch_gcv_create")
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            self._lib.coulps_batch_gcv_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        a = np.empty(2 * self.batch.n)
+        _check(self._lib.coulps_batch_gcv_info(self.handle, _f64p(a)), "coulps_batch_gcv_info")
+        return {"h_dot_rho": a[0::2].copy(), "residual": a[1::2].copy()}
+
+    def h(self, system):
+        Lx, Ly, Lz = self.batch.dims[system]
+        out = np.empty((Lz, Ly, Lx), dtype=np.float32)
+        _check(self._lib.coulps_batch_gcv_h(self.handle, int(system),
+                                            out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+               "coulps_batch_gcv_h")
+        return out
+
+    def eval(self, tg_ptr=None):
+        """T g of every system's field into device doubles at tg_ptr (None: internal)."""
+        _check(self._lib.coulps_batch_gcv_eval(self.handle,
+                                               ctypes.c_void_p(tg_ptr) if tg_ptr else None),
+               "coulps_batch_gcv_eval")
+
+    def run(self, n_meas, n_hb=1, n_or=3, c=1.0):
+        _check(self._lib.coulps_batch_gcv_run(self.handle, int(n_meas), int(n_hb), int(n_or),
+                                              float(c)), "coulps_batch_gcv_run")
+
+    def reset(self):
+        _check(self._lib.coulps_batch_gcv_reset(self.handle), "coulps_batch_gcv_reset")
+
+    def stats(self):
+        out = np.empty((self.batch.n, STAT_STRIDE))
+        _check(self._lib.coulps_batch_gcv_stats(self.handle, _f64p(out), out.size),
+               "coulps_batch_gcv_stats")
+        return out
+
+    def estimate(self):
+        m, s, t = (np.empty(self.batch.n) for _ in range(3))
+        n = np.empty(self.batch.n, dtype=np.int64)
+        _check(self._lib.coulps_batch_gcv_estimate(self.handle, _f64p(m), _f64p(s), _f64p(t),
+                                                   n.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))),
+               "coulps_batch_gcv_estimate")
+        return {"mean": m, "stderr": s, "tau_int": t, "n": n}
 
 
 # C-named module functions -------------------------------------------------

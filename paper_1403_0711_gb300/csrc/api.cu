@@ -1940,9 +1940,11 @@ struct coulps_gcv {
   double *d_ppart = nullptr;
 };
 
+}  // extern "C"
+
 // Dirichlet Green function of the (2R+1)^3 cube at its centre: A k = e_centre
 // by Gaussian elimination (at most 729 unknowns), in FP64, rounded to FP32.
-static std::vector<float> cube_green(int R) {
+std::vector<float> coulps::cube_green(int R) {
   const int m = 2 * R + 1, n = m * m * m;
   std::vector<double> A((size_t)n * n, 0.0), b(n, 0.0);
   auto id = [&](int x, int y, int z) { return (z * m + y) * m + x; };
@@ -1977,6 +1979,8 @@ static std::vector<float> cube_green(int R) {
   for (int i = 0; i < n; ++i) out[i] = (float)x[i];
   return out;
 }
+
+extern "C" {
 
 void coulps_gcv_destroy(coulps_gcv_t G) {
   if (!G) return;

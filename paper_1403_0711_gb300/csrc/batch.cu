@@ -32,6 +32,7 @@
 #include <new>
 #include <vector>
 
+#include "batch_internal.h"
 #include "device_common.cuh"
 #include "internal.h"
 #include "pair_march.cuh"
@@ -45,27 +46,6 @@ using namespace tile;
 
 constexpr int kBatchThreads = 256;
 constexpr int kBatchPassThreads = 256;
-
-struct BatchSystem {
-  int Lx, Ly, Lz, W, Wq, QW, TY, DZ;
-  long long field_off;     // first element of the system's field ([colour][z][y][h])
-  long long colour_elems;  // Lz * Ly * W
-  int goff_base;           // first gather offset of the system (y tile * Lz + z)
-  int item_begin;          // first tile of the system in the work list
-  int PTY, PDZ;            // fused-pass tile: rows, planes
-  int pgoff_base;          // first pass-tile gather offset of the system
-  int pitem_begin;         // first pass tile of the system in the pass work list
-  int QTY, QDZ;            // pass-pair tile: rows, planes (QTY = 0: no pair tile fits)
-  int qgoff_base;          // first pair-tile gather offset of the system
-  int qitem_begin;         // first pair tile of the system in the pair work list
-};
-
-// Tilings of one system's lattice: half-sweep, fused-pass, pass-pair tiles.
-enum Tiling { kTileHalf = 0, kTilePass = 1, kTilePair = 2 };
-
-struct BatchItem {
-  int sys, y0, z0, nz;
-};
 
 // Dynamic tile scheduler of the persistent kernels: a CTA takes the next
 // tile of the launch's list (tiles ordered largest first) from ctr[0]; after
@@ -321,60 +301,6 @@ __global__ void batch_reset_stats_kernel(double *stats, int n) {
 
 using namespace coulps;
 
-struct coulps_batch {
-  int n_sys = 0;
-  int precision = COULPS_F32, es = 4;
-  uint64_t seed = 0;
-  cudaStream_t stream = nullptr;
-  Allocator alloc = {nullptr, nullptr, nullptr};
-  std::vector<BatchSystem> sys;
-  std::vector<BatchItem> items;
-  void *field = nullptr;
-  size_t field_bytes = 0;
-  BatchSystem *d_sys = nullptr;
-  BatchItem *d_items = nullptr;
-  int *d_order = nullptr, *d_porder = nullptr;  // tile lists largest first
-  CUtensorMap *d_maps = nullptr;  // half-sweep maps: [copy][system][2]
-  // fused over-relaxation passes (fused >= 1): a second copy of the fields,
-  // the pass tiles, their maps [copy][system][2] and gather lists; with
-  // fused = 2 also the pair tiles
-  int fused = 0;
-  void *field2 = nullptr;
-  std::vector<BatchItem> pitems;
-  BatchItem *d_pitems = nullptr;
-  CUtensorMap *d_pmaps = nullptr;
-  uint32_t *d_pgoff = nullptr, *d_pgent = nullptr;
-  double *d_pgq = nullptr, *d_ppart = nullptr;
-  int pgrid = 0;
-  size_t psmem = 0;
-  std::vector<BatchItem> qitems;
-  BatchItem *d_qitems = nullptr;
-  int *d_qorder = nullptr;
-  CUtensorMap *d_qmaps = nullptr;
-  uint32_t *d_qgoff = nullptr, *d_qgent = nullptr;
-  double *d_qgq = nullptr, *d_qpart = nullptr;
-  int *d_ctr = nullptr;
-  int qgrid = 0, qthreads = 0;
-  size_t qsmem = 0;
-  uint32_t *d_pass = nullptr;
-  int *d_err = nullptr;
-  uint64_t pass = 0;
-  int grid = 0;        // persistent CTAs
-  size_t smem = 0;     // dynamic shared memory per CTA (largest system)
-  int grid2 = 0, threads2 = 0;  // the same with two quads per thread
-  bool layout_dirty = true;
-  // charges and estimator
-  bool has_charges = false;
-  std::vector<int64_t> offsets;
-  std::vector<int32_t> sites;
-  std::vector<double> q;
-  uint32_t *d_goff = nullptr, *d_gent = nullptr;
-  double *d_gq = nullptr, *d_part = nullptr, *d_stats = nullptr, *d_log = nullptr;
-  int64_t log_cap = 0;
-  size_t bytes = 0;
-  cudaGraphExec_t graph = nullptr;
-  int graph_hb = -1, graph_or = -1;
-};
 
 namespace {
 
@@ -951,6 +877,17 @@ int batch_check_error(coulps_batch *B) {
 
 }  // namespace
 
+namespace coulps {
+int batch_enqueue(coulps_batch *B, int n_hb, int n_or, bool measure) {
+  return batch_enqueue_compound(B, n_hb, n_or, measure);
+}
+int batch_sync(coulps_batch *B) { return batch_check_error(B); }
+}  // namespace coulps
+
+namespace {
+
+}  // namespace
+
 extern "C" {
 
 int coulps_batch_create(int n_systems, const int32_t *dims, int precision, uint64_t seed,
@@ -1316,6 +1253,42 @@ int coulps_batch_samples(coulps_batch_t B, double *QPe, int64_t cap, int64_t *n)
     CK(cudaStreamSynchronize(B->stream));
   }
   if (n) *n = m;
+  return COULPS_OK;
+}
+
+int coulps_batch_field_set(coulps_batch_t B, int system, const double *host) {
+  if (!B || !host || system < 0 || system >= B->n_sys) return COULPS_EINVAL;
+  const BatchSystem &S = B->sys[system];
+  std::vector<unsigned char> buf((size_t)2 * S.colour_elems * B->es, 0);
+  for (int z = 0; z < S.Lz; ++z)
+    for (int y = 0; y < S.Ly; ++y)
+      for (int x = 0; x < S.Lx; ++x) {
+        const size_t k = (size_t)((x + y + z) & 1) * S.colour_elems + ((size_t)z * S.Ly + y) * S.W +
+                         (x >> 1);
+        const double v = host[x + (size_t)S.Lx * (y + (size_t)S.Ly * z)];
+        if (B->precision == COULPS_F32)
+          reinterpret_cast<float *>(buf.data())[k] = (float)v;
+        else
+          reinterpret_cast<double *>(buf.data())[k] = v;
+      }
+  CK(cudaMemcpyAsync((char *)B->field + (size_t)S.field_off * B->es, buf.data(), buf.size(),
+                     cudaMemcpyHostToDevice, B->stream));
+  return batch_check_error(B);  // buf leaves scope
+}
+
+int coulps_batch_stats(coulps_batch_t B, double *out, int64_t cap) {
+  if (!B || !out) return COULPS_EINVAL;
+  const int64_t need = (int64_t)B->n_sys * kStatStride;
+  if (cap < need) return COULPS_EINVAL;
+  CK(cudaMemcpyAsync(out, B->d_stats, need * sizeof(double), cudaMemcpyDeviceToHost, B->stream));
+  return batch_check_error(B);
+}
+
+int coulps_batch_reset_stats(coulps_batch_t B) {
+  if (!B) return COULPS_EINVAL;
+  batch_reset_stats_kernel<<<(B->n_sys * kStatStride + 255) / 256, 256, 0, B->stream>>>(B->d_stats,
+                                                                                      B->n_sys);
+  CK(cudaGetLastError());
   return COULPS_OK;
 }
 

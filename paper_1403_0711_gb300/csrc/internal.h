@@ -1,6 +1,8 @@
 // Internal types shared by the host API and the kernel launchers.
 #pragma once
 
+#include <vector>
+
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -171,6 +173,9 @@ cudaError_t launch_measure_sets(const Geometry &g, const void *field, const SetT
 // T g = res[0] - Q (v . phi) into tg; partials >= 2 * nblk * n_chains
 // doubles, nblk = gcv_blocks(g).
 int gcv_blocks(const Geometry &g);
+// Dirichlet Green function of the (2R+1)^3 cube at its centre (FP32,
+// [dz][dy][dx] from -R; api.cu), the local P term's kernel.
+std::vector<float> cube_green(int R);
 cudaError_t gcv_solve(const Geometry &g, const double *rho_nat, double *u_nat, float *h32,
                       float *v_layout, double *scratch, int nblk_red, int n_iter, double *res,
                       cudaStream_t s);
