@@ -205,36 +205,88 @@ __device__ __forceinline__ double phi_at(const T *f, const BgcvSystem &S, int x,
 }
 
 // warp per charge: out[2 i] = q_i phi(r_i); out[2 i + 1] = q_i^2 phi(r_i) w_i
-// (R > 0), w_i = sum_d k(d) (A phi)(r_i + d) over the cube inside the box
-template <typename T>
+// (R > 0), w_i = sum_d k(d) (A phi)(r_i + d) over the cube inside the box.
+// The charges' neighbourhoods are scattered over the field and mostly not in
+// L2 after a sweep, so the kernel is bound by DRAM latency: lane t takes cube
+// point t and issues its seven loads unconditionally (coordinates clamped
+// into the box, the value masked after), and a warp loops over charges with
+// the next charge's record loaded before the current one's sums.
+template <typename T, int R>
 __global__ void __launch_bounds__(256)
     bgcv_charge_kernel(const T *__restrict__ field, const BgcvSystem *__restrict__ sys,
                        const int4 *__restrict__ qsite, const double *__restrict__ q, int64_t n_q,
-                       const float *__restrict__ kt, int R, double *__restrict__ out) {
+                       const float *__restrict__ kt, double *__restrict__ out) {
+  constexpr int m = 2 * R + 1, m3 = m * m * m;
+  constexpr int kPts = (m3 + 31) / 32;  // cube points per lane
   const int lane = threadIdx.x & 31;
-  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (i >= n_q) return;  // whole warps
-  const int4 r = qsite[i];  // x, y, z, system
-  const BgcvSystem S = sys[r.w];
-  const double p = phi_at(field, S, r.x, r.y, r.z);
-  double w = 0.0;
-  if (R > 0) {
-    const int m = 2 * R + 1, m3 = m * m * m;
-    for (int t = lane; t < m3; t += 32) {
+  float kl[kPts];
+#pragma unroll
+  for (int u = 0; u < kPts; ++u) kl[u] = lane + 32 * u < m3 ? __ldg(kt + lane + 32 * u) : 0.f;
+  int4 r = __ldg(qsite + i);
+  double qi = __ldg(q + i);
+  for (; i < n_q; i += warps) {
+    const BgcvSystem S = sys[r.w];
+    const int4 rn = i + warps < n_q ? __ldg(qsite + i + warps) : r;
+    const double qn = i + warps < n_q ? __ldg(q + i + warps) : 0.0;
+    const T *f = field + S.field_off;
+    const long long ce = S.colour_elems;
+    // phi at an in-box site (x, y, z), in the field's precision: FP32 fields
+    // keep A phi and the lane's share of w in FP32 (GB300's FP64 rate made the
+    // FP64 form of this kernel several times slower; any kernel k keeps the
+    // Stein term's mean 0, and FP32 rounding of w adds a zero-mean error of
+    // about 1e-6 relative), FP64 fields in FP64
+    auto at = [&](int x, int y, int z) -> T {
+      return f[(long long)((x + y + z) & 1) * ce + ((long long)z * S.Ly + y) * S.W + (x >> 1)];
+    };
+    const double p = (double)at(r.x, r.y, r.z);
+    T w = T(0);
+#pragma unroll
+    for (int u = 0; u < kPts; ++u) {
+      const int t = lane + 32 * u;
       const int xx = r.x + t % m - R, yy = r.y + (t / m) % m - R, zz = r.z + t / (m * m) - R;
-      if (xx < 0 || yy < 0 || zz < 0 || xx >= S.Lx || yy >= S.Ly || zz >= S.Lz) continue;
-      const double Ap = 6.0 * phi_at(field, S, xx, yy, zz) - phi_at(field, S, xx - 1, yy, zz) -
-                        phi_at(field, S, xx + 1, yy, zz) - phi_at(field, S, xx, yy - 1, zz) -
-                        phi_at(field, S, xx, yy + 1, zz) - phi_at(field, S, xx, yy, zz - 1) -
-                        phi_at(field, S, xx, yy, zz + 1);
-      w += (double)kt[t] * Ap;
+      const bool in = t < m3 && xx >= 0 && yy >= 0 && zz >= 0 && xx < S.Lx && yy < S.Ly && zz < S.Lz;
+      // the point and its six neighbours, clamped into the box; a neighbour
+      // outside the box is 0
+      const int xc = min(max(xx, 0), S.Lx - 1), yc = min(max(yy, 0), S.Ly - 1),
+                zc = min(max(zz, 0), S.Lz - 1);
+      const int xm = max(xc - 1, 0), xp = min(xc + 1, S.Lx - 1);
+      const int ym = max(yc - 1, 0), yp = min(yc + 1, S.Ly - 1);
+      const int zm = max(zc - 1, 0), zp = min(zc + 1, S.Lz - 1);
+      const T c0 = at(xc, yc, zc);
+      const T vxm = at(xm, yc, zc), vxp = at(xp, yc, zc);
+      const T vym = at(xc, ym, zc), vyp = at(xc, yp, zc);
+      const T vzm = at(xc, yc, zm), vzp = at(xc, yc, zp);
+      const T Ap = T(6) * c0 - (xc > 0 ? vxm : T(0)) - (xc < S.Lx - 1 ? vxp : T(0)) -
+                   (yc > 0 ? vym : T(0)) - (yc < S.Ly - 1 ? vyp : T(0)) -
+                   (zc > 0 ? vzm : T(0)) - (zc < S.Lz - 1 ? vzp : T(0));
+      if (in) w += (T)kl[u] * Ap;
     }
-    w = warp_sum(w);
+    const double wsum = warp_sum((double)w);
+    if (lane == 0) {
+      out[2 * i] = qi * p;
+      out[2 * i + 1] = qi * qi * p * wsum;
+    }
+    r = rn;
+    qi = qn;
   }
-  if (lane == 0) {
-    out[2 * i] = q[i] * p;
-    out[2 * i + 1] = R > 0 ? q[i] * q[i] * p * w : 0.0;
-  }
+}
+
+// R = 0: out[2 i] = q_i phi(r_i), out[2 i + 1] = 0 (thread per charge)
+template <typename T>
+__global__ void bgcv_charge0_kernel(const T *__restrict__ field, const BgcvSystem *__restrict__ sys,
+                                    const int4 *__restrict__ qsite, const double *__restrict__ q,
+                                    int64_t n_q, double *__restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_q) return;
+  const int4 r = qsite[i];
+  const BgcvSystem S = sys[r.w];
+  const double p = (double)field[S.field_off + (long long)((r.x + r.y + r.z) & 1) * S.colour_elems +
+                                 ((long long)r.z * S.Ly + r.y) * S.W + (r.x >> 1)];
+  out[2 * i] = q[i] * p;
+  out[2 * i + 1] = 0.0;
 }
 
 // warp per system: fixed-order sums of its chunks and charges, then
@@ -250,6 +302,7 @@ __global__ void bgcv_finish_kernel(const double *__restrict__ dpart,
   if (s >= n_sys) return;  // whole warps
   double d = 0.0, Q = 0.0, p = 0.0;
   for (int b = chunk_begin[s] + lane; b < chunk_begin[s + 1]; b += 32) d += dpart[b];
+#pragma unroll 4
   for (int64_t i = q_begin[s] + lane; i < q_begin[s + 1]; i += 32) {
     Q += qpart[2 * i];
     p += qpart[2 * i + 1];
@@ -286,6 +339,7 @@ struct coulps_batch_gcv {
   int64_t n_q = 0;
   float *d_k = nullptr;
   double *d_dpart = nullptr, *d_qpart = nullptr, *d_tg = nullptr, *d_cvstats = nullptr;
+  int sms = 0;  // multiprocessors of the device
   cudaGraphExec_t graph = nullptr;
   int graph_hb = -1, graph_or = -1;
   double graph_c = 0.0;
@@ -313,6 +367,39 @@ void drop_graph(coulps_batch_gcv *G) {
   G->graph = nullptr;
 }
 
+// q phi and the local P term of every charge: persistent warps (8 per block,
+// 8 blocks per SM)
+template <typename T>
+cudaError_t launch_charge(coulps_batch_gcv *G, const T *field) {
+  coulps_batch *B = G->B;
+  if (G->R == 0) {
+    bgcv_charge0_kernel<T><<<(int)((G->n_q + 255) / 256), 256, 0, B->stream>>>(
+        field, G->d_sys, G->d_qsite, G->d_q, G->n_q, G->d_qpart);
+    return cudaGetLastError();
+  }
+  const int64_t need = (G->n_q + 7) / 8;
+  const int blocks = (int)std::min<int64_t>(need, (int64_t)G->sms * 8);
+  switch (G->R) {
+    case 1:
+      bgcv_charge_kernel<T, 1><<<blocks, 256, 0, B->stream>>>(field, G->d_sys, G->d_qsite, G->d_q,
+                                                               G->n_q, G->d_k, G->d_qpart);
+      break;
+    case 2:
+      bgcv_charge_kernel<T, 2><<<blocks, 256, 0, B->stream>>>(field, G->d_sys, G->d_qsite, G->d_q,
+                                                               G->n_q, G->d_k, G->d_qpart);
+      break;
+    case 3:
+      bgcv_charge_kernel<T, 3><<<blocks, 256, 0, B->stream>>>(field, G->d_sys, G->d_qsite, G->d_q,
+                                                               G->n_q, G->d_k, G->d_qpart);
+      break;
+    default:
+      bgcv_charge_kernel<T, 4><<<blocks, 256, 0, B->stream>>>(field, G->d_sys, G->d_qsite, G->d_q,
+                                                               G->n_q, G->d_k, G->d_qpart);
+      break;
+  }
+  return cudaGetLastError();
+}
+
 // T g of every system's current field into tg (device, n_sys doubles)
 int bgcv_enqueue_eval(coulps_batch_gcv *G, double *tg) {
   coulps_batch *B = G->B;
@@ -325,16 +412,8 @@ int bgcv_enqueue_eval(coulps_batch_gcv *G, double *tg) {
         reinterpret_cast<const double *>(B->field), G->d_v, G->d_chunks, G->d_dpart);
   CK(cudaGetLastError());
   if (G->n_q > 0) {
-    const int blocks = (int)((G->n_q * 32 + 255) / 256);
-    if (B->precision == COULPS_F32)
-      bgcv_charge_kernel<float><<<blocks, 256, 0, B->stream>>>(
-          reinterpret_cast<const float *>(B->field), G->d_sys, G->d_qsite, G->d_q, G->n_q, G->d_k,
-          G->R, G->d_qpart);
-    else
-      bgcv_charge_kernel<double><<<blocks, 256, 0, B->stream>>>(
-          reinterpret_cast<const double *>(B->field), G->d_sys, G->d_qsite, G->d_q, G->n_q,
-          G->d_k, G->R, G->d_qpart);
-    CK(cudaGetLastError());
+    CK(B->precision == COULPS_F32 ? launch_charge<float>(G, reinterpret_cast<const float *>(B->field))
+                                  : launch_charge<double>(G, reinterpret_cast<const double *>(B->field)));
   }
   bgcv_finish_kernel<<<(B->n_sys + 7) / 8, 256, 0, B->stream>>>(
       G->d_dpart, G->d_chunk_begin, G->d_qpart, G->d_q_begin, G->d_c0, G->d_cP, B->n_sys, tg);
@@ -386,6 +465,15 @@ int coulps_batch_gcv_create(coulps_batch_t B, int n_iter, int R, coulps_batch_gc
   if (!G) return COULPS_ENOMEM;
   G->B = B;
   const int n_sys = B->n_sys;
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&G->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      delete G;
+      return COULPS_ECUDA;
+    }
+  }
   G->n_q = B->offsets[n_sys];
   G->R = G->n_q > 0 ? R : 0;
   // systems, natural-order offsets, chunks of the field array
@@ -455,12 +543,34 @@ int coulps_batch_gcv_create(coulps_batch_t B, int n_iter, int R, coulps_batch_gc
   if (G->R > 0) kt = cube_green(G->R);
   const int m = 2 * G->R + 1;
   const double k0 = G->R > 0 ? (double)kt[(G->R * m + G->R) * m + G->R] : 0.0;
+  // each system's charges in site order (z, y, x): the warps working at one
+  // time then read neighbouring parts of the field (L2 reuse)
+  std::vector<double> qs;
+  try {
+    qs.resize((size_t)G->n_q);
+  } catch (...) {
+    return fail(COULPS_ENOMEM);
+  }
+  std::vector<int64_t> perm;
   for (int s = 0; s < n_sys; ++s) {
     const BgcvSystem &g = G->sys[s];
+    perm.clear();
+    for (int64_t i = B->offsets[s]; i < B->offsets[s + 1]; ++i) perm.push_back(i);
+    auto key = [&](int64_t i) {
+      const int32_t *p = &B->sites[3 * i];
+      return ((int64_t)p[2] * g.Ly + p[1]) * g.Lx + p[0];
+    };
+    std::stable_sort(perm.begin(), perm.end(), [&](int64_t a, int64_t b) { return key(a) < key(b); });
+    // rho in the charges' input order (as the single-lattice solver adds them)
     for (int64_t i = B->offsets[s]; i < B->offsets[s + 1]; ++i) {
       const int32_t *p = &B->sites[3 * i];
       rho[g.nat_off + ((size_t)p[2] * g.Ly + p[1]) * g.Lx + p[0]] += B->q[i];
-      qsite[i] = make_int4(p[0], p[1], p[2], s);
+    }
+    for (size_t k = 0; k < perm.size(); ++k) {
+      const int64_t i = perm[k], o = B->offsets[s] + (int64_t)k;
+      const int32_t *p = &B->sites[3 * i];
+      qsite[o] = make_int4(p[0], p[1], p[2], s);
+      qs[o] = B->q[i];
       cP[s] += k0 * B->q[i] * B->q[i];
     }
   }
@@ -477,7 +587,7 @@ int coulps_batch_gcv_create(coulps_batch_t B, int n_iter, int R, coulps_batch_gc
       !up(G->d_chunk_begin, G->chunk_begin.data(), G->chunk_begin.size() * sizeof(int)) ||
       !up(G->d_q_begin, B->offsets.data(), (n_sys + 1) * sizeof(int64_t)) ||
       !up(G->d_qsite, qsite.data(), qsite.size() * sizeof(int4)) ||
-      !up(G->d_q, B->q.data(), B->q.size() * sizeof(double)) ||
+      !up(G->d_q, qs.data(), qs.size() * sizeof(double)) ||
       !up(G->d_cP, cP.data(), cP.size() * sizeof(double)) ||
       !up(d_rho, rho.data(), rho.size() * sizeof(double)) ||
       (G->R > 0 && !up(G->d_k, kt.data(), kt.size() * sizeof(float))))

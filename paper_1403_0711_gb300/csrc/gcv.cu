@@ -201,16 +201,20 @@ __global__ void __launch_bounds__(kGcvThreads)
   block_sum2(s, Q, partials + 2 * ((size_t)chain * gridDim.x + blockIdx.x));
 }
 
-// phi at (x, y, z) of one chain in the field layout (0 outside the box)
+// phi at (x, y, z) of one chain in the field layout (0 outside the box), in
+// the field's precision
 template <typename T>
-__device__ __forceinline__ double phi_at(const T *f, const Geometry &g, int x, int y, int z) {
-  if (x < 0 || y < 0 || z < 0 || x >= g.Lx || y >= g.Ly || z >= g.Lz) return 0.0;
+__device__ __forceinline__ T phi_at(const T *f, const Geometry &g, int x, int y, int z) {
+  if (x < 0 || y < 0 || z < 0 || x >= g.Lx || y >= g.Ly || z >= g.Lz) return T(0);
   const int c = (x + y + z) & 1;
-  return (double)f[(size_t)c * g.colour_elems + ((size_t)z * g.Ly + y) * g.W + (x >> 1)];
+  return f[(size_t)c * g.colour_elems + ((size_t)z * g.Ly + y) * g.W + (x >> 1)];
 }
 
 // warp per (charge, chain): q_i^2 phi(r_i) w_i; per block of 8 charges one
-// partial per chain
+// partial per chain.  A phi and each lane's share of w are in the field's
+// precision (FP32 fields: GB300's FP64 rate made the FP64 form several times
+// slower; any kernel k keeps the Stein term's mean 0 and FP32 rounding of w
+// adds a zero-mean error of about 1e-6 relative); lanes are added in FP64.
 template <typename T>
 __global__ void __launch_bounds__(256)
     gcv_p_kernel(const T *__restrict__ field, const Geometry g, const uint32_t *__restrict__ idx,
@@ -229,18 +233,18 @@ __global__ void __launch_bounds__(256)
     const int h = (int)(r % g.W), y = (int)((r / g.W) % g.Ly), z = (int)(r / ((uint32_t)g.W * g.Ly));
     const int x = 2 * h + ((c + y + z) & 1);
     const int m = 2 * R + 1, m3 = m * m * m;
-    double w = 0.0;
+    T wl = T(0);
     for (int t = lane; t < m3; t += 32) {
       const int dx = t % m - R, dy = (t / m) % m - R, dz = t / (m * m) - R;
       const int xx = x + dx, yy = y + dy, zz = z + dz;
       if (xx < 0 || yy < 0 || zz < 0 || xx >= g.Lx || yy >= g.Ly || zz >= g.Lz) continue;
-      const double Ap = 6.0 * phi_at(f, g, xx, yy, zz) - phi_at(f, g, xx - 1, yy, zz) -
-                        phi_at(f, g, xx + 1, yy, zz) - phi_at(f, g, xx, yy - 1, zz) -
-                        phi_at(f, g, xx, yy + 1, zz) - phi_at(f, g, xx, yy, zz - 1) -
-                        phi_at(f, g, xx, yy, zz + 1);
-      w += (double)kt[t] * Ap;
+      const T Ap = T(6) * phi_at(f, g, xx, yy, zz) - phi_at(f, g, xx - 1, yy, zz) -
+                   phi_at(f, g, xx + 1, yy, zz) - phi_at(f, g, xx, yy - 1, zz) -
+                   phi_at(f, g, xx, yy + 1, zz) - phi_at(f, g, xx, yy, zz - 1) -
+                   phi_at(f, g, xx, yy, zz + 1);
+      wl += (T)kt[t] * Ap;
     }
-    w = warp_sum(w);
+    const double w = warp_sum((double)wl);
     contrib = q[i] * q[i] * (double)f[e] * w;
   }
   __shared__ double red[8];

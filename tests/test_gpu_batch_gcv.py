@@ -30,6 +30,26 @@ def stream():
     return torch.cuda.Stream()
 
 
+def _p_scale(phi, sites, q, k):
+    """Magnitude against which FP32 evaluation of the local P term rounds:
+    sum_i q_i^2 |phi_i| sum_d |k(d)| (6 |phi| + sum of |phi| at the six
+    neighbours)(r_i + d)."""
+    R = (k.shape[0] - 1) // 2
+    a = np.abs(phi)
+    pad = np.pad(a, 1)
+    Aabs = (6 * a + pad[1:-1, 1:-1, :-2] + pad[1:-1, 1:-1, 2:] + pad[1:-1, :-2, 1:-1] +
+            pad[1:-1, 2:, 1:-1] + pad[:-2, 1:-1, 1:-1] + pad[2:, 1:-1, 1:-1])
+    Lz, Ly, Lx = phi.shape
+    tot = 0.0
+    for (x, y, z), qi in zip(np.asarray(sites).reshape(-1, 3), np.asarray(q, dtype=np.float64)):
+        z0, z1 = max(z - R, 0), min(z + R + 1, Lz)
+        y0, y1 = max(y - R, 0), min(y + R + 1, Ly)
+        x0, x1 = max(x - R, 0), min(x + R + 1, Lx)
+        kk = np.abs(k[z0 - z + R:z1 - z + R, y0 - y + R:y1 - y + R, x0 - x + R:x1 - x + R])
+        tot += qi * qi * a[z, y, x] * float(np.sum(kk * Aabs[z0:z1, y0:y1, x0:x1]))
+    return tot
+
+
 DIMS = [(23, 18, 15), (13, 7, 5), (16, 16, 16), (9, 11, 17), (1, 1, 1), (30, 4, 6)]
 
 
@@ -69,8 +89,10 @@ def test_h_and_stein_terms_match_oracle(cl, stream, prec, R):
             ref += ost.local_p_stein_term(phi, sites, q, kc)
         Q = float(np.sum(rho * phi))
         scale = abs(info["h_dot_rho"][k]) + abs(Q) * float(np.abs(ost.apply_A(h) * phi).sum())
-        # FP32: v . phi sums 16 FP32 products in FP32 (as the lattice's); FP64
-        # fields: FP64 products of the FP32 v
+        if R > 0:
+            scale += _p_scale(phi, sites, q, kc)
+        # FP32: v . phi sums 16 FP32 products in FP32 (as the lattice's) and the
+        # local term is evaluated in FP32; FP64 fields: FP64 throughout
         tol = 1e-6 if prec == 0 else 1e-12
         assert abs(tg[k] - ref) <= tol * scale + 1e-300, (k, tg[k], ref)
     g.close()

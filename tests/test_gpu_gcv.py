@@ -28,6 +28,26 @@ def stream():
     return torch.cuda.Stream()
 
 
+def _p_scale(phi, sites, q, k):
+    """Magnitude against which FP32 evaluation of the local P term rounds:
+    sum_i q_i^2 |phi_i| sum_d |k(d)| (6 |phi| + sum of |phi| at the six
+    neighbours)(r_i + d)."""
+    R = (k.shape[0] - 1) // 2
+    a = np.abs(phi)
+    pad = np.pad(a, 1)
+    Aabs = (6 * a + pad[1:-1, 1:-1, :-2] + pad[1:-1, 1:-1, 2:] + pad[1:-1, :-2, 1:-1] +
+            pad[1:-1, 2:, 1:-1] + pad[:-2, 1:-1, 1:-1] + pad[2:, 1:-1, 1:-1])
+    Lz, Ly, Lx = phi.shape
+    tot = 0.0
+    for (x, y, z), qi in zip(np.asarray(sites).reshape(-1, 3), np.asarray(q, dtype=np.float64)):
+        z0, z1 = max(z - R, 0), min(z + R + 1, Lz)
+        y0, y1 = max(y - R, 0), min(y + R + 1, Ly)
+        x0, x1 = max(x - R, 0), min(x + R + 1, Lx)
+        kk = np.abs(k[z0 - z + R:z1 - z + R, y0 - y + R:y1 - y + R, x0 - x + R:x1 - x + R])
+        tot += qi * qi * a[z, y, x] * float(np.sum(kk * Aabs[z0:z1, y0:y1, x0:x1]))
+    return tot
+
+
 @pytest.mark.parametrize("R", [0, 1, 2])
 def test_h_and_stein_term_match_oracle(cl, stream, R):
     import torch
@@ -53,7 +73,9 @@ def test_h_and_stein_term_match_oracle(cl, stream, R):
     g.eval(tg.data_ptr())
     lat.sync()
     tg = tg.cpu().numpy()
-    kc = ost.cube_green(R) if R > 0 else None
+    # the library keeps the local term's kernel in FP32 (any kernel gives a
+    # mean-zero term): compare with the oracle's kernel rounded the same way
+    kc = ost.cube_green(R).astype(np.float32).astype(np.float64) if R > 0 else None
     for k in range(3):
         phi = fields[k].astype(np.float32).astype(np.float64)  # as stored (FP32 lattice)
         ref = ost.global_stein_term(phi, rho, h)
@@ -61,7 +83,10 @@ def test_h_and_stein_term_match_oracle(cl, stream, R):
             ref += ost.local_p_stein_term(phi, sites, q, kc)
         Q = float(np.sum(rho * phi))
         scale = abs(info["h_dot_rho"]) + abs(Q) * float(np.abs(ost.apply_A(h) * phi).sum())
-        # v . phi: FP32 partial sums of 16 products, FP64 across them; k in FP32
+        if R > 0:
+            scale += _p_scale(phi, sites, q, kc)
+        # v . phi: FP32 partial sums of 16 products, FP64 across them; the local
+        # term of P evaluated in FP32 with k in FP32
         assert abs(tg[k] - ref) < 1e-6 * scale, (k, tg[k], ref)
     g.close()
     ch.close()
