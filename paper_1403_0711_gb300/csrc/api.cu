@@ -1938,6 +1938,9 @@ struct coulps_gcv {
   float *d_k = nullptr;
   double cP = 0.0;
   double *d_ppart = nullptr;
+  // the local term runs on a side stream beside the v . phi sums
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 }  // extern "C"
@@ -1985,6 +1988,11 @@ extern "C" {
 void coulps_gcv_destroy(coulps_gcv_t G) {
   if (!G) return;
   coulps_lattice *L = G->ch->lat;
+  if (L->stream) cudaStreamSynchronize(L->stream);
+  if (G->side) cudaStreamSynchronize(G->side);
+  if (G->ev_fork) cudaEventDestroy(G->ev_fork);
+  if (G->ev_join) cudaEventDestroy(G->ev_join);
+  if (G->side) cudaStreamDestroy(G->side);
   for (void *p : {(void *)G->d_rho, (void *)G->d_u, (void *)G->d_v, (void *)G->d_scratch,
                   (void *)G->d_c0res, (void *)G->d_partials, (void *)G->d_tg, (void *)G->d_h32,
                   (void *)G->d_k, (void *)G->d_ppart})
@@ -2002,6 +2010,13 @@ int coulps_gcv_create(coulps_charges_t C, int n_iter, int R, coulps_gcv_t *out) 
   if (!G) return COULPS_ENOMEM;
   G->ch = C;
   G->nblk = gcv_blocks(g);
+  if (cudaStreamCreateWithFlags(&G->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&G->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&G->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    coulps_gcv_destroy(G);
+    return COULPS_ECUDA;
+  }
   const size_t n = (size_t)g.Lx * g.Ly * g.Lz;
   G->d_rho = (double *)dev_alloc(L->alloc, n * sizeof(double), L->stream);
   G->d_u = (double *)dev_alloc(L->alloc, n * sizeof(double), L->stream);
@@ -2083,7 +2098,8 @@ int coulps_gcv_eval(coulps_gcv_t G, double *tg) {
   coulps_charges *C = G->ch;
   coulps_lattice *L = C->lat;
   CK(gcv_eval(L->g, L->field, G->d_v, C->d_idx, C->d_q, C->n, G->d_partials, G->nblk,
-              G->d_c0res, G->d_k, G->R, G->cP, G->d_ppart, tg ? tg : G->d_tg, L->stream));
+              G->d_c0res, G->d_k, G->R, G->cP, G->d_ppart, tg ? tg : G->d_tg, L->stream,
+              G->side, G->ev_fork, G->ev_join));
   return COULPS_OK;
 }
 
@@ -2102,7 +2118,8 @@ int coulps_gcv_run(coulps_gcv_t G, int n_meas, int n_hb, int n_or, double c) {
     if (!st && !fused) st = enqueue_measure(L, C);
     if (st) return st;
     CK(gcv_eval(L->g, L->field, G->d_v, C->d_idx, C->d_q, C->n, G->d_partials, G->nblk,
-                G->d_c0res, G->d_k, G->R, G->cP, G->d_ppart, G->d_tg, L->stream));
+                G->d_c0res, G->d_k, G->R, G->cP, G->d_ppart, G->d_tg, L->stream, G->side,
+                G->ev_fork, G->ev_join));
     CK(launch_cv_record(C->d_stats, G->d_tg, c, C->d_cvstats, L->g.n_chains, L->d_err,
                         L->stream));
     return COULPS_OK;

@@ -340,6 +340,11 @@ struct coulps_batch_gcv {
   float *d_k = nullptr;
   double *d_dpart = nullptr, *d_qpart = nullptr, *d_tg = nullptr, *d_cvstats = nullptr;
   int sms = 0;  // multiprocessors of the device
+  // the charge kernel (DRAM-latency-bound) runs on a side stream beside the
+  // v . phi kernel (bandwidth-bound); fork and join by events, which a stream
+  // capture turns into two branches of the graph
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaGraphExec_t graph = nullptr;
   int graph_hb = -1, graph_or = -1;
   double graph_c = 0.0;
@@ -370,10 +375,9 @@ void drop_graph(coulps_batch_gcv *G) {
 // q phi and the local P term of every charge: persistent warps (8 per block,
 // 8 blocks per SM)
 template <typename T>
-cudaError_t launch_charge(coulps_batch_gcv *G, const T *field) {
-  coulps_batch *B = G->B;
+cudaError_t launch_charge(coulps_batch_gcv *G, const T *field, cudaStream_t st) {
   if (G->R == 0) {
-    bgcv_charge0_kernel<T><<<(int)((G->n_q + 255) / 256), 256, 0, B->stream>>>(
+    bgcv_charge0_kernel<T><<<(int)((G->n_q + 255) / 256), 256, 0, st>>>(
         field, G->d_sys, G->d_qsite, G->d_q, G->n_q, G->d_qpart);
     return cudaGetLastError();
   }
@@ -381,19 +385,19 @@ cudaError_t launch_charge(coulps_batch_gcv *G, const T *field) {
   const int blocks = (int)std::min<int64_t>(need, (int64_t)G->sms * 8);
   switch (G->R) {
     case 1:
-      bgcv_charge_kernel<T, 1><<<blocks, 256, 0, B->stream>>>(field, G->d_sys, G->d_qsite, G->d_q,
+      bgcv_charge_kernel<T, 1><<<blocks, 256, 0, st>>>(field, G->d_sys, G->d_qsite, G->d_q,
                                                                G->n_q, G->d_k, G->d_qpart);
       break;
     case 2:
-      bgcv_charge_kernel<T, 2><<<blocks, 256, 0, B->stream>>>(field, G->d_sys, G->d_qsite, G->d_q,
+      bgcv_charge_kernel<T, 2><<<blocks, 256, 0, st>>>(field, G->d_sys, G->d_qsite, G->d_q,
                                                                G->n_q, G->d_k, G->d_qpart);
       break;
     case 3:
-      bgcv_charge_kernel<T, 3><<<blocks, 256, 0, B->stream>>>(field, G->d_sys, G->d_qsite, G->d_q,
+      bgcv_charge_kernel<T, 3><<<blocks, 256, 0, st>>>(field, G->d_sys, G->d_qsite, G->d_q,
                                                                G->n_q, G->d_k, G->d_qpart);
       break;
     default:
-      bgcv_charge_kernel<T, 4><<<blocks, 256, 0, B->stream>>>(field, G->d_sys, G->d_qsite, G->d_q,
+      bgcv_charge_kernel<T, 4><<<blocks, 256, 0, st>>>(field, G->d_sys, G->d_qsite, G->d_q,
                                                                G->n_q, G->d_k, G->d_qpart);
       break;
   }
@@ -404,6 +408,15 @@ cudaError_t launch_charge(coulps_batch_gcv *G, const T *field) {
 int bgcv_enqueue_eval(coulps_batch_gcv *G, double *tg) {
   coulps_batch *B = G->B;
   const int n_chunks = (int)G->chunks.size();
+  const bool fork = G->n_q > 0;
+  if (fork) {
+    CK(cudaEventRecord(G->ev_fork, B->stream));
+    CK(cudaStreamWaitEvent(G->side, G->ev_fork, 0));
+    CK(B->precision == COULPS_F32
+           ? launch_charge<float>(G, reinterpret_cast<const float *>(B->field), G->side)
+           : launch_charge<double>(G, reinterpret_cast<const double *>(B->field), G->side));
+    CK(cudaEventRecord(G->ev_join, G->side));
+  }
   if (B->precision == COULPS_F32)
     bgcv_dot_kernel<float><<<n_chunks, kBgcvThreads, 0, B->stream>>>(
         reinterpret_cast<const float *>(B->field), G->d_v, G->d_chunks, G->d_dpart);
@@ -411,10 +424,7 @@ int bgcv_enqueue_eval(coulps_batch_gcv *G, double *tg) {
     bgcv_dot_kernel<double><<<n_chunks, kBgcvThreads, 0, B->stream>>>(
         reinterpret_cast<const double *>(B->field), G->d_v, G->d_chunks, G->d_dpart);
   CK(cudaGetLastError());
-  if (G->n_q > 0) {
-    CK(B->precision == COULPS_F32 ? launch_charge<float>(G, reinterpret_cast<const float *>(B->field))
-                                  : launch_charge<double>(G, reinterpret_cast<const double *>(B->field)));
-  }
+  if (fork) CK(cudaStreamWaitEvent(B->stream, G->ev_join, 0));
   bgcv_finish_kernel<<<(B->n_sys + 7) / 8, 256, 0, B->stream>>>(
       G->d_dpart, G->d_chunk_begin, G->d_qpart, G->d_q_begin, G->d_c0, G->d_cP, B->n_sys, tg);
   CK(cudaGetLastError());
@@ -438,6 +448,11 @@ extern "C" {
 void coulps_batch_gcv_destroy(coulps_batch_gcv_t G) {
   if (!G) return;
   drop_graph(G);
+  if (G->B && G->B->stream) cudaStreamSynchronize(G->B->stream);
+  if (G->side) cudaStreamSynchronize(G->side);
+  if (G->ev_fork) cudaEventDestroy(G->ev_fork);
+  if (G->ev_join) cudaEventDestroy(G->ev_join);
+  if (G->side) cudaStreamDestroy(G->side);
   gfree(G, G->d_sys);
   gfree(G, G->d_chunks);
   gfree(G, G->d_chunk_begin);
@@ -468,9 +483,12 @@ int coulps_batch_gcv_create(coulps_batch_t B, int n_iter, int R, coulps_batch_gc
   {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&G->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaDeviceGetAttribute(&G->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&G->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&G->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&G->ev_join, cudaEventDisableTiming) != cudaSuccess) {
       cudaGetLastError();
-      delete G;
+      coulps_batch_gcv_destroy(G);
       return COULPS_ECUDA;
     }
   }

@@ -324,10 +324,30 @@ cudaError_t gcv_solve(const Geometry &g, const double *rho_nat, double *u_nat, f
   return cudaGetLastError();
 }
 
+// The local term (DRAM-latency-bound charge neighbourhoods) runs on `side`
+// beside the v . phi sums (bandwidth-bound), forked and joined by events
+// (two branches of a captured graph).
 cudaError_t gcv_eval(const Geometry &g, const void *field, const float *v_layout,
                      const uint32_t *idx, const double *q, int64_t n_q, double *partials,
                      int nblk, const double *c0, const float *kt, int R, double cP,
-                     double *ppart, double *tg, cudaStream_t s) {
+                     double *ppart, double *tg, cudaStream_t s, cudaStream_t side,
+                     cudaEvent_t fork, cudaEvent_t join) {
+  const int nblk_p = R > 0 && n_q > 0 ? (int)((n_q + 7) / 8) : 0;
+  cudaError_t e;
+  if (nblk_p > 0) {
+    if ((e = cudaEventRecord(fork, s)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(side, fork, 0)) != cudaSuccess)
+      return e;
+    dim3 pgrid(nblk_p, g.n_chains);
+    if (g.precision == COULPS_F32)
+      gcv_p_kernel<float><<<pgrid, 256, 0, side>>>(reinterpret_cast<const float *>(field), g, idx,
+                                                  q, n_q, kt, R, ppart);
+    else
+      gcv_p_kernel<double><<<pgrid, 256, 0, side>>>(reinterpret_cast<const double *>(field), g,
+                                                   idx, q, n_q, kt, R, ppart);
+    if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaEventRecord(join, side)) != cudaSuccess)
+      return e;
+  }
   dim3 grid(nblk, g.n_chains);
   if (g.precision == COULPS_F32)
     gcv_sample_kernel<float><<<grid, kGcvThreads, 0, s>>>(
@@ -335,16 +355,7 @@ cudaError_t gcv_eval(const Geometry &g, const void *field, const float *v_layout
   else
     gcv_sample_kernel<double><<<grid, kGcvThreads, 0, s>>>(
         reinterpret_cast<const double *>(field), g.chain_elems, v_layout, idx, q, n_q, partials);
-  const int nblk_p = R > 0 && n_q > 0 ? (int)((n_q + 7) / 8) : 0;
-  if (nblk_p > 0) {
-    dim3 pgrid(nblk_p, g.n_chains);
-    if (g.precision == COULPS_F32)
-      gcv_p_kernel<float><<<pgrid, 256, 0, s>>>(reinterpret_cast<const float *>(field), g, idx, q,
-                                               n_q, kt, R, ppart);
-    else
-      gcv_p_kernel<double><<<pgrid, 256, 0, s>>>(reinterpret_cast<const double *>(field), g, idx,
-                                                q, n_q, kt, R, ppart);
-  }
+  if (nblk_p > 0 && (e = cudaStreamWaitEvent(s, join, 0)) != cudaSuccess) return e;
   gcv_finish_kernel<<<(g.n_chains + 7) / 8, 256, 0, s>>>(partials, nblk, ppart, nblk_p,
                                                         g.n_chains, c0, nblk_p > 0 ? cP : 0.0, tg);
   return cudaGetLastError();

@@ -185,7 +185,8 @@ cudaError_t gcv_solve(const Geometry &g, const double *rho_nat, double *u_nat, f
 cudaError_t gcv_eval(const Geometry &g, const void *field, const float *v_layout,
                      const uint32_t *idx, const double *q, int64_t n_q, double *partials,
                      int nblk, const double *c0, const float *kt, int R, double cP,
-                     double *ppart, double *tg, cudaStream_t s);
+                     double *ppart, double *tg, cudaStream_t s, cudaStream_t side,
+                     cudaEvent_t fork, cudaEvent_t join);
 
 // Entry packing of the fused gather.
 constexpr uint32_t kGatherColourBit = 0x80000000u;
