@@ -76,8 +76,9 @@ __global__ void __launch_bounds__(256)
   }
   double sq = 0.0, sp = 0.0;
   int gbase = 0;
-  ring_init(smem);
-  march_tile<T, OR, GATHER, V>(j, *reinterpret_cast<const PhiloxKeys *>(a.round_keys), smem,
+  ring_init<kLatticeStages>(smem);
+  march_tile<T, OR, GATHER, V, kLatticeStages, kLatticeGroup>(
+      j, *reinterpret_cast<const PhiloxKeys *>(a.round_keys), smem,
                                a.err, gbase, sq, sp);
   if (GATHER) {
     const size_t cta = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
@@ -122,13 +123,14 @@ __global__ void __launch_bounds__(256)
   const PhiloxKeys &K = *reinterpret_cast<const PhiloxKeys *>(a.round_keys);
   double sq = 0.0, sp = 0.0;
   int gbase = 0;
-  ring_init(smem);
+  ring_init<kLatticeStages>(smem);
+  constexpr int S = kLatticeStages, G = kLatticeGroup;
   if (mode == 1) {
-    if (gather) march_tile<T, false, true>(j, K, smem, a.err, gbase, sq, sp);
-    else march_tile<T, false, false>(j, K, smem, a.err, gbase, sq, sp);
+    if (gather) march_tile<T, false, true, 1, S, G>(j, K, smem, a.err, gbase, sq, sp);
+    else march_tile<T, false, false, 1, S, G>(j, K, smem, a.err, gbase, sq, sp);
   } else {
-    if (gather) march_tile<T, true, true>(j, K, smem, a.err, gbase, sq, sp);
-    else march_tile<T, true, false>(j, K, smem, a.err, gbase, sq, sp);
+    if (gather) march_tile<T, true, true, 1, S, G>(j, K, smem, a.err, gbase, sq, sp);
+    else march_tile<T, true, false, 1, S, G>(j, K, smem, a.err, gbase, sq, sp);
   }
   if (gather) {
     const size_t cta = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
@@ -140,7 +142,7 @@ __global__ void __launch_bounds__(256)
 template <typename T>
 cudaError_t launch_mixed_t(const Geometry &g, const Tile &t, const CUtensorMap &tm_halo,
                            const CUtensorMap &tm_own, const MixedArgs &m, cudaStream_t s) {
-  const SmemLayout lay = smem_layout(t.ty, g.W, (int)sizeof(T), true);
+  const SmemLayout lay = smem_layout(t.ty, g.W, (int)sizeof(T), true, kLatticeStages);
   const size_t smem = (size_t)lay.total + 128;
   auto kfn = halfsweep_mixed_kernel<T>;
   static int configured_bytes = 0;
@@ -168,7 +170,7 @@ constexpr int quads_per_thread() {
 template <typename T, bool OR, bool GATHER>
 cudaError_t launch_t(const Geometry &g, const Tile &t, const CUtensorMap &tm_halo,
                      const CUtensorMap &tm_own, const SweepArgs &a, cudaStream_t s) {
-  const SmemLayout lay = smem_layout(t.ty, g.W, (int)sizeof(T), OR);
+  const SmemLayout lay = smem_layout(t.ty, g.W, (int)sizeof(T), OR, kLatticeStages);
   const size_t smem = (size_t)lay.total + 128;
   constexpr int V = quads_per_thread<T, OR, GATHER>();
   auto kfn = halfsweep_kernel<T, OR, GATHER, V>;
@@ -201,7 +203,7 @@ cudaError_t launch_p(const Geometry &g, const Tile &t, const CUtensorMap &tm_hal
 }  // namespace
 
 size_t halfsweep_smem_bytes(const Geometry &g, const Tile &t, bool overrelax) {
-  return (size_t)smem_layout(t.ty, g.W, g.es, overrelax).total + 128;
+  return (size_t)smem_layout(t.ty, g.W, g.es, overrelax, kLatticeStages).total + 128;
 }
 
 cudaError_t launch_halfsweep(const Geometry &g, const Tile &t, const CUtensorMap &tm_halo,

@@ -8,7 +8,16 @@
 namespace coulps {
 namespace tile {
 
+// Ring depth (slots of other-colour planes) and barrier group of a march:
+// the CTA synchronises once every GROUP planes and then refills the slots of
+// the planes it has finished, so copies run GROUP .. STAGES - GROUP planes
+// ahead.  A barrier per plane (GROUP = 1) was the heatbath half-sweep's second
+// stall; the single-lattice kernels use 8 slots in groups of 4, the
+// many-system kernel (whose largest systems' slots would cut its occupancy)
+// 4 slots in groups of 1.  At most 8 slots: 8 mbarriers fill the header's
+// first 64 bytes.
 constexpr int kStages = 4;
+constexpr int kLatticeStages = 8, kLatticeGroup = 4;
 
 __host__ __device__ inline int round_up_int(int v, int m) { return (v + m - 1) / m * m; }
 
@@ -22,12 +31,13 @@ struct SmemLayout {
 // barriers at 0, abort flag at 64, block reduction (2 x 32 doubles) at 128
 constexpr int kHeaderBytes = 1024;
 
-__host__ __device__ inline SmemLayout smem_layout(int TY, int W, int es, bool orx) {
+__host__ __device__ inline SmemLayout smem_layout(int TY, int W, int es, bool orx,
+                                                  int stages = kStages) {
   SmemLayout L;
   L.halo_bytes = (TY + 2) * W * es;
   L.own_bytes = orx ? TY * W * es : 0;
   L.slot_bytes = round_up_int(L.halo_bytes, 128) + round_up_int(L.own_bytes, 128);
-  L.total = kHeaderBytes + kStages * L.slot_bytes;
+  L.total = kHeaderBytes + stages * L.slot_bytes;
   return L;
 }
 
@@ -146,13 +156,15 @@ struct TileJob {
   COULPS_FIELD(const double *, g_q)
 };
 
-// Shared-memory ring header: kStages mbarriers and the abort flag.  Done
+// Shared-memory ring header: STAGES mbarriers and the abort flag.  Done
 // once per CTA; the barriers' phases then run on across every tile the CTA
 // streams (see `gbase` below).
+template <int STAGES = kStages>
 __device__ __forceinline__ void ring_init(unsigned char *smem) {
+  static_assert(STAGES <= 8 && (STAGES & (STAGES - 1)) == 0, "ring of at most 8, a power of 2");
   if (threadIdx.x == 0) {
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
-    for (int s = 0; s < kStages; ++s) mbar_init(smem_addr(&bars[s]), 1);
+    for (int s = 0; s < STAGES; ++s) mbar_init(smem_addr(&bars[s]), 1);
     *reinterpret_cast<volatile int *>(smem + 64) = 0;
     fence_mbar_init();
   }
@@ -171,11 +183,13 @@ __device__ __forceinline__ void ring_init(unsigned char *smem) {
 // addresses, predicates) at the cost of registers; the sites' arithmetic is
 // unchanged, so the results are bitwise those of V = 1.  The block has
 // ceil(QW / V) threads per row.
-template <typename T, bool OR, bool GATHER, int V = 1, typename Job>
+template <typename T, bool OR, bool GATHER, int V = 1, int STAGES = kStages, int GROUP = 1,
+          typename Job>
 __device__ bool march_tile(const Job &j, const PhiloxKeys &K, unsigned char *smem,
                            int *err, int &gbase, double &sq, double &sp) {
-  const SmemLayout lay = smem_layout(j.TY(), j.W(), (int)sizeof(T), OR);
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem);  // kStages barriers
+  static_assert(GROUP >= 1 && GROUP < STAGES, "copies must run ahead of the group");
+  const SmemLayout lay = smem_layout(j.TY(), j.W(), (int)sizeof(T), OR, STAGES);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem);  // STAGES barriers
   volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 64);
   unsigned char *ring = smem + kHeaderBytes;
   auto halo_slot = [&](int s) -> T * {
@@ -212,9 +226,9 @@ __device__ bool march_tile(const Job &j, const PhiloxKeys &K, unsigned char *sme
   }
 
   // Plane k of this tile is other-colour plane z0 - 1 + k; it is ring plane
-  // gb + k, in slot (gb + k) % kStages, completed in that slot's phase
-  // (gb + k) / kStages.
-  auto slot_of = [&](int k) { return (gb + k) & (kStages - 1); };
+  // gb + k, in slot (gb + k) % STAGES, completed in that slot's phase
+  // (gb + k) / STAGES.
+  auto slot_of = [&](int k) { return (gb + k) & (STAGES - 1); };
   auto issue = [&](int k) {
     const int s = slot_of(k);
     const uint32_t bar = smem_addr(&bars[s]);
@@ -224,12 +238,19 @@ __device__ bool march_tile(const Job &j, const PhiloxKeys &K, unsigned char *sme
     if (own) tma_load_4d(smem_addr(own_slot(s)), j.tm_own(), 0, j.y0(), j.z0() - 1 + k, j.map_own(), bar);
   };
   auto wait_plane = [&](int k) -> bool {
-    return mbar_wait_bounded(smem_addr(&bars[slot_of(k)]), (uint32_t)(((gb + k) / kStages) & 1));
+    return mbar_wait_bounded(smem_addr(&bars[slot_of(k)]), (uint32_t)(((gb + k) / STAGES) & 1));
   };
 
   int issued = 0;  // meaningful in thread 0 only
+  int t0_waited = -1;  // thread 0: planes 0 .. t0_waited waited for (drained on abort)
   if (tid == 0)
-    for (; issued < min(kStages, n_planes); ++issued) issue(issued);
+    for (; issued < min(STAGES, n_planes); ++issued) issue(issued);
+  // thread 0 refills every slot whose plane every thread has finished
+  // (planes 0 .. last_free), in order
+  auto refill = [&](int last_free) {
+    if (tid == 0)
+      while (issued < n_planes && issued - STAGES <= last_free) issue(issued++);
+  };
 
   T cm[V][4], c0[V][4], cp[V][4];
 #pragma unroll
@@ -246,13 +267,13 @@ __device__ bool march_tile(const Job &j, const PhiloxKeys &K, unsigned char *sme
 #pragma unroll
     for (int v = 0; v < V; ++v)
       if (qmem[v]) ld_quad(halo_slot(slot_of(1)) + (ty + 1) * W + 4 * (qx + v), c0[v]);
+  if (ok) t0_waited = 1;
   if (!ok) {
     atomicOr(err, kErrTimeout);
     *abort_flag = 1;
   }
   __syncthreads();
   bool aborted = *abort_flag != 0;
-  int done = 1;  // planes 0..done completed for every thread
 
   // per-thread constants of the plane loop
   // quad lanes past x = Lx - 1 (kept at 0), row parity 0 / 1, per quad
@@ -276,8 +297,14 @@ __device__ bool march_tile(const Job &j, const PhiloxKeys &K, unsigned char *sme
   // Plane k (z = z0 + k - 1): M, C, P are the other colour's quads of planes
   // z - 1, z, z + 1 (P loaded here).  The loop calls it with the names
   // rotated, so no register is copied from plane to plane.
+  //
+  // Between barriers a thread that finds the abort flag set only skips its
+  // work: whether the CTA stops is decided right after a barrier, where
+  // every thread reads the same flag (a thread leaving early would miss the
+  // barriers the others still reach).
   auto step = [&](int k, T(&M)[V][4], T(&C)[V][4], T(&P)[V][4]) -> bool {
-    const bool got = wait_plane(k + 1);
+    const bool got = *abort_flag == 0 && wait_plane(k + 1);
+    if (got) t0_waited = k + 1;
     const T *Pz = halo_slot(slot_of(k)) + hrow;  // row y of plane z
     if (got) {
 #pragma unroll
@@ -336,18 +363,19 @@ __device__ bool march_tile(const Job &j, const PhiloxKeys &K, unsigned char *sme
       atomicOr(err, kErrTimeout);
       *abort_flag = 1;
     }
-    __syncthreads();
-    if (*abort_flag) return false;
-    done = k + 1;
-    // plane k is no longer read: refill its slot with plane k + kStages
-    if (tid == 0 && issued < n_planes) issue(issued++);
     outp += pstride;
     par ^= 1;
+    if (k % GROUP == 0 || k == j.nz()) {
+      __syncthreads();
+      if (*abort_flag) return false;
+      // planes 0 .. k are no longer read: refill their slots
+      refill(k);
+    }
     return true;
   };
 
   if (!aborted) {
-    if (tid == 0 && issued < n_planes) issue(issued++);
+    refill(0);  // plane 0 was read only above
     for (int k = 1; k <= j.nz(); k += 3) {
       if (!step(k, cm, c0, cp)) { aborted = true; break; }
       if (k + 1 > j.nz()) break;
@@ -358,7 +386,7 @@ __device__ bool march_tile(const Job &j, const PhiloxKeys &K, unsigned char *sme
   }
   if (aborted && tid == 0) {
     // Leave no copy in flight into this CTA's shared memory.
-    for (int k = done + 1; k < issued; ++k)
+    for (int k = t0_waited + 1; k < issued; ++k)
       if (!wait_plane(k)) break;
   }
   gbase = gb + n_planes;
