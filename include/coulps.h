@@ -620,14 +620,16 @@ int coulps_cv_stein_sum(const float *g16, const float *D, const void *s2_bf16, c
  *            - sum_{x in R} g_x Aphi_x
  * where K_q is the divergence kernel summed over the offsets f of the last
  * layer with q - f inside R (per axis a subset of {-1, 0, 1}).  Ktab (device,
- * 216 x 16 x 16 x 27 floats) holds one K per class ix + 6 iy + 36 iz, the
+ * 216 x 27 x 16 x 16 floats, 16-byte aligned: K[class][e][c2][c1]) holds one
+ * K per class ix + 6 iy + 36 iz, the
  * per-axis index of the allowed set {-1} 0, {0} 1, {-1, 0} 2, {1} 3,
  * {0, 1} 4, {-1, 0, 1} 5 (f = -1 is bit 0).  g16 [b][E][16] FP32 (channel 0
  * read), s1, s2 BF16 [b][E][16] (16-byte aligned), Aphi [b][E], all in the
  * layout `interleave` of coulps_cv_pack_region (gutters are not read).  Each
- * site's sum over c1, e is FP32; the sums over sites are FP64 in a fixed
- * order.  scratch >= nb * |(R + 1) within E| doubles; out device nb doubles
- * (overwritten).  Asynchronous.  Errors: EINVAL, ECUDA. */
+ * site's sum over c1 and the nine offsets e of one z plane is FP32 (three per
+ * site); the sums over those are FP64 in a fixed order.  scratch >= 3 * nb *
+ * |(R + 1) within E| doubles; out device nb doubles (overwritten).
+ * Asynchronous.  Errors: EINVAL, ECUDA. */
 int coulps_cv_stein_region(const float *g16, const void *s1_bf16, const void *s2_bf16,
                            const float *Aphi, const float *Ktab, int nb, const int32_t *edims,
                            int interleave, const int32_t *lo, const int32_t *hi, double *scratch,
@@ -646,7 +648,7 @@ int coulps_cv_stein_region(const float *g16, const void *s1_bf16, const void *s2
  * the charge sites whose g is kept (all of them, or those inside R for
  * coulps_cv_stein_region) and their density.  M device 343 x 16 x 16 floats;
  * s1, s2 in the layout `interleave` (s1 and M 16-byte aligned).  Summed in
- * FP64, charges in order.  scratch >= 7 * nb * n_q doubles.  Asynchronous.
+ * FP64, charges in order.  scratch >= 49 * nb * n_q doubles.  Asynchronous.
  * Errors: EINVAL, ECUDA. */
 int coulps_cv_charge_term(const void *s1_bf16, const void *s2_bf16, const float *M,
                           const int32_t *q_xyz, const float *q_rho, int n_q, int nb,

@@ -362,23 +362,40 @@ int cv_conv3d_launch(const void *in_bf16, const void *wpack, const float *bias, 
   static bool configured = false;
   const int smem = kCvSmem + 1024;
   if (!configured) {
-    if (cudaFuncSetAttribute(cv_conv3d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    // the largest shared-memory carveout: the occupancy query below (and the
+    // launch) then count the 3 CTAs per SM that shared memory allows
+    if (cudaFuncSetAttribute(cv_conv3d_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared) != cudaSuccess ||
+        cudaFuncSetAttribute(cv_conv3d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              smem) != cudaSuccess) {
       cudaGetLastError();
       return COULPS_ECUDA;
     }
     configured = true;
   }
-  int dev = 0, sms = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cv_conv3d_kernel, kCvThreads, smem) !=
-          cudaSuccess ||
-      per_sm < 1) {
-    cudaGetLastError();
-    per_sm = 1;
+  // CTAs per SM from the device's limits and the kernel's registers (the
+  // occupancy query answered 1 for this kernel where shared memory allows
+  // 3), computed once
+  static int per_sm = 0, sms = 0;
+  if (per_sm == 0) {
+    int dev = 0, smem_sm = 0, regs_sm = 0;
+    cudaFuncAttributes fa;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) !=
+            cudaSuccess ||
+        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) !=
+            cudaSuccess ||
+        cudaFuncGetAttributes(&fa, cv_conv3d_kernel) != cudaSuccess) {
+      cudaGetLastError();
+      return COULPS_ECUDA;
+    }
+    const int by_smem = smem_sm / (smem + 1024);  // 1 KB reserved per CTA
+    const int by_regs = regs_sm / ((fa.numRegs + 7) / 8 * 8 * kCvThreads);
+    int n = by_smem < by_regs ? by_smem : by_regs;
+    if (n > 8) n = 8;  // 8 x 32 TMEM columns of 512
+    per_sm = n < 1 ? 1 : n;
   }
-  if (per_sm > 8) per_sm = 8;  // 8 x 32 TMEM columns of 512
   // rows per item: whole columns when there are enough of them, else chunks
   // of at least 2 rows, so that about two items per resident CTA exist
   const int slots = sms * per_sm;

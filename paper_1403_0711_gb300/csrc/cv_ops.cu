@@ -230,14 +230,17 @@ __global__ void cv_sum_partials_kernel(const double *__restrict__ partials, int 
 // 0 outside.  For q within one site of R the divergence picks the offsets f
 // with q - f inside R: per axis a mask over f in {-1, 0, 1} (bit f + 1),
 // masks 1, 2, 3, 4, 6, 7 mapped to the index 0..5, class = ix + 6 iy + 36 iz;
-// Ktab holds K[class][c2][c1][e].
+// Ktab holds K[class][e][c2][c1].
 // The sites q next to R split, per axis, into at most 5 runs of one class
 // (q = lo-1, q = lo, lo < q < hi-1, q = hi-1, q = hi, clipped to E and merged
 // when R is thin), so R + 1 is a union of at most 125 boxes of one class each.
-// One CTA takes up to kRedThreads (q, chain) items of one box: it stages the
-// box's kernel K[class] in shared memory as [e][c2][c1] and each thread forms
-// D[c2] = sum_{c1, e} K[c2][c1][e] s1[c1, q + e] for its item (K reads are
-// warp-wide broadcasts, four FMAs per 16-byte load), then s2[q] . D.
+// One CTA takes up to kRedThreads (q, chain, dz) items of one box: it stages
+// the box's kernel K[class] in shared memory as [e][c2][c1] and each thread
+// forms D[c2] = sum_{c1, e} K[c2][c1][e] s1[c1, q + e] over the 9 offsets e
+// of its z plane dz (K reads are warp-wide broadcasts, four FMAs per 16-byte
+// load), then its partial s2[q] . D; a site's three partials (one per dz) are
+// added in the finish.  (A thread per site and all 27 offsets gave a third
+// of the threads and waited on their loads.)
 struct RegionRuns {
   int start[3][5], len[3][5], cls[3][5];
   int nrun[3];
@@ -261,15 +264,17 @@ __global__ void __launch_bounds__(kRedThreads)
   while (box + 1 < r.n_box && r.cta_first[box + 1] <= (int)blockIdx.x) ++box;
   const int bx = box % r.nrun[0], by = (box / r.nrun[0]) % r.nrun[1], bz = box / (r.nrun[0] * r.nrun[1]);
   const int cls = r.cls[0][bx] + 6 * r.cls[1][by] + 36 * r.cls[2][bz];
-  const float *kg = Ktab + (size_t)cls * kRegionKFloats;  // [c2][c1][e]
-  for (int i = threadIdx.x; i < kRegionKFloats; i += kRedThreads) {
-    const int e = i % 27, c1 = (i / 27) % 16, c2 = i / (27 * 16);
-    K[(e * 16 + c2) * 16 + c1] = kg[i];
-  }
+  // the class's kernel, stored [e][c2][c1] as staged: a 16-byte copy
+  const float4 *kg = reinterpret_cast<const float4 *>(Ktab + (size_t)cls * kRegionKFloats);
+  for (int i = threadIdx.x; i < kRegionKFloats / 4; i += kRedThreads)
+    reinterpret_cast<float4 *>(K)[i] = kg[i];
   __syncthreads();
   const int lx = r.len[0][bx], ly = r.len[1][by], lz = r.len[2][bz];
   const int nq = lx * ly * lz;
-  const int item = (blockIdx.x - r.cta_first[box]) * kRedThreads + threadIdx.x;
+  // a warp takes one z plane dz of 32 consecutive items, so its K reads stay
+  // warp-wide broadcasts
+  const int item3 = (blockIdx.x - r.cta_first[box]) * kRedThreads + threadIdx.x;
+  const int dzi = (item3 >> 5) % 3, item = (item3 / 96) * 32 + (item3 & 31);
   if (item >= nq * r.nb) return;
   const int chain = item / nq, k = item % nq;
   const int x = r.start[0][bx] + k % lx, y = r.start[1][by] + (k / lx) % ly, z = r.start[2][bz] + k / (lx * ly);
@@ -277,7 +282,7 @@ __global__ void __launch_bounds__(kRedThreads)
   float D[16];
 #pragma unroll
   for (int c = 0; c < 16; ++c) D[c] = 0.f;
-  for (int e = 0; e < 27; ++e) {
+  for (int e = 9 * dzi; e < 9 * dzi + 9; ++e) {
     const int xx = x + e % 3 - 1, yy = y + (e / 3) % 3 - 1, zz = z + e / 9 - 1;
     if (xx < 0 || yy < 0 || zz < 0 || xx >= r.ex || yy >= r.ey || zz >= r.ez) continue;
     const uint4 *sp = reinterpret_cast<const uint4 *>(s1c + (zz * r.L.sz + yy * r.L.sy + xx) * 16);
@@ -319,10 +324,11 @@ __global__ void __launch_bounds__(kRedThreads)
     acc = fmaf(b.y, D[8 + 2 * i + 1], acc);
   }
   const int qi = ((z - r.qz0) * r.nqy + (y - r.qy0)) * r.nqx + (x - r.qx0);
-  part[(size_t)chain * ((size_t)r.nqx * r.nqy * r.nqz) + qi] = (double)acc;
+  part[((size_t)chain * ((size_t)r.nqx * r.nqy * r.nqz) + qi) * 3 + dzi] = (double)acc;
 }
 
 // out[b] = sum_q part[b][q] - sum_{x in R} g_x (A phi)_x, one CTA per chain
+// (part holds nq partials per chain)
 __global__ void __launch_bounds__(kRedThreads)
     cv_region_finish_kernel(const double *__restrict__ part, int nq, const float *__restrict__ g16,
                             const float *__restrict__ Aphi, BoxLayout L, int lox, int loy,
@@ -374,8 +380,10 @@ __device__ __forceinline__ void pair_axis(int a, int &f, int &e) {
   e = a < 2 ? a : (a < 5 ? a - 3 : a - 6);
 }
 
-// One CTA per (charge, 16 chains, az): thread (chain, c2) walks the 49 pairs
-// of one z offset class; the 16 chains of a CTA share each M row.
+// One CTA per (charge, 16 chains, (ay, az)): thread (chain, c2) walks the 7
+// pairs of one (y, z) offset class; the 16 chains of a CTA share each M row.
+// (With a CTA per z class, 49 pairs of dependent global loads per thread
+// left the kernel waiting on load latency.)
 __global__ void __launch_bounds__(kRedThreads)
     cv_charge_partial_kernel(const __nv_bfloat16 *__restrict__ s1,
                              const __nv_bfloat16 *__restrict__ s2, const float *__restrict__ M,
@@ -390,8 +398,10 @@ __global__ void __launch_bounds__(kRedThreads)
   const __nv_bfloat16 *s1c = s1 + (live ? chain : 0) * L.sb * 16;
   const __nv_bfloat16 *s2c = s2 + (live ? chain : 0) * L.sb * 16;
   float acc = 0.f;
-  const int p0 = 49 * blockIdx.z;
-  for (int p = p0; p < p0 + 49 && live; ++p) {
+  const int p0 = 7 * blockIdx.z;
+#pragma unroll
+  for (int p = p0; p < p0 + 7; ++p) {
+    if (!live) break;
     int fx, fy, fz, exx, eyy, ezz;
     pair_axis(p % 7, fx, exx);
     pair_axis((p / 7) % 7, fy, eyy);
@@ -420,17 +430,20 @@ __global__ void __launch_bounds__(kRedThreads)
   double v = (double)acc;
 #pragma unroll
   for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if (live && c2 == 0) partials[((size_t)chain * n_q + k) * 7 + blockIdx.z] = v * (double)qrho[k];
+  if (live && c2 == 0) partials[((size_t)chain * n_q + k) * 49 + blockIdx.z] = v * (double)qrho[k];
 }
 
 // out[b] += sum_k partials[b][k], k in order
 __global__ void cv_add_partials_kernel(const double *__restrict__ partials, int n_q, int nb,
                                        double *__restrict__ out) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= nb) return;
+  // one warp per chain: lane l adds entries l, l + 32, ..., then a fixed butterfly
+  const int b = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (b >= nb) return;  // whole warps
   double s = 0.0;
-  for (int k = 0; k < n_q; ++k) s += partials[(size_t)b * n_q + k];
-  out[b] += s;
+  for (int k = lane; k < n_q; k += 32) s += partials[(size_t)b * n_q + k];
+  s = warp_sum(s);
+  if (lane == 0) out[b] += s;
 }
 
 constexpr int kWgTile = 64;  // sites of one x row per shared-memory tile
@@ -551,7 +564,8 @@ int coulps_cv_stein_region(const float *g16, const void *s1_bf16, const void *s2
   if (nb < 1) return COULPS_EINVAL;
   for (int k = 0; k < 3; ++k)
     if (edims[k] < 1 || lo[k] < 0 || hi[k] > edims[k] || lo[k] >= hi[k]) return COULPS_EINVAL;
-  if ((reinterpret_cast<uintptr_t>(s1_bf16) | reinterpret_cast<uintptr_t>(s2_bf16)) & 15)
+  if ((reinterpret_cast<uintptr_t>(s1_bf16) | reinterpret_cast<uintptr_t>(s2_bf16) |
+       reinterpret_cast<uintptr_t>(Ktab)) & 15)
     return COULPS_EINVAL;
   RegionRuns r{};
   r.ex = edims[0]; r.ey = edims[1]; r.ez = edims[2];
@@ -565,12 +579,13 @@ int coulps_cv_stein_region(const float *g16, const void *s1_bf16, const void *s2
   r.qy0 = std::max(lo[1] - 1, 0); r.nqy = std::min(hi[1] + 1, edims[1]) - r.qy0;
   r.qz0 = std::max(lo[2] - 1, 0); r.nqz = std::min(hi[2] + 1, edims[2]) - r.qz0;
   const int64_t nq = (int64_t)r.nqx * r.nqy * r.nqz;
-  if (scratch_doubles < nq * nb) return COULPS_EINVAL;
+  if (scratch_doubles < 3 * nq * nb) return COULPS_EINVAL;
   r.n_box = r.nrun[0] * r.nrun[1] * r.nrun[2];
   int64_t ctas = 0;
   for (int b = 0; b < r.n_box; ++b) {
     const int bx = b % r.nrun[0], by = (b / r.nrun[0]) % r.nrun[1], bz = b / (r.nrun[0] * r.nrun[1]);
-    const int64_t items = (int64_t)r.len[0][bx] * r.len[1][by] * r.len[2][bz] * nb;
+    // 3 threads per item (one per z plane), in groups of 96 per 32 items
+    const int64_t items = 96 * (((int64_t)r.len[0][bx] * r.len[1][by] * r.len[2][bz] * nb + 31) / 32);
     r.cta_first[b] = (int)ctas;
     ctas += (items + kRedThreads - 1) / kRedThreads;
     if (ctas > 0x7fffffff) return COULPS_EINVAL;
@@ -579,7 +594,7 @@ int coulps_cv_stein_region(const float *g16, const void *s1_bf16, const void *s2
   cudaStream_t s = (cudaStream_t)stream;
   cv_region_div_kernel<<<(unsigned)ctas, kRedThreads, 0, s>>>(
       (const __nv_bfloat16 *)s1_bf16, (const __nv_bfloat16 *)s2_bf16, Ktab, r, scratch);
-  cv_region_finish_kernel<<<nb, kRedThreads, 0, s>>>(scratch, (int)nq, g16, Aphi, r.L, lo[0],
+  cv_region_finish_kernel<<<nb, kRedThreads, 0, s>>>(scratch, (int)(3 * nq), g16, Aphi, r.L, lo[0],
                                                      lo[1], lo[2], hi[0], hi[1], hi[2], out);
   return cudaGetLastError() == cudaSuccess ? COULPS_OK : COULPS_ECUDA;
 }
@@ -593,15 +608,15 @@ int coulps_cv_charge_term(const void *s1_bf16, const void *s2_bf16, const float 
   if (edims[0] < 1 || edims[1] < 1 || edims[2] < 1) return COULPS_EINVAL;
   if (n_q == 0) return COULPS_OK;
   if (nb > 65535 * 16) return COULPS_EINVAL;
-  if (scratch_doubles < (int64_t)nb * n_q * 7) return COULPS_EINVAL;
+  if (scratch_doubles < (int64_t)nb * n_q * 49) return COULPS_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   if ((reinterpret_cast<uintptr_t>(s1_bf16) | reinterpret_cast<uintptr_t>(M)) & 15)
     return COULPS_EINVAL;
-  cv_charge_partial_kernel<<<dim3(n_q, (nb + 15) / 16, 7), kRedThreads, 0, s>>>(
+  cv_charge_partial_kernel<<<dim3(n_q, (nb + 15) / 16, 49), kRedThreads, 0, s>>>(
       (const __nv_bfloat16 *)s1_bf16, (const __nv_bfloat16 *)s2_bf16, M, q_xyz, q_rho, n_q, nb,
       edims[0], edims[1], edims[2], box_layout(interleave, nb, edims[0], edims[1], edims[2]),
       scratch);
-  cv_add_partials_kernel<<<(nb + 127) / 128, 128, 0, s>>>(scratch, 7 * n_q, nb, out);
+  cv_add_partials_kernel<<<(nb + 3) / 4, 128, 0, s>>>(scratch, 49 * n_q, nb, out);
   return cudaGetLastError() == cudaSuccess ? COULPS_OK : COULPS_ECUDA;
 }
 

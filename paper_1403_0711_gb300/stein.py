@@ -343,7 +343,7 @@ class SteinCV(torch.nn.Module):
                 _vp(scratch), scratch.numel(), _vp(out), _stream()), "coulps_cv_stein_sum")
             nq = self._cq_xyz.shape[0]
             if nq:
-                cscr = torch.empty(7 * nq * n, dtype=torch.float64, device=dev)
+                cscr = torch.empty(49 * nq * n, dtype=torch.float64, device=dev)
                 coulps._check(lib.coulps_cv_charge_term(
                     _vp(s1), _vp(s2), _vp(M), _vp(self._cq_xyz), _vp(self._crho), nq, n,
                     (ctypes.c_int32 * 3)(Lx, Ly, Lz), 0, _vp(cscr), cscr.numel(), _vp(out),
@@ -582,7 +582,8 @@ class LocalSteinCV(SteinCV):
                 "w3": pack_weights(self._w3p()),
                 "b1": self.b1.detach().float().contiguous(), "b2": self.b2.detach().float().contiguous(),
                 "b3": self._b3p().detach().float().contiguous(),
-                "K": self.region_kernels().detach().float().contiguous(),
+                # per class [e][c2][c1], the order the region kernel stages
+                "K": self.region_kernels().detach().float().permute(0, 3, 1, 2).contiguous(),
                 "M": charge_matrix(*self.weights()).detach().float().contiguous(),
                 "err": torch.zeros(1, dtype=torch.int32, device=dev),
             }
@@ -623,7 +624,7 @@ class LocalSteinCV(SteinCV):
                           "coulps_cv_conv3d")
             if out is None:
                 out = torch.empty(n, dtype=torch.float64, device=dev)
-            scratch = torch.empty(self._q.shape[0] * n, dtype=torch.float64, device=dev)
+            scratch = torch.empty(3 * self._q.shape[0] * n, dtype=torch.float64, device=dev)
             ed = (ctypes.c_int32 * 3)(*self.edims)
             rl = (ctypes.c_int32 * 3)(*self.r_lo)
             rh = (ctypes.c_int32 * 3)(*self.r_hi)
@@ -632,7 +633,7 @@ class LocalSteinCV(SteinCV):
                 _vp(scratch), scratch.numel(), _vp(out), sp), "coulps_cv_stein_region")
             nq = self._cq_xyz.shape[0]
             if nq:
-                cscr = torch.empty(7 * nq * n, dtype=torch.float64, device=dev)
+                cscr = torch.empty(49 * nq * n, dtype=torch.float64, device=dev)
                 coulps._check(lib.coulps_cv_charge_term(
                     _vp(s1), _vp(s2), _vp(ev["M"]), _vp(self._cq_xyz), _vp(self._crho), nq, n, ed,
                     1, _vp(cscr), cscr.numel(), _vp(out), sp), "coulps_cv_charge_term")
