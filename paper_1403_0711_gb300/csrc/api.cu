@@ -221,15 +221,22 @@ int rebuild_maps(coulps_lattice *L) {
 // Fused-pass tile: rows + 2 halo rows of quads per CTA within 256 threads,
 // an odd row count (measured a little faster at 128^3: 13 rows 0.202 ms, 14
 // rows 0.211 ms per pass of 64 chains); z slabs of 32 planes (several CTAs
-// per column fill the GPU's slots evenly).
+// per column fill the GPU's slots evenly).  Rows of more than 42 quads leave
+// fewer than 5 rows in 256 threads, and the 4 halo rows of colour 1 are then
+// re-read for every row or two: such rows take up to 512 threads (measured,
+// one chain: 512^3 0.321 ms per pass with 1 row, 0.221 with 3, 0.183 with 5;
+// 384^3 0.104 with 7 rows; at 256^3 the 256-thread 5 rows are faster than 9
+// or 13 rows: 0.039, 0.041, 0.049 ms).
 Tile default_pass_tile(const Geometry &g) {
   const int qw = g.W / 4;
   int ty = 256 / qw - 2;
+  if (ty < 4) ty = 512 / qw - 2;
   if (ty > 1 && ty % 2 == 0) --ty;
   if (ty < 1) ty = 1;
   if (ty > g.Ly) ty = g.Ly;
   if (ty > 252) ty = 252;  // TMA box rows ty + 4 <= 256
   int dz = g.Lz >= 64 ? 32 : g.Lz;
+  while (ty > 1 && pass_smem_bytes(g, Tile{ty, dz}, true) > 227 * 1024) ty -= ty > 2 ? 2 : 1;
   return Tile{ty, dz};
 }
 
