@@ -625,15 +625,18 @@ int coulps_cv_stein_sum(const float *g16, const float *D, const void *s2_bf16, c
  * per-axis index of the allowed set {-1} 0, {0} 1, {-1, 0} 2, {1} 3,
  * {0, 1} 4, {-1, 0, 1} 5 (f = -1 is bit 0).  g16 [b][E][16] FP32 (channel 0
  * read), s1, s2 BF16 [b][E][16] (16-byte aligned), Aphi [b][E], all in the
- * layout `interleave` of coulps_cv_pack_region (gutters are not read).  Each
- * site's sum over c1 and the nine offsets e of one z plane is FP32 (three per
- * site); the sums over those are FP64 in a fixed order.  scratch >= 3 * nb *
- * |(R + 1) within E| doubles; out device nb doubles (overwritten).
- * Asynchronous.  Errors: EINVAL, ECUDA. */
+ * layout `interleave` of coulps_cv_pack_region (gutters are not read).  The
+ * sums over c1 and e run on the tensor cores (tcgen05, BF16 operands with K
+ * split into three BF16 parts that hold its FP32 value, FP32 accumulation):
+ * one FP32 value per (chain, site); the sums over sites are FP64 in a fixed
+ * order.  scratch >= nb * |(R + 1) within E| doubles; out device nb doubles
+ * (overwritten); err: device int, as for coulps_cv_conv3d (a bounded wait for
+ * the tensor cores that gave up ORs bit 1 into it and leaves out
+ * unspecified).  Asynchronous.  Errors: EINVAL, ECUDA. */
 int coulps_cv_stein_region(const float *g16, const void *s1_bf16, const void *s2_bf16,
                            const float *Aphi, const float *Ktab, int nb, const int32_t *edims,
                            int interleave, const int32_t *lo, const int32_t *hi, double *scratch,
-                           int64_t scratch_doubles, double *out, void *stream);
+                           int64_t scratch_doubles, double *out, int *err, void *stream);
 
 /* coulps_cv_charge_term: the part of the divergence that comes through the
  * net's third input channel rho phi (coulps_cv_pack_field writes
@@ -647,8 +650,10 @@ int coulps_cv_stein_region(const float *g16, const void *s1_bf16, const void *s2
  * int32, inside the box, box coordinates) and q_rho (device, n_q floats) are
  * the charge sites whose g is kept (all of them, or those inside R for
  * coulps_cv_stein_region) and their density.  M device 343 x 16 x 16 floats;
- * s1, s2 in the layout `interleave` (s1 and M 16-byte aligned).  Summed in
- * FP64, charges in order.  scratch >= 49 * nb * n_q doubles.  Asynchronous.
+ * s1, s2 in the layout `interleave` (s1, s2 and M 16-byte aligned).  The sum
+ * over the 7 pairs of one (ay, az) class is FP32 per chain and charge; those
+ * 49 n_q partials are summed in FP64, charges in order.  scratch >= 49 * nb *
+ * n_q doubles.  Asynchronous.
  * Errors: EINVAL, ECUDA. */
 int coulps_cv_charge_term(const void *s1_bf16, const void *s2_bf16, const float *M,
                           const int32_t *q_xyz, const float *q_rho, int n_q, int nb,

@@ -12,12 +12,17 @@
 // tcgen05.mma of shape 128 x 16 x 16 (kind::f16, BF16 operands, FP32
 // accumulator in 16 TMEM columns).  The A operand of offset (dz, dy, dx) is the
 // tile's x range shifted by dx in input row (y + dy, z + dz): the input rows
-// (x0-1 .. x0+128) arrive by TMA, each as two planes
-// of 8 channels (16 bytes per site), which is exactly the tensor core's
-// K-major core-matrix layout without swizzle (8 rows x 16 bytes per core
-// matrix, next 8 rows at +128 bytes, the second 8 channels at +plane): a shift
-// by dx is just a +16 byte start address.  Out-of-box rows, planes and x are
-// zero-filled by the TMA unit.  A CTA walks the y range of a work item (a
+// (x0-1 .. x0+128) are kept in shared memory as two planes of 8 channels (16
+// bytes per site), which is exactly the tensor core's K-major core-matrix
+// layout without swizzle (8 rows x 16 bytes per core matrix, next 8 rows at
+// +128 bytes, the second 8 channels at +plane): a shift by dx is just a +16
+// byte start address.  The rows are copied by the CTA's threads with
+// coalesced 16-byte loads (a row of one plane is 130 x 32 contiguous bytes)
+// and 16-byte shared stores into the two planes, out-of-box rows, planes and
+// x written as 0.  (TMA boxes of 8 channels made 780 copies of 16 bytes per
+// tile, and the TMA unit's rate for such small pieces, about one per 2.7
+// cycles per SM, set the kernel's time: 21 us per conv of 64 interleaved
+// 14^3 boxes.)  A CTA walks the y range of a work item (a
 // chunk of y_chunk rows of a column (b, z, x tile)), keeping 4 rows per input
 // plane in a ring, so each tile loads one new row per plane, one tile ahead;
 // the chunk length is chosen so that there are enough items to fill the GPU
@@ -36,6 +41,7 @@
 
 #include "device_common.cuh"
 #include "internal.h"
+#include "tc_common.cuh"
 
 namespace coulps {
 namespace {
@@ -43,7 +49,10 @@ namespace {
 constexpr int kCvThreads = 128;       // 4 warps = the 128 TMEM lanes
 constexpr int kTileX = 128;           // sites per tile (MMA M)
 constexpr int kRowSites = kTileX + 2; // with the x halo
-constexpr int kPlaneBytes = ((kRowSites * 16 + 127) / 128) * 128;  // 8 channels x 2 B per site
+// 8 channels x 2 B per site, + 32 bytes: the planes then start 64 bytes
+// apart modulo 128, so a quarter-warp's stores of 4 sites x 2 halves cover
+// the 32 banks once
+constexpr int kPlaneBytes = kRowSites * 16 + 32;
 constexpr int kRowBytes = 2 * kPlaneBytes;               // both channel halves
 constexpr int kRing = 4;                                 // input rows kept per z plane
 constexpr int kABytes = 3 * kRing * kRowBytes;           // 3 planes x 4 rows
@@ -60,71 +69,20 @@ constexpr int kCvSmem = kWOff + kWBytes;
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) |
                             ((128u >> 4) << 24);
 
-// Shared-memory matrix descriptor, no swizzle, K-major: start >> 4 (bits
-// 0-13), leading byte offset >> 4 (K direction, bits 16-29), stride byte
-// offset >> 4 (M/N direction, bits 32-45), descriptor version 1 (bit 46).
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
-}
-
-__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap *map, int c0, int c1,
-                                            int c2, int c3, int c4, uint32_t bar) {
+// 1D bulk copy global -> shared (16-byte aligned, size a multiple of 16),
+// completion signalled on `bar`.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes,
+                                          uint32_t bar) {
   asm volatile(
-      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
-      "[%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar)
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
       : "memory");
 }
 
-__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem),
-               "r"(ncols)
-               : "memory");
-}
-__device__ __forceinline__ void tmem_relinquish() {
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
-               : "memory");
-}
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-      : "memory");
-}
-__device__ __forceinline__ void fence_after_sync() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void fence_before_sync() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr)
-      : "memory");
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
 
 struct CvConvArgs {
+  const __nv_bfloat16 *in;  // [b][z][y][x][16] BF16
   const uint4 *wpack;  // kWBytes of weights in shared-memory order
   const float *bias;   // 16
   float *out;          // mode 0: h [b][z][y][x][16] FP32
@@ -141,29 +99,30 @@ struct CvConvArgs {
 // One CTA walks work items (a column (b, z, x tile) and a chunk of rows
 // y0 .. y1-1) and, within an item, the tiles y = y0 .. y1-1.  Tile y needs
 // input rows y-1, y, y+1 of planes z-1, z, z+1; the rows of each plane sit in
-// a 4-row ring, so each tile loads one new row per plane (row y+2, one tile
-// ahead).  Tile y's 27 MMAs go to TMEM buffer (count & 1) while the warps read
-// tile y-1 from the other buffer.
-__global__ void __launch_bounds__(kCvThreads)
-    cv_conv3d_kernel(const __grid_constant__ CUtensorMap tm_in, const CvConvArgs a) {
+// a 4-row ring.  While tile y's 27 MMAs run (into TMEM buffer count & 1) the
+// threads load row y+2 of the three planes into registers, read tile y-1 from
+// the other TMEM buffer, and then store the new row into the ring slot that
+// tile y-1 used; one barrier per tile publishes both.
+__global__ void __launch_bounds__(kCvThreads, 3) cv_conv3d_kernel(const CvConvArgs a) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem);  // [0..3] row ring, [4..5] MMA buffers
+      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem);  // [4..5] MMA buffers, [6] weights
   volatile uint32_t *tmem_slot = reinterpret_cast<volatile uint32_t *>(smem + 64);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 80);
-  const uint32_t sA = smem_addr(smem + kAOff), sW = smem_addr(smem + kWOff);
+  unsigned char *ringp = smem + kAOff;
+  const uint32_t sA = smem_addr(ringp), sW = smem_addr(smem + kWOff);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  for (int i = tid; i < kWBytes / 16; i += kCvThreads)
-    reinterpret_cast<uint4 *>(smem + kWOff)[i] = a.wpack[i];
+  // the weights: one bulk copy (a loop of 16-byte loads per thread left every
+  // CTA waiting on L2 latency before its first tile)
   if (tid == 0) {
-    prefetch_tensormap(&tm_in);
-    for (int i = 0; i < 6; ++i) mbar_init(smem_addr(&bars[i]), 1);
+    for (int i = 4; i < 7; ++i) mbar_init(smem_addr(&bars[i]), 1);
     *abort_flag = 0;
     fence_mbar_init();
+    mbar_arrive_expect_tx(smem_addr(&bars[6]), kWBytes);
+    bulk_load(smem_addr(smem + kWOff), a.wpack, kWBytes, smem_addr(&bars[6]));
   }
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   if (warp == 0) {
     tmem_alloc(smem_addr((const void *)tmem_slot), 32);
     tmem_relinquish();
@@ -172,22 +131,47 @@ __global__ void __launch_bounds__(kCvThreads)
   __syncthreads();
   fence_after_sync();
   const uint32_t tmem = *tmem_slot;
+  // only thread 0 issues MMAs: it alone waits for the weights, before its
+  // first MMA (the first rows are loaded by then)
+  bool w_ok = false;
   float bias[16];
 #pragma unroll
   for (int i = 0; i < 16; ++i) bias[i] = a.bias[i];
 
   const int xt = (a.Lx + kTileX - 1) / kTileX;
-  int64_t grow = 0;  // rows this CTA has loaded (ring position and phase)
+  int64_t grow = 0;   // rows this CTA has stored (ring position)
   int64_t gtile = 0;  // tiles this CTA has issued MMAs for (TMEM buffer and phase)
-  // thread 0's counts, for draining after a timeout
-  int64_t rows_issued = 0, rows_waited = 0, mma_issued = 0, mma_waited = 0;
+  int64_t mma_issued = 0, mma_waited = 0;  // thread 0's counts, for draining after a timeout
   bool aborted = false;
 
-  // row k of a column is input row yrow = k - 1; ring slot (grow + k) % 4
-  auto row_slot = [&](int64_t g) { return (int)(g % kRing); };
-  auto row_parity = [&](int64_t g) { return (uint32_t)((g / kRing) & 1); };
-  auto row_base = [&](int dzi, int64_t g) {
-    return sA + (uint32_t)((dzi * kRing + row_slot(g)) * kRowBytes);
+  // ring slot of row g (of this CTA's sequence): 3 planes x 2 channel halves
+  auto row_off = [&](int dzi, int64_t g) { return (dzi * kRing + (int)(g % kRing)) * kRowBytes; };
+  // One row (input row yrow of planes z-1, z, z+1, sites x0-1 .. x0+128) is
+  // 3 x 130 x 2 pieces of 16 bytes; thread t takes pieces t, t + 128, ...:
+  // piece c = (plane dzi = c / 260, site j = (c % 260) / 2, half h = c % 2),
+  // so a warp reads 512 contiguous bytes of one plane's row.
+  constexpr int kPieces = 3 * kRowSites * 2;
+  constexpr int kPer = (kPieces + kCvThreads - 1) / kCvThreads;  // 7
+  auto load_row = [&](int b, int z, int yrow, int x0, uint4 (&v)[kPer]) {
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+      const int c = tid + kCvThreads * i;
+      const int dzi = c / (2 * kRowSites), j = (c % (2 * kRowSites)) >> 1, h = c & 1;
+      const int zz = z + dzi - 1, x = x0 - 1 + j;
+      v[i] = make_uint4(0, 0, 0, 0);
+      if (c < kPieces && zz >= 0 && zz < a.Lz && yrow >= 0 && yrow < a.Ly && x >= 0 && x < a.Lx)
+        v[i] = *reinterpret_cast<const uint4 *>(
+            a.in + ((((size_t)b * a.Lz + zz) * a.Ly + yrow) * a.Lx + x) * 16 + 8 * h);
+    }
+  };
+  auto store_row = [&](int64_t g, const uint4 (&v)[kPer]) {
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+      const int c = tid + kCvThreads * i;
+      if (c >= kPieces) continue;
+      const int dzi = c / (2 * kRowSites), j = (c % (2 * kRowSites)) >> 1, h = c & 1;
+      *reinterpret_cast<uint4 *>(ringp + row_off(dzi, g) + h * kPlaneBytes + j * 16) = v[i];
+    }
   };
 
   auto epilogue = [&](int64_t tt, int b, int z, int y, int x0) {
@@ -234,95 +218,94 @@ __global__ void __launch_bounds__(kCvThreads)
     const int z = r % a.Lz;
     const int b = r / a.Lz;
     const int nrows = ny + 2;  // row k of the item is input row ylo - 1 + k
-    auto issue_row = [&](int k) {  // thread 0
-      const int64_t g = grow + k;
-      const uint32_t bar = smem_addr(&bars[row_slot(g)]);
-      mbar_arrive_expect_tx(bar, 6 * kRowSites * 16);
-      for (int dzi = 0; dzi < 3; ++dzi)
-        for (int h = 0; h < 2; ++h)
-          tma_load_5d(row_base(dzi, g) + h * kPlaneBytes, &tm_in, 8 * h, x0 - 1, ylo + k - 1,
-                      z + dzi - 1, b, bar);
-      ++rows_issued;
-    };
-    auto wait_row = [&](int k) -> bool {
-      const int64_t g = grow + k;
-      return mbar_wait_bounded(smem_addr(&bars[row_slot(g)]), row_parity(g));
-    };
-    if (tid == 0)
-      for (int k = 0; k < kRing && k < nrows; ++k) issue_row(k);
-    bool ok = wait_row(0) && wait_row(1);
-    if (tid == 0 && ok) rows_waited += 2;
-    for (int y = 0; y < ny; ++y) {  // tile ylo + y
-      ok = ok && wait_row(y + 2);
-      if (tid == 0 && ok) {
-        ++rows_waited;
-        fence_after_sync();
-        const int64_t tt = gtile;
-        const uint32_t d = tmem + (uint32_t)((tt & 1) * 16);
-        for (int o = 0; o < 27; ++o) {
-          const int dzi = o / 9, dyi = (o / 3) % 3, dx = o % 3;
-          const uint64_t da = smem_desc(row_base(dzi, grow + y + dyi) + dx * 16, kPlaneBytes, 128);
-          const uint64_t db = smem_desc(sW + o * 512, 256, 128);
-          mma_bf16(d, da, db, kIdesc, o > 0 ? 1u : 0u);
+    // rows 0 .. 2 before the first tile (nrows >= 3), all loads in flight
+    {
+      uint4 v0[kPer], v1[kPer], v2[kPer];
+      load_row(b, z, ylo - 1, x0, v0);
+      load_row(b, z, ylo, x0, v1);
+      load_row(b, z, ylo + 1, x0, v2);
+      store_row(grow, v0);
+      store_row(grow + 1, v1);
+      store_row(grow + 2, v2);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    for (int y = 0; y < ny; ++y) {  // tile ylo + y: rows y .. y + 2 of the item
+      bool ok = true;
+      if (tid == 0) {
+        if (!w_ok) ok = w_ok = mbar_wait_bounded(smem_addr(&bars[6]), 0);
+        if (ok) {
+          const int64_t tt = gtile;
+          const uint32_t d = tmem + (uint32_t)((tt & 1) * 16);
+          for (int o = 0; o < 27; ++o) {
+            const int dzi = o / 9, dyi = (o / 3) % 3, dx = o % 3;
+            const uint64_t da = smem_desc(sA + (uint32_t)row_off(dzi, grow + y + dyi) + dx * 16,
+                                          kPlaneBytes, 128);
+            const uint64_t db = smem_desc(sW + o * 512, 256, 128);
+            mma_bf16(d, da, db, kIdesc, o > 0 ? 1u : 0u);
+          }
+          mma_commit(smem_addr(&bars[4 + (tt & 1)]));
+          ++mma_issued;
         }
-        mma_commit(smem_addr(&bars[4 + (tt & 1)]));
-        ++mma_issued;
       }
+      // the next row (y + 3) into registers while the MMAs run
+      uint4 nv[kPer];
+      const bool more = y + 3 < nrows;
+      if (more) load_row(b, z, ylo + y + 2, x0, nv);
       if (y > 0) {
         const int64_t tp = gtile - 1;
         ok = ok && mbar_wait_bounded(smem_addr(&bars[4 + (tp & 1)]), (uint32_t)((tp >> 1) & 1));
-        if (tid == 0 && ok) {
-          ++mma_waited;
-          // row k = y + 3 reuses the ring slot of row k = y - 1, last read by tile y - 1
-          if (y + 3 < nrows) issue_row(y + 3);
-        }
+        if (tid == 0 && ok) ++mma_waited;
+        ok = __all_sync(0xffffffffu, ok);
+        fence_after_sync();
+        if (ok) epilogue(tp, b, z, ylo + y - 1, x0);
       }
+      // row y + 3 takes the slot of row y - 1, which only tile y - 1 (done) read
+      if (ok && more) store_row(grow + y + 3, nv);
       if (!ok) {
-        atomicOr(a.err, kErrTimeout);
+        if (lane == 0) atomicOr(a.err, kErrTimeout);
         *abort_flag = 1;
       }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       fence_before_sync();
-      __syncthreads();
+      __syncthreads();  // the new row and the free TMEM buffer, for tile y + 1
       fence_after_sync();
+      ++gtile;
       if (*abort_flag) {
         aborted = true;
         break;
       }
-      if (y > 0) epilogue(gtile - 1, b, z, ylo + y - 1, x0);
-      fence_before_sync();
-      __syncthreads();  // the TMEM buffer read above is free for tile y + 1
-      fence_after_sync();
-      ++gtile;
     }
     if (aborted) break;
     // last tile of the column
     {
       const int64_t tp = gtile - 1;
-      ok = mbar_wait_bounded(smem_addr(&bars[4 + (tp & 1)]), (uint32_t)((tp >> 1) & 1));
+      bool ok = mbar_wait_bounded(smem_addr(&bars[4 + (tp & 1)]), (uint32_t)((tp >> 1) & 1));
       if (tid == 0 && ok) ++mma_waited;
-      if (!ok) {
-        atomicOr(a.err, kErrTimeout);
+      ok = __all_sync(0xffffffffu, ok);
+      fence_after_sync();
+      if (ok) {
+        epilogue(tp, b, z, ylo + ny - 1, x0);
+      } else {
+        if (lane == 0) atomicOr(a.err, kErrTimeout);
         *abort_flag = 1;
       }
       fence_before_sync();
-      __syncthreads();
+      __syncthreads();  // the ring and both TMEM buffers are free for the next item
       fence_after_sync();
       if (*abort_flag) {
         aborted = true;
         break;
       }
-      epilogue(tp, b, z, ylo + ny - 1, x0);
-      fence_before_sync();
-      __syncthreads();
-      fence_after_sync();
     }
     grow += nrows;
   }
   if (aborted && tid == 0) {
-    // leave no copy or MMA in flight: every row issued and every committed
-    // tile not yet waited, in order, with bounded waits
-    for (int64_t g = rows_waited; g < rows_issued; ++g)
-      if (!mbar_wait_bounded(smem_addr(&bars[row_slot(g)]), row_parity(g))) break;
+    // leave no copy or MMA in flight: the weights and every committed tile
+    // not yet waited, in order, with bounded waits
+    if (!w_ok) mbar_wait_bounded(smem_addr(&bars[6]), 0);  // its phase 0, done or not
     for (int64_t t = mma_waited; t < mma_issued; ++t)
       if (!mbar_wait_bounded(smem_addr(&bars[4 + (t & 1)]), (uint32_t)((t >> 1) & 1))) break;
   }
@@ -336,19 +319,8 @@ __global__ void __launch_bounds__(kCvThreads)
 int cv_conv3d_launch(const void *in_bf16, const void *wpack, const float *bias, float *out,
                      void *out_a, void *out_s, int nb, int Lx, int Ly, int Lz, int x_period,
                      int *err, cudaStream_t s) {
-  auto enc = tensor_map_encoder();
-  if (!enc) return COULPS_ECUDA;
-  CUtensorMap map;
-  cuuint64_t dims[5] = {16, (cuuint64_t)Lx, (cuuint64_t)Ly, (cuuint64_t)Lz, (cuuint64_t)nb};
-  cuuint64_t strides[4] = {32, (cuuint64_t)Lx * 32, (cuuint64_t)Lx * Ly * 32,
-                           (cuuint64_t)Lx * Ly * Lz * 32};
-  cuuint32_t box[5] = {8, (cuuint32_t)kRowSites, 1, 1, 1};
-  cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-  if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(in_bf16), dims, strides,
-          box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-    return COULPS_ECUDA;
   CvConvArgs a;
+  a.in = reinterpret_cast<const __nv_bfloat16 *>(in_bf16);
   a.wpack = reinterpret_cast<const uint4 *>(wpack);
   a.bias = bias;
   a.out = out;
@@ -360,7 +332,7 @@ int cv_conv3d_launch(const void *in_bf16, const void *wpack, const float *bias, 
   a.n_cols = nb * Lz * ((Lx + kTileX - 1) / kTileX);
   a.err = err;
   static bool configured = false;
-  const int smem = kCvSmem + 1024;
+  const int smem = kCvSmem + 128;  // + alignment slack
   if (!configured) {
     // the largest shared-memory carveout: the occupancy query below (and the
     // launch) then count the 3 CTAs per SM that shared memory allows
@@ -406,7 +378,7 @@ int cv_conv3d_launch(const void *in_bf16, const void *wpack, const float *bias, 
   int grid = slots;
   if (grid > a.n_items) grid = a.n_items;
   if (grid < 1) return COULPS_OK;
-  cv_conv3d_kernel<<<grid, kCvThreads, smem, s>>>(map, a);
+  cv_conv3d_kernel<<<grid, kCvThreads, smem, s>>>(a);
   return cudaGetLastError() == cudaSuccess ? COULPS_OK : COULPS_ECUDA;
 }
 

@@ -28,6 +28,7 @@
 
 #include "device_common.cuh"
 #include "internal.h"
+#include "tc_common.cuh"
 
 namespace coulps {
 namespace {
@@ -234,13 +235,24 @@ __global__ void cv_sum_partials_kernel(const double *__restrict__ partials, int 
 // The sites q next to R split, per axis, into at most 5 runs of one class
 // (q = lo-1, q = lo, lo < q < hi-1, q = hi-1, q = hi, clipped to E and merged
 // when R is thin), so R + 1 is a union of at most 125 boxes of one class each.
-// One CTA takes up to kRedThreads (q, chain, dz) items of one box: it stages
-// the box's kernel K[class] in shared memory as [e][c2][c1] and each thread
-// forms D[c2] = sum_{c1, e} K[c2][c1][e] s1[c1, q + e] over the 9 offsets e
-// of its z plane dz (K reads are warp-wide broadcasts, four FMAs per 16-byte
-// load), then its partial s2[q] . D; a site's three partials (one per dz) are
-// added in the finish.  (A thread per site and all 27 offsets gave a third
-// of the threads and waited on their loads.)
+// The divergence over each box is a GEMM on the tensor cores (tcgen05).  A
+// tile is two x-adjacent sites of the box times 64 chains: 128 rows (the MMA's
+// M), row 64 s + c = site s, chain 64 g + c of chain group g, and
+//   D[row][n] = sum_e sum_c1 s1[c1, q + e] B_e[n][c1],
+// with B_e[16 p + c2][c1] the p-th BF16 part of K[class][e][c2][c1]: K = hi +
+// mid + lo, each part the BF16 rounding of what the parts before it leave,
+// so the three hold K's 24-bit FP32 significand and each product with a BF16
+// s1 value is exact (only the FP32 accumulation order differs from FP32
+// arithmetic).  One MMA of K = 16 per offset e (27 per tile) accumulates
+// N = 48 columns in TMEM; the epilogue adds the parts, dots the sum with
+// s2[q] and writes one FP32 value per (chain, site).  The tile's operand A
+// comes from one TMA box per channel half: the 4 x 3 x 3 sites around the
+// two sites for the 64 chains, [z][y][x][chain][8 channels], so the 64 rows
+// of one site and one offset are 1 KB of consecutive core matrices and the
+// second site's rows follow 1 KB later, one x step on: each offset's A is
+// a descriptor into the box, with no per-offset copy.  (Before: the same
+// sums on the FMA pipes, then a gather of every (row, offset) by 16-byte
+// copies; both ran 55 us per evaluation of 64 chains x 1000 sites.)
 struct RegionRuns {
   int start[3][5], len[3][5], cls[3][5];
   int nrun[3];
@@ -255,76 +267,222 @@ struct RegionRuns {
 
 constexpr int kRegionKFloats = 27 * 16 * 16;
 
-__global__ void __launch_bounds__(kRedThreads)
-    cv_region_div_kernel(const __nv_bfloat16 *__restrict__ s1, const __nv_bfloat16 *__restrict__ s2,
-                         const float *__restrict__ Ktab, const RegionRuns r,
-                         double *__restrict__ part) {
-  __shared__ __align__(16) float K[kRegionKFloats];  // [e][c2][c1]
+constexpr int kRgThreads = 128;               // 4 warps = the 128 TMEM lanes
+constexpr int kRgTPC = 4;                       // tiles per CTA (all of one box)
+constexpr int kRgHalf = 36 * 64 * 16;           // one channel half of a tile's box: 36,864 B
+constexpr int kRgABuf = 2 * kRgHalf;            // both halves: 73,728 B
+constexpr int kRgBe = 48 * 16 * 2;              // one offset's B: 48 rows x 16 channels BF16
+constexpr int kRgAOff = 1024;                   // header: mbarriers at 0, TMEM address at 64
+constexpr int kRgBOff = kRgAOff + 2 * kRgABuf;  // two A buffers
+constexpr int kRgSmem = kRgBOff + 27 * kRgBe;   // 189,952 bytes
+// tcgen05 instruction descriptor, kind::f16: D = F32, A = B = BF16, both
+// K-major, N = 48, M = 128
+constexpr uint32_t kRgIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((48u >> 3) << 17) |
+                              ((128u >> 4) << 24);
+
+// One CTA runs up to kRgTPC tiles of one class box.  Shared memory: the
+// class's B (staged once, K-major no-swizzle core matrices: element (n, c1)
+// of offset e at kRgBOff + e kRgBe + (n / 8) 128 + (c1 / 8) 768 + (n % 8) 16
+// + (c1 % 8) 2) and two A buffers, filled by TMA one tile ahead.  Tile t's
+// 27 MMAs read buffer t % 2; once they have completed, that buffer is
+// refilled with tile t + 2 while the warps read the accumulator.  Every wait
+// is bounded: on a timeout the CTA sets the error word, writes nothing more,
+// waits (bounded) for its copies and MMAs in flight and frees its TMEM.
+__global__ void __launch_bounds__(kRgThreads)
+    cv_region_mma_kernel(const __grid_constant__ CUtensorMap tm_s1,
+                         const __nv_bfloat16 *__restrict__ s2, const float *__restrict__ Ktab,
+                         const RegionRuns r, double *__restrict__ part, int *err) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *smem = align_smem128(smem_raw);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem);  // [0..1] A buffers, [2] MMAs
+  volatile uint32_t *tmem_slot = reinterpret_cast<volatile uint32_t *>(smem + 64);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 80);
+  const uint32_t sA = smem_addr(smem + kRgAOff), sB = smem_addr(smem + kRgBOff);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  // the box of this CTA: the last with cta_first[box] <= blockIdx.x
   int box = 0;
-  while (box + 1 < r.n_box && r.cta_first[box + 1] <= (int)blockIdx.x) ++box;
+  for (int lo = 0, hi = r.n_box - 1; lo <= hi;) {
+    const int mid = (lo + hi) >> 1;
+    if (r.cta_first[mid] <= (int)blockIdx.x) {
+      box = mid;
+      lo = mid + 1;
+    } else {
+      hi = mid - 1;
+    }
+  }
   const int bx = box % r.nrun[0], by = (box / r.nrun[0]) % r.nrun[1], bz = box / (r.nrun[0] * r.nrun[1]);
   const int cls = r.cls[0][bx] + 6 * r.cls[1][by] + 36 * r.cls[2][bz];
-  // the class's kernel, stored [e][c2][c1] as staged: a 16-byte copy
-  const float4 *kg = reinterpret_cast<const float4 *>(Ktab + (size_t)cls * kRegionKFloats);
-  for (int i = threadIdx.x; i < kRegionKFloats / 4; i += kRedThreads)
-    reinterpret_cast<float4 *>(K)[i] = kg[i];
-  __syncthreads();
   const int lx = r.len[0][bx], ly = r.len[1][by], lz = r.len[2][bz];
-  const int nq = lx * ly * lz;
-  // a warp takes one z plane dz of 32 consecutive items, so its K reads stay
-  // warp-wide broadcasts
-  const int item3 = (blockIdx.x - r.cta_first[box]) * kRedThreads + threadIdx.x;
-  const int dzi = (item3 >> 5) % 3, item = (item3 / 96) * 32 + (item3 & 31);
-  if (item >= nq * r.nb) return;
-  const int chain = item / nq, k = item % nq;
-  const int x = r.start[0][bx] + k % lx, y = r.start[1][by] + (k / lx) % ly, z = r.start[2][bz] + k / (lx * ly);
-  const __nv_bfloat16 *s1c = s1 + chain * r.L.sb * 16;
-  float D[16];
+  const int nxp = (lx + 1) >> 1, ncg = (r.nb + 63) >> 6;
+  const int tiles = nxp * ly * lz * ncg;
+  const int t0 = ((int)blockIdx.x - r.cta_first[box]) * kRgTPC;
+  const int nt = min(kRgTPC, tiles - t0);
+  const int64_t nq = (int64_t)r.nqx * r.nqy * r.nqz;
+
+  // tile t of this CTA: chain group, first site (x of site 0)
+  auto tile_of = [&](int t, int &cg, int &xs, int &ys, int &zs) {
+    int u = t0 + t;
+    cg = u % ncg;
+    u /= ncg;
+    xs = r.start[0][bx] + 2 * (u % nxp);
+    u /= nxp;
+    ys = r.start[1][by] + u % ly;
+    zs = r.start[2][bz] + u / ly;
+  };
+  auto issue = [&](int t) {  // thread 0
+    int cg, xs, ys, zs;
+    tile_of(t, cg, xs, ys, zs);
+    const uint32_t bar = smem_addr(&bars[t & 1]);
+    mbar_arrive_expect_tx(bar, kRgABuf);
+    for (int h = 0; h < 2; ++h)
+      tma_load_5d(sA + (uint32_t)((t & 1) * kRgABuf + h * kRgHalf), &tm_s1, 8 * h, 64 * cg,
+                  xs - 1, ys - 1, zs - 1, bar);
+  };
+
+  int issued = 0, waited = 0, mma_issued = 0, mma_waited = 0;  // thread 0's counts
+  if (tid == 0) {
+    prefetch_tensormap(&tm_s1);
+    for (int i = 0; i < 3; ++i) mbar_init(smem_addr(&bars[i]), 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+    for (; issued < 2 && issued < nt; ++issued) issue(issued);
+  }
+  if (warp == 0) {
+    tmem_alloc(smem_addr((const void *)tmem_slot), 64);
+    tmem_relinquish();
+  }
+
+  // B: the class kernel in three BF16 parts, 8 channels c1 per unit; every
+  // unit's loads are issued before any is used
+  {
+    const float *kc = Ktab + (size_t)cls * kRegionKFloats;
+    float4 f[7][2];
 #pragma unroll
-  for (int c = 0; c < 16; ++c) D[c] = 0.f;
-  for (int e = 9 * dzi; e < 9 * dzi + 9; ++e) {
-    const int xx = x + e % 3 - 1, yy = y + (e / 3) % 3 - 1, zz = z + e / 9 - 1;
-    if (xx < 0 || yy < 0 || zz < 0 || xx >= r.ex || yy >= r.ey || zz >= r.ez) continue;
-    const uint4 *sp = reinterpret_cast<const uint4 *>(s1c + (zz * r.L.sz + yy * r.L.sy + xx) * 16);
-    const uint4 u0 = sp[0], u1 = sp[1];
-    float v[16];
-    const __nv_bfloat162 *h0 = reinterpret_cast<const __nv_bfloat162 *>(&u0);
-    const __nv_bfloat162 *h1 = reinterpret_cast<const __nv_bfloat162 *>(&u1);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const float2 a = __bfloat1622float2(h0[i]), b = __bfloat1622float2(h1[i]);
-      v[2 * i] = a.x; v[2 * i + 1] = a.y; v[8 + 2 * i] = b.x; v[8 + 2 * i + 1] = b.y;
-    }
-    const float4 *ke = reinterpret_cast<const float4 *>(K + e * 256);
-#pragma unroll
-    for (int c2 = 0; c2 < 16; ++c2) {
-      float d = D[c2];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const float4 w = ke[c2 * 4 + j];
-        d = fmaf(w.x, v[4 * j], d);
-        d = fmaf(w.y, v[4 * j + 1], d);
-        d = fmaf(w.z, v[4 * j + 2], d);
-        d = fmaf(w.w, v[4 * j + 3], d);
+    for (int k = 0; k < 7; ++k) {
+      const int u = tid + kRgThreads * k;
+      if (u < 27 * 16 * 2) {
+        const float4 *src = reinterpret_cast<const float4 *>(kc + (u >> 5) * 256 + ((u >> 1) & 15) * 16 + 8 * (u & 1));
+        f[k][0] = src[0];
+        f[k][1] = src[1];
       }
-      D[c2] = d;
+    }
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+      const int u = tid + kRgThreads * k;
+      if (u >= 27 * 16 * 2) continue;
+      const int e = u >> 5, c2 = (u >> 1) & 15, hh = u & 1;
+      const float v[8] = {f[k][0].x, f[k][0].y, f[k][0].z, f[k][0].w,
+                          f[k][1].x, f[k][1].y, f[k][1].z, f[k][1].w};
+      __align__(16) __nv_bfloat16 pt[3][8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        float x = v[i];
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+          pt[p][i] = __float2bfloat16_rn(x);
+          x -= __bfloat162float(pt[p][i]);  // exact: x minus its own rounding
+        }
+      }
+#pragma unroll
+      for (int p = 0; p < 3; ++p) {
+        const int n = 16 * p + c2;
+        *reinterpret_cast<uint4 *>(smem + kRgBOff + e * kRgBe + (n >> 3) * 128 + hh * 768 + (n & 7) * 16) =
+            *reinterpret_cast<const uint4 *>(pt[p]);
+      }
     }
   }
-  const uint4 *sq = reinterpret_cast<const uint4 *>(s2 + (chain * r.L.sb + z * r.L.sz + y * r.L.sy + x) * 16);
-  const uint4 w0 = sq[0], w1 = sq[1];
-  const __nv_bfloat162 *g0 = reinterpret_cast<const __nv_bfloat162 *>(&w0);
-  const __nv_bfloat162 *g1 = reinterpret_cast<const __nv_bfloat162 *>(&w1);
-  float acc = 0.f;
+  // the B stores are made visible to the tensor core's async proxy
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+
+  bool aborted = false;
+  for (int t = 0; t < nt; ++t) {
+    int cg, xs, ys, zs;
+    tile_of(t, cg, xs, ys, zs);
+    // this thread's row: site s = tid / 64 (x = xs + s), chain 64 cg + tid % 64;
+    // its s2 is loaded before the waits
+    const int s = tid >> 6, chain = 64 * cg + (tid & 63);
+    const int x = xs + s;
+    const bool valid = chain < r.nb && x - r.start[0][bx] < lx;
+    uint4 w0 = make_uint4(0, 0, 0, 0), w1 = w0;
+    if (valid) {
+      const uint4 *sq = reinterpret_cast<const uint4 *>(
+          s2 + ((size_t)chain * r.L.sb + zs * r.L.sz + ys * r.L.sy + x) * 16);
+      w0 = sq[0];
+      w1 = sq[1];
+    }
+    bool ok = true;
+    if (tid == 0) {
+      ok = mbar_wait_bounded(smem_addr(&bars[t & 1]), (uint32_t)((t >> 1) & 1));
+      if (ok) {
+        ++waited;
+        fence_after_sync();
+        const uint32_t abuf = sA + (uint32_t)((t & 1) * kRgABuf);
+        for (int e = 0; e < 27; ++e) {
+          const int dx = e % 3, dy = (e / 3) % 3, dz = e / 9;  // offset + 1 per axis
+          const uint32_t pos = (uint32_t)((dz * 3 + dy) * 4 + dx);  // site 0's x is box x 1
+          mma_bf16(tmem, smem_desc(abuf + pos * 1024, kRgHalf, 128),
+                   smem_desc(sB + (uint32_t)(e * kRgBe), 768, 128), kRgIdesc, e > 0 ? 1u : 0u);
+        }
+        mma_commit(smem_addr(&bars[2]));
+        ++mma_issued;
+      }
+    }
+    ok = ok && mbar_wait_bounded(smem_addr(&bars[2]), (uint32_t)(t & 1));
+    if (tid == 0 && ok) {
+      ++mma_waited;
+      if (issued < nt) issue(issued++);  // the buffer of tile t is free: tile t + 2
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    if (!ok) {
+      if (lane == 0) atomicOr(err, kErrTimeout);
+      *abort_flag = 1;
+    }
+    fence_after_sync();
+    if (ok) {
+      float hi[16], mid[16], lo[16];
+      const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16);
+      tmem_ld16(ta, hi);
+      tmem_ld16(ta + 16, mid);
+      tmem_ld16(ta + 32, lo);
+      if (valid) {
+        const __nv_bfloat162 *g0 = reinterpret_cast<const __nv_bfloat162 *>(&w0);
+        const __nv_bfloat162 *g1 = reinterpret_cast<const __nv_bfloat162 *>(&w1);
+        float acc = 0.f;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const float2 a = __bfloat1622float2(g0[i]), b = __bfloat1622float2(g1[i]);
-    acc = fmaf(a.x, D[2 * i], acc);
-    acc = fmaf(a.y, D[2 * i + 1], acc);
-    acc = fmaf(b.x, D[8 + 2 * i], acc);
-    acc = fmaf(b.y, D[8 + 2 * i + 1], acc);
+        for (int i = 0; i < 4; ++i) {
+          const float2 a = __bfloat1622float2(g0[i]), b = __bfloat1622float2(g1[i]);
+          acc = fmaf(a.x, (lo[2 * i] + mid[2 * i]) + hi[2 * i], acc);
+          acc = fmaf(a.y, (lo[2 * i + 1] + mid[2 * i + 1]) + hi[2 * i + 1], acc);
+          acc = fmaf(b.x, (lo[8 + 2 * i] + mid[8 + 2 * i]) + hi[8 + 2 * i], acc);
+          acc = fmaf(b.y, (lo[9 + 2 * i] + mid[9 + 2 * i]) + hi[9 + 2 * i], acc);
+        }
+        const int qi = ((zs - r.qz0) * r.nqy + (ys - r.qy0)) * r.nqx + (x - r.qx0);
+        part[(size_t)chain * nq + qi] = (double)acc;
+      }
+    }
+    fence_before_sync();
+    __syncthreads();  // the accumulator is free for the next tile's MMAs
+    fence_after_sync();
+    if (*abort_flag) {
+      aborted = true;
+      break;
+    }
   }
-  const int qi = ((z - r.qz0) * r.nqy + (y - r.qy0)) * r.nqx + (x - r.qx0);
-  part[((size_t)chain * ((size_t)r.nqx * r.nqy * r.nqz) + qi) * 3 + dzi] = (double)acc;
+  if (aborted && tid == 0) {
+    // leave no copy or MMA in flight (bounded waits, in order)
+    for (int k = waited; k < issued; ++k)
+      if (!mbar_wait_bounded(smem_addr(&bars[k & 1]), (uint32_t)((k >> 1) & 1))) break;
+    for (int k = mma_waited; k < mma_issued; ++k)
+      if (!mbar_wait_bounded(smem_addr(&bars[2]), (uint32_t)(k & 1))) break;
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 64);
 }
 
 // out[b] = sum_q part[b][q] - sum_{x in R} g_x (A phi)_x, one CTA per chain
@@ -380,57 +538,92 @@ __device__ __forceinline__ void pair_axis(int a, int &f, int &e) {
   e = a < 2 ? a : (a < 5 ? a - 3 : a - 6);
 }
 
-// One CTA per (charge, 16 chains, (ay, az)): thread (chain, c2) walks the 7
-// pairs of one (y, z) offset class; the 16 chains of a CTA share each M row.
-// (With a CTA per z class, 49 pairs of dependent global loads per thread
-// left the kernel waiting on load latency.)
-__global__ void __launch_bounds__(kRedThreads)
+// One CTA per (charge, (ay, az) class, 64 chains), one thread per chain: the
+// class's seven M matrices are staged in shared memory and read as warp-wide
+// broadcasts (every lane of a warp reads the same element), and a thread
+// loads, per pair, its chain's s1 at x + f + e and s2 at x + f (two 32-byte
+// rows; positions outside the box are clamped into it and their terms
+// multiplied by 0) before forming sum_c2 s2[c2] sum_c1 M[c2][c1] s1[c1] in
+// FP32.  (A thread per (chain, c2) with M read from global memory made every
+// load instruction touch 16 different M rows: 27.5 us per evaluation of 8
+// charges x 64 chains, bound by L1 wavefronts and load latency.)
+constexpr int kChThreads = 64;
+
+__global__ void __launch_bounds__(kChThreads)
     cv_charge_partial_kernel(const __nv_bfloat16 *__restrict__ s1,
                              const __nv_bfloat16 *__restrict__ s2, const float *__restrict__ M,
                              const int32_t *__restrict__ qxyz, const float *__restrict__ qrho,
                              int n_q, int nb, int ex, int ey, int ez, BoxLayout L,
                              double *__restrict__ partials) {
+  __shared__ __align__(16) float Ms[7 * 256];  // [pair a][c2][c1]
   const int k = blockIdx.x;
-  const int c2 = threadIdx.x & 15;
-  const int chain = blockIdx.y * (kRedThreads / 16) + (threadIdx.x >> 4);
+  const int cz = blockIdx.z;  // (ay, az) class: pairs 7 cz .. 7 cz + 6
+  const int chain = blockIdx.y * kChThreads + threadIdx.x;
   const bool live = chain < nb;
-  const int x = qxyz[3 * k], y = qxyz[3 * k + 1], z = qxyz[3 * k + 2];
-  const __nv_bfloat16 *s1c = s1 + (live ? chain : 0) * L.sb * 16;
-  const __nv_bfloat16 *s2c = s2 + (live ? chain : 0) * L.sb * 16;
-  float acc = 0.f;
-  const int p0 = 7 * blockIdx.z;
-#pragma unroll
-  for (int p = p0; p < p0 + 7; ++p) {
-    if (!live) break;
-    int fx, fy, fz, exx, eyy, ezz;
-    pair_axis(p % 7, fx, exx);
-    pair_axis((p / 7) % 7, fy, eyy);
-    pair_axis(p / 49, fz, ezz);
-    const int qx = x + fx, qy = y + fy, qz = z + fz;
-    if (qx < 0 || qy < 0 || qz < 0 || qx >= ex || qy >= ey || qz >= ez) continue;
-    const int rx = qx + exx, ry = qy + eyy, rz = qz + ezz;
-    if (rx < 0 || ry < 0 || rz < 0 || rx >= ex || ry >= ey || rz >= ez) continue;
-    const uint4 *sp = reinterpret_cast<const uint4 *>(s1c + (rz * L.sz + ry * L.sy + rx) * 16);
-    const uint4 u0 = sp[0], u1 = sp[1];
-    const __nv_bfloat162 *h0 = reinterpret_cast<const __nv_bfloat162 *>(&u0);
-    const __nv_bfloat162 *h1 = reinterpret_cast<const __nv_bfloat162 *>(&u1);
-    const float4 *m = reinterpret_cast<const float4 *>(M + ((size_t)p * 16 + c2) * 16);
-    float d = 0.f;
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      const float2 a0 = __bfloat1622float2(h0[2 * i]), a1 = __bfloat1622float2(h0[2 * i + 1]);
-      const float2 b0 = __bfloat1622float2(h1[2 * i]), b1 = __bfloat1622float2(h1[2 * i + 1]);
-      const float4 wa = m[i], wb = m[2 + i];
-      d = fmaf(wa.x, a0.x, d); d = fmaf(wa.y, a0.y, d); d = fmaf(wa.z, a1.x, d); d = fmaf(wa.w, a1.y, d);
-      d = fmaf(wb.x, b0.x, d); d = fmaf(wb.y, b0.y, d); d = fmaf(wb.z, b1.x, d); d = fmaf(wb.w, b1.y, d);
-    }
-    acc = fmaf(__bfloat162float(s2c[(qz * L.sz + qy * L.sy + qx) * 16 + c2]), d, acc);
+  {
+    const float4 *src = reinterpret_cast<const float4 *>(M + (size_t)7 * cz * 256);
+    for (int i = threadIdx.x; i < 7 * 64; i += kChThreads) reinterpret_cast<float4 *>(Ms)[i] = src[i];
   }
-  // sum over the 16 c2 lanes of this chain (xor butterfly within the half-warp)
-  double v = (double)acc;
+  const int x = qxyz[3 * k], y = qxyz[3 * k + 1], z = qxyz[3 * k + 2];
+  const __nv_bfloat16 *s1c = s1 + (size_t)(live ? chain : 0) * L.sb * 16;
+  const __nv_bfloat16 *s2c = s2 + (size_t)(live ? chain : 0) * L.sb * 16;
+  int fy, fz, eyy, ezz;
+  pair_axis(cz % 7, fy, eyy);
+  pair_axis(cz / 7, fz, ezz);
+  const int qy = y + fy, qz = z + fz, ry = qy + eyy, rz = qz + ezz;
+  const bool yz_in = qy >= 0 && qz >= 0 && qy < ey && qz < ez && ry >= 0 && rz >= 0 && ry < ey && rz < ez;
+  const int qyc = min(max(qy, 0), ey - 1), qzc = min(max(qz, 0), ez - 1);
+  const int ryc = min(max(ry, 0), ey - 1), rzc = min(max(rz, 0), ez - 1);
+  uint4 u[7][2], w[7][2];
+  float on[7];
 #pragma unroll
-  for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if (live && c2 == 0) partials[((size_t)chain * n_q + k) * 49 + blockIdx.z] = v * (double)qrho[k];
+  for (int a = 0; a < 7; ++a) {
+    int fx, exx;
+    pair_axis(a, fx, exx);
+    const int qx = x + fx, rx = qx + exx;
+    on[a] = (live && yz_in && qx >= 0 && qx < ex && rx >= 0 && rx < ex) ? 1.f : 0.f;
+    const int qxc = min(max(qx, 0), ex - 1), rxc = min(max(rx, 0), ex - 1);
+    const uint4 *sp = reinterpret_cast<const uint4 *>(s1c + (rzc * L.sz + ryc * L.sy + rxc) * 16);
+    const uint4 *sq = reinterpret_cast<const uint4 *>(s2c + (qzc * L.sz + qyc * L.sy + qxc) * 16);
+    u[a][0] = sp[0];
+    u[a][1] = sp[1];
+    w[a][0] = sq[0];
+    w[a][1] = sq[1];
+  }
+  __syncthreads();  // Ms
+  float acc = 0.f;
+#pragma unroll
+  for (int a = 0; a < 7; ++a) {
+    float v[16], g[16];
+    const __nv_bfloat162 *h0 = reinterpret_cast<const __nv_bfloat162 *>(&u[a][0]);
+    const __nv_bfloat162 *h1 = reinterpret_cast<const __nv_bfloat162 *>(&u[a][1]);
+    const __nv_bfloat162 *g0 = reinterpret_cast<const __nv_bfloat162 *>(&w[a][0]);
+    const __nv_bfloat162 *g1 = reinterpret_cast<const __nv_bfloat162 *>(&w[a][1]);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float2 p0 = __bfloat1622float2(h0[i]), p1 = __bfloat1622float2(h1[i]);
+      const float2 q0 = __bfloat1622float2(g0[i]), q1 = __bfloat1622float2(g1[i]);
+      v[2 * i] = p0.x; v[2 * i + 1] = p0.y; v[8 + 2 * i] = p1.x; v[8 + 2 * i + 1] = p1.y;
+      g[2 * i] = q0.x; g[2 * i + 1] = q0.y; g[8 + 2 * i] = q1.x; g[8 + 2 * i + 1] = q1.y;
+    }
+    const float4 *ma = reinterpret_cast<const float4 *>(Ms + a * 256);
+    float sa = 0.f;
+#pragma unroll
+    for (int c2 = 0; c2 < 16; ++c2) {
+      float d = 0.f;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float4 m = ma[c2 * 4 + j];
+        d = fmaf(m.x, v[4 * j], d);
+        d = fmaf(m.y, v[4 * j + 1], d);
+        d = fmaf(m.z, v[4 * j + 2], d);
+        d = fmaf(m.w, v[4 * j + 3], d);
+      }
+      sa = fmaf(g[c2], d, sa);
+    }
+    acc = fmaf(on[a], sa, acc);
+  }
+  if (live) partials[((size_t)chain * n_q + k) * 49 + cz] = (double)acc * (double)qrho[k];
 }
 
 // out[b] += sum_k partials[b][k], k in order
@@ -558,8 +751,9 @@ int coulps_cv_stein_sum(const float *g16, const float *D, const void *s2_bf16, c
 int coulps_cv_stein_region(const float *g16, const void *s1_bf16, const void *s2_bf16,
                            const float *Aphi, const float *Ktab, int nb, const int32_t *edims,
                            int interleave, const int32_t *lo, const int32_t *hi, double *scratch,
-                           int64_t scratch_doubles, double *out, void *stream) {
-  if (!g16 || !s1_bf16 || !s2_bf16 || !Aphi || !Ktab || !edims || !lo || !hi || !scratch || !out)
+                           int64_t scratch_doubles, double *out, int *err, void *stream) {
+  if (!g16 || !s1_bf16 || !s2_bf16 || !Aphi || !Ktab || !edims || !lo || !hi || !scratch || !out ||
+      !err)
     return COULPS_EINVAL;
   if (nb < 1) return COULPS_EINVAL;
   for (int k = 0; k < 3; ++k)
@@ -579,22 +773,49 @@ int coulps_cv_stein_region(const float *g16, const void *s1_bf16, const void *s2
   r.qy0 = std::max(lo[1] - 1, 0); r.nqy = std::min(hi[1] + 1, edims[1]) - r.qy0;
   r.qz0 = std::max(lo[2] - 1, 0); r.nqz = std::min(hi[2] + 1, edims[2]) - r.qz0;
   const int64_t nq = (int64_t)r.nqx * r.nqy * r.nqz;
-  if (scratch_doubles < 3 * nq * nb) return COULPS_EINVAL;
+  if (scratch_doubles < nq * nb) return COULPS_EINVAL;
   r.n_box = r.nrun[0] * r.nrun[1] * r.nrun[2];
   int64_t ctas = 0;
+  const int64_t ncg = (nb + 63) / 64;
   for (int b = 0; b < r.n_box; ++b) {
     const int bx = b % r.nrun[0], by = (b / r.nrun[0]) % r.nrun[1], bz = b / (r.nrun[0] * r.nrun[1]);
-    // 3 threads per item (one per z plane), in groups of 96 per 32 items
-    const int64_t items = 96 * (((int64_t)r.len[0][bx] * r.len[1][by] * r.len[2][bz] * nb + 31) / 32);
+    // tiles of two x-adjacent sites x 64 chains, kRgTPC per CTA
+    const int64_t tiles = (int64_t)((r.len[0][bx] + 1) / 2) * r.len[1][by] * r.len[2][bz] * ncg;
+    if (tiles > 0x7fffffff) return COULPS_EINVAL;
     r.cta_first[b] = (int)ctas;
-    ctas += (items + kRedThreads - 1) / kRedThreads;
+    ctas += (tiles + kRgTPC - 1) / kRgTPC;
     if (ctas > 0x7fffffff) return COULPS_EINVAL;
   }
   r.cta_first[r.n_box] = (int)ctas;
+  // s1 as a 5D tensor (channel, chain, x, y, z) of E with zero fill outside
+  // it; box (8 channels, 64 chains, 4 x, 3 y, 3 z)
+  auto enc = tensor_map_encoder();
+  if (!enc) return COULPS_ECUDA;
+  CUtensorMap tm;
+  cuuint64_t dims[5] = {16, (cuuint64_t)nb, (cuuint64_t)edims[0], (cuuint64_t)edims[1],
+                        (cuuint64_t)edims[2]};
+  cuuint64_t strides[4] = {(cuuint64_t)r.L.sb * 32, 32, (cuuint64_t)r.L.sy * 32,
+                           (cuuint64_t)r.L.sz * 32};
+  cuuint32_t box[5] = {8, 64, 4, 3, 3};
+  cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(s1_bf16), dims, strides,
+          box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return COULPS_ECUDA;
   cudaStream_t s = (cudaStream_t)stream;
-  cv_region_div_kernel<<<(unsigned)ctas, kRedThreads, 0, s>>>(
-      (const __nv_bfloat16 *)s1_bf16, (const __nv_bfloat16 *)s2_bf16, Ktab, r, scratch);
-  cv_region_finish_kernel<<<nb, kRedThreads, 0, s>>>(scratch, (int)(3 * nq), g16, Aphi, r.L, lo[0],
+  const int smem = kRgSmem + 128;  // + alignment slack
+  static bool configured = false;
+  if (!configured) {
+    if (cudaFuncSetAttribute(cv_region_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem) != cudaSuccess) {
+      cudaGetLastError();
+      return COULPS_ECUDA;
+    }
+    configured = true;
+  }
+  cv_region_mma_kernel<<<(unsigned)ctas, kRgThreads, smem, s>>>(
+      tm, (const __nv_bfloat16 *)s2_bf16, Ktab, r, scratch, err);
+  cv_region_finish_kernel<<<nb, kRedThreads, 0, s>>>(scratch, (int)nq, g16, Aphi, r.L, lo[0],
                                                      lo[1], lo[2], hi[0], hi[1], hi[2], out);
   return cudaGetLastError() == cudaSuccess ? COULPS_OK : COULPS_ECUDA;
 }
@@ -607,12 +828,13 @@ int coulps_cv_charge_term(const void *s1_bf16, const void *s2_bf16, const float 
   if (nb < 1 || n_q < 0 || (n_q > 0 && (!q_xyz || !q_rho))) return COULPS_EINVAL;
   if (edims[0] < 1 || edims[1] < 1 || edims[2] < 1) return COULPS_EINVAL;
   if (n_q == 0) return COULPS_OK;
-  if (nb > 65535 * 16) return COULPS_EINVAL;
+  if ((nb + kChThreads - 1) / kChThreads > 65535) return COULPS_EINVAL;
   if (scratch_doubles < (int64_t)nb * n_q * 49) return COULPS_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
-  if ((reinterpret_cast<uintptr_t>(s1_bf16) | reinterpret_cast<uintptr_t>(M)) & 15)
+  if ((reinterpret_cast<uintptr_t>(s1_bf16) | reinterpret_cast<uintptr_t>(s2_bf16) |
+       reinterpret_cast<uintptr_t>(M)) & 15)
     return COULPS_EINVAL;
-  cv_charge_partial_kernel<<<dim3(n_q, (nb + 15) / 16, 49), kRedThreads, 0, s>>>(
+  cv_charge_partial_kernel<<<dim3(n_q, (nb + kChThreads - 1) / kChThreads, 49), kChThreads, 0, s>>>(
       (const __nv_bfloat16 *)s1_bf16, (const __nv_bfloat16 *)s2_bf16, M, q_xyz, q_rho, n_q, nb,
       edims[0], edims[1], edims[2], box_layout(interleave, nb, edims[0], edims[1], edims[2]),
       scratch);

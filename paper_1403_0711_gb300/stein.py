@@ -624,13 +624,14 @@ class LocalSteinCV(SteinCV):
                           "coulps_cv_conv3d")
             if out is None:
                 out = torch.empty(n, dtype=torch.float64, device=dev)
-            scratch = torch.empty(3 * self._q.shape[0] * n, dtype=torch.float64, device=dev)
+            scratch = torch.empty(self._q.shape[0] * n, dtype=torch.float64, device=dev)
             ed = (ctypes.c_int32 * 3)(*self.edims)
             rl = (ctypes.c_int32 * 3)(*self.r_lo)
             rh = (ctypes.c_int32 * 3)(*self.r_hi)
             coulps._check(lib.coulps_cv_stein_region(
                 _vp(g16), _vp(s1), _vp(s2), _vp(Aphi), _vp(ev["K"]), n, ed, 1, rl, rh,
-                _vp(scratch), scratch.numel(), _vp(out), sp), "coulps_cv_stein_region")
+                _vp(scratch), scratch.numel(), _vp(out), _vp(ev["err"]), sp),
+                "coulps_cv_stein_region")
             nq = self._cq_xyz.shape[0]
             if nq:
                 cscr = torch.empty(49 * nq * n, dtype=torch.float64, device=dev)
