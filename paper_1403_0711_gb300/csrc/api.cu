@@ -258,6 +258,30 @@ Tile default_pair_tile(const Geometry &g) {
   return Tile{ty, dz};
 }
 
+// SMs of the current device (0 if the query fails).
+int device_sms() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+// Halves a default tile's z slab (not below min_dz) while one launch over all
+// chains would have fewer than `target` CTAs: a single 128^3 chain otherwise
+// gives the pass pair 10 CTAs and the heatbath half-sweep 64 on 152 SMs.
+// Shorter slabs add halo planes (1 for a half-sweep or fused pass, 3 for a
+// pair), so lattices with enough CTAs keep the measured slabs.
+Tile fill_grid(const Geometry &g, Tile t, int target, int min_dz) {
+  if (t.ty < 1 || t.dz < 1) return t;
+  const int64_t rows = (g.Ly + t.ty - 1) / t.ty;
+  while (t.dz > min_dz && rows * ((g.Lz + t.dz - 1) / t.dz) * g.n_chains < target)
+    t.dz = std::max(min_dz, (t.dz + 1) / 2);
+  return t;
+}
+
 int rebuild_pass_maps(coulps_lattice *L) {
   if (!L->fused) return COULPS_OK;
   for (int b = 0; b < 2; ++b) {
@@ -1116,7 +1140,8 @@ int coulps_lattice_create(int Lx, int Ly, int Lz, int n_chains, int precision, u
   coulps_lattice *L = new (std::nothrow) coulps_lattice();
   if (!L) return COULPS_ENOMEM;
   L->g = g;
-  L->tile = default_tile(g);
+  const int sms = device_sms();
+  L->tile = fill_grid(g, default_tile(g), 2 * sms, 4);
   L->seed = seed;
   L->stream = (cudaStream_t)stream;
   L->alloc = g_allocator;
@@ -1166,8 +1191,9 @@ int coulps_set_fused(coulps_lattice_t L, int enable) {
     // row padding and never-written quads stay 0 in both copies
     CK(cudaMemsetAsync(L->field2, 0, fbytes, L->stream));
   }
-  if (L->ptile.ty == 0) L->ptile = default_pass_tile(L->g);
-  if (enable >= 3 && L->qtile.ty == 0) L->qtile = default_pair_tile(L->g);
+  if (L->ptile.ty == 0) L->ptile = fill_grid(L->g, default_pass_tile(L->g), 2 * device_sms(), 4);
+  if (enable >= 3 && L->qtile.ty == 0)
+    L->qtile = fill_grid(L->g, default_pair_tile(L->g), device_sms(), 8);
   L->fused = enable;
   int st = rebuild_maps(L);
   if (st) return st;
