@@ -246,13 +246,17 @@ __global__ void cv_sum_partials_kernel(const double *__restrict__ partials, int 
 // arithmetic).  One MMA of K = 16 per offset e (27 per tile) accumulates
 // N = 48 columns in TMEM; the epilogue adds the parts, dots the sum with
 // s2[q] and writes one FP32 value per (chain, site).  The tile's operand A
-// comes from one TMA box per channel half: the 4 x 3 x 3 sites around the
-// two sites for the 64 chains, [z][y][x][chain][8 channels], so the 64 rows
-// of one site and one offset are 1 KB of consecutive core matrices and the
-// second site's rows follow 1 KB later, one x step on: each offset's A is
-// a descriptor into the box, with no per-offset copy.  (Before: the same
-// sums on the FMA pipes, then a gather of every (row, offset) by 16-byte
-// copies; both ran 55 us per evaluation of 64 chains x 1000 sites.)
+// comes from one TMA box: the 4 x 3 x 3 sites around the two sites for the
+// 64 chains, [z][y][x][chain][16 channels], 32-byte rows in the 32-byte
+// swizzle that TMA writes and the tensor core reads (K-major, 8-row atoms of
+// 256 bytes whose rows 4-7 have their two 16-byte halves exchanged), so the
+// 64 rows of one site and one offset are 2 KB of consecutive atoms and the
+// second site's rows follow 2 KB later, one x step on: each offset's A is a
+// descriptor into the box, with no per-offset copy.  (Before: the same sums
+// on the FMA pipes, then a gather of every (row, offset) by 16-byte copies,
+// both 55 us per evaluation of 64 chains x 1000 sites; then two unswizzled
+// boxes of 8 channels per tile, whose 16-byte pieces the TMA unit issued at
+// about one per 2.7 cycles per SM: 27.5 us.)
 struct RegionRuns {
   int start[3][5], len[3][5], cls[3][5];
   int nrun[3];
@@ -269,8 +273,8 @@ constexpr int kRegionKFloats = 27 * 16 * 16;
 
 constexpr int kRgThreads = 128;               // 4 warps = the 128 TMEM lanes
 constexpr int kRgTPC = 4;                       // tiles per CTA (all of one box)
-constexpr int kRgHalf = 36 * 64 * 16;           // one channel half of a tile's box: 36,864 B
-constexpr int kRgABuf = 2 * kRgHalf;            // both halves: 73,728 B
+constexpr int kRgPos = 64 * 32;                // one block position: 64 chains x 32 B
+constexpr int kRgABuf = 36 * kRgPos;            // a tile's block: 73,728 B
 constexpr int kRgBe = 48 * 16 * 2;              // one offset's B: 48 rows x 16 channels BF16
 constexpr int kRgAOff = 1024;                   // header: mbarriers at 0, TMEM address at 64
 constexpr int kRgBOff = kRgAOff + 2 * kRgABuf;  // two A buffers
@@ -293,7 +297,9 @@ __global__ void __launch_bounds__(kRgThreads)
                          const __nv_bfloat16 *__restrict__ s2, const float *__restrict__ Ktab,
                          const RegionRuns r, double *__restrict__ part, int *err) {
   extern __shared__ unsigned char smem_raw[];
-  unsigned char *smem = align_smem128(smem_raw);
+  // 1 KB aligned: the A buffers' 32-byte swizzle repeats every 256 bytes
+  unsigned char *smem = reinterpret_cast<unsigned char *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem);  // [0..1] A buffers, [2] MMAs
   volatile uint32_t *tmem_slot = reinterpret_cast<volatile uint32_t *>(smem + 64);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 80);
@@ -335,9 +341,8 @@ __global__ void __launch_bounds__(kRgThreads)
     tile_of(t, cg, xs, ys, zs);
     const uint32_t bar = smem_addr(&bars[t & 1]);
     mbar_arrive_expect_tx(bar, kRgABuf);
-    for (int h = 0; h < 2; ++h)
-      tma_load_5d(sA + (uint32_t)((t & 1) * kRgABuf + h * kRgHalf), &tm_s1, 8 * h, 64 * cg,
-                  xs - 1, ys - 1, zs - 1, bar);
+    tma_load_5d(sA + (uint32_t)((t & 1) * kRgABuf), &tm_s1, 0, 64 * cg, xs - 1, ys - 1, zs - 1,
+                bar);
   };
 
   int issued = 0, waited = 0, mma_issued = 0, mma_waited = 0;  // thread 0's counts
@@ -425,7 +430,7 @@ __global__ void __launch_bounds__(kRgThreads)
         for (int e = 0; e < 27; ++e) {
           const int dx = e % 3, dy = (e / 3) % 3, dz = e / 9;  // offset + 1 per axis
           const uint32_t pos = (uint32_t)((dz * 3 + dy) * 4 + dx);  // site 0's x is box x 1
-          mma_bf16(tmem, smem_desc(abuf + pos * 1024, kRgHalf, 128),
+          mma_bf16(tmem, smem_desc_sw32(abuf + pos * kRgPos),
                    smem_desc(sB + (uint32_t)(e * kRgBe), 768, 128), kRgIdesc, e > 0 ? 1u : 0u);
         }
         mma_commit(smem_addr(&bars[2]));
@@ -788,7 +793,7 @@ int coulps_cv_stein_region(const float *g16, const void *s1_bf16, const void *s2
   }
   r.cta_first[r.n_box] = (int)ctas;
   // s1 as a 5D tensor (channel, chain, x, y, z) of E with zero fill outside
-  // it; box (8 channels, 64 chains, 4 x, 3 y, 3 z)
+  // it; box (16 channels, 64 chains, 4 x, 3 y, 3 z), 32-byte swizzle
   auto enc = tensor_map_encoder();
   if (!enc) return COULPS_ECUDA;
   CUtensorMap tm;
@@ -796,14 +801,14 @@ int coulps_cv_stein_region(const float *g16, const void *s1_bf16, const void *s2
                         (cuuint64_t)edims[2]};
   cuuint64_t strides[4] = {(cuuint64_t)r.L.sb * 32, 32, (cuuint64_t)r.L.sy * 32,
                            (cuuint64_t)r.L.sz * 32};
-  cuuint32_t box[5] = {8, 64, 4, 3, 3};
+  cuuint32_t box[5] = {16, 64, 4, 3, 3};
   cuuint32_t estr[5] = {1, 1, 1, 1, 1};
   if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(s1_bf16), dims, strides,
-          box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+          box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return COULPS_ECUDA;
   cudaStream_t s = (cudaStream_t)stream;
-  const int smem = kRgSmem + 128;  // + alignment slack
+  const int smem = kRgSmem + 1024;  // + alignment slack
   static bool configured = false;
   if (!configured) {
     if (cudaFuncSetAttribute(cv_region_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

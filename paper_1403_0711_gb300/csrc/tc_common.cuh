@@ -28,6 +28,14 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
          ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
+// The same for a K-major operand in the 32-byte swizzle (layout type 6 in
+// bits 61-63): 32-byte rows (K = 16 BF16, one MMA step), 8-row atoms of 256
+// bytes (stride byte offset), no leading offset within one atom's width.
+// The start address must be 256-byte aligned (base offset 0).
+__device__ __forceinline__ uint64_t smem_desc_sw32(uint32_t addr) {
+  return smem_desc(addr, 16, 256) | (6ull << 61);
+}
+
 __device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem),
                "r"(ncols)
