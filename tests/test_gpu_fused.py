@@ -68,6 +68,8 @@ def _rel(a, b):
     ((9, 1, 1), "F64", 1, 1, None, 2),
     ((25, 40, 3), "F32", 3, 1, (6, 1), 2),
     ((25, 40, 3), "F32", 1, 5, (6, 1), 1),
+    ((512, 12, 6), "F32", 1, 3, None, 1),   # 64-quad rows: the default 5-row, 512-thread tile
+    ((384, 9, 5), "F64", 1, 3, None, 1),    # 48-quad rows, FP64
 ])
 def test_fused_passes_equal_half_sweeps(cl, stream, L, prec, n_hb, n_or, tile, mode):
     from paper_1403_0711_gb300 import inputs
@@ -158,3 +160,31 @@ def test_fused_is_default_and_costs_a_second_copy(cl, stream):
     with pytest.raises(cl.CoulpsError):
         lat.set_pass_tile(0, 4)
     lat.close()
+
+
+def test_default_tile_shapes(cl, stream):
+    """Default shapes: fused-pass rows of more than 42 quads take up to 512
+    threads (a 512-site row gets 5 rows, not 1); the z slabs of a lattice too
+    small to fill the GPU are halved (not below 4 planes for a half-sweep or a
+    fused pass, 8 for a pair) until one launch has 2 CTAs per SM (1 for a pair),
+    and a lattice that fills it keeps 16 / 32 / 64 planes."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    wide = cl.Lattice((512, 12, 6), n_chains=1, precision=cl.F32, seed=1, stream=stream)
+    assert wide.info()["pass_ty"] == 5
+    wide.close()
+    small = cl.Lattice((64, 64, 64), n_chains=1, precision=cl.F32, seed=1, stream=stream)
+    info = small.info()
+    ty, dz = small.pair_tile()
+    # half-sweep 32 rows x 16 planes -> 2 x 4 CTAs per chain, halved to 4 planes
+    assert (info["ty"], info["dz"]) == (32, 4)
+    # fused pass 29 rows x 32 planes -> 3 x 2 CTAs, halved to 4 planes
+    assert (info["pass_ty"], info["pass_dz"]) == (29, 4)
+    # pair 58 rows x 32 planes -> 2 x 2 CTAs, halved to 8 planes
+    assert (ty, dz) == (58, 8)
+    small.close()
+    chains = 2 * sms  # 2 row tiles x 4 slabs x chains >= 2 x SMs: slabs kept
+    full = cl.Lattice((64, 64, 64), n_chains=chains, precision=cl.F32, seed=1, stream=stream)
+    info = full.info()
+    assert info["dz"] == 16 and info["pass_dz"] == 32
+    full.close()

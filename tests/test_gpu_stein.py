@@ -222,6 +222,40 @@ def test_region_evaluate_matches_oracle(env):
     lat.close()
 
 
+def test_region_evaluate_per_chain_across_chain_groups(env):
+    """The sub-box evaluation of one chain depends on that chain's field alone:
+    a lattice of 70 chains (two 64-chain groups of the region kernel's tiles,
+    the second partial) gives, for chains 0, 63, 64 and 69, bitwise the values
+    of a 4-chain lattice holding the same fields."""
+    torch, coulps, stream = env
+    from paper_1403_0711_gb300 import inputs, stein
+    L = (20, 18, 16)
+    lo, hi = (5, 4, 1), (11, 9, 6)
+    sites, q = inputs.uniform_q(L, 10, seed=8)
+    sites[:3] = [[6, 5, 2], [9, 7, 4], [7, 8, 3]]
+    rho = stein.charge_density(L, sites, q)
+    cv = stein.LocalSteinCV(L, lo, hi, seed=2, scale=0.6, w3_scale=0.1)
+    fields = inputs.gaussian_fields(L, 70, seed=21)
+    big = coulps.Lattice(L, n_chains=70, precision=coulps.F32, seed=15, stream=stream)
+    for k, f in enumerate(fields):
+        big.set_field(k, f)
+    tg_big = cv.evaluate(big, rho)
+    big.sync()
+    tg_big = tg_big.cpu().numpy()
+    pick = [0, 63, 64, 69]
+    small = coulps.Lattice(L, n_chains=len(pick), precision=coulps.F32, seed=15, stream=stream)
+    for j, k in enumerate(pick):
+        small.set_field(j, fields[k])
+    tg_small = cv.evaluate(small, rho)
+    small.sync()
+    tg_small = tg_small.cpu().numpy()
+    assert np.array_equal(tg_small, tg_big[pick]), (tg_small, tg_big[pick])
+    assert np.all(np.isfinite(tg_big)) and np.unique(tg_big).size == 70
+    assert int(cv._ev["err"].item()) == 0  # no bounded wait gave up
+    big.close()
+    small.close()
+
+
 def test_region_pack_matches_field(env):
     """coulps_cv_pack_region: phi, rho, rho phi (BF16) and A phi of the sub-box,
     A phi with the neighbours outside E taken from the full field."""
