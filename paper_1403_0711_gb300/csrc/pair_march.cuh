@@ -39,29 +39,6 @@ __host__ __device__ inline PairLayout pair_layout(int TY, int W, int es, bool a_
   return L;
 }
 
-// A quad (four same-colour sites of a row) as two pairs: sites 0, 1 and 2, 3.
-template <typename T> struct Pair2;
-template <> struct Pair2<float> { using type = float2; };
-template <> struct Pair2<double> { using type = double2; };
-
-template <typename T>
-struct Quad {
-  typename Pair2<T>::type a, b;
-};
-
-__device__ __forceinline__ float2 padd(float2 p, float2 q) { return __fadd2_rn(p, q); }
-__device__ __forceinline__ double2 padd(double2 p, double2 q) {
-  return make_double2(p.x + q.x, p.y + q.y);
-}
-__device__ __forceinline__ float2 pfma(float2 p, float2 q, float2 r) { return __ffma2_rn(p, q, r); }
-__device__ __forceinline__ double2 pfma(double2 p, double2 q, double2 r) {
-  return make_double2(fma(p.x, q.x, r.x), fma(p.y, q.y, r.y));
-}
-__device__ __forceinline__ float2 pneg(float2 p) { return make_float2(-p.x, -p.y); }
-__device__ __forceinline__ double2 pneg(double2 p) { return make_double2(-p.x, -p.y); }
-__device__ __forceinline__ float2 pset(float c) { return make_float2(c, c); }
-__device__ __forceinline__ double2 pset(double c) { return make_double2(c, c); }
-
 template <typename T>
 __device__ __forceinline__ Quad<T> qzero() {
   Quad<T> q;

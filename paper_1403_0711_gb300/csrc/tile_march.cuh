@@ -81,30 +81,54 @@ __device__ __forceinline__ void x_neighbours(bool odd, T e, const T (&C)[4], T (
   xs[3] = odd ? e : C[2];
 }
 
-// The heatbath deviates of one quad's four Philox words: FP32 as two packed
-// pairs under one tail vote of the active lanes (no divergent branch per
-// site; measured 0.156 against 0.159 ms per heatbath half-sweep at 128^3 x 64
-// chains), FP64 word by word.  Bitwise those of Noise<T>::of per word.
-template <typename T> struct QuadNoise1;
-template <> struct QuadNoise1<float> {
-  __device__ __forceinline__ static void of(uint4 w, float (&n)[4]) {
+// A quad (four same-colour sites of a row) as two pairs: sites 0, 1 and 2, 3.
+template <typename T> struct Pair2;
+template <> struct Pair2<float> { using type = float2; };
+template <> struct Pair2<double> { using type = double2; };
+
+template <typename T>
+struct Quad {
+  typename Pair2<T>::type a, b;
+};
+
+__device__ __forceinline__ float2 padd(float2 p, float2 q) { return __fadd2_rn(p, q); }
+__device__ __forceinline__ double2 padd(double2 p, double2 q) {
+  return make_double2(p.x + q.x, p.y + q.y);
+}
+__device__ __forceinline__ float2 pfma(float2 p, float2 q, float2 r) { return __ffma2_rn(p, q, r); }
+__device__ __forceinline__ double2 pfma(double2 p, double2 q, double2 r) {
+  return make_double2(fma(p.x, q.x, r.x), fma(p.y, q.y, r.y));
+}
+__device__ __forceinline__ float2 pneg(float2 p) { return make_float2(-p.x, -p.y); }
+__device__ __forceinline__ double2 pneg(double2 p) { return make_double2(-p.x, -p.y); }
+__device__ __forceinline__ float2 pset(float c) { return make_float2(c, c); }
+__device__ __forceinline__ double2 pset(double c) { return make_double2(c, c); }
+
+// The heatbath deviates of one quad's four Philox words as two pairs (sites
+// 0, 1 and 2, 3): FP32 as two packed pairs under one tail vote of the active
+// lanes (no divergent branch per site; measured 0.156 against 0.159 ms per
+// heatbath half-sweep at 128^3 x 64 chains), FP64 word by word.  Bitwise
+// those of Noise<T>::of per word.
+template <typename T> struct QuadNoise2;
+template <> struct QuadNoise2<float> {
+  __device__ __forceinline__ static void of(uint4 w, float2 (&n)[2]) {
     const uint32_t u[4] = {w.x, w.y, w.z, w.w};
-    float2 o[2];
-    hb_noise_pairs_f32<2>(u, o);
-    n[0] = o[0].x;
-    n[1] = o[0].y;
-    n[2] = o[1].x;
-    n[3] = o[1].y;
+    hb_noise_pairs_f32<2>(u, n);
   }
 };
-template <> struct QuadNoise1<double> {
-  __device__ __forceinline__ static void of(uint4 w, double (&n)[4]) {
-    n[0] = hb_noise_f64(w.x);
-    n[1] = hb_noise_f64(w.y);
-    n[2] = hb_noise_f64(w.z);
-    n[3] = hb_noise_f64(w.w);
+template <> struct QuadNoise2<double> {
+  __device__ __forceinline__ static void of(uint4 w, double2 (&n)[2]) {
+    n[0] = make_double2(hb_noise_f64(w.x), hb_noise_f64(w.y));
+    n[1] = make_double2(hb_noise_f64(w.z), hb_noise_f64(w.w));
   }
 };
+
+__device__ __forceinline__ float2 pair_of(const float (&a)[4], int h) {
+  return make_float2(a[2 * h], a[2 * h + 1]);
+}
+__device__ __forceinline__ double2 pair_of(const double (&a)[4], int h) {
+  return make_double2(a[2 * h], a[2 * h + 1]);
+}
 
 template <typename T> struct Coef;
 template <> struct Coef<float> {
@@ -324,32 +348,41 @@ __device__ bool march_tile(const Job &j, const PhiloxKeys &K, unsigned char *sme
 #pragma unroll
         for (int v = 0; v < V; ++v) {
           if (!qlive[v]) continue;
-          T ym[4], yp[4], xs[4], S[4], u[4];
+          T ym[4], yp[4], xs[4], u[4];
           ld_quad(Pz + 4 * v - W, ym);
           ld_quad(Pz + 4 * v + W, yp);
           const T e = odd ? (v + 1 < V ? C[v + 1 < V ? v + 1 : v][0] : edge)
                           : (v > 0 ? C[v > 0 ? v - 1 : v][3] : edge);
           x_neighbours(odd, e, C[v], xs);
+          // the sums and the update on packed pairs of sites (FP32: one
+          // instruction per pair, each lane rounded as the scalar form)
+          using P2 = typename Pair2<T>::type;
+          P2 S2[2], u2[2];
 #pragma unroll
-          for (int i = 0; i < 4; ++i)
-            S[i] = ((M[v][i] + P[v][i]) + (ym[i] + yp[i])) + (C[v][i] + xs[i]);
+          for (int h = 0; h < 2; ++h)
+            S2[h] = padd(padd(padd(pair_of(M[v], h), pair_of(P[v], h)),
+                              padd(pair_of(ym, h), pair_of(yp, h))),
+                         padd(pair_of(C[v], h), pair_of(xs, h)));
           if (!OR) {
             const uint32_t z = (uint32_t)(j.z0() + k - 1);
             const uint32_t quad =
                 (z * (uint32_t)j.Ly() + (uint32_t)y) * (uint32_t)j.Wq() + (uint32_t)(qx + v);
             const uint4 w = philox4x32_10(make_uint4(quad, j.pass(), j.rng_id(), (uint32_t)c), K);
-            T n4[4];
-            QuadNoise1<T>::of(w, n4);
-            u[0] = fma(S[0], Coef<T>::sixth, n4[0]);
-            u[1] = fma(S[1], Coef<T>::sixth, n4[1]);
-            u[2] = fma(S[2], Coef<T>::sixth, n4[2]);
-            u[3] = fma(S[3], Coef<T>::sixth, n4[3]);
+            P2 n2[2];
+            QuadNoise2<T>::of(w, n2);
+            u2[0] = pfma(S2[0], pset(Coef<T>::sixth), n2[0]);
+            u2[1] = pfma(S2[1], pset(Coef<T>::sixth), n2[1]);
           } else {
             T old[4];
             ld_quad(own_slot(slot_of(k)) + orow + 4 * v, old);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) u[i] = fma(S[i], Coef<T>::third, -old[i]);
+            for (int h = 0; h < 2; ++h)
+              u2[h] = pfma(S2[h], pset(Coef<T>::third), pneg(pair_of(old, h)));
           }
+          u[0] = u2[0].x;
+          u[1] = u2[0].y;
+          u[2] = u2[1].x;
+          u[3] = u2[1].y;
           const uint32_t pm = par ? pad1[v] : pad0[v];
           if (pm) {
 #pragma unroll
