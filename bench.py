@@ -187,10 +187,10 @@ def kernel_src_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
-    None if it holds another kernel or the kernel sources changed since it
-    was taken."""
+def profiled_traffic(kernel, key="dram_bytes_per_launch_full"):
+    """DRAM bytes per launch of `kernel` (or another per-launch figure, `key`)
+    from the committed ncu summary, or None if it holds another kernel or the
+    kernel sources changed since it was taken."""
     path = PROFILE_TRAFFIC.get(kernel)
     if path is None or not path.exists():
         return None
@@ -202,7 +202,7 @@ def profiled_traffic(kernel):
     if kv.get("kernel_src_sha256_16") != kernel_src_hash() or kv.get("kernel") != kernel:
         return None
     try:
-        return float(kv["dram_bytes_per_launch_full"])
+        return float(kv[key])
     except (KeyError, ValueError):
         return None
 
@@ -537,6 +537,31 @@ def run_ours(args):
                      "peak_kind": f"{peak_kind} (burst copy)",
                      "timing": f"CUDA events around every launch, one stream, {n_rf} compound "
                                "sweeps after the timed region"}, **dom)
+    # every sweep kernel of the step against both of its limits: HBM (algorithmic
+    # bytes / launch time, of the measured copy bandwidth) and instruction issue
+    # (warp instructions of the committed ncu capture / launch time, of the
+    # GPU's issue capacity at the clock sampled during the timed region: SMs x 4
+    # schedulers x 1 warp instruction per cycle)
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = clk.get("sm_mhz") if isinstance(clk, dict) and clk.get("sm_mhz") else 2070.0
+    by_kernel = {}
+    for k, (kname, kbytes) in kinds.items():
+        if not kt[k + "_n"]:
+            continue
+        kms = kt[k + "_ms"] / kt[k + "_n"]
+        kach = kbytes / (kms / 1e3) / 1e9
+        e = {"kernel": kname, "avg_launch_ms": kms, "algorithmic_bytes_per_launch": kbytes,
+             "achieved_GBps": kach, "hbm_frac": kach / peak,
+             "share_of_sweep_kernel_time": kt[k + "_ms"] / total_ms if total_ms else None,
+             "traffic": profiled_traffic(kname)}
+        winst = profiled_traffic(kname, "warp_instructions_per_launch_full")
+        if winst:
+            e["warp_instructions_per_launch"] = winst
+            e["issue_frac"] = winst / (kms / 1e3) / (sms * 4 * mhz * 1e6)
+        by_kernel[k] = e
+    roofline["by_kernel"] = by_kernel
+    roofline["issue_peak"] = {"warp_instructions_per_s": sms * 4 * mhz * 1e6, "sms": sms,
+                              "sm_mhz": mhz}
     sweep_launches = sum(kt[k + "_n"] for k in kinds) / n_rf  # all chains, one stream
 
     # spread: the step loop timed again, --repeats times, right after the
