@@ -612,6 +612,19 @@ int coulps_cv_stein_sum(const float *g16, const float *D, const void *s2_bf16, c
                         const void *s1_bf16, const float *dK, int nb, int Lx, int Ly, int Lz,
                         double *scratch, int64_t scratch_doubles, double *out, void *stream);
 
+/* coulps_cv_region_pack: the class kernels of coulps_cv_stein_region in the
+ * form its tensor-core kernel reads them, formed once per set of weights.
+ * Ktab (device, 216 x 27 x 16 x 16 floats, 16-byte aligned:
+ * K[class][e][c2][c1]) holds one divergence kernel per class ix + 6 iy + 36 iz
+ * (see below); kpack (device, 216 x 41472 bytes, 16-byte aligned) receives,
+ * per class, K split into three BF16 parts K = hi + mid + lo (each part the
+ * BF16 rounding of what the parts before it leave; together they hold K's
+ * FP32 value), stored as the tensor core's K-major operand without swizzle:
+ * the byte of row n = 16 p + c2 (part p), channel c1 and offset e at
+ * e 1536 + (n / 8) 128 + (c1 / 8) 768 + (n % 8) 16 + (c1 % 8) 2.
+ * Asynchronous on stream.  Errors: EINVAL, ECUDA. */
+int coulps_cv_region_pack(const float *Ktab, void *kpack, void *stream);
+
 /* coulps_cv_stein_region: the Stein term of a net g that is kept inside the
  * box R = [lo, hi) and set to 0 elsewhere (still a smooth field of phi, so the
  * term keeps mean 0), evaluated on a sub-box E (edims = x, y, z sizes) that
@@ -619,22 +632,21 @@ int coulps_cv_stein_sum(const float *g16, const float *D, const void *s2_bf16, c
  *   out[b] = sum_{q in R+1} sum_c2 s2[c2, q] sum_{c1, e} K_q[c2][c1][e] s1[c1, q + e]
  *            - sum_{x in R} g_x Aphi_x
  * where K_q is the divergence kernel summed over the offsets f of the last
- * layer with q - f inside R (per axis a subset of {-1, 0, 1}).  Ktab (device,
- * 216 x 27 x 16 x 16 floats, 16-byte aligned: K[class][e][c2][c1]) holds one
- * K per class ix + 6 iy + 36 iz, the
- * per-axis index of the allowed set {-1} 0, {0} 1, {-1, 0} 2, {1} 3,
- * {0, 1} 4, {-1, 0, 1} 5 (f = -1 is bit 0).  g16 [b][E][16] FP32 (channel 0
+ * layer with q - f inside R (per axis a subset of {-1, 0, 1}).  One K per
+ * class ix + 6 iy + 36 iz, the per-axis index of the allowed set {-1} 0,
+ * {0} 1, {-1, 0} 2, {1} 3, {0, 1} 4, {-1, 0, 1} 5 (f = -1 is bit 0), given as
+ * kpack, the output of coulps_cv_region_pack.  g16 [b][E][16] FP32 (channel 0
  * read), s1, s2 BF16 [b][E][16] (16-byte aligned), Aphi [b][E], all in the
  * layout `interleave` of coulps_cv_pack_region (gutters are not read).  The
- * sums over c1 and e run on the tensor cores (tcgen05, BF16 operands with K
- * split into three BF16 parts that hold its FP32 value, FP32 accumulation):
- * one FP32 value per (chain, site); the sums over sites are FP64 in a fixed
- * order.  scratch >= nb * |(R + 1) within E| doubles; out device nb doubles
- * (overwritten); err: device int, as for coulps_cv_conv3d (a bounded wait for
- * the tensor cores that gave up ORs bit 1 into it and leaves out
- * unspecified).  Asynchronous.  Errors: EINVAL, ECUDA. */
+ * sums over c1 and e run on the tensor cores (tcgen05, BF16 operands, K in its
+ * three parts, FP32 accumulation): one FP32 value per (chain, site); the sums
+ * over sites are FP64 in a fixed order.  scratch >= nb * |(R + 1) within E|
+ * doubles; out device nb doubles (overwritten); err: device int, as for
+ * coulps_cv_conv3d (a bounded wait for the tensor cores or their copies that
+ * gave up ORs bit 1 into it and leaves out unspecified).  Asynchronous.
+ * Errors: EINVAL, ECUDA. */
 int coulps_cv_stein_region(const float *g16, const void *s1_bf16, const void *s2_bf16,
-                           const float *Aphi, const float *Ktab, int nb, const int32_t *edims,
+                           const float *Aphi, const void *kpack, int nb, const int32_t *edims,
                            int interleave, const int32_t *lo, const int32_t *hi, double *scratch,
                            int64_t scratch_doubles, double *out, int *err, void *stream);
 

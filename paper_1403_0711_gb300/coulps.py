@@ -38,7 +38,8 @@ EXPORTS = (
     "coulps_batch_field_get", "coulps_cv_pack_weights", "coulps_cv_conv3d",
     "coulps_cv_conv3d_wgrad", "coulps_cv_pack_field", "coulps_cv_activate", "coulps_cv_stein_sum",
     "coulps_set_schedule", "coulps_cv_conv3d_tanh", "coulps_cv_pack_region",
-    "coulps_cv_stein_region", "coulps_cv_record", "coulps_cv_chain_stats", "coulps_cv_estimate",
+    "coulps_cv_stein_region", "coulps_cv_region_pack", "coulps_cv_record",
+    "coulps_cv_chain_stats", "coulps_cv_estimate",
     "coulps_cv_reset", "coulps_cv_charge_term", "coulps_set_fused", "coulps_set_pass_tile",
     "coulps_measure_sets", "coulps_run_sets", "coulps_gcv_create", "coulps_gcv_destroy",
     "coulps_gcv_info", "coulps_gcv_h", "coulps_gcv_eval", "coulps_gcv_run",
@@ -149,6 +150,7 @@ def load(path: str | Path | None = None):
         "coulps_cv_conv3d_tanh": (i32, [vp, vp, vp, vp, vp, i32, i32, i32, i32, i32, vp, vp]),
         "coulps_cv_pack_region": (i32, [vp, vp, P(ctypes.c_int32), P(ctypes.c_int32), i32, vp,
                                         vp]),
+        "coulps_cv_region_pack": (i32, [vp, vp, vp]),
         "coulps_cv_stein_region": (i32, [vp, vp, vp, vp, vp, i32, P(ctypes.c_int32), i32,
                                          P(ctypes.c_int32), P(ctypes.c_int32), vp, i64, vp, vp,
                                          vp]),

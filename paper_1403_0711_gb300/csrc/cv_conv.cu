@@ -69,16 +69,6 @@ constexpr int kCvSmem = kWOff + kWBytes;
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) |
                             ((128u >> 4) << 24);
 
-// 1D bulk copy global -> shared (16-byte aligned, size a multiple of 16),
-// completion signalled on `bar`.
-__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes,
-                                          uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-          "r"(dst),
-      "l"(src), "r"(bytes), "r"(bar)
-      : "memory");
-}
 
 
 struct CvConvArgs {

@@ -284,23 +284,61 @@ constexpr int kRgSmem = kRgBOff + 27 * kRgBe;   // 189,952 bytes
 constexpr uint32_t kRgIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((48u >> 3) << 17) |
                               ((128u >> 4) << 24);
 
+// The class kernels' B operands, formed once per set of weights: for class
+// cls, kRgBBytes bytes laid out as the region kernel keeps them in shared
+// memory (K-major no-swizzle core matrices: element (n, c1) of offset e at
+// e kRgBe + (n / 8) 128 + (c1 / 8) 768 + (n % 8) 16 + (c1 % 8) 2, row
+// n = 16 p + c2 holding part p of K[cls][e][c2][c1]).  One CTA per class,
+// 8 channels c1 per thread and unit.
+constexpr int kRgBBytes = 27 * kRgBe;  // 41,472
+
+__global__ void __launch_bounds__(256)
+    cv_region_pack_kernel(const float *__restrict__ Ktab, unsigned char *__restrict__ kpack) {
+  const int cls = blockIdx.x;
+  const float *kc = Ktab + (size_t)cls * kRegionKFloats;
+  unsigned char *dst = kpack + (size_t)cls * kRgBBytes;
+  for (int u = threadIdx.x; u < 27 * 16 * 2; u += blockDim.x) {
+    const int e = u >> 5, c2 = (u >> 1) & 15, hh = u & 1;
+    const float4 *src = reinterpret_cast<const float4 *>(kc + e * 256 + c2 * 16 + 8 * hh);
+    const float4 f0 = src[0], f1 = src[1];
+    const float v[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
+    __align__(16) __nv_bfloat16 pt[3][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      float x = v[i];
+#pragma unroll
+      for (int p = 0; p < 3; ++p) {
+        pt[p][i] = __float2bfloat16_rn(x);
+        x -= __bfloat162float(pt[p][i]);  // exact: x minus its own rounding
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+      const int n = 16 * p + c2;
+      *reinterpret_cast<uint4 *>(dst + e * kRgBe + (n >> 3) * 128 + hh * 768 + (n & 7) * 16) =
+          *reinterpret_cast<const uint4 *>(pt[p]);
+    }
+  }
+}
+
 // One CTA runs up to kRgTPC tiles of one class box.  Shared memory: the
-// class's B (staged once, K-major no-swizzle core matrices: element (n, c1)
-// of offset e at kRgBOff + e kRgBe + (n / 8) 128 + (c1 / 8) 768 + (n % 8) 16
-// + (c1 % 8) 2) and two A buffers, filled by TMA one tile ahead.  Tile t's
+// class's B (one bulk copy of its packed operand, see cv_region_pack_kernel;
+// staging and splitting the FP32 kernel in every CTA cost it 27 KB of loads
+// before its first tile) and two A buffers, filled by TMA one tile ahead.  Tile t's
 // 27 MMAs read buffer t % 2; once they have completed, that buffer is
 // refilled with tile t + 2 while the warps read the accumulator.  Every wait
 // is bounded: on a timeout the CTA sets the error word, writes nothing more,
 // waits (bounded) for its copies and MMAs in flight and frees its TMEM.
 __global__ void __launch_bounds__(kRgThreads)
     cv_region_mma_kernel(const __grid_constant__ CUtensorMap tm_s1,
-                         const __nv_bfloat16 *__restrict__ s2, const float *__restrict__ Ktab,
-                         const RegionRuns r, double *__restrict__ part, int *err) {
+                         const __nv_bfloat16 *__restrict__ s2,
+                         const unsigned char *__restrict__ kpack, const RegionRuns r,
+                         double *__restrict__ part, int *err) {
   extern __shared__ unsigned char smem_raw[];
   // 1 KB aligned: the A buffers' 32-byte swizzle repeats every 256 bytes
   unsigned char *smem = reinterpret_cast<unsigned char *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem);  // [0..1] A buffers, [2] MMAs
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem);  // [0..1] A buffers, [2] MMAs, [3] B
   volatile uint32_t *tmem_slot = reinterpret_cast<volatile uint32_t *>(smem + 64);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 80);
   const uint32_t sA = smem_addr(smem + kRgAOff), sB = smem_addr(smem + kRgBOff);
@@ -346,11 +384,14 @@ __global__ void __launch_bounds__(kRgThreads)
   };
 
   int issued = 0, waited = 0, mma_issued = 0, mma_waited = 0;  // thread 0's counts
+  bool b_ok = false;  // thread 0: the class's B has landed
   if (tid == 0) {
     prefetch_tensormap(&tm_s1);
-    for (int i = 0; i < 3; ++i) mbar_init(smem_addr(&bars[i]), 1);
+    for (int i = 0; i < 4; ++i) mbar_init(smem_addr(&bars[i]), 1);
     *abort_flag = 0;
     fence_mbar_init();
+    mbar_arrive_expect_tx(smem_addr(&bars[3]), kRgBBytes);
+    bulk_load(sB, kpack + (size_t)cls * kRgBBytes, kRgBBytes, smem_addr(&bars[3]));
     for (; issued < 2 && issued < nt; ++issued) issue(issued);
   }
   if (warp == 0) {
@@ -358,47 +399,6 @@ __global__ void __launch_bounds__(kRgThreads)
     tmem_relinquish();
   }
 
-  // B: the class kernel in three BF16 parts, 8 channels c1 per unit; every
-  // unit's loads are issued before any is used
-  {
-    const float *kc = Ktab + (size_t)cls * kRegionKFloats;
-    float4 f[7][2];
-#pragma unroll
-    for (int k = 0; k < 7; ++k) {
-      const int u = tid + kRgThreads * k;
-      if (u < 27 * 16 * 2) {
-        const float4 *src = reinterpret_cast<const float4 *>(kc + (u >> 5) * 256 + ((u >> 1) & 15) * 16 + 8 * (u & 1));
-        f[k][0] = src[0];
-        f[k][1] = src[1];
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < 7; ++k) {
-      const int u = tid + kRgThreads * k;
-      if (u >= 27 * 16 * 2) continue;
-      const int e = u >> 5, c2 = (u >> 1) & 15, hh = u & 1;
-      const float v[8] = {f[k][0].x, f[k][0].y, f[k][0].z, f[k][0].w,
-                          f[k][1].x, f[k][1].y, f[k][1].z, f[k][1].w};
-      __align__(16) __nv_bfloat16 pt[3][8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        float x = v[i];
-#pragma unroll
-        for (int p = 0; p < 3; ++p) {
-          pt[p][i] = __float2bfloat16_rn(x);
-          x -= __bfloat162float(pt[p][i]);  // exact: x minus its own rounding
-        }
-      }
-#pragma unroll
-      for (int p = 0; p < 3; ++p) {
-        const int n = 16 * p + c2;
-        *reinterpret_cast<uint4 *>(smem + kRgBOff + e * kRgBe + (n >> 3) * 128 + hh * 768 + (n & 7) * 16) =
-            *reinterpret_cast<const uint4 *>(pt[p]);
-      }
-    }
-  }
-  // the B stores are made visible to the tensor core's async proxy
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
@@ -423,8 +423,9 @@ __global__ void __launch_bounds__(kRgThreads)
     bool ok = true;
     if (tid == 0) {
       ok = mbar_wait_bounded(smem_addr(&bars[t & 1]), (uint32_t)((t >> 1) & 1));
+      if (ok) ++waited;
+      if (ok && !b_ok) ok = b_ok = mbar_wait_bounded(smem_addr(&bars[3]), 0);
       if (ok) {
-        ++waited;
         fence_after_sync();
         const uint32_t abuf = sA + (uint32_t)((t & 1) * kRgABuf);
         for (int e = 0; e < 27; ++e) {
@@ -480,6 +481,7 @@ __global__ void __launch_bounds__(kRgThreads)
   }
   if (aborted && tid == 0) {
     // leave no copy or MMA in flight (bounded waits, in order)
+    if (!b_ok) mbar_wait_bounded(smem_addr(&bars[3]), 0);
     for (int k = waited; k < issued; ++k)
       if (!mbar_wait_bounded(smem_addr(&bars[k & 1]), (uint32_t)((k >> 1) & 1))) break;
     for (int k = mma_waited; k < mma_issued; ++k)
@@ -754,17 +756,17 @@ int coulps_cv_stein_sum(const float *g16, const float *D, const void *s2_bf16, c
 }
 
 int coulps_cv_stein_region(const float *g16, const void *s1_bf16, const void *s2_bf16,
-                           const float *Aphi, const float *Ktab, int nb, const int32_t *edims,
+                           const float *Aphi, const void *kpack, int nb, const int32_t *edims,
                            int interleave, const int32_t *lo, const int32_t *hi, double *scratch,
                            int64_t scratch_doubles, double *out, int *err, void *stream) {
-  if (!g16 || !s1_bf16 || !s2_bf16 || !Aphi || !Ktab || !edims || !lo || !hi || !scratch || !out ||
+  if (!g16 || !s1_bf16 || !s2_bf16 || !Aphi || !kpack || !edims || !lo || !hi || !scratch || !out ||
       !err)
     return COULPS_EINVAL;
   if (nb < 1) return COULPS_EINVAL;
   for (int k = 0; k < 3; ++k)
     if (edims[k] < 1 || lo[k] < 0 || hi[k] > edims[k] || lo[k] >= hi[k]) return COULPS_EINVAL;
   if ((reinterpret_cast<uintptr_t>(s1_bf16) | reinterpret_cast<uintptr_t>(s2_bf16) |
-       reinterpret_cast<uintptr_t>(Ktab)) & 15)
+       reinterpret_cast<uintptr_t>(kpack)) & 15)
     return COULPS_EINVAL;
   RegionRuns r{};
   r.ex = edims[0]; r.ey = edims[1]; r.ez = edims[2];
@@ -819,9 +821,18 @@ int coulps_cv_stein_region(const float *g16, const void *s1_bf16, const void *s2
     configured = true;
   }
   cv_region_mma_kernel<<<(unsigned)ctas, kRgThreads, smem, s>>>(
-      tm, (const __nv_bfloat16 *)s2_bf16, Ktab, r, scratch, err);
+      tm, (const __nv_bfloat16 *)s2_bf16, (const unsigned char *)kpack, r, scratch, err);
   cv_region_finish_kernel<<<nb, kRedThreads, 0, s>>>(scratch, (int)nq, g16, Aphi, r.L, lo[0],
                                                      lo[1], lo[2], hi[0], hi[1], hi[2], out);
+  return cudaGetLastError() == cudaSuccess ? COULPS_OK : COULPS_ECUDA;
+}
+
+int coulps_cv_region_pack(const float *Ktab, void *kpack, void *stream) {
+  if (!Ktab || !kpack) return COULPS_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(Ktab) | reinterpret_cast<uintptr_t>(kpack)) & 15)
+    return COULPS_EINVAL;
+  cv_region_pack_kernel<<<216, 256, 0, (cudaStream_t)stream>>>(
+      Ktab, reinterpret_cast<unsigned char *>(kpack));
   return cudaGetLastError() == cudaSuccess ? COULPS_OK : COULPS_ECUDA;
 }
 

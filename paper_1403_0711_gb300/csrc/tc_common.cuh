@@ -8,6 +8,17 @@
 
 namespace coulps {
 
+// 1D bulk copy global -> shared (16-byte aligned, size a multiple of 16),
+// completion signalled on `bar`.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes,
+                                          uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
 // 5D tiled TMA load global -> shared, completion signalled on `bar`.  The
 // innermost coordinate c0 times the element size must be a multiple of 16
 // bytes (every caller passes 0 or 8 BF16 channels).

@@ -582,11 +582,20 @@ class LocalSteinCV(SteinCV):
                 "w3": pack_weights(self._w3p()),
                 "b1": self.b1.detach().float().contiguous(), "b2": self.b2.detach().float().contiguous(),
                 "b3": self._b3p().detach().float().contiguous(),
-                # per class [e][c2][c1], the order the region kernel stages
+                # per class [e][c2][c1], packed below for the region kernel
                 "K": self.region_kernels().detach().float().permute(0, 3, 1, 2).contiguous(),
                 "M": charge_matrix(*self.weights()).detach().float().contiguous(),
                 "err": torch.zeros(1, dtype=torch.int32, device=dev),
             }
+            # the class kernels as the region kernel's tensor-core operand
+            # (three BF16 parts each), formed once per set of weights
+            self._ev["Kpack"] = torch.empty(216 * 41472, dtype=torch.uint8, device=dev)
+            coulps._check(coulps.load().coulps_cv_region_pack(
+                _vp(self._ev["K"]), _vp(self._ev["Kpack"]),
+                ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)),
+                "coulps_cv_region_pack")
+            # evaluate runs on the lattice's stream, which may be another one
+            torch.cuda.current_stream(dev).synchronize()
 
     # -- evaluation with library kernels only, on the lattice's stream
     @torch.no_grad()
@@ -629,7 +638,7 @@ class LocalSteinCV(SteinCV):
             rl = (ctypes.c_int32 * 3)(*self.r_lo)
             rh = (ctypes.c_int32 * 3)(*self.r_hi)
             coulps._check(lib.coulps_cv_stein_region(
-                _vp(g16), _vp(s1), _vp(s2), _vp(Aphi), _vp(ev["K"]), n, ed, 1, rl, rh,
+                _vp(g16), _vp(s1), _vp(s2), _vp(Aphi), _vp(ev["Kpack"]), n, ed, 1, rl, rh,
                 _vp(scratch), scratch.numel(), _vp(out), _vp(ev["err"]), sp),
                 "coulps_cv_stein_region")
             nq = self._cq_xyz.shape[0]
