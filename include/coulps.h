@@ -635,17 +635,23 @@ int coulps_cv_region_pack(const float *Ktab, void *kpack, void *stream);
  * layer with q - f inside R (per axis a subset of {-1, 0, 1}).  One K per
  * class ix + 6 iy + 36 iz, the per-axis index of the allowed set {-1} 0,
  * {0} 1, {-1, 0} 2, {1} 3, {0, 1} 4, {-1, 0, 1} 5 (f = -1 is bit 0), given as
- * kpack, the output of coulps_cv_region_pack.  g16 [b][E][16] FP32 (channel 0
- * read), s1, s2 BF16 [b][E][16] (16-byte aligned), Aphi [b][E], all in the
- * layout `interleave` of coulps_cv_pack_region (gutters are not read).  The
+ * kpack, the output of coulps_cv_region_pack.  g_x, the net's output, is
+ * formed at the sites of R from the second layer's activations a2 (BF16
+ * [b][E][16], 16-byte aligned, 0 outside E as in the convs' zero padding)
+ * and the last layer: w3g (device, 27 x 16 floats [o][ci], o = 9 kz + 3 ky +
+ * kx, the weights of PyTorch layout W3[0][ci][kz][ky][kx], as the tensor-core
+ * convs use them: BF16 values) and bias b3g, summed in FP32.  s1, s2 BF16
+ * [b][E][16] (16-byte aligned), Aphi [b][E], all in the layout `interleave`
+ * of coulps_cv_pack_region (gutters are not read).  The
  * sums over c1 and e run on the tensor cores (tcgen05, BF16 operands, K in its
  * three parts, FP32 accumulation): one FP32 value per (chain, site); the sums
- * over sites are FP64 in a fixed order.  scratch >= nb * |(R + 1) within E|
- * doubles; out device nb doubles (overwritten); err: device int, as for
+ * over sites are FP64 in a fixed order.  scratch >= nb * (|(R + 1) within E|
+ * + |R|) doubles; out device nb doubles (overwritten); err: device int, as for
  * coulps_cv_conv3d (a bounded wait for the tensor cores or their copies that
  * gave up ORs bit 1 into it and leaves out unspecified).  Asynchronous.
  * Errors: EINVAL, ECUDA. */
-int coulps_cv_stein_region(const float *g16, const void *s1_bf16, const void *s2_bf16,
+int coulps_cv_stein_region(const void *a2_bf16, const float *w3g, float b3g,
+                           const void *s1_bf16, const void *s2_bf16,
                            const float *Aphi, const void *kpack, int nb, const int32_t *edims,
                            int interleave, const int32_t *lo, const int32_t *hi, double *scratch,
                            int64_t scratch_doubles, double *out, int *err, void *stream);

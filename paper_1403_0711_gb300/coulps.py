@@ -151,9 +151,9 @@ def load(path: str | Path | None = None):
         "coulps_cv_pack_region": (i32, [vp, vp, P(ctypes.c_int32), P(ctypes.c_int32), i32, vp,
                                         vp]),
         "coulps_cv_region_pack": (i32, [vp, vp, vp]),
-        "coulps_cv_stein_region": (i32, [vp, vp, vp, vp, vp, i32, P(ctypes.c_int32), i32,
-                                         P(ctypes.c_int32), P(ctypes.c_int32), vp, i64, vp, vp,
-                                         vp]),
+        "coulps_cv_stein_region": (i32, [vp, vp, ctypes.c_float, vp, vp, vp, vp, i32,
+                                         P(ctypes.c_int32), i32, P(ctypes.c_int32),
+                                         P(ctypes.c_int32), vp, i64, vp, vp, vp]),
         "coulps_cv_record": (i32, [vp, vp, f64]),
         "coulps_cv_chain_stats": (i32, [vp, P(f64), i64]),
         "coulps_cv_estimate": (i32, [vp, P(f64), P(f64), P(f64), P(i64)]),

@@ -492,22 +492,72 @@ __global__ void __launch_bounds__(kRgThreads)
   if (warp == 0) tmem_dealloc(tmem, 64);
 }
 
-// out[b] = sum_q part[b][q] - sum_{x in R} g_x (A phi)_x, one CTA per chain
-// (part holds nq partials per chain)
+// g_x (A phi)_x for every chain and site x of R, one thread each, into
+// gpart[chain][k] (k the site's index in R, x fastest).  g_x, the net's
+// output, is formed from the second layer's activations a2 and the last
+// layer's weights (w3g [o][ci], 27 x 16 floats holding BF16 values, o = 9 kz
+// + 3 ky + kx for the offset (kx, ky, kz) - 1, and bias b3g), summed in FP32:
+// only the sites of R need it.  Their neighbours lie in E, or outside the
+// lattice where E is clipped by its faces (zero padding, as in the convs).
+// (A tensor-core conv of all of E for the one output channel cost 20 us per
+// evaluation of 64 chains.)
 __global__ void __launch_bounds__(kRedThreads)
-    cv_region_finish_kernel(const double *__restrict__ part, int nq, const float *__restrict__ g16,
-                            const float *__restrict__ Aphi, BoxLayout L, int lox, int loy,
-                            int loz, int hix, int hiy, int hiz, double *__restrict__ out) {
+    cv_region_g_kernel(const __nv_bfloat16 *__restrict__ a2, const float *__restrict__ w3g,
+                       float b3g, const float *__restrict__ Aphi, BoxLayout L, int nb, int ex,
+                       int ey, int ez, int lox, int loy, int loz, int nrx, int nry, int nrz,
+                       double *__restrict__ gpart) {
+  __shared__ __align__(16) float w[27 * 16];
+  for (int i = threadIdx.x; i < 27 * 16; i += kRedThreads) w[i] = w3g[i];
+  __syncthreads();
+  const int nr = nrx * nry * nrz;
+  const int64_t i = (int64_t)blockIdx.x * kRedThreads + threadIdx.x;
+  if (i >= (int64_t)nr * nb) return;
+  const int chain = (int)(i / nr), k = (int)(i % nr);
+  const int x = lox + k % nrx, y = loy + (k / nrx) % nry, z = loz + k / (nrx * nry);
+  float g = b3g;
+#pragma unroll
+  for (int dz = 0; dz < 3; ++dz) {
+    // the nine rows of one z plane: loads first, then the FMAs
+    uint4 u[9][2];
+#pragma unroll
+    for (int o9 = 0; o9 < 9; ++o9) {
+      const int xx = x + o9 % 3 - 1, yy = y + o9 / 3 - 1, zz = z + dz - 1;
+      const bool in = xx >= 0 && yy >= 0 && zz >= 0 && xx < ex && yy < ey && zz < ez;
+      u[o9][0] = u[o9][1] = make_uint4(0, 0, 0, 0);
+      if (in) {
+        const uint4 *ap = reinterpret_cast<const uint4 *>(
+            a2 + (chain * L.sb + zz * L.sz + yy * L.sy + xx) * 16);
+        u[o9][0] = ap[0];
+        u[o9][1] = ap[1];
+      }
+    }
+#pragma unroll
+    for (int o9 = 0; o9 < 9; ++o9) {
+      const __nv_bfloat162 *h0 = reinterpret_cast<const __nv_bfloat162 *>(&u[o9][0]);
+      const __nv_bfloat162 *h1 = reinterpret_cast<const __nv_bfloat162 *>(&u[o9][1]);
+      const float *wo = w + (9 * dz + o9) * 16;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float2 p = __bfloat1622float2(h0[j]), q = __bfloat1622float2(h1[j]);
+        g = fmaf(wo[2 * j], p.x, g);
+        g = fmaf(wo[2 * j + 1], p.y, g);
+        g = fmaf(wo[8 + 2 * j], q.x, g);
+        g = fmaf(wo[9 + 2 * j], q.y, g);
+      }
+    }
+  }
+  gpart[i] = (double)g * (double)Aphi[chain * L.sb + z * L.sz + y * L.sy + x];
+}
+
+// out[b] = sum_q part[b][q] - sum_k gpart[b][k], one CTA per chain (part
+// holds nq partials per chain, gpart nr), fixed order.
+__global__ void __launch_bounds__(kRedThreads)
+    cv_region_finish_kernel(const double *__restrict__ part, int nq,
+                            const double *__restrict__ gpart, int nr, double *__restrict__ out) {
   const int chain = blockIdx.x;
   double acc = 0.0;
   for (int k = threadIdx.x; k < nq; k += kRedThreads) acc += part[(size_t)chain * nq + k];
-  const int nrx = hix - lox, nry = hiy - loy, nrz = hiz - loz;
-  const int nr = nrx * nry * nrz;
-  for (int k = threadIdx.x; k < nr; k += kRedThreads) {
-    const int x = lox + k % nrx, y = loy + (k / nrx) % nry, z = loz + k / (nrx * nry);
-    const int64_t o = chain * L.sb + z * L.sz + y * L.sy + x;
-    acc -= (double)g16[o * 16] * (double)Aphi[o];
-  }
+  for (int k = threadIdx.x; k < nr; k += kRedThreads) acc -= gpart[(size_t)chain * nr + k];
   block_sum_to(acc, out + chain);
 }
 
@@ -755,18 +805,20 @@ int coulps_cv_stein_sum(const float *g16, const float *D, const void *s2_bf16, c
   return cudaGetLastError() == cudaSuccess ? COULPS_OK : COULPS_ECUDA;
 }
 
-int coulps_cv_stein_region(const float *g16, const void *s1_bf16, const void *s2_bf16,
+int coulps_cv_stein_region(const void *a2_bf16, const float *w3g, float b3g,
+                           const void *s1_bf16, const void *s2_bf16,
                            const float *Aphi, const void *kpack, int nb, const int32_t *edims,
                            int interleave, const int32_t *lo, const int32_t *hi, double *scratch,
                            int64_t scratch_doubles, double *out, int *err, void *stream) {
-  if (!g16 || !s1_bf16 || !s2_bf16 || !Aphi || !kpack || !edims || !lo || !hi || !scratch || !out ||
+  if (!a2_bf16 || !w3g || !s1_bf16 || !s2_bf16 || !Aphi || !kpack || !edims || !lo || !hi ||
+      !scratch || !out ||
       !err)
     return COULPS_EINVAL;
   if (nb < 1) return COULPS_EINVAL;
   for (int k = 0; k < 3; ++k)
     if (edims[k] < 1 || lo[k] < 0 || hi[k] > edims[k] || lo[k] >= hi[k]) return COULPS_EINVAL;
   if ((reinterpret_cast<uintptr_t>(s1_bf16) | reinterpret_cast<uintptr_t>(s2_bf16) |
-       reinterpret_cast<uintptr_t>(kpack)) & 15)
+       reinterpret_cast<uintptr_t>(a2_bf16) | reinterpret_cast<uintptr_t>(kpack)) & 15)
     return COULPS_EINVAL;
   RegionRuns r{};
   r.ex = edims[0]; r.ey = edims[1]; r.ez = edims[2];
@@ -780,7 +832,8 @@ int coulps_cv_stein_region(const float *g16, const void *s1_bf16, const void *s2
   r.qy0 = std::max(lo[1] - 1, 0); r.nqy = std::min(hi[1] + 1, edims[1]) - r.qy0;
   r.qz0 = std::max(lo[2] - 1, 0); r.nqz = std::min(hi[2] + 1, edims[2]) - r.qz0;
   const int64_t nq = (int64_t)r.nqx * r.nqy * r.nqz;
-  if (scratch_doubles < nq * nb) return COULPS_EINVAL;
+  const int64_t nr_all = (int64_t)(hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2]);
+  if (scratch_doubles < (nq + nr_all) * nb) return COULPS_EINVAL;
   r.n_box = r.nrun[0] * r.nrun[1] * r.nrun[2];
   int64_t ctas = 0;
   const int64_t ncg = (nb + 63) / 64;
@@ -822,8 +875,13 @@ int coulps_cv_stein_region(const float *g16, const void *s1_bf16, const void *s2
   }
   cv_region_mma_kernel<<<(unsigned)ctas, kRgThreads, smem, s>>>(
       tm, (const __nv_bfloat16 *)s2_bf16, (const unsigned char *)kpack, r, scratch, err);
-  cv_region_finish_kernel<<<nb, kRedThreads, 0, s>>>(scratch, (int)nq, g16, Aphi, r.L, lo[0],
-                                                     lo[1], lo[2], hi[0], hi[1], hi[2], out);
+  const int nrx = hi[0] - lo[0], nry = hi[1] - lo[1], nrz = hi[2] - lo[2];
+  const int64_t nr = (int64_t)nrx * nry * nrz;
+  double *gpart = scratch + nq * nb;
+  cv_region_g_kernel<<<(unsigned)((nr * nb + kRedThreads - 1) / kRedThreads), kRedThreads, 0, s>>>(
+      (const __nv_bfloat16 *)a2_bf16, w3g, b3g, Aphi, r.L, nb, edims[0], edims[1], edims[2],
+      lo[0], lo[1], lo[2], nrx, nry, nrz, gpart);
+  cv_region_finish_kernel<<<nb, kRedThreads, 0, s>>>(scratch, (int)nq, gpart, (int)nr, out);
   return cudaGetLastError() == cudaSuccess ? COULPS_OK : COULPS_ECUDA;
 }
 

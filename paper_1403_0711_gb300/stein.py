@@ -579,12 +579,14 @@ class LocalSteinCV(SteinCV):
             dev = self.W1.device
             self._ev = {
                 "w1": pack_weights(self._w1p()), "w2": pack_weights(self.W2),
-                "w3": pack_weights(self._w3p()),
                 "b1": self.b1.detach().float().contiguous(), "b2": self.b2.detach().float().contiguous(),
-                "b3": self._b3p().detach().float().contiguous(),
                 # per class [e][c2][c1], packed below for the region kernel
                 "K": self.region_kernels().detach().float().permute(0, 3, 1, 2).contiguous(),
                 "M": charge_matrix(*self.weights()).detach().float().contiguous(),
+                # the last layer for the sites of R: [o][ci], o = 9 kz + 3 ky + kx
+                "w3g": self.weights()[2][0].detach().float().permute(1, 2, 3, 0)
+                       .reshape(27, 16).contiguous(),
+                "b3g": float(self.b3.detach()[0]),
                 "err": torch.zeros(1, dtype=torch.int32, device=dev),
             }
             # the class kernels as the region kernel's tensor-core operand
@@ -623,22 +625,22 @@ class LocalSteinCV(SteinCV):
             s1 = torch.empty_like(x0)
             a2 = torch.empty_like(x0)
             s2 = torch.empty_like(x0)
-            g16 = torch.empty(x0.shape, dtype=torch.float32, device=dev)
             for src, w, b, dst in ((x0, "w1", "b1", (a1, s1)), (a1, "w2", "b2", (a2, s2))):
                 coulps._check(lib.coulps_cv_conv3d_tanh(
                     _vp(src), _vp(ev[w]), _vp(ev[b]), _vp(dst[0]), _vp(dst[1]), 1, X, ey, ez, P,
                     _vp(ev["err"]), sp), "coulps_cv_conv3d_tanh")
-            coulps._check(lib.coulps_cv_conv3d(_vp(a2), _vp(ev["w3"]), _vp(ev["b3"]), _vp(g16), 1,
-                                               X, ey, ez, P, _vp(ev["err"]), sp),
-                          "coulps_cv_conv3d")
+            # the last layer is formed at the sites of R inside the region kernel
             if out is None:
                 out = torch.empty(n, dtype=torch.float64, device=dev)
-            scratch = torch.empty(self._q.shape[0] * n, dtype=torch.float64, device=dev)
+            nr = ((self.r_hi[0] - self.r_lo[0]) * (self.r_hi[1] - self.r_lo[1]) *
+                  (self.r_hi[2] - self.r_lo[2]))
+            scratch = torch.empty((self._q.shape[0] + nr) * n, dtype=torch.float64, device=dev)
             ed = (ctypes.c_int32 * 3)(*self.edims)
             rl = (ctypes.c_int32 * 3)(*self.r_lo)
             rh = (ctypes.c_int32 * 3)(*self.r_hi)
             coulps._check(lib.coulps_cv_stein_region(
-                _vp(g16), _vp(s1), _vp(s2), _vp(Aphi), _vp(ev["Kpack"]), n, ed, 1, rl, rh,
+                _vp(a2), _vp(ev["w3g"]), ev["b3g"], _vp(s1), _vp(s2), _vp(Aphi), _vp(ev["Kpack"]),
+                n, ed, 1, rl, rh,
                 _vp(scratch), scratch.numel(), _vp(out), _vp(ev["err"]), sp),
                 "coulps_cv_stein_region")
             nq = self._cq_xyz.shape[0]
