@@ -567,6 +567,15 @@ int coulps_cv_conv3d(const void *in_bf16, const void *wpack, const float *bias, 
 int coulps_cv_conv3d_tanh(const void *in_bf16, const void *wpack, const float *bias,
                           void *a_bf16, void *s_bf16, int nb, int Lx, int Ly, int Lz,
                           int x_period, int *err, void *stream);
+/* The same for the output rows y in [y0, y1) and planes z in [z0, z1) only
+ * (all x of them; the input is read one row and one plane around them, zero
+ * outside the box).  Other outputs are not written.  For layers whose
+ * consumers read only part of the box, such as the region terms below.
+ * Errors: EINVAL (an empty or out-of-box range), ECUDA. */
+int coulps_cv_conv3d_tanh_rows(const void *in_bf16, const void *wpack, const float *bias,
+                               void *a_bf16, void *s_bf16, int nb, int Lx, int Ly, int Lz,
+                               int x_period, int y0, int y1, int z0, int z1, int *err,
+                               void *stream);
 
 /* coulps_cv_conv3d_wgrad: weight gradient of coulps_cv_conv3d,
  *   dW[co][ci][o] = sum_{b, p} dh[b, p, co] a[b, p + o, ci]   (a = 0 outside),

@@ -37,7 +37,8 @@ EXPORTS = (
     "coulps_batch_run", "coulps_batch_sync", "coulps_batch_estimate", "coulps_batch_samples",
     "coulps_batch_field_get", "coulps_cv_pack_weights", "coulps_cv_conv3d",
     "coulps_cv_conv3d_wgrad", "coulps_cv_pack_field", "coulps_cv_activate", "coulps_cv_stein_sum",
-    "coulps_set_schedule", "coulps_cv_conv3d_tanh", "coulps_cv_pack_region",
+    "coulps_set_schedule", "coulps_cv_conv3d_tanh", "coulps_cv_conv3d_tanh_rows",
+    "coulps_cv_pack_region",
     "coulps_cv_stein_region", "coulps_cv_region_pack", "coulps_cv_record",
     "coulps_cv_chain_stats", "coulps_cv_estimate",
     "coulps_cv_reset", "coulps_cv_charge_term", "coulps_set_fused", "coulps_set_pass_tile",
@@ -148,6 +149,8 @@ def load(path: str | Path | None = None):
         "coulps_cv_stein_sum": (i32, [vp, vp, vp, vp, vp, vp, i32, i32, i32, i32, vp, i64, vp, vp]),
         "coulps_set_schedule": (i32, [vp, i32]),
         "coulps_cv_conv3d_tanh": (i32, [vp, vp, vp, vp, vp, i32, i32, i32, i32, i32, vp, vp]),
+        "coulps_cv_conv3d_tanh_rows": (i32, [vp, vp, vp, vp, vp, i32, i32, i32, i32, i32, i32, i32,
+                                             i32, i32, vp, vp]),
         "coulps_cv_pack_region": (i32, [vp, vp, P(ctypes.c_int32), P(ctypes.c_int32), i32, vp,
                                         vp]),
         "coulps_cv_region_pack": (i32, [vp, vp, vp]),

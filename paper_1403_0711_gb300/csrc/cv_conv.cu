@@ -80,9 +80,10 @@ struct CvConvArgs {
   int mode;
   int Lx, Ly, Lz, nb;
   int x_period;        // > 0: output columns x with x % x_period == x_period - 1 are 0
-  int n_cols;          // nb * Lz * ceil(Lx / 128): one column = all y of (b, z, x tile)
+  int y0, y1, z0, z1;  // output rows computed: y in [y0, y1), z in [z0, z1)
+  int n_cols;          // nb * (z1 - z0) * ceil(Lx / 128): one column = the y rows of (b, z, x tile)
   int y_chunk;         // rows of y per work item
-  int n_items;         // n_cols * ceil(Ly / y_chunk)
+  int n_items;         // n_cols * ceil((y1 - y0) / y_chunk)
   int *err;
 };
 
@@ -198,15 +199,16 @@ __global__ void __launch_bounds__(kCvThreads, 3) cv_conv3d_kernel(const CvConvAr
     }
   };
 
-  const int n_chunks = (a.Ly + a.y_chunk - 1) / a.y_chunk;
+  const int n_chunks = (a.y1 - a.y0 + a.y_chunk - 1) / a.y_chunk;
+  const int nz = a.z1 - a.z0;
   for (int item = blockIdx.x; item < a.n_items && !aborted; item += gridDim.x) {
     int r = item / n_chunks;
-    const int ylo = (item % n_chunks) * a.y_chunk;
-    const int ny = min(a.y_chunk, a.Ly - ylo);
+    const int ylo = a.y0 + (item % n_chunks) * a.y_chunk;
+    const int ny = min(a.y_chunk, a.y1 - ylo);
     const int x0 = (r % xt) * kTileX;
     r /= xt;
-    const int z = r % a.Lz;
-    const int b = r / a.Lz;
+    const int z = a.z0 + r % nz;
+    const int b = r / nz;
     const int nrows = ny + 2;  // row k of the item is input row ylo - 1 + k
     // rows 0 .. 2 before the first tile (nrows >= 3), all loads in flight
     {
@@ -308,7 +310,7 @@ __global__ void __launch_bounds__(kCvThreads, 3) cv_conv3d_kernel(const CvConvAr
 
 int cv_conv3d_launch(const void *in_bf16, const void *wpack, const float *bias, float *out,
                      void *out_a, void *out_s, int nb, int Lx, int Ly, int Lz, int x_period,
-                     int *err, cudaStream_t s) {
+                     int y0, int y1, int z0, int z1, int *err, cudaStream_t s) {
   CvConvArgs a;
   a.in = reinterpret_cast<const __nv_bfloat16 *>(in_bf16);
   a.wpack = reinterpret_cast<const uint4 *>(wpack);
@@ -319,7 +321,8 @@ int cv_conv3d_launch(const void *in_bf16, const void *wpack, const float *bias, 
   a.mode = out ? 0 : 1;
   a.Lx = Lx; a.Ly = Ly; a.Lz = Lz; a.nb = nb;
   a.x_period = x_period;
-  a.n_cols = nb * Lz * ((Lx + kTileX - 1) / kTileX);
+  a.y0 = y0; a.y1 = y1; a.z0 = z0; a.z1 = z1;
+  a.n_cols = nb * (z1 - z0) * ((Lx + kTileX - 1) / kTileX);
   a.err = err;
   static bool configured = false;
   const int smem = kCvSmem + 128;  // + alignment slack
@@ -361,10 +364,11 @@ int cv_conv3d_launch(const void *in_bf16, const void *wpack, const float *bias, 
   // rows per item: whole columns when there are enough of them, else chunks
   // of at least 2 rows, so that about two items per resident CTA exist
   const int slots = sms * per_sm;
-  a.y_chunk = Ly;
-  while (a.y_chunk > 2 && (int64_t)a.n_cols * ((Ly + a.y_chunk - 1) / a.y_chunk) < 2 * slots)
+  const int ny = y1 - y0;
+  a.y_chunk = ny;
+  while (a.y_chunk > 2 && (int64_t)a.n_cols * ((ny + a.y_chunk - 1) / a.y_chunk) < 2 * slots)
     a.y_chunk = (a.y_chunk + 1) / 2;
-  a.n_items = a.n_cols * ((Ly + a.y_chunk - 1) / a.y_chunk);
+  a.n_items = a.n_cols * ((ny + a.y_chunk - 1) / a.y_chunk);
   int grid = slots;
   if (grid > a.n_items) grid = a.n_items;
   if (grid < 1) return COULPS_OK;
@@ -406,7 +410,7 @@ extern "C" int coulps_cv_conv3d(const void *in_bf16, const void *wpack, const fl
                           reinterpret_cast<uintptr_t>(out);
   if (align & 15) return COULPS_EINVAL;
   return coulps::cv_conv3d_launch(in_bf16, wpack, bias, out, nullptr, nullptr, nb, Lx, Ly, Lz,
-                                  x_period, err, static_cast<cudaStream_t>(stream));
+                                  x_period, 0, Ly, 0, Lz, err, static_cast<cudaStream_t>(stream));
 }
 
 extern "C" int coulps_cv_conv3d_tanh(const void *in_bf16, const void *wpack, const float *bias,
@@ -419,5 +423,20 @@ extern "C" int coulps_cv_conv3d_tanh(const void *in_bf16, const void *wpack, con
                           reinterpret_cast<uintptr_t>(a_bf16) | reinterpret_cast<uintptr_t>(s_bf16);
   if (align & 15) return COULPS_EINVAL;
   return coulps::cv_conv3d_launch(in_bf16, wpack, bias, nullptr, a_bf16, s_bf16, nb, Lx, Ly, Lz,
-                                  x_period, err, static_cast<cudaStream_t>(stream));
+                                  x_period, 0, Ly, 0, Lz, err, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int coulps_cv_conv3d_tanh_rows(const void *in_bf16, const void *wpack,
+                                          const float *bias, void *a_bf16, void *s_bf16, int nb,
+                                          int Lx, int Ly, int Lz, int x_period, int y0, int y1,
+                                          int z0, int z1, int *err, void *stream) {
+  if (!in_bf16 || !wpack || !bias || !a_bf16 || !s_bf16 || !err) return COULPS_EINVAL;
+  if (nb < 1 || Lx < 1 || Ly < 1 || Lz < 1 || x_period < 0) return COULPS_EINVAL;
+  if (y0 < 0 || y1 > Ly || y0 >= y1 || z0 < 0 || z1 > Lz || z0 >= z1) return COULPS_EINVAL;
+  if ((int64_t)nb * Lz * ((Lx + 127) / 128) > 0x7fffffff) return COULPS_EINVAL;
+  const uintptr_t align = reinterpret_cast<uintptr_t>(in_bf16) | reinterpret_cast<uintptr_t>(wpack) |
+                          reinterpret_cast<uintptr_t>(a_bf16) | reinterpret_cast<uintptr_t>(s_bf16);
+  if (align & 15) return COULPS_EINVAL;
+  return coulps::cv_conv3d_launch(in_bf16, wpack, bias, nullptr, a_bf16, s_bf16, nb, Lx, Ly, Lz,
+                                  x_period, y0, y1, z0, z1, err, static_cast<cudaStream_t>(stream));
 }

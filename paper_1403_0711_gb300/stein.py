@@ -625,10 +625,15 @@ class LocalSteinCV(SteinCV):
             s1 = torch.empty_like(x0)
             a2 = torch.empty_like(x0)
             s2 = torch.empty_like(x0)
-            for src, w, b, dst in ((x0, "w1", "b1", (a1, s1)), (a1, "w2", "b2", (a2, s2))):
-                coulps._check(lib.coulps_cv_conv3d_tanh(
+            # rows and planes the region terms read: the first layer's outputs
+            # within 2 sites of R (s1 around R + 1, a1 for the second layer),
+            # the second layer's within 1 (s2 and a2 on R + 1)
+            for src, w, b, dst, m in ((x0, "w1", "b1", (a1, s1), 2), (a1, "w2", "b2", (a2, s2), 1)):
+                y0, y1 = max(self.r_lo[1] - m, 0), min(self.r_hi[1] + m, ey)
+                z0, z1 = max(self.r_lo[2] - m, 0), min(self.r_hi[2] + m, ez)
+                coulps._check(lib.coulps_cv_conv3d_tanh_rows(
                     _vp(src), _vp(ev[w]), _vp(ev[b]), _vp(dst[0]), _vp(dst[1]), 1, X, ey, ez, P,
-                    _vp(ev["err"]), sp), "coulps_cv_conv3d_tanh")
+                    y0, y1, z0, z1, _vp(ev["err"]), sp), "coulps_cv_conv3d_tanh_rows")
             # the last layer is formed at the sites of R inside the region kernel
             if out is None:
                 out = torch.empty(n, dtype=torch.float64, device=dev)
