@@ -492,15 +492,17 @@ __global__ void __launch_bounds__(kRgThreads)
   if (warp == 0) tmem_dealloc(tmem, 64);
 }
 
-// g_x (A phi)_x for every chain and site x of R, one thread each, into
-// gpart[chain][k] (k the site's index in R, x fastest).  g_x, the net's
-// output, is formed from the second layer's activations a2 and the last
-// layer's weights (w3g [o][ci], 27 x 16 floats holding BF16 values, o = 9 kz
-// + 3 ky + kx for the offset (kx, ky, kz) - 1, and bias b3g), summed in FP32:
-// only the sites of R need it.  Their neighbours lie in E, or outside the
-// lattice where E is clipped by its faces (zero padding, as in the convs).
-// (A tensor-core conv of all of E for the one output channel cost 20 us per
-// evaluation of 64 chains.)
+// g_x (A phi)_x for every chain and site x of R into gpart[chain][k] (k the
+// site's index in R, x fastest).  g_x, the net's output, is formed from the
+// second layer's activations a2 and the last layer's weights (w3g [o][ci], 27 x
+// 16 floats holding BF16 values, o = 9 kz + 3 ky + kx for the offset (kx, ky,
+// kz) - 1, and bias b3g): only the sites of R need it.  Their neighbours lie
+// in E, or outside the lattice where E is clipped by its faces (zero padding,
+// as in the convs).  Four lanes per site take the offsets o = j, j + 4, ...
+// (7, 7, 7 and 6 of them), all loads issued first; their FP32 sums are added
+// by a fixed xor butterfly.  (A tensor-core conv of all of E for the one
+// output channel cost 20 us per evaluation of 64 chains; one thread per site
+// with three rounds of loads, 14 us.)
 __global__ void __launch_bounds__(kRedThreads)
     cv_region_g_kernel(const __nv_bfloat16 *__restrict__ a2, const float *__restrict__ w3g,
                        float b3g, const float *__restrict__ Aphi, BoxLayout L, int nb, int ex,
@@ -510,43 +512,48 @@ __global__ void __launch_bounds__(kRedThreads)
   for (int i = threadIdx.x; i < 27 * 16; i += kRedThreads) w[i] = w3g[i];
   __syncthreads();
   const int nr = nrx * nry * nrz;
-  const int64_t i = (int64_t)blockIdx.x * kRedThreads + threadIdx.x;
-  if (i >= (int64_t)nr * nb) return;
-  const int chain = (int)(i / nr), k = (int)(i % nr);
+  const int64_t t = (int64_t)blockIdx.x * kRedThreads + threadIdx.x;
+  const int64_t i = t >> 2;  // (chain, site); whole warps stay for the shuffles
+  const int j = (int)(t & 3);
+  const bool live = i < (int64_t)nr * nb;
+  const int chain = live ? (int)(i / nr) : 0, k = live ? (int)(i % nr) : 0;
   const int x = lox + k % nrx, y = loy + (k / nrx) % nry, z = loz + k / (nrx * nry);
-  float g = b3g;
+  uint4 u[7][2];
 #pragma unroll
-  for (int dz = 0; dz < 3; ++dz) {
-    // the nine rows of one z plane: loads first, then the FMAs
-    uint4 u[9][2];
-#pragma unroll
-    for (int o9 = 0; o9 < 9; ++o9) {
-      const int xx = x + o9 % 3 - 1, yy = y + o9 / 3 - 1, zz = z + dz - 1;
-      const bool in = xx >= 0 && yy >= 0 && zz >= 0 && xx < ex && yy < ey && zz < ez;
-      u[o9][0] = u[o9][1] = make_uint4(0, 0, 0, 0);
-      if (in) {
-        const uint4 *ap = reinterpret_cast<const uint4 *>(
-            a2 + (chain * L.sb + zz * L.sz + yy * L.sy + xx) * 16);
-        u[o9][0] = ap[0];
-        u[o9][1] = ap[1];
-      }
-    }
-#pragma unroll
-    for (int o9 = 0; o9 < 9; ++o9) {
-      const __nv_bfloat162 *h0 = reinterpret_cast<const __nv_bfloat162 *>(&u[o9][0]);
-      const __nv_bfloat162 *h1 = reinterpret_cast<const __nv_bfloat162 *>(&u[o9][1]);
-      const float *wo = w + (9 * dz + o9) * 16;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const float2 p = __bfloat1622float2(h0[j]), q = __bfloat1622float2(h1[j]);
-        g = fmaf(wo[2 * j], p.x, g);
-        g = fmaf(wo[2 * j + 1], p.y, g);
-        g = fmaf(wo[8 + 2 * j], q.x, g);
-        g = fmaf(wo[9 + 2 * j], q.y, g);
-      }
+  for (int m = 0; m < 7; ++m) {
+    const int o = j + 4 * m;
+    const int xx = x + o % 3 - 1, yy = y + (o / 3) % 3 - 1, zz = z + o / 9 - 1;
+    const bool in = live && o < 27 && xx >= 0 && yy >= 0 && zz >= 0 && xx < ex && yy < ey &&
+                    zz < ez;
+    u[m][0] = u[m][1] = make_uint4(0, 0, 0, 0);
+    if (in) {
+      const uint4 *ap = reinterpret_cast<const uint4 *>(
+          a2 + (chain * L.sb + zz * L.sz + yy * L.sy + xx) * 16);
+      u[m][0] = ap[0];
+      u[m][1] = ap[1];
     }
   }
-  gpart[i] = (double)g * (double)Aphi[chain * L.sb + z * L.sz + y * L.sy + x];
+  float g = 0.f;
+#pragma unroll
+  for (int m = 0; m < 7; ++m) {
+    const int o = j + 4 * m;
+    if (o >= 27) continue;
+    const __nv_bfloat162 *h0 = reinterpret_cast<const __nv_bfloat162 *>(&u[m][0]);
+    const __nv_bfloat162 *h1 = reinterpret_cast<const __nv_bfloat162 *>(&u[m][1]);
+    const float *wo = w + o * 16;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float2 p = __bfloat1622float2(h0[q]), r = __bfloat1622float2(h1[q]);
+      g = fmaf(wo[2 * q], p.x, g);
+      g = fmaf(wo[2 * q + 1], p.y, g);
+      g = fmaf(wo[8 + 2 * q], r.x, g);
+      g = fmaf(wo[9 + 2 * q], r.y, g);
+    }
+  }
+  g += __shfl_xor_sync(0xffffffffu, g, 1);
+  g += __shfl_xor_sync(0xffffffffu, g, 2);
+  if (live && j == 0)
+    gpart[i] = (double)(g + b3g) * (double)Aphi[chain * L.sb + z * L.sz + y * L.sy + x];
 }
 
 // out[b] = sum_q part[b][q] - sum_k gpart[b][k], one CTA per chain (part
@@ -878,7 +885,8 @@ int coulps_cv_stein_region(const void *a2_bf16, const float *w3g, float b3g,
   const int nrx = hi[0] - lo[0], nry = hi[1] - lo[1], nrz = hi[2] - lo[2];
   const int64_t nr = (int64_t)nrx * nry * nrz;
   double *gpart = scratch + nq * nb;
-  cv_region_g_kernel<<<(unsigned)((nr * nb + kRedThreads - 1) / kRedThreads), kRedThreads, 0, s>>>(
+  cv_region_g_kernel<<<(unsigned)((4 * nr * nb + kRedThreads - 1) / kRedThreads), kRedThreads, 0,
+                       s>>>(
       (const __nv_bfloat16 *)a2_bf16, w3g, b3g, Aphi, r.L, nb, edims[0], edims[1], edims[2],
       lo[0], lo[1], lo[2], nrx, nry, nrz, gpart);
   cv_region_finish_kernel<<<nb, kRedThreads, 0, s>>>(scratch, (int)nq, gpart, (int)nr, out);
