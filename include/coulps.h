@@ -29,6 +29,9 @@
  *     non-finite sample) are recorded in a per-lattice error word and reported
  *     by the next synchronising call.
  *   - A handle must not be used from two host threads at once.
+ *   - One GPU per process (several processes for several GPUs): each kernel's
+ *     shared-memory size and per-SM occupancy are set up once, for the device
+ *     current at its first launch, and are not repeated for another device.
  */
 #ifndef COULPS_H
 #define COULPS_H
