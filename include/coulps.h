@@ -179,6 +179,22 @@ int coulps_run(coulps_lattice_t lat, coulps_charges_t ch, int n_therm, int n_mea
 int coulps_estimate(coulps_charges_t ch, double *mean, double *stderr_bm, double *tau_int,
                     int64_t *n);
 
+/* Pipelined estimates, for callers that read a result after every step
+ * without stalling the GPU on each read.  coulps_estimate_post queues, on the
+ * lattice's stream, a copy of the estimator state and of the lattice's error
+ * word as they will be after everything queued so far, into one of two
+ * pinned slots the set owns; it returns at once.  coulps_estimate_take waits
+ * for the oldest posted copy and returns what coulps_estimate would have
+ * returned at that point (the same pooling, and ETIMEOUT / ENONFINITE if the
+ * error word was set then).  At most two posts may be outstanding (EINVAL
+ * otherwise); take without an outstanding post is EINVAL.  A loop of
+ * (queue step k; post; take the result of step k - 1) keeps the next step
+ * queued while the host pools the last one.  Errors: EINVAL, ENOMEM (first
+ * post), ECUDA, ETIMEOUT, ENONFINITE (take). */
+int coulps_estimate_post(coulps_charges_t ch);
+int coulps_estimate_take(coulps_charges_t ch, double *mean, double *stderr_bm, double *tau_int,
+                         int64_t *n);
+
 /* Synchronise and copy the logged samples: QPe[(s*n_chains + k)*3 + {0,1,2}]
  * = (Q, P, e) of sample s of chain k, for s < min(samples taken, cap,
  * log_capacity).  *n receives the number of samples copied per chain. */

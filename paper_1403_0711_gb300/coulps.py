@@ -28,7 +28,8 @@ EXPORTS = (
     "coulps_lattice_create", "coulps_lattice_destroy", "coulps_set_stream",
     "coulps_lattice_info", "coulps_set_tile", "coulps_field_get", "coulps_field_set",
     "coulps_sweep", "coulps_sync", "coulps_charges_create", "coulps_charges_destroy",
-    "coulps_measure", "coulps_run", "coulps_estimate", "coulps_samples",
+    "coulps_measure", "coulps_run", "coulps_estimate", "coulps_estimate_post",
+    "coulps_estimate_take", "coulps_samples",
     "coulps_reset_stats", "coulps_checkpoint_save", "coulps_checkpoint_load",
     "coulps_charges_update", "coulps_chain_stats", "coulps_pool_stats", "coulps_set_profiling",
     "coulps_kernel_times", "coulps_measure_static",
@@ -113,6 +114,8 @@ def load(path: str | Path | None = None):
         "coulps_measure": (i32, [vp, vp]),
         "coulps_run": (i32, [vp, vp, i32, i32, i32, i32]),
         "coulps_estimate": (i32, [vp, P(f64), P(f64), P(f64), P(i64)]),
+        "coulps_estimate_post": (i32, [vp]),
+        "coulps_estimate_take": (i32, [vp, P(f64), P(f64), P(f64), P(i64)]),
         "coulps_samples": (i32, [vp, P(f64), i64, P(i64)]),
         "coulps_reset_stats": (i32, [vp]),
         "coulps_checkpoint_save": (i32, [vp, vp, ctypes.c_char_p]),
@@ -430,6 +433,20 @@ class Charges:
         n = ctypes.c_int64()
         _check(self._lib.coulps_estimate(self.handle, ctypes.byref(m), ctypes.byref(s),
                                          ctypes.byref(t), ctypes.byref(n)), "coulps_estimate")
+        return {"mean": m.value, "stderr": s.value, "tau_int": t.value, "n": n.value}
+
+    def estimate_post(self):
+        """Queue a copy of the estimator state as of everything queued so far
+        (coulps_estimate_post); at most two outstanding."""
+        _check(self._lib.coulps_estimate_post(self.handle), "coulps_estimate_post")
+
+    def estimate_take(self):
+        """The estimate of the oldest posted state (coulps_estimate_take)."""
+        m, s, t = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        n = ctypes.c_int64()
+        _check(self._lib.coulps_estimate_take(self.handle, ctypes.byref(m), ctypes.byref(s),
+                                              ctypes.byref(t), ctypes.byref(n)),
+               "coulps_estimate_take")
         return {"mean": m.value, "stderr": s.value, "tau_int": t.value, "n": n.value}
 
     def samples(self, cap=None):

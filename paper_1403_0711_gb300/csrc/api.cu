@@ -121,6 +121,12 @@ struct coulps_charges {
   double *d_partials = nullptr;  // scratch: [chain][nblk][2]
   double *d_stats = nullptr;     // [chain][kStatStride]
   double *d_cvstats = nullptr;   // [chain][kStatStride], control-variate samples
+  // coulps_estimate_post / _take: two pinned slots of the estimator state
+  // and the lattice's error word, each with the event that completes its copy
+  double *h_post = nullptr;  // [2][chain][kStatStride]
+  int *h_post_err = nullptr; // [2]
+  cudaEvent_t ev_post[2] = {nullptr, nullptr};
+  int64_t posted = 0, taken = 0;
   // off-lattice set: per particle 8 corner offsets, weights, weight gradients;
   // the last sample's Q per chain; running force sums [chain][particle][3]
   bool off = false;
@@ -1447,6 +1453,13 @@ void coulps_charges_destroy(coulps_charges_t C) {
     cudaEventSynchronize(C->staged);
     cudaEventDestroy(C->staged);
   }
+  for (int k = 0; k < 2; ++k)
+    if (C->ev_post[k]) {
+      cudaEventSynchronize(C->ev_post[k]);
+      cudaEventDestroy(C->ev_post[k]);
+    }
+  if (C->h_post) cudaFreeHost(C->h_post);
+  if (C->h_post_err) cudaFreeHost(C->h_post_err);
   if (C->h_idx) cudaFreeHost(C->h_idx);
   if (C->h_q) cudaFreeHost(C->h_q);
   if (C->gstaged) {
@@ -1655,6 +1668,45 @@ int coulps_estimate(coulps_charges_t C, double *mean, double *stderr_bm, double 
   int s = coulps_chain_stats(C, st.data(), (int64_t)st.size());
   if (s) return s;
   return coulps_pool_stats(st.data(), L->g.n_chains, mean, stderr_bm, tau_int, n);
+}
+
+int coulps_estimate_post(coulps_charges_t C) {
+  if (!C) return COULPS_EINVAL;
+  coulps_lattice *L = C->lat;
+  const size_t need = (size_t)L->g.n_chains * kStatStride;
+  if (C->posted - C->taken >= 2) return COULPS_EINVAL;  // both slots hold untaken states
+  if (!C->h_post) {
+    if (cudaMallocHost((void **)&C->h_post, 2 * need * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost((void **)&C->h_post_err, 2 * sizeof(int)) != cudaSuccess ||
+        cudaEventCreateWithFlags(&C->ev_post[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&C->ev_post[1], cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return COULPS_ENOMEM;
+    }
+  }
+  const int slot = (int)(C->posted & 1);
+  CK(cudaMemcpyAsync(C->h_post + slot * need, C->d_stats, need * sizeof(double),
+                     cudaMemcpyDeviceToHost, L->stream));
+  CK(cudaMemcpyAsync(C->h_post_err + slot, L->d_err, sizeof(int), cudaMemcpyDeviceToHost,
+                     L->stream));
+  CK(cudaEventRecord(C->ev_post[slot], L->stream));
+  ++C->posted;
+  return COULPS_OK;
+}
+
+int coulps_estimate_take(coulps_charges_t C, double *mean, double *stderr_bm, double *tau_int,
+                         int64_t *n) {
+  if (!C) return COULPS_EINVAL;
+  if (C->taken == C->posted) return COULPS_EINVAL;  // nothing posted
+  coulps_lattice *L = C->lat;
+  const size_t need = (size_t)L->g.n_chains * kStatStride;
+  const int slot = (int)(C->taken & 1);
+  CK(cudaEventSynchronize(C->ev_post[slot]));
+  ++C->taken;
+  const int e = C->h_post_err[slot];
+  if (e & kErrTimeout) return COULPS_ETIMEOUT;
+  if (e & kErrNonFinite) return COULPS_ENONFINITE;
+  return coulps_pool_stats(C->h_post + slot * need, L->g.n_chains, mean, stderr_bm, tau_int, n);
 }
 
 int coulps_samples(coulps_charges_t C, double *QPe, int64_t cap, int64_t *n) {

@@ -313,3 +313,49 @@ def test_phased_schedule_is_bitwise_identical(cl, stream, n_hb, n_or, chains, pr
     assert a[2] == b[2] and a[3] == b[3]
     if profiling:
         assert b[4]["mixed_n"] > 0 and a[4]["mixed_n"] == 0
+
+
+def test_pipelined_estimates_equal_synchronous(cl, stream):
+    """coulps_estimate_post / _take, one step behind, return for every step
+    exactly what coulps_estimate returns on an identical chain read
+    synchronously; the posting rules are enforced."""
+    from paper_1403_0711_gb300 import inputs
+    L = (24, 20, 18)
+    sites, q = inputs.plus_minus(L, 16, seed=5)
+
+    def chain():
+        lat = cl.Lattice(L, n_chains=6, precision=cl.F32, seed=41, stream=stream)
+        ch = cl.Charges(lat, sites, q)
+        ch.run(3, 0, 1, 3)
+        return lat, ch
+
+    lat, ch = chain()
+    sync = []
+    for _ in range(7):
+        ch.update(sites, q)
+        ch.run(0, 1, 1, 3)
+        sync.append(ch.estimate())
+    ch.close()
+    lat.close()
+
+    lat, ch = chain()
+    with pytest.raises(cl.CoulpsError):
+        ch.estimate_take()  # nothing posted
+    piped = []
+    for k in range(7):
+        ch.update(sites, q)
+        ch.run(0, 1, 1, 3)
+        ch.estimate_post()
+        if k > 0:
+            piped.append(ch.estimate_take())
+    piped.append(ch.estimate_take())
+    ch.estimate_post()
+    ch.estimate_post()
+    with pytest.raises(cl.CoulpsError):
+        ch.estimate_post()  # two states not taken yet
+    a, b = ch.estimate_take(), ch.estimate_take()
+    assert a == b == ch.estimate()
+    ch.close()
+    lat.close()
+    assert [e["n"] for e in piped] == [6 * (k + 1) for k in range(7)]
+    assert piped == sync
