@@ -685,15 +685,25 @@ int stage_gather(coulps_lattice *L, coulps_charges *C, Tile t) {
   }
   C->fused_nblk = ytiles * zslabs;
   if (!C->gstaged) {
-    if (cudaEventCreateWithFlags(&C->gstaged, cudaEventDisableTiming) != cudaSuccess) {
+    // all three or none: a failure leaves the set as it was
+    uint32_t *he = nullptr;
+    double *hq = nullptr;
+    cudaEvent_t ev = nullptr;
+    if (n > 0 && (cudaMallocHost((void **)&he, n * sizeof(uint32_t)) != cudaSuccess ||
+                  cudaMallocHost((void **)&hq, n * sizeof(double)) != cudaSuccess)) {
       cudaGetLastError();
-      return COULPS_ECUDA;
-    }
-    if (n > 0 && (cudaMallocHost((void **)&C->h_gent, n * sizeof(uint32_t)) != cudaSuccess ||
-                  cudaMallocHost((void **)&C->h_gq, n * sizeof(double)) != cudaSuccess)) {
-      cudaGetLastError();
+      if (he) cudaFreeHost(he);
       return COULPS_ENOMEM;
     }
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      if (he) cudaFreeHost(he);
+      if (hq) cudaFreeHost(hq);
+      return COULPS_ECUDA;
+    }
+    C->h_gent = he;
+    C->h_gq = hq;
+    C->gstaged = ev;
   } else {
     CK(cudaEventSynchronize(C->gstaged));  // the previous upload has left the staging
   }
@@ -1676,13 +1686,25 @@ int coulps_estimate_post(coulps_charges_t C) {
   const size_t need = (size_t)L->g.n_chains * kStatStride;
   if (C->posted - C->taken >= 2) return COULPS_EINVAL;  // both slots hold untaken states
   if (!C->h_post) {
-    if (cudaMallocHost((void **)&C->h_post, 2 * need * sizeof(double)) != cudaSuccess ||
-        cudaMallocHost((void **)&C->h_post_err, 2 * sizeof(int)) != cudaSuccess ||
-        cudaEventCreateWithFlags(&C->ev_post[0], cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&C->ev_post[1], cudaEventDisableTiming) != cudaSuccess) {
+    // all four or none: a failure leaves the set as it was
+    double *hp = nullptr;
+    int *he = nullptr;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    if (cudaMallocHost((void **)&hp, 2 * need * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost((void **)&he, 2 * sizeof(int)) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming) != cudaSuccess) {
       cudaGetLastError();
+      if (hp) cudaFreeHost(hp);
+      if (he) cudaFreeHost(he);
+      for (cudaEvent_t e : ev)
+        if (e) cudaEventDestroy(e);
       return COULPS_ENOMEM;
     }
+    C->h_post = hp;
+    C->h_post_err = he;
+    C->ev_post[0] = ev[0];
+    C->ev_post[1] = ev[1];
   }
   const int slot = (int)(C->posted & 1);
   CK(cudaMemcpyAsync(C->h_post + slot * need, C->d_stats, need * sizeof(double),
@@ -2255,12 +2277,21 @@ int coulps_charges_update(coulps_charges_t C, const int32_t *site, const double 
   const Geometry &g = L->g;
   const int64_t n = C->n;
   if (!C->h_idx) {
-    if (cudaMallocHost((void **)&C->h_idx, sizeof(uint32_t) * (size_t)n) != cudaSuccess ||
-        cudaMallocHost((void **)&C->h_q, sizeof(double) * (size_t)n) != cudaSuccess ||
-        cudaEventCreateWithFlags(&C->staged, cudaEventDisableTiming) != cudaSuccess) {
+    // all three or none: a failure leaves the set as it was
+    uint32_t *hi = nullptr;
+    double *hq = nullptr;
+    cudaEvent_t ev = nullptr;
+    if (cudaMallocHost((void **)&hi, sizeof(uint32_t) * (size_t)n) != cudaSuccess ||
+        cudaMallocHost((void **)&hq, sizeof(double) * (size_t)n) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
       cudaGetLastError();
+      if (hi) cudaFreeHost(hi);
+      if (hq) cudaFreeHost(hq);
       return COULPS_ENOMEM;
     }
+    C->h_idx = hi;
+    C->h_q = hq;
+    C->staged = ev;
   } else {
     // the previous upload must have left the staging buffers
     CK(cudaEventSynchronize(C->staged));

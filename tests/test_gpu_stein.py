@@ -433,3 +433,43 @@ def test_record_graph_matches_eager(env):
         ch.close()
         lat.close()
     assert np.array_equal(stats[0], stats[1])
+
+
+def test_region_pack_format(env):
+    """coulps_cv_region_pack writes, for every class, the three BF16 parts of K
+    (each the round-to-nearest-even BF16 of what the parts before it leave) at
+    the documented byte offsets, and the parts add back to K exactly."""
+    torch, coulps, stream = env
+    rng = np.random.default_rng(11)
+    K = (rng.standard_normal((216, 27, 16, 16)) * np.exp(rng.uniform(-6, 3, (216, 27, 16, 16))))
+    K = K.astype(np.float32)
+    dK = torch.from_numpy(K).cuda()
+    out = torch.empty(216 * 41472, dtype=torch.uint8, device="cuda")
+    lib = coulps.load()
+    import ctypes
+    st = lib.coulps_cv_region_pack(ctypes.c_void_p(dK.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                   ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == 0
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().view(np.uint16).reshape(216, 41472 // 2)
+
+    def bf16(x):  # float32 -> (bits, value), round to nearest even
+        b = x.view(np.uint32).astype(np.uint64)
+        r = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16).astype(np.uint16)
+        return r, (r.astype(np.uint32) << 16).view(np.float32)
+
+    want = np.zeros_like(got)
+    x = K.copy()
+    parts = []
+    for p in range(3):
+        bits, val = bf16(x)
+        parts.append(val)
+        x = (x - val).astype(np.float32)
+        e, c2, c1 = np.meshgrid(np.arange(27), np.arange(16), np.arange(16), indexing="ij")
+        n = 16 * p + c2
+        off = (e * 1536 + (n // 8) * 128 + (c1 // 8) * 768 + (n % 8) * 16 + (c1 % 8) * 2) // 2
+        want[:, off] = bits
+    assert np.array_equal(got, want)
+    total = parts[0].astype(np.float64) + parts[1] + parts[2]
+    assert np.array_equal(total.astype(np.float32), K)
+    assert np.max(np.abs(total - K.astype(np.float64)) / np.abs(K)) < 2.0 ** -24
