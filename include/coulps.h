@@ -52,7 +52,7 @@ extern "C" {
 #define COULPS_ENONFINITE (-5)   /* a sample or running sum became non-finite   */
 #define COULPS_EIO (-6)          /* checkpoint file could not be read/written   */
 #define COULPS_ECORRUPT (-7)     /* checkpoint checksum / header mismatch       */
-#define COULPS_EUNSUPPORTED (-8) /* shape or mode this build does not handle    */
+#define COULPS_EUNSUPPORTED (-8) /* shape or mode the library does not handle   */
 
 #define COULPS_F32 0 /* field and sweeps in FP32, estimator sums in FP64 */
 #define COULPS_F64 1 /* field, sweeps and estimator in FP64              */
