@@ -105,15 +105,23 @@ __device__ __forceinline__ float2 pset(float c) { return make_float2(c, c); }
 __device__ __forceinline__ double2 pset(double c) { return make_double2(c, c); }
 
 // The heatbath deviates of one quad's four Philox words as two pairs (sites
-// 0, 1 and 2, 3): FP32 as two packed pairs under one tail vote of the active
-// lanes (no divergent branch per site; measured 0.156 against 0.159 ms per
-// heatbath half-sweep at 128^3 x 64 chains), FP64 word by word.  Bitwise
-// those of Noise<T>::of per word.
+// 0, 1 and 2, 3): FP32 as packed pairs, each under its own tail vote of the
+// active lanes (no divergent branch per site), FP64 word by word.  Bitwise
+// those of Noise<T>::of per word.  A warp's vote over 64 words finds a tail
+// word (v >= 7, probability 0.0039 per word) 22% of the time, one over the
+// quad's 128 words 39%: measured at 128^3 x 64 chains, 0.1498 against 0.1538
+// ms per heatbath half-sweep with neighbour sums on packed pairs (before
+// those, the vote per quad measured faster than a vote per site: 0.156
+// against 0.159 ms).
 template <typename T> struct QuadNoise2;
 template <> struct QuadNoise2<float> {
   __device__ __forceinline__ static void of(uint4 w, float2 (&n)[2]) {
-    const uint32_t u[4] = {w.x, w.y, w.z, w.w};
-    hb_noise_pairs_f32<2>(u, n);
+    const uint32_t u0[2] = {w.x, w.y}, u1[2] = {w.z, w.w};
+    float2 a[1], b[1];
+    hb_noise_pairs_f32<1>(u0, a);
+    hb_noise_pairs_f32<1>(u1, b);
+    n[0] = a[0];
+    n[1] = b[0];
   }
 };
 template <> struct QuadNoise2<double> {
