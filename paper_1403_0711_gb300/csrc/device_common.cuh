@@ -61,33 +61,33 @@ template <> __device__ __forceinline__ float bcast<float>(float c) { return c; }
 template <> __device__ __forceinline__ float2 bcast<float2>(float c) { return make_float2(c, c); }
 
 template <typename V>
-__device__ __forceinline__ V erfcinv_q_main(V z) {  // z = v - 3.5, v < 7
-  V q = bcast<V>(-1.9502296e-10f);
-  q = vfma(q, z, bcast<V>(8.8274743e-10f));
-  q = vfma(q, z, bcast<V>(2.0195072e-08f));
-  q = vfma(q, z, bcast<V>(-2.3665939e-07f));
-  q = vfma(q, z, bcast<V>(-3.1320127e-07f));
-  q = vfma(q, z, bcast<V>(2.9303386e-05f));
-  q = vfma(q, z, bcast<V>(-0.00025333301f));
-  q = vfma(q, z, bcast<V>(-0.0010796369f));
-  q = vfma(q, z, bcast<V>(0.098941647f));
-  q = vfma(q, z, bcast<V>(0.85629088f));
+__device__ __forceinline__ V erfcinv_q_main(V z) {  // z = v - 4.5, v < 9
+  V q = bcast<V>(9.4230197e-12f);
+  q = vfma(q, z, bcast<V>(-9.9730543e-11f));
+  q = vfma(q, z, bcast<V>(-7.3713374e-10f));
+  q = vfma(q, z, bcast<V>(1.8971662e-08f));
+  q = vfma(q, z, bcast<V>(-9.0245905e-08f));
+  q = vfma(q, z, bcast<V>(-1.2787358e-06f));
+  q = vfma(q, z, bcast<V>(2.4949235e-05f));
+  q = vfma(q, z, bcast<V>(-0.00014325297f));
+  q = vfma(q, z, bcast<V>(-0.0016700856f));
+  q = vfma(q, z, bcast<V>(0.096136749f));
+  q = vfma(q, z, bcast<V>(0.95392835f));
   return q;
 }
 
 template <typename V>
-__device__ __forceinline__ V erfcinv_q_tail(V z) {  // z = sqrt(v) - 3.6, v >= 7
-  V q = bcast<V>(-1.7354193e-06f);
-  q = vfma(q, z, bcast<V>(1.368092e-05f));
-  q = vfma(q, z, bcast<V>(-3.4650988e-05f));
-  q = vfma(q, z, bcast<V>(-1.0538802e-05f));
-  q = vfma(q, z, bcast<V>(0.00027573694f));
-  q = vfma(q, z, bcast<V>(-0.00083418511f));
-  q = vfma(q, z, bcast<V>(0.0015974527f));
-  q = vfma(q, z, bcast<V>(-0.0025665793f));
-  q = vfma(q, z, bcast<V>(0.003804483f));
-  q = vfma(q, z, bcast<V>(0.48145521f));
-  q = vfma(q, z, bcast<V>(1.6339988f));
+__device__ __forceinline__ V erfcinv_q_tail(V z) {  // z = sqrt(v) - 3.6, v >= 9
+  V q = bcast<V>(6.5457465e-07f);
+  q = vfma(q, z, bcast<V>(8.3999657e-07f));
+  q = vfma(q, z, bcast<V>(-4.7697853e-05f));
+  q = vfma(q, z, bcast<V>(0.00027278936f));
+  q = vfma(q, z, bcast<V>(-0.00080441934f));
+  q = vfma(q, z, bcast<V>(0.001587657f));
+  q = vfma(q, z, bcast<V>(-0.0025733677f));
+  q = vfma(q, z, bcast<V>(0.0038068402f));
+  q = vfma(q, z, bcast<V>(0.48145568f));
+  q = vfma(q, z, bcast<V>(1.6339986f));
   return q;
 }
 
@@ -98,19 +98,23 @@ __device__ __forceinline__ V erfcinv_q_tail(V z) {  // z = sqrt(v) - 3.6, v >= 7
 // erfc^-1(u) / sqrt(3) = x q(v) with v = -log2(u (2 - u)) = -log2(u + u x);
 // q is smooth in v (the change of variable of M. Giles, "Approximating the
 // erfinv function", GPU Computing Gems, 2011, here in base 2) and is taken
-// as a degree-9 polynomial in v - 3.5 for v < 7 and a degree-10 polynomial in
+// as a degree-10 polynomial in v - 4.5 for v < 9 and a degree-9 polynomial in
 // sqrt(v) - 3.6 above (u >= 2^-32 keeps v < 32); 1/sqrt(3) is folded into
 // the coefficients.  Coefficients: our own weighted least-squares fit
-// (fit_erfcinv.py beside this file; fit error 3.6e-9 and 2.9e-8 relative).
-// Measured against FP64 erfc^-1 over the whole range: a few FP32 ulps.
+// (fit_erfcinv.py beside this file; fit error 5.5e-9 and 2.9e-8 relative;
+// emulated FP32 evaluation 2.5e-7 relative at most).  The split at v = 9
+// (u < 2^-10 or so, 1e-3 of the words) rather than 7 makes the tail rare
+// enough that a warp's vote over 64 words takes it 6% of the time instead of
+// 22%, for one more term in the common polynomial.  Measured against FP64
+// erfc^-1 over the whole range: a few FP32 ulps.
 __device__ __forceinline__ float hb_noise_f32(uint32_t w) {
   const uint32_t s = hb_small_side(w);
   const float u = fmaf(__uint2float_rn(s), 0x1p-31f, 0x1p-32f);
   const float x = fmaf(__uint2float_rn(0x7fffffffu - s), 0x1p-31f, 0x1p-32f);
   const float v = -__log2f(fmaf(u, x, u));
   float q;
-  if (v < 7.0f)
-    q = erfcinv_q_main(v - 3.5f);
+  if (v < 9.0f)
+    q = erfcinv_q_main(v - 4.5f);
   else
     q = erfcinv_q_tail(sqrtf(v) - 3.6f);
   // w < 2^31 (2r < 1): a negative term; the sign goes onto x (exact)
@@ -136,16 +140,16 @@ __device__ __forceinline__ void hb_noise_pairs_f32(const uint32_t (&w)[2 * NP], 
         half);
     const float2 t = __ffma2_rn(u, x[p], u);
     v[p] = make_float2(-__log2f(t.x), -__log2f(t.y));
-    q[p] = erfcinv_q_main(__fadd2_rn(v[p], make_float2(-3.5f, -3.5f)));
-    tail = tail || !(v[p].x < 7.0f) || !(v[p].y < 7.0f);
+    q[p] = erfcinv_q_main(__fadd2_rn(v[p], make_float2(-4.5f, -4.5f)));
+    tail = tail || !(v[p].x < 9.0f) || !(v[p].y < 9.0f);
   }
   if (__any_sync(__activemask(), tail)) {
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
       const float2 qt = erfcinv_q_tail(
           __fadd2_rn(make_float2(sqrtf(v[p].x), sqrtf(v[p].y)), make_float2(-3.6f, -3.6f)));
-      q[p].x = v[p].x < 7.0f ? q[p].x : qt.x;
-      q[p].y = v[p].y < 7.0f ? q[p].y : qt.y;
+      q[p].x = v[p].x < 9.0f ? q[p].x : qt.x;
+      q[p].y = v[p].y < 9.0f ? q[p].y : qt.y;
     }
   }
 #pragma unroll

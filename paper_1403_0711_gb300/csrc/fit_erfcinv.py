@@ -5,9 +5,9 @@ The deviate needs erfc^-1(u) / sqrt(3) for u in (0, 1].  It is written as
 x q(v) with x = 1 - u and v = -log2(u (2 - u)) = -log2(u (1 + x)), the change
 of variable of M. Giles ("Approximating the erfinv function", GPU Computing
 Gems Jade Edition, 2011) taken in base 2 so that the device's log2 is used
-as is: q is smooth in v, so two polynomials cover the range, one in v - 3.5
-for v < 7 and one in sqrt(v) - 3.6 for 7 <= v <= 33 (u >= 2^-32 keeps
-v < 32).  The factor 1/sqrt(3) of Eq. (phi) is folded into q.  The
+as is: q is smooth in v, so two polynomials cover the range, one of degree
+10 in v - 4.5 for v < 9 and one of degree 9 in sqrt(v) - 3.6 for
+9 <= v <= 33 (u >= 2^-32 keeps v < 32).  The factor 1/sqrt(3) of Eq. (phi) is folded into q.  The
 coefficients are fitted here from scratch: least squares on Chebyshev nodes,
 weighted by 1/q (relative error), reweighted a few times towards the
 equal-ripple (minimax) solution, against scipy's erfcinv in FP64.
@@ -19,9 +19,9 @@ import numpy as np
 from scipy.special import erfcinv
 
 N_NODES = 4000
-SPLIT = 7.0
-CENTRAL = (0.0, SPLIT, False, 3.5, 9)   # v range, in sqrt(v)?, centre, degree
-TAIL = (SPLIT, 33.0, True, 3.6, 10)
+SPLIT = 9.0
+CENTRAL = (0.0, SPLIT, False, 4.5, 10)  # v range, in sqrt(v)?, centre, degree
+TAIL = (SPLIT, 33.0, True, 3.6, 9)
 
 
 def target(v):
@@ -79,7 +79,7 @@ def emulate_fp32(central, tail, n=2_000_000, seed=0):
 def main():
     central, e1 = fit(*CENTRAL)
     tail, e2 = fit(*TAIL)
-    for name, c, e in (("central (v - 3.5)", central, e1), ("tail (sqrt(v) - 3.6)", tail, e2)):
+    for name, c, e in (("central (v - 4.5)", central, e1), ("tail (sqrt(v) - 3.6)", tail, e2)):
         print(f"{name}: max relative fit error {e:.2e}")
         print("  " + ", ".join(f"{float(np.float32(v)):.8g}f" for v in c))
     print(f"emulated FP32 evaluation: max relative error {emulate_fp32(central, tail):.2e}")

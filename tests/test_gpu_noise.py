@@ -29,9 +29,10 @@ def _words():
     edges = np.array([0, 1, 2, 3, 2**31 - 3, 2**31 - 2, 2**31 - 1, 2**31, 2**31 + 1, 2**31 + 2,
                       2**32 - 3, 2**32 - 2, 2**32 - 1], dtype=np.uint64)
     w.append(edges)
-    # around the branch: u (2 - u) = e^-5, u = 1 - sqrt(1 - e^-5)
-    s5 = int((1.0 - np.sqrt(1.0 - np.exp(-5.0))) * 2**31)
-    near = np.arange(s5 - 2000, s5 + 2000, dtype=np.uint64)
+    # around the FP32 deviate's switch between its two polynomials:
+    # v = -log2(u (2 - u)) = 9, u = 1 - sqrt(1 - 2^-9)
+    s9 = int((1.0 - np.sqrt(1.0 - 2.0**-9)) * 2**31)
+    near = np.arange(s9 - 2000, s9 + 2000, dtype=np.uint64)
     w += [near, (2**32 - 1) - near]
     # the first and last 20000 words of each side (r -> 0, r -> 1/2, r -> 1)
     k = np.arange(20000, dtype=np.uint64)
