@@ -12,18 +12,20 @@
 //
 // Work decomposition.  One CTA owns a tile of TY rows (all of x) of one
 // chain and marches through DZ consecutive z planes.  For each plane it needs
-// the other colour's planes z-1, z, z+1; these are streamed through a 4-slot
+// the other colour's planes z-1, z, z+1; these are streamed through a
 // shared-memory ring by TMA (one 4D box = TY+2 rows x W elements, the rows
-// y0-1 .. y0+TY of one plane), three planes ahead of use, each slot guarded
+// y0-1 .. y0+TY of one plane; 8 slots, the CTA synchronising once every 4
+// planes and then refilling the slots it has finished), each slot guarded
 // by an mbarrier.  Out-of-range rows and planes (y = -1, y = Ly, z = -1,
 // z = Lz) arrive zero-filled from the TMA unit, which is exactly the
 // Dirichlet ghost layer.  Each thread owns one quad of four same-colour sites
 // of one row and keeps the quad's values of planes z-1 and z in registers, so
 // per plane it reads from shared memory the quad of plane z+1, the quads of
 // rows y-1 and y+1 and one scalar for the x neighbour that lies in the next
-// or previous quad.  Over-relaxation also streams its own colour's plane
-// (TY rows) through the same ring.  Results go straight to global memory as
-// 16-byte (FP32) or 2 x 16-byte (FP64) stores.
+// or previous quad (FP32 heatbath: two quads per thread).  Over-relaxation
+// also streams its own colour's plane (TY rows) through the same ring.
+// Results go straight to global memory as 16-byte (FP32) or 2 x 16-byte
+// (FP64) stores.
 //
 // Fused gather.  On the last half-sweep of a measured compound sweep the
 // kernel also forms the tile's share of Q = sum q_i phi(r_i) and
